@@ -1,0 +1,102 @@
+"""Dense FP64 Gaussian-process oracle (numpy).
+
+TEST INFRASTRUCTURE ONLY: tests/, the smoke check and bench.py's CPU-baseline
+leg may import this module; the product package never does.
+
+Follows the paper's Sec. 2.2 and 2.3:
+  - Eq. quadraticKernelEq: K(x_i, x_j) = sf2 * exp(-d_ij^2 / (2 l2));
+  - Eq. d2Eq: d_ij^2 = sum_k ((x_ik - x_jk) / Dbar_k)^2, with Dbar_k the mean
+    separation between database inputs along dimension k (reading: the mean of
+    |x_ik - x_jk| over all pairs i < j; recomputed whenever the database
+    changes; a fallback scale when fewer than two entries or a zero spread);
+  - Eq. covarianceEq: C = K(X, X) + sn2 I;
+  - Eq. predMeanEq: mean = mu(X*) + K(X*, X) C^-1 (y - mu(X));
+  - Eq. predVarEq: var = diag(K(X*, X*) - K(X*, X) C^-1 K(X, X*)), the latent
+    variance with no noise term, clamped at zero;
+  - Eq. evidenceEq: log marginal likelihood.
+The Cholesky factorisation and triangular solves are numpy/scipy library
+primitives used as single steps.
+"""
+import numpy as np
+import scipy.linalg as sla
+
+
+def scales(X, fallback=1.0):
+    """Dbar_k: mean over all pairs i < j of |x_ik - x_jk| (Eq. d2Eq reading)."""
+    X = np.asarray(X, dtype=np.float64)
+    M, D = X.shape
+    fb = np.broadcast_to(np.asarray(fallback, dtype=np.float64), (D,))
+    out = np.array(fb, dtype=np.float64)
+    if M < 2:
+        return out
+    for k in range(D):
+        tot = 0.0
+        for i in range(M):
+            tot += np.abs(X[i + 1:, k] - X[i, k]).sum()
+        mean = tot / (M * (M - 1) / 2)
+        if mean > 0.0:
+            out[k] = mean
+    return out
+
+
+def sq_dist(A, B, dbar):
+    """Normalised squared distances d_ij^2 between rows of A and B (Eq. d2Eq)."""
+    A = np.asarray(A, dtype=np.float64) / dbar
+    B = np.asarray(B, dtype=np.float64) / dbar
+    diff = A[:, None, :] - B[None, :, :]
+    return (diff * diff).sum(axis=2)
+
+
+def kernel(A, B, dbar, sf2, l2):
+    """Squared-exponential covariance (Eq. quadraticKernelEq)."""
+    return sf2 * np.exp(-sq_dist(A, B, dbar) / (2.0 * l2))
+
+
+class GP:
+    """Fit on (X, y) with hyperparameters (sf2, l2, sn2) and an optional prior
+    mean function mu (callable on an (n, D) array; zero by default)."""
+
+    def __init__(self, X, y, sf2, l2, sn2, mu=None, dbar=None, fallback=1.0):
+        self.X = np.asarray(X, dtype=np.float64).reshape(len(y), -1) if len(y) else np.zeros((0, 1))
+        self.y = np.asarray(y, dtype=np.float64)
+        self.sf2, self.l2, self.sn2 = float(sf2), float(l2), float(sn2)
+        self.mu = mu
+        self.M = len(self.y)
+        if self.M == 0:
+            self.dbar = None
+            return
+        self.dbar = scales(self.X, fallback) if dbar is None else np.asarray(dbar, dtype=np.float64)
+        C = kernel(self.X, self.X, self.dbar, self.sf2, self.l2) + self.sn2 * np.eye(self.M)
+        self.C = C
+        self.L = np.linalg.cholesky(C)                              # C = L L^T
+        r = self.y - self._mu(self.X)
+        self.alpha = sla.cho_solve((self.L, True), r)               # C^-1 (y - mu(X))
+
+    def _mu(self, X):
+        if self.mu is None:
+            return np.zeros(len(X))
+        return np.asarray(self.mu(X), dtype=np.float64).reshape(len(X))
+
+    def predict(self, Xs):
+        """Posterior mean and latent variance at the rows of Xs."""
+        Xs = np.asarray(Xs, dtype=np.float64).reshape(len(Xs), -1)
+        m0 = self._mu(Xs)
+        if self.M == 0:
+            return m0, np.full(len(Xs), self.sf2)
+        Ks = kernel(Xs, self.X, self.dbar, self.sf2, self.l2)      # K(X*, X)
+        mean = m0 + Ks @ self.alpha
+        V = sla.solve_triangular(self.L, Ks.T, lower=True)          # L^-1 K(X, X*)
+        var = self.sf2 - (V * V).sum(axis=0)
+        return mean, np.maximum(var, 0.0)
+
+    def log_marginal_likelihood(self):
+        """Eq. evidenceEq with y replaced by y - mu(X)."""
+        r = self.y - self._mu(self.X)
+        return (-0.5 * r @ self.alpha - np.log(np.diag(self.L)).sum()
+                - 0.5 * self.M * np.log(2.0 * np.pi))
+
+
+def gate(sd, sigma_t):
+    """Alg. 1: an MD run is requested when the predicted standard deviation
+    exceeds the threshold (strict inequality)."""
+    return np.asarray(sd) > sigma_t

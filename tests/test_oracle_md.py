@@ -1,0 +1,227 @@
+"""Pins for the FP64 micro-element oracle (oracle/md_oracle.c).
+
+Each check ties the oracle to something other than itself: published
+known-answer vectors, closed forms of Eq. LJ, an independently coded
+all-pairs sum, energy derivatives, conservation laws, and equipartition.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.stats
+
+from oracle import md
+from tests.conftest import read_golden
+
+
+def small_element(**kw):
+    el = dict(h=5.0, Lx=7.5, Lz=7.5, density=0.8, T=1.1, g=0.0, steps_eq=0, steps_sample=0,
+              seed=1234, id=3)
+    el.update(kw)
+    return el
+
+
+# ---------------------------------------------------------------- random numbers
+def test_philox_known_answers():
+    rows = read_golden("philox4x32_10_kat.txt")
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(t, 16) for t in r]
+        assert md.philox4x32_10(v[0:4], v[4:6]) == v[6:10]
+
+
+def test_box_muller_normals_are_standard_normal():
+    z = np.concatenate([md.normals4(i, 7, 3, 1, 99) for i in range(6000)])
+    assert abs(z.mean()) < 4.0 / math.sqrt(len(z))
+    assert abs(z.var() - 1.0) < 0.05
+    assert scipy.stats.kstest(z, "norm").pvalue > 1e-3
+
+
+# ---------------------------------------------------------------- Eq. LJ closed form
+def test_lj_special_values():
+    assert md.lj_energy(1.0) == pytest.approx(0.0, abs=1e-14)
+    assert md.lj_force(1.0) == pytest.approx(24.0, rel=1e-14)
+    rmin = 2.0 ** (1.0 / 6.0)
+    assert md.lj_energy(rmin) == pytest.approx(-1.0, rel=1e-14)
+    assert md.lj_force(rmin) == pytest.approx(0.0, abs=1e-12)
+
+
+@pytest.mark.parametrize("r", [0.95, 1.1, 1.5, 2.0, 2.45])
+@pytest.mark.parametrize("eps,sig", [(1.0, 1.0), (0.2, 0.75)])
+def test_lj_force_is_minus_energy_derivative(r, eps, sig):
+    h = 1e-6
+    dudr = (md.lj_energy(r + h, eps, sig) - md.lj_energy(r - h, eps, sig)) / (2 * h)
+    assert md.lj_force(r, eps, sig) == pytest.approx(-dudr, rel=1e-7, abs=1e-9)
+
+
+def test_lj_reduced_scaling():
+    # U(r; eps, sig) = eps U(r / sig; 1, 1) and F(r; eps, sig) = (eps / sig) F(r / sig; 1, 1)
+    for r in (0.8, 1.3, 2.2):
+        assert md.lj_energy(r, 0.2, 0.75) == pytest.approx(0.2 * md.lj_energy(r / 0.75), rel=1e-13)
+        assert md.lj_force(r, 0.2, 0.75) == pytest.approx(0.2 / 0.75 * md.lj_force(r / 0.75), rel=1e-13)
+
+
+# ---------------------------------------------------------------- element build
+def test_element_counts_and_lattice():
+    p = md.make_params(dict(h=8.0, Lx=10.0, Lz=10.0, density=0.8, T=1.1, g=0.0))
+    nf, nw = md.counts(p)
+    assert nf == round(0.8 * 10 * 8 * 10)
+    # (100) FCC wall planes, 2 atoms per lateral cell, 3 planes, 2 walls
+    a0 = (4.0 / 1.0) ** (1.0 / 3.0)
+    assert nw == 2 * 3 * 2 * round(10 / a0) ** 2
+    x, v, a, sp = md.init(p)
+    assert (sp[:nf] == 0).all() and (sp[nf:] == 1).all()
+    # fluid inside the slab, walls at y <= 0 and y >= h, nobody overlapping
+    assert x[:nf, 1].min() > 0.5 and x[:nf, 1].max() < 7.5
+    assert (x[nf:, 1] <= 1e-12).sum() == nw // 2 and (x[nf:, 1] >= 8.0 - 1e-12).sum() == nw // 2
+    d = x[:, None, :] - x[None, :, :]
+    d[..., 0] -= 10.0 * np.round(d[..., 0] / 10.0)
+    d[..., 2] -= 10.0 * np.round(d[..., 2] / 10.0)
+    r = np.sqrt((d * d).sum(-1)) + np.eye(len(x)) * 100
+    assert r.min() > 0.9
+    # Maxwell-Boltzmann start: zero mean velocity per group, temperature T with 3(N-1) dof
+    for lo, hi in ((0, nf), (nf, nf + nw)):
+        assert np.abs(v[lo:hi].mean(axis=0)).max() < 1e-13
+        assert (v[lo:hi] ** 2).sum() / (3 * (hi - lo - 1)) == pytest.approx(1.1, rel=1e-12)
+    # anchors are the lattice sites
+    assert np.array_equal(a, x)
+
+
+# ---------------------------------------------------------------- forces
+def _jitter(x, rng, amp):
+    return x + rng.uniform(-amp, amp, x.shape)
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_cell_list_equals_all_pairs(mode):
+    rng = np.random.default_rng(mode)
+    phys = {} if mode != 1 else dict(eps_wf=0.2, sig_wf=0.75)
+    el = dict(h=8.0, Lx=10.0, Lz=8.0, density=0.8, T=1.1, g=0.0) if mode != 2 else \
+        dict(h=7.6, Lx=7.6, Lz=7.6, density=0.75, T=1.0, g=0.0)
+    p = md.make_params(el, mode=mode, **phys)
+    x, v, a, sp = md.init(p)
+    x = _jitter(x, rng, 0.15)
+    fb, wb, eb = md.lj_forces(p, x, sp, "brute")
+    fc, wc, ec = md.lj_forces(p, x, sp, "cells")
+    scale = np.abs(fb).max()
+    assert np.abs(fb - fc).max() <= 1e-12 * scale
+    assert np.abs(wb - wc).max() <= 1e-12 * np.abs(wb).max()
+    assert eb.sum() == pytest.approx(ec.sum(), rel=1e-12)
+    if mode == 2:  # no walls: Newton's third law makes the total LJ force vanish
+        assert np.abs(fb.sum(axis=0)).max() < 1e-10 * scale
+
+
+def test_total_force_is_minus_energy_gradient():
+    rng = np.random.default_rng(5)
+    p = md.make_params(small_element())
+    x, v, a, sp = md.init(p)
+    x = _jitter(x, rng, 0.1)
+    f, w, e = md.forces(p, x, a, sp)
+    nf = int((sp == 0).sum())
+    h = 1e-6
+    for i in list(rng.choice(nf, 4, replace=False)) + list(nf + rng.choice(len(sp) - nf, 4, replace=False)):
+        for k in range(3):
+            xp = x.copy(); xp[i, k] += h
+            xm = x.copy(); xm[i, k] -= h
+            ep = md.forces(p, xp, a, sp)[2].sum()
+            em = md.forces(p, xm, a, sp)[2].sum()
+            assert f[i, k] == pytest.approx(-(ep - em) / (2 * h), rel=1e-5, abs=1e-5)
+
+
+def test_virial_is_minus_energy_derivative_under_x_dilation():
+    # Sum over pairs of x_ij F_x,ij = -dU/de under x -> (1 + e) x, L_x -> (1 + e) L_x.
+    rng = np.random.default_rng(11)
+    el = dict(h=7.6, Lx=7.6, Lz=7.6, density=0.75, T=1.0, g=0.0)
+    p = md.make_params(el, mode=2)
+    x, v, a, sp = md.init(p)
+    x = _jitter(x, rng, 0.12)
+    f, w, e = md.lj_forces(p, x, sp, "brute")
+    eps = 1e-6
+    energies = []
+    for s in (1 + eps, 1 - eps):
+        ps = md.make_params(dict(el, Lx=7.6 * s), mode=2)
+        xs = x.copy(); xs[:, 0] *= s
+        energies.append(md.lj_forces(ps, xs, sp, "brute")[2].sum())
+    dude = (energies[0] - energies[1]) / (2 * eps)
+    assert w.sum() == pytest.approx(-dude, rel=1e-6)
+
+
+# ---------------------------------------------------------------- dynamics
+def _run(p, steps, use_cells=True):
+    x, v, a, sp = md.init(p)
+    acc, st = md.simulate(p, x, v, a, sp, 0, steps, use_cells)
+    return x, v, a, sp, acc, st
+
+
+def test_nve_energy_conservation_and_dt2_scaling():
+    # No thermostat, no body force: velocity Verlet (and G-JF at gamma = 0)
+    # conserves energy up to O(dt^2) fluctuations.
+    drifts = []
+    for dt in (0.004, 0.002):
+        p = md.make_params(small_element(T=0.9), gamma_wall=0.0, dt=dt)
+        nsteps = int(round(0.8 / dt))
+        x, v, a, sp = md.init(p)
+        es = []
+        for k in range(8):
+            acc, st = md.simulate(p, x, v, a, sp, k * nsteps // 8, (k + 1) * nsteps // 8)
+            es.append(acc.e_last)
+            if k == 0:
+                e_start = acc.e_first
+        es = np.array(es)
+        drifts.append(np.abs(es - e_start).max() / len(sp))
+    assert drifts[0] < 2e-3
+    ratio = drifts[0] / drifts[1]
+    assert 2.5 < ratio < 6.0, ratio
+
+
+def test_momentum_conserved_in_bulk_box():
+    p = md.make_params(dict(h=7.6, Lx=7.6, Lz=7.6, density=0.75, T=1.0, g=0.0), mode=2)
+    x, v, a, sp, acc, st = _run(p, 200)
+    assert st == 0
+    assert np.abs(v.sum(axis=0)).max() < 1e-10
+
+
+def test_langevin_walls_reach_target_temperature():
+    # Walls alone (no fluid), tethered and G-JF thermostatted: equipartition.
+    p = md.make_params(small_element(density=0.0, T=1.3), gamma_wall=5.0)
+    x, v, a, sp = md.init(p)
+    md.simulate(p, x, v, a, sp, 0, 600)
+    temps = []
+    for k in range(12):
+        md.simulate(p, x, v, a, sp, 600 + 100 * k, 700 + 100 * k)
+        temps.append((v ** 2).sum() / (3 * len(v)))
+    assert np.mean(temps) == pytest.approx(1.3, rel=0.03)
+
+
+def test_body_force_drives_flow_in_its_direction():
+    el = small_element(h=6.0, g=0.3, steps_eq=800, steps_sample=1600)
+    r = md.element(md.make_params(el))
+    assert r["status"] == 0
+    assert r["q"] > 3 * r["q_se"] > 0
+    # order of magnitude against planar Poiseuille with the LJ viscosity near
+    # this state point (eta ~ 2): q ~ m n^2 g h^3 L_z / (12 eta), slip makes it inexact
+    est = 0.8 * 0.8 * 0.3 * 5.0 ** 3 * 7.5 / (12 * 2.0)
+    assert est / 10 < r["q"] < est * 10
+
+
+def test_zero_force_gives_zero_flow():
+    el = small_element(h=6.0, g=0.0, steps_eq=400, steps_sample=2000)
+    r = md.element(md.make_params(el))
+    assert abs(r["q"]) < 3.5 * r["q_se"]
+
+
+def test_block_standard_error_matches_definition():
+    p = md.make_params(small_element(steps_sample=100), n_blocks=4)
+    acc = md.Accum()
+    rng = np.random.default_rng(0)
+    vals = rng.normal(size=100)
+    for k, val in enumerate(vals):
+        b = k * 4 // 100
+        acc.q_block[b] += val
+        acc.p_block[b] += 2 * val
+        acc.n_block[b] += 1
+    r = md.finalize(p, acc)
+    means = vals.reshape(4, 25).mean(axis=1)
+    assert r["q"] == pytest.approx(vals.mean(), rel=1e-13)
+    assert r["q_se"] == pytest.approx(np.std(means, ddof=1) / 2.0, rel=1e-12)
+    assert r["p_se"] == pytest.approx(2 * np.std(means, ddof=1) / 2.0, rel=1e-12)
