@@ -1,0 +1,293 @@
+"""Benchmark: micro-MD atom-steps/s on one GB300 (and weak scaling over ranks).
+
+A bench step is one pass of the whole hot path over one batch: the 64-element
+uneven batch (h ~ U[5, 20], lateral box 10-16, 500-5000 fluid atoms,
+g ~ U[0.005, 0.05], 20 000 steps each) with FP32 pair forces and FP64 state:
+element build, every MD step, on-device reduction of the time-averaged flow
+rates.  Each rank runs its own batch (independent micro-elements: no
+data-path collective), so scaling is weak.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+--impl reference times the FP64 CPU oracle (the paper has no code to run) on a
+bounded sample of the same workload on this machine's host cores.
+"""
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "micro-MD atom-steps/s"
+UNIT = "atom-steps/s"
+STEPS_PER_ELEMENT = 20000
+N_ELEMENTS = 64
+FP32_PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 flop x SM clock"
+ALG_FLOPS_PER_ATOM_STEP = 600.0      # 26.2 unique pairs x ~23 FP32 flops (Newton's third law)
+ALG_BYTES_PER_ATOM_STEP = 96.0       # FP64 x and v read and written once per step
+
+
+def _oracle_element_steps(args):
+    el, steps = args
+    from oracle import md as omd
+    el = dict(el, steps_eq=0, steps_sample=steps)
+    p = omd.make_params(el)
+    nf, nw = omd.counts(p)
+    t0 = time.perf_counter()
+    omd.element(p)
+    return (nf + nw) * steps, time.perf_counter() - t0
+
+
+def cpu_baseline(pool, els, steps):
+    t0 = time.perf_counter()
+    out = pool.map(_oracle_element_steps, [(e, steps) for e in els])
+    wall = time.perf_counter() - t0
+    units = sum(u for u, _ in out)
+    return units / wall, units, wall
+
+
+def sample_clocks_start(path):
+    try:
+        fh = open(path, "w")
+        proc = subprocess.Popen(
+            ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
+             "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+            stdout=fh, stderr=subprocess.DEVNULL)
+        return proc, fh
+    except Exception:
+        return None, None
+
+
+def sample_clocks_stop(proc, fh, path, gpu_index):
+    if proc is None:
+        return None
+    proc.terminate()
+    try:
+        proc.wait(timeout=5)
+    except Exception:
+        proc.kill()
+    fh.close()
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in open(path):
+        f = [t.strip() for t in line.split(",")]
+        if len(f) < 9 or f[0] != str(gpu_index):
+            continue
+        try:
+            sm.append(float(f[1]))
+            mx.append(float(f[2]))
+        except ValueError:
+            continue
+        for nm, val in zip(names, f[5:9]):
+            if val.lower() == "active":
+                reasons.add(nm)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+            "reasons": sorted(reasons)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    els = synth.batch_uneven(N_ELEMENTS, steps=STEPS_PER_ELEMENT)
+    cores = os.cpu_count() or 1
+    sample_els = els[:min(len(els), cores)]
+    sample_steps = 150
+    from oracle import md as omd
+    omd.build()
+    with mp.get_context("spawn").Pool(len(sample_els)) as pool:
+        for _ in range(args.warmup):
+            cpu_baseline(pool, sample_els, 20)
+        rates, walls = [], []
+        for _ in range(args.steps):
+            r, units, wall = cpu_baseline(pool, sample_els, sample_steps)
+            rates.append(r)
+            walls.append(wall)
+    value = statistics.mean(rates)
+    sample = "%d of the %d uneven elements, %d steps each, FP64 oracle, one process per element" % (
+        len(sample_els), N_ELEMENTS, sample_steps)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(walls),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "uneven batch: 64 elements, h 5-20, lateral 10-16, 500-5000 fluid atoms, "
+                                   "20000 steps (sampled)", "elements": N_ELEMENTS,
+                       "steps_per_element": STEPS_PER_ELEMENT},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": len(sample_els), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=1000,
+                    help="steps of the FP64-forces pass reported beside the headline")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    els = synth.batch_uneven(N_ELEMENTS, seed=synth.BASE_SEED + 1000 * rank, steps=STEPS_PER_ELEMENT)
+
+    # CPU pool first (spawned before any CUDA work)
+    pool = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        pool = mp.get_context("spawn").Pool(min(cores, len(els)))
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1603_04628_gb300 import native
+
+    stream = torch.cuda.Stream()
+    ctx = native.Context(local, native.PREC_FP32, stream=stream)
+    n_atoms = ctx.micro_plan(els)
+    units = n_atoms * STEPS_PER_ELEMENT
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    for _ in range(args.warmup):
+        ctx.micro_launch()
+        ctx.micro_results()
+    launches_per_step = ctx.launch_count()
+
+    clk_path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
+                            "bench_clocks_rank%d.csv" % rank)
+    proc, fh = sample_clocks_start(clk_path)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    times = []
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            flush.zero_()                     # L2 flush between timed iterations (256 MB > 129 MB L2)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.micro_launch()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sample_clocks_stop(proc, fh, clk_path, local)
+    res = ctx.micro_results()
+    bad = [r["status"] for r in res if r["status"] != 0]
+    ms = statistics.mean(times)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = units * world / (ms / 1e3)
+
+    # per-kernel durations (CUDA events on the context's stream) for the roofline
+    prof = ctx.micro_profile(200)
+    force_s = prof["force_ms"] / 1e3
+    sm_mhz = (clocks or {}).get("sm_max_mhz", 2070.0) or 2070.0
+    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    achieved = ALG_FLOPS_PER_ATOM_STEP * n_atoms / force_s / 1e12
+
+    # end to end through the public API: host descriptors in, host results out
+    e2e_times = []
+    for _ in range(max(1, min(args.steps, 2))):
+        t0 = time.perf_counter()
+        ctx2_res = ctx.micro_batch(els)
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_value = units * world / statistics.mean(e2e_times)
+    # element descriptors + offsets up, results down
+    h2d = len(els) * (256 + 16) + 16
+    d2h = len(els) * 72
+
+    # FP64-forces pass (same batch, shorter), reported beside the headline
+    fp64 = None
+    if args.fp64_steps > 0 and rank == 0:
+        els64 = [dict(e, steps_eq=args.fp64_steps // 5, steps_sample=args.fp64_steps - args.fp64_steps // 5)
+                 for e in els]
+        c64 = native.Context(local, native.PREC_FP64, stream=stream)
+        na = c64.micro_plan(els64)
+        c64.micro_launch(); c64.micro_results()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream); c64.micro_launch(); e1.record(stream); e1.synchronize()
+        fp64 = {"value": na * args.fp64_steps / (e0.elapsed_time(e1) / 1e3), "unit": UNIT,
+                "steps_per_element": args.fp64_steps, "dtype": "f64"}
+        c64.close()
+
+    cpu = None
+    if pool is not None:
+        sample_els = els[:min(len(els), os.cpu_count() or 1)]
+        rate, cu, wall = cpu_baseline(pool, sample_els, 150)
+        pool.close()
+        cpu = {"value": rate, "unit": UNIT, "cores": len(sample_els), "kind": "oracle",
+               "sample": "%d of the 64 uneven elements x 150 steps, FP64 oracle, one process per element "
+                         "(%.1f s wall)" % (len(sample_els), wall)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 forces + f64 state", "data": "synthetic",
+            "config": {"workload": "uneven batch: 64 elements, h 5-20, lateral 10-16, 500-5000 fluid atoms, "
+                                   "g 0.005-0.05, 20000 steps, FP32 forces + FP64 state",
+                       "elements": N_ELEMENTS, "atoms_per_rank": n_atoms, "steps_per_element": STEPS_PER_ELEMENT,
+                       "l2": "flushed between timed iterations (256 MB write)",
+                       "parallelism": "independent elements per rank" if world > 1 else "1 GPU"},
+            "roofline": {"bound": "alu", "kernel": "k_force_cells", "achieved": achieved, "peak": fp32_peak,
+                         "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                         "peak_note": FP32_PEAK_NOTE + " (derived, max SM clock)",
+                         "alg_flops_per_atom_step": ALG_FLOPS_PER_ATOM_STEP,
+                         "force_ms": prof["force_ms"], "integrate_ms": prof["integrate_ms"]},
+            "hbm_roofline": {"alg_bytes_per_atom_step": ALG_BYTES_PER_ATOM_STEP,
+                             "achieved_gbs": value / world * ALG_BYTES_PER_ATOM_STEP / 1e9,
+                             "peak_gbs": _peak_hbm(), "frac": value / world * ALG_BYTES_PER_ATOM_STEP / 1e9 /
+                             _peak_hbm()},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clocks,
+            "fp64_forces": fp64,
+            "element_status_errors": len(bad),
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def _peak_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"])
+    except Exception:
+        return 6800.0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,178 @@
+/*
+ * mdgp.h -- C ABI of the GB300 micro-MD + Gaussian-process library.
+ *
+ * The library runs the hot path of the hybrid continuum-atomistic scheme of
+ * Stephenson, Kermode & Lockerby (arXiv:1603.04628): batches of independent
+ * Lennard-Jones micro-elements (paper App. A; body force of Sec. 2.1
+ * Eq. momentumEq; time-averaged mass flow rate of Eq. continuityEq), the
+ * Gaussian-process surrogate that decides which macro sections need one
+ * (Sec. 2.2, Eqs. quadraticKernelEq, d2Eq, covarianceEq, predMeanEq,
+ * predVarEq), and the macro time step of Algorithm 1 (Sec. 2.4).
+ *
+ * Conventions for every entry point:
+ *   - Units are reduced Lennard-Jones units (eps = sigma = m = 1).
+ *   - Pointers are HOST pointers unless the name says _dev.  The caller owns
+ *     every array it passes; the library copies what it needs and keeps no
+ *     caller pointer after the call returns.
+ *   - Return value: MDGP_OK (0) or a negative mdgp_status.  On failure the
+ *     outputs are unspecified.  Per-element failures inside a batch do not
+ *     fail the call; they are reported in mdgp_result.status.
+ *   - A context is not thread-safe; use one context per host thread.
+ *   - All device work runs on one GPU, on the context's stream.
+ */
+#ifndef MDGP_H
+#define MDGP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MDGP_OK = 0,
+  MDGP_E_ARG = -1,       /* invalid argument (null pointer, size or geometry out of range) */
+  MDGP_E_NOMEM = -2,     /* device or host allocation failed */
+  MDGP_E_CUDA = -3,      /* a CUDA runtime call failed */
+  MDGP_E_UNSTABLE = -4,  /* an element blew up (non-finite state or atoms far outside the box) */
+  MDGP_E_NOTPD = -5,     /* GP covariance not positive definite */
+  MDGP_E_TIMEOUT = -6,   /* a bounded device-side wait gave up */
+  MDGP_E_STATE = -7,     /* call out of order (e.g. launch before plan) */
+  MDGP_E_OVERFLOW = -8   /* a cell held more atoms than the cell capacity */
+} mdgp_status;
+
+typedef enum {
+  MDGP_PREC_FP64 = 0,    /* FP64 pair forces and FP64 state */
+  MDGP_PREC_FP32 = 1     /* FP32 pair forces, FP64 positions, velocities and accumulators */
+} mdgp_precision;
+
+typedef struct mdgp_ctx mdgp_ctx;
+
+/* ------------------------------------------------------------------------ */
+/* Micro-element MD (paper App. A, Sec. 2.1).                                */
+/* ------------------------------------------------------------------------ */
+
+/* One micro-element: a fluid slab of height h between two FCC walls, periodic
+ * in x (streamwise, length Lx) and z (spanwise, length Lz).
+ * Every fluid atom feels the body force of Eq. momentumEq,
+ *   F = g_ext - (m / rho) dp/dx,  rho = m * density. */
+typedef struct {
+  double h;          /* distance between the innermost wall planes */
+  double dpdx;       /* local pressure gradient dp/dx */
+  double density;    /* fluid number density n; N_fluid = round(n Lx h Lz) */
+  double T;          /* target temperature (wall thermostat; initial velocities) */
+  int64_t steps_eq;      /* equilibration steps (not sampled) */
+  int64_t steps_sample;  /* sampling steps, split into n_blocks contiguous blocks */
+  double Lx, Lz;     /* periodic lengths; each must be >= 3 r_c */
+  double g_ext;      /* external force per atom F_ext (Eq. extForcing1 value at this time) */
+  uint64_t seed;     /* Philox key */
+  int32_t flags;     /* reserved, 0 */
+  int32_t id;        /* element id: Philox counter word 2 */
+} mdgp_element;
+
+/* Time-averaged outputs of one element. */
+typedef struct {
+  double q;        /* mean mass flow rate (m / Lx) sum_fluid v_x over the sampling steps */
+  double q_se;     /* its standard error: std(block means, ddof 1) / sqrt(n_blocks) */
+  double p;        /* mean P_xx of the fluid slab (kinetic + virial, fluid-wall pairs half) */
+  double p_se;     /* its standard error, same estimator */
+  double T_meas;   /* mean fluid kinetic temperature m <|v|^2> / 3 over the samples */
+  double e_drift;  /* (E_end - E_start) / N_atoms, E = kinetic + LJ (shifted) + tether */
+  int64_t n_fluid, n_wall;
+  int32_t status;  /* MDGP_OK or MDGP_E_UNSTABLE / MDGP_E_OVERFLOW for this element */
+  int32_t reserved;
+} mdgp_result;
+
+/* Physics constants shared by all elements of a context. */
+typedef struct {
+  double dt;            /* time step (default 0.005) */
+  double rc;            /* LJ cut-off (default 2.5); energy shifted, force truncated */
+  double k_tether;      /* wall spring constant (default 150) */
+  double gamma_wall;    /* Langevin friction on wall atoms, G-JF scheme (default 1) */
+  double wall_density;  /* FCC wall number density (default 1) */
+  double eps_wf, sig_wf;  /* wall-fluid LJ pair (default 1, 1) */
+  double eps_ww, sig_ww;  /* wall-wall LJ pair (default 1, 1) */
+  double fluid_margin;  /* gap between the wall plane and the fluid lattice (default 0.7) */
+  double tau_T;         /* Berendsen time constant, mode 1 (default 0.5) */
+  double mass;          /* atom mass (default 1) */
+  int32_t n_blocks;     /* blocks for the standard error (default 10, max 64) */
+  int32_t mode;         /* 0: tethered walls + Langevin wall thermostat; 1: frozen walls +
+                           Berendsen on the fluid's v_z (paper App. A) */
+  int32_t wall_planes;  /* FCC (100) planes per wall (default 3) */
+  int32_t cell_capacity;/* atoms per cell slot array; 0 = choose automatically */
+} mdgp_md_params;
+
+/* Fill *out with the defaults listed above.  Returns MDGP_E_ARG on null. */
+int mdgp_md_params_default(mdgp_md_params* out);
+
+/* Create a context on CUDA device `device` computing pair forces in
+ * `precision` (mdgp_precision).  *out receives the handle; free it with
+ * mdgp_destroy.  MDGP_E_CUDA if the device cannot be used. */
+int mdgp_create(mdgp_ctx** out, int device, int precision);
+int mdgp_destroy(mdgp_ctx* ctx);
+
+/* Replace the physics constants (copied).  Invalidates any plan. */
+int mdgp_set_md_params(mdgp_ctx* ctx, const mdgp_md_params* params);
+
+/* Run all work of this context on `stream` (a cudaStream_t, not owned; it
+ * must not be the legacy default stream, because the step loop is captured
+ * into a CUDA graph).  0 selects the context's own non-blocking stream, which
+ * is also the initial choice.  Invalidates any plan. */
+int mdgp_set_stream(mdgp_ctx* ctx, void* stream);
+
+/* Run n elements to completion and write n results (host arrays).  Blocking.
+ * Equivalent to mdgp_micro_plan + mdgp_micro_launch + mdgp_micro_results.
+ * Elements whose steps_eq + steps_sample differ run as separate sub-batches.
+ * MDGP_E_ARG: n < 1, a null pointer, Lx or Lz < 3 r_c, h <= 2 fluid_margin,
+ * density < 0, steps_sample < 0. */
+int mdgp_micro_batch(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, mdgp_result* out);
+
+/* Plan a batch: validate, lay the atoms and cells out in device memory,
+ * upload the element descriptors and capture the step loop in a CUDA graph.
+ * *n_atoms (may be null) receives the total atom count.  All elements must
+ * share steps_eq + steps_sample (MDGP_E_ARG otherwise). */
+int mdgp_micro_plan(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int64_t* n_atoms);
+
+/* Enqueue the planned batch on the context's stream: build the elements,
+ * replay the step graph, reduce the results on the device.  Asynchronous;
+ * MDGP_E_STATE without a plan. */
+int mdgp_micro_launch(mdgp_ctx* ctx);
+
+/* Wait for the launched batch and copy its n results to the host. */
+int mdgp_micro_results(mdgp_ctx* ctx, mdgp_result* out, int64_t n);
+
+/* Number of kernel launches the last mdgp_micro_launch enqueued (graph
+ * nodes counted one by one). */
+int64_t mdgp_micro_launch_count(const mdgp_ctx* ctx);
+
+/* Copy the planned batch's current atom state to the host: positions and
+ * velocities as (n_atoms x 3) row-major doubles, atoms ordered element by
+ * element, fluid first then walls (either pointer may be null). */
+int mdgp_micro_state(mdgp_ctx* ctx, double* x, double* v, int64_t n_atoms);
+
+/* LJ pair forces of ONE element at the given positions (n_atoms x 3,
+ * fluid then walls, as built for `el`), computed by the library's cell-list
+ * force kernel in the context's precision: forces (n_atoms x 3), each fluid
+ * atom's x-virial share (half of x_ij F_x,ij for every pair it is in; 0 for
+ * wall atoms) and per-atom shifted LJ energies (half per pair).  Any output
+ * may be null. */
+int mdgp_md_forces(mdgp_ctx* ctx, const mdgp_element* el, const double* x, int64_t n_atoms,
+                   double* f, double* wxx, double* epot);
+
+/* Time the planned batch's kernels one by one: rebuild the elements and run
+ * the first `steps` steps without the graph, with CUDA events on the
+ * context's stream around every launch.  ms[0] = mean integration kernel
+ * time, ms[1] = mean pair-force kernel time (milliseconds per launch),
+ * ms[2] = atoms, ms[3] = cells.  Leaves the batch state mid-run (launch it
+ * again for results).  MDGP_E_STATE without a plan. */
+int mdgp_micro_profile(mdgp_ctx* ctx, int64_t steps, double* ms);
+
+/* Last CUDA error string seen by the context (static storage). */
+const char* mdgp_last_error(const mdgp_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MDGP_H */

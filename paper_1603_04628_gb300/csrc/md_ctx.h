@@ -1,0 +1,38 @@
+// Library context: device buffers, stream, captured step graphs.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "mdgp.h"
+#include "md_internal.cuh"
+
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+struct mdgp_ctx {
+  int device = 0;
+  int precision = MDGP_PREC_FP64;
+  mdgp_md_params params;
+  cudaStream_t stream = nullptr;      // stream all work is enqueued on
+  cudaStream_t own_stream = nullptr;  // created with the context
+  char err[256] = {0};
+  // MD batch
+  bool planned = false;
+  long long n_el = 0, steps = 0, n_atoms = 0;
+  long long chunk = 256;  // steps per captured graph
+  long long graph_K = 0, graph_rem_K = 0;
+  cudaGraphExec_t graph_full = nullptr, graph_rem = nullptr;
+  long long launches = 0;
+  mdgp::BatchDev B;
+  mdgp::PhysDev P;
+  DevBuf d_el, d_aoff, d_coff, d_atomf64, d_force, d_atom_el, d_cell_el, d_counts, d_slots, d_acc, d_grp,
+      d_status, d_results, d_step;
+  std::vector<DevBuf*> all_bufs() {
+    return {&d_el, &d_aoff, &d_coff, &d_atomf64, &d_force, &d_atom_el, &d_cell_el, &d_counts, &d_slots,
+            &d_acc, &d_grp, &d_status, &d_results, &d_step};
+  }
+  void release_extra() {}
+};

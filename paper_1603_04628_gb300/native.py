@@ -1,0 +1,206 @@
+"""Thin ctypes binding of libmdgp.so (include/mdgp.h).  Argument marshalling
+only: every step of the path runs in the library's CUDA kernels.  There is no
+CPU fallback -- if the library is missing this module raises."""
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libmdgp.so")
+
+MDGP_OK = 0
+STATUS = {0: "MDGP_OK", -1: "MDGP_E_ARG", -2: "MDGP_E_NOMEM", -3: "MDGP_E_CUDA", -4: "MDGP_E_UNSTABLE",
+          -5: "MDGP_E_NOTPD", -6: "MDGP_E_TIMEOUT", -7: "MDGP_E_STATE", -8: "MDGP_E_OVERFLOW"}
+PREC_FP64 = 0
+PREC_FP32 = 1
+
+
+class Element(ctypes.Structure):
+    _fields_ = [("h", ctypes.c_double), ("dpdx", ctypes.c_double), ("density", ctypes.c_double),
+                ("T", ctypes.c_double), ("steps_eq", ctypes.c_int64), ("steps_sample", ctypes.c_int64),
+                ("Lx", ctypes.c_double), ("Lz", ctypes.c_double), ("g_ext", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("flags", ctypes.c_int32), ("id", ctypes.c_int32)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("q", ctypes.c_double), ("q_se", ctypes.c_double), ("p", ctypes.c_double),
+                ("p_se", ctypes.c_double), ("T_meas", ctypes.c_double), ("e_drift", ctypes.c_double),
+                ("n_fluid", ctypes.c_int64), ("n_wall", ctypes.c_int64), ("status", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class MDParams(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("rc", ctypes.c_double), ("k_tether", ctypes.c_double),
+                ("gamma_wall", ctypes.c_double), ("wall_density", ctypes.c_double),
+                ("eps_wf", ctypes.c_double), ("sig_wf", ctypes.c_double), ("eps_ww", ctypes.c_double),
+                ("sig_ww", ctypes.c_double), ("fluid_margin", ctypes.c_double), ("tau_T", ctypes.c_double),
+                ("mass", ctypes.c_double), ("n_blocks", ctypes.c_int32), ("mode", ctypes.c_int32),
+                ("wall_planes", ctypes.c_int32), ("cell_capacity", ctypes.c_int32)]
+
+
+class MdgpError(RuntimeError):
+    pass
+
+
+_lib = None
+
+
+def lib():
+    """Load libmdgp.so (built by paper_1603_04628_gb300.build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise MdgpError("CUDA library %s is not built; run __graft_entry__.build()" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i64, dp = ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "mdgp_md_params_default": ([ctypes.POINTER(MDParams)], ctypes.c_int),
+        "mdgp_create": ([ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "mdgp_destroy": ([vp], ctypes.c_int),
+        "mdgp_set_md_params": ([vp, ctypes.POINTER(MDParams)], ctypes.c_int),
+        "mdgp_set_stream": ([vp, vp], ctypes.c_int),
+        "mdgp_micro_batch": ([vp, ctypes.POINTER(Element), i64, ctypes.POINTER(Result)], ctypes.c_int),
+        "mdgp_micro_plan": ([vp, ctypes.POINTER(Element), i64, ctypes.POINTER(i64)], ctypes.c_int),
+        "mdgp_micro_launch": ([vp], ctypes.c_int),
+        "mdgp_micro_results": ([vp, ctypes.POINTER(Result), i64], ctypes.c_int),
+        "mdgp_micro_launch_count": ([vp], i64),
+        "mdgp_micro_state": ([vp, dp, dp, i64], ctypes.c_int),
+        "mdgp_md_forces": ([vp, ctypes.POINTER(Element), dp, i64, dp, dp, dp], ctypes.c_int),
+        "mdgp_micro_profile": ([vp, i64, dp], ctypes.c_int),
+        "mdgp_last_error": ([vp], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def _check(ctx, st, what):
+    if st != MDGP_OK:
+        msg = lib().mdgp_last_error(ctx) if ctx else b""
+        raise MdgpError("%s failed: %s (%s)" % (what, STATUS.get(st, st), (msg or b"").decode()))
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def to_element(d):
+    e = Element()
+    e.h, e.dpdx, e.density, e.T = float(d["h"]), float(d.get("dpdx", 0.0)), float(d["density"]), float(d["T"])
+    e.steps_eq, e.steps_sample = int(d.get("steps_eq", 0)), int(d.get("steps_sample", 0))
+    e.Lx, e.Lz, e.g_ext = float(d["Lx"]), float(d["Lz"]), float(d.get("g_ext", d.get("g", 0.0)))
+    e.seed = int(d.get("seed", 0)) & 0xFFFFFFFFFFFFFFFF
+    e.flags = int(d.get("flags", 0))
+    e.id = int(d.get("id", 0))
+    return e
+
+
+def elements_array(els):
+    arr = (Element * len(els))()
+    for i, d in enumerate(els):
+        arr[i] = to_element(d)
+    return arr
+
+
+def result_dict(r):
+    return {k: getattr(r, k) for k, _ in Result._fields_ if k != "reserved"}
+
+
+def md_params_default():
+    p = MDParams()
+    _check(None, lib().mdgp_md_params_default(ctypes.byref(p)), "mdgp_md_params_default")
+    return p
+
+
+class Context:
+    """Owns one mdgp_ctx (device buffers, stream, captured graphs)."""
+
+    def __init__(self, device=0, precision=PREC_FP64, stream=None, **md_params):
+        self.h = ctypes.c_void_p()
+        _check(None, lib().mdgp_create(ctypes.byref(self.h), int(device), int(precision)), "mdgp_create")
+        self.precision = precision
+        if md_params:
+            self.set_md_params(**md_params)
+        if stream is not None:
+            self.set_stream(stream)
+
+    def close(self):
+        if self.h:
+            lib().mdgp_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_md_params(self, **kw):
+        p = md_params_default()
+        for k, v in kw.items():
+            setattr(p, k, v)
+        _check(self.h, lib().mdgp_set_md_params(self.h, ctypes.byref(p)), "mdgp_set_md_params")
+
+    def set_stream(self, stream):
+        handle = getattr(stream, "cuda_stream", stream)
+        _check(self.h, lib().mdgp_set_stream(self.h, ctypes.c_void_p(int(handle))), "mdgp_set_stream")
+
+    def micro_batch(self, els):
+        arr = elements_array(els)
+        out = (Result * len(els))()
+        _check(self.h, lib().mdgp_micro_batch(self.h, arr, len(els), out), "mdgp_micro_batch")
+        return [result_dict(r) for r in out]
+
+    def micro_plan(self, els):
+        arr = elements_array(els)
+        n = ctypes.c_int64()
+        _check(self.h, lib().mdgp_micro_plan(self.h, arr, len(els), ctypes.byref(n)), "mdgp_micro_plan")
+        self._n_el = len(els)
+        self.n_atoms = int(n.value)
+        return self.n_atoms
+
+    def micro_launch(self):
+        _check(self.h, lib().mdgp_micro_launch(self.h), "mdgp_micro_launch")
+
+    def micro_results(self):
+        out = (Result * self._n_el)()
+        _check(self.h, lib().mdgp_micro_results(self.h, out, self._n_el), "mdgp_micro_results")
+        return [result_dict(r) for r in out]
+
+    def launch_count(self):
+        return int(lib().mdgp_micro_launch_count(self.h))
+
+    def micro_state(self):
+        x = np.zeros((self.n_atoms, 3))
+        v = np.zeros((self.n_atoms, 3))
+        _check(self.h, lib().mdgp_micro_state(self.h, _dp(x), _dp(v), self.n_atoms), "mdgp_micro_state")
+        return x, v
+
+    def micro_profile(self, steps=100):
+        """Mean per-launch milliseconds of the integration and pair-force kernels."""
+        ms = np.zeros(4)
+        _check(self.h, lib().mdgp_micro_profile(self.h, int(steps), _dp(ms)), "mdgp_micro_profile")
+        return dict(integrate_ms=float(ms[0]), force_ms=float(ms[1]), atoms=int(ms[2]), cells=int(ms[3]))
+
+    def md_forces(self, el, x):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        n = len(x)
+        f = np.zeros((n, 3)); w = np.zeros(n); e = np.zeros(n)
+        e1 = to_element(el)
+        _check(self.h, lib().mdgp_md_forces(self.h, ctypes.byref(e1), _dp(x), n, _dp(f), _dp(w), _dp(e)),
+               "mdgp_md_forces")
+        return f, w, e
+
+
+# Same names as the C ABI.
+def mdgp_create(device=0, precision=PREC_FP64):
+    return Context(device, precision)
+
+
+def mdgp_micro_batch(ctx, elements):
+    return ctx.micro_batch(elements)

@@ -1,0 +1,242 @@
+"""GPU micro-element MD against the FP64 oracle, through the C ABI.
+
+Tolerances:
+  - pair forces, FP64 path: max_i |dF_i| <= 1e-12 * max(|F_i|, F_rms);
+  - pair forces, FP32 path: max_i |dF_i| <= 2e-5 * max(|F_i|, F_rms);
+    atoms with a pair within 1e-6 of r_c (where the truncated force is
+    discontinuous) are held to |dF_i| <= 2 |F(r_c)| instead;
+  - positions after the first 100 steps, FP64 path: <= 1e-6 sigma;
+  - long-run flow rate, FP32 forces: within the ensemble z-score bound below.
+"""
+import math
+import multiprocessing as mp
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import md as omd
+
+pytestmark = pytest.mark.gpu
+
+FP_TOL = {0: 1e-12, 1: 2e-5}
+
+
+@pytest.fixture(scope="module")
+def native():
+    from paper_1603_04628_gb300 import build, native as nat
+    build.build()
+    return nat
+
+
+def _force_err(f, ref, skip=None):
+    d = np.linalg.norm(f - ref, axis=1)
+    mag = np.linalg.norm(ref, axis=1)
+    frms = math.sqrt((mag ** 2).mean())
+    rel = d / np.maximum(mag, frms)
+    if skip is not None:
+        rel = rel[~skip]
+    return float(rel.max())
+
+
+def _cutoff_ambiguous(el, x, sp, ref):
+    """Atoms with a pair within 1e-6 of r_c: the truncated force jumps by
+    |F(r_c)| there, so which side a finite-precision r^2 lands on is arbitrary.
+    Returned with the bound their error must still meet."""
+    lo = omd.lj_forces(omd.make_params(el, rc=2.5 - 1e-6), x, sp, "cells")[0]
+    hi = omd.lj_forces(omd.make_params(el, rc=2.5 + 1e-6), x, sp, "cells")[0]
+    amb = (np.abs(lo - ref).max(axis=1) > 0) | (np.abs(hi - ref).max(axis=1) > 0)
+    return amb, 2.0 * abs(omd.lj_force(2.5))
+
+
+def _wrap_dx(dx, p):
+    dx = dx.copy()
+    dx[:, 0] -= p.Lx * np.round(dx[:, 0] / p.Lx)
+    dx[:, 2] -= p.Lz * np.round(dx[:, 2] / p.Lz)
+    return dx
+
+
+def _configs():
+    rng = np.random.default_rng(17)
+    out = []
+    el = synth.element_plain()
+    p = omd.make_params(el)
+    x, v, a, sp = omd.init(p)
+    out.append(("lattice+jitter", el, x + rng.uniform(-0.1, 0.1, x.shape), sp))
+    x2, v2 = x.copy(), v.copy()
+    omd.simulate(p, x2, v2, a, sp, 0, 300)
+    out.append(("liquid after 300 steps", el, x2, sp))
+    el3 = synth.batch_uneven(3, seed=5, steps=100)[2]
+    p3 = omd.make_params(el3)
+    x3, v3, a3, sp3 = omd.init(p3)
+    omd.simulate(p3, x3, v3, a3, sp3, 0, 100)
+    out.append(("uneven element", el3, x3, sp3))
+    return out
+
+
+CONFIGS = None
+
+
+def configs():
+    global CONFIGS
+    if CONFIGS is None:
+        CONFIGS = _configs()
+    return CONFIGS
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("which", [0, 1, 2])
+def test_pair_forces_match_oracle(native, prec, which):
+    name, el, x, sp = configs()[which]
+    p = omd.make_params(el)
+    fr, wr, er = omd.lj_forces(p, x, sp, "cells")
+    amb, jump = _cutoff_ambiguous(el, x, sp, fr)
+    ctx = native.Context(0, prec)
+    f, w, e = ctx.md_forces(el, x)
+    err = _force_err(f, fr, amb)
+    assert err <= FP_TOL[prec], (name, err)
+    assert np.abs(f - fr)[amb].max(initial=0.0) <= jump
+    # fluid atoms' x-virial shares (the pressure measurement's input) and energies
+    tol = 1e-11 if prec == 0 else 2e-5
+    fl = sp == 0
+    assert np.abs(w[fl] - wr[fl]).max() <= tol * max(np.abs(wr[fl]).max(), 1.0)
+    assert (w[~fl] == 0).all()
+    assert e.sum() == pytest.approx(er.sum(), rel=tol)
+    ctx.close()
+
+
+def test_pair_forces_at_maximum_element_size(native):
+    # the tallest, widest and densest element of the stress workload
+    el = dict(h=40.0, Lx=31.0, Lz=31.0, density=0.9, T=1.1, g_ext=0.0, seed=3, id=9)
+    p = omd.make_params(el)
+    x, v, a, sp = omd.init(p)
+    x = x + np.random.default_rng(1).uniform(-0.08, 0.08, x.shape)
+    fr, wr, er = omd.lj_forces(p, x, sp, "cells")
+    amb, jump = _cutoff_ambiguous(el, x, sp, fr)
+    for prec in (0, 1):
+        ctx = native.Context(0, prec)
+        f, w, e = ctx.md_forces(el, x)
+        assert _force_err(f, fr, amb) <= FP_TOL[prec]
+        assert np.abs(f - fr)[amb].max(initial=0.0) <= jump
+        ctx.close()
+
+
+def test_first_100_steps_positions_fp64(native):
+    el = synth.element_plain(steps_eq=100, steps_sample=0)
+    ctx = native.Context(0, native.PREC_FP64)
+    ctx.micro_plan([el])
+    ctx.micro_launch()
+    res = ctx.micro_results()[0]
+    xg, vg = ctx.micro_state()
+    p = omd.make_params(el)
+    x, v, a, sp = omd.init(p)
+    omd.simulate(p, x, v, a, sp, 0, 100)
+    assert res["status"] == 0
+    assert np.abs(_wrap_dx(xg - x, p)).max() <= 1e-6
+    assert np.abs(vg - v).max() <= 1e-5
+    ctx.close()
+
+
+def test_short_run_measurements_fp64(native):
+    # 150 steps, 100 sampled: identical trajectories give identical averages
+    el = synth.element_plain(steps_eq=50, steps_sample=100, g=0.05)
+    ctx = native.Context(0, native.PREC_FP64)
+    res = ctx.micro_batch([el])[0]
+    ref = omd.element(omd.make_params(el))
+    for k in ("q", "p", "T_meas", "q_se", "p_se", "e_drift"):
+        assert res[k] == pytest.approx(ref[k], rel=1e-7, abs=1e-9), k
+    assert (res["n_fluid"], res["n_wall"]) == (ref["n_fluid"], ref["n_wall"])
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_ragged_batch_matches_each_element(native, prec):
+    els = synth.batch_uneven(5, seed=11, steps=60)
+    els[2] = dict(els[2], dpdx=0.01)          # pressure-gradient input (Eq. momentumEq)
+    ctx = native.Context(0, prec)
+    ctx.micro_plan(els)
+    ctx.micro_launch()
+    res = ctx.micro_results()
+    xg, vg = ctx.micro_state()
+    off = 0
+    for el, r in zip(els, res):
+        p = omd.make_params(el)
+        x, v, a, sp = omd.init(p)
+        acc, st = omd.simulate(p, x, v, a, sp, 0, 60)
+        ref = omd.finalize(p, acc)
+        n = len(sp)
+        dx = np.abs(_wrap_dx(xg[off:off + n] - x, p)).max()
+        off += n
+        assert r["status"] == 0
+        if prec == 0:
+            assert dx <= 1e-6
+            assert r["q"] == pytest.approx(ref["q"], rel=1e-7, abs=1e-9)
+        else:
+            assert dx <= 1e-3          # FP32 forces: trajectories stay close over 60 steps
+            assert r["q"] == pytest.approx(ref["q"], rel=1e-2, abs=0.05)
+    assert off == len(xg)
+    ctx.close()
+
+
+def test_edge_cases(native):
+    ctx = native.Context(0, native.PREC_FP64)
+    with pytest.raises(native.MdgpError):
+        ctx.micro_batch([dict(synth.element_plain(), Lx=7.0)])       # fewer than 3 cells along x
+    with pytest.raises(native.MdgpError):
+        ctx.micro_batch([])
+    # no sampling steps: no averages
+    r = ctx.micro_batch([synth.element_plain(steps_eq=10, steps_sample=0)])[0]
+    assert r["status"] == 0 and math.isnan(r["q"])
+    # walls only
+    r = ctx.micro_batch([dict(synth.element_plain(steps_eq=5, steps_sample=20), density=0.0)])[0]
+    assert r["status"] == 0 and r["n_fluid"] == 0 and r["n_wall"] > 0
+    # fewer samples than blocks
+    r = ctx.micro_batch([synth.element_plain(steps_eq=0, steps_sample=3)])[0]
+    ref = omd.element(omd.make_params(synth.element_plain(steps_eq=0, steps_sample=3)))
+    assert r["q"] == pytest.approx(ref["q"], rel=1e-8)
+    assert r["q_se"] == pytest.approx(ref["q_se"], rel=1e-6)
+    # a cell capacity that is too small is reported, never written past
+    ctx.set_md_params(cell_capacity=8)
+    ctx.micro_plan([synth.element_plain(steps_eq=2, steps_sample=2)])
+    ctx.micro_launch()
+    assert ctx.micro_results()[0]["status"] == -8
+    ctx.close()
+
+
+def test_uneven_step_counts_split_into_groups(native):
+    els = [synth.element_plain(steps_eq=10, steps_sample=20, elem_id=0),
+           synth.element_plain(steps_eq=5, steps_sample=40, elem_id=1, seed=9)]
+    ctx = native.Context(0, native.PREC_FP64)
+    res = ctx.micro_batch(els)
+    for el, r in zip(els, res):
+        ref = omd.element(omd.make_params(el))
+        assert r["q"] == pytest.approx(ref["q"], rel=1e-7, abs=1e-9)
+    ctx.close()
+
+
+def _oracle_run(el):
+    return omd.element(omd.make_params(el))
+
+
+def test_long_run_flow_rate_fp32_within_oracle_ensemble(native):
+    # configuration of the single plain element, 2000 + 3000 steps, body force
+    # 0.05 (a clear signal), eight seeds on each side
+    seeds = [101 + k for k in range(8)]
+    els = [synth.element_plain(seed=s, g=0.05, elem_id=k) for k, s in enumerate(seeds)]
+    ctx_pool = mp.get_context("spawn")
+    with ctx_pool.Pool(8) as pool:
+        refs = pool.map(_oracle_run, els)
+    ctx = native.Context(0, native.PREC_FP32)
+    res = ctx.micro_batch(els)
+    ctx.close()
+    for key, sek in (("q", "q_se"), ("p", "p_se")):
+        g = np.array([r[key] for r in res])
+        o = np.array([r[key] for r in refs])
+        se_g = math.sqrt(sum(r[sek] ** 2 for r in res)) / len(res)
+        se_o = math.sqrt(sum(r[sek] ** 2 for r in refs)) / len(refs)
+        z = abs(g.mean() - o.mean()) / math.sqrt(se_g ** 2 + se_o ** 2)
+        print("%s: gpu %.4f oracle %.4f z %.2f" % (key, g.mean(), o.mean(), z))
+        assert z < 3.0, (key, z)
+    tg = np.mean([r["T_meas"] for r in res])
+    to = np.mean([r["T_meas"] for r in refs])
+    assert tg == pytest.approx(to, rel=0.02)
