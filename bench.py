@@ -142,6 +142,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=1000,
                     help="steps of the FP64-forces pass reported beside the headline")
+    ap.add_argument("--steps-per-element", type=int, default=STEPS_PER_ELEMENT,
+                    help="MD steps per element (shorter runs for profiling only)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -149,7 +151,8 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    els = synth.batch_uneven(N_ELEMENTS, seed=synth.BASE_SEED + 1000 * rank, steps=STEPS_PER_ELEMENT)
+    steps_el = args.steps_per_element
+    els = synth.batch_uneven(N_ELEMENTS, seed=synth.BASE_SEED + 1000 * rank, steps=steps_el)
 
     # CPU pool first (spawned before any CUDA work)
     pool = None
@@ -168,7 +171,7 @@ def main():
     stream = torch.cuda.Stream()
     ctx = native.Context(local, native.PREC_FP32, stream=stream)
     n_atoms = ctx.micro_plan(els)
-    units = n_atoms * STEPS_PER_ELEMENT
+    units = n_atoms * steps_el
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     for _ in range(args.warmup):
@@ -207,7 +210,7 @@ def main():
     value = units * world / (ms / 1e3)
 
     # per-kernel durations (CUDA events on the context's stream) for the roofline
-    prof = ctx.micro_profile(200)
+    prof = ctx.micro_profile(min(200, steps_el))
     force_s = prof["force_ms"] / 1e3
     sm_mhz = (clocks or {}).get("sm_max_mhz", 2070.0) or 2070.0
     fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
@@ -254,8 +257,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 forces + f64 state", "data": "synthetic",
             "config": {"workload": "uneven batch: 64 elements, h 5-20, lateral 10-16, 500-5000 fluid atoms, "
-                                   "g 0.005-0.05, 20000 steps, FP32 forces + FP64 state",
-                       "elements": N_ELEMENTS, "atoms_per_rank": n_atoms, "steps_per_element": STEPS_PER_ELEMENT,
+                                   "g 0.005-0.05, %d steps, FP32 forces + FP64 state" % steps_el,
+                       "elements": N_ELEMENTS, "atoms_per_rank": n_atoms, "steps_per_element": steps_el,
                        "l2": "flushed between timed iterations (256 MB write)",
                        "parallelism": "independent elements per rank" if world > 1 else "1 GPU"},
             "roofline": {"bound": "alu", "kernel": "k_force_cells", "achieved": achieved, "peak": fp32_peak,

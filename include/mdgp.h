@@ -39,7 +39,8 @@ typedef enum {
   MDGP_E_NOTPD = -5,     /* GP covariance not positive definite */
   MDGP_E_TIMEOUT = -6,   /* a bounded device-side wait gave up */
   MDGP_E_STATE = -7,     /* call out of order (e.g. launch before plan) */
-  MDGP_E_OVERFLOW = -8   /* a cell held more atoms than the cell capacity */
+  MDGP_E_OVERFLOW = -8,  /* an atom had more neighbours than the list capacity */
+  MDGP_E_SKIN = -9       /* an atom moved more than half the list skin between rebuilds */
 } mdgp_status;
 
 typedef enum {
@@ -80,7 +81,7 @@ typedef struct {
   double T_meas;   /* mean fluid kinetic temperature m <|v|^2> / 3 over the samples */
   double e_drift;  /* (E_end - E_start) / N_atoms, E = kinetic + LJ (shifted) + tether */
   int64_t n_fluid, n_wall;
-  int32_t status;  /* MDGP_OK or MDGP_E_UNSTABLE / MDGP_E_OVERFLOW for this element */
+  int32_t status;  /* MDGP_OK, or MDGP_E_UNSTABLE / _OVERFLOW / _SKIN for this element */
   int32_t reserved;
 } mdgp_result;
 
@@ -100,7 +101,11 @@ typedef struct {
   int32_t mode;         /* 0: tethered walls + Langevin wall thermostat; 1: frozen walls +
                            Berendsen on the fluid's v_z (paper App. A) */
   int32_t wall_planes;  /* FCC (100) planes per wall (default 3) */
-  int32_t cell_capacity;/* atoms per cell slot array; 0 = choose automatically */
+  int32_t list_capacity;/* neighbour-list entries per atom (default 128; a batch that
+                           overflows it is rerun by mdgp_micro_batch with twice as many) */
+  double skin;          /* Verlet-list skin beyond r_c (default 0.4) */
+  int32_t rebuild_every;/* steps between list rebuilds; 0 = from the skin and T (default 0) */
+  int32_t reserved;
 } mdgp_md_params;
 
 /* Fill *out with the defaults listed above.  Returns MDGP_E_ARG on null. */
@@ -142,9 +147,15 @@ int mdgp_micro_launch(mdgp_ctx* ctx);
 /* Wait for the launched batch and copy its n results to the host. */
 int mdgp_micro_results(mdgp_ctx* ctx, mdgp_result* out, int64_t n);
 
-/* Number of kernel launches the last mdgp_micro_launch enqueued (graph
- * nodes counted one by one). */
+/* Number of kernels the last launched batch ran (graph nodes counted one by
+ * one, including the neighbour-list rebuilds that ran); valid after
+ * mdgp_micro_results. */
 int64_t mdgp_micro_launch_count(const mdgp_ctx* ctx);
+
+/* Number of neighbour-list rebuilds the last batch ran (valid after
+ * mdgp_micro_results).  A rebuild runs when some atom has moved more than
+ * half the skin since the previous one. */
+int64_t mdgp_micro_rebuild_count(const mdgp_ctx* ctx);
 
 /* Copy the planned batch's current atom state to the host: positions and
  * velocities as (n_atoms x 3) row-major doubles, atoms ordered element by
@@ -152,8 +163,9 @@ int64_t mdgp_micro_launch_count(const mdgp_ctx* ctx);
 int mdgp_micro_state(mdgp_ctx* ctx, double* x, double* v, int64_t n_atoms);
 
 /* LJ pair forces of ONE element at the given positions (n_atoms x 3,
- * fluid then walls, as built for `el`), computed by the library's cell-list
- * force kernel in the context's precision: forces (n_atoms x 3), each fluid
+ * fluid then walls, as built for `el`), computed by the library's production
+ * path (cell binning, cell-order sort, Verlet lists, list force kernel) in the
+ * context's precision: forces (n_atoms x 3), each fluid
  * atom's x-virial share (half of x_ij F_x,ij for every pair it is in; 0 for
  * wall atoms) and per-atom shifted LJ energies (half per pair).  Any output
  * may be null. */
@@ -163,10 +175,50 @@ int mdgp_md_forces(mdgp_ctx* ctx, const mdgp_element* el, const double* x, int64
 /* Time the planned batch's kernels one by one: rebuild the elements and run
  * the first `steps` steps without the graph, with CUDA events on the
  * context's stream around every launch.  ms[0] = mean integration kernel
- * time, ms[1] = mean pair-force kernel time (milliseconds per launch),
- * ms[2] = atoms, ms[3] = cells.  Leaves the batch state mid-run (launch it
- * again for results).  MDGP_E_STATE without a plan. */
+ * time, ms[1] = mean pair-force kernel time, ms[2] = mean time of one whole
+ * neighbour-list rebuild (5 kernels), all in milliseconds; ms[3] = atoms,
+ * ms[4] = cells, ms[5] = steps between rebuilds.  Leaves the batch state
+ * mid-run (launch it again for results).  MDGP_E_STATE without a plan. */
 int mdgp_micro_profile(mdgp_ctx* ctx, int64_t steps, double* ms);
+
+/* ------------------------------------------------------------------------ */
+/* Gaussian-process surrogate (paper Sec. 2.2), FP64 on the GPU.             */
+/* ------------------------------------------------------------------------ */
+
+typedef struct mdgp_gp mdgp_gp;
+
+/* Hyperparameters theta = (sf2, l2, sn2) of Sec. 2.3 and the input scaling
+ * of Eq. d2Eq. */
+typedef struct {
+  double sf2;              /* signal variance sigma_f^2 (> 0) */
+  double l2;               /* length scale ell^2 in normalised input space (> 0) */
+  double sn2;              /* noise variance sigma_n^2 added to the diagonal (Eq. covarianceEq, >= 0) */
+  double fallback_scale;   /* scale used where the mean separation is undefined (< 2 entries or
+                              zero spread); <= 0 means 1 */
+  const double* fixed_scales; /* D scales to use instead of the database's mean separations, or null */
+} mdgp_gp_params;
+
+/* Fit a GP to M database entries (Eqs. quadraticKernelEq, d2Eq,
+ * covarianceEq): X is M x D row-major, y has M outputs, mu_X (nullable) the
+ * prior mean at the inputs (zero in the paper; a learned mean otherwise).
+ * The scale of dimension k is the mean of |x_ik - x_jk| over all pairs
+ * i < j.  Builds C = K + sn2 I and its Cholesky factor and
+ * alpha = C^-1 (y - mu_X) in FP64 on the device.  M = 0 gives the prior.
+ * Limits: 0 <= M <= 16384, 1 <= D <= 8.  MDGP_E_NOTPD if C is not positive
+ * definite.  *out is freed with mdgp_gp_free; it uses ctx's device and
+ * stream and must not outlive ctx. */
+int mdgp_gp_fit(mdgp_ctx* ctx, const double* X, const double* y, int64_t M, int32_t D,
+                const mdgp_gp_params* params, const double* mu_X, mdgp_gp** out);
+
+/* Posterior at m queries Xs (m x D): mean = mu_Xs + K(Xs, X) alpha
+ * (Eq. predMeanEq) and the latent variance sf2 - K(Xs, X) C^-1 K(X, Xs) on
+ * the diagonal (Eq. predVarEq), clamped at 0.  mu_Xs may be null (zero prior
+ * mean).  Host arrays; blocking. */
+int mdgp_gp_predict(mdgp_gp* gp, const double* Xs, int64_t m, const double* mu_Xs, double* mean, double* var);
+
+/* The D input scales the fit used (Eq. d2Eq denominators). */
+int mdgp_gp_scales(const mdgp_gp* gp, double* scales);
+int mdgp_gp_free(mdgp_gp* gp);
 
 /* Last CUDA error string seen by the context (static storage). */
 const char* mdgp_last_error(const mdgp_ctx* ctx);

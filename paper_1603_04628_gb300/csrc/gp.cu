@@ -1,0 +1,439 @@
+// Gaussian-process surrogate on the GPU, FP64 throughout (paper Sec. 2.2):
+//   - Eq. d2Eq scales: mean pairwise separation of the database inputs per
+//     dimension (recomputed at every fit);
+//   - Eq. quadraticKernelEq + Eq. covarianceEq: C = K(X, X) + sn2 I;
+//   - blocked right-looking Cholesky C = L L^T (32 x 32 tiles);
+//   - alpha = C^-1 (y - mu(X)) by forward and backward substitution;
+//   - Eq. predMeanEq / predVarEq: per query, k* = K(x*, X), mean =
+//     mu(x*) + k*.alpha, v = L^-1 k*, var = sf2 - |v|^2 (latent variance,
+//     clamped at zero), fused into one kernel per query.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "mdgp.h"
+#include "md_ctx.h"
+
+namespace {
+
+constexpr int TB = 32;            // Cholesky tile
+constexpr int kMaxD = 8;          // input dimensions supported
+constexpr int kMaxM = 16384;      // database entries supported (predict keeps v in shared memory)
+constexpr unsigned kFullMask = 0xffffffffu;
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFullMask, v, o);
+  return v;
+}
+
+// sum over pairs i < j of |x_ik - x_jk|, per dimension k (atomics into out[k])
+__global__ void k_gp_pairsep(const double* X, int M, int D, double* out) {
+  __shared__ double part[kMaxD][8];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double acc[kMaxD];
+  for (int k = 0; k < D; ++k) acc[k] = 0.0;
+  if (i < M) {
+    for (int j = i + 1; j < M; ++j)
+      for (int k = 0; k < D; ++k) acc[k] += fabs(X[(size_t)i * D + k] - X[(size_t)j * D + k]);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int k = 0; k < D; ++k) {
+    const double s = warp_sum_d(acc[k]);
+    if (lane == 0) part[k][wid] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < D) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += part[threadIdx.x][w];
+    atomicAdd(&out[threadIdx.x], s);
+  }
+}
+
+// Turn the pair sums into scales; fall back where undefined.
+__global__ void k_gp_scales(double* sums, int M, int D, double fallback, const double* fixed) {
+  const int k = threadIdx.x;
+  if (k >= D) return;
+  if (fixed) { sums[k] = fixed[k]; return; }
+  double s = fallback;
+  if (M >= 2) {
+    const double m = sums[k] / (0.5 * (double)M * (double)(M - 1));
+    if (m > 0.0) s = m;
+  }
+  sums[k] = s;
+}
+
+__device__ __forceinline__ double se_kernel(const double* a, const double* b, const double* scale, int D,
+                                            double sf2, double l2) {
+  double d2 = 0.0;
+  for (int k = 0; k < D; ++k) {
+    const double t = (a[k] - b[k]) / scale[k];
+    d2 += t * t;
+  }
+  return sf2 * exp(-d2 / (2.0 * l2));
+}
+
+// C (Mp x Mp, row-major, lower part used): K + sn2 I, identity on the padding.
+__global__ void k_gp_cov(const double* X, int M, int Mp, int D, const double* scale, double sf2, double l2,
+                         double sn2, double* C) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y;
+  if (j >= Mp) return;
+  double v;
+  if (i < M && j < M) {
+    v = se_kernel(X + (size_t)i * D, X + (size_t)j * D, scale, D, sf2, l2);
+    if (i == j) v += sn2;
+  } else {
+    v = (i == j) ? 1.0 : 0.0;
+  }
+  C[(size_t)i * Mp + j] = v;
+}
+
+// Cholesky of the diagonal tile kb in place (lower).  One block of TB x TB
+// threads; a non-positive pivot sets *status.
+__global__ void k_potrf_diag(double* A, int Mp, int kb, int* status) {
+  __shared__ double T[TB][TB + 1];
+  const int r = threadIdx.y, c = threadIdx.x;
+  const size_t base = (size_t)kb * TB;
+  T[r][c] = A[(base + r) * Mp + base + c];
+  __syncthreads();
+  for (int k = 0; k < TB; ++k) {
+    if (r == k && c == k) {
+      const double d = T[k][k];
+      if (!(d > 0.0)) atomicMin(status, MDGP_E_NOTPD);
+      T[k][k] = sqrt(d > 0.0 ? d : 1e-300);
+    }
+    __syncthreads();
+    if (c == k && r > k) T[r][k] /= T[k][k];
+    __syncthreads();
+    if (r > k && c > k && c <= r) T[r][c] -= T[r][k] * T[c][k];
+    __syncthreads();
+  }
+  A[(base + r) * Mp + base + c] = c <= r ? T[r][c] : 0.0;
+}
+
+// Panel: A_ik <- A_ik L_kk^-T for every tile row i > kb (one block per tile).
+__global__ void k_trsm_panel(double* A, int Mp, int kb) {
+  __shared__ double L[TB][TB + 1];
+  __shared__ double X[TB][TB + 1];
+  const int r = threadIdx.y, c = threadIdx.x;
+  const int ib = kb + 1 + blockIdx.x;
+  const size_t kr = (size_t)kb * TB, ir = (size_t)ib * TB;
+  L[r][c] = A[(kr + r) * Mp + kr + c];
+  X[r][c] = A[(ir + r) * Mp + kr + c];
+  __syncthreads();
+  // row r of X solves x L^T = a: x_j = (a_j - sum_{l<j} x_l L_jl) / L_jj
+  if (c == 0) {
+    for (int j = 0; j < TB; ++j) {
+      double s = X[r][j];
+      for (int l = 0; l < j; ++l) s -= X[r][l] * L[j][l];
+      X[r][j] = s / L[j][j];
+    }
+  }
+  __syncthreads();
+  A[(ir + r) * Mp + kr + c] = X[r][c];
+}
+
+// Trailing update: A_ij -= L_ik L_jk^T for kb < j <= i (one block per tile).
+__global__ void k_syrk_update(double* A, int Mp, int kb, int nt) {
+  __shared__ double Li[TB][TB + 1];
+  __shared__ double Lj[TB][TB + 1];
+  // map blockIdx.x to a lower-triangle tile (i, j) of the trailing matrix
+  int t = blockIdx.x, i = 0;
+  while (t > i) { t -= i + 1; ++i; }
+  const int j = t;
+  const int ib = kb + 1 + i, jb = kb + 1 + j;
+  if (ib >= nt) return;
+  const int r = threadIdx.y, c = threadIdx.x;
+  const size_t kr = (size_t)kb * TB;
+  Li[r][c] = A[((size_t)ib * TB + r) * Mp + kr + c];
+  Lj[r][c] = A[((size_t)jb * TB + r) * Mp + kr + c];
+  __syncthreads();
+  double s = 0.0;
+#pragma unroll 8
+  for (int l = 0; l < TB; ++l) s += Li[r][l] * Lj[c][l];
+  A[((size_t)ib * TB + r) * Mp + (size_t)jb * TB + c] -= s;
+}
+
+// Forward then backward substitution for one right-hand side (alpha).
+__global__ void k_gp_alpha(const double* L, int M, int Mp, const double* y, const double* mu, double* alpha) {
+  extern __shared__ double z[];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < Mp; i += nt) z[i] = i < M ? y[i] - (mu ? mu[i] : 0.0) : 0.0;
+  __syncthreads();
+  // forward: L z = r, one row at a time with a block-wide dot product
+  __shared__ double red[32];
+  for (int i = 0; i < Mp; ++i) {
+    double s = 0.0;
+    for (int j = tid; j < i; j += nt) s += L[(size_t)i * Mp + j] * z[j];
+    s = warp_sum_d(s);
+    if ((tid & 31) == 0) red[tid >> 5] = s;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < nt / 32; ++w) t += red[w];
+      z[i] = (z[i] - t) / L[(size_t)i * Mp + i];
+    }
+    __syncthreads();
+  }
+  // backward: L^T a = z
+  for (int i = Mp - 1; i >= 0; --i) {
+    double s = 0.0;
+    for (int j = i + 1 + tid; j < Mp; j += nt) s += L[(size_t)j * Mp + i] * z[j];
+    s = warp_sum_d(s);
+    if ((tid & 31) == 0) red[tid >> 5] = s;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < nt / 32; ++w) t += red[w];
+      z[i] = (z[i] - t) / L[(size_t)i * Mp + i];
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < M; i += nt) alpha[i] = z[i];
+}
+
+// One query per block: k*, mean, v = L^-1 k* by blocked forward
+// substitution (tile rows of TB: a block-wide update, then one warp solves
+// the TB x TB triangle), var = sf2 - |v|^2.
+__global__ void k_gp_predict(const double* X, const double* L, const double* alpha, const double* scale,
+                             int M, int Mp, int D, double sf2, double l2, const double* Xs, const double* mus,
+                             double* mean, double* var) {
+  extern __shared__ double v[];
+  __shared__ double xq[kMaxD];
+  __shared__ double red[32];
+  const int q = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5;
+  if (tid < D) xq[tid] = Xs[(size_t)q * D + tid];
+  __syncthreads();
+  double dot = 0.0;
+  for (int i = tid; i < Mp; i += nt) {
+    const double k = i < M ? se_kernel(xq, X + (size_t)i * D, scale, D, sf2, l2) : 0.0;
+    v[i] = k;
+    if (i < M) dot += k * alpha[i];
+  }
+  dot = warp_sum_d(dot);
+  if (lane == 0) red[wid] = dot;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < nt / 32; ++w) t += red[w];
+    mean[q] = (mus ? mus[q] : 0.0) + t;
+  }
+  __syncthreads();
+  const int nblk = Mp / TB;
+  for (int kb = 0; kb < nblk; ++kb) {
+    // update rows of tile kb with the solved part: v_r -= sum_{j < kb*TB} L_rj v_j
+    const int r0 = kb * TB;
+    // nt/TB threads per row
+    const int per = nt / TB;
+    const int row = r0 + tid / per, sub = tid % per;
+    double s = 0.0;
+    for (int j = sub; j < r0; j += per) s += L[(size_t)row * Mp + j] * v[j];
+    // reduce the `per` partial sums of this row (per is a power of two <= 32)
+    for (int o = per >> 1; o > 0; o >>= 1) s += __shfl_down_sync(kFullMask, s, o, per);
+    __syncthreads();
+    if (sub == 0) v[row] -= s;
+    __syncthreads();
+    // triangle solve by warp 0: lane r owns row r0 + r
+    if (wid == 0) {
+      double x = v[r0 + lane];
+      for (int j = 0; j < TB; ++j) {
+        if (lane == j) x /= L[(size_t)(r0 + j) * Mp + r0 + j];
+        const double xs = __shfl_sync(kFullMask, x, j);   // solved unknown j
+        if (lane > j) x -= L[(size_t)(r0 + lane) * Mp + r0 + j] * xs;
+      }
+      v[r0 + lane] = x;
+    }
+    __syncthreads();
+  }
+  double ss = 0.0;
+  for (int i = tid; i < M; i += nt) ss += v[i] * v[i];
+  ss = warp_sum_d(ss);
+  if (lane == 0) red[wid] = ss;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < nt / 32; ++w) t += red[w];
+    const double vv = sf2 - t;
+    var[q] = vv > 0.0 ? vv : 0.0;
+  }
+}
+
+}  // namespace
+
+struct mdgp_gp {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int M = 0, Mp = 0, D = 0;
+  double sf2 = 1, l2 = 1, sn2 = 0;
+  double *dX = nullptr, *dL = nullptr, *dalpha = nullptr, *dscale = nullptr;
+  double *dq = nullptr, *dmu = nullptr, *dmean = nullptr, *dvar = nullptr;
+  size_t qcap = 0;
+  int launches = 0;
+  char err[128] = {0};
+};
+
+static int gp_err(mdgp_gp* g, cudaError_t e) {
+  if (e == cudaSuccess) return MDGP_OK;
+  if (g) std::snprintf(g->err, sizeof(g->err), "%s", cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? MDGP_E_NOMEM : MDGP_E_CUDA;
+}
+
+#define GK(expr)                                  \
+  do {                                            \
+    cudaError_t e_ = (expr);                      \
+    if (e_ != cudaSuccess) return gp_err(g, e_);  \
+  } while (0)
+
+static void gp_release(mdgp_gp* g) {
+  for (double** p : {&g->dX, &g->dL, &g->dalpha, &g->dscale, &g->dq, &g->dmu, &g->dmean, &g->dvar})
+    if (*p) { cudaFree(*p); *p = nullptr; }
+}
+
+static int gp_fit_impl(mdgp_gp* g, const double* X, const double* y, const double* mu_X,
+                       const mdgp_gp_params* p) {
+  const int M = g->M, D = g->D, Mp = g->Mp;
+  cudaStream_t s = g->stream;
+  GK(cudaMalloc(&g->dscale, sizeof(double) * kMaxD));
+  GK(cudaMemsetAsync(g->dscale, 0, sizeof(double) * kMaxD, s));
+  if (M == 0) {
+    std::vector<double> fb(D, p->fallback_scale > 0 ? p->fallback_scale : 1.0);
+    GK(cudaMemcpyAsync(g->dscale, fb.data(), sizeof(double) * D, cudaMemcpyHostToDevice, s));
+    GK(cudaStreamSynchronize(s));
+    return MDGP_OK;
+  }
+  double *dy = nullptr, *dmuX = nullptr, *dfixed = nullptr;
+  int* dstatus = nullptr;
+  GK(cudaMalloc(&g->dX, sizeof(double) * M * D));
+  GK(cudaMalloc(&g->dL, sizeof(double) * (size_t)Mp * Mp));
+  GK(cudaMalloc(&g->dalpha, sizeof(double) * Mp));
+  GK(cudaMalloc(&dy, sizeof(double) * M));
+  GK(cudaMalloc(&dstatus, sizeof(int)));
+  GK(cudaMemcpyAsync(g->dX, X, sizeof(double) * M * D, cudaMemcpyHostToDevice, s));
+  GK(cudaMemcpyAsync(dy, y, sizeof(double) * M, cudaMemcpyHostToDevice, s));
+  GK(cudaMemsetAsync(dstatus, 0, sizeof(int), s));
+  if (mu_X) {
+    GK(cudaMalloc(&dmuX, sizeof(double) * M));
+    GK(cudaMemcpyAsync(dmuX, mu_X, sizeof(double) * M, cudaMemcpyHostToDevice, s));
+  }
+  if (p->fixed_scales) {
+    GK(cudaMalloc(&dfixed, sizeof(double) * D));
+    GK(cudaMemcpyAsync(dfixed, p->fixed_scales, sizeof(double) * D, cudaMemcpyHostToDevice, s));
+  }
+  const double fallback = p->fallback_scale > 0 ? p->fallback_scale : 1.0;
+  if (!p->fixed_scales) {
+    k_gp_pairsep<<<(M + 255) / 256, 256, 0, s>>>(g->dX, M, D, g->dscale);
+    g->launches++;
+  }
+  k_gp_scales<<<1, 32, 0, s>>>(g->dscale, M, D, fallback, dfixed);
+  k_gp_cov<<<dim3((Mp + 127) / 128, Mp), 128, 0, s>>>(g->dX, M, Mp, D, g->dscale, g->sf2, g->l2, g->sn2, g->dL);
+  g->launches += 2;
+  const int nt = Mp / TB;
+  for (int kb = 0; kb < nt; ++kb) {
+    k_potrf_diag<<<1, dim3(TB, TB), 0, s>>>(g->dL, Mp, kb, dstatus);
+    g->launches++;
+    const int rest = nt - kb - 1;
+    if (rest > 0) {
+      k_trsm_panel<<<rest, dim3(TB, TB), 0, s>>>(g->dL, Mp, kb);
+      k_syrk_update<<<rest * (rest + 1) / 2, dim3(TB, TB), 0, s>>>(g->dL, Mp, kb, nt);
+      g->launches += 2;
+    }
+  }
+  k_gp_alpha<<<1, 256, sizeof(double) * Mp, s>>>(g->dL, M, Mp, dy, dmuX, g->dalpha);
+  g->launches++;
+  int status = 0;
+  GK(cudaGetLastError());
+  GK(cudaMemcpyAsync(&status, dstatus, sizeof(int), cudaMemcpyDeviceToHost, s));
+  GK(cudaStreamSynchronize(s));
+  cudaFree(dy);
+  cudaFree(dstatus);
+  if (dmuX) cudaFree(dmuX);
+  if (dfixed) cudaFree(dfixed);
+  return status ? status : MDGP_OK;
+}
+
+extern "C" {
+
+int mdgp_gp_fit(mdgp_ctx* ctx, const double* X, const double* y, int64_t M, int32_t D,
+                const mdgp_gp_params* params, const double* mu_X, mdgp_gp** out) {
+  if (!ctx || !params || !out || M < 0 || M > kMaxM || D < 1 || D > kMaxD) return MDGP_E_ARG;
+  if (M > 0 && (!X || !y)) return MDGP_E_ARG;
+  if (!(params->sf2 > 0) || !(params->l2 > 0) || !(params->sn2 >= 0)) return MDGP_E_ARG;
+  *out = nullptr;
+  cudaSetDevice(ctx->device);
+  mdgp_gp* g = new (std::nothrow) mdgp_gp();
+  if (!g) return MDGP_E_NOMEM;
+  g->device = ctx->device;
+  g->stream = ctx->stream;
+  g->M = (int)M;
+  g->Mp = (int)((M + TB - 1) / TB * TB);
+  g->D = D;
+  g->sf2 = params->sf2;
+  g->l2 = params->l2;
+  g->sn2 = params->sn2;
+  int st = gp_fit_impl(g, X, y, mu_X, params);
+  if (st != MDGP_OK) {
+    std::snprintf(ctx->err, sizeof(ctx->err), "gp fit: %s", g->err[0] ? g->err : "not positive definite");
+    gp_release(g);
+    delete g;
+    return st;
+  }
+  *out = g;
+  return MDGP_OK;
+}
+
+int mdgp_gp_predict(mdgp_gp* g, const double* Xs, int64_t m, const double* mu_Xs, double* mean, double* var) {
+  if (!g || m < 0 || (m > 0 && (!Xs || !mean || !var))) return MDGP_E_ARG;
+  if (m == 0) return MDGP_OK;
+  cudaSetDevice(g->device);
+  if (g->M == 0) {  // empty database: the prior (paper Sec. 3.1)
+    for (int64_t q = 0; q < m; ++q) {
+      mean[q] = mu_Xs ? mu_Xs[q] : 0.0;
+      var[q] = g->sf2;
+    }
+    return MDGP_OK;
+  }
+  cudaStream_t s = g->stream;
+  if ((size_t)m > g->qcap) {
+    for (double** p : {&g->dq, &g->dmu, &g->dmean, &g->dvar})
+      if (*p) { cudaFree(*p); *p = nullptr; }
+    GK(cudaMalloc(&g->dq, sizeof(double) * m * g->D));
+    GK(cudaMalloc(&g->dmu, sizeof(double) * m));
+    GK(cudaMalloc(&g->dmean, sizeof(double) * m));
+    GK(cudaMalloc(&g->dvar, sizeof(double) * m));
+    g->qcap = (size_t)m;
+  }
+  GK(cudaMemcpyAsync(g->dq, Xs, sizeof(double) * m * g->D, cudaMemcpyHostToDevice, s));
+  if (mu_Xs) GK(cudaMemcpyAsync(g->dmu, mu_Xs, sizeof(double) * m, cudaMemcpyHostToDevice, s));
+  const size_t smem = sizeof(double) * g->Mp;
+  if (smem > 48 * 1024)
+    GK(cudaFuncSetAttribute(k_gp_predict, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_gp_predict<<<(unsigned)m, 256, smem, s>>>(g->dX, g->dL, g->dalpha, g->dscale, g->M, g->Mp, g->D, g->sf2,
+                                              g->l2, g->dq, mu_Xs ? g->dmu : nullptr, g->dmean, g->dvar);
+  g->launches++;
+  GK(cudaGetLastError());
+  GK(cudaMemcpyAsync(mean, g->dmean, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
+  GK(cudaMemcpyAsync(var, g->dvar, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
+  GK(cudaStreamSynchronize(s));
+  return MDGP_OK;
+}
+
+int mdgp_gp_scales(const mdgp_gp* g, double* scales) {
+  if (!g || !scales) return MDGP_E_ARG;
+  cudaSetDevice(g->device);
+  if (cudaMemcpy(scales, g->dscale, sizeof(double) * g->D, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return MDGP_E_CUDA;
+  return MDGP_OK;
+}
+
+int mdgp_gp_free(mdgp_gp* g) {
+  if (!g) return MDGP_E_ARG;
+  cudaSetDevice(g->device);
+  gp_release(g);
+  delete g;
+  return MDGP_OK;
+}
+
+}  // extern "C"

@@ -18,21 +18,25 @@ struct mdgp_ctx {
   mdgp_md_params params;
   cudaStream_t stream = nullptr;      // stream all work is enqueued on
   cudaStream_t own_stream = nullptr;  // created with the context
+  cudaStream_t side_stream = nullptr; // captures the conditional rebuild bodies
   char err[256] = {0};
   // MD batch
   bool planned = false;
   long long n_el = 0, steps = 0, n_atoms = 0;
-  long long chunk = 256;  // steps per captured graph
+  long long chunk = 256;  // steps per captured graph (rounded to the rebuild interval)
+  long long rebuild_every = 1;
   long long graph_K = 0, graph_rem_K = 0;
   cudaGraphExec_t graph_full = nullptr, graph_rem = nullptr;
-  long long launches = 0;
+  long long launches = 0;              // kernels enqueued by the last launch (graph bodies: 2 per step)
+  long long launches_with_rebuilds = 0;  // ... plus the rebuild kernels that ran
+  long long rebuilds = 0;
   mdgp::BatchDev B;
   mdgp::PhysDev P;
-  DevBuf d_el, d_aoff, d_coff, d_atomf64, d_force, d_atom_el, d_cell_el, d_counts, d_slots, d_acc, d_grp,
-      d_status, d_results, d_step;
+  DevBuf d_el, d_aoff, d_coff, d_state, d_ints, d_cells, d_pos, d_pbuild, d_force, d_list, d_out, d_acc,
+      d_grp, d_status, d_results, d_step, d_flags;
   std::vector<DevBuf*> all_bufs() {
-    return {&d_el, &d_aoff, &d_coff, &d_atomf64, &d_force, &d_atom_el, &d_cell_el, &d_counts, &d_slots,
-            &d_acc, &d_grp, &d_status, &d_results, &d_step};
+    return {&d_el, &d_aoff, &d_coff, &d_state, &d_ints, &d_cells, &d_pos, &d_pbuild, &d_force, &d_list,
+            &d_out, &d_acc, &d_grp, &d_status, &d_results, &d_step, &d_flags};
   }
   void release_extra() {}
 };

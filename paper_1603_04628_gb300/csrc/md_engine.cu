@@ -1,5 +1,6 @@
 // Micro-element MD engine: host planner, CUDA-graph step loop and the C ABI
 // entry points declared in include/mdgp.h (paper App. A and Sec. 2.1).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -23,9 +24,9 @@ int set_err(mdgp_ctx* c, cudaError_t e) {
   return e == cudaErrorMemoryAllocation ? MDGP_E_NOMEM : MDGP_E_CUDA;
 }
 
-#define CK(expr)                                   \
-  do {                                             \
-    cudaError_t e_ = (expr);                       \
+#define CK(expr)                                    \
+  do {                                              \
+    cudaError_t e_ = (expr);                        \
     if (e_ != cudaSuccess) return set_err(ctx, e_); \
   } while (0)
 
@@ -41,10 +42,10 @@ int ensure(mdgp_ctx* ctx, DevBuf& b, size_t bytes) {
   return MDGP_OK;
 }
 
-// Element geometry (shared definition with the paper's App. A readings:
-// FCC fluid lattice in the slab, FCC (100) wall planes, cells >= r_c).
+// Element geometry from the paper's App. A with the stated readings: FCC
+// fluid lattice filling the slab, FCC (100) wall planes, cells of side at
+// least the list radius r_c + skin.
 int describe(const mdgp_md_params& p, const mdgp_element& el, ElemDev& E, std::string* why) {
-  if (!(el.Lx >= 3.0 * p.rc) || !(el.Lz >= 3.0 * p.rc)) { *why = "Lx and Lz must be >= 3 r_c"; return MDGP_E_ARG; }
   if (!(el.h > 2.0 * p.fluid_margin)) { *why = "h must exceed twice the fluid margin"; return MDGP_E_ARG; }
   if (!(el.density >= 0.0) || !(el.T > 0.0) || el.steps_eq < 0 || el.steps_sample < 0) {
     *why = "density >= 0, T > 0 and non-negative step counts required";
@@ -53,8 +54,8 @@ int describe(const mdgp_md_params& p, const mdgp_element& el, ElemDev& E, std::s
   std::memset(&E, 0, sizeof(E));
   E.Lx = el.Lx; E.Lz = el.Lz; E.h = el.h;
   E.T = el.T;
-  E.g = el.g_ext - (p.mass / (p.mass * el.density > 0 ? p.mass * el.density : 1.0)) * el.dpdx;
-  if (el.density <= 0.0) E.g = el.g_ext;
+  // Eq. momentumEq: F = F_ext - (m / rho) dp/dx with rho = m n
+  E.g = el.density > 0.0 ? el.g_ext - el.dpdx / el.density : el.g_ext;
   E.vsd = std::sqrt(el.T / p.mass);
   E.beta_sd = std::sqrt(2.0 * p.gamma_wall * el.T * p.dt);
   E.seed = el.seed;
@@ -65,7 +66,6 @@ int describe(const mdgp_md_params& p, const mdgp_element& el, ElemDev& E, std::s
   int nb = p.n_blocks < kMaxBlocks ? p.n_blocks : kMaxBlocks;
   if (el.steps_sample < nb) nb = (int)el.steps_sample;
   E.nb = nb;
-  // fluid
   const long nf = lround_half_up(el.density * el.Lx * el.h * el.Lz);
   E.nf = (int)nf;
   const double af = std::cbrt(4.0 / el.density);
@@ -81,7 +81,6 @@ int describe(const mdgp_md_params& p, const mdgp_element& el, ElemDev& E, std::s
   E.fc[0] = (int)cx; E.fc[1] = (int)cy; E.fc[2] = (int)cz;
   E.fb[0] = el.Lx / cx; E.fb[1] = ly / cy; E.fb[2] = el.Lz / cz;
   E.fy0 = p.fluid_margin;
-  // walls
   const double a0 = std::cbrt(4.0 / p.wall_density);
   long wnx = lround_half_up(el.Lx / a0), wnz = lround_half_up(el.Lz / a0);
   if (wnx < 1) wnx = 1;
@@ -89,37 +88,21 @@ int describe(const mdgp_md_params& p, const mdgp_element& el, ElemDev& E, std::s
   E.wnx = (int)wnx; E.wnz = (int)wnz;
   E.wax = el.Lx / wnx; E.waz = el.Lz / wnz; E.wdy = 0.5 * a0;
   E.nw = 2 * p.wall_planes * 2 * (int)wnx * (int)wnz;
-  // cells
   const double th = 0.5 * a0 * (p.wall_planes - 1);
   const double ylo = -th - 1.0, yhi = el.h + th + 1.0;
   E.ylo = ylo;
-  E.nc[0] = (int)std::floor(el.Lx / p.rc);
-  E.nc[2] = (int)std::floor(el.Lz / p.rc);
-  E.nc[1] = (int)std::floor((yhi - ylo) / p.rc);
+  const double rl = p.rc + p.skin;
+  E.nc[0] = (int)std::floor(el.Lx / rl);
+  E.nc[2] = (int)std::floor(el.Lz / rl);
+  E.nc[1] = (int)std::floor((yhi - ylo) / rl);
+  if (!(E.nc[0] >= 3) || !(E.nc[2] >= 3)) { *why = "Lx and Lz must be >= 3 (r_c + skin)"; return MDGP_E_ARG; }
   if (E.nc[1] < 1) E.nc[1] = 1;
   E.cs[0] = el.Lx / E.nc[0]; E.cs[1] = (yhi - ylo) / E.nc[1]; E.cs[2] = el.Lz / E.nc[2];
   for (int d = 0; d < 3; ++d) { E.inv_cs[d] = 1.0 / E.cs[d]; E.csf[d] = (float)E.cs[d]; }
   return MDGP_OK;
 }
 
-// Slots needed per cell: the densest layer (fluid density peaks about 1.6x
-// next to a wall) plus every wall plane falling into one cell, with margin.
-int auto_capacity(const mdgp_md_params& p, const std::vector<ElemDev>& Es, const std::vector<mdgp_element>& els) {
-  double worst = 0.0;
-  for (size_t i = 0; i < Es.size(); ++i) {
-    const ElemDev& E = Es[i];
-    const double vol = E.cs[0] * E.cs[1] * E.cs[2];
-    const double fluid = 1.8 * els[i].density * vol;
-    const double per_plane = 2.0 * E.cs[0] * E.cs[2] / (E.wax * E.waz);
-    const double planes = std::fmin((double)p.wall_planes, std::ceil(E.cs[1] / E.wdy) + 1.0);
-    worst = std::fmax(worst, fluid + per_plane * planes);
-  }
-  int cap = (int)std::ceil(1.5 * worst + 8.0);
-  cap = (cap + 31) / 32 * 32;
-  return cap < 32 ? 32 : cap;
-}
-
-PhysDev make_phys(const mdgp_md_params& p, int cap) {
+PhysDev make_phys(const mdgp_md_params& p, int list_cap) {
   PhysDev P;
   std::memset(&P, 0, sizeof(P));
   P.dt = p.dt;
@@ -131,8 +114,10 @@ PhysDev make_phys(const mdgp_md_params& p, int cap) {
   P.gjf_a = (1.0 - c) / (1.0 + c);
   P.gjf_b = 1.0 / (1.0 + c);
   P.rc2 = p.rc * p.rc;
+  P.rl2 = (p.rc + p.skin) * (p.rc + p.skin);
   const double eps[3] = {1.0, p.eps_wf, p.eps_ww};
   const double sig[3] = {1.0, p.sig_wf, p.sig_ww};
+  P.uniform = 1;
   for (int t = 0; t < 3; ++t) {
     P.eps[t] = eps[t];
     P.sig2[t] = sig[t] * sig[t];
@@ -141,12 +126,15 @@ PhysDev make_phys(const mdgp_md_params& p, int cap) {
     P.active[t] = 1;
     P.epsf[t] = (float)eps[t];
     P.sig2f[t] = (float)(sig[t] * sig[t]);
+    if (eps[t] != 1.0 || sig[t] != 1.0) P.uniform = 0;
   }
-  if (p.mode == 1) P.active[2] = 0;
+  if (p.mode == 1) { P.active[2] = 0; P.uniform = 0; }
   P.mode = p.mode;
   P.wall_planes = p.wall_planes;
-  P.cap = cap;
+  P.list_cap = list_cap;
   P.rc2f = (float)(p.rc * p.rc);
+  P.rl2f = (float)P.rl2;
+  P.half_skin2f = (float)(0.25 * p.skin * p.skin);
   return P;
 }
 
@@ -155,28 +143,72 @@ inline unsigned grid_for(long long n, int threads) {
   return (unsigned)(g < 1 ? 1 : g);
 }
 
+// Steps between list rebuilds: no atom may move more than skin/2 in that
+// time; the speed bound is 8 thermal standard deviations per component.
+int rebuild_interval(const mdgp_md_params& p, double Tmax) {
+  if (p.rebuild_every > 0) return p.rebuild_every;
+  const double vmax = 8.0 * std::sqrt(Tmax / p.mass);
+  int r = (int)std::floor(0.5 * p.skin / (vmax * p.dt));
+  return r < 1 ? 1 : r;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
 // Kernel enqueue helpers (precision dispatch).
 // ---------------------------------------------------------------------------
-static void enqueue_integrate(mdgp_ctx* ctx, int k, int mode) {
+static void enqueue_integrate(mdgp_ctx* ctx, int k, int mode, cudaGraphConditionalHandle h = 0,
+                              int use_cond = 0) {
   const unsigned g = grid_for(ctx->B.n_atoms, 256);
   if (ctx->precision == MDGP_PREC_FP32)
-    k_integrate<float, SlotF><<<g, 256, 0, ctx->stream>>>(ctx->B, ctx->P, k, mode);
+    k_integrate<float, float4><<<g, 256, 0, ctx->stream>>>(ctx->B, ctx->P, k, mode, h, use_cond);
   else
-    k_integrate<double, SlotD><<<g, 256, 0, ctx->stream>>>(ctx->B, ctx->P, k, mode);
+    k_integrate<double, Pos64><<<g, 256, 0, ctx->stream>>>(ctx->B, ctx->P, k, mode, h, use_cond);
   ctx->launches++;
 }
 
-static void enqueue_force(mdgp_ctx* ctx, int k, bool energy) {
-  const unsigned g = grid_for(ctx->B.n_cells * 32, 128);
+// Neighbour-list rebuild: bin, per-element scan, permute into cell order,
+// copy back, build the lists (5 kernels on `s`).
+static void enqueue_rebuild(mdgp_ctx* ctx, cudaStream_t s) {
+  const unsigned g = grid_for(ctx->B.n_atoms, 256);
+  k_bin<<<g, 256, 0, s>>>(ctx->B);
+  k_scan<<<(unsigned)ctx->n_el, 1024, 0, s>>>(ctx->B);
+  const unsigned gb = grid_for(ctx->B.n_cells * 32, 128);
   if (ctx->precision == MDGP_PREC_FP32) {
-    if (energy) k_force_cells<SlotF, float, true><<<g, 128, 0, ctx->stream>>>(ctx->B, ctx->P, k);
-    else k_force_cells<SlotF, float, false><<<g, 128, 0, ctx->stream>>>(ctx->B, ctx->P, k);
+    k_permute<float4><<<g, 256, 0, s>>>(ctx->B);
+    k_copy_back<<<g, 256, 0, s>>>(ctx->B);
+    k_build<float4><<<gb, 128, 0, s>>>(ctx->B, ctx->P);
   } else {
-    if (energy) k_force_cells<SlotD, double, true><<<g, 128, 0, ctx->stream>>>(ctx->B, ctx->P, k);
-    else k_force_cells<SlotD, double, false><<<g, 128, 0, ctx->stream>>>(ctx->B, ctx->P, k);
+    k_permute<Pos64><<<g, 256, 0, s>>>(ctx->B);
+    k_copy_back<<<g, 256, 0, s>>>(ctx->B);
+    k_build<Pos64><<<gb, 128, 0, s>>>(ctx->B, ctx->P);
+  }
+}
+
+static void enqueue_rebuild(mdgp_ctx* ctx) {
+  enqueue_rebuild(ctx, ctx->stream);
+  ctx->launches += 5;
+}
+
+static void enqueue_force(mdgp_ctx* ctx, bool energy) {
+  const unsigned g = grid_for(ctx->B.n_atoms, 128);
+  const bool uni = ctx->P.uniform != 0;
+  if (ctx->precision == MDGP_PREC_FP32) {
+    if (uni) {
+      if (energy) k_force<float4, float, true, true><<<g, 128, 0, ctx->stream>>>(ctx->B, ctx->P);
+      else k_force<float4, float, true, false><<<g, 128, 0, ctx->stream>>>(ctx->B, ctx->P);
+    } else {
+      if (energy) k_force<float4, float, false, true><<<g, 128, 0, ctx->stream>>>(ctx->B, ctx->P);
+      else k_force<float4, float, false, false><<<g, 128, 0, ctx->stream>>>(ctx->B, ctx->P);
+    }
+  } else {
+    if (uni) {
+      if (energy) k_force<Pos64, double, true, true><<<g, 128, 0, ctx->stream>>>(ctx->B, ctx->P);
+      else k_force<Pos64, double, true, false><<<g, 128, 0, ctx->stream>>>(ctx->B, ctx->P);
+    } else {
+      if (energy) k_force<Pos64, double, false, true><<<g, 128, 0, ctx->stream>>>(ctx->B, ctx->P);
+      else k_force<Pos64, double, false, false><<<g, 128, 0, ctx->stream>>>(ctx->B, ctx->P);
+    }
   }
   ctx->launches++;
 }
@@ -188,8 +220,14 @@ static void enqueue_energy(mdgp_ctx* ctx, int which) {
   ctx->launches++;
 }
 
+static void enqueue_export(mdgp_ctx* ctx, int what) {
+  const unsigned g = grid_for(ctx->B.n_atoms, 256);
+  if (ctx->precision == MDGP_PREC_FP32) k_export<float><<<g, 256, 0, ctx->stream>>>(ctx->B, what);
+  else k_export<double><<<g, 256, 0, ctx->stream>>>(ctx->B, what);
+}
+
 // Per element: means, block standard errors, temperature and energy drift.
-__global__ void k_finalize(BatchDev B, PhysDev P, mdgp_result* out) {
+__global__ void k_finalize(BatchDev B, mdgp_result* out) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= B.n_el) return;
   const ElemDev& E = B.el[e];
@@ -235,19 +273,66 @@ __global__ void k_finalize(BatchDev B, PhysDev P, mdgp_result* out) {
 // ---------------------------------------------------------------------------
 // Planning.
 // ---------------------------------------------------------------------------
-static int plan_impl(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int cap_override) {
-  ctx->planned = false;
+static void drop_graphs(mdgp_ctx* ctx) {
   if (ctx->graph_full) { cudaGraphExecDestroy(ctx->graph_full); ctx->graph_full = nullptr; }
   if (ctx->graph_rem) { cudaGraphExecDestroy(ctx->graph_rem); ctx->graph_rem = nullptr; }
+  ctx->graph_K = ctx->graph_rem_K = 0;
+}
+
+// Record `nsteps` steps into a graph.  Each step is: integrate, an IF node
+// whose body rebuilds the neighbour lists (raised by the integrate kernel
+// when some atom moved more than half the skin since the last build), and
+// the force kernel.  The last node advances the step counter.
+static int capture_steps(mdgp_ctx* ctx, long long nsteps, cudaGraphExec_t* out) {
+  cudaGraph_t g;
+  CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+  for (long long k = 0; k < nsteps; ++k) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t cg;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* edges = nullptr;
+    size_t ndeps = 0;
+    CK(cudaStreamGetCaptureInfo(ctx->stream, &cs, nullptr, &cg, &deps, &edges, &ndeps));
+    cudaGraphConditionalHandle h;
+    CK(cudaGraphConditionalHandleCreate(&h, cg, 0, cudaGraphCondAssignDefault));
+    enqueue_integrate(ctx, (int)k, kFinish | kStage1, h, 1);
+    CK(cudaStreamGetCaptureInfo(ctx->stream, &cs, nullptr, &cg, &deps, &edges, &ndeps));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeIf;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, cg, deps, edges, ndeps, &cp));
+    CK(cudaStreamUpdateCaptureDependencies(ctx->stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    CK(cudaStreamBeginCaptureToGraph(ctx->side_stream, body, nullptr, nullptr, 0,
+                                     cudaStreamCaptureModeThreadLocal));
+    enqueue_rebuild(ctx, ctx->side_stream);
+    cudaGraph_t body_out;
+    CK(cudaStreamEndCapture(ctx->side_stream, &body_out));
+    enqueue_force(ctx, false);
+  }
+  k_advance<<<1, 32, 0, ctx->stream>>>((long long*)ctx->d_step.ptr, nsteps);
+  cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+  if (e != cudaSuccess) return set_err(ctx, e);
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  return set_err(ctx, e);
+}
+
+static int plan_impl(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int list_cap_override) {
+  ctx->planned = false;
+  drop_graphs(ctx);
   if (ctx->params.mode != 0) {
     std::snprintf(ctx->err, sizeof(ctx->err), "only mode 0 (tethered walls) runs on the GPU");
     return MDGP_E_ARG;
   }
   std::vector<ElemDev> Es((size_t)n);
-  std::vector<mdgp_element> els(el, el + n);
   std::vector<long long> aoff((size_t)n + 1), coff((size_t)n + 1);
   long long atoms = 0, cells = 0;
   const long long S = el[0].steps_eq + el[0].steps_sample;
+  double Tmax = 0.0;
   for (int64_t i = 0; i < n; ++i) {
     std::string why;
     int st = describe(ctx->params, el[i], Es[i], &why);
@@ -259,38 +344,47 @@ static int plan_impl(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int cap_o
       std::snprintf(ctx->err, sizeof(ctx->err), "elements of one plan must share steps_eq + steps_sample");
       return MDGP_E_ARG;
     }
+    Tmax = std::max(Tmax, el[i].T);
     Es[i].atom0 = atoms;
     Es[i].cell0 = cells;
     aoff[i] = atoms;
     coff[i] = cells;
     atoms += (long long)Es[i].nf + Es[i].nw;
     cells += (long long)Es[i].nc[0] * Es[i].nc[1] * Es[i].nc[2];
+    if ((long long)Es[i].nf + Es[i].nw >= (1LL << 26)) {
+      std::snprintf(ctx->err, sizeof(ctx->err), "element %lld has more than 2^26 atoms", (long long)i);
+      return MDGP_E_ARG;
+    }
   }
   aoff[n] = atoms;
   coff[n] = cells;
-  if (atoms >= (1LL << 30)) {
-    std::snprintf(ctx->err, sizeof(ctx->err), "batch too large (2^30 atoms max)");
+  if (atoms >= (1LL << 31) - 1) {
+    std::snprintf(ctx->err, sizeof(ctx->err), "batch too large (2^31 atoms max)");
     return MDGP_E_ARG;
   }
-  int cap = ctx->params.cell_capacity > 0 ? ctx->params.cell_capacity : auto_capacity(ctx->params, Es, els);
-  if (cap_override > cap) cap = cap_override;
+  int list_cap = ctx->params.list_capacity > 0 ? ctx->params.list_capacity : 128;
+  if (list_cap_override > list_cap) list_cap = list_cap_override;
   const size_t fsz = ctx->precision == MDGP_PREC_FP32 ? 4 : 8;
-  const size_t ssz = ctx->precision == MDGP_PREC_FP32 ? sizeof(SlotF) : sizeof(SlotD);
+  const size_t psz = ctx->precision == MDGP_PREC_FP32 ? sizeof(float4) : sizeof(Pos64);
+  const size_t N = (size_t)atoms, C = (size_t)cells;
   int st;
   if ((st = ensure(ctx, ctx->d_el, sizeof(ElemDev) * n))) return st;
   if ((st = ensure(ctx, ctx->d_aoff, sizeof(long long) * (n + 1)))) return st;
   if ((st = ensure(ctx, ctx->d_coff, sizeof(long long) * (n + 1)))) return st;
-  if ((st = ensure(ctx, ctx->d_atomf64, sizeof(double) * 9 * atoms))) return st;
-  if ((st = ensure(ctx, ctx->d_force, fsz * 5 * atoms))) return st;
-  if ((st = ensure(ctx, ctx->d_atom_el, sizeof(int) * atoms))) return st;
-  if ((st = ensure(ctx, ctx->d_cell_el, sizeof(int) * cells))) return st;
-  if ((st = ensure(ctx, ctx->d_counts, sizeof(int) * 2 * cells))) return st;
-  if ((st = ensure(ctx, ctx->d_slots, ssz * (size_t)cap * cells))) return st;
+  if ((st = ensure(ctx, ctx->d_state, sizeof(double) * 18 * N))) return st;
+  if ((st = ensure(ctx, ctx->d_ints, sizeof(int) * 8 * N))) return st;
+  if ((st = ensure(ctx, ctx->d_cells, sizeof(int) * 4 * C))) return st;
+  if ((st = ensure(ctx, ctx->d_pos, psz * N))) return st;
+  if ((st = ensure(ctx, ctx->d_pbuild, sizeof(float4) * N))) return st;
+  if ((st = ensure(ctx, ctx->d_force, fsz * 5 * N))) return st;
+  if ((st = ensure(ctx, ctx->d_list, sizeof(unsigned) * (size_t)list_cap * N))) return st;
+  if ((st = ensure(ctx, ctx->d_out, sizeof(double) * 6 * N))) return st;
   if ((st = ensure(ctx, ctx->d_acc, sizeof(double) * kAccStride * n))) return st;
   if ((st = ensure(ctx, ctx->d_grp, sizeof(double) * 2 * kGrpStride * n))) return st;
   if ((st = ensure(ctx, ctx->d_status, sizeof(int) * n))) return st;
   if ((st = ensure(ctx, ctx->d_results, sizeof(mdgp_result) * n))) return st;
   if ((st = ensure(ctx, ctx->d_step, sizeof(long long)))) return st;
+  if ((st = ensure(ctx, ctx->d_flags, sizeof(int) * 4))) return st;
   CK(cudaMemcpyAsync(ctx->d_el.ptr, Es.data(), sizeof(ElemDev) * n, cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(ctx->d_aoff.ptr, aoff.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(ctx->d_coff.ptr, coff.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, ctx->stream));
@@ -301,63 +395,49 @@ static int plan_impl(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int cap_o
   B.atom_off = (const long long*)ctx->d_aoff.ptr;
   B.cell_off = (const long long*)ctx->d_coff.ptr;
   B.n_el = (int)n;
-  B.cap = cap;
+  B.list_cap = list_cap;
   B.n_atoms = atoms;
   B.n_cells = cells;
-  double* f64 = (double*)ctx->d_atomf64.ptr;
-  B.x = f64; B.y = f64 + atoms; B.z = f64 + 2 * atoms;
-  B.vx = f64 + 3 * atoms; B.vy = f64 + 4 * atoms; B.vz = f64 + 5 * atoms;
-  B.ax = f64 + 6 * atoms; B.ay = f64 + 7 * atoms; B.az = f64 + 8 * atoms;
+  double* sd = (double*)ctx->d_state.ptr;
+  for (int k = 0; k < 9; ++k) { B.st[k] = sd + k * N; B.st2[k] = sd + (9 + k) * N; }
+  int* ip = (int*)ctx->d_ints.ptr;
+  B.orig = ip; B.cell = ip + N; B.orig2 = ip + 2 * N; B.cell2 = ip + 3 * N;
+  B.atom_el = ip + 4 * N; B.newcell = ip + 5 * N; B.slot = ip + 6 * N; B.nlist = ip + 7 * N;
+  int* cp = (int*)ctx->d_cells.ptr;
+  B.cell_el = cp; B.ccount = cp + C; B.cstart = cp + 2 * C; B.csize = cp + 3 * C;
+  B.pos = ctx->d_pos.ptr;
+  B.pbuild = (float4*)ctx->d_pbuild.ptr;
   char* fb = (char*)ctx->d_force.ptr;
-  B.fx = fb; B.fy = fb + fsz * atoms; B.fz = fb + 2 * fsz * atoms;
-  B.wxx = fb + 3 * fsz * atoms; B.epot = fb + 4 * fsz * atoms;
-  B.atom_el = (int*)ctx->d_atom_el.ptr;
-  B.cell_el = (int*)ctx->d_cell_el.ptr;
-  B.counts = (int*)ctx->d_counts.ptr;
-  B.slots = ctx->d_slots.ptr;
+  B.fx = fb; B.fy = fb + fsz * N; B.fz = fb + 2 * fsz * N;
+  B.wxx = fb + 3 * fsz * N; B.epot = fb + 4 * fsz * N;
+  B.list = (unsigned*)ctx->d_list.ptr;
+  B.out = (double*)ctx->d_out.ptr;
   B.acc = (double*)ctx->d_acc.ptr;
   B.grp = (double*)ctx->d_grp.ptr;
   B.status = (int*)ctx->d_status.ptr;
   B.step_base = (const long long*)ctx->d_step.ptr;
-  ctx->P = make_phys(ctx->params, cap);
+  B.flags = (int*)ctx->d_flags.ptr;
+  ctx->P = make_phys(ctx->params, list_cap);
   ctx->n_el = n;
   ctx->steps = S;
   ctx->n_atoms = atoms;
-  k_fill_maps<<<grid_for(atoms > cells ? atoms : cells, 256) < 2048 ? grid_for(atoms > cells ? atoms : cells, 256) : 2048,
-                256, 0, ctx->stream>>>(B);
+  ctx->rebuild_every = rebuild_interval(ctx->params, Tmax > 0 ? Tmax : 1.0);
+  const long long big = atoms > cells ? atoms : cells;
+  const unsigned gm = grid_for(big, 256);
+  k_fill_maps<<<gm < 4096 ? gm : 4096, 256, 0, ctx->stream>>>(B);
   CK(cudaGetLastError());
 
-  // Capture the step loop: chunks of K steps, each kernel reading the step
-  // counter that a final node advances by K.
+  // Step loop graphs: chunks of K steps plus a remainder chunk.
   const long long K = ctx->chunk;
-  // The first step of a chunk must also finish the previous step; only the
-  // very first step of the run has nothing to finish.  Chunk graphs therefore
-  // always finish at k = 0, and the launch does step 0 eagerly.
-  ctx->graph_K = 0;
-  ctx->graph_rem_K = 0;
-  if (S > 1) {
-    const long long body = S - 1;
-    const long long Kc = body < K ? body : K;
-    auto capture_fin = [&](long long nsteps, cudaGraphExec_t* out) -> int {
-      cudaGraph_t g;
-      CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-      for (long long k = 0; k < nsteps; ++k) {
-        enqueue_integrate(ctx, (int)k, kFinish | kStage1 | kBin);
-        enqueue_force(ctx, (int)k, false);
-      }
-      k_advance<<<1, 32, 0, ctx->stream>>>((long long*)ctx->d_step.ptr, nsteps);
-      cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
-      if (e != cudaSuccess) return set_err(ctx, e);
-      e = cudaGraphInstantiate(out, g, 0);
-      cudaGraphDestroy(g);
-      return set_err(ctx, e);
-    };
+  if (S > 0) {
     const long long saved = ctx->launches;
-    if ((st = capture_fin(Kc, &ctx->graph_full))) return st;
-    ctx->graph_K = Kc;
-    const long long rem = body % Kc;
+    if (S >= K) {
+      if ((st = capture_steps(ctx, K, &ctx->graph_full))) return st;
+      ctx->graph_K = K;
+    }
+    const long long rem = S % K;
     if (rem) {
-      if ((st = capture_fin(rem, &ctx->graph_rem))) return st;
+      if ((st = capture_steps(ctx, rem, &ctx->graph_rem))) return st;
       ctx->graph_rem_K = rem;
     }
     ctx->launches = saved;
@@ -367,47 +447,52 @@ static int plan_impl(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int cap_o
   return MDGP_OK;
 }
 
-static int launch_impl(mdgp_ctx* ctx) {
-  if (!ctx->planned) return MDGP_E_STATE;
-  ctx->launches = 0;
+// kernels in one chunk graph, rebuild bodies not counted
+static long long graph_launches(long long nsteps) { return 2 * nsteps + 1; }
+
+// Reset the accumulators and build the elements (lattice, anchors,
+// Maxwell-Boltzmann velocities).
+static int start_batch(mdgp_ctx* ctx) {
   const int n = (int)ctx->n_el;
-  const long long S = ctx->steps;
   CK(cudaMemsetAsync(ctx->d_acc.ptr, 0, sizeof(double) * kAccStride * n, ctx->stream));
   CK(cudaMemsetAsync(ctx->d_grp.ptr, 0, sizeof(double) * 2 * kGrpStride * n, ctx->stream));
   CK(cudaMemsetAsync(ctx->d_status.ptr, 0, sizeof(int) * n, ctx->stream));
-  CK(cudaMemsetAsync(ctx->d_counts.ptr, 0, sizeof(int) * 2 * ctx->B.n_cells, ctx->stream));
+  CK(cudaMemsetAsync(ctx->B.ccount, 0, sizeof(int) * ctx->B.n_cells, ctx->stream));
   CK(cudaMemsetAsync(ctx->d_step.ptr, 0, sizeof(long long), ctx->stream));
+  CK(cudaMemsetAsync(ctx->B.flags, 0, sizeof(int) * 4, ctx->stream));
   k_init_atoms<<<grid_for(ctx->B.n_atoms, 256), 256, 0, ctx->stream>>>(ctx->B, ctx->P);
   k_init_fix<<<grid_for(ctx->B.n_atoms, 256), 256, 0, ctx->stream>>>(ctx->B, ctx->P);
   ctx->launches += 2;
-  // forces and energy at the initial positions (step "-1" count buffer)
-  enqueue_integrate(ctx, -1, kBin);
-  enqueue_force(ctx, -1, true);
+  return MDGP_OK;
+}
+
+static int launch_impl(mdgp_ctx* ctx) {
+  if (!ctx->planned) return MDGP_E_STATE;
+  ctx->launches = 0;
+  int st;
+  if ((st = start_batch(ctx))) return st;
+  enqueue_rebuild(ctx);
+  enqueue_force(ctx, true);
   enqueue_energy(ctx, kAccE0);
+  const long long S = ctx->steps;
   if (S > 0) {
-    // step 0 has nothing to finish
-    enqueue_integrate(ctx, 0, kStage1 | kBin);
-    enqueue_force(ctx, 0, false);
-    k_advance<<<1, 32, 0, ctx->stream>>>((long long*)ctx->d_step.ptr, 1);
-    ctx->launches++;
     if (ctx->graph_K > 0) {
-      const long long body = S - 1;
-      const long long full = body / ctx->graph_K;
+      const long long full = S / ctx->graph_K;
       for (long long r = 0; r < full; ++r) {
         CK(cudaGraphLaunch(ctx->graph_full, ctx->stream));
-        ctx->launches += 2 * ctx->graph_K + 1;
-      }
-      if (ctx->graph_rem_K) {
-        CK(cudaGraphLaunch(ctx->graph_rem, ctx->stream));
-        ctx->launches += 2 * ctx->graph_rem_K + 1;
+        ctx->launches += graph_launches(ctx->graph_K);
       }
     }
-    // finish the last step (s = S), then its energy at the final positions
+    if (ctx->graph_rem_K) {
+      CK(cudaGraphLaunch(ctx->graph_rem, ctx->stream));
+      ctx->launches += graph_launches(ctx->graph_rem_K);
+    }
+    // finish the last step (s = S), then the energy at the final positions
     enqueue_integrate(ctx, 0, kFinish);
-    enqueue_force(ctx, -1, true);
+    enqueue_force(ctx, true);
   }
   enqueue_energy(ctx, kAccE1);
-  k_finalize<<<grid_for(n, 128), 128, 0, ctx->stream>>>(ctx->B, ctx->P, (mdgp_result*)ctx->d_results.ptr);
+  k_finalize<<<grid_for(ctx->n_el, 128), 128, 0, ctx->stream>>>(ctx->B, (mdgp_result*)ctx->d_results.ptr);
   ctx->launches++;
   CK(cudaGetLastError());
   return MDGP_OK;
@@ -416,7 +501,22 @@ static int launch_impl(mdgp_ctx* ctx) {
 static int results_impl(mdgp_ctx* ctx, mdgp_result* out, int64_t n) {
   if (!ctx->planned) return MDGP_E_STATE;
   if (n != ctx->n_el || !out) return MDGP_E_ARG;
+  int flags[4];
   CK(cudaMemcpyAsync(out, ctx->d_results.ptr, sizeof(mdgp_result) * n, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(flags, ctx->B.flags, sizeof(flags), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  // every rebuild is 5 kernels; the launch sequence counted one eagerly
+  ctx->rebuilds = flags[2];
+  ctx->launches_with_rebuilds = ctx->launches + 5LL * (flags[2] - 1);
+  return MDGP_OK;
+}
+
+static int export_impl(mdgp_ctx* ctx, int what, std::vector<double>& buf) {
+  const size_t N = (size_t)ctx->n_atoms;
+  enqueue_export(ctx, what);
+  CK(cudaGetLastError());
+  buf.resize(6 * N);
+  CK(cudaMemcpyAsync(buf.data(), ctx->B.out, sizeof(double) * 6 * N, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   return MDGP_OK;
 }
@@ -442,7 +542,9 @@ int mdgp_md_params_default(mdgp_md_params* out) {
   out->n_blocks = 10;
   out->mode = 0;
   out->wall_planes = 3;
-  out->cell_capacity = 0;
+  out->list_capacity = 128;
+  out->skin = 0.4;
+  out->rebuild_every = 0;
   return MDGP_OK;
 }
 
@@ -456,8 +558,8 @@ int mdgp_create(mdgp_ctx** out, int device, int precision) {
   mdgp_md_params_default(&ctx->params);
   cudaError_t e = cudaSetDevice(device);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->side_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
-    std::snprintf(ctx->err, sizeof(ctx->err), "%s", cudaGetErrorString(e));
     delete ctx;
     return MDGP_E_CUDA;
   }
@@ -469,11 +571,11 @@ int mdgp_create(mdgp_ctx** out, int device, int precision) {
 int mdgp_destroy(mdgp_ctx* ctx) {
   if (!ctx) return MDGP_E_ARG;
   cudaSetDevice(ctx->device);
-  if (ctx->graph_full) cudaGraphExecDestroy(ctx->graph_full);
-  if (ctx->graph_rem) cudaGraphExecDestroy(ctx->graph_rem);
+  drop_graphs(ctx);
   for (DevBuf* b : ctx->all_bufs()) if (b->ptr) cudaFree(b->ptr);
   ctx->release_extra();
   if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+  if (ctx->side_stream) cudaStreamDestroy(ctx->side_stream);
   delete ctx;
   return MDGP_OK;
 }
@@ -481,7 +583,8 @@ int mdgp_destroy(mdgp_ctx* ctx) {
 int mdgp_set_md_params(mdgp_ctx* ctx, const mdgp_md_params* p) {
   if (!ctx || !p) return MDGP_E_ARG;
   if (!(p->dt > 0) || !(p->rc > 0) || p->n_blocks < 1 || p->wall_planes < 1 || !(p->mass > 0) ||
-      !(p->wall_density > 0) || p->gamma_wall < 0 || p->cell_capacity < 0)
+      !(p->wall_density > 0) || p->gamma_wall < 0 || p->list_capacity < 0 || !(p->skin >= 0) ||
+      p->rebuild_every < 0)
     return MDGP_E_ARG;
   ctx->params = *p;
   ctx->planned = false;
@@ -515,7 +618,9 @@ int mdgp_micro_results(mdgp_ctx* ctx, mdgp_result* out, int64_t n) {
   return results_impl(ctx, out, n);
 }
 
-int64_t mdgp_micro_launch_count(const mdgp_ctx* ctx) { return ctx ? ctx->launches : -1; }
+int64_t mdgp_micro_launch_count(const mdgp_ctx* ctx) { return ctx ? ctx->launches_with_rebuilds : -1; }
+
+int64_t mdgp_micro_rebuild_count(const mdgp_ctx* ctx) { return ctx ? ctx->rebuilds : -1; }
 
 int mdgp_micro_batch(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, mdgp_result* out) {
   if (!ctx || !el || !out || n < 1) return MDGP_E_ARG;
@@ -536,7 +641,7 @@ int mdgp_micro_batch(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, mdgp_resu
       bool overflow = false;
       for (auto& r : res) overflow |= r.status == MDGP_E_OVERFLOW;
       if (!overflow) break;
-      cap = 2 * ctx->B.cap;  // more slots per cell and run again
+      cap = 2 * ctx->B.list_cap;  // longer neighbour lists and run again
     }
     for (size_t j = 0; j < sub.size(); ++j) out[kv.second[j]] = res[j];
   }
@@ -548,11 +653,9 @@ int mdgp_micro_state(mdgp_ctx* ctx, double* x, double* v, int64_t n_atoms) {
   if (!ctx->planned) return MDGP_E_STATE;
   if (n_atoms != ctx->n_atoms) return MDGP_E_ARG;
   cudaSetDevice(ctx->device);
-  std::vector<double> buf((size_t)6 * n_atoms);
-  CK(cudaMemcpyAsync(buf.data(), ctx->B.x, sizeof(double) * 3 * n_atoms, cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaMemcpyAsync(buf.data() + 3 * n_atoms, ctx->B.vx, sizeof(double) * 3 * n_atoms, cudaMemcpyDeviceToHost,
-                     ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
+  std::vector<double> buf;
+  int st = export_impl(ctx, 0, buf);
+  if (st) return st;
   for (int64_t i = 0; i < n_atoms; ++i)
     for (int d = 0; d < 3; ++d) {
       if (x) x[3 * i + d] = buf[(size_t)d * n_atoms + i];
@@ -571,30 +674,25 @@ int mdgp_md_forces(mdgp_ctx* ctx, const mdgp_element* el, const double* x, int64
   int st = plan_impl(ctx, &e1, 1, 0);
   if (st) return st;
   if (n_atoms != ctx->n_atoms) return MDGP_E_ARG;
+  if ((st = start_batch(ctx))) return st;
+  // replace the lattice positions by the caller's (absolute, original order;
+  // the freshly built element is still in original order)
   std::vector<double> soa((size_t)3 * n_atoms);
   for (int64_t i = 0; i < n_atoms; ++i)
     for (int d = 0; d < 3; ++d) soa[(size_t)d * n_atoms + i] = x[3 * i + d];
-  CK(cudaMemcpyAsync(ctx->B.x, soa.data(), sizeof(double) * 3 * n_atoms, cudaMemcpyHostToDevice, ctx->stream));
-  CK(cudaMemsetAsync(ctx->d_counts.ptr, 0, sizeof(int) * 2 * ctx->B.n_cells, ctx->stream));
-  CK(cudaMemsetAsync(ctx->d_status.ptr, 0, sizeof(int), ctx->stream));
-  CK(cudaMemsetAsync(ctx->d_step.ptr, 0, sizeof(long long), ctx->stream));
-  enqueue_integrate(ctx, -1, kBin);
-  enqueue_force(ctx, -1, true);
-  CK(cudaGetLastError());
-  const size_t fsz = ctx->precision == MDGP_PREC_FP32 ? 4 : 8;
-  std::vector<char> raw(fsz * 5 * n_atoms);
+  for (int d = 0; d < 3; ++d)
+    CK(cudaMemcpyAsync(ctx->B.st[d], soa.data() + (size_t)d * n_atoms, sizeof(double) * n_atoms,
+                       cudaMemcpyHostToDevice, ctx->stream));
+  enqueue_rebuild(ctx);
+  enqueue_force(ctx, true);
+  std::vector<double> buf;
+  if ((st = export_impl(ctx, 1, buf))) return st;
   int status = 0;
-  CK(cudaMemcpyAsync(raw.data(), ctx->B.fx, fsz * 5 * n_atoms, cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaMemcpyAsync(&status, ctx->d_status.ptr, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
-  auto get = [&](int arr, int64_t i) -> double {
-    if (fsz == 4) return (double)((const float*)raw.data())[(size_t)arr * n_atoms + i];
-    return ((const double*)raw.data())[(size_t)arr * n_atoms + i];
-  };
+  CK(cudaMemcpy(&status, ctx->d_status.ptr, sizeof(int), cudaMemcpyDeviceToHost));
   for (int64_t i = 0; i < n_atoms; ++i) {
-    if (f) for (int d = 0; d < 3; ++d) f[3 * i + d] = get(d, i);
-    if (wxx) wxx[i] = get(3, i);
-    if (epot) epot[i] = get(4, i);
+    if (f) for (int d = 0; d < 3; ++d) f[3 * i + d] = buf[(size_t)d * n_atoms + i];
+    if (wxx) wxx[i] = buf[(size_t)3 * n_atoms + i];
+    if (epot) epot[i] = buf[(size_t)4 * n_atoms + i];
   }
   return status ? status : MDGP_OK;
 }
@@ -604,41 +702,41 @@ int mdgp_micro_profile(mdgp_ctx* ctx, int64_t steps, double* ms) {
   if (!ctx->planned) return MDGP_E_STATE;
   if (steps > ctx->steps) steps = ctx->steps;
   cudaSetDevice(ctx->device);
-  const int n = (int)ctx->n_el;
-  CK(cudaMemsetAsync(ctx->d_acc.ptr, 0, sizeof(double) * kAccStride * n, ctx->stream));
-  CK(cudaMemsetAsync(ctx->d_grp.ptr, 0, sizeof(double) * 2 * kGrpStride * n, ctx->stream));
-  CK(cudaMemsetAsync(ctx->d_status.ptr, 0, sizeof(int) * n, ctx->stream));
-  CK(cudaMemsetAsync(ctx->d_counts.ptr, 0, sizeof(int) * 2 * ctx->B.n_cells, ctx->stream));
-  CK(cudaMemsetAsync(ctx->d_step.ptr, 0, sizeof(long long), ctx->stream));
-  k_init_atoms<<<grid_for(ctx->B.n_atoms, 256), 256, 0, ctx->stream>>>(ctx->B, ctx->P);
-  k_init_fix<<<grid_for(ctx->B.n_atoms, 256), 256, 0, ctx->stream>>>(ctx->B, ctx->P);
-  enqueue_integrate(ctx, -1, kBin);
-  enqueue_force(ctx, -1, false);
+  int st;
+  if ((st = start_batch(ctx))) return st;
+  enqueue_rebuild(ctx);
+  enqueue_force(ctx, false);
   std::vector<cudaEvent_t> ev((size_t)(3 * steps + 1));
   for (auto& e : ev) CK(cudaEventCreate(&e));
   CK(cudaEventRecord(ev[0], ctx->stream));
   for (int64_t k = 0; k < steps; ++k) {
-    // step_base stays 0: kernel k uses step k
-    enqueue_integrate(ctx, (int)k, (k == 0 ? 0 : kFinish) | kStage1 | kBin);
+    // the step counter stays 0: launch k works on step k
+    enqueue_integrate(ctx, (int)k, kFinish | kStage1);
     CK(cudaEventRecord(ev[3 * k + 1], ctx->stream));
-    enqueue_force(ctx, (int)k, false);
+    if (k % ctx->rebuild_every == 0) enqueue_rebuild(ctx);
     CK(cudaEventRecord(ev[3 * k + 2], ctx->stream));
+    enqueue_force(ctx, false);
     CK(cudaEventRecord(ev[3 * k + 3], ctx->stream));
   }
   CK(cudaStreamSynchronize(ctx->stream));
-  double t_int = 0.0, t_force = 0.0;
+  double t_int = 0.0, t_reb = 0.0, t_force = 0.0;
+  long long nreb = 0;
   for (int64_t k = 0; k < steps; ++k) {
-    float a = 0.f, b = 0.f;
+    float a = 0.f, b = 0.f, c = 0.f;
     cudaEventElapsedTime(&a, ev[3 * k], ev[3 * k + 1]);
     cudaEventElapsedTime(&b, ev[3 * k + 1], ev[3 * k + 2]);
+    cudaEventElapsedTime(&c, ev[3 * k + 2], ev[3 * k + 3]);
     t_int += a;
-    t_force += b;
+    t_force += c;
+    if (k % ctx->rebuild_every == 0) { t_reb += b; ++nreb; }
   }
   for (auto& e : ev) cudaEventDestroy(e);
   ms[0] = t_int / steps;
   ms[1] = t_force / steps;
-  ms[2] = (double)ctx->n_atoms;
-  ms[3] = (double)ctx->B.n_cells;
+  ms[2] = nreb ? t_reb / nreb : 0.0;
+  ms[3] = (double)ctx->n_atoms;
+  ms[4] = (double)ctx->B.n_cells;
+  ms[5] = (double)ctx->rebuild_every;
   return MDGP_OK;
 }
 

@@ -1,16 +1,23 @@
 // Internal device-side types of the micro-element MD engine.
 //
-// Layout in HBM (one flattened batch, elements back to back):
-//   atoms   SoA FP64 x, y, z, v_x, v_y, v_z, anchor x/y/z (wall tether sites);
-//           forces in the pair-force precision (float or double) SoA;
-//           per-atom x-virial share and shifted LJ energy; atom -> element map.
-//           Within an element: fluid atoms first, then bottom and top walls.
-//   cells   per element a grid of ncx x ncy x ncz cells of side >= r_c
-//           (x, z periodic; y spans both walls); a fixed-capacity slot array
-//           per cell holding cell-centre-relative positions + a tag
-//           (atom << 1 | species); two count buffers used on alternate steps.
-//   accum   per element FP64 block sums of q and P_xx, temperature sum and
-//           energies (the time-averaged measurements of the paper's Sec. 2.1).
+// Layout in HBM (one flattened batch, elements back to back; element e owns
+// atoms [atom0, atom0 + nf + nw) and cells [cell0, cell0 + ncx*ncy*ncz)):
+//   atoms  kept in cell order (re-sorted at every neighbour-list rebuild);
+//          FP64 SoA: position as an offset from the centre of the atom's
+//          reference cell (the cell it was binned into at the last rebuild),
+//          velocity, and for wall atoms the tether anchor in the same frame;
+//          int32 original index (element-local, fluid first) and reference
+//          cell; the pair-force input position (float4 or double4: offset
+//          from the cell centre, w = species) and its value at the last
+//          rebuild (skin check); forces, fluid x-virial share and energy in
+//          the pair-force precision.
+//   lists  per atom up to list_cap neighbour entries, entry-major
+//          ([k][atom], so a warp's loads coalesce): bits 0-25 the neighbour's
+//          element-local sorted index, bits 26-31 the cell shift
+//          (dx+1, dy+1, dz+1) in 2 bits each.
+//   cells  count (binning atomics), start and size after the per-element scan.
+//   accum  per element FP64 block sums of q and P_xx, temperature sum and the
+//          start/end energies (the time-averaged measurements of Sec. 2.1).
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -18,15 +25,24 @@
 namespace mdgp {
 
 constexpr int kMaxBlocks = 64;
-// per-element accumulator layout (doubles)
 constexpr int kAccQ = 0;                      // q block sums [kMaxBlocks]
 constexpr int kAccP = kMaxBlocks;             // P_xx block sums [kMaxBlocks]
-constexpr int kAccT = 2 * kMaxBlocks;         // sum of fluid kinetic temperature
+constexpr int kAccT = 2 * kMaxBlocks;         // sum of fluid m|v|^2 over samples
 constexpr int kAccE0 = 2 * kMaxBlocks + 1;    // total energy before the first step
 constexpr int kAccE1 = 2 * kMaxBlocks + 2;    // total energy after the last step
 constexpr int kAccStride = 2 * kMaxBlocks + 4;
-// per-element init sums: per group (fluid, wall) sum v_x, v_y, v_z, sum v^2
-constexpr int kGrpStride = 8;
+constexpr int kGrpStride = 8;                 // init sums per group: sum v, sum v^2
+constexpr unsigned kJMask = 0x03FFFFFFu;      // neighbour index bits of a list entry
+
+// status codes written per element (match mdgp_status)
+constexpr int kStUnstable = -4;
+constexpr int kStOverflow = -8;
+constexpr int kStSkin = -9;
+
+// FP64 pair-force input position (offset from the cell centre, w = species).
+struct __align__(32) Pos64 {
+  double x, y, z, w;
+};
 
 struct ElemDev {
   double Lx, Lz, h, ylo;
@@ -55,40 +71,45 @@ struct PhysDev {
   double dt, hdt_m, inv_m, mass;
   double k_tether;
   double gjf_a, gjf_b;
-  double rc2;
+  double rc2, rl2;                     // cut-off and list radius squared
   double eps[3], sig2[3], eshift[3];   // pair type t = species_i + species_j
   int active[3];
+  int uniform;                         // all three pair types (1, 1) and active
   int mode;
   int wall_planes;
-  int cap;
-  float rc2f;
+  int list_cap;
+  float rc2f, rl2f, half_skin2f;
   float epsf[3], sig2f[3];
 };
-
-// Cell slot entries: position relative to the cell centre and a tag.
-struct SlotF { float x, y, z; int tag; };
-struct __align__(16) SlotD { double x, y, z; int tag; int pad; };
 
 struct BatchDev {
   const ElemDev* el;
   const long long* atom_off;   // [n_el + 1]
   const long long* cell_off;   // [n_el + 1]
   int n_el;
-  int cap;
+  int list_cap;
   long long n_atoms, n_cells;
-  double *x, *y, *z, *vx, *vy, *vz, *ax, *ay, *az;
-  void *fx, *fy, *fz;          // float or double
-  void *wxx, *epot;            // float or double
-  int* atom_el;
+  // current atom state (cell order) and the permutation target
+  double* st[9];               // ox oy oz vx vy vz ax ay az
+  double* st2[9];
+  int *orig, *cell, *orig2, *cell2;
+  int* atom_el;                // fixed: elements keep their atom ranges
   int* cell_el;
-  int* counts;                 // [2 * n_cells]
-  void* slots;                 // [n_cells * cap]
-  double* acc;                 // [n_el * kAccStride]
-  double* grp;                 // [n_el * 2 * kGrpStride]
-  int* status;                 // [n_el]
-  const long long* step_base;  // device step counter (advanced per graph chunk)
+  void* pos;                   // float4 or double4 [n_atoms]
+  float4* pbuild;              // pos at the last rebuild
+  void *fx, *fy, *fz, *wxx, *epot;
+  int *ccount, *cstart, *csize;   // [n_cells]
+  int *newcell, *slot;            // [n_atoms]
+  unsigned* list;                 // [list_cap * n_atoms]
+  int* nlist;                     // [n_atoms]
+  double* acc;                    // [n_el * kAccStride]
+  double* grp;                    // [n_el * 2 * kGrpStride]
+  int* status;                    // [n_el]
+  const long long* step_base;     // device step counter (advanced per graph chunk)
+  double* out;                    // export scratch [6 * n_atoms] (original order)
+  int* flags;                     // [0] rebuild needed, [1] blocks done, [2] rebuilds run
 };
 
-enum : int { kFinish = 1, kStage1 = 2, kBin = 4 };
+enum : int { kFinish = 1, kStage1 = 2 };
 
 }  // namespace mdgp

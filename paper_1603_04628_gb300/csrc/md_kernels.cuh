@@ -24,20 +24,32 @@ __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
   return c;
 }
 
-// Three standard normals (Box-Muller on the block's first and second pairs).
+// Three standard normals by Box-Muller on the block's two pairs of uniforms,
+// in double (FP64 path) or in single precision from the top 24 bits (FP32
+// path: the noise enters the FP64 update as a small term).
+template <typename T>
 __device__ __forceinline__ void normals3(uint32_t atom, uint32_t step, uint32_t elem, uint32_t stream,
                                          unsigned long long seed, double& n0, double& n1, double& n2) {
   const uint4 r = philox10(make_uint4(atom, step, elem, stream), (uint32_t)seed, (uint32_t)(seed >> 32));
-  const double inv32 = 2.3283064365386962890625e-10;  // 2^-32
-  double u1 = ((double)r.x + 0.5) * inv32, u2 = ((double)r.y + 0.5) * inv32;
-  double u3 = ((double)r.z + 0.5) * inv32, u4 = ((double)r.w + 0.5) * inv32;
-  double rad1 = sqrt(-2.0 * log(u1)), rad2 = sqrt(-2.0 * log(u3));
-  double s1, c1, s2, c2;
-  sincospi(2.0 * u2, &s1, &c1);
-  sincospi(2.0 * u4, &s2, &c2);
-  n0 = rad1 * c1;
-  n1 = rad1 * s1;
-  n2 = rad2 * c2;
+  if constexpr (sizeof(T) == 8) {
+    const double inv32 = 2.3283064365386962890625e-10;  // 2^-32
+    const double u1 = ((double)r.x + 0.5) * inv32, u2 = ((double)r.y + 0.5) * inv32;
+    const double u3 = ((double)r.z + 0.5) * inv32, u4 = ((double)r.w + 0.5) * inv32;
+    const double rad1 = sqrt(-2.0 * log(u1)), rad2 = sqrt(-2.0 * log(u3));
+    double s1, c1, s2, c2;
+    sincospi(2.0 * u2, &s1, &c1);
+    sincospi(2.0 * u4, &s2, &c2);
+    n0 = rad1 * c1; n1 = rad1 * s1; n2 = rad2 * c2;
+  } else {
+    const float inv24 = 5.9604644775390625e-8f;  // 2^-24
+    const float u1 = ((float)(r.x >> 8) + 0.5f) * inv24, u2 = ((float)(r.y >> 8) + 0.5f) * inv24;
+    const float u3 = ((float)(r.z >> 8) + 0.5f) * inv24, u4 = ((float)(r.w >> 8) + 0.5f) * inv24;
+    const float rad1 = sqrtf(-2.0f * logf(u1)), rad2 = sqrtf(-2.0f * logf(u3));
+    float s1, c1, s2, c2;
+    sincospif(2.0f * u2, &s1, &c1);
+    sincospif(2.0f * u4, &s2, &c2);
+    n0 = (double)(rad1 * c1); n1 = (double)(rad1 * s1); n2 = (double)(rad2 * c2);
+  }
 }
 
 template <typename T>
@@ -48,8 +60,8 @@ __device__ __forceinline__ T warp_sum(T v) {
 }
 
 // Warp-cooperative segmented reduction: lanes with equal key >= 0 add their
-// NV values; one atomicAdd per (key, value) at dst(key)[i].  All 32 lanes
-// must call it.
+// NV values; one atomicAdd per (key, value) at dst(key, i).  All 32 lanes of
+// the warp must call it.
 template <int NV, typename DstFn>
 __device__ __forceinline__ void seg_add(int key, const double (&val)[NV], DstFn dst) {
   const int lane = threadIdx.x & 31;
@@ -68,7 +80,6 @@ __device__ __forceinline__ void seg_add(int key, const double (&val)[NV], DstFn 
 }
 
 __device__ __forceinline__ double wrap_periodic(double x, double L) {
-  // into [0, L); atoms move far less than L per step
   if (x >= L) x -= L;
   if (x < 0.0) x += L;
   if (x >= L || x < 0.0) x -= L * floor(x / L);
@@ -76,6 +87,35 @@ __device__ __forceinline__ double wrap_periodic(double x, double L) {
 }
 
 __device__ __forceinline__ double min_image(double d, double L) { return d - L * rint(d / L); }
+
+__device__ __forceinline__ void cell_coords(const ElemDev& E, long long c, int& ix, int& iy, int& iz) {
+  const long long l = c - E.cell0;
+  iz = (int)(l % E.nc[2]);
+  iy = (int)((l / E.nc[2]) % E.nc[1]);
+  ix = (int)(l / ((long long)E.nc[2] * E.nc[1]));
+}
+
+__device__ __forceinline__ void cell_center(const ElemDev& E, long long c, double& cx, double& cy, double& cz) {
+  int ix, iy, iz;
+  cell_coords(E, c, ix, iy, iz);
+  cx = ((double)ix + 0.5) * E.cs[0];
+  cy = E.ylo + ((double)iy + 0.5) * E.cs[1];
+  cz = ((double)iz + 0.5) * E.cs[2];
+}
+
+// Absolute position of atom i (x and z wrapped into the periodic box).
+__device__ __forceinline__ void abs_position(const BatchDev& B, const ElemDev& E, long long i, double& x,
+                                             double& y, double& z) {
+  x = B.st[0][i]; y = B.st[1][i]; z = B.st[2][i];
+  const int c = B.cell[i];
+  if (c >= 0) {
+    double cx, cy, cz;
+    cell_center(E, c, cx, cy, cz);
+    x += cx; y += cy; z += cz;
+  }
+  x = wrap_periodic(x, E.Lx);
+  z = wrap_periodic(z, E.Lz);
+}
 
 // ---------------------------------------------------------------------------
 // Maps: atom -> element and cell -> element by binary search on the offsets.
@@ -104,8 +144,8 @@ __global__ void k_fill_maps(BatchDev B) {
 // ---------------------------------------------------------------------------
 // Element build: FCC fluid lattice with evenly spread vacancies, FCC (100)
 // wall planes with anchors, Maxwell-Boltzmann velocities from the init stream
-// (paper: "fluid atoms in a lattice, with zero mean velocity").  Group sums
-// for the mean-velocity removal go to B.grp.
+// (paper: "fluid atoms in a lattice, with zero mean velocity").  Positions are
+// written absolute (reference cell -1) until the first rebuild.
 // ---------------------------------------------------------------------------
 __global__ void k_init_atoms(BatchDev B, PhysDev P) {
   const long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -148,12 +188,14 @@ __global__ void k_init_atoms(BatchDev B, PhysDev P) {
       py = wall == 0 ? -(double)k * E.wdy : E.h + (double)k * E.wdy;
       pz = ((double)j + oz) * E.waz;
     }
-    B.x[a] = px; B.y[a] = py; B.z[a] = pz;
-    B.ax[a] = px; B.ay[a] = py; B.az[a] = pz;
+    B.st[0][a] = px; B.st[1][a] = py; B.st[2][a] = pz;
+    B.st[6][a] = px; B.st[7][a] = py; B.st[8][a] = pz;
+    B.orig[a] = (int)l;
+    B.cell[a] = -1;
     double n0, n1, n2;
-    normals3((uint32_t)l, 0u, (uint32_t)E.id, 0u, E.seed, n0, n1, n2);
+    normals3<double>((uint32_t)l, 0u, (uint32_t)E.id, 0u, E.seed, n0, n1, n2);
     const double vx = E.vsd * n0, vy = E.vsd * n1, vz = E.vsd * n2;
-    B.vx[a] = vx; B.vy[a] = vy; B.vz[a] = vz;
+    B.st[3][a] = vx; B.st[4][a] = vy; B.st[5][a] = vz;
     key = 2 * e + group;
     val[0] = vx; val[1] = vy; val[2] = vz; val[3] = vx * vx + vy * vy + vz * vz;
   }
@@ -167,167 +209,162 @@ __global__ void k_init_fix(BatchDev B, PhysDev P) {
   if (a >= B.n_atoms) return;
   const int e = B.atom_el[a];
   const ElemDev& E = B.el[e];
-  const long long l = a - E.atom0;
-  const int group = l < E.nf ? 0 : 1;
+  const int group = B.orig[a] < E.nf ? 0 : 1;
   const double cnt = group == 0 ? (double)E.nf : (double)E.nw;
   const double* g = B.grp + (size_t)(2 * e + group) * kGrpStride;
   const double mx = g[0] / cnt, my = g[1] / cnt, mz = g[2] / cnt;
-  double vx = B.vx[a] - mx, vy = B.vy[a] - my, vz = B.vz[a] - mz;
+  double vx = B.st[3][a] - mx, vy = B.st[4][a] - my, vz = B.st[5][a] - mz;
   const double ke2 = P.mass * (g[3] - cnt * (mx * mx + my * my + mz * mz));
   if (cnt > 1.0 && ke2 > 0.0) {
     const double s = sqrt(E.T / (ke2 / (3.0 * (cnt - 1.0))));
     vx *= s; vy *= s; vz *= s;
   }
-  B.vx[a] = vx; B.vy[a] = vy; B.vz[a] = vz;
+  B.st[3][a] = vx; B.st[4][a] = vy; B.st[5][a] = vz;
 }
 
 // ---------------------------------------------------------------------------
-// Fused integration kernel.  With s the step being started:
-//   kFinish  completes step s-1: v = u + dt/(2m) F(x) and samples it;
-//   kStage1  first stage of step s: fluid velocity-Verlet half kick + drift,
-//            tethered wall atoms G-JF (Gronbech-Jensen & Farago 2013);
-//   kBin     bins the new positions into cell slots of count buffer (s & 1)
-//            and clears the other count buffer.
-// F(x) = LJ (from the force kernel) + body force g on fluid atoms (Eq.
-// momentumEq) + tether -k (r - r0) on wall atoms.
+// Neighbour-list rebuild, step 1: bin every atom into its cell (counting
+// sort histogram by atomics; x and z periodic, y clamped to the edge cells).
 // ---------------------------------------------------------------------------
-template <typename FT, typename Slot>
-__global__ void __launch_bounds__(256) k_integrate(BatchDev B, PhysDev P, int k, int mode) {
-  const long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const long long s = *B.step_base + k;
-  int mkey = -1;
-  int mblk = 0;
-  double mval[3] = {0.0, 0.0, 0.0};
-  if (a < B.n_atoms) {
-    const int e = B.atom_el[a];
-    const ElemDev& E = B.el[e];
-    const long long l = a - E.atom0;
-    const bool fluid = l < E.nf;
-    double x = B.x[a], y = B.y[a], z = B.z[a];
-    double vx = B.vx[a], vy = B.vy[a], vz = B.vz[a];
-    if (mode & (kFinish | kStage1)) {
-      double fx = (double)static_cast<const FT*>(B.fx)[a];
-      double fy = (double)static_cast<const FT*>(B.fy)[a];
-      double fz = (double)static_cast<const FT*>(B.fz)[a];
-      if (fluid) {
-        fx += E.g;
-      } else {
-        const double dx = min_image(x - B.ax[a], E.Lx), dy = y - B.ay[a], dz = min_image(z - B.az[a], E.Lz);
-        fx -= P.k_tether * dx; fy -= P.k_tether * dy; fz -= P.k_tether * dz;
-      }
-      if (mode & kFinish) {
-        vx += P.hdt_m * fx; vy += P.hdt_m * fy; vz += P.hdt_m * fz;
-        const long long ks = s - 1 - E.steps_eq;
-        const double v2 = vx * vx + vy * vy + vz * vz;
-        if (!(v2 < 1e30) || !(fabs(y) < 1e6)) atomicMin(&B.status[e], -4);
-        if (fluid && ks >= 0 && ks < E.steps_sample && E.nb > 0) {
-          mkey = e;
-          mblk = (int)((ks * E.nb) / E.steps_sample);
-          mval[0] = P.mass * vx;
-          mval[1] = P.mass * vx * vx + (double)static_cast<const FT*>(B.wxx)[a];
-          mval[2] = P.mass * v2;
-        }
-      }
-      if (mode & kStage1) {
-        if (fluid) {
-          vx += P.hdt_m * fx; vy += P.hdt_m * fy; vz += P.hdt_m * fz;
-          x += P.dt * vx; y += P.dt * vy; z += P.dt * vz;
-        } else {
-          double b0 = 0.0, b1 = 0.0, b2 = 0.0;
-          if (E.beta_sd > 0.0) {
-            normals3((uint32_t)l, (uint32_t)s, (uint32_t)E.id, 1u, E.seed, b0, b1, b2);
-            b0 *= E.beta_sd; b1 *= E.beta_sd; b2 *= E.beta_sd;
-          }
-          const double bdt = P.gjf_b * P.dt, h2m = P.dt / (2.0 * P.mass), i2m = 1.0 / (2.0 * P.mass);
-          x += bdt * (vx + h2m * fx + b0 * i2m);
-          y += bdt * (vy + h2m * fy + b1 * i2m);
-          z += bdt * (vz + h2m * fz + b2 * i2m);
-          const double bm = P.gjf_b * P.inv_m;
-          vx = P.gjf_a * vx + h2m * P.gjf_a * fx + bm * b0;
-          vy = P.gjf_a * vy + h2m * P.gjf_a * fy + bm * b1;
-          vz = P.gjf_a * vz + h2m * P.gjf_a * fz + bm * b2;
-        }
-        x = wrap_periodic(x, E.Lx);
-        z = wrap_periodic(z, E.Lz);
-        B.x[a] = x; B.y[a] = y; B.z[a] = z;
-      }
-      B.vx[a] = vx; B.vy[a] = vy; B.vz[a] = vz;
+__global__ void __launch_bounds__(256) k_bin(BatchDev B) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i == 0) atomicAdd(&B.flags[2], 1);
+  if (i >= B.n_atoms) return;
+  const ElemDev& E = B.el[B.atom_el[i]];
+  double x, y, z;
+  abs_position(B, E, i, x, y, z);
+  int ix = (int)(x * E.inv_cs[0]), iz = (int)(z * E.inv_cs[2]);
+  const double yr = (y - E.ylo) * E.inv_cs[1];
+  const int iy = yr < 0.0 ? 0 : (yr >= (double)E.nc[1] ? E.nc[1] - 1 : (int)yr);
+  ix = ix < 0 ? 0 : (ix >= E.nc[0] ? E.nc[0] - 1 : ix);
+  iz = iz < 0 ? 0 : (iz >= E.nc[2] ? E.nc[2] - 1 : iz);
+  const long long c = E.cell0 + ((long long)ix * E.nc[1] + iy) * E.nc[2] + iz;
+  B.newcell[i] = (int)c;
+  B.slot[i] = atomicAdd(&B.ccount[c], 1);
+}
+
+// Step 2: per element (one block), exclusive scan of the cell counts; cell c
+// then owns sorted atoms [start, start + size).  Counts are cleared for the
+// next rebuild.
+__global__ void __launch_bounds__(1024) k_scan(BatchDev B) {
+  __shared__ int warp_tot[32];
+  __shared__ int carry;
+  const ElemDev& E = B.el[blockIdx.x];
+  const long long ncell = (long long)E.nc[0] * E.nc[1] * E.nc[2];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (long long base = 0; base < ncell; base += blockDim.x) {
+    const long long c = base + threadIdx.x;
+    const int v = c < ncell ? B.ccount[E.cell0 + c] : 0;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, x, o);
+      if (lane >= o) x += y;
     }
-    if (mode & kBin) {
-      // cell of the (wrapped) position; y outside the grid clamps to the edge cells
-      const double xw = wrap_periodic(x, E.Lx), zw = wrap_periodic(z, E.Lz);
-      int ix = (int)(xw * E.inv_cs[0]), iz = (int)(zw * E.inv_cs[2]);
-      const double yr = (y - E.ylo) * E.inv_cs[1];
-      int iy = yr < 0.0 ? 0 : (yr >= (double)E.nc[1] ? E.nc[1] - 1 : (int)yr);
-      ix = ix >= E.nc[0] ? E.nc[0] - 1 : ix;
-      iz = iz >= E.nc[2] ? E.nc[2] - 1 : iz;
-      const long long c = E.cell0 + ((long long)ix * E.nc[1] + iy) * E.nc[2] + iz;
-      const int slot = atomicAdd(&B.counts[(s & 1) * B.n_cells + c], 1);
-      if (slot < B.cap) {
-        Slot q;
-        q.x = xw - ((double)ix + 0.5) * E.cs[0];
-        q.y = y - (E.ylo + ((double)iy + 0.5) * E.cs[1]);
-        q.z = zw - ((double)iz + 0.5) * E.cs[2];
-        q.tag = (int)((a << 1) | (fluid ? 0 : 1));
-        static_cast<Slot*>(B.slots)[c * B.cap + slot] = q;
-      } else {
-        atomicMin(&B.status[e], -8);
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      int t = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, t, o);
+        if (lane >= o) t += y;
       }
+      warp_tot[lane] = t;  // inclusive prefix of warp totals
     }
-  }
-  if (mode & kFinish) {
-    seg_add<3>(mkey, mval, [&](int e, int i) {
-      return B.acc + (size_t)e * kAccStride + (i == 0 ? kAccQ + mblk : (i == 1 ? kAccP + mblk : kAccT));
-    });
-  }
-  if (mode & kBin) {
-    int* other = B.counts + ((s + 1) & 1) * B.n_cells;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long c = a; c < B.n_cells; c += stride) other[c] = 0;
+    __syncthreads();
+    const int before = carry + (wid > 0 ? warp_tot[wid - 1] : 0) + x - v;
+    if (c < ncell) {
+      B.cstart[E.cell0 + c] = (int)(E.atom0 + before);
+      B.csize[E.cell0 + c] = v;
+      B.ccount[E.cell0 + c] = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = before + v;
+    __syncthreads();
   }
 }
 
-// ---------------------------------------------------------------------------
-// LJ pair forces by a warp-cooperative cell sweep: one warp per target cell,
-// one lane per atom of the cell; the lanes walk the 27 neighbour cells'
-// slots together (every lane reads the same slot: a broadcast).  Eq. LJ with
-// cut-off r_c; energy shifted by U(r_c) per pair type.  Positions are
-// relative to cell centres, so the FP32 path forms x_i - x_j from small
-// numbers: t = (p_i - lo) - p_j, d = t - hi, where hi + lo is the cell shift.
-// Writes the LJ force, the x-virial share (fluid atoms only, half per pair)
-// and, with ENERGY, half the shifted pair energy per atom.
-// ---------------------------------------------------------------------------
-template <typename Slot, typename T, bool ENERGY>
-__global__ void __launch_bounds__(128) k_force_cells(BatchDev B, PhysDev P, int k) {
-  const long long s = *B.step_base + k;
+// Step 3: move every atom to its cell-ordered slot; positions become offsets
+// from the new reference cell's centre, anchors likewise (minimum image).
+template <typename PT>
+__global__ void __launch_bounds__(256) k_permute(BatchDev B) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= B.n_atoms) return;
+  const ElemDev& E = B.el[B.atom_el[i]];
+  const int c = B.newcell[i];
+  const long long dst = (long long)B.cstart[c] + B.slot[i];
+  double x, y, z;
+  abs_position(B, E, i, x, y, z);
+  double cx, cy, cz;
+  cell_center(E, c, cx, cy, cz);
+  const double ox = x - cx, oy = y - cy, oz = z - cz;
+  const int l = B.orig[i];
+  const bool wall = l >= E.nf;
+  double ax = 0.0, ay = 0.0, az = 0.0;
+  if (wall) {
+    ax = B.st[6][i]; ay = B.st[7][i]; az = B.st[8][i];
+    const int c0 = B.cell[i];
+    if (c0 >= 0) {
+      double px, py, pz;
+      cell_center(E, c0, px, py, pz);
+      ax += px; ay += py; az += pz;
+    }
+    ax = min_image(ax - cx, E.Lx);
+    ay = ay - cy;
+    az = min_image(az - cz, E.Lz);
+  }
+  B.st2[0][dst] = ox; B.st2[1][dst] = oy; B.st2[2][dst] = oz;
+  B.st2[3][dst] = B.st[3][i]; B.st2[4][dst] = B.st[4][i]; B.st2[5][dst] = B.st[5][i];
+  B.st2[6][dst] = ax; B.st2[7][dst] = ay; B.st2[8][dst] = az;
+  B.orig2[dst] = l;
+  B.cell2[dst] = c;
+  const float spf = wall ? 1.0f : 0.0f;
+  if constexpr (sizeof(PT) == 16) {
+    static_cast<float4*>(B.pos)[dst] = make_float4((float)ox, (float)oy, (float)oz, spf);
+  } else {
+    static_cast<Pos64*>(B.pos)[dst] = Pos64{ox, oy, oz, (double)spf};
+  }
+  B.pbuild[dst] = make_float4((float)ox, (float)oy, (float)oz, 0.0f);
+}
+
+__global__ void __launch_bounds__(256) k_copy_back(BatchDev B) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= B.n_atoms) return;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) B.st[k][i] = B.st2[k][i];
+  B.orig[i] = B.orig2[i];
+  B.cell[i] = B.cell2[i];
+}
+
+// Step 4: Verlet lists by a warp-cooperative sweep: one warp per cell, one
+// lane per atom of the cell; the lanes walk each neighbour cell's atoms
+// together (same address on every lane: a broadcast) and keep those within
+// r_c + skin.  The shift between the two reference cells is warp-uniform.
+template <typename PT>
+__global__ void __launch_bounds__(128) k_build(BatchDev B, PhysDev P) {
+  using T = decltype(PT::x);
   const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= B.n_cells) return;
   const int e = B.cell_el[warp];
   const ElemDev& E = B.el[e];
-  const long long lc = warp - E.cell0;
+  int cx, cy, cz;
+  cell_coords(E, warp, cx, cy, cz);
   const int ncx = E.nc[0], ncy = E.nc[1], ncz = E.nc[2];
-  const int cz = (int)(lc % ncz), cy = (int)((lc / ncz) % ncy), cx = (int)(lc / ((long long)ncz * ncy));
-  const int* counts = B.counts + (s & 1) * B.n_cells;
-  const Slot* slots = static_cast<const Slot*>(B.slots);
-  const int cap = B.cap;
-  const int nown = min(counts[warp], cap);
-  T rc2, eps[3], sig2[3];
-  if constexpr (sizeof(T) == 4) {
-    rc2 = P.rc2f;
-    for (int t = 0; t < 3; ++t) { eps[t] = P.epsf[t]; sig2[t] = P.sig2f[t]; }
-  } else {
-    rc2 = P.rc2;
-    for (int t = 0; t < 3; ++t) { eps[t] = P.eps[t]; sig2[t] = P.sig2[t]; }
-  }
-  for (int base = 0; base < nown; base += 32) {
-    const int i = base + lane;
-    const bool act = i < nown;
-    Slot me;
-    if (act) me = slots[warp * cap + i];
-    else { me.x = me.y = me.z = (T)0; me.tag = -1; }
-    const int spi = me.tag & 1;
-    T fx = 0, fy = 0, fz = 0, w = 0, u = 0;
+  const int s0 = B.cstart[warp], n0 = B.csize[warp];
+  const PT* pos = static_cast<const PT*>(B.pos);
+  const T rl2 = sizeof(T) == 4 ? (T)P.rl2f : (T)P.rl2;
+  const long long N = B.n_atoms;
+  for (int base = 0; base < n0; base += 32) {
+    const int i = s0 + base + lane;
+    const bool act = base + lane < n0;
+    PT me;
+    if (act) me = pos[i];
+    else { me.x = me.y = me.z = (T)1e9; me.w = (T)0; }
+    int cnt = 0;
     for (int dx = -1; dx <= 1; ++dx) {
       int jx = cx + dx;
       jx = jx < 0 ? jx + ncx : (jx >= ncx ? jx - ncx : jx);
@@ -338,46 +375,225 @@ __global__ void __launch_bounds__(128) k_force_cells(BatchDev B, PhysDev P, int 
           int jz = cz + dz;
           jz = jz < 0 ? jz + ncz : (jz >= ncz ? jz - ncz : jz);
           const long long c2 = E.cell0 + ((long long)jx * ncy + jy) * ncz + jz;
-          // x_i - x_j = p_i - p_j - delta * cs, cs split into hi + lo
-          T hx, hy, hz, qx, qy, qz;
-          if constexpr (sizeof(T) == 4) {
-            const float hix = (float)E.cs[0], hiy = (float)E.cs[1], hiz = (float)E.cs[2];
-            const float lox = (float)(E.cs[0] - (double)hix), loy = (float)(E.cs[1] - (double)hiy),
-                        loz = (float)(E.cs[2] - (double)hiz);
-            hx = dx * hix; hy = dy * hiy; hz = dz * hiz;
-            qx = me.x - dx * lox; qy = me.y - dy * loy; qz = me.z - dz * loz;
-          } else {
-            hx = dx * E.cs[0]; hy = dy * E.cs[1]; hz = dz * E.cs[2];
-            qx = me.x; qy = me.y; qz = me.z;
-          }
-          const int n2 = min(counts[c2], cap);
-          const Slot* sl = slots + c2 * cap;
-          for (int j = 0; j < n2; ++j) {
-            const Slot o = sl[j];
-            const T ddx = (qx - o.x) - hx, ddy = (qy - o.y) - hy, ddz = (qz - o.z) - hz;
+          const T hx = (T)dx * (T)E.cs[0], hy = (T)dy * (T)E.cs[1], hz = (T)dz * (T)E.cs[2];
+          const T qx = me.x - hx, qy = me.y - hy, qz = me.z - hz;
+          const int j0 = B.cstart[c2], nj = B.csize[c2];
+          const unsigned code = ((unsigned)(dx + 1) << 26) | ((unsigned)(dy + 1) << 28) | ((unsigned)(dz + 1) << 30);
+          for (int j = j0; j < j0 + nj; ++j) {
+            const PT o = pos[j];
+            const T ddx = qx - o.x, ddy = qy - o.y, ddz = qz - o.z;
             const T r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-            const int t = spi + (o.tag & 1);
-            if (act && r2 < rc2 && o.tag != me.tag && P.active[t]) {
-              T inv2;
-              if constexpr (sizeof(T) == 4) inv2 = __frcp_rn(r2); else inv2 = 1.0 / r2;
-              const T s2 = sig2[t] * inv2;
-              const T s6 = s2 * s2 * s2;
-              const T fs = (T)24 * eps[t] * inv2 * s6 * ((T)2 * s6 - (T)1);
-              fx += fs * ddx; fy += fs * ddy; fz += fs * ddz;
-              if (spi == 0) w += (T)0.5 * fs * ddx * ddx;
-              if (ENERGY) u += (T)0.5 * ((T)4 * eps[t] * (s6 * s6 - s6) - (T)P.eshift[t]);
+            if (act && r2 < rl2 && j != i) {
+              if (cnt < B.list_cap) B.list[(long long)cnt * N + i] = (unsigned)(j - E.atom0) | code;
+              ++cnt;
             }
           }
         }
       }
     }
     if (act) {
-      const long long atom = me.tag >> 1;
-      static_cast<T*>(B.fx)[atom] = fx;
-      static_cast<T*>(B.fy)[atom] = fy;
-      static_cast<T*>(B.fz)[atom] = fz;
-      static_cast<T*>(B.wxx)[atom] = w;
-      if (ENERGY) static_cast<T*>(B.epot)[atom] = u;
+      B.nlist[i] = cnt < B.list_cap ? cnt : B.list_cap;
+      if (cnt > B.list_cap) atomicMin(&B.status[e], kStOverflow);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// LJ pair forces over the Verlet lists: one thread per atom (cell order, so
+// a warp's neighbours are shared in L1).  Eq. LJ truncated at r_c, energy
+// shifted by U(r_c) per pair type.  The displacement is formed from
+// cell-centre offsets: d = (p_i - p_j) - delta * cs, delta in {-1, 0, 1}^3
+// from the entry's shift bits, so FP32 only ever rounds numbers below ~3.
+// Writes the LJ force, the x-virial share of fluid atoms (half per pair) and,
+// with ENERGY, half the shifted pair energy per atom.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float shift_unit(unsigned bits2) {
+  // bits2 in {0, 1, 2} -> {-1, 0, 1}, exactly, without an int-to-float convert
+  return __int_as_float(0x4B400000 | (int)bits2) - 12582913.0f;
+}
+
+template <typename PT, typename T, bool UNIFORM, bool ENERGY>
+struct PairAcc {
+  T fx = 0, fy = 0, fz = 0, w = 0, u = 0;
+  __device__ __forceinline__ void add(const PT& me, const PT& o, unsigned ent, T csx, T csy, T csz, int spi,
+                                      T rc2, const T (&eps)[3], const T (&sig2)[3], const PhysDev& P) {
+    const float sx = shift_unit((ent >> 26) & 3u), sy = shift_unit((ent >> 28) & 3u), sz = shift_unit(ent >> 30);
+    T ddx, ddy, ddz;
+    if constexpr (sizeof(T) == 4) {
+      ddx = fmaf(-sx, csx, me.x - o.x);
+      ddy = fmaf(-sy, csy, me.y - o.y);
+      ddz = fmaf(-sz, csz, me.z - o.z);
+    } else {
+      ddx = (me.x - o.x) - (double)sx * csx;
+      ddy = (me.y - o.y) - (double)sy * csy;
+      ddz = (me.z - o.z) - (double)sz * csz;
+    }
+    const T r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+    T inv2;
+    if constexpr (sizeof(T) == 4) inv2 = __frcp_rn(r2); else inv2 = 1.0 / r2;
+    T e_, s2;
+    int t = 0;
+    if constexpr (UNIFORM) {
+      e_ = (T)1; s2 = inv2;
+    } else {
+      t = spi + (o.w != (T)0 ? 1 : 0);
+      e_ = eps[t];
+      s2 = sig2[t] * inv2;
+    }
+    const T s6 = s2 * s2 * s2;
+    T fs = (T)24 * e_ * inv2 * s6 * ((T)2 * s6 - (T)1);
+    bool in = r2 < rc2;
+    if constexpr (!UNIFORM) in = in && P.active[t];
+    fs = in ? fs : (T)0;
+    fx += fs * ddx; fy += fs * ddy; fz += fs * ddz;
+    w += fs * ddx * ddx;
+    if (ENERGY) u += in ? ((T)4 * e_ * (s6 * s6 - s6) - (T)P.eshift[t]) : (T)0;
+  }
+};
+
+template <typename PT, typename T, bool UNIFORM, bool ENERGY>
+__global__ void __launch_bounds__(128) k_force(BatchDev B, PhysDev P) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= B.n_atoms) return;
+  const ElemDev& E = B.el[B.atom_el[i]];
+  const PT* pos = static_cast<const PT*>(B.pos);
+  const PT me = pos[i];
+  const T csx = (T)E.cs[0], csy = (T)E.cs[1], csz = (T)E.cs[2];
+  const PT* posj = pos + E.atom0;
+  const int n = B.nlist[i];
+  const long long N = B.n_atoms;
+  T rc2, eps[3], sig2[3];
+  if constexpr (sizeof(T) == 4) {
+    rc2 = P.rc2f;
+    for (int t = 0; t < 3; ++t) { eps[t] = P.epsf[t]; sig2[t] = P.sig2f[t]; }
+  } else {
+    rc2 = P.rc2;
+    for (int t = 0; t < 3; ++t) { eps[t] = P.eps[t]; sig2[t] = P.sig2[t]; }
+  }
+  const int spi = me.w != (T)0 ? 1 : 0;
+  // padding entry: the atom itself seen one cell over in x, always beyond r_c
+  const unsigned pad = (unsigned)(i - E.atom0) | (2u << 26) | (1u << 28) | (1u << 30);
+  PairAcc<PT, T, UNIFORM, ENERGY> acc;
+  const unsigned* lst = B.list + i;
+  for (int k = 0; k < n; k += 4) {
+    const unsigned e0 = __ldg(lst + (long long)k * N);
+    const unsigned e1 = k + 1 < n ? __ldg(lst + (long long)(k + 1) * N) : pad;
+    const unsigned e2 = k + 2 < n ? __ldg(lst + (long long)(k + 2) * N) : pad;
+    const unsigned e3 = k + 3 < n ? __ldg(lst + (long long)(k + 3) * N) : pad;
+    const PT o0 = posj[e0 & kJMask], o1 = posj[e1 & kJMask], o2 = posj[e2 & kJMask], o3 = posj[e3 & kJMask];
+    acc.add(me, o0, e0, csx, csy, csz, spi, rc2, eps, sig2, P);
+    acc.add(me, o1, e1, csx, csy, csz, spi, rc2, eps, sig2, P);
+    acc.add(me, o2, e2, csx, csy, csz, spi, rc2, eps, sig2, P);
+    acc.add(me, o3, e3, csx, csy, csz, spi, rc2, eps, sig2, P);
+  }
+  static_cast<T*>(B.fx)[i] = acc.fx;
+  static_cast<T*>(B.fy)[i] = acc.fy;
+  static_cast<T*>(B.fz)[i] = acc.fz;
+  static_cast<T*>(B.wxx)[i] = spi == 0 ? (T)0.5 * acc.w : (T)0;
+  if (ENERGY) static_cast<T*>(B.epot)[i] = (T)0.5 * acc.u;
+}
+
+// ---------------------------------------------------------------------------
+// Fused integration kernel, one thread per atom.  With s the step started:
+//   kFinish  completes step s-1: v = u + dt/(2m) F(x), samples it;
+//   kStage1  first stage of step s: fluid velocity-Verlet half kick + drift,
+//            tethered wall atoms G-JF (Gronbech-Jensen & Farago 2013);
+// then publishes the pair-force input position and checks the list skin.
+// F(x) = LJ (force kernel) + body force g on fluid atoms (Eq. momentumEq) +
+// tether -k (r - r0) on wall atoms.
+// ---------------------------------------------------------------------------
+template <typename FT, typename PT>
+__global__ void __launch_bounds__(256) k_integrate(BatchDev B, PhysDev P, int k, int mode,
+                                                   cudaGraphConditionalHandle hcond, int use_cond) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long s = *B.step_base + k;
+  int mkey = -1;
+  int mblk = 0;
+  double mval[3] = {0.0, 0.0, 0.0};
+  if (i < B.n_atoms) {
+    const int e = B.atom_el[i];
+    const ElemDev& E = B.el[e];
+    const int l = B.orig[i];
+    const bool fluid = l < E.nf;
+    double x = B.st[0][i], y = B.st[1][i], z = B.st[2][i];
+    double vx = B.st[3][i], vy = B.st[4][i], vz = B.st[5][i];
+    double fx = (double)static_cast<const FT*>(B.fx)[i];
+    double fy = (double)static_cast<const FT*>(B.fy)[i];
+    double fz = (double)static_cast<const FT*>(B.fz)[i];
+    if (fluid) {
+      fx += E.g;
+    } else {
+      fx -= P.k_tether * (x - B.st[6][i]);
+      fy -= P.k_tether * (y - B.st[7][i]);
+      fz -= P.k_tether * (z - B.st[8][i]);
+    }
+    if ((mode & kFinish) && s >= 1 && s - 1 < E.steps_total) {
+      vx += P.hdt_m * fx; vy += P.hdt_m * fy; vz += P.hdt_m * fz;
+      const long long ks = s - 1 - E.steps_eq;
+      const double v2 = vx * vx + vy * vy + vz * vz;
+      if (!(v2 < 1e30) || !(fabs(y) < 1e6)) atomicMin(&B.status[e], kStUnstable);
+      if (fluid && ks >= 0 && ks < E.steps_sample && E.nb > 0) {
+        mkey = e;
+        mblk = (int)((ks * E.nb) / E.steps_sample);
+        mval[0] = P.mass * vx;
+        mval[1] = P.mass * vx * vx + (double)static_cast<const FT*>(B.wxx)[i];
+        mval[2] = P.mass * v2;
+      }
+    }
+    if ((mode & kStage1) && s < E.steps_total) {
+      if (fluid) {
+        vx += P.hdt_m * fx; vy += P.hdt_m * fy; vz += P.hdt_m * fz;
+        x += P.dt * vx; y += P.dt * vy; z += P.dt * vz;
+      } else {
+        double b0 = 0.0, b1 = 0.0, b2 = 0.0;
+        if (E.beta_sd > 0.0) {
+          normals3<FT>((uint32_t)l, (uint32_t)s, (uint32_t)E.id, 1u, E.seed, b0, b1, b2);
+          b0 *= E.beta_sd; b1 *= E.beta_sd; b2 *= E.beta_sd;
+        }
+        const double bdt = P.gjf_b * P.dt, h2m = P.dt / (2.0 * P.mass), i2m = 1.0 / (2.0 * P.mass);
+        x += bdt * (vx + h2m * fx + b0 * i2m);
+        y += bdt * (vy + h2m * fy + b1 * i2m);
+        z += bdt * (vz + h2m * fz + b2 * i2m);
+        const double bm = P.gjf_b * P.inv_m;
+        vx = P.gjf_a * vx + h2m * P.gjf_a * fx + bm * b0;
+        vy = P.gjf_a * vy + h2m * P.gjf_a * fy + bm * b1;
+        vz = P.gjf_a * vz + h2m * P.gjf_a * fz + bm * b2;
+      }
+      B.st[0][i] = x; B.st[1][i] = y; B.st[2][i] = z;
+      const float xf = (float)x, yf = (float)y, zf = (float)z;
+      if constexpr (sizeof(PT) == 16) {
+        static_cast<float4*>(B.pos)[i] = make_float4(xf, yf, zf, fluid ? 0.0f : 1.0f);
+      } else {
+        static_cast<Pos64*>(B.pos)[i] = Pos64{x, y, z, fluid ? 0.0 : 1.0};
+      }
+      // an atom that moved more than half the skin since the lists were
+      // built asks for a rebuild before the next force evaluation
+      const float4 pb = B.pbuild[i];
+      const float ex = xf - pb.x, ey = yf - pb.y, ez = zf - pb.z;
+      if (ex * ex + ey * ey + ez * ez > P.half_skin2f) {
+        if (use_cond) atomicOr(&B.flags[0], 1);
+        else atomicMin(&B.status[e], kStSkin);
+      }
+    }
+    B.st[3][i] = vx; B.st[4][i] = vy; B.st[5][i] = vz;
+  }
+  if (mode & kFinish) {
+    seg_add<3>(mkey, mval, [&](int e, int q) {
+      return B.acc + (size_t)e * kAccStride + (q == 0 ? kAccQ + mblk : (q == 1 ? kAccP + mblk : kAccT));
+    });
+  }
+  if (use_cond) {
+    // the last block to finish turns the flag into the graph condition (one
+    // caller of cudaGraphSetConditional) and clears the flag words
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      const int prev = atomicAdd(&B.flags[1], 1);
+      if (prev == (int)gridDim.x - 1) {
+        const int need = atomicExch(&B.flags[0], 0);
+        atomicExch(&B.flags[1], 0);
+        if (need) cudaGraphSetConditional(hcond, 1u);
+      }
     }
   }
 }
@@ -385,24 +601,46 @@ __global__ void __launch_bounds__(128) k_force_cells(BatchDev B, PhysDev P, int 
 // Total energy per element (kinetic + shifted LJ + tether) into acc[which].
 template <typename FT>
 __global__ void k_energy(BatchDev B, PhysDev P, int which) {
-  const long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   int key = -1;
   double val[1] = {0.0};
-  if (a < B.n_atoms) {
-    const int e = B.atom_el[a];
+  if (i < B.n_atoms) {
+    const int e = B.atom_el[i];
     const ElemDev& E = B.el[e];
-    const bool fluid = (a - E.atom0) < E.nf;
-    const double vx = B.vx[a], vy = B.vy[a], vz = B.vz[a];
-    double en = 0.5 * P.mass * (vx * vx + vy * vy + vz * vz) + (double)static_cast<const FT*>(B.epot)[a];
-    if (!fluid) {
-      const double dx = min_image(B.x[a] - B.ax[a], E.Lx), dy = B.y[a] - B.ay[a],
-                   dz = min_image(B.z[a] - B.az[a], E.Lz);
+    const double vx = B.st[3][i], vy = B.st[4][i], vz = B.st[5][i];
+    double en = 0.5 * P.mass * (vx * vx + vy * vy + vz * vz) + (double)static_cast<const FT*>(B.epot)[i];
+    if (B.orig[i] >= E.nf) {
+      const double dx = B.st[0][i] - B.st[6][i], dy = B.st[1][i] - B.st[7][i], dz = B.st[2][i] - B.st[8][i];
       en += 0.5 * P.k_tether * (dx * dx + dy * dy + dz * dz);
     }
     key = e;
     val[0] = en;
   }
   seg_add<1>(key, val, [&](int e, int) { return B.acc + (size_t)e * kAccStride + which; });
+}
+
+// Copy state (what = 0: wrapped positions and velocities; what = 1: forces,
+// virial shares and energies) into B.out in the original atom order.
+template <typename FT>
+__global__ void k_export(BatchDev B, int what) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= B.n_atoms) return;
+  const ElemDev& E = B.el[B.atom_el[i]];
+  const long long dst = E.atom0 + B.orig[i];
+  const long long N = B.n_atoms;
+  if (what == 0) {
+    double x, y, z;
+    abs_position(B, E, i, x, y, z);
+    B.out[dst] = x; B.out[N + dst] = y; B.out[2 * N + dst] = z;
+    B.out[3 * N + dst] = B.st[3][i]; B.out[4 * N + dst] = B.st[4][i]; B.out[5 * N + dst] = B.st[5][i];
+  } else {
+    B.out[dst] = (double)static_cast<const FT*>(B.fx)[i];
+    B.out[N + dst] = (double)static_cast<const FT*>(B.fy)[i];
+    B.out[2 * N + dst] = (double)static_cast<const FT*>(B.fz)[i];
+    B.out[3 * N + dst] = (double)static_cast<const FT*>(B.wxx)[i];
+    B.out[4 * N + dst] = (double)static_cast<const FT*>(B.epot)[i];
+    B.out[5 * N + dst] = 0.0;
+  }
 }
 
 __global__ void k_advance(long long* step, long long by) {

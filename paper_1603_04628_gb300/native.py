@@ -11,7 +11,8 @@ LIB_PATH = os.path.join(_PKG, "libmdgp.so")
 
 MDGP_OK = 0
 STATUS = {0: "MDGP_OK", -1: "MDGP_E_ARG", -2: "MDGP_E_NOMEM", -3: "MDGP_E_CUDA", -4: "MDGP_E_UNSTABLE",
-          -5: "MDGP_E_NOTPD", -6: "MDGP_E_TIMEOUT", -7: "MDGP_E_STATE", -8: "MDGP_E_OVERFLOW"}
+          -5: "MDGP_E_NOTPD", -6: "MDGP_E_TIMEOUT", -7: "MDGP_E_STATE", -8: "MDGP_E_OVERFLOW",
+          -9: "MDGP_E_SKIN"}
 PREC_FP64 = 0
 PREC_FP32 = 1
 
@@ -36,7 +37,13 @@ class MDParams(ctypes.Structure):
                 ("eps_wf", ctypes.c_double), ("sig_wf", ctypes.c_double), ("eps_ww", ctypes.c_double),
                 ("sig_ww", ctypes.c_double), ("fluid_margin", ctypes.c_double), ("tau_T", ctypes.c_double),
                 ("mass", ctypes.c_double), ("n_blocks", ctypes.c_int32), ("mode", ctypes.c_int32),
-                ("wall_planes", ctypes.c_int32), ("cell_capacity", ctypes.c_int32)]
+                ("wall_planes", ctypes.c_int32), ("list_capacity", ctypes.c_int32),
+                ("skin", ctypes.c_double), ("rebuild_every", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class GPParams(ctypes.Structure):
+    _fields_ = [("sf2", ctypes.c_double), ("l2", ctypes.c_double), ("sn2", ctypes.c_double),
+                ("fallback_scale", ctypes.c_double), ("fixed_scales", ctypes.POINTER(ctypes.c_double))]
 
 
 class MdgpError(RuntimeError):
@@ -66,10 +73,16 @@ def lib():
         "mdgp_micro_launch": ([vp], ctypes.c_int),
         "mdgp_micro_results": ([vp, ctypes.POINTER(Result), i64], ctypes.c_int),
         "mdgp_micro_launch_count": ([vp], i64),
+        "mdgp_micro_rebuild_count": ([vp], i64),
         "mdgp_micro_state": ([vp, dp, dp, i64], ctypes.c_int),
         "mdgp_md_forces": ([vp, ctypes.POINTER(Element), dp, i64, dp, dp, dp], ctypes.c_int),
         "mdgp_micro_profile": ([vp, i64, dp], ctypes.c_int),
         "mdgp_last_error": ([vp], ctypes.c_char_p),
+        "mdgp_gp_fit": ([vp, dp, dp, i64, ctypes.c_int32, ctypes.POINTER(GPParams), dp, ctypes.POINTER(vp)],
+                        ctypes.c_int),
+        "mdgp_gp_predict": ([vp, dp, i64, dp, dp, dp], ctypes.c_int),
+        "mdgp_gp_scales": ([vp, dp], ctypes.c_int),
+        "mdgp_gp_free": ([vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -142,7 +155,10 @@ class Context:
 
     def set_md_params(self, **kw):
         p = md_params_default()
+        names = {f for f, _ in MDParams._fields_}
         for k, v in kw.items():
+            if k not in names:
+                raise MdgpError("unknown MD parameter %r" % k)
             setattr(p, k, v)
         _check(self.h, lib().mdgp_set_md_params(self.h, ctypes.byref(p)), "mdgp_set_md_params")
 
@@ -175,6 +191,9 @@ class Context:
     def launch_count(self):
         return int(lib().mdgp_micro_launch_count(self.h))
 
+    def rebuild_count(self):
+        return int(lib().mdgp_micro_rebuild_count(self.h))
+
     def micro_state(self):
         x = np.zeros((self.n_atoms, 3))
         v = np.zeros((self.n_atoms, 3))
@@ -183,9 +202,10 @@ class Context:
 
     def micro_profile(self, steps=100):
         """Mean per-launch milliseconds of the integration and pair-force kernels."""
-        ms = np.zeros(4)
+        ms = np.zeros(6)
         _check(self.h, lib().mdgp_micro_profile(self.h, int(steps), _dp(ms)), "mdgp_micro_profile")
-        return dict(integrate_ms=float(ms[0]), force_ms=float(ms[1]), atoms=int(ms[2]), cells=int(ms[3]))
+        return dict(integrate_ms=float(ms[0]), force_ms=float(ms[1]), rebuild_ms=float(ms[2]),
+                    atoms=int(ms[3]), cells=int(ms[4]), rebuild_every=int(ms[5]))
 
     def md_forces(self, el, x):
         x = np.ascontiguousarray(x, dtype=np.float64)
@@ -197,6 +217,50 @@ class Context:
         return f, w, e
 
 
+class GP:
+    """A fitted Gaussian process (mdgp_gp) living on ctx's device."""
+
+    def __init__(self, ctx, X, y, sf2, l2, sn2, mu_X=None, fallback_scale=1.0, fixed_scales=None):
+        X = np.ascontiguousarray(np.asarray(X, dtype=np.float64).reshape(len(y), -1) if len(y) else
+                                 np.zeros((0, np.asarray(X).shape[-1] if np.ndim(X) == 2 else 1)))
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        self.D = X.shape[1]
+        p = GPParams(float(sf2), float(l2), float(sn2), float(fallback_scale), None)
+        self._fixed = None
+        if fixed_scales is not None:
+            self._fixed = np.ascontiguousarray(fixed_scales, dtype=np.float64)
+            p.fixed_scales = _dp(self._fixed)
+        mu = None if mu_X is None else _dp(np.ascontiguousarray(mu_X, dtype=np.float64))
+        self.h = ctypes.c_void_p()
+        self.ctx = ctx
+        _check(ctx.h, lib().mdgp_gp_fit(ctx.h, _dp(X), _dp(y), len(y), self.D, ctypes.byref(p), mu,
+                                        ctypes.byref(self.h)), "mdgp_gp_fit")
+
+    def predict(self, Xs, mu_Xs=None):
+        Xs = np.ascontiguousarray(np.asarray(Xs, dtype=np.float64).reshape(-1, self.D))
+        m = len(Xs)
+        mean = np.zeros(m); var = np.zeros(m)
+        mu = None if mu_Xs is None else _dp(np.ascontiguousarray(mu_Xs, dtype=np.float64))
+        _check(None, lib().mdgp_gp_predict(self.h, _dp(Xs), m, mu, _dp(mean), _dp(var)), "mdgp_gp_predict")
+        return mean, var
+
+    def scales(self):
+        out = np.zeros(self.D)
+        _check(None, lib().mdgp_gp_scales(self.h, _dp(out)), "mdgp_gp_scales")
+        return out
+
+    def close(self):
+        if self.h:
+            lib().mdgp_gp_free(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 # Same names as the C ABI.
 def mdgp_create(device=0, precision=PREC_FP64):
     return Context(device, precision)
@@ -204,3 +268,11 @@ def mdgp_create(device=0, precision=PREC_FP64):
 
 def mdgp_micro_batch(ctx, elements):
     return ctx.micro_batch(elements)
+
+
+def mdgp_gp_fit(ctx, X, y, sf2, l2, sn2, mu_X=None, **kw):
+    return GP(ctx, X, y, sf2, l2, sn2, mu_X=mu_X, **kw)
+
+
+def mdgp_gp_predict(gp, Xs, mu_Xs=None):
+    return gp.predict(Xs, mu_Xs)

@@ -53,7 +53,7 @@ def batch_stress(n=4096, seed=BASE_SEED + 5, steps=10000, eq_fraction=0.2):
         h = rng.uniform(5.0, 40.0)
         dens = rng.uniform(0.7, 0.9)
         nf = np.exp(rng.uniform(np.log(2000.0), np.log(32000.0)))
-        lat = max(7.5, float(np.sqrt(nf / (dens * h))))
+        lat = max(9.0, float(np.sqrt(nf / (dens * h))))
         g = rng.uniform(0.005, 0.05)
         out.append(dict(h=float(h), Lx=lat, Lz=lat, density=float(dens), T=1.1, g_ext=float(g),
                         dpdx=0.0, steps_eq=steps_eq, steps_sample=int(steps) - steps_eq,

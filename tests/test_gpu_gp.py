@@ -1,0 +1,87 @@
+"""GPU Gaussian process (FP64) against the oracle, through the C ABI.
+
+Tolerance: posterior mean within 1e-10 relative to max(|mean|, max|y|) and
+variance within 1e-10 relative to sf2 (the variance can cancel towards 0)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import gp as ogp
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1603_04628_gb300 import build, native
+    build.build()
+    c = native.Context(0, native.PREC_FP64)
+    yield c
+    c.close()
+
+
+def _cmp(gpu, ref, y, sf2):
+    mg, vg = gpu
+    mr, vr = ref
+    scale = max(np.abs(y).max() if len(y) else 1.0, 1.0)
+    assert np.abs(mg - mr).max() <= TOL * scale, np.abs(mg - mr).max()
+    assert np.abs(vg - vr).max() <= TOL * sf2, np.abs(vg - vr).max()
+
+
+@pytest.mark.parametrize("M,D", [(1, 2), (3, 2), (31, 2), (32, 3), (33, 2), (200, 2), (517, 3)])
+def test_posterior_matches_oracle(ctx, M, D):
+    from paper_1603_04628_gb300 import native
+    X, y = synth.gp_dataset(M, seed=M, D=D)
+    Xs = synth.gp_queries(97, seed=M + 1, D=D)
+    sf2, l2, sn2 = 1.3, 1.0, 0.0025
+    ref = ogp.GP(X, y, sf2, l2, sn2)
+    g = native.GP(ctx, X, y, sf2, l2, sn2)
+    np.testing.assert_allclose(g.scales(), ref.dbar, rtol=1e-12)
+    _cmp(g.predict(Xs), ref.predict(Xs), y, sf2)
+    # at the training inputs too
+    _cmp(g.predict(X), ref.predict(X), y, sf2)
+    g.close()
+
+
+def test_prior_mean_and_fixed_scales(ctx):
+    from paper_1603_04628_gb300 import native
+    X, y = synth.gp_dataset(150, seed=4)
+    Xs = synth.gp_queries(40, seed=5)
+    mu = lambda Z: 0.5 * Z[:, 0] - 3.0 * Z[:, 1]
+    scales = np.array([2.0, 0.03])
+    ref = ogp.GP(X, y, 0.7, 1.5, 0.01, mu=mu, dbar=scales)
+    g = native.GP(ctx, X, y, 0.7, 1.5, 0.01, mu_X=mu(X), fixed_scales=scales)
+    _cmp(g.predict(Xs, mu_Xs=mu(Xs)), ref.predict(Xs), y, 0.7)
+    g.close()
+
+
+def test_empty_database_and_no_queries(ctx):
+    from paper_1603_04628_gb300 import native
+    g = native.GP(ctx, np.zeros((0, 2)), np.zeros(0), 2.0, 1.0, 0.1)
+    mean, var = g.predict(np.array([[1.0, 2.0], [3.0, 4.0]]), mu_Xs=np.array([0.5, -1.0]))
+    np.testing.assert_array_equal(mean, [0.5, -1.0])
+    np.testing.assert_array_equal(var, [2.0, 2.0])
+    assert g.predict(np.zeros((0, 2)))[0].shape == (0,)
+    g.close()
+
+
+def test_not_positive_definite_is_reported(ctx):
+    from paper_1603_04628_gb300 import native
+    X = np.array([[1.0, 2.0], [1.0, 2.0]])     # duplicate inputs, no noise: singular C
+    with pytest.raises(native.MdgpError):
+        native.GP(ctx, X, np.array([1.0, 1.0]), 1.0, 1.0, 0.0)
+
+
+def test_large_database(ctx):
+    from paper_1603_04628_gb300 import native
+    X, y = synth.gp_dataset(2000, seed=9)
+    Xs = synth.gp_queries(200, seed=10)
+    ref = ogp.GP(X, y, 1.0, 1.0, 0.0025)
+    g = native.GP(ctx, X, y, 1.0, 1.0, 0.0025)
+    mg, vg = g.predict(Xs)
+    mr, vr = ref.predict(Xs)
+    # conditioning of C grows with M; same bound scaled by the mean's size
+    assert np.abs(mg - mr).max() <= 1e-9 * max(np.abs(y).max(), 1.0)
+    assert np.abs(vg - vr).max() <= 1e-10
+    g.close()

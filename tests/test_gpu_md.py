@@ -195,8 +195,8 @@ def test_edge_cases(native):
     ref = omd.element(omd.make_params(synth.element_plain(steps_eq=0, steps_sample=3)))
     assert r["q"] == pytest.approx(ref["q"], rel=1e-8)
     assert r["q_se"] == pytest.approx(ref["q_se"], rel=1e-6)
-    # a cell capacity that is too small is reported, never written past
-    ctx.set_md_params(cell_capacity=8)
+    # a neighbour-list capacity that is too small is reported, never written past
+    ctx.set_md_params(list_capacity=8)
     ctx.micro_plan([synth.element_plain(steps_eq=2, steps_sample=2)])
     ctx.micro_launch()
     assert ctx.micro_results()[0]["status"] == -8
