@@ -1,0 +1,164 @@
+"""Algorithm 1 (hybrid scheme with on-the-fly GP learning), plain Python.
+
+TEST INFRASTRUCTURE ONLY: tests/, the smoke check and bench.py's CPU-baseline
+leg may import this module; the product package never does.
+
+Macro model (paper Sec. 2.1, Eqs. subsEq, continuityEq, momentumEq; readings
+for the parts the paper leaves open are marked READING):
+  - N periodic sections at x_j = j dx (Eq. subsEq with L = N dx); heights
+    h_j = h0 (1 - 0.5 cos(2 pi x_j / L)) (the converging-diverging channel in
+    the benchmark's form; the paper's Eq. heightEq has the same shape);
+  - state: fluid number density n_j (mass density m n_j, m = 1);
+  - READING: pressure from a linear equation of state p = K (n - n0) (the
+    paper uses a second GP on pre-simulations for p; a linear law keeps the
+    same role of a density-dependent pressure);
+  - pressure gradient by periodic central differences (Alg. 1, the p' line);
+  - READING: the sinusoidal inlet-outlet pressure difference
+    dP(t) = dP_A sin(2 pi t / period) of the periodic channel acts as a
+    uniform gradient -dP / L; the GP input is x = (h_j, G_j) with
+    G_j = dp/dx_j - dP / L, and an MD element gets dpdx = G_j, so every fluid
+    atom feels F = -G_j / n_j (Eq. momentumEq with F_ext folded into G);
+  - q-GP (Eqs. quadraticKernelEq-predVarEq) on the database of (x, q) pairs,
+    refit whenever the database grows; gate sd > sigma_t (strict);
+  - READING: sigma_n is fixed during a macro step.  The paper measured it
+    once beforehand (Sec. 2.3) and kept it; here it is the configured value,
+    or optionally (sn2_from_data) the mean standard error of the database's
+    MD runs as they stood at the start of the step.  Holding it fixed within
+    a step keeps the gate a function of the inputs alone;
+  - continuity, Eq. continuityEq discretised with central differences:
+    n_j <- n_j - dt / A_j (q_{j+1} - q_{j-1}) / (2 dx), A_j = h_j L_z.
+"""
+import math
+
+import numpy as np
+
+from . import gp as ogp
+
+
+class Channel:
+    def __init__(self, n_sections=8, dx=50.0, h0=12.0, Lx=10.0, Lz=10.0, K=10.0, n0=0.8, dP_amp=0.0,
+                 period=1000.0, dt=20.0, T=1.1, steps_eq=100, steps_sample=100, seed=7, sf2=1.0, l2=1.0,
+                 sn2_default=0.0025, sn2_from_data=False, density0=None):
+        self.N = int(n_sections)
+        self.dx, self.h0, self.Lx, self.Lz = float(dx), float(h0), float(Lx), float(Lz)
+        self.K, self.n0, self.dP_amp, self.period, self.dt = float(K), float(n0), float(dP_amp), float(period), float(dt)
+        self.T, self.steps_eq, self.steps_sample, self.seed = float(T), int(steps_eq), int(steps_sample), int(seed)
+        self.sf2, self.l2, self.sn2_default, self.sn2_from_data = float(sf2), float(l2), float(sn2_default), bool(sn2_from_data)
+        L = self.N * self.dx
+        x = np.arange(self.N) * self.dx
+        self.h = self.h0 * (1.0 - 0.5 * np.cos(2.0 * math.pi * x / L))
+        self.n = np.full(self.N, self.n0) if density0 is None else np.array(density0, dtype=np.float64)
+        self.i = 0                       # macro steps taken
+        self.X = np.zeros((0, 2))
+        self.y = np.zeros(0)
+        self.se = np.zeros(0)
+        self.md_calls = 0
+
+    # ------------------------------------------------------------------ helpers
+    def sn2(self):
+        """Noise variance for the coming step."""
+        if self.sn2_from_data and len(self.se) > 0:
+            return float(np.mean(self.se)) ** 2
+        return self.sn2_default
+
+    def gradients(self, t):
+        p = self.K * (self.n - self.n0)
+        dpdx = (np.roll(p, -1) - np.roll(p, 1)) / (2.0 * self.dx)
+        dP = self.dP_amp * math.sin(2.0 * math.pi * t / self.period)
+        return dpdx - dP / (self.N * self.dx)
+
+    def element(self, j, G, call_id):
+        return dict(h=float(self.h[j]), dpdx=float(G), density=float(self.n[j]), T=self.T,
+                    steps_eq=self.steps_eq, steps_sample=self.steps_sample, Lx=self.Lx, Lz=self.Lz,
+                    g_ext=0.0, seed=self.seed, id=int(call_id))
+
+    def continuity(self, q):
+        A = self.h * self.Lz
+        self.n = self.n - self.dt / A * (np.roll(q, -1) - np.roll(q, 1)) / (2.0 * self.dx)
+
+    # ------------------------------------------------------------------ Alg. 1
+    def step_sequential(self, sigma_t, md_fn):
+        """One macro step exactly as Algorithm 1 orders it: for each section,
+        a GP prediction on the current database; an MD run (appended at once,
+        covariance refit) whenever the predicted sd exceeds sigma_t."""
+        self.i += 1
+        t = self.i * self.dt
+        G = self.gradients(t)
+        sn2 = self.sn2()
+        q = np.zeros(self.N); sd = np.zeros(self.N); from_md = np.zeros(self.N, bool)
+        for j in range(self.N):
+            x = np.array([[self.h[j], G[j]]])
+            g = ogp.GP(self.X, self.y, self.sf2, self.l2, sn2)
+            m, v = g.predict(x)
+            sd[j] = math.sqrt(v[0])
+            if ogp.gate(sd[j], sigma_t):
+                r = md_fn(self.element(j, G[j], self.md_calls))
+                self.md_calls += 1
+                self.X = np.vstack([self.X, x])
+                self.y = np.append(self.y, r["q"])
+                self.se = np.append(self.se, r["q_se"])
+                q[j] = r["q"]
+                from_md[j] = True
+            else:
+                q[j] = m[0]
+        self.continuity(q)
+        return dict(q=q, sd=sd, from_md=from_md, G=G)
+
+    def step_batched(self, sigma_t, md_batch_fn):
+        """The same step with all MD runs of the step in one batch.  The gate
+        depends only on the inputs X (the posterior variance does not involve
+        y, and the scales of Eq. d2Eq come from X alone), so the set of MD
+        sections is decided first; the means of the other sections are then
+        taken with the database as Algorithm 1 would have it at that section
+        (all MD results of earlier sections appended)."""
+        self.i += 1
+        t = self.i * self.dt
+        G = self.gradients(t)
+        sn2 = self.sn2()
+        X0 = self.X
+        Xv = self.X
+        sd = np.zeros(self.N); from_md = np.zeros(self.N, bool)
+        for j in range(self.N):
+            x = np.array([[self.h[j], G[j]]])
+            g = ogp.GP(Xv, np.zeros(len(Xv)), self.sf2, self.l2, sn2)   # y does not enter the variance
+            v = g.predict(x)[1]
+            sd[j] = math.sqrt(v[0])
+            if ogp.gate(sd[j], sigma_t):
+                from_md[j] = True
+                Xv = np.vstack([Xv, x])
+        md_idx = np.nonzero(from_md)[0]
+        els = [self.element(j, G[j], self.md_calls + k) for k, j in enumerate(md_idx)]
+        res = md_batch_fn(els) if els else []
+        self.md_calls += len(els)
+        q = np.zeros(self.N)
+        X, y, se = X0, self.y, self.se
+        k = 0
+        for j in range(self.N):
+            if from_md[j]:
+                q[j] = res[k]["q"]
+                X = np.vstack([X, [[self.h[j], G[j]]]])
+                y = np.append(y, res[k]["q"])
+                se = np.append(se, res[k]["q_se"])
+                k += 1
+            else:
+                g = ogp.GP(X, y, self.sf2, self.l2, sn2)
+                q[j] = g.predict(np.array([[self.h[j], G[j]]]))[0][0]
+        self.X, self.y, self.se = X, y, se
+        self.continuity(q)
+        return dict(q=q, sd=sd, from_md=from_md, G=G)
+
+
+def relative_error(q_hist, Q_hist):
+    """Eq. error: sum_i |qbar_i - Q_i| / sum_i |Q_i| over the time history of
+    the section-averaged flow rate (the stray bracket in the printed equation
+    dropped)."""
+    q = np.asarray(q_hist, dtype=np.float64)
+    Q = np.asarray(Q_hist, dtype=np.float64)
+    return float(np.abs(q - Q).sum() / np.abs(Q).sum())
+
+
+def speedup(t_end_steps, n_atoms_full, steps_per_sim, n_sims, mean_atoms_per_sim):
+    """Eq. speedup: t_end N_af / (tbar_sim N_sim Nbar_ah)."""
+    if n_sims == 0:
+        return math.inf
+    return float(t_end_steps * n_atoms_full / (steps_per_sim * n_sims * mean_atoms_per_sim))

@@ -1,0 +1,73 @@
+"""Algorithm 1 oracle: the batched form takes exactly the sequential form's
+decisions and values; macro-model invariants (mass conservation, the
+empty-database prior, thresholds above sigma_f)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import hybrid
+
+
+def fake_md(el):
+    """Deterministic stand-in for an MD run: a smooth flow law in (h, G)
+    plus a hashed perturbation, with a fixed standard error."""
+    h, G = el["h"], el["dpdx"]
+    noise = math.sin(12.9898 * el["id"] + 78.233 * h) * 0.05
+    return {"q": -0.8 * h ** 3 * G / 24.0 + noise, "q_se": 0.05}
+
+
+def fake_batch(els):
+    return [fake_md(e) for e in els]
+
+
+def channel(**kw):
+    base = dict(n_sections=16, dx=50.0, h0=12.0, K=10.0, dP_amp=400.0, period=1000.0, dt=20.0,
+                sf2=1.0, l2=1.0, sn2_default=0.05 ** 2)
+    base.update(kw)
+    return hybrid.Channel(**base)
+
+
+@pytest.mark.parametrize("sigma_t", [0.05, 0.2, 0.5])
+def test_batched_step_equals_sequential(sigma_t):
+    a, b = channel(), channel()
+    for step in range(12):
+        ra = a.step_sequential(sigma_t, fake_md)
+        rb = b.step_batched(sigma_t, fake_batch)
+        assert (ra["from_md"] == rb["from_md"]).all(), step
+        np.testing.assert_allclose(ra["sd"], rb["sd"], rtol=1e-10, atol=1e-13)
+        np.testing.assert_allclose(ra["q"], rb["q"], rtol=1e-9, atol=1e-12)
+        np.testing.assert_allclose(a.n, b.n, rtol=1e-12)
+    assert a.md_calls == b.md_calls > 0
+
+
+def test_mass_is_conserved():
+    c = channel()
+    mass0 = (c.n * c.h * c.Lz * c.dx).sum()
+    for _ in range(10):
+        c.step_batched(0.2, fake_batch)
+    assert (c.n * c.h * c.Lz * c.dx).sum() == pytest.approx(mass0, rel=1e-12)
+
+
+def test_threshold_above_signal_never_runs_md():
+    # empty database: sd = sigma_f everywhere; sigma_t > sigma_f -> prior mean 0 (paper Sec. 3.1)
+    c = channel(sf2=0.36)
+    for _ in range(3):
+        r = c.step_sequential(0.61, fake_md)
+        assert not r["from_md"].any()
+        np.testing.assert_array_equal(r["q"], 0.0)
+        np.testing.assert_allclose(r["sd"], 0.6)
+    assert c.md_calls == 0
+
+
+def test_zero_threshold_runs_md_everywhere():
+    c = channel()
+    r = c.step_batched(0.0, fake_batch)
+    assert r["from_md"].all() or r["sd"].min() > 0   # every sd > 0 asks for MD
+    assert c.md_calls == r["from_md"].sum()
+
+
+def test_error_and_speedup_definitions():
+    assert hybrid.relative_error([1.0, 2.0], [1.0, 4.0]) == pytest.approx(2.0 / 5.0)
+    assert hybrid.speedup(1000, 5000, 100, 5, 1000) == pytest.approx(10.0)
+    assert hybrid.speedup(1000, 5000, 100, 0, 1000) == math.inf
