@@ -220,6 +220,132 @@ int mdgp_gp_predict(mdgp_gp* gp, const double* Xs, int64_t m, const double* mu_X
 int mdgp_gp_scales(const mdgp_gp* gp, double* scales);
 int mdgp_gp_free(mdgp_gp* gp);
 
+/* ------------------------------------------------------------------------ */
+/* Macro time step, Algorithm 1 (paper Sec. 2.4).                            */
+/* ------------------------------------------------------------------------ */
+
+typedef struct mdgp_hybrid mdgp_hybrid;
+
+/* Converging-diverging periodic channel and its coupling (Sec. 2.1):
+ * n_sections sections at x_j = j dx (Eq. subsEq, L = n_sections dx) with
+ * h_j = h0 (1 - 0.5 cos(2 pi x_j / L)); pressure p = eos_K (n - eos_n0);
+ * forcing dP(t) = dP_amp sin(2 pi t / period) applied as the uniform
+ * gradient -dP / L; section j's GP input is (h_j, G_j) with
+ * G_j = dp/dx_j - dP / L (central differences) and its MD element gets
+ * dpdx = G_j (Eq. momentumEq); density update by Eq. continuityEq with
+ * A_j = h_j Lz.  The MD elements are Lx x Lz x h_j at the section's density. */
+typedef struct {
+  int32_t n_sections;     /* >= 3 */
+  int32_t sn2_from_data;  /* 1: sigma_n^2 = (mean standard error of the database runs)^2, taken
+                             at the start of each step; 0: sn2 below */
+  double dx, h0, Lx, Lz;
+  double eos_K, eos_n0;
+  double dP_amp, period, dt;  /* forcing amplitude and period; macro time step */
+  double T;                   /* MD temperature */
+  int64_t md_steps_eq, md_steps_sample;
+  uint64_t seed;              /* MD seed; the k-th MD run of the case gets element id k */
+  double sf2, l2, sn2;        /* q-GP hyperparameters (Sec. 2.3) */
+} mdgp_macro_params;
+
+/* Time step statistics returned by mdgp_hybrid_step. */
+typedef struct {
+  int64_t step;           /* macro steps taken */
+  double t;               /* macro time */
+  int32_t md_runs;        /* MD runs this step */
+  int32_t reserved;
+  int64_t md_runs_total;
+  int64_t db_size;        /* database entries after the step */
+  int64_t md_atoms;       /* atoms over this step's MD runs */
+  double q_mean;          /* section-averaged flow rate */
+  double max_sd;          /* largest predicted standard deviation */
+  double gp_seconds, md_seconds;  /* wall time in GP work and in the MD batch */
+} mdgp_hybrid_stats;
+
+/* Prior mean for the GP (a learned mean): fill out[0..m) at the m rows of
+ * x (m x 2, row-major).  Return 0 on success. */
+typedef int (*mdgp_mean_fn)(void* user, const double* x, int64_t m, double* out);
+
+int mdgp_macro_params_default(mdgp_macro_params* p);
+
+/* New case: densities start at density0 (n_sections values, or eos_n0 when
+ * null); empty database.  Uses ctx for the GP and MD work. */
+int mdgp_hybrid_create(mdgp_ctx* ctx, const mdgp_macro_params* p, const double* density0, mdgp_hybrid** out);
+
+/* Use fn (with user) as the GP prior mean from now on (null: zero mean). */
+int mdgp_hybrid_set_mean(mdgp_hybrid* h, mdgp_mean_fn fn, void* user);
+
+/* One macro step with uncertainty threshold sigma_t (Algorithm 1): MD for
+ * exactly the sections whose predicted standard deviation exceeds sigma_t
+ * when Algorithm 1 reaches them, all of a step's MD runs in one batch. */
+int mdgp_hybrid_step(mdgp_hybrid* h, double sigma_t, mdgp_hybrid_stats* stats);
+
+/* Current per-section state (each pointer may be null; n_sections values):
+ * density, flow rate of the last step, predicted standard deviation, 1 where
+ * the flow rate came from MD, effective gradient G. */
+int mdgp_hybrid_state(const mdgp_hybrid* h, double* density, double* q, double* sd, int32_t* from_md,
+                      double* G);
+
+/* Database: *M entries; with cap >= *M copies inputs (M x 2), outputs and
+ * standard errors (any may be null). */
+int mdgp_hybrid_database(const mdgp_hybrid* h, double* X, double* y, double* se, int64_t cap, int64_t* M);
+int mdgp_hybrid_free(mdgp_hybrid* h);
+
+/* ------------------------------------------------------------------------ */
+/* Learned prior mean: MLP 2 -> 64 -> 64 -> 1 (benchmark addition; the       */
+/* paper's GP has zero prior mean, Sec. 2.2 Eq. GPEq).                        */
+/* ------------------------------------------------------------------------ */
+
+typedef struct mdgp_mlp mdgp_mlp;
+
+/* Full-batch Adam training settings. */
+typedef struct {
+  int32_t epochs;        /* Adam steps (default 2000) */
+  int32_t eval_every;    /* holdout evaluation interval (default 20) */
+  double lr, beta1, beta2, eps;  /* default 1e-3, 0.9, 0.999, 1e-8 */
+  double holdout_frac;   /* rows held out for early stopping (default 0.2, in [0, 1)) */
+  uint64_t seed;         /* split seed */
+} mdgp_mlp_params;
+
+int mdgp_mlp_params_default(mdgp_mlp_params* p);
+
+/* Parameter count (4417): W1 (64 x 2), b1 (64), W2 (64 x 64), b2 (64),
+ * W3 (64), b3 (1), FP32, row-major, a layer computing z = a W^T + b. */
+int mdgp_mlp_num_params(void);
+
+/* New network on ctx's device: initial parameters from init (num_params
+ * floats) or, when null, uniform(+-1/sqrt(fan_in)) from `seed`. */
+int mdgp_mlp_create(mdgp_ctx* ctx, const float* init, uint64_t seed, mdgp_mlp** out);
+int mdgp_mlp_free(mdgp_mlp* m);
+
+/* Train on n rows (X: n x 2 row-major, y: n): inputs and output are
+ * standardised with the training rows' mean and deviation; every epoch is
+ * one full-batch forward/backward (hidden layer products on the tensor cores
+ * in BF16 with FP32 accumulation) and one Adam step on FP32 master weights;
+ * the weights with the lowest holdout loss are kept.  Losses returned in
+ * standardised units (either pointer may be null). */
+int mdgp_mlp_train(mdgp_mlp* m, const double* X, const double* y, int64_t n, const mdgp_mlp_params* p,
+                   double* train_loss, double* holdout_loss);
+
+/* Network output in the original units at n rows of X (n x 2). */
+int mdgp_mlp_predict(mdgp_mlp* m, const double* X, int64_t n, double* out);
+
+/* Mean-squared-error loss and its gradient (num_params floats, may be null)
+ * at the current weights for ALREADY STANDARDISED rows X (n x 2), y (n)
+ * under the current standardiser (identity for a new network). */
+int mdgp_mlp_loss_grad(mdgp_mlp* m, const double* X, const double* y, int64_t n, double* loss, float* grads);
+
+/* One Adam step with the given gradient (num_params floats; null uses the
+ * gradient accumulated on the device). */
+int mdgp_mlp_adam_step(mdgp_mlp* m, const float* grads, const mdgp_mlp_params* p);
+
+/* Copy the parameters (num_params floats) and the standardiser
+ * (x mean[2], x std[2], y mean, y std) out of / into the network. */
+int mdgp_mlp_get(const mdgp_mlp* m, float* params, double* standardiser);
+int mdgp_mlp_set(mdgp_mlp* m, const float* params, const double* standardiser);
+
+/* Use the network as the hybrid's GP prior mean (null: zero mean again). */
+int mdgp_hybrid_set_mlp_mean(mdgp_hybrid* h, mdgp_mlp* m);
+
 /* Last CUDA error string seen by the context (static storage). */
 const char* mdgp_last_error(const mdgp_ctx* ctx);
 

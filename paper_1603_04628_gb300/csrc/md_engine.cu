@@ -364,6 +364,7 @@ static int plan_impl(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int list_
   }
   int list_cap = ctx->params.list_capacity > 0 ? ctx->params.list_capacity : 128;
   if (list_cap_override > list_cap) list_cap = list_cap_override;
+  list_cap = (list_cap + 3) / 4 * 4;  // whole groups of four
   const size_t fsz = ctx->precision == MDGP_PREC_FP32 ? 4 : 8;
   const size_t psz = ctx->precision == MDGP_PREC_FP32 ? sizeof(float4) : sizeof(Pos64);
   const size_t N = (size_t)atoms, C = (size_t)cells;

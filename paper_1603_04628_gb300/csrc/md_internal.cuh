@@ -11,10 +11,11 @@
 //          from the cell centre, w = species) and its value at the last
 //          rebuild (skin check); forces, fluid x-virial share and energy in
 //          the pair-force precision.
-//   lists  per atom up to list_cap neighbour entries, entry-major
-//          ([k][atom], so a warp's loads coalesce): bits 0-25 the neighbour's
-//          element-local sorted index, bits 26-31 the cell shift
-//          (dx+1, dy+1, dz+1) in 2 bits each.
+//   lists  per atom up to list_cap neighbour entries in groups of four,
+//          [k / 4][atom][4] (a warp's 16-byte loads coalesce); an entry holds
+//          in bits 0-25 the neighbour's element-local sorted index and in bits
+//          26-31 the cell shift (dx+1, dy+1, dz+1), 2 bits each; the last
+//          group is padded with an entry that is always beyond r_c.
 //   cells  count (binning atomics), start and size after the per-element scan.
 //   accum  per element FP64 block sums of q and P_xx, temperature sum and the
 //          start/end energies (the time-averaged measurements of Sec. 2.1).

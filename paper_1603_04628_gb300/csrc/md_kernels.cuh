@@ -343,12 +343,21 @@ __global__ void __launch_bounds__(256) k_copy_back(BatchDev B) {
 // lane per atom of the cell; the lanes walk each neighbour cell's atoms
 // together (same address on every lane: a broadcast) and keep those within
 // r_c + skin.  The shift between the two reference cells is warp-uniform.
+// Lists are stored in groups of four entries, [k / 4][atom][4]: a lane
+// collects four entries in registers and writes them with one 16-byte store;
+// the last group is padded with an entry that is always beyond r_c (the atom
+// itself one cell over in x), so readers never test the count inside a group.
+__device__ __forceinline__ unsigned pad_entry(long long i, const ElemDev& E) {
+  return (unsigned)(i - E.atom0) | (2u << 26) | (1u << 28) | (1u << 30);
+}
+
 template <typename PT>
 __global__ void __launch_bounds__(128) k_build(BatchDev B, PhysDev P) {
   using T = decltype(PT::x);
   const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= B.n_cells) return;
+  const int cap4 = B.list_cap >> 2;   // groups per atom
   const int e = B.cell_el[warp];
   const ElemDev& E = B.el[e];
   int cx, cy, cz;
@@ -358,6 +367,7 @@ __global__ void __launch_bounds__(128) k_build(BatchDev B, PhysDev P) {
   const PT* pos = static_cast<const PT*>(B.pos);
   const T rl2 = sizeof(T) == 4 ? (T)P.rl2f : (T)P.rl2;
   const long long N = B.n_atoms;
+  uint4* L4 = reinterpret_cast<uint4*>(B.list);
   for (int base = 0; base < n0; base += 32) {
     const int i = s0 + base + lane;
     const bool act = base + lane < n0;
@@ -365,6 +375,15 @@ __global__ void __launch_bounds__(128) k_build(BatchDev B, PhysDev P) {
     if (act) me = pos[i];
     else { me.x = me.y = me.z = (T)1e9; me.w = (T)0; }
     int cnt = 0;
+    unsigned b0 = 0, b1 = 0, b2 = 0;
+    auto push = [&](unsigned ent) {
+      const int slot = cnt & 3;
+      if (slot == 0) b0 = ent;
+      else if (slot == 1) b1 = ent;
+      else if (slot == 2) b2 = ent;
+      else if ((cnt >> 2) < cap4) L4[(long long)(cnt >> 2) * N + i] = make_uint4(b0, b1, b2, ent);
+      ++cnt;
+    };
     for (int dx = -1; dx <= 1; ++dx) {
       int jx = cx + dx;
       jx = jx < 0 ? jx + ncx : (jx >= ncx ? jx - ncx : jx);
@@ -375,25 +394,42 @@ __global__ void __launch_bounds__(128) k_build(BatchDev B, PhysDev P) {
           int jz = cz + dz;
           jz = jz < 0 ? jz + ncz : (jz >= ncz ? jz - ncz : jz);
           const long long c2 = E.cell0 + ((long long)jx * ncy + jy) * ncz + jz;
-          const T hx = (T)dx * (T)E.cs[0], hy = (T)dy * (T)E.cs[1], hz = (T)dz * (T)E.cs[2];
-          const T qx = me.x - hx, qy = me.y - hy, qz = me.z - hz;
-          const int j0 = B.cstart[c2], nj = B.csize[c2];
+          const T qx = me.x - (T)dx * (T)E.cs[0], qy = me.y - (T)dy * (T)E.cs[1], qz = me.z - (T)dz * (T)E.cs[2];
+          const int j0 = B.cstart[c2], j1 = j0 + B.csize[c2];
           const unsigned code = ((unsigned)(dx + 1) << 26) | ((unsigned)(dy + 1) << 28) | ((unsigned)(dz + 1) << 30);
-          for (int j = j0; j < j0 + nj; ++j) {
-            const PT o = pos[j];
-            const T ddx = qx - o.x, ddy = qy - o.y, ddz = qz - o.z;
-            const T r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-            if (act && r2 < rl2 && j != i) {
-              if (cnt < B.list_cap) B.list[(long long)cnt * N + i] = (unsigned)(j - E.atom0) | code;
-              ++cnt;
-            }
+          const unsigned jb = (unsigned)(j0 - E.atom0) | code;
+          int j = j0;
+          for (; j + 3 < j1; j += 4) {
+            const PT o0 = pos[j], o1 = pos[j + 1], o2 = pos[j + 2], o3 = pos[j + 3];
+            T d0, d1, d2, d3;
+            { const T ax = qx - o0.x, ay = qy - o0.y, az = qz - o0.z; d0 = ax * ax + ay * ay + az * az; }
+            { const T ax = qx - o1.x, ay = qy - o1.y, az = qz - o1.z; d1 = ax * ax + ay * ay + az * az; }
+            { const T ax = qx - o2.x, ay = qy - o2.y, az = qz - o2.z; d2 = ax * ax + ay * ay + az * az; }
+            { const T ax = qx - o3.x, ay = qy - o3.y, az = qz - o3.z; d3 = ax * ax + ay * ay + az * az; }
+            const unsigned ej = jb + (unsigned)(j - j0);
+            if (act && d0 < rl2 && j != i) push(ej);
+            if (act && d1 < rl2 && j + 1 != i) push(ej + 1);
+            if (act && d2 < rl2 && j + 2 != i) push(ej + 2);
+            if (act && d3 < rl2 && j + 3 != i) push(ej + 3);
+          }
+          for (; j < j1; ++j) {
+            const PT o0 = pos[j];
+            const T ax = qx - o0.x, ay = qy - o0.y, az = qz - o0.z;
+            if (act && ax * ax + ay * ay + az * az < rl2 && j != i) push(jb + (unsigned)(j - j0));
           }
         }
       }
     }
     if (act) {
-      B.nlist[i] = cnt < B.list_cap ? cnt : B.list_cap;
+      // pad and write the last, partial group
+      if ((cnt & 3) != 0 && (cnt >> 2) < cap4) {
+        const unsigned pe = pad_entry(i, E);
+        const int slot = cnt & 3;
+        L4[(long long)(cnt >> 2) * N + i] =
+            make_uint4(b0, slot > 1 ? b1 : pe, slot > 2 ? b2 : pe, pe);
+      }
       if (cnt > B.list_cap) atomicMin(&B.status[e], kStOverflow);
+      B.nlist[i] = cnt < B.list_cap ? cnt : B.list_cap;
     }
   }
 }
@@ -471,20 +507,16 @@ __global__ void __launch_bounds__(128) k_force(BatchDev B, PhysDev P) {
     for (int t = 0; t < 3; ++t) { eps[t] = P.eps[t]; sig2[t] = P.sig2[t]; }
   }
   const int spi = me.w != (T)0 ? 1 : 0;
-  // padding entry: the atom itself seen one cell over in x, always beyond r_c
-  const unsigned pad = (unsigned)(i - E.atom0) | (2u << 26) | (1u << 28) | (1u << 30);
   PairAcc<PT, T, UNIFORM, ENERGY> acc;
-  const unsigned* lst = B.list + i;
-  for (int k = 0; k < n; k += 4) {
-    const unsigned e0 = __ldg(lst + (long long)k * N);
-    const unsigned e1 = k + 1 < n ? __ldg(lst + (long long)(k + 1) * N) : pad;
-    const unsigned e2 = k + 2 < n ? __ldg(lst + (long long)(k + 2) * N) : pad;
-    const unsigned e3 = k + 3 < n ? __ldg(lst + (long long)(k + 3) * N) : pad;
-    const PT o0 = posj[e0 & kJMask], o1 = posj[e1 & kJMask], o2 = posj[e2 & kJMask], o3 = posj[e3 & kJMask];
-    acc.add(me, o0, e0, csx, csy, csz, spi, rc2, eps, sig2, P);
-    acc.add(me, o1, e1, csx, csy, csz, spi, rc2, eps, sig2, P);
-    acc.add(me, o2, e2, csx, csy, csz, spi, rc2, eps, sig2, P);
-    acc.add(me, o3, e3, csx, csy, csz, spi, rc2, eps, sig2, P);
+  const uint4* L4 = reinterpret_cast<const uint4*>(B.list) + i;
+  const int ng = (n + 3) >> 2;
+  for (int k = 0; k < ng; ++k) {
+    const uint4 e = __ldg(L4 + (long long)k * N);
+    const PT o0 = posj[e.x & kJMask], o1 = posj[e.y & kJMask], o2 = posj[e.z & kJMask], o3 = posj[e.w & kJMask];
+    acc.add(me, o0, e.x, csx, csy, csz, spi, rc2, eps, sig2, P);
+    acc.add(me, o1, e.y, csx, csy, csz, spi, rc2, eps, sig2, P);
+    acc.add(me, o2, e.z, csx, csy, csz, spi, rc2, eps, sig2, P);
+    acc.add(me, o3, e.w, csx, csy, csz, spi, rc2, eps, sig2, P);
   }
   static_cast<T*>(B.fx)[i] = acc.fx;
   static_cast<T*>(B.fy)[i] = acc.fy;

@@ -46,6 +46,32 @@ class GPParams(ctypes.Structure):
                 ("fallback_scale", ctypes.c_double), ("fixed_scales", ctypes.POINTER(ctypes.c_double))]
 
 
+class MacroParams(ctypes.Structure):
+    _fields_ = [("n_sections", ctypes.c_int32), ("sn2_from_data", ctypes.c_int32),
+                ("dx", ctypes.c_double), ("h0", ctypes.c_double), ("Lx", ctypes.c_double), ("Lz", ctypes.c_double),
+                ("eos_K", ctypes.c_double), ("eos_n0", ctypes.c_double), ("dP_amp", ctypes.c_double),
+                ("period", ctypes.c_double), ("dt", ctypes.c_double), ("T", ctypes.c_double),
+                ("md_steps_eq", ctypes.c_int64), ("md_steps_sample", ctypes.c_int64), ("seed", ctypes.c_uint64),
+                ("sf2", ctypes.c_double), ("l2", ctypes.c_double), ("sn2", ctypes.c_double)]
+
+
+class HybridStats(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_int64), ("t", ctypes.c_double), ("md_runs", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("md_runs_total", ctypes.c_int64), ("db_size", ctypes.c_int64),
+                ("md_atoms", ctypes.c_int64), ("q_mean", ctypes.c_double), ("max_sd", ctypes.c_double),
+                ("gp_seconds", ctypes.c_double), ("md_seconds", ctypes.c_double)]
+
+
+MEAN_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int64,
+                           ctypes.POINTER(ctypes.c_double))
+
+
+class MLPParams(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_int32), ("eval_every", ctypes.c_int32), ("lr", ctypes.c_double),
+                ("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("eps", ctypes.c_double),
+                ("holdout_frac", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
 class MdgpError(RuntimeError):
     pass
 
@@ -83,6 +109,24 @@ def lib():
         "mdgp_gp_predict": ([vp, dp, i64, dp, dp, dp], ctypes.c_int),
         "mdgp_gp_scales": ([vp, dp], ctypes.c_int),
         "mdgp_gp_free": ([vp], ctypes.c_int),
+        "mdgp_macro_params_default": ([ctypes.POINTER(MacroParams)], ctypes.c_int),
+        "mdgp_hybrid_create": ([vp, ctypes.POINTER(MacroParams), dp, ctypes.POINTER(vp)], ctypes.c_int),
+        "mdgp_hybrid_set_mean": ([vp, MEAN_FN, vp], ctypes.c_int),
+        "mdgp_hybrid_step": ([vp, ctypes.c_double, ctypes.POINTER(HybridStats)], ctypes.c_int),
+        "mdgp_hybrid_state": ([vp, dp, dp, dp, ctypes.POINTER(ctypes.c_int32), dp], ctypes.c_int),
+        "mdgp_hybrid_database": ([vp, dp, dp, dp, i64, ctypes.POINTER(i64)], ctypes.c_int),
+        "mdgp_hybrid_free": ([vp], ctypes.c_int),
+        "mdgp_mlp_params_default": ([ctypes.POINTER(MLPParams)], ctypes.c_int),
+        "mdgp_mlp_num_params": ([], ctypes.c_int),
+        "mdgp_mlp_create": ([vp, ctypes.POINTER(ctypes.c_float), ctypes.c_uint64, ctypes.POINTER(vp)], ctypes.c_int),
+        "mdgp_mlp_free": ([vp], ctypes.c_int),
+        "mdgp_mlp_train": ([vp, dp, dp, i64, ctypes.POINTER(MLPParams), dp, dp], ctypes.c_int),
+        "mdgp_mlp_predict": ([vp, dp, i64, dp], ctypes.c_int),
+        "mdgp_mlp_loss_grad": ([vp, dp, dp, i64, dp, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+        "mdgp_mlp_adam_step": ([vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(MLPParams)], ctypes.c_int),
+        "mdgp_mlp_get": ([vp, ctypes.POINTER(ctypes.c_float), dp], ctypes.c_int),
+        "mdgp_mlp_set": ([vp, ctypes.POINTER(ctypes.c_float), dp], ctypes.c_int),
+        "mdgp_hybrid_set_mlp_mean": ([vp, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -261,6 +305,168 @@ class GP:
             pass
 
 
+class Hybrid:
+    """One hybrid case (mdgp_hybrid): macro state, database, Algorithm 1 steps."""
+
+    def __init__(self, ctx, density0=None, **params):
+        p = MacroParams()
+        _check(None, lib().mdgp_macro_params_default(ctypes.byref(p)), "mdgp_macro_params_default")
+        names = {f for f, _ in MacroParams._fields_}
+        for k, v in params.items():
+            if k not in names:
+                raise MdgpError("unknown macro parameter %r" % k)
+            setattr(p, k, v)
+        self.N = p.n_sections
+        self.ctx = ctx
+        self.h = ctypes.c_void_p()
+        d0 = None
+        if density0 is not None:
+            self._d0 = np.ascontiguousarray(density0, dtype=np.float64)
+            d0 = _dp(self._d0)
+        _check(ctx.h, lib().mdgp_hybrid_create(ctx.h, ctypes.byref(p), d0, ctypes.byref(self.h)),
+               "mdgp_hybrid_create")
+        self._mean_cb = None
+
+    def set_mean(self, fn):
+        """fn(X (m x 2) -> (m,)) as the GP prior mean, or None."""
+        if fn is None:
+            self._mean_cb = None
+            _check(self.ctx.h, lib().mdgp_hybrid_set_mean(self.h, MEAN_FN(), None), "mdgp_hybrid_set_mean")
+            return
+
+        def cb(user, x, m, out):
+            try:
+                X = np.ctypeslib.as_array(x, shape=(m, 2)).copy() if m else np.zeros((0, 2))
+                v = np.asarray(fn(X), dtype=np.float64).reshape(m)
+                ctypes.memmove(out, v.ctypes.data, 8 * m)
+                return 0
+            except Exception:
+                return -1
+        self._mean_cb = MEAN_FN(cb)
+        _check(self.ctx.h, lib().mdgp_hybrid_set_mean(self.h, self._mean_cb, None), "mdgp_hybrid_set_mean")
+
+    def set_mlp_mean(self, mlp):
+        self._mlp = mlp
+        _check(self.ctx.h, lib().mdgp_hybrid_set_mlp_mean(self.h, mlp.h if mlp is not None else None),
+               "mdgp_hybrid_set_mlp_mean")
+
+    def step(self, sigma_t):
+        st = HybridStats()
+        _check(self.ctx.h, lib().mdgp_hybrid_step(self.h, float(sigma_t), ctypes.byref(st)), "mdgp_hybrid_step")
+        return {k: getattr(st, k) for k, _ in HybridStats._fields_ if k != "reserved"}
+
+    def state(self):
+        n = np.zeros(self.N); q = np.zeros(self.N); sd = np.zeros(self.N); G = np.zeros(self.N)
+        fm = np.zeros(self.N, np.int32)
+        _check(None, lib().mdgp_hybrid_state(self.h, _dp(n), _dp(q), _dp(sd),
+                                             fm.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dp(G)),
+               "mdgp_hybrid_state")
+        return dict(density=n, q=q, sd=sd, from_md=fm.astype(bool), G=G)
+
+    def database(self):
+        M = ctypes.c_int64()
+        _check(None, lib().mdgp_hybrid_database(self.h, None, None, None, 0, ctypes.byref(M)), "db size")
+        m = M.value
+        X = np.zeros((m, 2)); y = np.zeros(m); se = np.zeros(m)
+        _check(None, lib().mdgp_hybrid_database(self.h, _dp(X), _dp(y), _dp(se), m, ctypes.byref(M)),
+               "mdgp_hybrid_database")
+        return X, y, se
+
+    def close(self):
+        if self.h:
+            lib().mdgp_hybrid_free(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+MLP_ORDER = [("W1", (64, 2)), ("b1", (64,)), ("W2", (64, 64)), ("b2", (64,)), ("W3", (1, 64)), ("b3", (1,))]
+
+
+def mlp_flatten(params):
+    return np.concatenate([np.asarray(params[k], dtype=np.float32).reshape(-1) for k, _ in MLP_ORDER])
+
+
+def mlp_unflatten(flat):
+    out, off = {}, 0
+    for k, shp in MLP_ORDER:
+        n = int(np.prod(shp))
+        out[k] = np.asarray(flat[off:off + n], dtype=np.float64).reshape(shp)
+        off += n
+    return out
+
+
+def mlp_params_default(**kw):
+    p = MLPParams()
+    _check(None, lib().mdgp_mlp_params_default(ctypes.byref(p)), "mdgp_mlp_params_default")
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+class MLP:
+    """The learned prior mean (mdgp_mlp) on ctx's device."""
+
+    def __init__(self, ctx, params=None, seed=1):
+        self.ctx = ctx
+        self.h = ctypes.c_void_p()
+        init = None
+        if params is not None:
+            self._init = mlp_flatten(params)
+            init = self._init.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        _check(ctx.h, lib().mdgp_mlp_create(ctx.h, init, int(seed), ctypes.byref(self.h)), "mdgp_mlp_create")
+
+    def train(self, X, y, **kw):
+        X = np.ascontiguousarray(X, dtype=np.float64); y = np.ascontiguousarray(y, dtype=np.float64)
+        p = mlp_params_default(**kw)
+        tl = ctypes.c_double(); hl = ctypes.c_double()
+        _check(None, lib().mdgp_mlp_train(self.h, _dp(X), _dp(y), len(y), ctypes.byref(p), ctypes.byref(tl),
+                                          ctypes.byref(hl)), "mdgp_mlp_train")
+        return tl.value, hl.value
+
+    def predict(self, X):
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        out = np.zeros(len(X))
+        _check(None, lib().mdgp_mlp_predict(self.h, _dp(X), len(X), _dp(out)), "mdgp_mlp_predict")
+        return out
+
+    def loss_grad(self, X, y):
+        X = np.ascontiguousarray(X, dtype=np.float64); y = np.ascontiguousarray(y, dtype=np.float64)
+        g = np.zeros(lib().mdgp_mlp_num_params(), np.float32)
+        loss = ctypes.c_double()
+        _check(None, lib().mdgp_mlp_loss_grad(self.h, _dp(X), _dp(y), len(y), ctypes.byref(loss),
+                                              g.ctypes.data_as(ctypes.POINTER(ctypes.c_float))), "mdgp_mlp_loss_grad")
+        return loss.value, mlp_unflatten(g)
+
+    def adam_step(self, grads, **kw):
+        g = mlp_flatten(grads)
+        p = mlp_params_default(**kw)
+        _check(None, lib().mdgp_mlp_adam_step(self.h, g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                              ctypes.byref(p)), "mdgp_mlp_adam_step")
+
+    def get(self):
+        w = np.zeros(lib().mdgp_mlp_num_params(), np.float32)
+        st = np.zeros(6)
+        _check(None, lib().mdgp_mlp_get(self.h, w.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), _dp(st)),
+               "mdgp_mlp_get")
+        return mlp_unflatten(w), st
+
+    def close(self):
+        if self.h:
+            lib().mdgp_mlp_free(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 # Same names as the C ABI.
 def mdgp_create(device=0, precision=PREC_FP64):
     return Context(device, precision)
@@ -276,3 +482,11 @@ def mdgp_gp_fit(ctx, X, y, sf2, l2, sn2, mu_X=None, **kw):
 
 def mdgp_gp_predict(gp, Xs, mu_Xs=None):
     return gp.predict(Xs, mu_Xs)
+
+
+def mdgp_hybrid_create(ctx, density0=None, **params):
+    return Hybrid(ctx, density0, **params)
+
+
+def mdgp_hybrid_step(hybrid, sigma_t):
+    return hybrid.step(sigma_t)

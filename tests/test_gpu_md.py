@@ -219,24 +219,35 @@ def _oracle_run(el):
 
 
 def test_long_run_flow_rate_fp32_within_oracle_ensemble(native):
-    # configuration of the single plain element, 2000 + 3000 steps, body force
-    # 0.05 (a clear signal), eight seeds on each side
-    seeds = [101 + k for k in range(8)]
+    # the plain element (2000 + 3000 steps) with body force 0.05, sixteen seeds
+    # on each side; the standard error of each ensemble mean is the spread
+    # across seeds / sqrt(16) (independent runs), the bound is |z| < 3
+    seeds = [301 + k for k in range(16)]
     els = [synth.element_plain(seed=s, g=0.05, elem_id=k) for k, s in enumerate(seeds)]
     ctx_pool = mp.get_context("spawn")
-    with ctx_pool.Pool(8) as pool:
+    with ctx_pool.Pool(16) as pool:
         refs = pool.map(_oracle_run, els)
     ctx = native.Context(0, native.PREC_FP32)
     res = ctx.micro_batch(els)
     ctx.close()
-    for key, sek in (("q", "q_se"), ("p", "p_se")):
+    for key in ("q", "p", "T_meas"):
         g = np.array([r[key] for r in res])
         o = np.array([r[key] for r in refs])
-        se_g = math.sqrt(sum(r[sek] ** 2 for r in res)) / len(res)
-        se_o = math.sqrt(sum(r[sek] ** 2 for r in refs)) / len(refs)
-        z = abs(g.mean() - o.mean()) / math.sqrt(se_g ** 2 + se_o ** 2)
+        se = math.sqrt(g.var(ddof=1) / len(g) + o.var(ddof=1) / len(o))
+        z = abs(g.mean() - o.mean()) / se
         print("%s: gpu %.4f oracle %.4f z %.2f" % (key, g.mean(), o.mean(), z))
         assert z < 3.0, (key, z)
-    tg = np.mean([r["T_meas"] for r in res])
-    to = np.mean([r["T_meas"] for r in refs])
-    assert tg == pytest.approx(to, rel=0.02)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_energy_conservation_without_thermostat_or_forcing(native, prec):
+    # NVE (gamma = 0, g = 0): velocity Verlet conserves energy up to O(dt^2)
+    # fluctuations; a pair missed by the neighbour lists would show as a jump
+    el = synth.element_plain(steps_eq=1500, steps_sample=500, g=0.0)
+    ctx = native.Context(0, prec, gamma_wall=0.0)
+    r = ctx.micro_batch([el])[0]
+    ctx.close()
+    ref = omd.element(omd.make_params(el, gamma_wall=0.0))
+    assert r["status"] == 0
+    assert abs(ref["e_drift"]) < 2e-3
+    assert abs(r["e_drift"]) < 2e-3 + 2 * abs(ref["e_drift"])
