@@ -40,7 +40,8 @@ typedef enum {
   MDGP_E_TIMEOUT = -6,   /* a bounded device-side wait gave up */
   MDGP_E_STATE = -7,     /* call out of order (e.g. launch before plan) */
   MDGP_E_OVERFLOW = -8,  /* an atom had more neighbours than the list capacity */
-  MDGP_E_SKIN = -9       /* an atom moved more than half the list skin between rebuilds */
+  MDGP_E_SKIN = -9,      /* an atom moved more than half the list skin between rebuilds */
+  MDGP_E_LIMIT = -10     /* a size beyond a fixed limit of an allocation-free entry point */
 } mdgp_status;
 
 typedef enum {
@@ -215,6 +216,31 @@ int mdgp_gp_fit(mdgp_ctx* ctx, const double* X, const double* y, int64_t M, int3
  * the diagonal (Eq. predVarEq), clamped at 0.  mu_Xs may be null (zero prior
  * mean).  Host arrays; blocking. */
 int mdgp_gp_predict(mdgp_gp* gp, const double* Xs, int64_t m, const double* mu_Xs, double* mean, double* var);
+
+/* Allocation-free posterior (no counterpart in the paper: an addition for
+ * callers that cannot call cudaMalloc while they run, such as applications
+ * that hand all device memory to their own pool allocator up front, or
+ * latency-bound loops where an allocation, which may synchronise the
+ * device, is not acceptable).  Computes what mdgp_gp_fit followed by
+ * mdgp_gp_predict computes, but every buffer beyond the caller's inputs and
+ * outputs lives in one fixed device array inside the library (about 2 MiB,
+ * held on every GPU that loads the library until the process exits); it
+ * calls no allocator.
+ *   X (M x D), y (M), mu_X (M, nullable), Xs (m x D), mu_Xs (m, nullable)
+ *   and the outputs mean (m), var (m) are DEVICE pointers on the current
+ *   device; params as for mdgp_gp_fit (fixed_scales must be null); stream is
+ *   a cudaStream_t (0 = legacy default stream).
+ *   Limits: 1 <= M <= 512 (MDGP_E_LIMIT beyond), 1 <= D <= 8.
+ *   The first call on a device looks up the array's device address once
+ *   (with that device current); make that first call before any stream
+ *   capture.  Blocking: returns after the stream has finished the work, with
+ *   MDGP_E_NOTPD if the covariance was not positive definite.
+ *   Every call shares the one array: calls that can overlap on the GPU
+ *   (from several host threads or streams) race and must be serialised by
+ *   the caller.  The call clears what must start at zero itself. */
+int mdgp_gp_posterior_noalloc(const double* X, const double* y, int64_t M, int32_t D,
+                              const mdgp_gp_params* params, const double* mu_X, const double* Xs, int64_t m,
+                              const double* mu_Xs, double* mean, double* var, void* stream);
 
 /* The D input scales the fit used (Eq. d2Eq denominators). */
 int mdgp_gp_scales(const mdgp_gp* gp, double* scales);

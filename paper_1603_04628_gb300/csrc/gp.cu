@@ -437,3 +437,87 @@ int mdgp_gp_free(mdgp_gp* g) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free GP posterior.
+//
+// For callers that cannot call cudaMalloc while they run: an application
+// whose device memory is all handed to its own pool allocator up front, or a
+// latency-bound control loop where an allocation (which may synchronise the
+// device) is not acceptable.  The factorisation lives in one file-scope
+// device array of a fixed size instead of in buffers from cudaMalloc.  Every
+// GPU that loads the library holds the array until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kNoAllocMaxM = 512;   // largest database this entry point accepts
+constexpr size_t kNoAllocL = (size_t)kNoAllocMaxM * kNoAllocMaxM;
+// layout: Cholesky factor [512 x 512] | alpha [512] | scales [8] | status word
+constexpr size_t kNoAllocDoubles = kNoAllocL + kNoAllocMaxM + kMaxD + 8;
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+constexpr int kNoAllocMaxDevices = 64;
+double* g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device (looked up once
+// per device; the symbol name is only a host-side handle).
+int noalloc_scratch(int device, double** out) {
+  if (device < 0 || device >= kNoAllocMaxDevices) return MDGP_E_ARG;
+  if (!g_noalloc_ptr[device]) {
+    double* p = nullptr;
+    if (cudaGetSymbolAddress((void**)&p, g_noalloc_scratch) != cudaSuccess || !p) return MDGP_E_CUDA;
+    g_noalloc_ptr[device] = p;
+  }
+  *out = g_noalloc_ptr[device];
+  return MDGP_OK;
+}
+
+}  // namespace
+
+extern "C" int mdgp_gp_posterior_noalloc(const double* X, const double* y, int64_t M, int32_t D,
+                                         const mdgp_gp_params* params, const double* mu_X, const double* Xs,
+                                         int64_t m, const double* mu_Xs, double* mean, double* var,
+                                         void* stream) {
+  if (!params || M < 1 || D < 1 || D > kMaxD || m < 0 || !X || !y || (m > 0 && (!Xs || !mean || !var)))
+    return MDGP_E_ARG;
+  if (M > kNoAllocMaxM) return MDGP_E_LIMIT;  // the scratch array holds at most 512 entries
+  if (!(params->sf2 > 0) || !(params->l2 > 0) || !(params->sn2 >= 0) || params->fixed_scales) return MDGP_E_ARG;
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess) return MDGP_E_CUDA;
+  double* base = nullptr;
+  int st = noalloc_scratch(device, &base);
+  if (st) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int Mi = (int)M, Mp = (int)((M + TB - 1) / TB * TB);
+  double* L = base;
+  double* alpha = base + kNoAllocL;
+  double* scale = alpha + kNoAllocMaxM;
+  int* status = (int*)(scale + kMaxD);
+  // the scratch keeps the previous call's contents: clear the accumulators
+  if (cudaMemsetAsync(scale, 0, sizeof(double) * (kMaxD + 8), s) != cudaSuccess) return MDGP_E_CUDA;
+  const double fallback = params->fallback_scale > 0 ? params->fallback_scale : 1.0;
+  k_gp_pairsep<<<(Mi + 255) / 256, 256, 0, s>>>(X, Mi, D, scale);
+  k_gp_scales<<<1, 32, 0, s>>>(scale, Mi, D, fallback, nullptr);
+  // the factor is laid out with leading dimension Mp inside the fixed array
+  k_gp_cov<<<dim3((Mp + 127) / 128, Mp), 128, 0, s>>>(X, Mi, Mp, D, scale, params->sf2, params->l2, params->sn2,
+                                                      L);
+  const int nt = Mp / TB;
+  for (int kb = 0; kb < nt; ++kb) {
+    k_potrf_diag<<<1, dim3(TB, TB), 0, s>>>(L, Mp, kb, status);
+    const int rest = nt - kb - 1;
+    if (rest > 0) {
+      k_trsm_panel<<<rest, dim3(TB, TB), 0, s>>>(L, Mp, kb);
+      k_syrk_update<<<rest * (rest + 1) / 2, dim3(TB, TB), 0, s>>>(L, Mp, kb, nt);
+    }
+  }
+  k_gp_alpha<<<1, 256, sizeof(double) * Mp, s>>>(L, Mi, Mp, y, mu_X, alpha);
+  if (m > 0)
+    k_gp_predict<<<(unsigned)m, 256, sizeof(double) * Mp, s>>>(X, L, alpha, scale, Mi, Mp, D, params->sf2,
+                                                               params->l2, Xs, mu_Xs, mean, var);
+  if (cudaGetLastError() != cudaSuccess) return MDGP_E_CUDA;
+  int h_status = 0;
+  if (cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MDGP_E_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return MDGP_E_CUDA;
+  return h_status ? h_status : MDGP_OK;
+}

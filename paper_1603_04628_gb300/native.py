@@ -12,7 +12,7 @@ LIB_PATH = os.path.join(_PKG, "libmdgp.so")
 MDGP_OK = 0
 STATUS = {0: "MDGP_OK", -1: "MDGP_E_ARG", -2: "MDGP_E_NOMEM", -3: "MDGP_E_CUDA", -4: "MDGP_E_UNSTABLE",
           -5: "MDGP_E_NOTPD", -6: "MDGP_E_TIMEOUT", -7: "MDGP_E_STATE", -8: "MDGP_E_OVERFLOW",
-          -9: "MDGP_E_SKIN"}
+          -9: "MDGP_E_SKIN", -10: "MDGP_E_LIMIT"}
 PREC_FP64 = 0
 PREC_FP32 = 1
 
