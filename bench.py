@@ -34,6 +34,7 @@ N_ELEMENTS = 64
 FP32_PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 flop x SM clock"
 ALG_FLOPS_PER_ATOM_STEP = 600.0      # 26.2 unique pairs x ~23 FP32 flops (Newton's third law)
 ALG_BYTES_PER_ATOM_STEP = 96.0       # FP64 x and v read and written once per step
+CPU_SAMPLE_STEPS = 1000              # oracle steps per sampled element (~10-20 s of CPU work)
 
 
 def _oracle_element_steps(args):
@@ -105,7 +106,7 @@ def run_reference(args):
     els = synth.batch_uneven(N_ELEMENTS, steps=STEPS_PER_ELEMENT)
     cores = os.cpu_count() or 1
     sample_els = els[:min(len(els), cores)]
-    sample_steps = 150
+    sample_steps = args.sample_steps
     from oracle import md as omd
     omd.build()
     with mp.get_context("spawn").Pool(len(sample_els)) as pool:
@@ -144,15 +145,30 @@ def main():
                     help="steps of the FP64-forces pass reported beside the headline")
     ap.add_argument("--steps-per-element", type=int, default=STEPS_PER_ELEMENT,
                     help="MD steps per element (shorter runs for profiling only)")
+    ap.add_argument("--case", default="micro", choices=["micro", "channel"],
+                    help="micro: the uneven micro-element batch (default); channel: the full hybrid "
+                         "(Algorithm 1) threshold sweep on the 200-section channel")
+    ap.add_argument("--channel-steps", type=int, default=100)
+    ap.add_argument("--sample-steps", type=int, default=300,
+                    help="oracle steps per sampled element in the reference arm")
+    ap.add_argument("--workload", default="uneven", choices=["uneven", "stress"],
+                    help="uneven: 64 elements, 500-5000 fluid atoms, 20000 steps (default); stress: 4096 "
+                         "elements, 2k-32k fluid atoms, 60 M atoms, 10000 steps")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.case == "channel":
+        return run_channel_case(args)
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    steps_el = args.steps_per_element
-    els = synth.batch_uneven(N_ELEMENTS, seed=synth.BASE_SEED + 1000 * rank, steps=steps_el)
+    if args.workload == "stress":
+        steps_el = args.steps_per_element if args.steps_per_element != STEPS_PER_ELEMENT else 10000
+        els = synth.batch_stress(seed=synth.BASE_SEED + 5 + 1000 * rank, steps=steps_el)
+    else:
+        steps_el = args.steps_per_element
+        els = synth.batch_uneven(N_ELEMENTS, seed=synth.BASE_SEED + 1000 * rank, steps=steps_el)
 
     # CPU pool first (spawned before any CUDA work)
     pool = None
@@ -245,23 +261,27 @@ def main():
     cpu = None
     if pool is not None:
         sample_els = els[:min(len(els), os.cpu_count() or 1)]
-        rate, cu, wall = cpu_baseline(pool, sample_els, 150)
+        csteps = CPU_SAMPLE_STEPS if args.workload == "uneven" else CPU_SAMPLE_STEPS // 10
+        rate, cu, wall = cpu_baseline(pool, sample_els, csteps)
         pool.close()
         cpu = {"value": rate, "unit": UNIT, "cores": len(sample_els), "kind": "oracle",
-               "sample": "%d of the 64 uneven elements x 150 steps, FP64 oracle, one process per element "
-                         "(%.1f s wall)" % (len(sample_els), wall)}
+               "sample": "%d of the %d elements x %d steps, FP64 oracle, one process per element "
+                         "(%.1f s wall)" % (len(sample_els), len(els), csteps, wall)}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 forces + f64 state", "data": "synthetic",
-            "config": {"workload": "uneven batch: 64 elements, h 5-20, lateral 10-16, 500-5000 fluid atoms, "
-                                   "g 0.005-0.05, %d steps, FP32 forces + FP64 state" % steps_el,
-                       "elements": N_ELEMENTS, "atoms_per_rank": n_atoms, "steps_per_element": steps_el,
+            "config": {"workload": ("uneven batch: 64 elements, h 5-20, lateral 10-16, 500-5000 fluid atoms, "
+                                    "g 0.005-0.05, %d steps, FP32 forces + FP64 state" % steps_el)
+                       if args.workload == "uneven" else
+                       ("stress batch: 4096 elements, h 5-40, n 0.7-0.9, 2k-32k fluid atoms, %d steps, FP32 forces "
+                        "+ FP64 state" % steps_el),
+                       "elements": len(els), "atoms_per_rank": n_atoms, "steps_per_element": steps_el,
                        "l2": "flushed between timed iterations (256 MB write)",
                        "parallelism": "independent elements per rank" if world > 1 else "1 GPU"},
-            "roofline": {"bound": "alu", "kernel": "k_force_cells", "achieved": achieved, "peak": fp32_peak,
+            "roofline": {"bound": "alu", "kernel": "k_force", "achieved": achieved, "peak": fp32_peak,
                          "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
                          "peak_note": FP32_PEAK_NOTE + " (derived, max SM clock)",
                          "alg_flops_per_atom_step": ALG_FLOPS_PER_ATOM_STEP,
@@ -281,6 +301,35 @@ def main():
     ctx.close()
     if dist:
         dist.destroy_process_group()
+    return 0
+
+
+def run_channel_case(args):
+    """Hybrid speed-up against the MD-everywhere reference at each threshold
+    of the sweep (paper Sec. 3.1, Eqs. error and speedup)."""
+    import torch
+    from paper_1603_04628_gb300 import cases, native
+    torch.cuda.set_device(0)
+    ctx = native.Context(0, native.PREC_FP32)
+    sn = 0.5
+    params = dict(n_sections=200, dx=50.0, h0=12.0, Lx=10.0, Lz=10.0, eos_K=10.0, eos_n0=0.8, dP_amp=400.0,
+                  period=1000.0, dt=20.0, T=1.1, md_steps_eq=2000, md_steps_sample=3000, seed=synth.BASE_SEED,
+                  sf2=(20 * sn) ** 2, l2=1.0, sn2=sn ** 2, sn2_from_data=0)
+    thresholds = [f * sn for f in (0.5, 1.0, 2.0, 4.0, 8.0)]
+    out = cases.channel_sweep(ctx, thresholds, n_steps=args.channel_steps, seed_noise=synth.BASE_SEED + 99,
+                              **params)
+    ref = out["reference"]
+    rows = [{k: r[k] for k in ("sigma_t", "md_runs", "error", "speedup_eq", "wall_s", "wall_vs_reference",
+                                "gp_s", "md_s")} for r in out["rows"]]
+    line = {"metric": "hybrid speed-up vs MD-everywhere at set flow error", "case": "channel",
+            "unit": "x", "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": "200-section converging-diverging channel, h0 = 12, 100 macro steps, "
+                                   "plain 10 x h x 10 elements (2000 + 3000 steps, FP32 forces)",
+                       "sigma_n": sn, "sigma_f": 20 * sn},
+            "reference": {"md_runs": ref["md_runs"], "wall_s": ref["wall_s"]},
+            "thermal_noise_error": out.get("noise_error"), "rows": rows}
+    print(json.dumps(line), flush=True)
+    ctx.close()
     return 0
 
 

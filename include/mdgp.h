@@ -99,14 +99,21 @@ typedef struct {
   double tau_T;         /* Berendsen time constant, mode 1 (default 0.5) */
   double mass;          /* atom mass (default 1) */
   int32_t n_blocks;     /* blocks for the standard error (default 10, max 64) */
-  int32_t mode;         /* 0: tethered walls + Langevin wall thermostat; 1: frozen walls +
-                           Berendsen on the fluid's v_z (paper App. A) */
+  int32_t mode;         /* 0: tethered walls + Langevin wall thermostat; 1: frozen walls (no
+                           wall-wall pairs) + Berendsen on the fluid's v_z with time constant tau_T
+                           (paper App. A; pair it with eps_wf 0.2, sig_wf 0.75, wall_density 4,
+                           rc 4, dt 0.0025, T 2.44 for the paper's parameters) */
   int32_t wall_planes;  /* FCC (100) planes per wall (default 3) */
   int32_t list_capacity;/* neighbour-list entries per atom (default 128; a batch that
                            overflows it is rerun by mdgp_micro_batch with twice as many) */
   double skin;          /* Verlet-list skin beyond r_c (default 0.4) */
-  int32_t rebuild_every;/* steps between list rebuilds; 0 = from the skin and T (default 0) */
-  int32_t reserved;
+  int32_t rebuild_every;/* eager paths (mdgp_micro_profile): steps between list rebuilds; 0 = from
+                           the skin and T.  Graph replays rebuild when an atom has moved skin/2. */
+  int32_t build_variant;/* list build: 0 = cell columns staged in shared memory by bulk async
+                           copies, 1 = direct reads of global memory (lanes over a cell's
+                           atoms), 2 = warp ballots over bounding-box-culled candidates
+                           (lanes over candidates; default).  All three give each atom the
+                           same set of neighbours within r_c + skin. */
 } mdgp_md_params;
 
 /* Fill *out with the defaults listed above.  Returns MDGP_E_ARG on null. */
@@ -302,7 +309,10 @@ int mdgp_hybrid_set_mean(mdgp_hybrid* h, mdgp_mean_fn fn, void* user);
 
 /* One macro step with uncertainty threshold sigma_t (Algorithm 1): MD for
  * exactly the sections whose predicted standard deviation exceeds sigma_t
- * when Algorithm 1 reaches them, all of a step's MD runs in one batch. */
+ * when Algorithm 1 reaches them, all of a step's MD runs in one batch.
+ * sigma_t = 0 runs MD at every section without evaluating the GP (the
+ * MD-everywhere reference; the database still grows).  MDGP_E_ARG for a
+ * negative or NaN sigma_t. */
 int mdgp_hybrid_step(mdgp_hybrid* h, double sigma_t, mdgp_hybrid_stats* stats);
 
 /* Current per-section state (each pointer may be null; n_sections values):
@@ -371,6 +381,15 @@ int mdgp_mlp_set(mdgp_mlp* m, const float* params, const double* standardiser);
 
 /* Use the network as the hybrid's GP prior mean (null: zero mean again). */
 int mdgp_hybrid_set_mlp_mean(mdgp_hybrid* h, mdgp_mlp* m);
+
+/* Choose the neighbour-list skin (0.3-0.6) and the list-build variant for
+ * this batch by timing: each candidate runs the batch for probe_steps steps
+ * (after one warm-up run) with CUDA events on the context's stream; the
+ * fastest is kept in the context (and copied to *best, its atom-steps/s to
+ * *best_rate; either may be null).  Results do not depend on the choice
+ * beyond rounding. */
+int mdgp_autotune(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int64_t probe_steps, mdgp_md_params* best,
+                  double* best_rate);
 
 /* Last CUDA error string seen by the context (static storage). */
 const char* mdgp_last_error(const mdgp_ctx* ctx);

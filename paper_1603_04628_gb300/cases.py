@@ -1,0 +1,127 @@
+"""The converging-diverging channel case (paper Sec. 3; Algorithm 1) driven
+through the library's C ABI.
+
+run_channel() advances one hybrid case for n_steps macro steps at a given
+uncertainty threshold and returns the section-averaged flow-rate history, the
+MD call count and wall times.  channel_sweep() runs a threshold sweep plus the
+sigma_t = 0 case that runs MD at every section and step, which stands in for
+the paper's full-MD reference (that data is not available here), and reports
+for each threshold:
+  - Eq. error: sum_i |qbar_i - Q_i| / sum_i |Q_i| against the sigma_t = 0 run;
+  - the same quantity between two sigma_t = 0 runs with different MD seeds
+    (the thermal noise of the reference);
+  - Eq. speedup: t_end N_af / (tbar_sim N_sim Nbar_ah), with N_af the atoms a
+    full MD of the whole channel would hold;
+  - the measured wall time against the sigma_t = 0 run's.
+"""
+import math
+import time
+
+import numpy as np
+
+from . import native
+
+
+def channel_atoms(params):
+    """Atoms of a full MD of the whole channel: fluid at the initial density
+    over every section's cross-section plus the two tethered walls."""
+    N, dx, h0, Lz, n0 = params["n_sections"], params["dx"], params["h0"], params["Lz"], params["eos_n0"]
+    x = np.arange(N) * dx
+    h = h0 * (1.0 - 0.5 * np.cos(2.0 * math.pi * x / (N * dx)))
+    fluid = float((n0 * h * Lz * dx).sum())
+    a0 = 4.0 ** (1.0 / 3.0)
+    walls = 2 * 3 * 2 * (N * dx / a0) * (Lz / a0)
+    return fluid + walls
+
+
+def run_channel(ctx, sigma_t, n_steps, mlp=None, sf2=None, **params):
+    p = dict(params)
+    if sf2 is not None:
+        p["sf2"] = sf2
+    hy = native.Hybrid(ctx, **p)
+    if mlp is not None:
+        hy.set_mlp_mean(mlp)
+    qbar, md_runs, md_atoms = [], 0, 0
+    t0 = time.perf_counter()
+    gp_s = md_s = 0.0
+    for _ in range(n_steps):
+        st = hy.step(sigma_t)
+        qbar.append(st["q_mean"])
+        md_runs += st["md_runs"]
+        md_atoms += st["md_atoms"]
+        gp_s += st["gp_seconds"]
+        md_s += st["md_seconds"]
+    wall = time.perf_counter() - t0
+    X, y, se = hy.database()
+    hy.close()
+    return dict(sigma_t=sigma_t, qbar=np.array(qbar), md_runs=md_runs, md_atoms=md_atoms, wall_s=wall,
+                gp_s=gp_s, md_s=md_s, db=(X, y, se))
+
+
+def error(q, Q):
+    return float(np.abs(np.asarray(q) - np.asarray(Q)).sum() / np.abs(np.asarray(Q)).sum())
+
+
+def channel_sweep(ctx, thresholds, n_steps=100, seed_noise=None, **params):
+    ref = run_channel(ctx, 0.0, n_steps, **params)
+    out = {"reference": ref}
+    if seed_noise is not None:
+        noise = run_channel(ctx, 0.0, n_steps, **dict(params, seed=seed_noise))
+        out["noise_error"] = error(noise["qbar"], ref["qbar"])
+        out["noise"] = noise
+    md_steps = params["md_steps_eq"] + params["md_steps_sample"]
+    t_end_steps = n_steps * params["dt"] / 0.005
+    n_af = channel_atoms(params)
+    rows = []
+    for s in thresholds:
+        r = run_channel(ctx, s, n_steps, **params)
+        mean_atoms = r["md_atoms"] / r["md_runs"] if r["md_runs"] else 0.0
+        rows.append(dict(
+            sigma_t=s, md_runs=r["md_runs"], error=error(r["qbar"], ref["qbar"]),
+            speedup_eq=(t_end_steps * n_af / (md_steps * r["md_runs"] * mean_atoms)) if r["md_runs"] else math.inf,
+            wall_s=r["wall_s"], wall_vs_reference=ref["wall_s"] / r["wall_s"] if r["wall_s"] > 0 else math.inf,
+            gp_s=r["gp_s"], md_s=r["md_s"], result=r))
+    out["rows"] = rows
+    return out
+
+
+def md_database(ctx, n_elements, seed, h_range=(6.0, 18.0), G_range=(-0.06, 0.06), density=0.8, T=1.1,
+                steps_eq=1000, steps_sample=2000, Lx=10.0, Lz=10.0):
+    """A training database from the library's MD: elements drawn uniformly over
+    the channel's (h, G) range; returns inputs (n x 2), flow rates, errors."""
+    rng = np.random.default_rng(seed)
+    h = rng.uniform(*h_range, n_elements)
+    G = rng.uniform(*G_range, n_elements)
+    els = [dict(h=float(h[k]), dpdx=float(G[k]), density=density, T=T, steps_eq=steps_eq,
+                steps_sample=steps_sample, Lx=Lx, Lz=Lz, g_ext=0.0, seed=int(seed), id=k)
+           for k in range(n_elements)]
+    res = ctx.micro_batch(els)
+    X = np.column_stack([h, G])
+    return X, np.array([r["q"] for r in res]), np.array([r["q_se"] for r in res])
+
+
+def learned_mean(ctx, X, y, sigma_n, epochs=2000, lr=3e-3, seed=1):
+    """Train the MLP prior mean on the database; the residual GP's sigma_f is
+    the network's holdout RMS error, floored at twice the noise level."""
+    net = native.MLP(ctx, seed=seed)
+    train, hold = net.train(X, y, epochs=epochs, lr=lr, eval_every=25)
+    resid = y - net.predict(X)
+    _, st = net.get()
+    rms_hold = math.sqrt(hold) * st[5] if hold == hold else float(np.sqrt(np.mean(resid ** 2)))
+    sf_res = max(rms_hold, 2.0 * sigma_n)
+    return net, sf_res, dict(train_loss=train, holdout_loss=hold, rms_holdout=rms_hold)
+
+
+def mlp_comparison(ctx, thresholds, n_steps, net, sf_res, sf_plain, reference_q=None, **params):
+    """MD calls and flow error of the plain-GP hybrid against the learned-mean
+    hybrid at matched thresholds."""
+    rows = []
+    for s in thresholds:
+        a = run_channel(ctx, s, n_steps, sf2=sf_plain ** 2, **params)
+        b = run_channel(ctx, s, n_steps, mlp=net, sf2=sf_res ** 2, **params)
+        row = dict(sigma_t=s, md_runs_plain=a["md_runs"], md_runs_mlp=b["md_runs"])
+        if reference_q is not None:
+            row["error_plain"] = error(a["qbar"], reference_q)
+            row["error_mlp"] = error(b["qbar"], reference_q)
+        rows.append(row)
+    return rows

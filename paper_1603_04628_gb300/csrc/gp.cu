@@ -156,38 +156,54 @@ __global__ void k_syrk_update(double* A, int Mp, int kb, int nt) {
   A[((size_t)ib * TB + r) * Mp + (size_t)jb * TB + c] -= s;
 }
 
-// Forward then backward substitution for one right-hand side (alpha).
+// alpha = C^-1 (y - mu) by blocked forward then backward substitution in one
+// block: for each tile row of TB, the block updates the TB right-hand sides
+// with the part already solved, then one warp solves the TB x TB triangle.
 __global__ void k_gp_alpha(const double* L, int M, int Mp, const double* y, const double* mu, double* alpha) {
   extern __shared__ double z[];
   const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5;
+  const int per = nt / TB;   // threads per row of a tile (a power of two <= 32)
   for (int i = tid; i < Mp; i += nt) z[i] = i < M ? y[i] - (mu ? mu[i] : 0.0) : 0.0;
   __syncthreads();
-  // forward: L z = r, one row at a time with a block-wide dot product
-  __shared__ double red[32];
-  for (int i = 0; i < Mp; ++i) {
+  const int nblk = Mp / TB;
+  // forward: L z = r
+  for (int kb = 0; kb < nblk; ++kb) {
+    const int r0 = kb * TB, row = r0 + tid / per, sub = tid % per;
     double s = 0.0;
-    for (int j = tid; j < i; j += nt) s += L[(size_t)i * Mp + j] * z[j];
-    s = warp_sum_d(s);
-    if ((tid & 31) == 0) red[tid >> 5] = s;
+    for (int j = sub; j < r0; j += per) s += L[(size_t)row * Mp + j] * z[j];
+    for (int o = per >> 1; o > 0; o >>= 1) s += __shfl_down_sync(kFullMask, s, o, per);
     __syncthreads();
-    if (tid == 0) {
-      double t = 0.0;
-      for (int w = 0; w < nt / 32; ++w) t += red[w];
-      z[i] = (z[i] - t) / L[(size_t)i * Mp + i];
+    if (sub == 0) z[row] -= s;
+    __syncthreads();
+    if (wid == 0) {
+      double x = z[r0 + lane];
+      for (int j = 0; j < TB; ++j) {
+        if (lane == j) x /= L[(size_t)(r0 + j) * Mp + r0 + j];
+        const double xs = __shfl_sync(kFullMask, x, j);
+        if (lane > j) x -= L[(size_t)(r0 + lane) * Mp + r0 + j] * xs;
+      }
+      z[r0 + lane] = x;
     }
     __syncthreads();
   }
-  // backward: L^T a = z
-  for (int i = Mp - 1; i >= 0; --i) {
+  // backward: L^T a = z, tile rows from the last
+  for (int kb = nblk - 1; kb >= 0; --kb) {
+    const int r0 = kb * TB, row = r0 + tid / per, sub = tid % per;
     double s = 0.0;
-    for (int j = i + 1 + tid; j < Mp; j += nt) s += L[(size_t)j * Mp + i] * z[j];
-    s = warp_sum_d(s);
-    if ((tid & 31) == 0) red[tid >> 5] = s;
+    for (int j = r0 + TB + sub; j < Mp; j += per) s += L[(size_t)j * Mp + row] * z[j];
+    for (int o = per >> 1; o > 0; o >>= 1) s += __shfl_down_sync(kFullMask, s, o, per);
     __syncthreads();
-    if (tid == 0) {
-      double t = 0.0;
-      for (int w = 0; w < nt / 32; ++w) t += red[w];
-      z[i] = (z[i] - t) / L[(size_t)i * Mp + i];
+    if (sub == 0) z[row] -= s;
+    __syncthreads();
+    if (wid == 0) {
+      double x = z[r0 + lane];
+      for (int j = TB - 1; j >= 0; --j) {
+        if (lane == j) x /= L[(size_t)(r0 + j) * Mp + r0 + j];
+        const double xs = __shfl_sync(kFullMask, x, j);
+        if (lane < j) x -= L[(size_t)(r0 + j) * Mp + r0 + lane] * xs;
+      }
+      z[r0 + lane] = x;
     }
     __syncthreads();
   }
@@ -341,6 +357,8 @@ static int gp_fit_impl(mdgp_gp* g, const double* X, const double* y, const doubl
       g->launches += 2;
     }
   }
+  if (sizeof(double) * Mp > 48 * 1024)
+    GK(cudaFuncSetAttribute(k_gp_alpha, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(double) * Mp)));
   k_gp_alpha<<<1, 256, sizeof(double) * Mp, s>>>(g->dL, M, Mp, dy, dmuX, g->dalpha);
   g->launches++;
   int status = 0;

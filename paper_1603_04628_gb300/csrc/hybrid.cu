@@ -165,12 +165,27 @@ int mdgp_hybrid_step(mdgp_hybrid* H, double sigma_t, mdgp_hybrid_stats* stats) {
   const double sn2 = sn2_for_step(H);
   std::vector<double> Xq((size_t)2 * N);
   for (int j = 0; j < N; ++j) { Xq[2 * j] = H->h[j]; Xq[2 * j + 1] = H->G[j]; }
-  // gate pass: variance on the inputs only, appending gated inputs in order
+  // gate pass: variance on the inputs only, appending gated inputs in order.
+  // sigma_t <= 0 sends every section to MD whatever the variance (the
+  // reference run), so no GP work is done then.
   const int64_t M0 = (int64_t)H->y.size();
   std::vector<double> Xv(H->X), yv((size_t)M0, 0.0), mv(H->mX);
   std::vector<int> md_idx;
   std::vector<double> mean((size_t)N), var((size_t)N);
   int j0 = 0;
+  if (!(sigma_t > 0.0)) {
+    for (int j = 0; j < N; ++j) {
+      md_idx.push_back(j);
+      H->sd[j] = NAN;
+      if (H->mean_fn) {
+        std::vector<double> mq;
+        int st2 = prior_mean(H, Xq.data() + 2 * j, 1, mq);
+        if (st2) return st2;
+        mv.push_back(mq[0]);
+      }
+    }
+    j0 = N;
+  }
   while (j0 < N) {
     const int64_t Mv = (int64_t)(Xv.size() / 2);
     int st = fit_predict(H, Xv, yv, mv, Mv, sn2, Xq.data() + 2 * j0, N - j0, mean.data() + j0, var.data() + j0);

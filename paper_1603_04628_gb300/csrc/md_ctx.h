@@ -25,6 +25,8 @@ struct mdgp_ctx {
   long long n_el = 0, steps = 0, n_atoms = 0;
   long long chunk = 256;  // steps per captured graph (rounded to the rebuild interval)
   long long rebuild_every = 1;
+  long long n_columns = 0;  // (x, y) cell columns over the batch
+  int stage_bytes = 0;      // dynamic shared memory of the staged list build
   long long graph_K = 0, graph_rem_K = 0;
   cudaGraphExec_t graph_full = nullptr, graph_rem = nullptr;
   long long launches = 0;              // kernels enqueued by the last launch (graph bodies: 2 per step)
@@ -32,11 +34,11 @@ struct mdgp_ctx {
   long long rebuilds = 0;
   mdgp::BatchDev B;
   mdgp::PhysDev P;
-  DevBuf d_el, d_aoff, d_coff, d_state, d_ints, d_cells, d_pos, d_pbuild, d_force, d_list, d_out, d_acc,
-      d_grp, d_status, d_results, d_step, d_flags;
+  DevBuf d_el, d_aoff, d_coff, d_koff, d_state, d_ints, d_cells, d_pos, d_pbuild, d_force, d_list, d_out, d_acc,
+      d_grp, d_status, d_results, d_step, d_flags, d_tz;
   std::vector<DevBuf*> all_bufs() {
-    return {&d_el, &d_aoff, &d_coff, &d_state, &d_ints, &d_cells, &d_pos, &d_pbuild, &d_force, &d_list,
-            &d_out, &d_acc, &d_grp, &d_status, &d_results, &d_step, &d_flags};
+    return {&d_el, &d_aoff, &d_coff, &d_koff, &d_state, &d_ints, &d_cells, &d_pos, &d_pbuild, &d_force, &d_list,
+            &d_out, &d_acc, &d_grp, &d_status, &d_results, &d_step, &d_flags, &d_tz};
   }
   void release_extra() {}
 };

@@ -98,7 +98,15 @@ int describe(const mdgp_md_params& p, const mdgp_element& el, ElemDev& E, std::s
   if (!(E.nc[0] >= 3) || !(E.nc[2] >= 3)) { *why = "Lx and Lz must be >= 3 (r_c + skin)"; return MDGP_E_ARG; }
   if (E.nc[1] < 1) E.nc[1] = 1;
   E.cs[0] = el.Lx / E.nc[0]; E.cs[1] = (yhi - ylo) / E.nc[1]; E.cs[2] = el.Lz / E.nc[2];
-  for (int d = 0; d < 3; ++d) { E.inv_cs[d] = 1.0 / E.cs[d]; E.csf[d] = (float)E.cs[d]; }
+  for (int d = 0; d < 3; ++d) {
+    E.inv_cs[d] = 1.0 / E.cs[d];
+    E.csf[d] = (float)E.cs[d];
+    E.cs_lo[d] = (float)(E.cs[d] - (double)E.csf[d]);
+    E.inv_csf[d] = (float)E.inv_cs[d];
+  }
+  E.g_kick = (float)(0.5 * p.dt / p.mass * E.g);
+  E.Tf = (float)E.T;
+  E.beta_sdf = (float)E.beta_sd;
   return MDGP_OK;
 }
 
@@ -131,10 +139,19 @@ PhysDev make_phys(const mdgp_md_params& p, int list_cap) {
   if (p.mode == 1) { P.active[2] = 0; P.uniform = 0; }
   P.mode = p.mode;
   P.wall_planes = p.wall_planes;
+  P.tau_T = p.tau_T;
   P.list_cap = list_cap;
   P.rc2f = (float)(p.rc * p.rc);
   P.rl2f = (float)P.rl2;
   P.half_skin2f = (float)(0.25 * p.skin * p.skin);
+  P.dtf = (float)p.dt;
+  P.hdt_mf = (float)P.hdt_m;
+  P.massf = (float)p.mass;
+  P.inv_mf = (float)P.inv_m;
+  P.k_tetherf = (float)p.k_tether;
+  P.gjf_af = (float)P.gjf_a;
+  P.gjf_bf = (float)P.gjf_b;
+  P.dt_tauf = p.tau_T > 0.0 ? (float)(p.dt / p.tau_T) : 0.0f;
   return P;
 }
 
@@ -160,28 +177,54 @@ int rebuild_interval(const mdgp_md_params& p, double Tmax) {
 static void enqueue_integrate(mdgp_ctx* ctx, int k, int mode, cudaGraphConditionalHandle h = 0,
                               int use_cond = 0) {
   const unsigned g = grid_for(ctx->B.n_atoms, 256);
-  if (ctx->precision == MDGP_PREC_FP32)
-    k_integrate<float, float4><<<g, 256, 0, ctx->stream>>>(ctx->B, ctx->P, k, mode, h, use_cond);
-  else
-    k_integrate<double, Pos64><<<g, 256, 0, ctx->stream>>>(ctx->B, ctx->P, k, mode, h, use_cond);
+  const bool frozen = ctx->params.mode == 1;
+  if (ctx->precision == MDGP_PREC_FP32) {
+    if (frozen) k_integrate_df<true><<<g, 256, 0, ctx->stream>>>(ctx->B, ctx->P, k, mode, h, use_cond);
+    else k_integrate_df<false><<<g, 256, 0, ctx->stream>>>(ctx->B, ctx->P, k, mode, h, use_cond);
+  } else {
+    if (frozen) k_integrate<double, Pos64, true><<<g, 256, 0, ctx->stream>>>(ctx->B, ctx->P, k, mode, h, use_cond);
+    else k_integrate<double, Pos64, false><<<g, 256, 0, ctx->stream>>>(ctx->B, ctx->P, k, mode, h, use_cond);
+  }
   ctx->launches++;
+}
+
+// Integration of one step: one fused launch, or for frozen-wall elements with
+// the Berendsen thermostat two launches (the thermostat needs the element's
+// sum of m v_z^2 between the half kick and the measurement).
+static void enqueue_step_integrate(mdgp_ctx* ctx, int k, bool stage1, cudaGraphConditionalHandle h = 0,
+                                   int use_cond = 0) {
+  if (ctx->params.mode == 1) {
+    enqueue_integrate(ctx, k, kFinish | kTzSum);
+    enqueue_integrate(ctx, k, kTzApply | (stage1 ? kStage1 : 0), h, use_cond);
+  } else {
+    enqueue_integrate(ctx, k, kFinish | (stage1 ? kStage1 : 0), h, use_cond);
+  }
 }
 
 // Neighbour-list rebuild: bin, per-element scan, permute into cell order,
 // copy back, build the lists (5 kernels on `s`).
 static void enqueue_rebuild(mdgp_ctx* ctx, cudaStream_t s) {
   const unsigned g = grid_for(ctx->B.n_atoms, 256);
-  k_bin<<<g, 256, 0, s>>>(ctx->B);
+  if (ctx->precision == MDGP_PREC_FP32) k_bin<true><<<g, 256, 0, s>>>(ctx->B);
+  else k_bin<false><<<g, 256, 0, s>>>(ctx->B);
   k_scan<<<(unsigned)ctx->n_el, 1024, 0, s>>>(ctx->B);
   const unsigned gb = grid_for(ctx->B.n_cells * 32, 128);
+  const unsigned gc = (unsigned)ctx->n_columns;
+  const unsigned gw = grid_for(ctx->B.n_cells, kBallotWarps);
+  const int variant = ctx->params.build_variant;
+  const size_t ballot_smem = sizeof(float4) * kBallotWarps * kBallotCap;
   if (ctx->precision == MDGP_PREC_FP32) {
     k_permute<float4><<<g, 256, 0, s>>>(ctx->B);
     k_copy_back<<<g, 256, 0, s>>>(ctx->B);
-    k_build<float4><<<gb, 128, 0, s>>>(ctx->B, ctx->P);
+    if (variant == 2) k_build_ballot<<<gw, kBallotWarps * 32, ballot_smem, s>>>(ctx->B, ctx->P);
+    else if (variant == 0) k_build_staged<float4><<<gc, 128, ctx->stage_bytes, s>>>(ctx->B, ctx->P, ctx->stage_bytes);
+    else k_build<float4><<<gb, 128, 0, s>>>(ctx->B, ctx->P);
   } else {
     k_permute<Pos64><<<g, 256, 0, s>>>(ctx->B);
     k_copy_back<<<g, 256, 0, s>>>(ctx->B);
-    k_build<Pos64><<<gb, 128, 0, s>>>(ctx->B, ctx->P);
+    if (variant == 2) k_build_ballot<<<gw, kBallotWarps * 32, ballot_smem, s>>>(ctx->B, ctx->P);
+    else if (variant == 0) k_build_staged<Pos64><<<gc, 128, ctx->stage_bytes, s>>>(ctx->B, ctx->P, ctx->stage_bytes);
+    else k_build<Pos64><<<gb, 128, 0, s>>>(ctx->B, ctx->P);
   }
 }
 
@@ -295,7 +338,7 @@ static int capture_steps(mdgp_ctx* ctx, long long nsteps, cudaGraphExec_t* out) 
     CK(cudaStreamGetCaptureInfo(ctx->stream, &cs, nullptr, &cg, &deps, &edges, &ndeps));
     cudaGraphConditionalHandle h;
     CK(cudaGraphConditionalHandleCreate(&h, cg, 0, cudaGraphCondAssignDefault));
-    enqueue_integrate(ctx, (int)k, kFinish | kStage1, h, 1);
+    enqueue_step_integrate(ctx, (int)k, true, h, 1);
     CK(cudaStreamGetCaptureInfo(ctx->stream, &cs, nullptr, &cg, &deps, &edges, &ndeps));
     cudaGraphNodeParams cp = {};
     cp.type = cudaGraphNodeTypeConditional;
@@ -324,13 +367,17 @@ static int capture_steps(mdgp_ctx* ctx, long long nsteps, cudaGraphExec_t* out) 
 static int plan_impl(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int list_cap_override) {
   ctx->planned = false;
   drop_graphs(ctx);
-  if (ctx->params.mode != 0) {
-    std::snprintf(ctx->err, sizeof(ctx->err), "only mode 0 (tethered walls) runs on the GPU");
+  if (ctx->params.mode != 0 && ctx->params.mode != 1) {
+    std::snprintf(ctx->err, sizeof(ctx->err), "mode must be 0 (tethered walls) or 1 (frozen walls)");
+    return MDGP_E_ARG;
+  }
+  if (ctx->params.mode == 1 && !(ctx->params.tau_T > 0)) {
+    std::snprintf(ctx->err, sizeof(ctx->err), "mode 1 needs tau_T > 0");
     return MDGP_E_ARG;
   }
   std::vector<ElemDev> Es((size_t)n);
-  std::vector<long long> aoff((size_t)n + 1), coff((size_t)n + 1);
-  long long atoms = 0, cells = 0;
+  std::vector<long long> aoff((size_t)n + 1), coff((size_t)n + 1), koff((size_t)n + 1);
+  long long atoms = 0, cells = 0, columns = 0;
   const long long S = el[0].steps_eq + el[0].steps_sample;
   double Tmax = 0.0;
   for (int64_t i = 0; i < n; ++i) {
@@ -349,6 +396,8 @@ static int plan_impl(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int list_
     Es[i].cell0 = cells;
     aoff[i] = atoms;
     coff[i] = cells;
+    koff[i] = columns;
+    columns += (long long)Es[i].nc[0] * Es[i].nc[1];
     atoms += (long long)Es[i].nf + Es[i].nw;
     cells += (long long)Es[i].nc[0] * Es[i].nc[1] * Es[i].nc[2];
     if ((long long)Es[i].nf + Es[i].nw >= (1LL << 26)) {
@@ -358,6 +407,7 @@ static int plan_impl(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int list_
   }
   aoff[n] = atoms;
   coff[n] = cells;
+  koff[n] = columns;
   if (atoms >= (1LL << 31) - 1) {
     std::snprintf(ctx->err, sizeof(ctx->err), "batch too large (2^31 atoms max)");
     return MDGP_E_ARG;
@@ -372,6 +422,7 @@ static int plan_impl(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int list_
   if ((st = ensure(ctx, ctx->d_el, sizeof(ElemDev) * n))) return st;
   if ((st = ensure(ctx, ctx->d_aoff, sizeof(long long) * (n + 1)))) return st;
   if ((st = ensure(ctx, ctx->d_coff, sizeof(long long) * (n + 1)))) return st;
+  if ((st = ensure(ctx, ctx->d_koff, sizeof(long long) * (n + 1)))) return st;
   if ((st = ensure(ctx, ctx->d_state, sizeof(double) * 18 * N))) return st;
   if ((st = ensure(ctx, ctx->d_ints, sizeof(int) * 8 * N))) return st;
   if ((st = ensure(ctx, ctx->d_cells, sizeof(int) * 4 * C))) return st;
@@ -386,15 +437,18 @@ static int plan_impl(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int list_
   if ((st = ensure(ctx, ctx->d_results, sizeof(mdgp_result) * n))) return st;
   if ((st = ensure(ctx, ctx->d_step, sizeof(long long)))) return st;
   if ((st = ensure(ctx, ctx->d_flags, sizeof(int) * 4))) return st;
+  if ((st = ensure(ctx, ctx->d_tz, sizeof(double) * 2 * n))) return st;
   CK(cudaMemcpyAsync(ctx->d_el.ptr, Es.data(), sizeof(ElemDev) * n, cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(ctx->d_aoff.ptr, aoff.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(ctx->d_coff.ptr, coff.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->d_koff.ptr, koff.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, ctx->stream));
 
   BatchDev& B = ctx->B;
   std::memset(&B, 0, sizeof(B));
   B.el = (const ElemDev*)ctx->d_el.ptr;
   B.atom_off = (const long long*)ctx->d_aoff.ptr;
   B.cell_off = (const long long*)ctx->d_coff.ptr;
+  B.col_off = (const long long*)ctx->d_koff.ptr;
   B.n_el = (int)n;
   B.list_cap = list_cap;
   B.n_atoms = atoms;
@@ -418,7 +472,15 @@ static int plan_impl(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int list_
   B.status = (int*)ctx->d_status.ptr;
   B.step_base = (const long long*)ctx->d_step.ptr;
   B.flags = (int*)ctx->d_flags.ptr;
+  B.tz = (double*)ctx->d_tz.ptr;
   ctx->P = make_phys(ctx->params, list_cap);
+  ctx->n_columns = columns;
+  // staging buffer of the column build: 64 KB (FP32) / 112 KB (FP64) of positions
+  ctx->stage_bytes = ctx->precision == MDGP_PREC_FP32 ? 64 * 1024 : 112 * 1024;
+  if (ctx->precision == MDGP_PREC_FP32)
+    CK(cudaFuncSetAttribute(k_build_staged<float4>, cudaFuncAttributeMaxDynamicSharedMemorySize, ctx->stage_bytes));
+  else
+    CK(cudaFuncSetAttribute(k_build_staged<Pos64>, cudaFuncAttributeMaxDynamicSharedMemorySize, ctx->stage_bytes));
   ctx->n_el = n;
   ctx->steps = S;
   ctx->n_atoms = atoms;
@@ -449,7 +511,7 @@ static int plan_impl(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int list_
 }
 
 // kernels in one chunk graph, rebuild bodies not counted
-static long long graph_launches(long long nsteps) { return 2 * nsteps + 1; }
+static long long graph_launches(long long nsteps, int mode) { return (mode == 1 ? 3 : 2) * nsteps + 1; }
 
 // Reset the accumulators and build the elements (lattice, anchors,
 // Maxwell-Boltzmann velocities).
@@ -461,8 +523,15 @@ static int start_batch(mdgp_ctx* ctx) {
   CK(cudaMemsetAsync(ctx->B.ccount, 0, sizeof(int) * ctx->B.n_cells, ctx->stream));
   CK(cudaMemsetAsync(ctx->d_step.ptr, 0, sizeof(long long), ctx->stream));
   CK(cudaMemsetAsync(ctx->B.flags, 0, sizeof(int) * 4, ctx->stream));
-  k_init_atoms<<<grid_for(ctx->B.n_atoms, 256), 256, 0, ctx->stream>>>(ctx->B, ctx->P);
-  k_init_fix<<<grid_for(ctx->B.n_atoms, 256), 256, 0, ctx->stream>>>(ctx->B, ctx->P);
+  CK(cudaMemsetAsync(ctx->B.tz, 0, sizeof(double) * 2 * n, ctx->stream));
+  const unsigned ga = grid_for(ctx->B.n_atoms, 256);
+  if (ctx->precision == MDGP_PREC_FP32) {
+    k_init_atoms<true><<<ga, 256, 0, ctx->stream>>>(ctx->B, ctx->P);
+    k_init_fix<true><<<ga, 256, 0, ctx->stream>>>(ctx->B, ctx->P);
+  } else {
+    k_init_atoms<false><<<ga, 256, 0, ctx->stream>>>(ctx->B, ctx->P);
+    k_init_fix<false><<<ga, 256, 0, ctx->stream>>>(ctx->B, ctx->P);
+  }
   ctx->launches += 2;
   return MDGP_OK;
 }
@@ -481,15 +550,15 @@ static int launch_impl(mdgp_ctx* ctx) {
       const long long full = S / ctx->graph_K;
       for (long long r = 0; r < full; ++r) {
         CK(cudaGraphLaunch(ctx->graph_full, ctx->stream));
-        ctx->launches += graph_launches(ctx->graph_K);
+        ctx->launches += graph_launches(ctx->graph_K, ctx->params.mode);
       }
     }
     if (ctx->graph_rem_K) {
       CK(cudaGraphLaunch(ctx->graph_rem, ctx->stream));
-      ctx->launches += graph_launches(ctx->graph_rem_K);
+      ctx->launches += graph_launches(ctx->graph_rem_K, ctx->params.mode);
     }
     // finish the last step (s = S), then the energy at the final positions
-    enqueue_integrate(ctx, 0, kFinish);
+    enqueue_step_integrate(ctx, 0, false);
     enqueue_force(ctx, true);
   }
   enqueue_energy(ctx, kAccE1);
@@ -546,6 +615,7 @@ int mdgp_md_params_default(mdgp_md_params* out) {
   out->list_capacity = 128;
   out->skin = 0.4;
   out->rebuild_every = 0;
+  out->build_variant = 2;
   return MDGP_OK;
 }
 
@@ -585,7 +655,7 @@ int mdgp_set_md_params(mdgp_ctx* ctx, const mdgp_md_params* p) {
   if (!ctx || !p) return MDGP_E_ARG;
   if (!(p->dt > 0) || !(p->rc > 0) || p->n_blocks < 1 || p->wall_planes < 1 || !(p->mass > 0) ||
       !(p->wall_density > 0) || p->gamma_wall < 0 || p->list_capacity < 0 || !(p->skin >= 0) ||
-      p->rebuild_every < 0)
+      p->rebuild_every < 0 || p->build_variant < 0 || p->build_variant > 2)
     return MDGP_E_ARG;
   ctx->params = *p;
   ctx->planned = false;
@@ -678,9 +748,19 @@ int mdgp_md_forces(mdgp_ctx* ctx, const mdgp_element* el, const double* x, int64
   if ((st = start_batch(ctx))) return st;
   // replace the lattice positions by the caller's (absolute, original order;
   // the freshly built element is still in original order)
+  // (double-float state with FP32 pair forces: each value as the float pair
+  // hi = fl(x), lo = fl(x - hi) in the same 8 bytes)
   std::vector<double> soa((size_t)3 * n_atoms);
   for (int64_t i = 0; i < n_atoms; ++i)
-    for (int d = 0; d < 3; ++d) soa[(size_t)d * n_atoms + i] = x[3 * i + d];
+    for (int d = 0; d < 3; ++d) {
+      const double v = x[3 * i + d];
+      if (ctx->precision == MDGP_PREC_FP32) {
+        const float pair[2] = {(float)v, (float)(v - (double)(float)v)};
+        std::memcpy(&soa[(size_t)d * n_atoms + i], pair, sizeof(pair));
+      } else {
+        soa[(size_t)d * n_atoms + i] = v;
+      }
+    }
   for (int d = 0; d < 3; ++d)
     CK(cudaMemcpyAsync(ctx->B.st[d], soa.data() + (size_t)d * n_atoms, sizeof(double) * n_atoms,
                        cudaMemcpyHostToDevice, ctx->stream));
@@ -712,7 +792,7 @@ int mdgp_micro_profile(mdgp_ctx* ctx, int64_t steps, double* ms) {
   CK(cudaEventRecord(ev[0], ctx->stream));
   for (int64_t k = 0; k < steps; ++k) {
     // the step counter stays 0: launch k works on step k
-    enqueue_integrate(ctx, (int)k, kFinish | kStage1);
+    enqueue_step_integrate(ctx, (int)k, true);
     CK(cudaEventRecord(ev[3 * k + 1], ctx->stream));
     if (k % ctx->rebuild_every == 0) enqueue_rebuild(ctx);
     CK(cudaEventRecord(ev[3 * k + 2], ctx->stream));
@@ -739,6 +819,48 @@ int mdgp_micro_profile(mdgp_ctx* ctx, int64_t steps, double* ms) {
   ms[4] = (double)ctx->B.n_cells;
   ms[5] = (double)ctx->rebuild_every;
   return MDGP_OK;
+}
+
+int mdgp_autotune(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int64_t probe_steps, mdgp_md_params* best,
+                  double* best_rate) {
+  if (!ctx || !el || n < 1 || probe_steps < 1) return MDGP_E_ARG;
+  cudaSetDevice(ctx->device);
+  const mdgp_md_params base = ctx->params;
+  std::vector<mdgp_element> probe(el, el + n);
+  for (auto& e : probe) { e.steps_eq = probe_steps; e.steps_sample = 0; }
+  const double skins[] = {0.3, 0.4, 0.5, 0.6};
+  double top = -1.0;
+  mdgp_md_params chosen = base;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  for (double skin : skins) {
+    for (int variant = 0; variant <= 2; ++variant) {
+      mdgp_md_params trial = base;
+      trial.skin = skin;
+      trial.build_variant = variant;
+      ctx->params = trial;
+      int st = plan_impl(ctx, probe.data(), n, 0);
+      if (st == MDGP_E_ARG) continue;       // geometry too small for this skin
+      if (st) { ctx->params = base; return st; }
+      if ((st = launch_impl(ctx))) { ctx->params = base; return st; }   // warm-up
+      CK(cudaEventRecord(e0, ctx->stream));
+      if ((st = launch_impl(ctx))) { ctx->params = base; return st; }
+      CK(cudaEventRecord(e1, ctx->stream));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      const double rate = (double)ctx->n_atoms * (double)probe_steps / (ms * 1e-3);
+      if (rate > top) { top = rate; chosen = trial; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->params = top > 0 ? chosen : base;
+  ctx->planned = false;
+  if (best) *best = ctx->params;
+  if (best_rate) *best_rate = top;
+  return top > 0 ? MDGP_OK : MDGP_E_ARG;
 }
 
 const char* mdgp_last_error(const mdgp_ctx* ctx) { return ctx ? ctx->err : "null context"; }

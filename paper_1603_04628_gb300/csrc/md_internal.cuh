@@ -3,7 +3,9 @@
 // Layout in HBM (one flattened batch, elements back to back; element e owns
 // atoms [atom0, atom0 + nf + nw) and cells [cell0, cell0 + ncx*ncy*ncz)):
 //   atoms  kept in cell order (re-sorted at every neighbour-list rebuild);
-//          FP64 SoA: position as an offset from the centre of the atom's
+//          SoA, FP64 with FP64 pair forces and double-float (two FP32 words,
+//          hi + lo, ~44-bit significand) with FP32 pair forces, in the same
+//          8 bytes per value: position as an offset from the centre of the atom's
 //          reference cell (the cell it was binned into at the last rebuild),
 //          velocity, and for wall atoms the tether anchor in the same frame;
 //          int32 original index (element-local, fluid first) and reference
@@ -65,7 +67,10 @@ struct ElemDev {
   int id;
   int nb;              // blocks actually used
   float csf[3];        // cell sizes as float
-  float pad;
+  float cs_lo[3];      // cs - csf: the cell sizes as double-float numbers
+  float inv_csf[3];
+  float g_kick;        // dt/(2m) g as float (double-float state)
+  float Tf, beta_sdf;
 };
 
 struct PhysDev {
@@ -78,15 +83,19 @@ struct PhysDev {
   int uniform;                         // all three pair types (1, 1) and active
   int mode;
   int wall_planes;
+  double tau_T;                        // Berendsen time constant (mode 1)
   int list_cap;
   float rc2f, rl2f, half_skin2f;
   float epsf[3], sig2f[3];
+  // float copies for the double-float state updates (pair-force precision FP32)
+  float dtf, hdt_mf, massf, inv_mf, k_tetherf, gjf_af, gjf_bf, dt_tauf;
 };
 
 struct BatchDev {
   const ElemDev* el;
   const long long* atom_off;   // [n_el + 1]
   const long long* cell_off;   // [n_el + 1]
+  const long long* col_off;    // [n_el + 1] prefix of the (x, y) cell columns
   int n_el;
   int list_cap;
   long long n_atoms, n_cells;
@@ -109,8 +118,14 @@ struct BatchDev {
   const long long* step_base;     // device step counter (advanced per graph chunk)
   double* out;                    // export scratch [6 * n_atoms] (original order)
   int* flags;                     // [0] rebuild needed, [1] blocks done, [2] rebuilds run
+  double* tz;                     // [2 * n_el] per-element sum of m v_z^2 (two step-parity slots)
 };
 
-enum : int { kFinish = 1, kStage1 = 2 };
+// integration kernel phases: kFinish = second half kick (+ measurement unless
+// kTzSum), kStage1 = first half kick + drift.  Frozen-wall elements with the
+// Berendsen thermostat on v_z split a step over two launches: kFinish | kTzSum
+// (half kick, per-element sum of m v_z^2), then kTzApply | kStage1 (scale v_z,
+// measure, next half kick and drift).
+enum : int { kFinish = 1, kStage1 = 2, kTzSum = 4, kTzApply = 8 };
 
 }  // namespace mdgp

@@ -27,6 +27,19 @@ __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
 // Three standard normals by Box-Muller on the block's two pairs of uniforms,
 // in double (FP64 path) or in single precision from the top 24 bits (FP32
 // path: the noise enters the FP64 update as a small term).
+__device__ __forceinline__ void normals3f(uint32_t atom, uint32_t step, uint32_t elem, uint32_t stream,
+                                          unsigned long long seed, float& n0, float& n1, float& n2) {
+  const uint4 r = philox10(make_uint4(atom, step, elem, stream), (uint32_t)seed, (uint32_t)(seed >> 32));
+  const float inv24 = 5.9604644775390625e-8f;  // 2^-24
+  const float u1 = ((float)(r.x >> 8) + 0.5f) * inv24, u2 = ((float)(r.y >> 8) + 0.5f) * inv24;
+  const float u3 = ((float)(r.z >> 8) + 0.5f) * inv24, u4 = ((float)(r.w >> 8) + 0.5f) * inv24;
+  const float rad1 = sqrtf(-2.0f * logf(u1)), rad2 = sqrtf(-2.0f * logf(u3));
+  float s1, c1, s2, c2;
+  sincospif(2.0f * u2, &s1, &c1);
+  sincospif(2.0f * u4, &s2, &c2);
+  n0 = rad1 * c1; n1 = rad1 * s1; n2 = rad2 * c2;
+}
+
 template <typename T>
 __device__ __forceinline__ void normals3(uint32_t atom, uint32_t step, uint32_t elem, uint32_t stream,
                                          unsigned long long seed, double& n0, double& n1, double& n2) {
@@ -41,14 +54,9 @@ __device__ __forceinline__ void normals3(uint32_t atom, uint32_t step, uint32_t 
     sincospi(2.0 * u4, &s2, &c2);
     n0 = rad1 * c1; n1 = rad1 * s1; n2 = rad2 * c2;
   } else {
-    const float inv24 = 5.9604644775390625e-8f;  // 2^-24
-    const float u1 = ((float)(r.x >> 8) + 0.5f) * inv24, u2 = ((float)(r.y >> 8) + 0.5f) * inv24;
-    const float u3 = ((float)(r.z >> 8) + 0.5f) * inv24, u4 = ((float)(r.w >> 8) + 0.5f) * inv24;
-    const float rad1 = sqrtf(-2.0f * logf(u1)), rad2 = sqrtf(-2.0f * logf(u3));
-    float s1, c1, s2, c2;
-    sincospif(2.0f * u2, &s1, &c1);
-    sincospif(2.0f * u4, &s2, &c2);
-    n0 = (double)(rad1 * c1); n1 = (double)(rad1 * s1); n2 = (double)(rad2 * c2);
+    float a, b, c;
+    normals3f(atom, step, elem, stream, seed, a, b, c);
+    n0 = (double)a; n1 = (double)b; n2 = (double)c;
   }
 }
 
@@ -79,6 +87,58 @@ __device__ __forceinline__ void seg_add(int key, const double (&val)[NV], DstFn 
   }
 }
 
+// Block-level segmented reduction for 256-thread blocks: every thread puts
+// (key, NV values) into shared memory.  When the whole block shares one key
+// (the usual case: atoms of one element are contiguous) a shared-memory tree
+// adds the values with 255 FP64 adds per value and one atomicAdd; otherwise
+// 8 threads each scan 32 entries and add each run of equal keys.  Keys < 0
+// are skipped.  All threads of the block must call it.
+template <int NV, typename DstFn>
+__device__ __forceinline__ void block_seg_add(int key, const double (&val)[NV], DstFn dst) {
+  __shared__ int skey[256];
+  __shared__ double sval[NV][256];
+  const int t = threadIdx.x;
+  skey[t] = key;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) sval[i][t] = val[i];
+  __syncthreads();
+  const int k0 = skey[0];
+  if (__syncthreads_and(key == k0)) {
+    if (k0 < 0) return;
+    for (int h = 128; h > 0; h >>= 1) {
+      if (t < h)
+#pragma unroll
+        for (int i = 0; i < NV; ++i) sval[i][t] += sval[i][t + h];
+      __syncthreads();
+    }
+    if (t < NV) atomicAdd(dst(k0, t), sval[t][0]);
+    return;
+  }
+  if (t < 8) {
+    int cur = -1;
+    double acc[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+    for (int r = t * 32; r < t * 32 + 32; ++r) {
+      const int k = skey[r];
+      if (k != cur) {
+        if (cur >= 0)
+#pragma unroll
+          for (int i = 0; i < NV; ++i) atomicAdd(dst(cur, i), acc[i]);
+        cur = k;
+#pragma unroll
+        for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+      }
+      if (k >= 0)
+#pragma unroll
+        for (int i = 0; i < NV; ++i) acc[i] += sval[i][r];
+    }
+    if (cur >= 0)
+#pragma unroll
+      for (int i = 0; i < NV; ++i) atomicAdd(dst(cur, i), acc[i]);
+  }
+}
+
 __device__ __forceinline__ double wrap_periodic(double x, double L) {
   if (x >= L) x -= L;
   if (x < 0.0) x += L;
@@ -103,10 +163,66 @@ __device__ __forceinline__ void cell_center(const ElemDev& E, long long c, doubl
   cz = ((double)iz + 0.5) * E.cs[2];
 }
 
+// ---------------------------------------------------------------------------
+// Double-float state (pair forces in FP32).  A value is hi + lo with
+// hi = fl(hi + lo).  Sums use Knuth's TwoSum of the high parts, products the
+// exact FMA product (Dekker), so every update runs on the FP32 pipes (FP64
+// issues at 1/64 of the FP32 rate on this part) and keeps about 44
+// significant bits.  Stored as float2 in the 8-byte state slots.
+// ---------------------------------------------------------------------------
+struct dfl {
+  float hi, lo;
+};
+
+__device__ __forceinline__ dfl df_norm(float s, float e) {   // Fast2Sum, |s| >= |e|
+  const float h = __fadd_rn(s, e);
+  return {h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ dfl df_add(dfl a, float b) {
+  const float s = __fadd_rn(a.hi, b), bb = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b, bb)), a.lo);
+  return df_norm(s, e);
+}
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+  const float s = __fadd_rn(a.hi, b.hi), bb = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb)), __fadd_rn(a.lo, b.lo));
+  return df_norm(s, e);
+}
+__device__ __forceinline__ dfl df_mul(float c, dfl a) {
+  const float p = __fmul_rn(c, a.hi);
+  const float e = __fmaf_rn(c, a.lo, __fmaf_rn(c, a.hi, -p));
+  return df_norm(p, e);
+}
+// a - b rounded to float (the two are close: tether stretch, displacement)
+__device__ __forceinline__ float df_diff(dfl a, dfl b) { return __fsub_rn(a.hi, b.hi) + __fsub_rn(a.lo, b.lo); }
+__device__ __forceinline__ dfl df_from(double d) {
+  const float h = (float)d;
+  return {h, (float)(d - (double)h)};
+}
+__device__ __forceinline__ double df_to(dfl a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ dfl df_ld(const double* p, long long i) {
+  const float2 v = reinterpret_cast<const float2*>(p)[i];
+  return {v.x, v.y};
+}
+__device__ __forceinline__ void df_st(double* p, long long i, dfl a) {
+  reinterpret_cast<float2*>(p)[i] = make_float2(a.hi, a.lo);
+}
+
+// One state value as a double, in either representation.
+template <bool DF>
+__device__ __forceinline__ double st_get(const double* p, long long i) {
+  if constexpr (DF) return df_to(df_ld(p, i)); else return p[i];
+}
+template <bool DF>
+__device__ __forceinline__ void st_put(double* p, long long i, double v) {
+  if constexpr (DF) df_st(p, i, df_from(v)); else p[i] = v;
+}
+
 // Absolute position of atom i (x and z wrapped into the periodic box).
+template <bool DF>
 __device__ __forceinline__ void abs_position(const BatchDev& B, const ElemDev& E, long long i, double& x,
                                              double& y, double& z) {
-  x = B.st[0][i]; y = B.st[1][i]; z = B.st[2][i];
+  x = st_get<DF>(B.st[0], i); y = st_get<DF>(B.st[1], i); z = st_get<DF>(B.st[2], i);
   const int c = B.cell[i];
   if (c >= 0) {
     double cx, cy, cz;
@@ -147,6 +263,7 @@ __global__ void k_fill_maps(BatchDev B) {
 // (paper: "fluid atoms in a lattice, with zero mean velocity").  Positions are
 // written absolute (reference cell -1) until the first rebuild.
 // ---------------------------------------------------------------------------
+template <bool DF>
 __global__ void k_init_atoms(BatchDev B, PhysDev P) {
   const long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   int key = -1;
@@ -188,14 +305,14 @@ __global__ void k_init_atoms(BatchDev B, PhysDev P) {
       py = wall == 0 ? -(double)k * E.wdy : E.h + (double)k * E.wdy;
       pz = ((double)j + oz) * E.waz;
     }
-    B.st[0][a] = px; B.st[1][a] = py; B.st[2][a] = pz;
-    B.st[6][a] = px; B.st[7][a] = py; B.st[8][a] = pz;
+    st_put<DF>(B.st[0], a, px); st_put<DF>(B.st[1], a, py); st_put<DF>(B.st[2], a, pz);
+    st_put<DF>(B.st[6], a, px); st_put<DF>(B.st[7], a, py); st_put<DF>(B.st[8], a, pz);
     B.orig[a] = (int)l;
     B.cell[a] = -1;
     double n0, n1, n2;
     normals3<double>((uint32_t)l, 0u, (uint32_t)E.id, 0u, E.seed, n0, n1, n2);
     const double vx = E.vsd * n0, vy = E.vsd * n1, vz = E.vsd * n2;
-    B.st[3][a] = vx; B.st[4][a] = vy; B.st[5][a] = vz;
+    st_put<DF>(B.st[3], a, vx); st_put<DF>(B.st[4], a, vy); st_put<DF>(B.st[5], a, vz);
     key = 2 * e + group;
     val[0] = vx; val[1] = vy; val[2] = vz; val[3] = vx * vx + vy * vy + vz * vz;
   }
@@ -204,6 +321,7 @@ __global__ void k_init_atoms(BatchDev B, PhysDev P) {
 
 // Remove each group's mean velocity, then rescale it to exactly T with
 // 3 (N_g - 1) degrees of freedom.
+template <bool DF>
 __global__ void k_init_fix(BatchDev B, PhysDev P) {
   const long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (a >= B.n_atoms) return;
@@ -213,31 +331,53 @@ __global__ void k_init_fix(BatchDev B, PhysDev P) {
   const double cnt = group == 0 ? (double)E.nf : (double)E.nw;
   const double* g = B.grp + (size_t)(2 * e + group) * kGrpStride;
   const double mx = g[0] / cnt, my = g[1] / cnt, mz = g[2] / cnt;
-  double vx = B.st[3][a] - mx, vy = B.st[4][a] - my, vz = B.st[5][a] - mz;
+  double vx = st_get<DF>(B.st[3], a) - mx, vy = st_get<DF>(B.st[4], a) - my, vz = st_get<DF>(B.st[5], a) - mz;
   const double ke2 = P.mass * (g[3] - cnt * (mx * mx + my * my + mz * mz));
-  if (cnt > 1.0 && ke2 > 0.0) {
+  if (group == 1 && P.mode == 1) {       // frozen walls do not move
+    vx = vy = vz = 0.0;
+  } else if (cnt > 1.0 && ke2 > 0.0) {
     const double s = sqrt(E.T / (ke2 / (3.0 * (cnt - 1.0))));
     vx *= s; vy *= s; vz *= s;
   }
-  B.st[3][a] = vx; B.st[4][a] = vy; B.st[5][a] = vz;
+  st_put<DF>(B.st[3], a, vx); st_put<DF>(B.st[4], a, vy); st_put<DF>(B.st[5], a, vz);
 }
 
 // ---------------------------------------------------------------------------
 // Neighbour-list rebuild, step 1: bin every atom into its cell (counting
 // sort histogram by atomics; x and z periodic, y clamped to the edge cells).
 // ---------------------------------------------------------------------------
+// With the double-float state an atom already in a reference cell is binned
+// from its offset: the new cell is the reference cell plus
+// floor(offset / cs + 1/2) per axis (x, z wrapped, y clamped), in FP32.
+template <bool DF>
 __global__ void __launch_bounds__(256) k_bin(BatchDev B) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i == 0) atomicAdd(&B.flags[2], 1);
   if (i >= B.n_atoms) return;
   const ElemDev& E = B.el[B.atom_el[i]];
-  double x, y, z;
-  abs_position(B, E, i, x, y, z);
-  int ix = (int)(x * E.inv_cs[0]), iz = (int)(z * E.inv_cs[2]);
-  const double yr = (y - E.ylo) * E.inv_cs[1];
-  const int iy = yr < 0.0 ? 0 : (yr >= (double)E.nc[1] ? E.nc[1] - 1 : (int)yr);
-  ix = ix < 0 ? 0 : (ix >= E.nc[0] ? E.nc[0] - 1 : ix);
-  iz = iz < 0 ? 0 : (iz >= E.nc[2] ? E.nc[2] - 1 : iz);
+  int ix, iy, iz;
+  const int c0 = B.cell[i];
+  if (DF && c0 >= 0) {
+    int rx, ry, rz;
+    cell_coords(E, c0, rx, ry, rz);
+    const float ox = df_ld(B.st[0], i).hi, oy = df_ld(B.st[1], i).hi, oz = df_ld(B.st[2], i).hi;
+    ix = rx + (int)floorf(fmaf(ox, E.inv_csf[0], 0.5f));
+    iy = ry + (int)floorf(fmaf(oy, E.inv_csf[1], 0.5f));
+    iz = rz + (int)floorf(fmaf(oz, E.inv_csf[2], 0.5f));
+    ix = ix < 0 ? ix + E.nc[0] : (ix >= E.nc[0] ? ix - E.nc[0] : ix);
+    iz = iz < 0 ? iz + E.nc[2] : (iz >= E.nc[2] ? iz - E.nc[2] : iz);
+    ix = ix < 0 ? 0 : (ix >= E.nc[0] ? E.nc[0] - 1 : ix);
+    iz = iz < 0 ? 0 : (iz >= E.nc[2] ? E.nc[2] - 1 : iz);
+    iy = iy < 0 ? 0 : (iy >= E.nc[1] ? E.nc[1] - 1 : iy);
+  } else {
+    double x, y, z;
+    abs_position<DF>(B, E, i, x, y, z);
+    ix = (int)(x * E.inv_cs[0]); iz = (int)(z * E.inv_cs[2]);
+    const double yr = (y - E.ylo) * E.inv_cs[1];
+    iy = yr < 0.0 ? 0 : (yr >= (double)E.nc[1] ? E.nc[1] - 1 : (int)yr);
+    ix = ix < 0 ? 0 : (ix >= E.nc[0] ? E.nc[0] - 1 : ix);
+    iz = iz < 0 ? 0 : (iz >= E.nc[2] ? E.nc[2] - 1 : iz);
+  }
   const long long c = E.cell0 + ((long long)ix * E.nc[1] + iy) * E.nc[2] + iz;
   B.newcell[i] = (int)c;
   B.slot[i] = atomicAdd(&B.ccount[c], 1);
@@ -289,45 +429,75 @@ __global__ void __launch_bounds__(1024) k_scan(BatchDev B) {
 
 // Step 3: move every atom to its cell-ordered slot; positions become offsets
 // from the new reference cell's centre, anchors likewise (minimum image).
+// With the double-float state an atom that had a reference cell is rebased
+// by the cell step between the two centres (-delta * cs per axis, delta
+// wrapped to the nearest image in x and z), in FP32 arithmetic.
 template <typename PT>
 __global__ void __launch_bounds__(256) k_permute(BatchDev B) {
+  constexpr bool DF = sizeof(PT) == 16;
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= B.n_atoms) return;
   const ElemDev& E = B.el[B.atom_el[i]];
   const int c = B.newcell[i];
   const long long dst = (long long)B.cstart[c] + B.slot[i];
-  double x, y, z;
-  abs_position(B, E, i, x, y, z);
-  double cx, cy, cz;
-  cell_center(E, c, cx, cy, cz);
-  const double ox = x - cx, oy = y - cy, oz = z - cz;
   const int l = B.orig[i];
   const bool wall = l >= E.nf;
-  double ax = 0.0, ay = 0.0, az = 0.0;
-  if (wall) {
-    ax = B.st[6][i]; ay = B.st[7][i]; az = B.st[8][i];
-    const int c0 = B.cell[i];
+  const int c0 = B.cell[i];
+  float fx, fy, fz;   // the new offsets as float (pair-force input)
+  if constexpr (DF) {
     if (c0 >= 0) {
-      double px, py, pz;
-      cell_center(E, c0, px, py, pz);
-      ax += px; ay += py; az += pz;
+      int rx, ry, rz, jx, jy, jz;
+      cell_coords(E, c0, rx, ry, rz);
+      cell_coords(E, c, jx, jy, jz);
+      int dx = jx - rx, dz = jz - rz;
+      const int dy = jy - ry;
+      if (2 * dx > E.nc[0]) dx -= E.nc[0]; else if (2 * dx < -E.nc[0]) dx += E.nc[0];
+      if (2 * dz > E.nc[2]) dz -= E.nc[2]; else if (2 * dz < -E.nc[2]) dz += E.nc[2];
+      const dfl sx = df_mul(-(float)dx, dfl{E.csf[0], E.cs_lo[0]});
+      const dfl sy = df_mul(-(float)dy, dfl{E.csf[1], E.cs_lo[1]});
+      const dfl sz = df_mul(-(float)dz, dfl{E.csf[2], E.cs_lo[2]});
+      const dfl ox = df_add(df_ld(B.st[0], i), sx), oy = df_add(df_ld(B.st[1], i), sy),
+                oz = df_add(df_ld(B.st[2], i), sz);
+      df_st(B.st2[0], dst, ox); df_st(B.st2[1], dst, oy); df_st(B.st2[2], dst, oz);
+      fx = ox.hi; fy = oy.hi; fz = oz.hi;
+      if (wall) {
+        df_st(B.st2[6], dst, df_add(df_ld(B.st[6], i), sx));
+        df_st(B.st2[7], dst, df_add(df_ld(B.st[7], i), sy));
+        df_st(B.st2[8], dst, df_add(df_ld(B.st[8], i), sz));
+      } else {
+        df_st(B.st2[6], dst, dfl{0.f, 0.f}); df_st(B.st2[7], dst, dfl{0.f, 0.f}); df_st(B.st2[8], dst, dfl{0.f, 0.f});
+      }
     }
-    ax = min_image(ax - cx, E.Lx);
-    ay = ay - cy;
-    az = min_image(az - cz, E.Lz);
   }
-  B.st2[0][dst] = ox; B.st2[1][dst] = oy; B.st2[2][dst] = oz;
+  if (!DF || c0 < 0) {
+    double x, y, z;
+    abs_position<DF>(B, E, i, x, y, z);
+    double cx, cy, cz;
+    cell_center(E, c, cx, cy, cz);
+    const double ox = x - cx, oy = y - cy, oz = z - cz;
+    double ax = 0.0, ay = 0.0, az = 0.0;
+    if (wall) {
+      ax = st_get<DF>(B.st[6], i); ay = st_get<DF>(B.st[7], i); az = st_get<DF>(B.st[8], i);
+      if (c0 >= 0) {
+        double px, py, pz;
+        cell_center(E, c0, px, py, pz);
+        ax += px; ay += py; az += pz;
+      }
+      ax = min_image(ax - cx, E.Lx);
+      ay = ay - cy;
+      az = min_image(az - cz, E.Lz);
+    }
+    st_put<DF>(B.st2[0], dst, ox); st_put<DF>(B.st2[1], dst, oy); st_put<DF>(B.st2[2], dst, oz);
+    st_put<DF>(B.st2[6], dst, ax); st_put<DF>(B.st2[7], dst, ay); st_put<DF>(B.st2[8], dst, az);
+    fx = (float)ox; fy = (float)oy; fz = (float)oz;
+    if constexpr (!DF) static_cast<Pos64*>(B.pos)[dst] = Pos64{ox, oy, oz, wall ? 1.0 : 0.0};
+  }
+  // velocities move as raw 8-byte words in either representation
   B.st2[3][dst] = B.st[3][i]; B.st2[4][dst] = B.st[4][i]; B.st2[5][dst] = B.st[5][i];
-  B.st2[6][dst] = ax; B.st2[7][dst] = ay; B.st2[8][dst] = az;
   B.orig2[dst] = l;
   B.cell2[dst] = c;
-  const float spf = wall ? 1.0f : 0.0f;
-  if constexpr (sizeof(PT) == 16) {
-    static_cast<float4*>(B.pos)[dst] = make_float4((float)ox, (float)oy, (float)oz, spf);
-  } else {
-    static_cast<Pos64*>(B.pos)[dst] = Pos64{ox, oy, oz, (double)spf};
-  }
-  B.pbuild[dst] = make_float4((float)ox, (float)oy, (float)oz, 0.0f);
+  if constexpr (DF) static_cast<float4*>(B.pos)[dst] = make_float4(fx, fy, fz, wall ? 1.0f : 0.0f);
+  B.pbuild[dst] = make_float4(fx, fy, fz, 0.0f);
 }
 
 __global__ void __launch_bounds__(256) k_copy_back(BatchDev B) {
@@ -376,13 +546,15 @@ __global__ void __launch_bounds__(128) k_build(BatchDev B, PhysDev P) {
     else { me.x = me.y = me.z = (T)1e9; me.w = (T)0; }
     int cnt = 0;
     unsigned b0 = 0, b1 = 0, b2 = 0;
-    auto push = [&](unsigned ent) {
+    // append without divergence: every lane runs the same selects; only the
+    // lanes whose group of four is complete store it
+    auto push = [&](bool take, unsigned ent) {
       const int slot = cnt & 3;
-      if (slot == 0) b0 = ent;
-      else if (slot == 1) b1 = ent;
-      else if (slot == 2) b2 = ent;
-      else if ((cnt >> 2) < cap4) L4[(long long)(cnt >> 2) * N + i] = make_uint4(b0, b1, b2, ent);
-      ++cnt;
+      b0 = (take && slot == 0) ? ent : b0;
+      b1 = (take && slot == 1) ? ent : b1;
+      b2 = (take && slot == 2) ? ent : b2;
+      if (take && slot == 3 && (cnt >> 2) < cap4) L4[(long long)(cnt >> 2) * N + i] = make_uint4(b0, b1, b2, ent);
+      cnt += take ? 1 : 0;
     };
     for (int dx = -1; dx <= 1; ++dx) {
       int jx = cx + dx;
@@ -407,15 +579,15 @@ __global__ void __launch_bounds__(128) k_build(BatchDev B, PhysDev P) {
             { const T ax = qx - o2.x, ay = qy - o2.y, az = qz - o2.z; d2 = ax * ax + ay * ay + az * az; }
             { const T ax = qx - o3.x, ay = qy - o3.y, az = qz - o3.z; d3 = ax * ax + ay * ay + az * az; }
             const unsigned ej = jb + (unsigned)(j - j0);
-            if (act && d0 < rl2 && j != i) push(ej);
-            if (act && d1 < rl2 && j + 1 != i) push(ej + 1);
-            if (act && d2 < rl2 && j + 2 != i) push(ej + 2);
-            if (act && d3 < rl2 && j + 3 != i) push(ej + 3);
+            push(act && d0 < rl2 && j != i, ej);
+            push(act && d1 < rl2 && j + 1 != i, ej + 1);
+            push(act && d2 < rl2 && j + 2 != i, ej + 2);
+            push(act && d3 < rl2 && j + 3 != i, ej + 3);
           }
           for (; j < j1; ++j) {
             const PT o0 = pos[j];
             const T ax = qx - o0.x, ay = qy - o0.y, az = qz - o0.z;
-            if (act && ax * ax + ay * ay + az * az < rl2 && j != i) push(jb + (unsigned)(j - j0));
+            push(act && ax * ax + ay * ay + az * az < rl2 && j != i, jb + (unsigned)(j - j0));
           }
         }
       }
@@ -434,6 +606,286 @@ __global__ void __launch_bounds__(128) k_build(BatchDev B, PhysDev P) {
   }
 }
 
+// Staged list build: one block per (x, y) cell column of an element.  In cell
+// order each of the 9 neighbouring columns (x + dx, y + dy) is one contiguous
+// range of positions, so the block stages them into shared memory with at
+// most 9 bulk asynchronous copies (cp.async.bulk, completed on an mbarrier),
+// then its warps take the column's cells in turn and sweep each cell's 27
+// neighbour cells from shared memory.  A neighbourhood larger than the
+// dynamic shared memory falls back to reading global memory in the same
+// loop.  The wait on the mbarrier is bounded; on timeout the element is
+// marked failed and the block reads global memory instead.
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               :: "r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned phase) {
+  unsigned ok;
+  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+               : "=r"(ok) : "r"(smem_addr(bar)), "r"(phase) : "memory");
+  return ok != 0;
+}
+
+template <typename PT>
+__global__ void __launch_bounds__(128) k_build_staged(BatchDev B, PhysDev P, int smem_bytes) {
+  using T = decltype(PT::x);
+  extern __shared__ __align__(128) unsigned char sraw[];
+  __shared__ uint64_t bar;
+  __shared__ int col_lo[9], col_n[9], col_soff[9];
+  __shared__ int use_smem;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarp = blockDim.x >> 5;
+  // column -> element by binary search over the column offsets
+  const long long colg = blockIdx.x;
+  int lo = 0, hi = B.n_el - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (B.col_off[mid] <= colg) lo = mid; else hi = mid - 1;
+  }
+  const int e = lo;
+  const ElemDev& E = B.el[e];
+  const int ncx = E.nc[0], ncy = E.nc[1], ncz = E.nc[2];
+  const int col = (int)(colg - B.col_off[e]);
+  const int cx = col / ncy, cy = col % ncy;
+  const PT* gpos = static_cast<const PT*>(B.pos);
+  if (tid == 0) {
+    int total = 0;
+    for (int k = 0; k < 9; ++k) {
+      const int dx = k / 3 - 1, dy = k % 3 - 1;
+      int jx = cx + dx;
+      jx = jx < 0 ? jx + ncx : (jx >= ncx ? jx - ncx : jx);
+      const int jy = cy + dy;
+      if (jy < 0 || jy >= ncy) { col_lo[k] = 0; col_n[k] = 0; col_soff[k] = total; continue; }
+      const long long c0 = E.cell0 + ((long long)jx * ncy + jy) * ncz;
+      const int a = B.cstart[c0], b = B.cstart[c0 + ncz - 1] + B.csize[c0 + ncz - 1];
+      col_lo[k] = a;
+      col_n[k] = b - a;
+      col_soff[k] = total;
+      total += b - a;
+    }
+    use_smem = (long long)total * (long long)sizeof(PT) <= (long long)smem_bytes ? 1 : 0;
+    if (use_smem && total > 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&bar)));
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                   :: "r"(smem_addr(&bar)), "r"((unsigned)(total * sizeof(PT))) : "memory");
+      PT* sp = reinterpret_cast<PT*>(sraw);
+      for (int k = 0; k < 9; ++k)
+        if (col_n[k] > 0) bulk_g2s(sp + col_soff[k], gpos + col_lo[k], (unsigned)(col_n[k] * sizeof(PT)), &bar);
+    }
+  }
+  __syncthreads();
+  bool staged = use_smem != 0;
+  if (staged && col_soff[8] + col_n[8] > 0) {
+    // bounded wait for the copies (phase 0)
+    bool done = false;
+    for (long long it = 0; it < (1LL << 26) && !done; ++it) done = mbar_try_wait(&bar, 0);
+    if (!done) atomicMin(&B.status[e], kStUnstable);
+    staged = __syncthreads_and(done ? 1 : 0) != 0;
+  }
+  const PT* spos = reinterpret_cast<const PT*>(sraw);
+  const T rl2 = sizeof(T) == 4 ? (T)P.rl2f : (T)P.rl2;
+  const long long N = B.n_atoms;
+  const int cap4 = B.list_cap >> 2;
+  uint4* L4 = reinterpret_cast<uint4*>(B.list);
+  for (int cz = wid; cz < ncz; cz += nwarp) {
+    const long long cell = E.cell0 + ((long long)cx * ncy + cy) * ncz + cz;
+    const int s0 = B.cstart[cell], n0 = B.csize[cell];
+    for (int base = 0; base < n0; base += 32) {
+      const int i = s0 + base + lane;
+      const bool act = base + lane < n0;
+      PT me;
+      if (act) me = staged ? spos[col_soff[4] + (i - col_lo[4])] : gpos[i];
+      else { me.x = me.y = me.z = (T)1e9; me.w = (T)0; }
+      int cnt = 0;
+      unsigned b0 = 0, b1 = 0, b2 = 0;
+      auto push = [&](bool take, unsigned ent) {
+        const int slot = cnt & 3;
+        b0 = (take && slot == 0) ? ent : b0;
+        b1 = (take && slot == 1) ? ent : b1;
+        b2 = (take && slot == 2) ? ent : b2;
+        if (take && slot == 3 && (cnt >> 2) < cap4) L4[(long long)(cnt >> 2) * N + i] = make_uint4(b0, b1, b2, ent);
+        cnt += take ? 1 : 0;
+      };
+      for (int k = 0; k < 9; ++k) {
+        if (col_n[k] == 0) continue;
+        const int dx = k / 3 - 1, dy = k % 3 - 1;
+        int jx = cx + dx;
+        jx = jx < 0 ? jx + ncx : (jx >= ncx ? jx - ncx : jx);
+        const long long c0 = E.cell0 + ((long long)jx * ncy + (cy + dy)) * ncz;
+        // positions of this column: shared memory (index shifted by off) or global
+        const PT* src = staged ? spos : gpos;
+        const int off = staged ? col_soff[k] - col_lo[k] : 0;
+        for (int dz = -1; dz <= 1; ++dz) {
+          int jz = cz + dz;
+          jz = jz < 0 ? jz + ncz : (jz >= ncz ? jz - ncz : jz);
+          const long long c2 = c0 + jz;
+          const T qx = me.x - (T)dx * (T)E.cs[0], qy = me.y - (T)dy * (T)E.cs[1], qz = me.z - (T)dz * (T)E.cs[2];
+          const int j0 = B.cstart[c2], j1 = j0 + B.csize[c2];
+          const unsigned code = ((unsigned)(dx + 1) << 26) | ((unsigned)(dy + 1) << 28) | ((unsigned)(dz + 1) << 30);
+          const unsigned jb = (unsigned)(j0 - E.atom0) | code;
+          int j = j0;
+          for (; j + 3 < j1; j += 4) {
+            const PT o0 = src[j + off], o1 = src[j + 1 + off], o2 = src[j + 2 + off], o3 = src[j + 3 + off];
+            T d0, d1, d2, d3;
+            { const T ax = qx - o0.x, ay = qy - o0.y, az = qz - o0.z; d0 = ax * ax + ay * ay + az * az; }
+            { const T ax = qx - o1.x, ay = qy - o1.y, az = qz - o1.z; d1 = ax * ax + ay * ay + az * az; }
+            { const T ax = qx - o2.x, ay = qy - o2.y, az = qz - o2.z; d2 = ax * ax + ay * ay + az * az; }
+            { const T ax = qx - o3.x, ay = qy - o3.y, az = qz - o3.z; d3 = ax * ax + ay * ay + az * az; }
+            const unsigned ej = jb + (unsigned)(j - j0);
+            push(act && d0 < rl2 && j != i, ej);
+            push(act && d1 < rl2 && j + 1 != i, ej + 1);
+            push(act && d2 < rl2 && j + 2 != i, ej + 2);
+            push(act && d3 < rl2 && j + 3 != i, ej + 3);
+          }
+          for (; j < j1; ++j) {
+            const PT o0 = src[j + off];
+            const T ax = qx - o0.x, ay = qy - o0.y, az = qz - o0.z;
+            push(act && ax * ax + ay * ay + az * az < rl2 && j != i, jb + (unsigned)(j - j0));
+          }
+        }
+      }
+      if (act) {
+        if ((cnt & 3) != 0 && (cnt >> 2) < cap4) {
+          const unsigned pe = pad_entry(i, E);
+          const int slot = cnt & 3;
+          L4[(long long)(cnt >> 2) * N + i] = make_uint4(b0, slot > 1 ? b1 : pe, slot > 2 ? b2 : pe, pe);
+        }
+        if (cnt > B.list_cap) atomicMin(&B.status[e], kStOverflow);
+        B.nlist[i] = cnt < B.list_cap ? cnt : B.list_cap;
+      }
+    }
+  }
+}
+
+// Ballot list build: one warp per cell, lanes over candidates.  The warp
+// first gathers, from the cell's 27 neighbour cells, the atoms that lie
+// within r_c + skin of the bounding box of the cell's own atoms (any other
+// atom is out of range of every atom of the cell) into a per-warp shared
+// buffer: position shifted into the home cell's frame, list entry in w.
+// Then, atom by atom, the 32 lanes test 32 buffered candidates at once and
+// the accepted entries go to the atom's list at its running count plus
+// their rank in the ballot mask.  Entries keep the candidate order, the
+// neighbour cells in (dx, dy, dz) order.  A neighbourhood larger than the
+// buffer is swept in several passes; the running counts then persist in
+// nlist between passes.  Works from pbuild (float4), so one kernel serves
+// both pair-force precisions.
+constexpr int kBallotWarps = 4;
+constexpr int kBallotCap = 512;   // buffered candidates per warp (16 B each)
+
+__global__ void __launch_bounds__(kBallotWarps * 32) k_build_ballot(BatchDev B, PhysDev P) {
+  extern __shared__ __align__(16) float4 cbuf_all[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const long long cell = (long long)blockIdx.x * kBallotWarps + wid;
+  if (cell >= B.n_cells) return;
+  float4* cbuf = cbuf_all + wid * kBallotCap;
+  const int s0 = B.cstart[cell], n0 = B.csize[cell];
+  if (n0 == 0) return;
+  const int e = B.cell_el[cell];
+  const ElemDev& E = B.el[e];
+  int cx, cy, cz;
+  cell_coords(E, cell, cx, cy, cz);
+  const int ncx = E.nc[0], ncy = E.nc[1], ncz = E.nc[2];
+  const float csx = E.csf[0], csy = E.csf[1], csz = E.csf[2];
+  const float rl2 = P.rl2f;
+  const float4* pb = B.pbuild;
+  // bounding box of the cell's own atoms
+  float lx = 3.0e38f, ly = 3.0e38f, lz = 3.0e38f, hx = -3.0e38f, hy = -3.0e38f, hz = -3.0e38f;
+  for (int a = lane; a < n0; a += 32) {
+    const float4 p = pb[s0 + a];
+    lx = fminf(lx, p.x); ly = fminf(ly, p.y); lz = fminf(lz, p.z);
+    hx = fmaxf(hx, p.x); hy = fmaxf(hy, p.y); hz = fmaxf(hz, p.z);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lx = fminf(lx, __shfl_xor_sync(kFull, lx, o)); ly = fminf(ly, __shfl_xor_sync(kFull, ly, o));
+    lz = fminf(lz, __shfl_xor_sync(kFull, lz, o)); hx = fmaxf(hx, __shfl_xor_sync(kFull, hx, o));
+    hy = fmaxf(hy, __shfl_xor_sync(kFull, hy, o)); hz = fmaxf(hz, __shfl_xor_sync(kFull, hz, o));
+  }
+  const unsigned lt = (1u << lane) - 1u;
+  const long long N4 = B.n_atoms * 4;
+  const int cap = B.list_cap;
+  unsigned* L = B.list;
+  int k27 = 0, joff = 0;   // resume point of the candidate gather
+  bool first = true, last = false;
+  while (!last) {
+    // gather up to kBallotCap candidates
+    int m = 0;
+    while (k27 < 27 && m + 32 <= kBallotCap) {
+      const int dx = k27 / 9 - 1, dy = (k27 / 3) % 3 - 1, dz = k27 % 3 - 1;
+      const int jy = cy + dy;
+      if (jy < 0 || jy >= ncy) { ++k27; joff = 0; continue; }
+      int jx = cx + dx, jz = cz + dz;
+      jx = jx < 0 ? jx + ncx : (jx >= ncx ? jx - ncx : jx);
+      jz = jz < 0 ? jz + ncz : (jz >= ncz ? jz - ncz : jz);
+      const long long c2 = E.cell0 + ((long long)jx * ncy + jy) * ncz + jz;
+      const int n2 = B.csize[c2];
+      if (joff >= n2) { ++k27; joff = 0; continue; }
+      const int j = B.cstart[c2] + joff + lane;
+      const bool valid = joff + lane < n2;
+      float4 p = valid ? pb[j] : make_float4(3.0e18f, 3.0e18f, 3.0e18f, 0.0f);
+      p.x = fmaf((float)dx, csx, p.x);
+      p.y = fmaf((float)dy, csy, p.y);
+      p.z = fmaf((float)dz, csz, p.z);
+      const float ex = fmaxf(fmaxf(lx - p.x, p.x - hx), 0.0f);
+      const float ey = fmaxf(fmaxf(ly - p.y, p.y - hy), 0.0f);
+      const float ez = fmaxf(fmaxf(lz - p.z, p.z - hz), 0.0f);
+      const bool keep = valid && ex * ex + ey * ey + ez * ez < rl2;
+      const unsigned mk = __ballot_sync(kFull, keep);
+      if (keep) {
+        const unsigned ent = (unsigned)(j - E.atom0) | ((unsigned)(dx + 1) << 26) | ((unsigned)(dy + 1) << 28) |
+                             ((unsigned)(dz + 1) << 30);
+        cbuf[m + __popc(mk & lt)] = make_float4(p.x, p.y, p.z, __uint_as_float(ent));
+      }
+      m += __popc(mk);
+      joff += 32;
+    }
+    last = k27 >= 27;
+    __syncwarp();
+    // sweep the buffer for every atom of the cell
+    for (int base = 0; base < n0; base += 32) {
+      const int na = n0 - base < 32 ? n0 - base : 32;
+      const float4 mine = lane < na ? pb[s0 + base + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int a = 0; a < na; ++a) {
+        const long long i = s0 + base + a;
+        const float mx = __shfl_sync(kFull, mine.x, a), my = __shfl_sync(kFull, mine.y, a),
+                    mz = __shfl_sync(kFull, mine.z, a);
+        const unsigned self = (unsigned)(i - E.atom0) | (1u << 26) | (1u << 28) | (1u << 30);
+        int cnt = first ? 0 : B.nlist[i];
+        unsigned* Li = L + i * 4;
+#pragma unroll 2
+        for (int c = 0; c < m; c += 32) {
+          const bool in = c + lane < m;
+          const float4 q = cbuf[in ? c + lane : 0];
+          const float ax = mx - q.x, ay = my - q.y, az = mz - q.z;
+          const unsigned ent = __float_as_uint(q.w);
+          const bool take = in && ax * ax + ay * ay + az * az < rl2 && ent != self;
+          const unsigned mk = __ballot_sync(kFull, take);
+          const int kk = cnt + __popc(mk & lt);
+          if (take && kk < cap) Li[(long long)(kk >> 2) * N4 + (kk & 3)] = ent;
+          cnt += __popc(mk);
+        }
+        if (last) {
+          // pad the last partial group with an entry beyond r_c
+          const int kk = cnt + lane;
+          if (cnt < cap && lane < ((4 - (cnt & 3)) & 3))
+            Li[(long long)(kk >> 2) * N4 + (kk & 3)] = pad_entry(i, E);
+          if (lane == 0) {
+            if (cnt > cap) atomicMin(&B.status[e], kStOverflow);
+            B.nlist[i] = cnt < cap ? cnt : cap;
+          }
+        } else if (lane == 0) {
+          B.nlist[i] = cnt;
+        }
+      }
+    }
+    __syncwarp();
+    first = false;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // LJ pair forces over the Verlet lists: one thread per atom (cell order, so
 // a warp's neighbours are shared in L1).  Eq. LJ truncated at r_c, energy
@@ -443,6 +895,13 @@ __global__ void __launch_bounds__(128) k_build(BatchDev B, PhysDev P) {
 // Writes the LJ force, the x-virial share of fluid atoms (half per pair) and,
 // with ENERGY, half the shifted pair energy per atom.
 // ---------------------------------------------------------------------------
+// Approximate reciprocal (PTX rcp.approx.ftz.f32: one MUFU op, <= 1 ulp).
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 __device__ __forceinline__ float shift_unit(unsigned bits2) {
   // bits2 in {0, 1, 2} -> {-1, 0, 1}, exactly, without an int-to-float convert
   return __int_as_float(0x4B400000 | (int)bits2) - 12582913.0f;
@@ -466,7 +925,7 @@ struct PairAcc {
     }
     const T r2 = ddx * ddx + ddy * ddy + ddz * ddz;
     T inv2;
-    if constexpr (sizeof(T) == 4) inv2 = __frcp_rn(r2); else inv2 = 1.0 / r2;
+    if constexpr (sizeof(T) == 4) inv2 = rcp_approx(r2); else inv2 = 1.0 / r2;
     T e_, s2;
     int t = 0;
     if constexpr (UNIFORM) {
@@ -477,12 +936,14 @@ struct PairAcc {
       s2 = sig2[t] * inv2;
     }
     const T s6 = s2 * s2 * s2;
-    T fs = (T)24 * e_ * inv2 * s6 * ((T)2 * s6 - (T)1);
+    // F/r = 24 eps inv2 s6 (2 s6 - 1) = eps inv2 s6 (48 s6 - 24)
+    T fs = e_ * inv2 * s6 * ((T)48 * s6 - (T)24);
     bool in = r2 < rc2;
     if constexpr (!UNIFORM) in = in && P.active[t];
     fs = in ? fs : (T)0;
-    fx += fs * ddx; fy += fs * ddy; fz += fs * ddz;
-    w += fs * ddx * ddx;
+    const T tx = fs * ddx;
+    fx += tx; fy += fs * ddy; fz += fs * ddz;
+    w += tx * ddx;
     if (ENERGY) u += in ? ((T)4 * e_ * (s6 * s6 - s6) - (T)P.eshift[t]) : (T)0;
   }
 };
@@ -510,7 +971,23 @@ __global__ void __launch_bounds__(128) k_force(BatchDev B, PhysDev P) {
   PairAcc<PT, T, UNIFORM, ENERGY> acc;
   const uint4* L4 = reinterpret_cast<const uint4*>(B.list) + i;
   const int ng = (n + 3) >> 2;
-  for (int k = 0; k < ng; ++k) {
+  int k = 0;
+  // two groups of four entries per iteration: eight gathers in flight
+  for (; k + 1 < ng; k += 2) {
+    const uint4 e = __ldg(L4 + (long long)k * N);
+    const uint4 f = __ldg(L4 + (long long)(k + 1) * N);
+    const PT o0 = posj[e.x & kJMask], o1 = posj[e.y & kJMask], o2 = posj[e.z & kJMask], o3 = posj[e.w & kJMask];
+    const PT o4 = posj[f.x & kJMask], o5 = posj[f.y & kJMask], o6 = posj[f.z & kJMask], o7 = posj[f.w & kJMask];
+    acc.add(me, o0, e.x, csx, csy, csz, spi, rc2, eps, sig2, P);
+    acc.add(me, o1, e.y, csx, csy, csz, spi, rc2, eps, sig2, P);
+    acc.add(me, o2, e.z, csx, csy, csz, spi, rc2, eps, sig2, P);
+    acc.add(me, o3, e.w, csx, csy, csz, spi, rc2, eps, sig2, P);
+    acc.add(me, o4, f.x, csx, csy, csz, spi, rc2, eps, sig2, P);
+    acc.add(me, o5, f.y, csx, csy, csz, spi, rc2, eps, sig2, P);
+    acc.add(me, o6, f.z, csx, csy, csz, spi, rc2, eps, sig2, P);
+    acc.add(me, o7, f.w, csx, csy, csz, spi, rc2, eps, sig2, P);
+  }
+  if (k < ng) {
     const uint4 e = __ldg(L4 + (long long)k * N);
     const PT o0 = posj[e.x & kJMask], o1 = posj[e.y & kJMask], o2 = posj[e.z & kJMask], o3 = posj[e.w & kJMask];
     acc.add(me, o0, e.x, csx, csy, csz, spi, rc2, eps, sig2, P);
@@ -532,51 +1009,86 @@ __global__ void __launch_bounds__(128) k_force(BatchDev B, PhysDev P) {
 //            tethered wall atoms G-JF (Gronbech-Jensen & Farago 2013);
 // then publishes the pair-force input position and checks the list skin.
 // F(x) = LJ (force kernel) + body force g on fluid atoms (Eq. momentumEq) +
-// tether -k (r - r0) on wall atoms.
-// ---------------------------------------------------------------------------
-template <typename FT, typename PT>
+// tether -k (r - r0) on wall atoms.  Between launches a fluid atom stores the
+// half-step velocity u; when both phases run, the two half kicks with the
+// same force are one update u <- u + dt F/m, and the full-step velocity is
+// formed only where it is sampled.  Frozen-wall elements (FROZEN) with the
+// Berendsen thermostat split a step over two launches (kTzSum, kTzApply).
+template <typename FT, typename PT, bool FROZEN>
 __global__ void __launch_bounds__(256) k_integrate(BatchDev B, PhysDev P, int k, int mode,
                                                    cudaGraphConditionalHandle hcond, int use_cond) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long s = *B.step_base + k;
-  int mkey = -1;
+  int mkey = -1, tzkey = -1;
   int mblk = 0;
-  double mval[3] = {0.0, 0.0, 0.0};
+  double mval[3] = {0.0, 0.0, 0.0}, tzval[1] = {0.0};
   if (i < B.n_atoms) {
     const int e = B.atom_el[i];
     const ElemDev& E = B.el[e];
     const int l = B.orig[i];
     const bool fluid = l < E.nf;
+    const bool frozen = FROZEN && !fluid;
+    const bool stepped = s >= 1 && s - 1 < E.steps_total;   // a step s-1 to finish
+    const bool starting = s < E.steps_total;                // a step s to start
+    const bool fin = (mode & kFinish) && stepped;
+    const bool st1 = (mode & kStage1) && starting;
+    const long long ks = s - 1 - E.steps_eq;
+    const bool sample = stepped && ks >= 0 && ks < E.steps_sample && E.nb > 0 &&
+                        ((mode & kTzApply) || ((mode & kFinish) && !(mode & kTzSum)));
     double x = B.st[0][i], y = B.st[1][i], z = B.st[2][i];
     double vx = B.st[3][i], vy = B.st[4][i], vz = B.st[5][i];
     double fx = (double)static_cast<const FT*>(B.fx)[i];
     double fy = (double)static_cast<const FT*>(B.fy)[i];
     double fz = (double)static_cast<const FT*>(B.fz)[i];
+    bool moved = false;
     if (fluid) {
       fx += E.g;
-    } else {
+      if (sample) {
+        // full-step velocity of step s-1 (this thread holds u unless a
+        // previous launch already finished the step)
+        const bool have_full = !(mode & kFinish);
+        const double wx = have_full ? vx : vx + P.hdt_m * fx;
+        const double wy = have_full ? vy : vy + P.hdt_m * fy;
+        double wz = have_full ? vz : vz + P.hdt_m * fz;
+        if (FROZEN && (mode & kTzApply) && E.nf > 0) {
+          const double tzm = B.tz[2 * e + ((s - 1) & 1)] / (double)E.nf;
+          if (tzm > 0.0) wz *= sqrt(1.0 + P.dt / P.tau_T * (E.T / tzm - 1.0));
+        }
+        mval[0] = P.mass * wx;
+        mval[1] = P.mass * wx * wx + (double)static_cast<const FT*>(B.wxx)[i];
+        mval[2] = P.mass * (wx * wx + wy * wy + wz * wz);
+      }
+      if (FROZEN && (mode & (kTzSum | kTzApply))) {
+        // thermostat path: finish and start are separate launches
+        if (fin) { vx += P.hdt_m * fx; vy += P.hdt_m * fy; vz += P.hdt_m * fz; }
+        if ((mode & kTzSum) && stepped) tzval[0] = P.mass * vz * vz;
+        if ((mode & kTzApply) && stepped && E.nf > 0) {
+          const double tzm = B.tz[2 * e + ((s - 1) & 1)] / (double)E.nf;
+          if (tzm > 0.0) vz *= sqrt(1.0 + P.dt / P.tau_T * (E.T / tzm - 1.0));
+        }
+        if (st1) {
+          vx += P.hdt_m * fx; vy += P.hdt_m * fy; vz += P.hdt_m * fz;
+          x += P.dt * vx; y += P.dt * vy; z += P.dt * vz;
+          moved = true;
+        }
+      } else if (fin && st1) {
+        const double dtm = 2.0 * P.hdt_m;
+        vx += dtm * fx; vy += dtm * fy; vz += dtm * fz;
+        x += P.dt * vx; y += P.dt * vy; z += P.dt * vz;
+        moved = true;
+      } else if (fin) {
+        vx += P.hdt_m * fx; vy += P.hdt_m * fy; vz += P.hdt_m * fz;
+      } else if (st1) {
+        vx += P.hdt_m * fx; vy += P.hdt_m * fy; vz += P.hdt_m * fz;
+        x += P.dt * vx; y += P.dt * vy; z += P.dt * vz;
+        moved = true;
+      }
+    } else if (!frozen) {
       fx -= P.k_tether * (x - B.st[6][i]);
       fy -= P.k_tether * (y - B.st[7][i]);
       fz -= P.k_tether * (z - B.st[8][i]);
-    }
-    if ((mode & kFinish) && s >= 1 && s - 1 < E.steps_total) {
-      vx += P.hdt_m * fx; vy += P.hdt_m * fy; vz += P.hdt_m * fz;
-      const long long ks = s - 1 - E.steps_eq;
-      const double v2 = vx * vx + vy * vy + vz * vz;
-      if (!(v2 < 1e30) || !(fabs(y) < 1e6)) atomicMin(&B.status[e], kStUnstable);
-      if (fluid && ks >= 0 && ks < E.steps_sample && E.nb > 0) {
-        mkey = e;
-        mblk = (int)((ks * E.nb) / E.steps_sample);
-        mval[0] = P.mass * vx;
-        mval[1] = P.mass * vx * vx + (double)static_cast<const FT*>(B.wxx)[i];
-        mval[2] = P.mass * v2;
-      }
-    }
-    if ((mode & kStage1) && s < E.steps_total) {
-      if (fluid) {
-        vx += P.hdt_m * fx; vy += P.hdt_m * fy; vz += P.hdt_m * fz;
-        x += P.dt * vx; y += P.dt * vy; z += P.dt * vz;
-      } else {
+      if (fin) { vx += P.hdt_m * fx; vy += P.hdt_m * fy; vz += P.hdt_m * fz; }
+      if (st1) {
         double b0 = 0.0, b1 = 0.0, b2 = 0.0;
         if (E.beta_sd > 0.0) {
           normals3<FT>((uint32_t)l, (uint32_t)s, (uint32_t)E.id, 1u, E.seed, b0, b1, b2);
@@ -590,9 +1102,20 @@ __global__ void __launch_bounds__(256) k_integrate(BatchDev B, PhysDev P, int k,
         vx = P.gjf_a * vx + h2m * P.gjf_a * fx + bm * b0;
         vy = P.gjf_a * vy + h2m * P.gjf_a * fy + bm * b1;
         vz = P.gjf_a * vz + h2m * P.gjf_a * fz + bm * b2;
+        moved = true;
       }
+    } else {
+      vx = vy = vz = 0.0;
+    }
+    if (sample || (FROZEN && (mode & kTzSum) && stepped)) {
+      // every atom of the element joins its element's reduction (walls add 0)
+      mkey = e * kMaxBlocks + (int)(sample ? (ks * E.nb) / E.steps_sample : 0);
+      tzkey = e;
+    }
+    if (moved) {
       B.st[0][i] = x; B.st[1][i] = y; B.st[2][i] = z;
       const float xf = (float)x, yf = (float)y, zf = (float)z;
+      if (!(fabsf(yf) < 1e6f) || !(fabsf(xf) < 1e6f) || !(fabsf(zf) < 1e6f)) atomicMin(&B.status[e], kStUnstable);
       if constexpr (sizeof(PT) == 16) {
         static_cast<float4*>(B.pos)[i] = make_float4(xf, yf, zf, fluid ? 0.0f : 1.0f);
       } else {
@@ -609,14 +1132,203 @@ __global__ void __launch_bounds__(256) k_integrate(BatchDev B, PhysDev P, int k,
     }
     B.st[3][i] = vx; B.st[4][i] = vy; B.st[5][i] = vz;
   }
-  if (mode & kFinish) {
-    seg_add<3>(mkey, mval, [&](int e, int q) {
-      return B.acc + (size_t)e * kAccStride + (q == 0 ? kAccQ + mblk : (q == 1 ? kAccP + mblk : kAccT));
+  if (FROZEN && (mode & kTzSum)) {
+    const int slot = (int)((s - 1) & 1);
+    const int key = (mode & kTzSum) ? tzkey : -1;
+    block_seg_add<1>(key, tzval, [&](int e, int) { return B.tz + 2 * e + slot; });
+  }
+  if (FROZEN && (mode & kTzApply)) {
+    // clear the other parity slot for the next step's sum
+    const long long tcount = (long long)gridDim.x * blockDim.x;
+    for (long long t = i; t < B.n_el; t += tcount) B.tz[2 * t + (s & 1)] = 0.0;
+  }
+  if ((mode & kTzApply) || ((mode & kFinish) && !(mode & kTzSum))) {
+    block_seg_add<3>(mkey, mval, [&](int kk, int q) {
+      const int e = kk / kMaxBlocks, b = kk % kMaxBlocks;
+      return B.acc + (size_t)e * kAccStride + (q == 0 ? kAccQ + b : (q == 1 ? kAccP + b : kAccT));
     });
   }
   if (use_cond) {
     // the last block to finish turns the flag into the graph condition (one
     // caller of cudaGraphSetConditional) and clears the flag words
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      const int prev = atomicAdd(&B.flags[1], 1);
+      if (prev == (int)gridDim.x - 1) {
+        const int need = atomicExch(&B.flags[0], 0);
+        atomicExch(&B.flags[1], 0);
+        if (need) cudaGraphSetConditional(hcond, 1u);
+      }
+    }
+  }
+}
+
+// Block-level segmented reduction of FP32 values for 256-thread blocks: when
+// the whole block shares one key, each warp adds its lanes in FP32 and the
+// eight warp sums are added in FP64 by NV threads (one atomicAdd each);
+// otherwise the values go through block_seg_add in FP64.  All threads of the
+// block must call it.
+template <int NV, typename DstFn>
+__device__ __forceinline__ void block_seg_add_f(int key, const float (&val)[NV], DstFn dst) {
+  __shared__ int k0s;
+  __shared__ float wsum[NV][8];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  if (t == 0) k0s = key;
+  __syncthreads();
+  const int k0 = k0s;
+  if (__syncthreads_and(key == k0)) {
+    if (k0 < 0) return;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      const float v = warp_sum(val[q]);
+      if (lane == 0) wsum[q][w] = v;
+    }
+    __syncthreads();
+    if (t < NV) {
+      double acc = 0.0;
+      for (int r = 0; r < (int)(blockDim.x >> 5); ++r) acc += (double)wsum[t][r];
+      atomicAdd(dst(k0, t), acc);
+    }
+    return;
+  }
+  double dv[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) dv[q] = (double)val[q];
+  block_seg_add<NV>(key, dv, dst);
+}
+
+// The integration step with the double-float state (FP32 pair forces): the
+// same phases and formulas as k_integrate, every update in FP32 operations.
+// Per-atom measurement terms are formed in FP32 and summed per warp in FP32,
+// then across warps, blocks and steps in FP64.
+template <bool FROZEN>
+__global__ void __launch_bounds__(256) k_integrate_df(BatchDev B, PhysDev P, int k, int mode,
+                                                      cudaGraphConditionalHandle hcond, int use_cond) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long s = *B.step_base + k;
+  int mkey = -1, tzkey = -1;
+  float mval[3] = {0.f, 0.f, 0.f}, tzval[1] = {0.f};
+  if (i < B.n_atoms) {
+    const int e = B.atom_el[i];
+    const ElemDev& E = B.el[e];
+    const int l = B.orig[i];
+    const bool fluid = l < E.nf;
+    const bool frozen = FROZEN && !fluid;
+    const bool stepped = s >= 1 && s - 1 < E.steps_total;
+    const bool starting = s < E.steps_total;
+    const bool fin = (mode & kFinish) && stepped;
+    const bool st1 = (mode & kStage1) && starting;
+    const long long ks = s - 1 - E.steps_eq;
+    const bool sample = stepped && ks >= 0 && ks < E.steps_sample && E.nb > 0 &&
+                        ((mode & kTzApply) || ((mode & kFinish) && !(mode & kTzSum)));
+    dfl x = df_ld(B.st[0], i), y = df_ld(B.st[1], i), z = df_ld(B.st[2], i);
+    dfl vx = df_ld(B.st[3], i), vy = df_ld(B.st[4], i), vz = df_ld(B.st[5], i);
+    float fx = static_cast<const float*>(B.fx)[i];
+    float fy = static_cast<const float*>(B.fy)[i];
+    float fz = static_cast<const float*>(B.fz)[i];
+    const float h = P.hdt_mf, dt = P.dtf;
+    bool moved = false;
+    if (fluid) {
+      // the body force enters as its own kick, dt/(2m) g, so that it is not
+      // rounded against the much larger pair force
+      const float gk = E.g_kick;
+      float lam = 1.0f;
+      if (FROZEN && (mode & kTzApply) && E.nf > 0) {
+        const float tzm = (float)B.tz[2 * e + ((s - 1) & 1)] / (float)E.nf;
+        if (tzm > 0.0f) lam = sqrtf(1.0f + P.dt_tauf * (E.Tf / tzm - 1.0f));
+      }
+      if (sample) {
+        const bool have_full = !(mode & kFinish);
+        const float wx = have_full ? vx.hi + vx.lo : vx.hi + (vx.lo + (__fmul_rn(h, fx) + gk));
+        const float wy = have_full ? vy.hi + vy.lo : vy.hi + __fmaf_rn(h, fy, vy.lo);
+        float wz = have_full ? vz.hi + vz.lo : vz.hi + __fmaf_rn(h, fz, vz.lo);
+        wz *= lam;
+        mval[0] = P.massf * wx;
+        mval[1] = P.massf * wx * wx + static_cast<const float*>(B.wxx)[i];
+        mval[2] = P.massf * (wx * wx + wy * wy + wz * wz);
+      }
+      const float hfx = __fmul_rn(h, fx), hfy = __fmul_rn(h, fy), hfz = __fmul_rn(h, fz);
+      if (FROZEN && (mode & (kTzSum | kTzApply))) {
+        if (fin) { vx = df_add(df_add(vx, hfx), gk); vy = df_add(vy, hfy); vz = df_add(vz, hfz); }
+        if ((mode & kTzSum) && stepped) tzval[0] = P.massf * vz.hi * vz.hi;
+        if ((mode & kTzApply) && stepped) vz = df_mul(lam, vz);
+        if (st1) {
+          vx = df_add(df_add(vx, hfx), gk); vy = df_add(vy, hfy); vz = df_add(vz, hfz);
+          moved = true;
+        }
+      } else {
+        // both half kicks of a fused launch use the same force
+        const int kicks = (fin ? 1 : 0) + (st1 ? 1 : 0);
+        if (kicks > 0) {
+          const float kf = (float)kicks;
+          vx = df_add(df_add(vx, __fmul_rn(kf, hfx)), __fmul_rn(kf, gk));
+          vy = df_add(vy, __fmul_rn(kf, hfy));
+          vz = df_add(vz, __fmul_rn(kf, hfz));
+        }
+        moved = st1;
+      }
+      if (moved) {
+        x = df_add(x, df_mul(dt, vx)); y = df_add(y, df_mul(dt, vy)); z = df_add(z, df_mul(dt, vz));
+      }
+    } else if (!frozen) {
+      fx = __fmaf_rn(-P.k_tetherf, df_diff(x, df_ld(B.st[6], i)), fx);
+      fy = __fmaf_rn(-P.k_tetherf, df_diff(y, df_ld(B.st[7], i)), fy);
+      fz = __fmaf_rn(-P.k_tetherf, df_diff(z, df_ld(B.st[8], i)), fz);
+      if (fin) { vx = df_add(vx, __fmul_rn(h, fx)); vy = df_add(vy, __fmul_rn(h, fy)); vz = df_add(vz, __fmul_rn(h, fz)); }
+      if (st1) {
+        float b0 = 0.f, b1 = 0.f, b2 = 0.f;
+        if (E.beta_sdf > 0.f) {
+          normals3f((uint32_t)l, (uint32_t)s, (uint32_t)E.id, 1u, E.seed, b0, b1, b2);
+          b0 *= E.beta_sdf; b1 *= E.beta_sdf; b2 *= E.beta_sdf;
+        }
+        // G-JF: x += b dt (v + dt/(2m) f + beta/(2m)); v = a v + a dt/(2m) f + (b/m) beta
+        const float bdt = P.gjf_bf * dt, i2m = 0.5f * P.inv_mf, bm = P.gjf_bf * P.inv_mf, a = P.gjf_af;
+        const float px = __fmaf_rn(h, fx, b0 * i2m), py = __fmaf_rn(h, fy, b1 * i2m), pz = __fmaf_rn(h, fz, b2 * i2m);
+        x = df_add(x, df_mul(bdt, df_add(vx, px)));
+        y = df_add(y, df_mul(bdt, df_add(vy, py)));
+        z = df_add(z, df_mul(bdt, df_add(vz, pz)));
+        vx = df_add(df_mul(a, vx), __fmaf_rn(h * a, fx, bm * b0));
+        vy = df_add(df_mul(a, vy), __fmaf_rn(h * a, fy, bm * b1));
+        vz = df_add(df_mul(a, vz), __fmaf_rn(h * a, fz, bm * b2));
+        moved = true;
+      }
+    } else {
+      vx = vy = vz = dfl{0.f, 0.f};
+    }
+    if (sample || (FROZEN && (mode & kTzSum) && stepped)) {
+      mkey = e * kMaxBlocks + (int)(sample ? (ks * E.nb) / E.steps_sample : 0);
+      tzkey = e;
+    }
+    if (moved) {
+      df_st(B.st[0], i, x); df_st(B.st[1], i, y); df_st(B.st[2], i, z);
+      const float xf = x.hi, yf = y.hi, zf = z.hi;
+      if (!(fabsf(yf) < 1e6f) || !(fabsf(xf) < 1e6f) || !(fabsf(zf) < 1e6f)) atomicMin(&B.status[e], kStUnstable);
+      static_cast<float4*>(B.pos)[i] = make_float4(xf, yf, zf, fluid ? 0.0f : 1.0f);
+      const float4 pb = B.pbuild[i];
+      const float ex = xf - pb.x, ey = yf - pb.y, ez = zf - pb.z;
+      if (ex * ex + ey * ey + ez * ez > P.half_skin2f) {
+        if (use_cond) atomicOr(&B.flags[0], 1);
+        else atomicMin(&B.status[e], kStSkin);
+      }
+    }
+    df_st(B.st[3], i, vx); df_st(B.st[4], i, vy); df_st(B.st[5], i, vz);
+  }
+  if (FROZEN && (mode & kTzSum)) {
+    const int slot = (int)((s - 1) & 1);
+    block_seg_add_f<1>(tzkey, tzval, [&](int e, int) { return B.tz + 2 * e + slot; });
+  }
+  if (FROZEN && (mode & kTzApply)) {
+    const long long tcount = (long long)gridDim.x * blockDim.x;
+    for (long long t = i; t < B.n_el; t += tcount) B.tz[2 * t + (s & 1)] = 0.0;
+  }
+  if ((mode & kTzApply) || ((mode & kFinish) && !(mode & kTzSum))) {
+    block_seg_add_f<3>(mkey, mval, [&](int kk, int q) {
+      const int e = kk / kMaxBlocks, b = kk % kMaxBlocks;
+      return B.acc + (size_t)e * kAccStride + (q == 0 ? kAccQ + b : (q == 1 ? kAccP + b : kAccT));
+    });
+  }
+  if (use_cond) {
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();
@@ -639,10 +1351,15 @@ __global__ void k_energy(BatchDev B, PhysDev P, int which) {
   if (i < B.n_atoms) {
     const int e = B.atom_el[i];
     const ElemDev& E = B.el[e];
-    const double vx = B.st[3][i], vy = B.st[4][i], vz = B.st[5][i];
+    constexpr bool DF = sizeof(FT) == 4;
+    const double vx = st_get<DF>(B.st[3], i), vy = st_get<DF>(B.st[4], i), vz = st_get<DF>(B.st[5], i);
     double en = 0.5 * P.mass * (vx * vx + vy * vy + vz * vz) + (double)static_cast<const FT*>(B.epot)[i];
-    if (B.orig[i] >= E.nf) {
-      const double dx = B.st[0][i] - B.st[6][i], dy = B.st[1][i] - B.st[7][i], dz = B.st[2][i] - B.st[8][i];
+    if (B.orig[i] >= E.nf && P.mode == 1) {
+      en = 0.0;                     // frozen walls carry no dynamical energy
+    } else if (B.orig[i] >= E.nf) {
+      const double dx = st_get<DF>(B.st[0], i) - st_get<DF>(B.st[6], i),
+                   dy = st_get<DF>(B.st[1], i) - st_get<DF>(B.st[7], i),
+                   dz = st_get<DF>(B.st[2], i) - st_get<DF>(B.st[8], i);
       en += 0.5 * P.k_tether * (dx * dx + dy * dy + dz * dz);
     }
     key = e;
@@ -661,10 +1378,13 @@ __global__ void k_export(BatchDev B, int what) {
   const long long dst = E.atom0 + B.orig[i];
   const long long N = B.n_atoms;
   if (what == 0) {
+    constexpr bool DF = sizeof(FT) == 4;
     double x, y, z;
-    abs_position(B, E, i, x, y, z);
+    abs_position<DF>(B, E, i, x, y, z);
     B.out[dst] = x; B.out[N + dst] = y; B.out[2 * N + dst] = z;
-    B.out[3 * N + dst] = B.st[3][i]; B.out[4 * N + dst] = B.st[4][i]; B.out[5 * N + dst] = B.st[5][i];
+    B.out[3 * N + dst] = st_get<DF>(B.st[3], i);
+    B.out[4 * N + dst] = st_get<DF>(B.st[4], i);
+    B.out[5 * N + dst] = st_get<DF>(B.st[5], i);
   } else {
     B.out[dst] = (double)static_cast<const FT*>(B.fx)[i];
     B.out[N + dst] = (double)static_cast<const FT*>(B.fy)[i];

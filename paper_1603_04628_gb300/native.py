@@ -38,7 +38,7 @@ class MDParams(ctypes.Structure):
                 ("sig_ww", ctypes.c_double), ("fluid_margin", ctypes.c_double), ("tau_T", ctypes.c_double),
                 ("mass", ctypes.c_double), ("n_blocks", ctypes.c_int32), ("mode", ctypes.c_int32),
                 ("wall_planes", ctypes.c_int32), ("list_capacity", ctypes.c_int32),
-                ("skin", ctypes.c_double), ("rebuild_every", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("skin", ctypes.c_double), ("rebuild_every", ctypes.c_int32), ("build_variant", ctypes.c_int32)]
 
 
 class GPParams(ctypes.Structure):
@@ -103,6 +103,7 @@ def lib():
         "mdgp_micro_state": ([vp, dp, dp, i64], ctypes.c_int),
         "mdgp_md_forces": ([vp, ctypes.POINTER(Element), dp, i64, dp, dp, dp], ctypes.c_int),
         "mdgp_micro_profile": ([vp, i64, dp], ctypes.c_int),
+        "mdgp_autotune": ([vp, ctypes.POINTER(Element), i64, i64, ctypes.POINTER(MDParams), dp], ctypes.c_int),
         "mdgp_last_error": ([vp], ctypes.c_char_p),
         "mdgp_gp_fit": ([vp, dp, dp, i64, ctypes.c_int32, ctypes.POINTER(GPParams), dp, ctypes.POINTER(vp)],
                         ctypes.c_int),
@@ -243,6 +244,16 @@ class Context:
         v = np.zeros((self.n_atoms, 3))
         _check(self.h, lib().mdgp_micro_state(self.h, _dp(x), _dp(v), self.n_atoms), "mdgp_micro_state")
         return x, v
+
+    def autotune(self, els, probe_steps=400):
+        """Pick skin and list-build variant for this batch by timing; returns
+        (chosen parameters as a dict, atom-steps/s of the best probe)."""
+        arr = elements_array(els)
+        best = MDParams()
+        rate = ctypes.c_double()
+        _check(self.h, lib().mdgp_autotune(self.h, arr, len(els), int(probe_steps), ctypes.byref(best),
+                                           ctypes.byref(rate)), "mdgp_autotune")
+        return {k: getattr(best, k) for k, _ in MDParams._fields_}, rate.value
 
     def micro_profile(self, steps=100):
         """Mean per-launch milliseconds of the integration and pair-force kernels."""

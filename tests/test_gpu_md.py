@@ -251,3 +251,80 @@ def test_energy_conservation_without_thermostat_or_forcing(native, prec):
     assert r["status"] == 0
     assert abs(ref["e_drift"]) < 2e-3
     assert abs(r["e_drift"]) < 2e-3 + 2 * abs(ref["e_drift"])
+
+
+@pytest.mark.parametrize("cfg", [1, 2])
+def test_list_build_variants_find_the_same_pairs(native, cfg):
+    # staged (0), direct (1) and ballot (2) builds must give every atom the
+    # same neighbours within r_c; the order of atoms inside a cell comes from
+    # binning atomics and differs from call to call, so the forces agree up
+    # to FP64 summation order
+    name, el, x, sp = configs()[cfg]
+    out = []
+    for variant in (0, 1, 2):
+        ctx = native.Context(0, native.PREC_FP64, build_variant=variant)
+        out.append(ctx.md_forces(el, x))
+        ctx.close()
+    f0, w0, e0 = out[0]
+    scale = max(np.abs(f0).max(), 1.0)
+    for f, w, e in out[1:]:
+        assert np.abs(f - f0).max() <= 1e-12 * scale
+        assert np.abs(w - w0).max() <= 1e-12 * max(np.abs(w0).max(), 1.0)
+        assert abs(e.sum() - e0.sum()) <= 1e-12 * max(np.abs(e0).sum(), 1.0)
+
+
+def test_ballot_build_multi_pass_matches_oracle(native):
+    # dense walls (wall density 4) and r_c = 4 put far more than one shared
+    # buffer of candidates around each cell and more than 32 atoms in a cell:
+    # the ballot build sweeps in several passes
+    el = dict(h=8.0, Lx=13.5, Lz=13.5, density=0.75, T=2.44, g_ext=0.0, dpdx=0.0, steps_eq=0, steps_sample=0,
+              seed=3, id=0)
+    p = omd.make_params(el, **PAPER_MODE)
+    x, v, a, sp = omd.init(p)
+    rng = np.random.default_rng(5)
+    x = x + rng.normal(0.0, 0.05, x.shape) * (sp[:, None] == 0)
+    fr, wr, er = omd.lj_forces(p, x, sp, "cells")
+    ctx = native.Context(0, native.PREC_FP64, build_variant=2, list_capacity=1600, **PAPER_MODE)
+    f, w, e = ctx.md_forces(el, x)
+    ctx.close()
+    assert _force_err(f, fr) <= FP_TOL[0]
+    fl = sp == 0
+    assert np.abs(w[fl] - wr[fl]).max() <= 1e-11 * max(np.abs(wr[fl]).max(), 1.0)
+
+
+def test_autotune_keeps_results_exact(native):
+    els = synth.batch_uneven(6, seed=13, steps=60)
+    ctx = native.Context(0, native.PREC_FP64)
+    chosen, rate = ctx.autotune(els, probe_steps=40)
+    assert chosen["skin"] in (0.3, 0.4, 0.5, 0.6) and chosen["build_variant"] in (0, 1, 2)
+    assert rate > 0
+    res = ctx.micro_batch(els)
+    for el, r in zip(els, res):
+        ref = omd.element(omd.make_params(el))
+        assert r["q"] == pytest.approx(ref["q"], rel=1e-7, abs=1e-9)
+    ctx.close()
+
+
+PAPER_MODE = dict(mode=1, eps_wf=0.2, sig_wf=0.75, wall_density=4.0, rc=4.0, dt=0.0025, tau_T=0.5)
+
+
+def test_paper_mode_frozen_walls_berendsen_fp64(native):
+    # App. A parameters: frozen dense walls, wall-fluid (0.2, 0.75), r_c = 4,
+    # dt = 0.0025, T = 2.44, Berendsen on the fluid's v_z
+    el = dict(h=10.0, Lx=15.0, Lz=15.0, density=0.75, T=2.44, g_ext=0.02, dpdx=0.0, steps_eq=60,
+              steps_sample=40, seed=77, id=5)
+    ctx = native.Context(0, native.PREC_FP64, list_capacity=640, **PAPER_MODE)
+    ctx.micro_plan([el])
+    ctx.micro_launch()
+    r = ctx.micro_results()[0]
+    xg, vg = ctx.micro_state()
+    ctx.close()
+    p = omd.make_params(el, **PAPER_MODE)
+    x, v, a, sp = omd.init(p)
+    acc, st = omd.simulate(p, x, v, a, sp, 0, 100)
+    ref = omd.finalize(p, acc)
+    assert r["status"] == 0
+    assert np.abs(_wrap_dx(xg - x, p)).max() <= 1e-6
+    assert np.abs(_wrap_dx(xg[sp == 1] - a[sp == 1], p)).max() <= 1e-12   # walls did not move
+    for k in ("q", "p", "T_meas", "e_drift"):
+        assert r[k] == pytest.approx(ref[k], rel=1e-7, abs=1e-9), k
