@@ -212,7 +212,7 @@ static void enqueue_rebuild(mdgp_ctx* ctx, cudaStream_t s) {
   const unsigned gc = (unsigned)ctx->n_columns;
   const unsigned gw = grid_for(ctx->B.n_cells, kBallotWarps);
   const int variant = ctx->params.build_variant;
-  const size_t ballot_smem = sizeof(float4) * kBallotWarps * kBallotCap;
+  const size_t ballot_smem = (size_t)kBallotWarps * kBallotWarpBytes;
   if (ctx->precision == MDGP_PREC_FP32) {
     k_permute<float4><<<g, 256, 0, s>>>(ctx->B);
     k_copy_back<<<g, 256, 0, s>>>(ctx->B);

@@ -765,22 +765,32 @@ __global__ void __launch_bounds__(128) k_build_staged(BatchDev B, PhysDev P, int
 // within r_c + skin of the bounding box of the cell's own atoms (any other
 // atom is out of range of every atom of the cell) into a per-warp shared
 // buffer: position shifted into the home cell's frame, list entry in w.
-// Then, atom by atom, the 32 lanes test 32 buffered candidates at once and
-// the accepted entries go to the atom's list at its running count plus
-// their rank in the ballot mask.  Entries keep the candidate order, the
-// neighbour cells in (dx, dy, dz) order.  A neighbourhood larger than the
-// buffer is swept in several passes; the running counts then persist in
-// nlist between passes.  Works from pbuild (float4), so one kernel serves
-// both pair-force precisions.
-constexpr int kBallotWarps = 4;
-constexpr int kBallotCap = 512;   // buffered candidates per warp (16 B each)
+// The gather walks the 27 cells as one flat index range (lane k of the warp
+// holds cell k's start, size and shift; a lane finds its cell by a binary
+// search over the size prefix), so consecutive chunks load independently.
+// The cell's atoms are then taken octant by octant (sign of the offset from
+// the cell centre): the buffer is filtered once more against the octant's
+// box into an index list, about half as long, and for each atom of the
+// octant the 32 lanes test 32 listed candidates at once; accepted entries
+// go to the atom's list at its running count plus their rank in the ballot
+// mask.  Entries keep the candidate order, the neighbour cells in
+// (dx, dy, dz) order.  A neighbourhood larger than the buffer is swept in
+// several passes; the running counts then persist in nlist between passes.
+// Works from pbuild (float4), so one kernel serves both pair-force
+// precisions.  The same atom never tests itself: its own candidate is at
+// distance exactly 0 (the zero shift adds 0), which the range test
+// 0 < d^2 < (r_c + skin)^2 excludes.
+constexpr int kBallotWarps = 2;
+constexpr int kBallotCap = 512;   // buffered candidates per warp
+constexpr int kBallotWarpBytes = (kBallotCap + 32) * 16 + (kBallotCap + 32) * 2;
 
-__global__ void __launch_bounds__(kBallotWarps * 32) k_build_ballot(BatchDev B, PhysDev P) {
-  extern __shared__ __align__(16) float4 cbuf_all[];
+__global__ void __launch_bounds__(kBallotWarps * 32, 10) k_build_ballot(BatchDev B, PhysDev P) {
+  extern __shared__ __align__(16) unsigned char bsm[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const long long cell = (long long)blockIdx.x * kBallotWarps + wid;
   if (cell >= B.n_cells) return;
-  float4* cbuf = cbuf_all + wid * kBallotCap;
+  float4* cbuf = reinterpret_cast<float4*>(bsm + wid * kBallotWarpBytes);
+  unsigned short* oidx = reinterpret_cast<unsigned short*>(cbuf + kBallotCap + 32);
   const int s0 = B.cstart[cell], n0 = B.csize[cell];
   if (n0 == 0) return;
   const int e = B.cell_el[cell];
@@ -790,7 +800,9 @@ __global__ void __launch_bounds__(kBallotWarps * 32) k_build_ballot(BatchDev B, 
   const int ncx = E.nc[0], ncy = E.nc[1], ncz = E.nc[2];
   const float csx = E.csf[0], csy = E.csf[1], csz = E.csf[2];
   const float rl2 = P.rl2f;
+  const unsigned rl2u = __float_as_uint(rl2) - 1u;
   const float4* pb = B.pbuild;
+  const float4 far4 = make_float4(1.0e18f, 1.0e18f, 1.0e18f, 0.0f);
   // bounding box of the cell's own atoms
   float lx = 3.0e38f, ly = 3.0e38f, lz = 3.0e38f, hx = -3.0e38f, hy = -3.0e38f, hz = -3.0e38f;
   for (int a = lane; a < n0; a += 32) {
@@ -804,81 +816,128 @@ __global__ void __launch_bounds__(kBallotWarps * 32) k_build_ballot(BatchDev B, 
     lz = fminf(lz, __shfl_xor_sync(kFull, lz, o)); hx = fmaxf(hx, __shfl_xor_sync(kFull, hx, o));
     hy = fmaxf(hy, __shfl_xor_sync(kFull, hy, o)); hz = fmaxf(hz, __shfl_xor_sync(kFull, hz, o));
   }
-  const unsigned lt = (1u << lane) - 1u;
-  const long long N4 = B.n_atoms * 4;
-  const int cap = B.list_cap;
-  unsigned* L = B.list;
-  int k27 = 0, joff = 0;   // resume point of the candidate gather
-  bool first = true, last = false;
-  while (!last) {
-    // gather up to kBallotCap candidates
-    int m = 0;
-    while (k27 < 27 && m + 32 <= kBallotCap) {
-      const int dx = k27 / 9 - 1, dy = (k27 / 3) % 3 - 1, dz = k27 % 3 - 1;
-      const int jy = cy + dy;
-      if (jy < 0 || jy >= ncy) { ++k27; joff = 0; continue; }
+  // neighbour table: lane k < 27 holds cell k = 9 (dx+1) + 3 (dy+1) + (dz+1)
+  int nst = 0, nsz = 0;
+  unsigned ncode = 0;
+  float nsx = 0.f, nsy = 0.f, nsz_f = 0.f;
+  if (lane < 27) {
+    const int dx = lane / 9 - 1, dy = (lane / 3) % 3 - 1, dz = lane % 3 - 1;
+    const int jy = cy + dy;
+    if (jy >= 0 && jy < ncy) {
       int jx = cx + dx, jz = cz + dz;
       jx = jx < 0 ? jx + ncx : (jx >= ncx ? jx - ncx : jx);
       jz = jz < 0 ? jz + ncz : (jz >= ncz ? jz - ncz : jz);
       const long long c2 = E.cell0 + ((long long)jx * ncy + jy) * ncz + jz;
-      const int n2 = B.csize[c2];
-      if (joff >= n2) { ++k27; joff = 0; continue; }
-      const int j = B.cstart[c2] + joff + lane;
-      const bool valid = joff + lane < n2;
-      float4 p = valid ? pb[j] : make_float4(3.0e18f, 3.0e18f, 3.0e18f, 0.0f);
-      p.x = fmaf((float)dx, csx, p.x);
-      p.y = fmaf((float)dy, csy, p.y);
-      p.z = fmaf((float)dz, csz, p.z);
+      nst = B.cstart[c2];
+      nsz = B.csize[c2];
+    }
+    ncode = ((unsigned)(dx + 1) << 26) | ((unsigned)(dy + 1) << 28) | ((unsigned)(dz + 1) << 30);
+    nsx = (float)dx * csx; nsy = (float)dy * csy; nsz_f = (float)dz * csz;
+  }
+  int pre = nsz;   // inclusive prefix of the sizes over the lanes
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(kFull, pre, o);
+    if (lane >= o) pre += t;
+  }
+  const int excl = pre - nsz;
+  const int total = __shfl_sync(kFull, pre, 31);
+  const unsigned lt = (1u << lane) - 1u;
+  const long long N4 = B.n_atoms * 4;
+  const int cap = B.list_cap;
+  unsigned* L = B.list;
+  if (lane == 0) cbuf[kBallotCap] = far4;   // the padding target of the index lists
+  int f0 = 0;
+  bool first = true, last = false;
+  while (!last) {
+    // gather up to kBallotCap candidates
+    int m = 0;
+#pragma unroll 2
+    for (; f0 < total && m + 32 <= kBallotCap; f0 += 32) {
+      const int f = f0 + lane;
+      int k = 0;
+#pragma unroll
+      for (int st = 16; st > 0; st >>= 1) {
+        const int pv = __shfl_sync(kFull, pre, k + st - 1);
+        if (pv <= f) k += st;
+      }
+      const int jn = __shfl_sync(kFull, nst, k), je = __shfl_sync(kFull, excl, k);
+      const unsigned code = __shfl_sync(kFull, ncode, k);
+      const float ox = __shfl_sync(kFull, nsx, k), oy = __shfl_sync(kFull, nsy, k), oz = __shfl_sync(kFull, nsz_f, k);
+      const bool valid = f < total;
+      const int j = jn + (f - je);
+      float4 p = valid ? pb[j] : far4;
+      p.x += ox; p.y += oy; p.z += oz;
       const float ex = fmaxf(fmaxf(lx - p.x, p.x - hx), 0.0f);
       const float ey = fmaxf(fmaxf(ly - p.y, p.y - hy), 0.0f);
       const float ez = fmaxf(fmaxf(lz - p.z, p.z - hz), 0.0f);
       const bool keep = valid && ex * ex + ey * ey + ez * ez < rl2;
       const unsigned mk = __ballot_sync(kFull, keep);
-      if (keep) {
-        const unsigned ent = (unsigned)(j - E.atom0) | ((unsigned)(dx + 1) << 26) | ((unsigned)(dy + 1) << 28) |
-                             ((unsigned)(dz + 1) << 30);
-        cbuf[m + __popc(mk & lt)] = make_float4(p.x, p.y, p.z, __uint_as_float(ent));
-      }
+      if (keep) cbuf[m + __popc(mk & lt)] = make_float4(p.x, p.y, p.z, __uint_as_float((unsigned)(j - E.atom0) | code));
       m += __popc(mk);
-      joff += 32;
     }
-    last = k27 >= 27;
+    last = f0 >= total;
+    const int mpad = (m + 31) & ~31;
+    if (m + lane < mpad) cbuf[m + lane] = far4;
     __syncwarp();
-    // sweep the buffer for every atom of the cell
     for (int base = 0; base < n0; base += 32) {
       const int na = n0 - base < 32 ? n0 - base : 32;
       const float4 mine = lane < na ? pb[s0 + base + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
-      for (int a = 0; a < na; ++a) {
-        const long long i = s0 + base + a;
-        const float mx = __shfl_sync(kFull, mine.x, a), my = __shfl_sync(kFull, mine.y, a),
-                    mz = __shfl_sync(kFull, mine.z, a);
-        const unsigned self = (unsigned)(i - E.atom0) | (1u << 26) | (1u << 28) | (1u << 30);
-        int cnt = first ? 0 : B.nlist[i];
-        unsigned* Li = L + i * 4;
+      const int oct = lane < na ? ((mine.x > 0.f ? 1 : 0) | (mine.y > 0.f ? 2 : 0) | (mine.z > 0.f ? 4 : 0)) : 8;
+      for (int o = 0; o < 8; ++o) {
+        unsigned mo = __ballot_sync(kFull, oct == o);
+        if (mo == 0) continue;
+        // the octant's box: the cell's box split at the centre
+        const float bxl = (o & 1) ? fmaxf(lx, 0.f) : lx, bxh = (o & 1) ? hx : fminf(hx, 0.f);
+        const float byl = (o & 2) ? fmaxf(ly, 0.f) : ly, byh = (o & 2) ? hy : fminf(hy, 0.f);
+        const float bzl = (o & 4) ? fmaxf(lz, 0.f) : lz, bzh = (o & 4) ? hz : fminf(hz, 0.f);
+        int q = 0;
+        for (int c = 0; c < mpad; c += 32) {
+          const float4 p = cbuf[c + lane];
+          const float ex = fmaxf(fmaxf(bxl - p.x, p.x - bxh), 0.0f);
+          const float ey = fmaxf(fmaxf(byl - p.y, p.y - byh), 0.0f);
+          const float ez = fmaxf(fmaxf(bzl - p.z, p.z - bzh), 0.0f);
+          const bool keep = ex * ex + ey * ey + ez * ez < rl2;
+          const unsigned mk = __ballot_sync(kFull, keep);
+          if (keep) oidx[q + __popc(mk & lt)] = (unsigned short)(c + lane);
+          q += __popc(mk);
+        }
+        const int qpad = (q + 31) & ~31;
+        if (q + lane < qpad) oidx[q + lane] = (unsigned short)kBallotCap;
+        __syncwarp();
+        while (mo) {
+          const int a = __ffs(mo) - 1;
+          mo &= mo - 1;
+          const long long i = s0 + base + a;
+          const float mx = __shfl_sync(kFull, mine.x, a), my = __shfl_sync(kFull, mine.y, a),
+                      mz = __shfl_sync(kFull, mine.z, a);
+          int cnt = first ? 0 : B.nlist[i];
+          unsigned* Li = L + i * 4;
 #pragma unroll 2
-        for (int c = 0; c < m; c += 32) {
-          const bool in = c + lane < m;
-          const float4 q = cbuf[in ? c + lane : 0];
-          const float ax = mx - q.x, ay = my - q.y, az = mz - q.z;
-          const unsigned ent = __float_as_uint(q.w);
-          const bool take = in && ax * ax + ay * ay + az * az < rl2 && ent != self;
-          const unsigned mk = __ballot_sync(kFull, take);
-          const int kk = cnt + __popc(mk & lt);
-          if (take && kk < cap) Li[(long long)(kk >> 2) * N4 + (kk & 3)] = ent;
-          cnt += __popc(mk);
-        }
-        if (last) {
-          // pad the last partial group with an entry beyond r_c
-          const int kk = cnt + lane;
-          if (cnt < cap && lane < ((4 - (cnt & 3)) & 3))
-            Li[(long long)(kk >> 2) * N4 + (kk & 3)] = pad_entry(i, E);
-          if (lane == 0) {
-            if (cnt > cap) atomicMin(&B.status[e], kStOverflow);
-            B.nlist[i] = cnt < cap ? cnt : cap;
+          for (int c = 0; c < qpad; c += 32) {
+            const float4 cq = cbuf[oidx[c + lane]];
+            const float ax = mx - cq.x, ay = my - cq.y, az = mz - cq.z;
+            const float d2 = ax * ax + ay * ay + az * az;
+            const bool take = __float_as_uint(d2) - 1u < rl2u;   // 0 < d2 < rl2
+            const unsigned mk = __ballot_sync(kFull, take);
+            const int kk = cnt + __popc(mk & lt);
+            if (take && kk < cap) Li[(long long)(kk >> 2) * N4 + (kk & 3)] = __float_as_uint(cq.w);
+            cnt += __popc(mk);
           }
-        } else if (lane == 0) {
-          B.nlist[i] = cnt;
+          if (last) {
+            // pad the last partial group with an entry beyond r_c
+            const int kk = cnt + lane;
+            if (cnt < cap && lane < ((4 - (cnt & 3)) & 3))
+              Li[(long long)(kk >> 2) * N4 + (kk & 3)] = pad_entry(i, E);
+            if (lane == 0) {
+              if (cnt > cap) atomicMin(&B.status[e], kStOverflow);
+              B.nlist[i] = cnt < cap ? cnt : cap;
+            }
+          } else if (lane == 0) {
+            B.nlist[i] = cnt;
+          }
         }
+        __syncwarp();
       }
     }
     __syncwarp();
