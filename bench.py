@@ -2,7 +2,8 @@
 
 A bench step is one pass of the whole hot path over one batch: the 64-element
 uneven batch (h ~ U[5, 20], lateral box 10-16, 500-5000 fluid atoms,
-g ~ U[0.005, 0.05], 20 000 steps each) with FP32 pair forces and FP64 state:
+g ~ U[0.005, 0.05], 20 000 steps each) with FP32 pair forces and the atom
+state in double-float (two FP32 words, ~44-bit significand):
 element build, every MD step, on-device reduction of the time-averaged flow
 rates.  Each rank runs its own batch (independent micro-elements: no
 data-path collective), so scaling is weak.
@@ -32,7 +33,8 @@ UNIT = "atom-steps/s"
 STEPS_PER_ELEMENT = 20000
 N_ELEMENTS = 64
 FP32_PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 flop x SM clock"
-ALG_FLOPS_PER_ATOM_STEP = 600.0      # 26.2 unique pairs x ~23 FP32 flops (Newton's third law)
+ALG_FLOPS_PER_ATOM_STEP = 600.0      # 26.2 unique pairs x ~23 FP32 flops (Newton's third law);
+                                     # the integration's few flops per atom are not counted
 ALG_BYTES_PER_ATOM_STEP = 96.0       # FP64 x and v read and written once per step
 CPU_SAMPLE_STEPS = 1000              # oracle steps per sampled element (~10-20 s of CPU work)
 
@@ -272,16 +274,17 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32 forces + f64 state", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32 forces + double-f32 state", "data": "synthetic",
             "config": {"workload": ("uneven batch: 64 elements, h 5-20, lateral 10-16, 500-5000 fluid atoms, "
-                                    "g 0.005-0.05, %d steps, FP32 forces + FP64 state" % steps_el)
+                                    "g 0.005-0.05, %d steps, FP32 forces + double-float state" % steps_el)
                        if args.workload == "uneven" else
                        ("stress batch: 4096 elements, h 5-40, n 0.7-0.9, 2k-32k fluid atoms, %d steps, FP32 forces "
-                        "+ FP64 state" % steps_el),
+                        "+ double-float state" % steps_el),
                        "elements": len(els), "atoms_per_rank": n_atoms, "steps_per_element": steps_el,
                        "l2": "flushed between timed iterations (256 MB write)",
                        "parallelism": "independent elements per rank" if world > 1 else "1 GPU"},
-            "roofline": {"bound": "alu", "kernel": "k_force", "achieved": achieved, "peak": fp32_peak,
+            "roofline": {"bound": "alu", "kernel": "k_step_df (pair forces + integration, one launch per step)",
+                         "achieved": achieved, "peak": fp32_peak,
                          "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
                          "peak_note": FP32_PEAK_NOTE + " (derived, max SM clock)",
                          "alg_flops_per_atom_step": ALG_FLOPS_PER_ATOM_STEP,

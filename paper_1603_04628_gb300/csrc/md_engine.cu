@@ -233,27 +233,53 @@ static void enqueue_rebuild(mdgp_ctx* ctx) {
   ctx->launches += 5;
 }
 
-static void enqueue_force(mdgp_ctx* ctx, bool energy) {
+// Pair forces of step *step_base + k (with per-atom energies if `energy`).
+static void enqueue_force(mdgp_ctx* ctx, bool energy, int k) {
   const unsigned g = grid_for(ctx->B.n_atoms, 128);
   const bool uni = ctx->P.uniform != 0;
+  cudaStream_t s = ctx->stream;
   if (ctx->precision == MDGP_PREC_FP32) {
     if (uni) {
-      if (energy) k_force<float4, float, true, true><<<g, 128, 0, ctx->stream>>>(ctx->B, ctx->P);
-      else k_force<float4, float, true, false><<<g, 128, 0, ctx->stream>>>(ctx->B, ctx->P);
+      if (energy) k_force<float4, float, true, true><<<g, 128, 0, s>>>(ctx->B, ctx->P, k);
+      else k_force<float4, float, true, false><<<g, 128, 0, s>>>(ctx->B, ctx->P, k);
     } else {
-      if (energy) k_force<float4, float, false, true><<<g, 128, 0, ctx->stream>>>(ctx->B, ctx->P);
-      else k_force<float4, float, false, false><<<g, 128, 0, ctx->stream>>>(ctx->B, ctx->P);
+      if (energy) k_force<float4, float, false, true><<<g, 128, 0, s>>>(ctx->B, ctx->P, k);
+      else k_force<float4, float, false, false><<<g, 128, 0, s>>>(ctx->B, ctx->P, k);
     }
   } else {
     if (uni) {
-      if (energy) k_force<Pos64, double, true, true><<<g, 128, 0, ctx->stream>>>(ctx->B, ctx->P);
-      else k_force<Pos64, double, true, false><<<g, 128, 0, ctx->stream>>>(ctx->B, ctx->P);
+      if (energy) k_force<Pos64, double, true, true><<<g, 128, 0, s>>>(ctx->B, ctx->P, k);
+      else k_force<Pos64, double, true, false><<<g, 128, 0, s>>>(ctx->B, ctx->P, k);
     } else {
-      if (energy) k_force<Pos64, double, false, true><<<g, 128, 0, ctx->stream>>>(ctx->B, ctx->P);
-      else k_force<Pos64, double, false, false><<<g, 128, 0, ctx->stream>>>(ctx->B, ctx->P);
+      if (energy) k_force<Pos64, double, false, true><<<g, 128, 0, s>>>(ctx->B, ctx->P, k);
+      else k_force<Pos64, double, false, false><<<g, 128, 0, s>>>(ctx->B, ctx->P, k);
     }
   }
   ctx->launches++;
+}
+
+// FP32 pair forces: one fused launch per step (forces + integration, the
+// forces kept in registers); with the frozen-wall thermostat the fused launch
+// finishes the step and sums m v_z^2 (storing the forces), and a second
+// launch applies the thermostat and starts the next step.
+static void enqueue_step_fused(mdgp_ctx* ctx, int k, bool stage1, cudaGraphConditionalHandle h = 0,
+                               int use_cond = 0) {
+  constexpr int kT = 128;
+  const unsigned g = grid_for(ctx->B.n_atoms, kT);
+  const bool uni = ctx->P.uniform != 0;
+  cudaStream_t s = ctx->stream;
+  if (ctx->params.mode == 1) {
+    const int m = kFinish | kTzSum;
+    if (uni) k_step_df<true, true, true><<<g, kT, 0, s>>>(ctx->B, ctx->P, k, m, 0, 0);
+    else k_step_df<false, true, true><<<g, kT, 0, s>>>(ctx->B, ctx->P, k, m, 0, 0);
+    ctx->launches++;
+    enqueue_integrate(ctx, k, kTzApply | (stage1 ? kStage1 : 0), h, use_cond);
+  } else {
+    const int m = kFinish | (stage1 ? kStage1 : 0);
+    if (uni) k_step_df<true, false, false><<<g, kT, 0, s>>>(ctx->B, ctx->P, k, m, h, use_cond);
+    else k_step_df<false, false, false><<<g, kT, 0, s>>>(ctx->B, ctx->P, k, m, h, use_cond);
+    ctx->launches++;
+  }
 }
 
 static void enqueue_energy(mdgp_ctx* ctx, int which) {
@@ -338,7 +364,9 @@ static int capture_steps(mdgp_ctx* ctx, long long nsteps, cudaGraphExec_t* out) 
     CK(cudaStreamGetCaptureInfo(ctx->stream, &cs, nullptr, &cg, &deps, &edges, &ndeps));
     cudaGraphConditionalHandle h;
     CK(cudaGraphConditionalHandleCreate(&h, cg, 0, cudaGraphCondAssignDefault));
-    enqueue_step_integrate(ctx, (int)k, true, h, 1);
+    const bool fused = ctx->precision == MDGP_PREC_FP32;
+    if (fused) enqueue_step_fused(ctx, (int)k, true, h, 1);
+    else enqueue_step_integrate(ctx, (int)k, true, h, 1);
     CK(cudaStreamGetCaptureInfo(ctx->stream, &cs, nullptr, &cg, &deps, &edges, &ndeps));
     cudaGraphNodeParams cp = {};
     cp.type = cudaGraphNodeTypeConditional;
@@ -354,7 +382,7 @@ static int capture_steps(mdgp_ctx* ctx, long long nsteps, cudaGraphExec_t* out) 
     enqueue_rebuild(ctx, ctx->side_stream);
     cudaGraph_t body_out;
     CK(cudaStreamEndCapture(ctx->side_stream, &body_out));
-    enqueue_force(ctx, false);
+    if (!fused) enqueue_force(ctx, false, (int)k + 1);
   }
   k_advance<<<1, 32, 0, ctx->stream>>>((long long*)ctx->d_step.ptr, nsteps);
   cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
@@ -426,7 +454,8 @@ static int plan_impl(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int list_
   if ((st = ensure(ctx, ctx->d_state, sizeof(double) * 18 * N))) return st;
   if ((st = ensure(ctx, ctx->d_ints, sizeof(int) * 8 * N))) return st;
   if ((st = ensure(ctx, ctx->d_cells, sizeof(int) * 4 * C))) return st;
-  if ((st = ensure(ctx, ctx->d_pos, psz * N))) return st;
+  const size_t npos = ctx->precision == MDGP_PREC_FP32 ? 2 : 1;
+  if ((st = ensure(ctx, ctx->d_pos, npos * psz * N))) return st;
   if ((st = ensure(ctx, ctx->d_pbuild, sizeof(float4) * N))) return st;
   if ((st = ensure(ctx, ctx->d_force, fsz * 5 * N))) return st;
   if ((st = ensure(ctx, ctx->d_list, sizeof(unsigned) * (size_t)list_cap * N))) return st;
@@ -460,7 +489,8 @@ static int plan_impl(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int list_
   B.atom_el = ip + 4 * N; B.newcell = ip + 5 * N; B.slot = ip + 6 * N; B.nlist = ip + 7 * N;
   int* cp = (int*)ctx->d_cells.ptr;
   B.cell_el = cp; B.ccount = cp + C; B.cstart = cp + 2 * C; B.csize = cp + 3 * C;
-  B.pos = ctx->d_pos.ptr;
+  B.posb[0] = ctx->d_pos.ptr;
+  B.posb[1] = (char*)ctx->d_pos.ptr + (npos - 1) * psz * N;
   B.pbuild = (float4*)ctx->d_pbuild.ptr;
   char* fb = (char*)ctx->d_force.ptr;
   B.fx = fb; B.fy = fb + fsz * N; B.fz = fb + 2 * fsz * N;
@@ -511,7 +541,13 @@ static int plan_impl(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int list_
 }
 
 // kernels in one chunk graph, rebuild bodies not counted
-static long long graph_launches(long long nsteps, int mode) { return (mode == 1 ? 3 : 2) * nsteps + 1; }
+// Kernel launches of a captured chunk of nsteps steps (rebuilds not counted):
+// FP32 one fused launch per step (two with the frozen-wall thermostat), FP64
+// integration (one or two) plus forces; one counter advance per chunk.
+static long long graph_launches(long long nsteps, int mode, int precision) {
+  const long long per = precision == MDGP_PREC_FP32 ? (mode == 1 ? 2 : 1) : (mode == 1 ? 3 : 2);
+  return per * nsteps + 1;
+}
 
 // Reset the accumulators and build the elements (lattice, anchors,
 // Maxwell-Boltzmann velocities).
@@ -542,7 +578,7 @@ static int launch_impl(mdgp_ctx* ctx) {
   int st;
   if ((st = start_batch(ctx))) return st;
   enqueue_rebuild(ctx);
-  enqueue_force(ctx, true);
+  enqueue_force(ctx, true, 0);
   enqueue_energy(ctx, kAccE0);
   const long long S = ctx->steps;
   if (S > 0) {
@@ -550,16 +586,17 @@ static int launch_impl(mdgp_ctx* ctx) {
       const long long full = S / ctx->graph_K;
       for (long long r = 0; r < full; ++r) {
         CK(cudaGraphLaunch(ctx->graph_full, ctx->stream));
-        ctx->launches += graph_launches(ctx->graph_K, ctx->params.mode);
+        ctx->launches += graph_launches(ctx->graph_K, ctx->params.mode, ctx->precision);
       }
     }
     if (ctx->graph_rem_K) {
       CK(cudaGraphLaunch(ctx->graph_rem, ctx->stream));
-      ctx->launches += graph_launches(ctx->graph_rem_K, ctx->params.mode);
+      ctx->launches += graph_launches(ctx->graph_rem_K, ctx->params.mode, ctx->precision);
     }
     // finish the last step (s = S), then the energy at the final positions
-    enqueue_step_integrate(ctx, 0, false);
-    enqueue_force(ctx, true);
+    if (ctx->precision == MDGP_PREC_FP32) enqueue_step_fused(ctx, 0, false);
+    else enqueue_step_integrate(ctx, 0, false);
+    enqueue_force(ctx, true, 0);
   }
   enqueue_energy(ctx, kAccE1);
   k_finalize<<<grid_for(ctx->n_el, 128), 128, 0, ctx->stream>>>(ctx->B, (mdgp_result*)ctx->d_results.ptr);
@@ -765,7 +802,7 @@ int mdgp_md_forces(mdgp_ctx* ctx, const mdgp_element* el, const double* x, int64
     CK(cudaMemcpyAsync(ctx->B.st[d], soa.data() + (size_t)d * n_atoms, sizeof(double) * n_atoms,
                        cudaMemcpyHostToDevice, ctx->stream));
   enqueue_rebuild(ctx);
-  enqueue_force(ctx, true);
+  enqueue_force(ctx, true, 0);
   std::vector<double> buf;
   if ((st = export_impl(ctx, 1, buf))) return st;
   int status = 0;
@@ -786,17 +823,21 @@ int mdgp_micro_profile(mdgp_ctx* ctx, int64_t steps, double* ms) {
   int st;
   if ((st = start_batch(ctx))) return st;
   enqueue_rebuild(ctx);
-  enqueue_force(ctx, false);
+  const bool fused = ctx->precision == MDGP_PREC_FP32;
+  if (!fused) enqueue_force(ctx, false, 0);
   std::vector<cudaEvent_t> ev((size_t)(3 * steps + 1));
   for (auto& e : ev) CK(cudaEventCreate(&e));
   CK(cudaEventRecord(ev[0], ctx->stream));
   for (int64_t k = 0; k < steps; ++k) {
-    // the step counter stays 0: launch k works on step k
-    enqueue_step_integrate(ctx, (int)k, true);
+    // the step counter stays 0: launch k works on step k.  FP32: the fused
+    // step (forces + integration), then the rebuild; FP64: integration,
+    // rebuild, forces of the next step.
+    if (fused) enqueue_step_fused(ctx, (int)k, true);
+    else enqueue_step_integrate(ctx, (int)k, true);
     CK(cudaEventRecord(ev[3 * k + 1], ctx->stream));
     if (k % ctx->rebuild_every == 0) enqueue_rebuild(ctx);
     CK(cudaEventRecord(ev[3 * k + 2], ctx->stream));
-    enqueue_force(ctx, false);
+    if (!fused) enqueue_force(ctx, false, (int)k + 1);
     CK(cudaEventRecord(ev[3 * k + 3], ctx->stream));
   }
   CK(cudaStreamSynchronize(ctx->stream));
@@ -812,8 +853,13 @@ int mdgp_micro_profile(mdgp_ctx* ctx, int64_t steps, double* ms) {
     if (k % ctx->rebuild_every == 0) { t_reb += b; ++nreb; }
   }
   for (auto& e : ev) cudaEventDestroy(e);
-  ms[0] = t_int / steps;
-  ms[1] = t_force / steps;
+  if (fused) {
+    ms[0] = 0.0;
+    ms[1] = t_int / steps;
+  } else {
+    ms[0] = t_int / steps;
+    ms[1] = t_force / steps;
+  }
   ms[2] = nreb ? t_reb / nreb : 0.0;
   ms[3] = (double)ctx->n_atoms;
   ms[4] = (double)ctx->B.n_cells;

@@ -105,7 +105,9 @@ struct BatchDev {
   int *orig, *cell, *orig2, *cell2;
   int* atom_el;                // fixed: elements keep their atom ranges
   int* cell_el;
-  void* pos;                   // float4 or double4 [n_atoms]
+  void* posb[2];               // pair-force input positions, float4 or Pos64 [n_atoms]:
+                               // the forces of step s read posb[s & 1] (FP32: two
+                               // buffers; FP64: both point to one)
   float4* pbuild;              // pos at the last rebuild
   void *fx, *fy, *fz, *wxx, *epot;
   int *ccount, *cstart, *csize;   // [n_cells]

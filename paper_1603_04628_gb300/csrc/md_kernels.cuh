@@ -87,12 +87,13 @@ __device__ __forceinline__ void seg_add(int key, const double (&val)[NV], DstFn 
   }
 }
 
-// Block-level segmented reduction for 256-thread blocks: every thread puts
-// (key, NV values) into shared memory.  When the whole block shares one key
-// (the usual case: atoms of one element are contiguous) a shared-memory tree
-// adds the values with 255 FP64 adds per value and one atomicAdd; otherwise
-// 8 threads each scan 32 entries and add each run of equal keys.  Keys < 0
-// are skipped.  All threads of the block must call it.
+// Block-level segmented reduction for blocks of up to 256 threads (a power
+// of two): every thread puts (key, NV values) into shared memory.  When the
+// whole block shares one key (the usual case: atoms of one element are
+// contiguous) a shared-memory tree adds the values with one FP64 add per
+// thread and value and one atomicAdd; otherwise up to 8 threads each scan
+// 32 entries and add each run of equal keys.  Keys < 0 are skipped.  All
+// threads of the block must call it.
 template <int NV, typename DstFn>
 __device__ __forceinline__ void block_seg_add(int key, const double (&val)[NV], DstFn dst) {
   __shared__ int skey[256];
@@ -105,7 +106,7 @@ __device__ __forceinline__ void block_seg_add(int key, const double (&val)[NV], 
   const int k0 = skey[0];
   if (__syncthreads_and(key == k0)) {
     if (k0 < 0) return;
-    for (int h = 128; h > 0; h >>= 1) {
+    for (int h = (int)blockDim.x >> 1; h > 0; h >>= 1) {
       if (t < h)
 #pragma unroll
         for (int i = 0; i < NV; ++i) sval[i][t] += sval[i][t + h];
@@ -114,12 +115,12 @@ __device__ __forceinline__ void block_seg_add(int key, const double (&val)[NV], 
     if (t < NV) atomicAdd(dst(k0, t), sval[t][0]);
     return;
   }
-  if (t < 8) {
+  if (t * 32 < (int)blockDim.x) {
     int cur = -1;
     double acc[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i) acc[i] = 0.0;
-    for (int r = t * 32; r < t * 32 + 32; ++r) {
+    for (int r = t * 32; r < t * 32 + 32 && r < (int)blockDim.x; ++r) {
       const int k = skey[r];
       if (k != cur) {
         if (cur >= 0)
@@ -490,13 +491,18 @@ __global__ void __launch_bounds__(256) k_permute(BatchDev B) {
     st_put<DF>(B.st2[0], dst, ox); st_put<DF>(B.st2[1], dst, oy); st_put<DF>(B.st2[2], dst, oz);
     st_put<DF>(B.st2[6], dst, ax); st_put<DF>(B.st2[7], dst, ay); st_put<DF>(B.st2[8], dst, az);
     fx = (float)ox; fy = (float)oy; fz = (float)oz;
-    if constexpr (!DF) static_cast<Pos64*>(B.pos)[dst] = Pos64{ox, oy, oz, wall ? 1.0 : 0.0};
+    if constexpr (!DF) static_cast<Pos64*>(B.posb[0])[dst] = Pos64{ox, oy, oz, wall ? 1.0 : 0.0};
   }
   // velocities move as raw 8-byte words in either representation
   B.st2[3][dst] = B.st[3][i]; B.st2[4][dst] = B.st[4][i]; B.st2[5][dst] = B.st[5][i];
   B.orig2[dst] = l;
   B.cell2[dst] = c;
-  if constexpr (DF) static_cast<float4*>(B.pos)[dst] = make_float4(fx, fy, fz, wall ? 1.0f : 0.0f);
+  if constexpr (DF) {
+    // both buffers: the next force evaluation reads one of them
+    const float4 q = make_float4(fx, fy, fz, wall ? 1.0f : 0.0f);
+    static_cast<float4*>(B.posb[0])[dst] = q;
+    static_cast<float4*>(B.posb[1])[dst] = q;
+  }
   B.pbuild[dst] = make_float4(fx, fy, fz, 0.0f);
 }
 
@@ -521,6 +527,14 @@ __device__ __forceinline__ unsigned pad_entry(long long i, const ElemDev& E) {
   return (unsigned)(i - E.atom0) | (2u << 26) | (1u << 28) | (1u << 30);
 }
 
+// Positions a list build reads: the rebuild-time copy (float4) or the single
+// FP64 buffer.
+template <typename PT>
+__device__ __forceinline__ const PT* build_positions(const BatchDev& B) {
+  if constexpr (sizeof(PT) == 16) return reinterpret_cast<const PT*>(B.pbuild);
+  else return static_cast<const PT*>(B.posb[0]);
+}
+
 template <typename PT>
 __global__ void __launch_bounds__(128) k_build(BatchDev B, PhysDev P) {
   using T = decltype(PT::x);
@@ -534,7 +548,7 @@ __global__ void __launch_bounds__(128) k_build(BatchDev B, PhysDev P) {
   cell_coords(E, warp, cx, cy, cz);
   const int ncx = E.nc[0], ncy = E.nc[1], ncz = E.nc[2];
   const int s0 = B.cstart[warp], n0 = B.csize[warp];
-  const PT* pos = static_cast<const PT*>(B.pos);
+  const PT* pos = build_positions<PT>(B);
   const T rl2 = sizeof(T) == 4 ? (T)P.rl2f : (T)P.rl2;
   const long long N = B.n_atoms;
   uint4* L4 = reinterpret_cast<uint4*>(B.list);
@@ -649,7 +663,7 @@ __global__ void __launch_bounds__(128) k_build_staged(BatchDev B, PhysDev P, int
   const int ncx = E.nc[0], ncy = E.nc[1], ncz = E.nc[2];
   const int col = (int)(colg - B.col_off[e]);
   const int cx = col / ncy, cy = col % ncy;
-  const PT* gpos = static_cast<const PT*>(B.pos);
+  const PT* gpos = build_positions<PT>(B);
   if (tid == 0) {
     int total = 0;
     for (int k = 0; k < 9; ++k) {
@@ -1007,12 +1021,12 @@ struct PairAcc {
   }
 };
 
+// Pair forces on atom i over its list, positions from pos (this step's
+// buffer); spi = the atom's species.
 template <typename PT, typename T, bool UNIFORM, bool ENERGY>
-__global__ void __launch_bounds__(128) k_force(BatchDev B, PhysDev P) {
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= B.n_atoms) return;
+__device__ __forceinline__ PairAcc<PT, T, UNIFORM, ENERGY> pair_force(const BatchDev& B, const PhysDev& P,
+                                                                      long long i, const PT* pos, int& spi) {
   const ElemDev& E = B.el[B.atom_el[i]];
-  const PT* pos = static_cast<const PT*>(B.pos);
   const PT me = pos[i];
   const T csx = (T)E.cs[0], csy = (T)E.cs[1], csz = (T)E.cs[2];
   const PT* posj = pos + E.atom0;
@@ -1026,7 +1040,7 @@ __global__ void __launch_bounds__(128) k_force(BatchDev B, PhysDev P) {
     rc2 = P.rc2;
     for (int t = 0; t < 3; ++t) { eps[t] = P.eps[t]; sig2[t] = P.sig2[t]; }
   }
-  const int spi = me.w != (T)0 ? 1 : 0;
+  spi = me.w != (T)0 ? 1 : 0;
   PairAcc<PT, T, UNIFORM, ENERGY> acc;
   const uint4* L4 = reinterpret_cast<const uint4*>(B.list) + i;
   const int ng = (n + 3) >> 2;
@@ -1054,6 +1068,18 @@ __global__ void __launch_bounds__(128) k_force(BatchDev B, PhysDev P) {
     acc.add(me, o2, e.z, csx, csy, csz, spi, rc2, eps, sig2, P);
     acc.add(me, o3, e.w, csx, csy, csz, spi, rc2, eps, sig2, P);
   }
+  return acc;
+}
+
+// Pair forces of step *step_base + k into fx, fy, fz (+ virial share, energy).
+template <typename PT, typename T, bool UNIFORM, bool ENERGY>
+__global__ void __launch_bounds__(128) k_force(BatchDev B, PhysDev P, int k) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= B.n_atoms) return;
+  const long long s = *B.step_base + k;
+  int spi;
+  const PairAcc<PT, T, UNIFORM, ENERGY> acc =
+      pair_force<PT, T, UNIFORM, ENERGY>(B, P, i, static_cast<const PT*>(B.posb[s & 1]), spi);
   static_cast<T*>(B.fx)[i] = acc.fx;
   static_cast<T*>(B.fy)[i] = acc.fy;
   static_cast<T*>(B.fz)[i] = acc.fz;
@@ -1176,9 +1202,9 @@ __global__ void __launch_bounds__(256) k_integrate(BatchDev B, PhysDev P, int k,
       const float xf = (float)x, yf = (float)y, zf = (float)z;
       if (!(fabsf(yf) < 1e6f) || !(fabsf(xf) < 1e6f) || !(fabsf(zf) < 1e6f)) atomicMin(&B.status[e], kStUnstable);
       if constexpr (sizeof(PT) == 16) {
-        static_cast<float4*>(B.pos)[i] = make_float4(xf, yf, zf, fluid ? 0.0f : 1.0f);
+        static_cast<float4*>(B.posb[0])[i] = make_float4(xf, yf, zf, fluid ? 0.0f : 1.0f);
       } else {
-        static_cast<Pos64*>(B.pos)[i] = Pos64{x, y, z, fluid ? 0.0 : 1.0};
+        static_cast<Pos64*>(B.posb[0])[i] = Pos64{x, y, z, fluid ? 0.0 : 1.0};
       }
       // an atom that moved more than half the skin since the lists were
       // built asks for a rebuild before the next force evaluation
@@ -1260,129 +1286,141 @@ __device__ __forceinline__ void block_seg_add_f(int key, const float (&val)[NV],
 // The integration step with the double-float state (FP32 pair forces): the
 // same phases and formulas as k_integrate, every update in FP32 operations.
 // Per-atom measurement terms are formed in FP32 and summed per warp in FP32,
-// then across warps, blocks and steps in FP64.
-template <bool FROZEN>
-__global__ void __launch_bounds__(256) k_integrate_df(BatchDev B, PhysDev P, int k, int mode,
-                                                      cudaGraphConditionalHandle hcond, int use_cond) {
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const long long s = *B.step_base + k;
+// then across warps, blocks and steps in FP64.  Positions are double
+// buffered: the pair forces of step s read posb[s & 1], and the launch that
+// runs stage 1 of step s writes every atom's new position to
+// posb[(s + 1) & 1] (moved or not), so a fused kernel can read one buffer
+// while it writes the other.
+struct StepOut {
   int mkey = -1, tzkey = -1;
-  float mval[3] = {0.f, 0.f, 0.f}, tzval[1] = {0.f};
-  if (i < B.n_atoms) {
-    const int e = B.atom_el[i];
-    const ElemDev& E = B.el[e];
-    const int l = B.orig[i];
-    const bool fluid = l < E.nf;
-    const bool frozen = FROZEN && !fluid;
-    const bool stepped = s >= 1 && s - 1 < E.steps_total;
-    const bool starting = s < E.steps_total;
-    const bool fin = (mode & kFinish) && stepped;
-    const bool st1 = (mode & kStage1) && starting;
-    const long long ks = s - 1 - E.steps_eq;
-    const bool sample = stepped && ks >= 0 && ks < E.steps_sample && E.nb > 0 &&
-                        ((mode & kTzApply) || ((mode & kFinish) && !(mode & kTzSum)));
-    dfl x = df_ld(B.st[0], i), y = df_ld(B.st[1], i), z = df_ld(B.st[2], i);
-    dfl vx = df_ld(B.st[3], i), vy = df_ld(B.st[4], i), vz = df_ld(B.st[5], i);
-    float fx = static_cast<const float*>(B.fx)[i];
-    float fy = static_cast<const float*>(B.fy)[i];
-    float fz = static_cast<const float*>(B.fz)[i];
-    const float h = P.hdt_mf, dt = P.dtf;
-    bool moved = false;
-    if (fluid) {
-      // the body force enters as its own kick, dt/(2m) g, so that it is not
-      // rounded against the much larger pair force
-      const float gk = E.g_kick;
-      float lam = 1.0f;
-      if (FROZEN && (mode & kTzApply) && E.nf > 0) {
-        const float tzm = (float)B.tz[2 * e + ((s - 1) & 1)] / (float)E.nf;
-        if (tzm > 0.0f) lam = sqrtf(1.0f + P.dt_tauf * (E.Tf / tzm - 1.0f));
-      }
-      if (sample) {
-        const bool have_full = !(mode & kFinish);
-        const float wx = have_full ? vx.hi + vx.lo : vx.hi + (vx.lo + (__fmul_rn(h, fx) + gk));
-        const float wy = have_full ? vy.hi + vy.lo : vy.hi + __fmaf_rn(h, fy, vy.lo);
-        float wz = have_full ? vz.hi + vz.lo : vz.hi + __fmaf_rn(h, fz, vz.lo);
-        wz *= lam;
-        mval[0] = P.massf * wx;
-        mval[1] = P.massf * wx * wx + static_cast<const float*>(B.wxx)[i];
-        mval[2] = P.massf * (wx * wx + wy * wy + wz * wz);
-      }
-      const float hfx = __fmul_rn(h, fx), hfy = __fmul_rn(h, fy), hfz = __fmul_rn(h, fz);
-      if (FROZEN && (mode & (kTzSum | kTzApply))) {
-        if (fin) { vx = df_add(df_add(vx, hfx), gk); vy = df_add(vy, hfy); vz = df_add(vz, hfz); }
-        if ((mode & kTzSum) && stepped) tzval[0] = P.massf * vz.hi * vz.hi;
-        if ((mode & kTzApply) && stepped) vz = df_mul(lam, vz);
-        if (st1) {
-          vx = df_add(df_add(vx, hfx), gk); vy = df_add(vy, hfy); vz = df_add(vz, hfz);
-          moved = true;
-        }
-      } else {
-        // both half kicks of a fused launch use the same force
-        const int kicks = (fin ? 1 : 0) + (st1 ? 1 : 0);
-        if (kicks > 0) {
-          const float kf = (float)kicks;
-          vx = df_add(df_add(vx, __fmul_rn(kf, hfx)), __fmul_rn(kf, gk));
-          vy = df_add(vy, __fmul_rn(kf, hfy));
-          vz = df_add(vz, __fmul_rn(kf, hfz));
-        }
-        moved = st1;
-      }
-      if (moved) {
-        x = df_add(x, df_mul(dt, vx)); y = df_add(y, df_mul(dt, vy)); z = df_add(z, df_mul(dt, vz));
-      }
-    } else if (!frozen) {
-      fx = __fmaf_rn(-P.k_tetherf, df_diff(x, df_ld(B.st[6], i)), fx);
-      fy = __fmaf_rn(-P.k_tetherf, df_diff(y, df_ld(B.st[7], i)), fy);
-      fz = __fmaf_rn(-P.k_tetherf, df_diff(z, df_ld(B.st[8], i)), fz);
-      if (fin) { vx = df_add(vx, __fmul_rn(h, fx)); vy = df_add(vy, __fmul_rn(h, fy)); vz = df_add(vz, __fmul_rn(h, fz)); }
+  float mval[3] = {0.f, 0.f, 0.f};
+  float tz[1] = {0.f};
+};
+
+template <bool FROZEN>
+__device__ __forceinline__ void integrate_df_atom(const BatchDev& B, const PhysDev& P, long long i, long long s,
+                                                  int mode, int use_cond, float fx, float fy, float fz, float wxx,
+                                                  StepOut& o) {
+  const int e = B.atom_el[i];
+  const ElemDev& E = B.el[e];
+  const int l = B.orig[i];
+  const bool fluid = l < E.nf;
+  const bool frozen = FROZEN && !fluid;
+  const bool stepped = s >= 1 && s - 1 < E.steps_total;
+  const bool starting = s < E.steps_total;
+  const bool fin = (mode & kFinish) && stepped;
+  const bool st1 = (mode & kStage1) && starting;
+  const long long ks = s - 1 - E.steps_eq;
+  const bool sample = stepped && ks >= 0 && ks < E.steps_sample && E.nb > 0 &&
+                      ((mode & kTzApply) || ((mode & kFinish) && !(mode & kTzSum)));
+  dfl x = df_ld(B.st[0], i), y = df_ld(B.st[1], i), z = df_ld(B.st[2], i);
+  dfl vx = df_ld(B.st[3], i), vy = df_ld(B.st[4], i), vz = df_ld(B.st[5], i);
+  const float h = P.hdt_mf, dt = P.dtf;
+  bool moved = false;
+  if (fluid) {
+    // the body force enters as its own kick, dt/(2m) g, so that it is not
+    // rounded against the much larger pair force
+    const float gk = E.g_kick;
+    float lam = 1.0f;
+    if (FROZEN && (mode & kTzApply) && E.nf > 0) {
+      const float tzm = (float)B.tz[2 * e + ((s - 1) & 1)] / (float)E.nf;
+      if (tzm > 0.0f) lam = sqrtf(1.0f + P.dt_tauf * (E.Tf / tzm - 1.0f));
+    }
+    if (sample) {
+      const bool have_full = !(mode & kFinish);
+      const float wx = have_full ? vx.hi + vx.lo : vx.hi + (vx.lo + (__fmul_rn(h, fx) + gk));
+      const float wy = have_full ? vy.hi + vy.lo : vy.hi + __fmaf_rn(h, fy, vy.lo);
+      float wz = have_full ? vz.hi + vz.lo : vz.hi + __fmaf_rn(h, fz, vz.lo);
+      wz *= lam;
+      o.mval[0] = P.massf * wx;
+      o.mval[1] = P.massf * wx * wx + wxx;
+      o.mval[2] = P.massf * (wx * wx + wy * wy + wz * wz);
+    }
+    const float hfx = __fmul_rn(h, fx), hfy = __fmul_rn(h, fy), hfz = __fmul_rn(h, fz);
+    if (FROZEN && (mode & (kTzSum | kTzApply))) {
+      if (fin) { vx = df_add(df_add(vx, hfx), gk); vy = df_add(vy, hfy); vz = df_add(vz, hfz); }
+      if ((mode & kTzSum) && stepped) o.tz[0] = P.massf * vz.hi * vz.hi;
+      if ((mode & kTzApply) && stepped) vz = df_mul(lam, vz);
       if (st1) {
-        float b0 = 0.f, b1 = 0.f, b2 = 0.f;
-        if (E.beta_sdf > 0.f) {
-          normals3f((uint32_t)l, (uint32_t)s, (uint32_t)E.id, 1u, E.seed, b0, b1, b2);
-          b0 *= E.beta_sdf; b1 *= E.beta_sdf; b2 *= E.beta_sdf;
-        }
-        // G-JF: x += b dt (v + dt/(2m) f + beta/(2m)); v = a v + a dt/(2m) f + (b/m) beta
-        const float bdt = P.gjf_bf * dt, i2m = 0.5f * P.inv_mf, bm = P.gjf_bf * P.inv_mf, a = P.gjf_af;
-        const float px = __fmaf_rn(h, fx, b0 * i2m), py = __fmaf_rn(h, fy, b1 * i2m), pz = __fmaf_rn(h, fz, b2 * i2m);
-        x = df_add(x, df_mul(bdt, df_add(vx, px)));
-        y = df_add(y, df_mul(bdt, df_add(vy, py)));
-        z = df_add(z, df_mul(bdt, df_add(vz, pz)));
-        vx = df_add(df_mul(a, vx), __fmaf_rn(h * a, fx, bm * b0));
-        vy = df_add(df_mul(a, vy), __fmaf_rn(h * a, fy, bm * b1));
-        vz = df_add(df_mul(a, vz), __fmaf_rn(h * a, fz, bm * b2));
+        vx = df_add(df_add(vx, hfx), gk); vy = df_add(vy, hfy); vz = df_add(vz, hfz);
         moved = true;
       }
     } else {
-      vx = vy = vz = dfl{0.f, 0.f};
-    }
-    if (sample || (FROZEN && (mode & kTzSum) && stepped)) {
-      mkey = e * kMaxBlocks + (int)(sample ? (ks * E.nb) / E.steps_sample : 0);
-      tzkey = e;
+      // both half kicks of a fused launch use the same force
+      const int kicks = (fin ? 1 : 0) + (st1 ? 1 : 0);
+      if (kicks > 0) {
+        const float kf = (float)kicks;
+        vx = df_add(df_add(vx, __fmul_rn(kf, hfx)), __fmul_rn(kf, gk));
+        vy = df_add(vy, __fmul_rn(kf, hfy));
+        vz = df_add(vz, __fmul_rn(kf, hfz));
+      }
+      moved = st1;
     }
     if (moved) {
-      df_st(B.st[0], i, x); df_st(B.st[1], i, y); df_st(B.st[2], i, z);
-      const float xf = x.hi, yf = y.hi, zf = z.hi;
-      if (!(fabsf(yf) < 1e6f) || !(fabsf(xf) < 1e6f) || !(fabsf(zf) < 1e6f)) atomicMin(&B.status[e], kStUnstable);
-      static_cast<float4*>(B.pos)[i] = make_float4(xf, yf, zf, fluid ? 0.0f : 1.0f);
-      const float4 pb = B.pbuild[i];
-      const float ex = xf - pb.x, ey = yf - pb.y, ez = zf - pb.z;
-      if (ex * ex + ey * ey + ez * ez > P.half_skin2f) {
-        if (use_cond) atomicOr(&B.flags[0], 1);
-        else atomicMin(&B.status[e], kStSkin);
-      }
+      x = df_add(x, df_mul(dt, vx)); y = df_add(y, df_mul(dt, vy)); z = df_add(z, df_mul(dt, vz));
     }
-    df_st(B.st[3], i, vx); df_st(B.st[4], i, vy); df_st(B.st[5], i, vz);
+  } else if (!frozen) {
+    fx = __fmaf_rn(-P.k_tetherf, df_diff(x, df_ld(B.st[6], i)), fx);
+    fy = __fmaf_rn(-P.k_tetherf, df_diff(y, df_ld(B.st[7], i)), fy);
+    fz = __fmaf_rn(-P.k_tetherf, df_diff(z, df_ld(B.st[8], i)), fz);
+    if (fin) { vx = df_add(vx, __fmul_rn(h, fx)); vy = df_add(vy, __fmul_rn(h, fy)); vz = df_add(vz, __fmul_rn(h, fz)); }
+    if (st1) {
+      float b0 = 0.f, b1 = 0.f, b2 = 0.f;
+      if (E.beta_sdf > 0.f) {
+        normals3f((uint32_t)l, (uint32_t)s, (uint32_t)E.id, 1u, E.seed, b0, b1, b2);
+        b0 *= E.beta_sdf; b1 *= E.beta_sdf; b2 *= E.beta_sdf;
+      }
+      // G-JF: x += b dt (v + dt/(2m) f + beta/(2m)); v = a v + a dt/(2m) f + (b/m) beta
+      const float bdt = P.gjf_bf * dt, i2m = 0.5f * P.inv_mf, bm = P.gjf_bf * P.inv_mf, a = P.gjf_af;
+      const float px = __fmaf_rn(h, fx, b0 * i2m), py = __fmaf_rn(h, fy, b1 * i2m), pz = __fmaf_rn(h, fz, b2 * i2m);
+      x = df_add(x, df_mul(bdt, df_add(vx, px)));
+      y = df_add(y, df_mul(bdt, df_add(vy, py)));
+      z = df_add(z, df_mul(bdt, df_add(vz, pz)));
+      vx = df_add(df_mul(a, vx), __fmaf_rn(h * a, fx, bm * b0));
+      vy = df_add(df_mul(a, vy), __fmaf_rn(h * a, fy, bm * b1));
+      vz = df_add(df_mul(a, vz), __fmaf_rn(h * a, fz, bm * b2));
+      moved = true;
+    }
+  } else {
+    vx = vy = vz = dfl{0.f, 0.f};
   }
+  if (sample || (FROZEN && (mode & kTzSum) && stepped)) {
+    o.mkey = e * kMaxBlocks + (int)(sample ? (ks * E.nb) / E.steps_sample : 0);
+    o.tzkey = e;
+  }
+  if (moved) {
+    df_st(B.st[0], i, x); df_st(B.st[1], i, y); df_st(B.st[2], i, z);
+    const float xf = x.hi, yf = y.hi, zf = z.hi;
+    if (!(fabsf(yf) < 1e6f) || !(fabsf(xf) < 1e6f) || !(fabsf(zf) < 1e6f)) atomicMin(&B.status[e], kStUnstable);
+    const float4 pb = B.pbuild[i];
+    const float ex = xf - pb.x, ey = yf - pb.y, ez = zf - pb.z;
+    if (ex * ex + ey * ey + ez * ez > P.half_skin2f) {
+      if (use_cond) atomicOr(&B.flags[0], 1);
+      else atomicMin(&B.status[e], kStSkin);
+    }
+  }
+  if (mode & kStage1) static_cast<float4*>(B.posb[(s + 1) & 1])[i] = make_float4(x.hi, y.hi, z.hi, fluid ? 0.0f : 1.0f);
+  df_st(B.st[3], i, vx); df_st(B.st[4], i, vy); df_st(B.st[5], i, vz);
+}
+
+// Block reductions of the step's measurement terms and, with use_cond, the
+// rebuild condition: the last block to finish turns the skin flag into the
+// graph condition (one caller of cudaGraphSetConditional) and clears the
+// flag words.  All threads of the block call it.
+template <bool FROZEN>
+__device__ __forceinline__ void integrate_df_epilogue(const BatchDev& B, long long s, int mode, const StepOut& o,
+                                                      cudaGraphConditionalHandle hcond, int use_cond) {
   if (FROZEN && (mode & kTzSum)) {
     const int slot = (int)((s - 1) & 1);
-    block_seg_add_f<1>(tzkey, tzval, [&](int e, int) { return B.tz + 2 * e + slot; });
+    block_seg_add_f<1>(o.tzkey, o.tz, [&](int e, int) { return B.tz + 2 * e + slot; });
   }
   if (FROZEN && (mode & kTzApply)) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long tcount = (long long)gridDim.x * blockDim.x;
     for (long long t = i; t < B.n_el; t += tcount) B.tz[2 * t + (s & 1)] = 0.0;
   }
   if ((mode & kTzApply) || ((mode & kFinish) && !(mode & kTzSum))) {
-    block_seg_add_f<3>(mkey, mval, [&](int kk, int q) {
+    block_seg_add_f<3>(o.mkey, o.mval, [&](int kk, int q) {
       const int e = kk / kMaxBlocks, b = kk % kMaxBlocks;
       return B.acc + (size_t)e * kAccStride + (q == 0 ? kAccQ + b : (q == 1 ? kAccP + b : kAccT));
     });
@@ -1399,6 +1437,46 @@ __global__ void __launch_bounds__(256) k_integrate_df(BatchDev B, PhysDev P, int
       }
     }
   }
+}
+
+template <bool FROZEN>
+__global__ void __launch_bounds__(256) k_integrate_df(BatchDev B, PhysDev P, int k, int mode,
+                                                      cudaGraphConditionalHandle hcond, int use_cond) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long s = *B.step_base + k;
+  StepOut o;
+  if (i < B.n_atoms)
+    integrate_df_atom<FROZEN>(B, P, i, s, mode, use_cond, static_cast<const float*>(B.fx)[i],
+                              static_cast<const float*>(B.fy)[i], static_cast<const float*>(B.fz)[i],
+                              static_cast<const float*>(B.wxx)[i], o);
+  integrate_df_epilogue<FROZEN>(B, s, mode, o, hcond, use_cond);
+}
+
+// One whole MD step per launch with the double-float state: the pair forces
+// of step s (positions posb[s & 1]) and, in the same thread, the integration
+// phases in `mode` with them (finish step s-1, stage 1 of step s writing
+// posb[(s + 1) & 1]).  The forces stay in registers unless STORE (the
+// frozen-wall thermostat path, whose second launch needs them).
+template <bool UNIFORM, bool FROZEN, bool STORE>
+__global__ void __launch_bounds__(128) k_step_df(BatchDev B, PhysDev P, int k, int mode,
+                                                 cudaGraphConditionalHandle hcond, int use_cond) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long s = *B.step_base + k;
+  StepOut o;
+  if (i < B.n_atoms) {
+    const float4* pos = static_cast<const float4*>(B.posb[s & 1]);
+    int spi;
+    const PairAcc<float4, float, UNIFORM, false> f = pair_force<float4, float, UNIFORM, false>(B, P, i, pos, spi);
+    const float wxx = spi == 0 ? 0.5f * f.w : 0.0f;
+    if (STORE) {
+      static_cast<float*>(B.fx)[i] = f.fx;
+      static_cast<float*>(B.fy)[i] = f.fy;
+      static_cast<float*>(B.fz)[i] = f.fz;
+      static_cast<float*>(B.wxx)[i] = wxx;
+    }
+    integrate_df_atom<FROZEN>(B, P, i, s, mode, use_cond, f.fx, f.fy, f.fz, wxx, o);
+  }
+  integrate_df_epilogue<FROZEN>(B, s, mode, o, hcond, use_cond);
 }
 
 // Total energy per element (kinetic + shifted LJ + tether) into acc[which].
