@@ -114,6 +114,11 @@ typedef struct {
                            atoms), 2 = warp ballots over bounding-box-culled candidates
                            (lanes over candidates; default).  All three give each atom the
                            same set of neighbours within r_c + skin. */
+  int32_t persistent;   /* FP32 pair forces: 1 = the step loop is one persistent cooperative
+                           kernel per list-rebuild interval (steps separated by a grid barrier,
+                           inside a graph WHILE loop; default), 0 = one launch per step with a
+                           conditional rebuild after each.  FP64 pair forces always use the
+                           latter.  Same results either way. */
 } mdgp_md_params;
 
 /* Fill *out with the defaults listed above.  Returns MDGP_E_ARG on null. */

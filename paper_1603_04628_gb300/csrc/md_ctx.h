@@ -19,6 +19,7 @@ struct mdgp_ctx {
   cudaStream_t stream = nullptr;      // stream all work is enqueued on
   cudaStream_t own_stream = nullptr;  // created with the context
   cudaStream_t side_stream = nullptr; // captures the conditional rebuild bodies
+  cudaStream_t side_stream2 = nullptr;  // nested capture (rebuild inside the step loop's WHILE body)
   char err[256] = {0};
   // MD batch
   bool planned = false;
@@ -29,6 +30,8 @@ struct mdgp_ctx {
   int stage_bytes = 0;      // dynamic shared memory of the staged list build
   long long graph_K = 0, graph_rem_K = 0;
   cudaGraphExec_t graph_full = nullptr, graph_rem = nullptr;
+  cudaGraphExec_t graph_while = nullptr;  // persistent step loop (FP32 pair forces)
+  unsigned persist_grid = 0;              // co-resident blocks of the persistent step kernel
   long long launches = 0;              // kernels enqueued by the last launch (graph bodies: 2 per step)
   long long launches_with_rebuilds = 0;  // ... plus the rebuild kernels that ran
   long long rebuilds = 0;

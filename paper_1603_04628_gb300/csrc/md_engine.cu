@@ -345,6 +345,7 @@ __global__ void k_finalize(BatchDev B, mdgp_result* out) {
 static void drop_graphs(mdgp_ctx* ctx) {
   if (ctx->graph_full) { cudaGraphExecDestroy(ctx->graph_full); ctx->graph_full = nullptr; }
   if (ctx->graph_rem) { cudaGraphExecDestroy(ctx->graph_rem); ctx->graph_rem = nullptr; }
+  if (ctx->graph_while) { cudaGraphExecDestroy(ctx->graph_while); ctx->graph_while = nullptr; }
   ctx->graph_K = ctx->graph_rem_K = 0;
 }
 
@@ -388,6 +389,76 @@ static int capture_steps(mdgp_ctx* ctx, long long nsteps, cudaGraphExec_t* out) 
   cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
   if (e != cudaSuccess) return set_err(ctx, e);
   e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  return set_err(ctx, e);
+}
+
+// Persistent step loop (FP32 pair forces): a graph with one WHILE node
+// whose body is [cooperative k_steps_persist launch] -> IF (rebuild) {the 5
+// rebuild kernels}.  The step kernel runs steps until the lists need a
+// rebuild or all S steps have been started, and sets both conditions.
+static int capture_while(mdgp_ctx* ctx, cudaGraphExec_t* out) {
+  cudaGraph_t g = nullptr;
+  CK(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle hw;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&hw, g, 1, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams wp = {};
+  wp.type = cudaGraphNodeTypeConditional;
+  wp.conditional.handle = hw;
+  wp.conditional.type = cudaGraphCondTypeWhile;
+  wp.conditional.size = 1;
+  cudaGraphNode_t wnode;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&wnode, g, nullptr, nullptr, 0, &wp);
+  if (e != cudaSuccess) { cudaGraphDestroy(g); return set_err(ctx, e); }
+  cudaGraph_t body = wp.conditional.phGraph_out[0];
+  cudaGraphConditionalHandle hr;
+  e = cudaGraphConditionalHandleCreate(&hr, body, 0, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess)
+    e = cudaStreamBeginCaptureToGraph(ctx->side_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) { cudaGraphDestroy(g); return set_err(ctx, e); }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ctx->persist_grid);
+  cfg.blockDim = dim3(128);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = ctx->side_stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const bool uni = ctx->P.uniform != 0, frozen = ctx->params.mode == 1;
+  const long long S = ctx->steps;
+  if (uni && !frozen) e = cudaLaunchKernelEx(&cfg, k_steps_persist<true, false>, ctx->B, ctx->P, S, hr, hw);
+  else if (!uni && !frozen) e = cudaLaunchKernelEx(&cfg, k_steps_persist<false, false>, ctx->B, ctx->P, S, hr, hw);
+  else if (uni) e = cudaLaunchKernelEx(&cfg, k_steps_persist<true, true>, ctx->B, ctx->P, S, hr, hw);
+  else e = cudaLaunchKernelEx(&cfg, k_steps_persist<false, true>, ctx->B, ctx->P, S, hr, hw);
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t cg;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* edges = nullptr;
+  size_t ndeps = 0;
+  if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(ctx->side_stream, &cs, nullptr, &cg, &deps, &edges, &ndeps);
+  cudaGraphNodeParams ip = {};
+  ip.type = cudaGraphNodeTypeConditional;
+  ip.conditional.handle = hr;
+  ip.conditional.type = cudaGraphCondTypeIf;
+  ip.conditional.size = 1;
+  cudaGraphNode_t inode;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&inode, cg, deps, edges, ndeps, &ip);
+  if (e == cudaSuccess)
+    e = cudaStreamUpdateCaptureDependencies(ctx->side_stream, &inode, nullptr, 1, cudaStreamSetCaptureDependencies);
+  if (e == cudaSuccess)
+    e = cudaStreamBeginCaptureToGraph(ctx->side_stream2, ip.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    enqueue_rebuild(ctx, ctx->side_stream2);
+    cudaGraph_t tmp;
+    e = cudaStreamEndCapture(ctx->side_stream2, &tmp);
+  }
+  cudaGraph_t tmp2;
+  const cudaError_t e2 = cudaStreamEndCapture(ctx->side_stream, &tmp2);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
   cudaGraphDestroy(g);
   return set_err(ctx, e);
 }
@@ -465,7 +536,7 @@ static int plan_impl(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int list_
   if ((st = ensure(ctx, ctx->d_status, sizeof(int) * n))) return st;
   if ((st = ensure(ctx, ctx->d_results, sizeof(mdgp_result) * n))) return st;
   if ((st = ensure(ctx, ctx->d_step, sizeof(long long)))) return st;
-  if ((st = ensure(ctx, ctx->d_flags, sizeof(int) * 4))) return st;
+  if ((st = ensure(ctx, ctx->d_flags, sizeof(int) * kFlags))) return st;
   if ((st = ensure(ctx, ctx->d_tz, sizeof(double) * 2 * n))) return st;
   CK(cudaMemcpyAsync(ctx->d_el.ptr, Es.data(), sizeof(ElemDev) * n, cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(ctx->d_aoff.ptr, aoff.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, ctx->stream));
@@ -500,7 +571,7 @@ static int plan_impl(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int list_
   B.acc = (double*)ctx->d_acc.ptr;
   B.grp = (double*)ctx->d_grp.ptr;
   B.status = (int*)ctx->d_status.ptr;
-  B.step_base = (const long long*)ctx->d_step.ptr;
+  B.step_base = (long long*)ctx->d_step.ptr;
   B.flags = (int*)ctx->d_flags.ptr;
   B.tz = (double*)ctx->d_tz.ptr;
   ctx->P = make_phys(ctx->params, list_cap);
@@ -520,9 +591,30 @@ static int plan_impl(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int list_
   k_fill_maps<<<gm < 4096 ? gm : 4096, 256, 0, ctx->stream>>>(B);
   CK(cudaGetLastError());
 
-  // Step loop graphs: chunks of K steps plus a remainder chunk.
+  // Step loop: FP32 pair forces run the persistent WHILE graph (when
+  // params.persistent is set and the device takes the cooperative launch),
+  // otherwise chunks of K steps with one conditional rebuild per step.
   const long long K = ctx->chunk;
-  if (S > 0) {
+  bool use_while = false;
+  if (S > 0 && ctx->precision == MDGP_PREC_FP32 && ctx->params.persistent) {
+    int sms = 0, per_sm = 0;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+    const bool uni = ctx->P.uniform != 0, frozen = ctx->params.mode == 1;
+    cudaError_t e;
+    if (uni && !frozen) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_steps_persist<true, false>, 128, 0);
+    else if (!uni && !frozen) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_steps_persist<false, false>, 128, 0);
+    else if (uni) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_steps_persist<true, true>, 128, 0);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_steps_persist<false, true>, 128, 0);
+    if (e != cudaSuccess) return set_err(ctx, e);
+    const long long chunks = (atoms + 127) / 128;
+    const long long cap = (long long)per_sm * sms;
+    ctx->persist_grid = (unsigned)(chunks < cap ? chunks : cap);
+    const long long saved = ctx->launches;
+    if (ctx->persist_grid > 0 && capture_while(ctx, &ctx->graph_while) == MDGP_OK) use_while = true;
+    else cudaGetLastError();   // fall back to the per-step graphs
+    ctx->launches = saved;
+  }
+  if (S > 0 && !use_while) {
     const long long saved = ctx->launches;
     if (S >= K) {
       if ((st = capture_steps(ctx, K, &ctx->graph_full))) return st;
@@ -558,7 +650,7 @@ static int start_batch(mdgp_ctx* ctx) {
   CK(cudaMemsetAsync(ctx->d_status.ptr, 0, sizeof(int) * n, ctx->stream));
   CK(cudaMemsetAsync(ctx->B.ccount, 0, sizeof(int) * ctx->B.n_cells, ctx->stream));
   CK(cudaMemsetAsync(ctx->d_step.ptr, 0, sizeof(long long), ctx->stream));
-  CK(cudaMemsetAsync(ctx->B.flags, 0, sizeof(int) * 4, ctx->stream));
+  CK(cudaMemsetAsync(ctx->B.flags, 0, sizeof(int) * kFlags, ctx->stream));
   CK(cudaMemsetAsync(ctx->B.tz, 0, sizeof(double) * 2 * n, ctx->stream));
   const unsigned ga = grid_for(ctx->B.n_atoms, 256);
   if (ctx->precision == MDGP_PREC_FP32) {
@@ -582,6 +674,9 @@ static int launch_impl(mdgp_ctx* ctx) {
   enqueue_energy(ctx, kAccE0);
   const long long S = ctx->steps;
   if (S > 0) {
+    if (ctx->graph_while) {
+      CK(cudaGraphLaunch(ctx->graph_while, ctx->stream));   // persistent launches counted on the device
+    }
     if (ctx->graph_K > 0) {
       const long long full = S / ctx->graph_K;
       for (long long r = 0; r < full; ++r) {
@@ -608,13 +703,13 @@ static int launch_impl(mdgp_ctx* ctx) {
 static int results_impl(mdgp_ctx* ctx, mdgp_result* out, int64_t n) {
   if (!ctx->planned) return MDGP_E_STATE;
   if (n != ctx->n_el || !out) return MDGP_E_ARG;
-  int flags[4];
+  int flags[kFlags];
   CK(cudaMemcpyAsync(out, ctx->d_results.ptr, sizeof(mdgp_result) * n, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaMemcpyAsync(flags, ctx->B.flags, sizeof(flags), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   // every rebuild is 5 kernels; the launch sequence counted one eagerly
   ctx->rebuilds = flags[2];
-  ctx->launches_with_rebuilds = ctx->launches + 5LL * (flags[2] - 1);
+  ctx->launches_with_rebuilds = ctx->launches + 5LL * (flags[2] - 1) + flags[3];
   return MDGP_OK;
 }
 
@@ -653,6 +748,7 @@ int mdgp_md_params_default(mdgp_md_params* out) {
   out->skin = 0.4;
   out->rebuild_every = 0;
   out->build_variant = 2;
+  out->persistent = 1;
   return MDGP_OK;
 }
 
@@ -667,6 +763,7 @@ int mdgp_create(mdgp_ctx** out, int device, int precision) {
   cudaError_t e = cudaSetDevice(device);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->side_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->side_stream2, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     delete ctx;
     return MDGP_E_CUDA;
@@ -684,6 +781,7 @@ int mdgp_destroy(mdgp_ctx* ctx) {
   ctx->release_extra();
   if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
   if (ctx->side_stream) cudaStreamDestroy(ctx->side_stream);
+  if (ctx->side_stream2) cudaStreamDestroy(ctx->side_stream2);
   delete ctx;
   return MDGP_OK;
 }
@@ -692,7 +790,7 @@ int mdgp_set_md_params(mdgp_ctx* ctx, const mdgp_md_params* p) {
   if (!ctx || !p) return MDGP_E_ARG;
   if (!(p->dt > 0) || !(p->rc > 0) || p->n_blocks < 1 || p->wall_planes < 1 || !(p->mass > 0) ||
       !(p->wall_density > 0) || p->gamma_wall < 0 || p->list_capacity < 0 || !(p->skin >= 0) ||
-      p->rebuild_every < 0 || p->build_variant < 0 || p->build_variant > 2)
+      p->rebuild_every < 0 || p->build_variant < 0 || p->build_variant > 2 || p->persistent < 0 || p->persistent > 1)
     return MDGP_E_ARG;
   ctx->params = *p;
   ctx->planned = false;

@@ -1299,7 +1299,7 @@ struct StepOut {
 
 template <bool FROZEN>
 __device__ __forceinline__ void integrate_df_atom(const BatchDev& B, const PhysDev& P, long long i, long long s,
-                                                  int mode, int use_cond, float fx, float fy, float fz, float wxx,
+                                                  int mode, int* skin_flag, float fx, float fy, float fz, float wxx,
                                                   StepOut& o) {
   const int e = B.atom_el[i];
   const ElemDev& E = B.el[e];
@@ -1323,7 +1323,8 @@ __device__ __forceinline__ void integrate_df_atom(const BatchDev& B, const PhysD
     const float gk = E.g_kick;
     float lam = 1.0f;
     if (FROZEN && (mode & kTzApply) && E.nf > 0) {
-      const float tzm = (float)B.tz[2 * e + ((s - 1) & 1)] / (float)E.nf;
+      // summed by atomics in L2 by this step's first phase: read past L1
+      const float tzm = (float)__ldcg(&B.tz[2 * e + ((s - 1) & 1)]) / (float)E.nf;
       if (tzm > 0.0f) lam = sqrtf(1.0f + P.dt_tauf * (E.Tf / tzm - 1.0f));
     }
     if (sample) {
@@ -1395,7 +1396,7 @@ __device__ __forceinline__ void integrate_df_atom(const BatchDev& B, const PhysD
     const float4 pb = B.pbuild[i];
     const float ex = xf - pb.x, ey = yf - pb.y, ez = zf - pb.z;
     if (ex * ex + ey * ey + ez * ez > P.half_skin2f) {
-      if (use_cond) atomicOr(&B.flags[0], 1);
+      if (skin_flag) atomicOr(skin_flag, 1);
       else atomicMin(&B.status[e], kStSkin);
     }
   }
@@ -1446,7 +1447,7 @@ __global__ void __launch_bounds__(256) k_integrate_df(BatchDev B, PhysDev P, int
   const long long s = *B.step_base + k;
   StepOut o;
   if (i < B.n_atoms)
-    integrate_df_atom<FROZEN>(B, P, i, s, mode, use_cond, static_cast<const float*>(B.fx)[i],
+    integrate_df_atom<FROZEN>(B, P, i, s, mode, use_cond ? &B.flags[0] : nullptr, static_cast<const float*>(B.fx)[i],
                               static_cast<const float*>(B.fy)[i], static_cast<const float*>(B.fz)[i],
                               static_cast<const float*>(B.wxx)[i], o);
   integrate_df_epilogue<FROZEN>(B, s, mode, o, hcond, use_cond);
@@ -1474,9 +1475,108 @@ __global__ void __launch_bounds__(128) k_step_df(BatchDev B, PhysDev P, int k, i
       static_cast<float*>(B.fz)[i] = f.fz;
       static_cast<float*>(B.wxx)[i] = wxx;
     }
-    integrate_df_atom<FROZEN>(B, P, i, s, mode, use_cond, f.fx, f.fy, f.fz, wxx, o);
+    integrate_df_atom<FROZEN>(B, P, i, s, mode, use_cond ? &B.flags[0] : nullptr, f.fx, f.fy, f.fz, wxx, o);
   }
   integrate_df_epilogue<FROZEN>(B, s, mode, o, hcond, use_cond);
+}
+
+// Grid-wide barrier for a cooperative launch (every block resident): block
+// leaders count arrivals on flags[kFlagBarCount]; the last one resets the
+// count and advances the generation word flags[kFlagBarGen], the others wait
+// for the generation to change.  The wait is bounded: false if it gave up.
+__device__ __forceinline__ bool grid_barrier(int* flags) {
+  __syncthreads();
+  int ok = 1;
+  if (threadIdx.x == 0) {
+    volatile int* gen = flags + kFlagBarGen;
+    const int g = *gen;
+    __threadfence();
+    if (atomicAdd(flags + kFlagBarCount, 1) == (int)gridDim.x - 1) {
+      atomicExch(flags + kFlagBarCount, 0);
+      __threadfence();
+      atomicAdd(flags + kFlagBarGen, 1);
+    } else {
+      long long it = 0;
+      while (*gen == g) {
+        if (++it > (1LL << 22)) { ok = 0; break; }   // ~0.1-1 s
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  return __syncthreads_and(ok) != 0;
+}
+
+// Persistent MD steps with the double-float state (FP32 pair forces): one
+// cooperative launch runs whole steps (the k_step_df work, blocks striding
+// over 128-atom chunks) separated by grid barriers, until an atom has moved
+// half the skin (the lists must be rebuilt before the next force evaluation)
+// or step S has been started.  Step s writes its skin flag to word s mod 3
+// of flags[kFlagSkin..]; every block reads it after the step's last barrier,
+// before the next barrier, so the word of step s + 1 (last read two barriers
+// ago) is cleared during step s.  On
+// exit block 0 stores the step counter and sets the graph conditions: the
+// rebuild (IF) and whether steps remain (WHILE).  With the frozen-wall
+// thermostat a step is two phases with a barrier between them.  A barrier
+// that gives up marks every element unstable and ends the run.
+template <bool UNIFORM, bool FROZEN>
+__global__ void __launch_bounds__(128) k_steps_persist(BatchDev B, PhysDev P, long long S,
+                                                       cudaGraphConditionalHandle h_rebuild,
+                                                       cudaGraphConditionalHandle h_more) {
+  const long long nchunks = (B.n_atoms + 127) / 128;
+  long long s = *B.step_base;
+  bool rebuild = false, failed = false;
+  while (s < S) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) B.flags[kFlagSkin + (int)((s + 1) % 3)] = 0;
+    int* skin = &B.flags[kFlagSkin + (int)(s % 3)];
+    const float4* pos = static_cast<const float4*>(B.posb[s & 1]);
+    const int m1 = FROZEN ? (kFinish | kTzSum) : (kFinish | kStage1);
+    for (long long c = blockIdx.x; c < nchunks; c += gridDim.x) {
+      const long long i = c * 128 + threadIdx.x;
+      StepOut o;
+      if (i < B.n_atoms) {
+        int spi;
+        const PairAcc<float4, float, UNIFORM, false> f = pair_force<float4, float, UNIFORM, false>(B, P, i, pos, spi);
+        const float wxx = spi == 0 ? 0.5f * f.w : 0.0f;
+        if (FROZEN) {
+          static_cast<float*>(B.fx)[i] = f.fx;
+          static_cast<float*>(B.fy)[i] = f.fy;
+          static_cast<float*>(B.fz)[i] = f.fz;
+          static_cast<float*>(B.wxx)[i] = wxx;
+        }
+        integrate_df_atom<FROZEN>(B, P, i, s, m1, skin, f.fx, f.fy, f.fz, wxx, o);
+      }
+      integrate_df_epilogue<FROZEN>(B, s, m1, o, 0, 0);
+    }
+    if (!grid_barrier(B.flags)) { failed = true; break; }
+    if (FROZEN) {
+      const int m2 = kTzApply | kStage1;
+      for (long long c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        const long long i = c * 128 + threadIdx.x;
+        StepOut o;
+        if (i < B.n_atoms)
+          integrate_df_atom<FROZEN>(B, P, i, s, m2, skin, static_cast<const float*>(B.fx)[i],
+                                    static_cast<const float*>(B.fy)[i], static_cast<const float*>(B.fz)[i],
+                                    static_cast<const float*>(B.wxx)[i], o);
+        integrate_df_epilogue<FROZEN>(B, s, m2, o, 0, 0);
+      }
+      if (!grid_barrier(B.flags)) { failed = true; break; }
+    }
+    rebuild = *(volatile int*)skin != 0;
+    ++s;
+    if (rebuild) break;
+  }
+  if (failed) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < B.n_el;
+         e += (long long)gridDim.x * blockDim.x)
+      atomicMin(&B.status[e], kStUnstable);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *B.step_base = s;
+    atomicAdd(&B.flags[3], 1);
+    cudaGraphSetConditional(h_rebuild, (rebuild && !failed) ? 1u : 0u);
+    cudaGraphSetConditional(h_more, (s < S && !failed) ? 1u : 0u);
+  }
 }
 
 // Total energy per element (kinetic + shifted LJ + tether) into acc[which].

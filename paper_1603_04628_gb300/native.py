@@ -38,7 +38,8 @@ class MDParams(ctypes.Structure):
                 ("sig_ww", ctypes.c_double), ("fluid_margin", ctypes.c_double), ("tau_T", ctypes.c_double),
                 ("mass", ctypes.c_double), ("n_blocks", ctypes.c_int32), ("mode", ctypes.c_int32),
                 ("wall_planes", ctypes.c_int32), ("list_capacity", ctypes.c_int32),
-                ("skin", ctypes.c_double), ("rebuild_every", ctypes.c_int32), ("build_variant", ctypes.c_int32)]
+                ("skin", ctypes.c_double), ("rebuild_every", ctypes.c_int32), ("build_variant", ctypes.c_int32),
+                ("persistent", ctypes.c_int32)]
 
 
 class GPParams(ctypes.Structure):

@@ -328,3 +328,40 @@ def test_paper_mode_frozen_walls_berendsen_fp64(native):
     assert np.abs(_wrap_dx(xg[sp == 1] - a[sp == 1], p)).max() <= 1e-12   # walls did not move
     for k in ("q", "p", "T_meas", "e_drift"):
         assert r[k] == pytest.approx(ref[k], rel=1e-7, abs=1e-9), k
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_persistent_step_loop_matches_per_step_launches(native, mode):
+    # the persistent step kernel (grid barriers between steps, rebuilds in a
+    # graph WHILE loop) and one launch per step do the same arithmetic; the
+    # order of atoms inside a cell (binning atomics) may differ, so the
+    # trajectories agree to FP32 summation order over a short run
+    els = synth.batch_uneven(6, seed=21, steps=80)
+    kw = PAPER_MODE if mode == 1 else {}
+    if mode == 1:
+        # r_c = 4: the box must hold three cells of r_c + skin along x and z
+        els = [dict(e, T=2.44, density=0.75, Lx=15.0, Lz=15.0) for e in els]
+    out = []
+    for persistent in (1, 0):
+        ctx = native.Context(0, native.PREC_FP32, persistent=persistent, list_capacity=640 if mode else 128, **kw)
+        ctx.micro_plan(els)
+        ctx.micro_launch()
+        res = ctx.micro_results()
+        x, v = ctx.micro_state()
+        out.append((res, x, v, ctx.rebuild_count()))
+        ctx.close()
+    (ra, xa, va, na), (rb, xb, vb, nb) = out
+    assert all(r["status"] == 0 for r in ra + rb)
+    assert na > 1 and nb > 1
+    off = 0
+    for el, r in zip(els, ra):
+        n = r["n_fluid"] + r["n_wall"]
+        d = xa[off:off + n] - xb[off:off + n]
+        d[:, 0] -= el["Lx"] * np.round(d[:, 0] / el["Lx"])
+        d[:, 2] -= el["Lz"] * np.round(d[:, 2] / el["Lz"])
+        assert np.abs(d).max() < 1e-3
+        off += n
+    assert off == len(xa)
+    assert np.abs(va - vb).max() < 1e-2
+    for a, b in zip(ra, rb):
+        assert a["q"] == pytest.approx(b["q"], rel=1e-2, abs=1e-3)
