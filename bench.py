@@ -37,6 +37,9 @@ ALG_FLOPS_PER_ATOM_STEP = 600.0      # 26.2 unique pairs x ~23 FP32 flops (Newto
                                      # the integration's few flops per atom are not counted
 ALG_BYTES_PER_ATOM_STEP = 96.0       # FP64 x and v read and written once per step
 CPU_SAMPLE_STEPS = 1000              # oracle steps per sampled element (~10-20 s of CPU work)
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_step_df launch on this
+# workload (ncu capture, cold cache, 400 steps per element)
+STEP_KERNEL_TRAFFIC_BYTES = 73.9e6
 
 
 def _oracle_element_steps(args):
@@ -196,6 +199,7 @@ def main():
         ctx.micro_launch()
         ctx.micro_results()
     launches_per_step = ctx.launch_count()
+    rebuilds_per_step = ctx.rebuild_count()
 
     clk_path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
                             "bench_clocks_rank%d.csv" % rank)
@@ -285,10 +289,17 @@ def main():
                        "parallelism": "independent elements per rank" if world > 1 else "1 GPU"},
             "roofline": {"bound": "alu", "kernel": "k_step_df (pair forces + integration, one launch per step)",
                          "achieved": achieved, "peak": fp32_peak,
-                         "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                         "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                         "traffic": STEP_KERNEL_TRAFFIC_BYTES if args.workload == "uneven" else None,
                          "peak_note": FP32_PEAK_NOTE + " (derived, max SM clock)",
                          "alg_flops_per_atom_step": ALG_FLOPS_PER_ATOM_STEP,
-                         "force_ms": prof["force_ms"], "integrate_ms": prof["integrate_ms"]},
+                         "force_ms": prof["force_ms"], "integrate_ms": prof["integrate_ms"],
+                         "timing": "one k_step_df launch (= one MD step of the batch) timed with CUDA "
+                                   "events on the context's stream; the timed run executes the same "
+                                   "per-step code inside the persistent k_steps_persist",
+                         "persistent_step_us": (ms * 1e3 - rebuilds_per_step * prof["rebuild_ms"] * 1e3)
+                                               / steps_el,
+                         "rebuilds_per_run": rebuilds_per_step, "rebuild_ms": prof["rebuild_ms"]},
             "hbm_roofline": {"alg_bytes_per_atom_step": ALG_BYTES_PER_ATOM_STEP,
                              "achieved_gbs": value / world * ALG_BYTES_PER_ATOM_STEP / 1e9,
                              "peak_gbs": _peak_hbm(), "frac": value / world * ALG_BYTES_PER_ATOM_STEP / 1e9 /
