@@ -32,6 +32,8 @@ struct mdgp_ctx {
   cudaGraphExec_t graph_full = nullptr, graph_rem = nullptr;
   cudaGraphExec_t graph_while = nullptr;  // persistent step loop (FP32 pair forces)
   unsigned persist_grid = 0;              // co-resident blocks of the persistent step kernel
+  int persist_threads = 128;              // its block size
+  int persist_atoms = 128;                // atoms per block (<= persist_threads)
   long long launches = 0;              // kernels enqueued by the last launch (graph bodies: 2 per step)
   long long launches_with_rebuilds = 0;  // ... plus the rebuild kernels that ran
   long long rebuilds = 0;

@@ -418,7 +418,7 @@ static int capture_while(mdgp_ctx* ctx, cudaGraphExec_t* out) {
   if (e != cudaSuccess) { cudaGraphDestroy(g); return set_err(ctx, e); }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(ctx->persist_grid);
-  cfg.blockDim = dim3(128);
+  cfg.blockDim = dim3(ctx->persist_threads);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = ctx->side_stream;
   cudaLaunchAttribute at[1];
@@ -428,10 +428,11 @@ static int capture_while(mdgp_ctx* ctx, cudaGraphExec_t* out) {
   cfg.numAttrs = 1;
   const bool uni = ctx->P.uniform != 0, frozen = ctx->params.mode == 1;
   const long long S = ctx->steps;
-  if (uni && !frozen) e = cudaLaunchKernelEx(&cfg, k_steps_persist<true, false>, ctx->B, ctx->P, S, hr, hw);
-  else if (!uni && !frozen) e = cudaLaunchKernelEx(&cfg, k_steps_persist<false, false>, ctx->B, ctx->P, S, hr, hw);
-  else if (uni) e = cudaLaunchKernelEx(&cfg, k_steps_persist<true, true>, ctx->B, ctx->P, S, hr, hw);
-  else e = cudaLaunchKernelEx(&cfg, k_steps_persist<false, true>, ctx->B, ctx->P, S, hr, hw);
+  const int A = ctx->persist_atoms;
+  if (uni && !frozen) e = cudaLaunchKernelEx(&cfg, k_steps_persist<true, false>, ctx->B, ctx->P, S, A, hr, hw);
+  else if (!uni && !frozen) e = cudaLaunchKernelEx(&cfg, k_steps_persist<false, false>, ctx->B, ctx->P, S, A, hr, hw);
+  else if (uni) e = cudaLaunchKernelEx(&cfg, k_steps_persist<true, true>, ctx->B, ctx->P, S, A, hr, hw);
+  else e = cudaLaunchKernelEx(&cfg, k_steps_persist<false, true>, ctx->B, ctx->P, S, A, hr, hw);
   cudaStreamCaptureStatus cs;
   cudaGraph_t cg;
   const cudaGraphNode_t* deps = nullptr;
@@ -597,18 +598,47 @@ static int plan_impl(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int list_
   const long long K = ctx->chunk;
   bool use_while = false;
   if (S > 0 && ctx->precision == MDGP_PREC_FP32 && ctx->params.persistent) {
-    int sms = 0, per_sm = 0;
+    // Persistent grid: R co-resident blocks per SM, each taking A = N / (R x
+    // SMs) atoms rounded up, so that every SM holds about N / SMs atoms (the
+    // step ends with the most loaded SM); the block is A rounded up to whole
+    // warps.  The R with the fewest warps per SM (the least idle lanes) among
+    // those that fit wins.
+    int sms = 0;
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
     const bool uni = ctx->P.uniform != 0, frozen = ctx->params.mode == 1;
-    cudaError_t e;
-    if (uni && !frozen) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_steps_persist<true, false>, 128, 0);
-    else if (!uni && !frozen) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_steps_persist<false, false>, 128, 0);
-    else if (uni) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_steps_persist<true, true>, 128, 0);
-    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_steps_persist<false, true>, 128, 0);
-    if (e != cudaSuccess) return set_err(ctx, e);
-    const long long chunks = (atoms + 127) / 128;
-    const long long cap = (long long)per_sm * sms;
-    ctx->persist_grid = (unsigned)(chunks < cap ? chunks : cap);
+    auto occupancy = [&](int threads, int* per_sm) {
+      if (uni && !frozen) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_steps_persist<true, false>, threads, 0);
+      if (!uni && !frozen) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_steps_persist<false, false>, threads, 0);
+      if (uni) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_steps_persist<true, true>, threads, 0);
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_steps_persist<false, true>, threads, 0);
+    };
+    ctx->persist_grid = 0;
+    long long best_warps = 1LL << 40;
+    for (int R = 1; R <= 32; ++R) {
+      const long long slots = (long long)sms * R;
+      const long long A = (atoms + slots - 1) / slots;
+      const int T = (int)((A + 31) / 32 * 32);
+      // at least 128 threads: smaller blocks put more separate atom ranges on
+      // an SM and lose L1 reuse of the neighbour positions (measured slower)
+      if (T > 256 || T < 128) continue;   // larger batches: 256-thread blocks striding over chunks
+      int per_sm = 0;
+      if (occupancy(T, &per_sm) != cudaSuccess) return set_err(ctx, cudaGetLastError());
+      const long long warps = (long long)R * (T / 32);
+      if (per_sm >= R && warps < best_warps) {
+        best_warps = warps;
+        ctx->persist_atoms = (int)A;
+        ctx->persist_threads = T;
+        ctx->persist_grid = (unsigned)((atoms + A - 1) / A);
+      }
+    }
+    if (ctx->persist_grid == 0) {
+      int per_sm = 0;
+      if (occupancy(256, &per_sm) != cudaSuccess) return set_err(ctx, cudaGetLastError());
+      const long long chunks = (atoms + 255) / 256, cap = (long long)per_sm * sms;
+      ctx->persist_atoms = 256;
+      ctx->persist_threads = 256;
+      ctx->persist_grid = (unsigned)(chunks < cap ? chunks : cap);
+    }
     const long long saved = ctx->launches;
     if (ctx->persist_grid > 0 && capture_while(ctx, &ctx->graph_while) == MDGP_OK) use_while = true;
     else cudaGetLastError();   // fall back to the per-step graphs
@@ -703,7 +733,7 @@ static int launch_impl(mdgp_ctx* ctx) {
 static int results_impl(mdgp_ctx* ctx, mdgp_result* out, int64_t n) {
   if (!ctx->planned) return MDGP_E_STATE;
   if (n != ctx->n_el || !out) return MDGP_E_ARG;
-  int flags[kFlags];
+  int flags[16];   // the counters; the barrier words are not needed here
   CK(cudaMemcpyAsync(out, ctx->d_results.ptr, sizeof(mdgp_result) * n, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaMemcpyAsync(flags, ctx->B.flags, sizeof(flags), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));

@@ -36,10 +36,10 @@ constexpr int kAccE1 = 2 * kMaxBlocks + 2;    // total energy after the last ste
 constexpr int kAccStride = 2 * kMaxBlocks + 4;
 constexpr int kGrpStride = 8;                 // init sums per group: sum v, sum v^2
 constexpr unsigned kJMask = 0x03FFFFFFu;      // neighbour index bits of a list entry
-constexpr int kFlags = 16;                    // flag words (see BatchDev::flags)
-constexpr int kFlagSkin = 4;
-constexpr int kFlagBarCount = 7;
+constexpr int kFlagSkin = 4;                  // flag words (see BatchDev::flags)
 constexpr int kFlagBarGen = 8;
+constexpr int kFlagBarCount = 10;             // 64-bit, words 10-11
+constexpr int kFlags = 16;
 
 // status codes written per element (match mdgp_status)
 constexpr int kStUnstable = -4;
@@ -126,7 +126,8 @@ struct BatchDev {
   double* out;                    // export scratch [6 * n_atoms] (original order)
   int* flags;                     // [kFlags]: [0] rebuild needed, [1] blocks done, [2] rebuilds
                                   // run, [3] persistent step launches, [4..6] skin flags by
-                                  // step mod 3, [7..8] grid barrier count and generation
+                                  // step mod 3, [8] grid barrier generation, [10..11] its
+                                  // 64-bit arrival count
   double* tz;                     // [2 * n_el] per-element sum of m v_z^2 (two step-parity slots)
 };
 

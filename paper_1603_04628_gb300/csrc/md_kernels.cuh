@@ -87,13 +87,13 @@ __device__ __forceinline__ void seg_add(int key, const double (&val)[NV], DstFn 
   }
 }
 
-// Block-level segmented reduction for blocks of up to 256 threads (a power
-// of two): every thread puts (key, NV values) into shared memory.  When the
-// whole block shares one key (the usual case: atoms of one element are
-// contiguous) a shared-memory tree adds the values with one FP64 add per
-// thread and value and one atomicAdd; otherwise up to 8 threads each scan
-// 32 entries and add each run of equal keys.  Keys < 0 are skipped.  All
-// threads of the block must call it.
+// Block-level segmented reduction for blocks of up to 256 threads: every
+// thread puts (key, NV values) into shared memory.  When the whole block
+// shares one key (the usual case: atoms of one element are contiguous) a
+// shared-memory tree over 256 slots (the slots past the block zeroed) adds
+// the values and one atomicAdd per value writes the sum; otherwise up to 8
+// threads each scan 32 entries and add each run of equal keys.  Keys < 0 are
+// skipped.  All threads of the block must call it.
 template <int NV, typename DstFn>
 __device__ __forceinline__ void block_seg_add(int key, const double (&val)[NV], DstFn dst) {
   __shared__ int skey[256];
@@ -102,14 +102,17 @@ __device__ __forceinline__ void block_seg_add(int key, const double (&val)[NV], 
   skey[t] = key;
 #pragma unroll
   for (int i = 0; i < NV; ++i) sval[i][t] = val[i];
+  for (int t2 = t + (int)blockDim.x; t2 < 256; t2 += (int)blockDim.x)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) sval[i][t2] = 0.0;
   __syncthreads();
   const int k0 = skey[0];
   if (__syncthreads_and(key == k0)) {
     if (k0 < 0) return;
-    for (int h = (int)blockDim.x >> 1; h > 0; h >>= 1) {
-      if (t < h)
+    for (int h = 128; h > 0; h >>= 1) {
+      for (int t2 = t; t2 < h; t2 += (int)blockDim.x)
 #pragma unroll
-        for (int i = 0; i < NV; ++i) sval[i][t] += sval[i][t + h];
+        for (int i = 0; i < NV; ++i) sval[i][t2] += sval[i][t2 + h];
       __syncthreads();
     }
     if (t < NV) atomicAdd(dst(k0, t), sval[t][0]);
@@ -1480,29 +1483,40 @@ __global__ void __launch_bounds__(128) k_step_df(BatchDev B, PhysDev P, int k, i
   integrate_df_epilogue<FROZEN>(B, s, mode, o, hcond, use_cond);
 }
 
-// Grid-wide barrier for a cooperative launch (every block resident): block
-// leaders count arrivals on flags[kFlagBarCount]; the last one resets the
-// count and advances the generation word flags[kFlagBarGen], the others wait
-// for the generation to change.  The wait is bounded: false if it gave up.
+// Grid-wide barrier for a cooperative launch (every block resident).  The
+// arrival count never resets: before barrier g (the generation word's value)
+// it holds g x gridDim blocks, so the block whose arrival makes it
+// (g + 1) x gridDim publishes generation g + 1 with a release store, and the
+// other leaders wait for it with acquire loads.  One atomic and one store on
+// the release path.  The wait is bounded: false if it gave up.
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ bool grid_barrier(int* flags) {
   __syncthreads();
   int ok = 1;
   if (threadIdx.x == 0) {
-    volatile int* gen = flags + kFlagBarGen;
-    const int g = *gen;
+    unsigned* gen = reinterpret_cast<unsigned*>(flags + kFlagBarGen);
+    unsigned long long* cnt = reinterpret_cast<unsigned long long*>(flags + kFlagBarCount);
+    const unsigned g = ld_acquire_gpu(gen);
     __threadfence();
-    if (atomicAdd(flags + kFlagBarCount, 1) == (int)gridDim.x - 1) {
-      atomicExch(flags + kFlagBarCount, 0);
-      __threadfence();
-      atomicAdd(flags + kFlagBarGen, 1);
+    const unsigned long long target = (unsigned long long)(g + 1u) * gridDim.x;
+    if (atomicAdd(cnt, 1ull) == target - 1ull) {
+      __threadfence();   // the other blocks' arrivals (and their writes) before the release
+      st_release_gpu(gen, g + 1u);
     } else {
       long long it = 0;
-      while (*gen == g) {
+      while (ld_acquire_gpu(gen) == g) {
         if (++it > (1LL << 22)) { ok = 0; break; }   // ~0.1-1 s
-        __nanosleep(64);
+        __nanosleep(32);
       }
     }
-    __threadfence();
   }
   return __syncthreads_and(ok) != 0;
 }
@@ -1518,12 +1532,16 @@ __device__ __forceinline__ bool grid_barrier(int* flags) {
 // exit block 0 stores the step counter and sets the graph conditions: the
 // rebuild (IF) and whether steps remain (WHILE).  With the frozen-wall
 // thermostat a step is two phases with a barrier between them.  A barrier
-// that gives up marks every element unstable and ends the run.
+// that gives up marks every element unstable and ends the run.  Block c
+// takes atoms [c A, (c + 1) A) with A <= blockDim.x chosen by the host so
+// that every SM holds the same number of atoms (the step ends with the
+// most loaded SM).
 template <bool UNIFORM, bool FROZEN>
-__global__ void __launch_bounds__(128) k_steps_persist(BatchDev B, PhysDev P, long long S,
-                                                       cudaGraphConditionalHandle h_rebuild,
-                                                       cudaGraphConditionalHandle h_more) {
-  const long long nchunks = (B.n_atoms + 127) / 128;
+__global__ void __launch_bounds__(256, 5) k_steps_persist(BatchDev B, PhysDev P, long long S, int A,
+                                                      cudaGraphConditionalHandle h_rebuild,
+                                                      cudaGraphConditionalHandle h_more) {
+  const long long nchunks = (B.n_atoms + A - 1) / A;
+  const bool lane_used = (int)threadIdx.x < A;
   long long s = *B.step_base;
   bool rebuild = false, failed = false;
   while (s < S) {
@@ -1532,7 +1550,7 @@ __global__ void __launch_bounds__(128) k_steps_persist(BatchDev B, PhysDev P, lo
     const float4* pos = static_cast<const float4*>(B.posb[s & 1]);
     const int m1 = FROZEN ? (kFinish | kTzSum) : (kFinish | kStage1);
     for (long long c = blockIdx.x; c < nchunks; c += gridDim.x) {
-      const long long i = c * 128 + threadIdx.x;
+      const long long i = lane_used ? c * A + threadIdx.x : B.n_atoms;
       StepOut o;
       if (i < B.n_atoms) {
         int spi;
@@ -1552,7 +1570,7 @@ __global__ void __launch_bounds__(128) k_steps_persist(BatchDev B, PhysDev P, lo
     if (FROZEN) {
       const int m2 = kTzApply | kStage1;
       for (long long c = blockIdx.x; c < nchunks; c += gridDim.x) {
-        const long long i = c * 128 + threadIdx.x;
+        const long long i = lane_used ? c * A + threadIdx.x : B.n_atoms;
         StepOut o;
         if (i < B.n_atoms)
           integrate_df_atom<FROZEN>(B, P, i, s, m2, skin, static_cast<const float*>(B.fx)[i],
