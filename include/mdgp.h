@@ -212,6 +212,8 @@ typedef struct {
   double fallback_scale;   /* scale used where the mean separation is undefined (< 2 entries or
                               zero spread); <= 0 means 1 */
   const double* fixed_scales; /* D scales to use instead of the database's mean separations, or null */
+  const double* fallback_scales; /* D per-dimension fallbacks (entries <= 0 take fallback_scale),
+                                    or null; copied during the call */
 } mdgp_gp_params;
 
 /* Fit a GP to M database entries (Eqs. quadraticKernelEq, d2Eq,

@@ -47,6 +47,10 @@ class Channel:
         L = self.N * self.dx
         x = np.arange(self.N) * self.dx
         self.h = self.h0 * (1.0 - 0.5 * np.cos(2.0 * math.pi * x / L))
+        # Eq. d2Eq's mean separation is undefined for an input without spread
+        # (all h equal; the uniform gradient of the first steps): h then takes
+        # h0 / 2, G the forcing gradient amplitude dP_amp / L
+        self.fallback = np.array([0.5 * self.h0, self.dP_amp / L if self.dP_amp > 0 else 1.0])
         self.n = np.full(self.N, self.n0) if density0 is None else np.array(density0, dtype=np.float64)
         self.i = 0                       # macro steps taken
         self.X = np.zeros((0, 2))
@@ -88,7 +92,7 @@ class Channel:
         q = np.zeros(self.N); sd = np.zeros(self.N); from_md = np.zeros(self.N, bool)
         for j in range(self.N):
             x = np.array([[self.h[j], G[j]]])
-            g = ogp.GP(self.X, self.y, self.sf2, self.l2, sn2)
+            g = ogp.GP(self.X, self.y, self.sf2, self.l2, sn2, fallback=self.fallback)
             m, v = g.predict(x)
             sd[j] = math.sqrt(v[0])
             if ogp.gate(sd[j], sigma_t):
@@ -120,7 +124,7 @@ class Channel:
         sd = np.zeros(self.N); from_md = np.zeros(self.N, bool)
         for j in range(self.N):
             x = np.array([[self.h[j], G[j]]])
-            g = ogp.GP(Xv, np.zeros(len(Xv)), self.sf2, self.l2, sn2)   # y does not enter the variance
+            g = ogp.GP(Xv, np.zeros(len(Xv)), self.sf2, self.l2, sn2, fallback=self.fallback)   # y does not enter the variance
             v = g.predict(x)[1]
             sd[j] = math.sqrt(v[0])
             if ogp.gate(sd[j], sigma_t):
@@ -141,7 +145,7 @@ class Channel:
                 se = np.append(se, res[k]["q_se"])
                 k += 1
             else:
-                g = ogp.GP(X, y, self.sf2, self.l2, sn2)
+                g = ogp.GP(X, y, self.sf2, self.l2, sn2, fallback=self.fallback)
                 q[j] = g.predict(np.array([[self.h[j], G[j]]]))[0][0]
         self.X, self.y, self.se = X, y, se
         self.continuity(q)

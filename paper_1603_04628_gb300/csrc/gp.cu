@@ -52,11 +52,26 @@ __global__ void k_gp_pairsep(const double* X, int M, int D, double* out) {
 }
 
 // Turn the pair sums into scales; fall back where undefined.
-__global__ void k_gp_scales(double* sums, int M, int D, double fallback, const double* fixed) {
+// Per-dimension scale used where the mean separation is undefined.
+struct Fallback {
+  double v[kMaxD];
+};
+
+static Fallback make_fallback(const mdgp_gp_params* p, int D) {
+  Fallback f;
+  const double one = p->fallback_scale > 0 ? p->fallback_scale : 1.0;
+  for (int k = 0; k < kMaxD; ++k) f.v[k] = one;
+  if (p->fallback_scales)
+    for (int k = 0; k < D; ++k)
+      if (p->fallback_scales[k] > 0) f.v[k] = p->fallback_scales[k];
+  return f;
+}
+
+__global__ void k_gp_scales(double* sums, int M, int D, Fallback fallback, const double* fixed) {
   const int k = threadIdx.x;
   if (k >= D) return;
   if (fixed) { sums[k] = fixed[k]; return; }
-  double s = fallback;
+  double s = fallback.v[k];
   if (M >= 2) {
     const double m = sums[k] / (0.5 * (double)M * (double)(M - 1));
     if (m > 0.0) s = m;
@@ -315,7 +330,8 @@ static int gp_fit_impl(mdgp_gp* g, const double* X, const double* y, const doubl
   GK(cudaMalloc(&g->dscale, sizeof(double) * kMaxD));
   GK(cudaMemsetAsync(g->dscale, 0, sizeof(double) * kMaxD, s));
   if (M == 0) {
-    std::vector<double> fb(D, p->fallback_scale > 0 ? p->fallback_scale : 1.0);
+    const Fallback f = make_fallback(p, D);
+    std::vector<double> fb(f.v, f.v + D);
     GK(cudaMemcpyAsync(g->dscale, fb.data(), sizeof(double) * D, cudaMemcpyHostToDevice, s));
     GK(cudaStreamSynchronize(s));
     return MDGP_OK;
@@ -338,7 +354,7 @@ static int gp_fit_impl(mdgp_gp* g, const double* X, const double* y, const doubl
     GK(cudaMalloc(&dfixed, sizeof(double) * D));
     GK(cudaMemcpyAsync(dfixed, p->fixed_scales, sizeof(double) * D, cudaMemcpyHostToDevice, s));
   }
-  const double fallback = p->fallback_scale > 0 ? p->fallback_scale : 1.0;
+  const Fallback fallback = make_fallback(p, D);
   if (!p->fixed_scales) {
     k_gp_pairsep<<<(M + 255) / 256, 256, 0, s>>>(g->dX, M, D, g->dscale);
     g->launches++;
@@ -514,7 +530,7 @@ extern "C" int mdgp_gp_posterior_noalloc(const double* X, const double* y, int64
   int* status = (int*)(scale + kMaxD);
   // the scratch keeps the previous call's contents: clear the accumulators
   if (cudaMemsetAsync(scale, 0, sizeof(double) * (kMaxD + 8), s) != cudaSuccess) return MDGP_E_CUDA;
-  const double fallback = params->fallback_scale > 0 ? params->fallback_scale : 1.0;
+  const Fallback fallback = make_fallback(params, D);
   k_gp_pairsep<<<(Mi + 255) / 256, 256, 0, s>>>(X, Mi, D, scale);
   k_gp_scales<<<1, 32, 0, s>>>(scale, Mi, D, fallback, nullptr);
   // the factor is laid out with leading dimension Mp inside the fixed array

@@ -65,7 +65,13 @@ int fit_predict(mdgp_hybrid* H, const std::vector<double>& X, const std::vector<
   gp.sf2 = H->p.sf2;
   gp.l2 = H->p.l2;
   gp.sn2 = sn2;
+  // a dimension without spread in the database (all h equal, or the uniform
+  // gradient of the first steps) takes its natural scale: h0 / 2 for h, the
+  // forcing gradient amplitude dP_amp / L for G
+  const double L = H->p.n_sections * H->p.dx;
+  const double fb[2] = {0.5 * H->p.h0, H->p.dP_amp > 0 ? H->p.dP_amp / L : 1.0};
   gp.fallback_scale = 1.0;
+  gp.fallback_scales = fb;
   mdgp_gp* g = nullptr;
   int st = mdgp_gp_fit(H->ctx, M ? X.data() : nullptr, M ? y.data() : nullptr, M, 2, &gp,
                        (H->mean_fn && M) ? mX.data() : nullptr, &g);

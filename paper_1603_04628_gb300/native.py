@@ -44,7 +44,8 @@ class MDParams(ctypes.Structure):
 
 class GPParams(ctypes.Structure):
     _fields_ = [("sf2", ctypes.c_double), ("l2", ctypes.c_double), ("sn2", ctypes.c_double),
-                ("fallback_scale", ctypes.c_double), ("fixed_scales", ctypes.POINTER(ctypes.c_double))]
+                ("fallback_scale", ctypes.c_double), ("fixed_scales", ctypes.POINTER(ctypes.c_double)),
+                ("fallback_scales", ctypes.POINTER(ctypes.c_double))]
 
 
 class MacroParams(ctypes.Structure):
@@ -276,12 +277,17 @@ class Context:
 class GP:
     """A fitted Gaussian process (mdgp_gp) living on ctx's device."""
 
-    def __init__(self, ctx, X, y, sf2, l2, sn2, mu_X=None, fallback_scale=1.0, fixed_scales=None):
+    def __init__(self, ctx, X, y, sf2, l2, sn2, mu_X=None, fallback_scale=1.0, fixed_scales=None,
+                 fallback_scales=None):
         X = np.ascontiguousarray(np.asarray(X, dtype=np.float64).reshape(len(y), -1) if len(y) else
                                  np.zeros((0, np.asarray(X).shape[-1] if np.ndim(X) == 2 else 1)))
         y = np.ascontiguousarray(y, dtype=np.float64)
         self.D = X.shape[1]
-        p = GPParams(float(sf2), float(l2), float(sn2), float(fallback_scale), None)
+        p = GPParams(float(sf2), float(l2), float(sn2), float(fallback_scale), None, None)
+        self._fb = None
+        if fallback_scales is not None:
+            self._fb = np.ascontiguousarray(fallback_scales, dtype=np.float64)
+            p.fallback_scales = _dp(self._fb)
         self._fixed = None
         if fixed_scales is not None:
             self._fixed = np.ascontiguousarray(fixed_scales, dtype=np.float64)

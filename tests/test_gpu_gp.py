@@ -85,3 +85,20 @@ def test_large_database(ctx):
     assert np.abs(mg - mr).max() <= 1e-9 * max(np.abs(y).max(), 1.0)
     assert np.abs(vg - vr).max() <= 1e-10
     g.close()
+
+
+def test_per_dimension_fallback_scales(ctx):
+    from paper_1603_04628_gb300 import native
+    # dimension 1 has no spread: its scale is the per-dimension fallback
+    X = np.array([[0.0, 5.0], [1.0, 5.0], [3.0, 5.0]])
+    y = np.array([0.1, 0.4, -0.2])
+    g = native.GP(ctx, X, y, 1.0, 1.0, 0.01, fallback_scales=[0.7, 0.3])
+    np.testing.assert_allclose(g.scales(), [2.0, 0.3], rtol=1e-14)
+    ref = ogp.GP(X, y, 1.0, 1.0, 0.01, fallback=[0.7, 0.3])
+    Xs = np.array([[0.5, 5.1], [2.0, 4.8]])
+    m, v = g.predict(Xs)
+    mr, vr = ref.predict(Xs)
+    np.testing.assert_allclose(m, mr, rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(v, vr, rtol=1e-10, atol=1e-12)
+    g.close()
+

@@ -16,6 +16,20 @@ def test_scales_mean_pairwise_separation():
     # pairs along dim 0: |0-1|, |0-3|, |1-3| -> mean 2; dim 1 has no spread -> fallback
     np.testing.assert_allclose(gp.scales(X, fallback=0.7), [2.0, 0.7], rtol=0, atol=0)
     np.testing.assert_allclose(gp.scales(X[:1], fallback=1.0), [1.0, 1.0])
+    # per-dimension fallbacks apply only where the separation is undefined
+    np.testing.assert_allclose(gp.scales(X, fallback=[0.7, 0.3]), [2.0, 0.3], rtol=0, atol=0)
+    np.testing.assert_allclose(gp.scales(X[:1], fallback=[0.7, 0.3]), [0.7, 0.3])
+
+
+def test_channel_fallback_scales_are_h0_half_and_forcing_gradient():
+    from oracle import hybrid
+    ch = hybrid.Channel(n_sections=8, dx=50.0, h0=12.0, dP_amp=400.0)
+    np.testing.assert_allclose(ch.fallback, [6.0, 400.0 / (8 * 50.0)])
+    # the first step's inputs share one G: that dimension takes dP_amp / L
+    X = np.column_stack([ch.h, np.full(ch.N, -0.01)])
+    d = gp.scales(X, fallback=ch.fallback)
+    assert d[1] == pytest.approx(1.0)
+    assert d[0] > 0 and d[0] != 6.0
 
 
 def test_one_point_golden():
