@@ -40,6 +40,7 @@ CPU_SAMPLE_STEPS = 1000              # oracle steps per sampled element (~10-20 
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_step_df launch on this
 # workload (ncu capture, cold cache, 400 steps per element)
 STEP_KERNEL_TRAFFIC_BYTES = 73.9e6
+FP64_PEAK_TFLOPS = 0.99              # FP64 FMA chain measured on this GB300
 
 
 def _oracle_element_steps(args):
@@ -154,8 +155,11 @@ def main():
                     help="micro: the uneven micro-element batch (default); channel: the full hybrid "
                          "(Algorithm 1) threshold sweep on the 200-section channel")
     ap.add_argument("--channel-steps", type=int, default=100)
+    ap.add_argument("--paper-form", action="store_true",
+                    help="channel case with the paper's p-GP and (h, n, F) q-GP inputs")
     ap.add_argument("--sample-steps", type=int, default=300,
                     help="oracle steps per sampled element in the reference arm")
+    ap.add_argument("--no-gp-mlp", action="store_true", help="skip the GP and MLP timings")
     ap.add_argument("--workload", default="uneven", choices=["uneven", "stress"],
                     help="uneven: 64 elements, 500-5000 fluid atoms, 20000 steps (default); stress: 4096 "
                          "elements, 2k-32k fluid atoms, 60 M atoms, 10000 steps")
@@ -274,6 +278,12 @@ def main():
                 "steps_per_element": args.fp64_steps, "dtype": "f64"}
         c64.close()
 
+    # GP fit + predict (FP64 Cholesky) and the MLP prior mean, reported beside
+    # the MD headline (they are small against MD in every workload)
+    gp_mlp = None
+    if rank == 0 and args.workload == "uneven" and not args.no_gp_mlp:
+        gp_mlp = gp_mlp_timings(native, local)
+
     cpu = None
     if pool is not None:
         sample_els = els[:min(len(els), os.cpu_count() or 1)]
@@ -319,6 +329,7 @@ def main():
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
             "fp64_forces": fp64,
+            "gp_mlp": gp_mlp,
             "element_status_errors": len(bad),
             "element_status_codes": sorted(set(bad)),
             "list_capacity": cap,
@@ -328,6 +339,45 @@ def main():
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def gp_mlp_timings(native, device):
+    """Wall times of the GP (fit on M = 2000 entries in D = 2, predict 200
+    queries) and of the MLP prior mean (1000 epochs on 10^4 rows); the fit's
+    FP64 Cholesky rate against the measured FP64 peak."""
+    import numpy as np
+    ctx = native.Context(device, native.PREC_FP64)
+    M, m = 2000, 200
+    X, y = synth.gp_dataset(M, seed=synth.BASE_SEED + 21)
+    Xs = synth.gp_queries(m, seed=synth.BASE_SEED + 22)
+    g = native.GP(ctx, X, y, 1.0, 1.0, 0.0025)          # warm-up (allocations, module load)
+    g.predict(Xs); g.close()
+    reps = 5
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        g = native.GP(ctx, X, y, 1.0, 1.0, 0.0025)
+        g.close()
+    fit_s = (time.perf_counter() - t0) / reps
+    g = native.GP(ctx, X, y, 1.0, 1.0, 0.0025)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        g.predict(Xs)
+    pred_s = (time.perf_counter() - t0) / reps
+    g.close()
+    chol_flops = M ** 3 / 3.0
+    Xm = np.random.default_rng(synth.BASE_SEED + 23).uniform([6.0, -0.05], [18.0, 0.05], (10000, 2))
+    ym = np.sin(Xm[:, 0]) + 10.0 * Xm[:, 1]
+    net = native.MLP(ctx, seed=3)
+    t0 = time.perf_counter()
+    net.train(Xm, ym, epochs=1000, eval_every=100)
+    mlp_s = time.perf_counter() - t0
+    ctx.close()
+    return {"gp_fit_s": fit_s, "gp_predict_s": pred_s, "gp_M": M, "gp_queries": m,
+            "gp_fit_fp64_tflops": chol_flops / fit_s / 1e12, "fp64_peak_tflops": FP64_PEAK_TFLOPS,
+            "fp64_peak_note": "measured FP64 FMA chain on this GB300 (0.99 TFLOP/s)",
+            "gp_fit_frac": chol_flops / fit_s / 1e12 / FP64_PEAK_TFLOPS,
+            "mlp_train_s": mlp_s, "mlp_rows": len(ym), "mlp_epochs": 1000,
+            "timing": "wall clock of the C-ABI calls (host in/out), mean of 5 for the GP"}
 
 
 def run_channel_case(args):
@@ -342,8 +392,19 @@ def run_channel_case(args):
                   period=1000.0, dt=20.0, T=1.1, md_steps_eq=2000, md_steps_sample=3000, seed=synth.BASE_SEED,
                   sf2=(20 * sn) ** 2, l2=1.0, sn2=sn ** 2, sn2_from_data=0)
     thresholds = [f * sn for f in (0.5, 1.0, 2.0, 4.0, 8.0)]
+    pressure_db, form = None, "q-GP on (h, G), linear equation of state"
+    if args.paper_form:
+        # the paper's form (Sec. 2.4): p-GP over (h, n) from pre-simulations,
+        # q-GP on (h, n, F)
+        import numpy as np
+        X, p, p_se = cases.pressure_sweep(ctx, np.linspace(6.0, 18.0, 5), np.linspace(0.6, 1.0, 9),
+                                          T=params["T"], seed=synth.BASE_SEED + 7)
+        psn = float(np.mean(p_se))
+        pressure_db = (X, p, float(np.var(p)), 1.0, psn ** 2)
+        params["inputs"] = 1
+        form = "q-GP on (h, n, F), p-GP on (h, n) from %d pre-simulations (mean p SE %.3f)" % (len(p), psn)
     out = cases.channel_sweep(ctx, thresholds, n_steps=args.channel_steps, seed_noise=synth.BASE_SEED + 99,
-                              **params)
+                              pressure_db=pressure_db, **params)
     ref = out["reference"]
     rows = [{k: r[k] for k in ("sigma_t", "md_runs", "error", "speedup_eq", "wall_s", "wall_vs_reference",
                                 "gp_s", "md_s")} for r in out["rows"]]
@@ -351,7 +412,7 @@ def run_channel_case(args):
             "unit": "x", "n_gpus": 1, "data": "synthetic",
             "config": {"workload": "200-section converging-diverging channel, h0 = 12, 100 macro steps, "
                                    "plain 10 x h x 10 elements (2000 + 3000 steps, FP32 forces)",
-                       "sigma_n": sn, "sigma_f": 20 * sn},
+                       "sigma_n": sn, "sigma_f": 20 * sn, "form": form},
             "reference": {"md_runs": ref["md_runs"], "wall_s": ref["wall_s"]},
             "thermal_noise_error": out.get("noise_error"), "rows": rows}
     print(json.dumps(line), flush=True)

@@ -288,6 +288,9 @@ typedef struct {
   int64_t md_steps_eq, md_steps_sample;
   uint64_t seed;              /* MD seed; the k-th MD run of the case gets element id k */
   double sf2, l2, sn2;        /* q-GP hyperparameters (Sec. 2.3) */
+  int32_t inputs;             /* q-GP inputs: 0 = (h, G); 1 = the paper's (h, n, F) with
+                                 F = -G / n the force per unit mass on the fluid (Sec. 2.4) */
+  int32_t reserved;
 } mdgp_macro_params;
 
 /* Time step statistics returned by mdgp_hybrid_step. */
@@ -305,7 +308,8 @@ typedef struct {
 } mdgp_hybrid_stats;
 
 /* Prior mean for the GP (a learned mean): fill out[0..m) at the m rows of
- * x (m x 2, row-major).  Return 0 on success. */
+ * x (m x D row-major, D = 2 or 3 by mdgp_macro_params.inputs).  Return 0 on
+ * success. */
 typedef int (*mdgp_mean_fn)(void* user, const double* x, int64_t m, double* out);
 
 int mdgp_macro_params_default(mdgp_macro_params* p);
@@ -314,7 +318,8 @@ int mdgp_macro_params_default(mdgp_macro_params* p);
  * null); empty database.  Uses ctx for the GP and MD work. */
 int mdgp_hybrid_create(mdgp_ctx* ctx, const mdgp_macro_params* p, const double* density0, mdgp_hybrid** out);
 
-/* Use fn (with user) as the GP prior mean from now on (null: zero mean). */
+/* Use fn (with user) as the GP prior mean from now on (null: zero mean).
+ * mdgp_hybrid_set_mlp_mean needs the 2-input form (inputs = 0). */
 int mdgp_hybrid_set_mean(mdgp_hybrid* h, mdgp_mean_fn fn, void* user);
 
 /* One macro step with uncertainty threshold sigma_t (Algorithm 1): MD for
@@ -331,9 +336,18 @@ int mdgp_hybrid_step(mdgp_hybrid* h, double sigma_t, mdgp_hybrid_stats* stats);
 int mdgp_hybrid_state(const mdgp_hybrid* h, double* density, double* q, double* sd, int32_t* from_md,
                       double* G);
 
-/* Database: *M entries; with cap >= *M copies inputs (M x 2), outputs and
- * standard errors (any may be null). */
+/* Database: *M entries; with cap >= *M copies inputs (M x D, D = 2 or 3 by
+ * mdgp_macro_params.inputs), outputs and standard errors (any may be null). */
 int mdgp_hybrid_database(const mdgp_hybrid* h, double* X, double* y, double* se, int64_t cap, int64_t* M);
+
+/* Pressure from a GP instead of the linear equation of state (the paper's
+ * p-GP, Sec. 2.4): fit on M pre-simulation results, X (M x 2, row-major:
+ * channel height h, density n) and measured pressures y, with hyperparameters
+ * (sf2, l2, sn2) and the scales of Eq. d2Eq; every later step takes
+ * p_j = its posterior mean at (h_j, n_j).  M = 0 returns to the linear law.
+ * The arrays are copied.  MDGP_E_ARG on bad sizes or hyperparameters. */
+int mdgp_hybrid_set_pressure(mdgp_hybrid* h, const double* X, const double* y, int64_t M, double sf2, double l2,
+                             double sn2);
 int mdgp_hybrid_free(mdgp_hybrid* h);
 
 /* ------------------------------------------------------------------------ */

@@ -9,15 +9,17 @@ for the parts the paper leaves open are marked READING):
     h_j = h0 (1 - 0.5 cos(2 pi x_j / L)) (the converging-diverging channel in
     the benchmark's form; the paper's Eq. heightEq has the same shape);
   - state: fluid number density n_j (mass density m n_j, m = 1);
-  - READING: pressure from a linear equation of state p = K (n - n0) (the
-    paper uses a second GP on pre-simulations for p; a linear law keeps the
-    same role of a density-dependent pressure);
+  - pressure from a linear equation of state p = K (n - n0) (READING), or
+    as in the paper (Sec. 2.4) from a second GP, the p-GP over (h, n),
+    fitted once to pressures measured in pre-simulations and evaluated at
+    its posterior mean;
   - pressure gradient by periodic central differences (Alg. 1, the p' line);
   - READING: the sinusoidal inlet-outlet pressure difference
     dP(t) = dP_A sin(2 pi t / period) of the periodic channel acts as a
-    uniform gradient -dP / L; the GP input is x = (h_j, G_j) with
-    G_j = dp/dx_j - dP / L, and an MD element gets dpdx = G_j, so every fluid
-    atom feels F = -G_j / n_j (Eq. momentumEq with F_ext folded into G);
+    uniform gradient -dP / L; with G_j = dp/dx_j - dP / L an MD element gets
+    dpdx = G_j, so every fluid atom feels F = -G_j / n_j (Eq. momentumEq
+    with F_ext folded into G); the q-GP input is x = (h_j, G_j), or the
+    paper's (h_j, n_j, F_j) (inputs = 1);
   - q-GP (Eqs. quadraticKernelEq-predVarEq) on the database of (x, q) pairs,
     refit whenever the database grows; gate sd > sigma_t (strict);
   - READING: sigma_n is fixed during a macro step.  The paper measured it
@@ -38,7 +40,7 @@ from . import gp as ogp
 class Channel:
     def __init__(self, n_sections=8, dx=50.0, h0=12.0, Lx=10.0, Lz=10.0, K=10.0, n0=0.8, dP_amp=0.0,
                  period=1000.0, dt=20.0, T=1.1, steps_eq=100, steps_sample=100, seed=7, sf2=1.0, l2=1.0,
-                 sn2_default=0.0025, sn2_from_data=False, density0=None):
+                 sn2_default=0.0025, sn2_from_data=False, density0=None, inputs=0, pressure_db=None):
         self.N = int(n_sections)
         self.dx, self.h0, self.Lx, self.Lz = float(dx), float(h0), float(Lx), float(Lz)
         self.K, self.n0, self.dP_amp, self.period, self.dt = float(K), float(n0), float(dP_amp), float(period), float(dt)
@@ -48,12 +50,23 @@ class Channel:
         x = np.arange(self.N) * self.dx
         self.h = self.h0 * (1.0 - 0.5 * np.cos(2.0 * math.pi * x / L))
         # Eq. d2Eq's mean separation is undefined for an input without spread
-        # (all h equal; the uniform gradient of the first steps): h then takes
-        # h0 / 2, G the forcing gradient amplitude dP_amp / L
-        self.fallback = np.array([0.5 * self.h0, self.dP_amp / L if self.dP_amp > 0 else 1.0])
+        # (all h equal; the uniform gradient of the first steps; a uniform
+        # density): h then takes h0 / 2, G the forcing gradient amplitude
+        # dP_amp / L (F that over n0), n a tenth of n0
+        g = self.dP_amp / L if self.dP_amp > 0 else 1.0
+        self.D = 3 if inputs == 1 else 2
+        self.fallback = (np.array([0.5 * self.h0, g]) if self.D == 2 else
+                         np.array([0.5 * self.h0, 0.1 * self.n0, g / self.n0]))
+        # p-GP (Sec. 2.4): (X (M x 2: h, n), p, sf2, l2, sn2), or None for the linear law
+        self.pgp = None
+        if pressure_db is not None:
+            Xp, yp, psf2, pl2, psn2 = pressure_db
+            if len(yp):
+                self.pgp = ogp.GP(np.asarray(Xp, dtype=np.float64).reshape(-1, 2), np.asarray(yp, dtype=np.float64),
+                                  psf2, pl2, psn2, fallback=[0.5 * self.h0, 0.1 * self.n0])
         self.n = np.full(self.N, self.n0) if density0 is None else np.array(density0, dtype=np.float64)
         self.i = 0                       # macro steps taken
-        self.X = np.zeros((0, 2))
+        self.X = np.zeros((0, self.D))
         self.y = np.zeros(0)
         self.se = np.zeros(0)
         self.md_calls = 0
@@ -65,8 +78,19 @@ class Channel:
             return float(np.mean(self.se)) ** 2
         return self.sn2_default
 
+    def pressure(self):
+        if self.pgp is not None:
+            return self.pgp.predict(np.column_stack([self.h, self.n]))[0]
+        return self.K * (self.n - self.n0)
+
+    def inputs(self, j, G):
+        """Section j's q-GP input row."""
+        if self.D == 2:
+            return np.array([[self.h[j], G[j]]])
+        return np.array([[self.h[j], self.n[j], -G[j] / self.n[j]]])
+
     def gradients(self, t):
-        p = self.K * (self.n - self.n0)
+        p = self.pressure()
         dpdx = (np.roll(p, -1) - np.roll(p, 1)) / (2.0 * self.dx)
         dP = self.dP_amp * math.sin(2.0 * math.pi * t / self.period)
         return dpdx - dP / (self.N * self.dx)
@@ -91,7 +115,7 @@ class Channel:
         sn2 = self.sn2()
         q = np.zeros(self.N); sd = np.zeros(self.N); from_md = np.zeros(self.N, bool)
         for j in range(self.N):
-            x = np.array([[self.h[j], G[j]]])
+            x = self.inputs(j, G)
             g = ogp.GP(self.X, self.y, self.sf2, self.l2, sn2, fallback=self.fallback)
             m, v = g.predict(x)
             sd[j] = math.sqrt(v[0])
@@ -123,7 +147,7 @@ class Channel:
         Xv = self.X
         sd = np.zeros(self.N); from_md = np.zeros(self.N, bool)
         for j in range(self.N):
-            x = np.array([[self.h[j], G[j]]])
+            x = self.inputs(j, G)
             g = ogp.GP(Xv, np.zeros(len(Xv)), self.sf2, self.l2, sn2, fallback=self.fallback)   # y does not enter the variance
             v = g.predict(x)[1]
             sd[j] = math.sqrt(v[0])
@@ -140,13 +164,13 @@ class Channel:
         for j in range(self.N):
             if from_md[j]:
                 q[j] = res[k]["q"]
-                X = np.vstack([X, [[self.h[j], G[j]]]])
+                X = np.vstack([X, self.inputs(j, G)])
                 y = np.append(y, res[k]["q"])
                 se = np.append(se, res[k]["q_se"])
                 k += 1
             else:
                 g = ogp.GP(X, y, self.sf2, self.l2, sn2, fallback=self.fallback)
-                q[j] = g.predict(np.array([[self.h[j], G[j]]]))[0][0]
+                q[j] = g.predict(self.inputs(j, G))[0][0]
         self.X, self.y, self.se = X, y, se
         self.continuity(q)
         return dict(q=q, sd=sd, from_md=from_md, G=G)

@@ -34,13 +34,15 @@ def channel_atoms(params):
     return fluid + walls
 
 
-def run_channel(ctx, sigma_t, n_steps, mlp=None, sf2=None, **params):
+def run_channel(ctx, sigma_t, n_steps, mlp=None, sf2=None, pressure_db=None, **params):
     p = dict(params)
     if sf2 is not None:
         p["sf2"] = sf2
     hy = native.Hybrid(ctx, **p)
     if mlp is not None:
         hy.set_mlp_mean(mlp)
+    if pressure_db is not None:
+        hy.set_pressure(*pressure_db)
     qbar, md_runs, md_atoms = [], 0, 0
     t0 = time.perf_counter()
     gp_s = md_s = 0.0
@@ -62,11 +64,22 @@ def error(q, Q):
     return float(np.abs(np.asarray(q) - np.asarray(Q)).sum() / np.abs(np.asarray(Q)).sum())
 
 
-def channel_sweep(ctx, thresholds, n_steps=100, seed_noise=None, **params):
-    ref = run_channel(ctx, 0.0, n_steps, **params)
+def pressure_sweep(ctx, hs, densities, T=1.1, steps_eq=2000, steps_sample=3000, Lx=10.0, Lz=10.0, seed=1):
+    """Pre-simulations for the p-GP (paper Sec. 2.4): one MD element per
+    (h, n) pair with no flow forcing; returns inputs (M x 2: h, n), the
+    measured pressures and their standard errors."""
+    pairs = [(float(h), float(n)) for h in hs for n in densities]
+    els = [dict(h=h, Lx=Lx, Lz=Lz, density=n, T=T, g_ext=0.0, dpdx=0.0, steps_eq=steps_eq,
+                steps_sample=steps_sample, seed=int(seed), id=k) for k, (h, n) in enumerate(pairs)]
+    res = ctx.micro_batch(els)
+    return (np.array(pairs), np.array([r["p"] for r in res]), np.array([r["p_se"] for r in res]))
+
+
+def channel_sweep(ctx, thresholds, n_steps=100, seed_noise=None, pressure_db=None, **params):
+    ref = run_channel(ctx, 0.0, n_steps, pressure_db=pressure_db, **params)
     out = {"reference": ref}
     if seed_noise is not None:
-        noise = run_channel(ctx, 0.0, n_steps, **dict(params, seed=seed_noise))
+        noise = run_channel(ctx, 0.0, n_steps, pressure_db=pressure_db, **dict(params, seed=seed_noise))
         out["noise_error"] = error(noise["qbar"], ref["qbar"])
         out["noise"] = noise
     md_steps = params["md_steps_eq"] + params["md_steps_sample"]
@@ -74,7 +87,7 @@ def channel_sweep(ctx, thresholds, n_steps=100, seed_noise=None, **params):
     n_af = channel_atoms(params)
     rows = []
     for s in thresholds:
-        r = run_channel(ctx, s, n_steps, **params)
+        r = run_channel(ctx, s, n_steps, pressure_db=pressure_db, **params)
         mean_atoms = r["md_atoms"] / r["md_runs"] if r["md_runs"] else 0.0
         rows.append(dict(
             sigma_t=s, md_runs=r["md_runs"], error=error(r["qbar"], ref["qbar"]),

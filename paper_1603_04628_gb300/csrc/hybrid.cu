@@ -1,10 +1,12 @@
 // Macro time step of the hybrid scheme (paper Algorithm 1, Sec. 2.4) on top
 // of the library's GP and micro-batch entry points.
 //
-// One step: pressure from the equation of state, central-difference
+// One step: pressure from the equation of state (linear, or the p-GP of Sec.
+// 2.4 over (h, n) fitted to pressure pre-simulations), central-difference
 // gradients, the GP gate over all sections, one batched MD launch for the
 // gated sections, the means of the other sections, and the continuity update
-// (Eq. continuityEq).  The gate depends on the database inputs only (the
+// (Eq. continuityEq).  The q-GP inputs are (h, G) or the paper's (h, n, F)
+// with F = -G / n the force per unit mass on the fluid (Eq. momentumEq).  The gate depends on the database inputs only (the
 // posterior variance of Eq. predVarEq does not involve the outputs, and the
 // scales of Eq. d2Eq come from the inputs), so the set of sections Algorithm 1
 // sends to MD is decided before any MD runs; each non-MD section's mean then
@@ -27,10 +29,12 @@ struct mdgp_hybrid {
   long long md_total = 0;
   std::vector<double> h, n, q, sd, G;
   std::vector<int32_t> from_md;
-  std::vector<double> X, y, se;   // database: inputs (h, G) row-major, outputs, standard errors
+  int D = 2;                      // q-GP input dimension: (h, G) or (h, n, F)
+  std::vector<double> X, y, se;   // database: inputs row-major (D per entry), outputs, standard errors
   std::vector<double> mX;         // prior mean at the database inputs (learned mean), if any
   mdgp_mean_fn mean_fn = nullptr;
   void* mean_user = nullptr;
+  mdgp_gp* pgp = nullptr;         // pressure GP over (h, n), if set
 };
 
 namespace {
@@ -56,6 +60,33 @@ int prior_mean(mdgp_hybrid* H, const double* Xq, int64_t m, std::vector<double>&
   return H->mean_fn(H->mean_user, Xq, m, out.data());
 }
 
+// Natural scale of each q-GP input, used where the database has no spread in
+// it (all h equal; the uniform gradient of the first steps; uniform density):
+// h0 / 2 for h, the forcing gradient amplitude dP_amp / L for G (and that
+// over n0 for F), a tenth of n0 for n.
+void fallback_scales(const mdgp_hybrid* H, double* fb) {
+  const double L = H->p.n_sections * H->p.dx;
+  const double g = H->p.dP_amp > 0 ? H->p.dP_amp / L : 1.0;
+  fb[0] = 0.5 * H->p.h0;
+  if (H->D == 2) {
+    fb[1] = g;
+  } else {
+    fb[1] = 0.1 * H->p.eos_n0;
+    fb[2] = g / H->p.eos_n0;
+  }
+}
+
+// Section j's q-GP input row.
+void input_row(const mdgp_hybrid* H, int j, double* x) {
+  x[0] = H->h[j];
+  if (H->D == 2) {
+    x[1] = H->G[j];
+  } else {
+    x[1] = H->n[j];
+    x[2] = -H->G[j] / H->n[j];
+  }
+}
+
 // Fit on (X, y) rows [0, M) and predict the rows of Xq.
 int fit_predict(mdgp_hybrid* H, const std::vector<double>& X, const std::vector<double>& y,
                 const std::vector<double>& mX, int64_t M, double sn2, const double* Xq, int64_t m,
@@ -65,15 +96,12 @@ int fit_predict(mdgp_hybrid* H, const std::vector<double>& X, const std::vector<
   gp.sf2 = H->p.sf2;
   gp.l2 = H->p.l2;
   gp.sn2 = sn2;
-  // a dimension without spread in the database (all h equal, or the uniform
-  // gradient of the first steps) takes its natural scale: h0 / 2 for h, the
-  // forcing gradient amplitude dP_amp / L for G
-  const double L = H->p.n_sections * H->p.dx;
-  const double fb[2] = {0.5 * H->p.h0, H->p.dP_amp > 0 ? H->p.dP_amp / L : 1.0};
+  double fb[3];
+  fallback_scales(H, fb);
   gp.fallback_scale = 1.0;
   gp.fallback_scales = fb;
   mdgp_gp* g = nullptr;
-  int st = mdgp_gp_fit(H->ctx, M ? X.data() : nullptr, M ? y.data() : nullptr, M, 2, &gp,
+  int st = mdgp_gp_fit(H->ctx, M ? X.data() : nullptr, M ? y.data() : nullptr, M, H->D, &gp,
                        (H->mean_fn && M) ? mX.data() : nullptr, &g);
   if (st) return st;
   std::vector<double> mq;
@@ -108,12 +136,13 @@ int mdgp_macro_params_default(mdgp_macro_params* p) {
   p->l2 = 1.0;
   p->sn2 = 0.25;
   p->sn2_from_data = 0;
+  p->inputs = 0;
   return MDGP_OK;
 }
 
 int mdgp_hybrid_create(mdgp_ctx* ctx, const mdgp_macro_params* p, const double* density0, mdgp_hybrid** out) {
   if (!ctx || !p || !out || p->n_sections < 3 || !(p->dx > 0) || !(p->h0 > 0) || !(p->dt > 0) ||
-      !(p->period > 0) || !(p->sf2 > 0) || !(p->l2 > 0) || !(p->sn2 >= 0))
+      !(p->period > 0) || !(p->sf2 > 0) || !(p->l2 > 0) || !(p->sn2 >= 0) || p->inputs < 0 || p->inputs > 1)
     return MDGP_E_ARG;
   *out = nullptr;
   mdgp_hybrid* H = new (std::nothrow) mdgp_hybrid();
@@ -121,6 +150,7 @@ int mdgp_hybrid_create(mdgp_ctx* ctx, const mdgp_macro_params* p, const double* 
   H->ctx = ctx;
   H->p = *p;
   H->N = p->n_sections;
+  H->D = p->inputs == 1 ? 3 : 2;
   const double L = H->N * p->dx;
   H->h.resize(H->N);
   H->n.resize(H->N);
@@ -150,7 +180,7 @@ static int mlp_mean_fn(void* user, const double* x, int64_t m, double* out) {
 }
 
 int mdgp_hybrid_set_mlp_mean(mdgp_hybrid* H, mdgp_mlp* m) {
-  if (!H) return MDGP_E_ARG;
+  if (!H || (m && H->D != 2)) return MDGP_E_ARG;   // the network takes 2 inputs
   return m ? mdgp_hybrid_set_mean(H, mlp_mean_fn, m) : mdgp_hybrid_set_mean(H, nullptr, nullptr);
 }
 
@@ -161,16 +191,24 @@ int mdgp_hybrid_step(mdgp_hybrid* H, double sigma_t, mdgp_hybrid_stats* stats) {
   double t_gp = 0.0, t_md = 0.0, t0 = now_s();
   H->step += 1;
   const double t = H->step * P.dt;
-  // pressure gradient (central differences, periodic) and the forcing
+  // pressure (equation of state or p-GP mean), its gradient (central
+  // differences, periodic) and the forcing
   const double dP = P.dP_amp * std::sin(2.0 * M_PI * t / P.period);
-  for (int j = 0; j < N; ++j) {
-    const double pp = P.eos_K * (H->n[(j + 1) % N] - P.eos_n0);
-    const double pm = P.eos_K * (H->n[(j + N - 1) % N] - P.eos_n0);
-    H->G[j] = (pp - pm) / (2.0 * P.dx) - dP / (N * P.dx);
+  std::vector<double> pr((size_t)N);
+  if (H->pgp) {
+    std::vector<double> Xp((size_t)2 * N), pv((size_t)N);
+    for (int j = 0; j < N; ++j) { Xp[2 * j] = H->h[j]; Xp[2 * j + 1] = H->n[j]; }
+    int st = mdgp_gp_predict(H->pgp, Xp.data(), N, nullptr, pr.data(), pv.data());
+    if (st) return st;
+  } else {
+    for (int j = 0; j < N; ++j) pr[j] = P.eos_K * (H->n[j] - P.eos_n0);
   }
+  for (int j = 0; j < N; ++j)
+    H->G[j] = (pr[(j + 1) % N] - pr[(j + N - 1) % N]) / (2.0 * P.dx) - dP / (N * P.dx);
   const double sn2 = sn2_for_step(H);
-  std::vector<double> Xq((size_t)2 * N);
-  for (int j = 0; j < N; ++j) { Xq[2 * j] = H->h[j]; Xq[2 * j + 1] = H->G[j]; }
+  const int D = H->D;
+  std::vector<double> Xq((size_t)D * N);
+  for (int j = 0; j < N; ++j) input_row(H, j, Xq.data() + (size_t)D * j);
   // gate pass: variance on the inputs only, appending gated inputs in order.
   // sigma_t <= 0 sends every section to MD whatever the variance (the
   // reference run), so no GP work is done then.
@@ -185,7 +223,7 @@ int mdgp_hybrid_step(mdgp_hybrid* H, double sigma_t, mdgp_hybrid_stats* stats) {
       H->sd[j] = NAN;
       if (H->mean_fn) {
         std::vector<double> mq;
-        int st2 = prior_mean(H, Xq.data() + 2 * j, 1, mq);
+        int st2 = prior_mean(H, Xq.data() + (size_t)D * j, 1, mq);
         if (st2) return st2;
         mv.push_back(mq[0]);
       }
@@ -193,8 +231,9 @@ int mdgp_hybrid_step(mdgp_hybrid* H, double sigma_t, mdgp_hybrid_stats* stats) {
     j0 = N;
   }
   while (j0 < N) {
-    const int64_t Mv = (int64_t)(Xv.size() / 2);
-    int st = fit_predict(H, Xv, yv, mv, Mv, sn2, Xq.data() + 2 * j0, N - j0, mean.data() + j0, var.data() + j0);
+    const int64_t Mv = (int64_t)(Xv.size() / D);
+    int st = fit_predict(H, Xv, yv, mv, Mv, sn2, Xq.data() + (size_t)D * j0, N - j0, mean.data() + j0,
+                         var.data() + j0);
     if (st) return st;
     int j = j0;
     for (; j < N; ++j) {
@@ -203,12 +242,11 @@ int mdgp_hybrid_step(mdgp_hybrid* H, double sigma_t, mdgp_hybrid_stats* stats) {
     }
     if (j == N) break;
     md_idx.push_back(j);
-    Xv.push_back(H->h[j]);
-    Xv.push_back(H->G[j]);
+    for (int d = 0; d < D; ++d) Xv.push_back(Xq[(size_t)D * j + d]);
     yv.push_back(0.0);
     if (H->mean_fn) {
       std::vector<double> mq;
-      int st2 = prior_mean(H, Xq.data() + 2 * j, 1, mq);
+      int st2 = prior_mean(H, Xq.data() + (size_t)D * j, 1, mq);
       if (st2) return st2;
       mv.push_back(mq[0]);
     }
@@ -250,8 +288,7 @@ int mdgp_hybrid_step(mdgp_hybrid* H, double sigma_t, mdgp_hybrid_stats* stats) {
     if (k < nmd && md_idx[k] == j) {
       H->q[j] = res[k].q;
       H->from_md[j] = 1;
-      H->X.push_back(H->h[j]);
-      H->X.push_back(H->G[j]);
+      for (int d = 0; d < D; ++d) H->X.push_back(Xq[(size_t)D * j + d]);
       H->y.push_back(res[k].q);
       H->se.push_back(res[k].q_se);
       if (H->mean_fn) H->mX.push_back(mv[(size_t)M0 + k]);
@@ -261,7 +298,7 @@ int mdgp_hybrid_step(mdgp_hybrid* H, double sigma_t, mdgp_hybrid_stats* stats) {
     }
     const int jend = (k < nmd) ? md_idx[k] : N;
     const int64_t M = (int64_t)H->y.size();
-    int st = fit_predict(H, H->X, H->y, H->mX, M, sn2, Xq.data() + 2 * j, jend - j, mean.data() + j,
+    int st = fit_predict(H, H->X, H->y, H->mX, M, sn2, Xq.data() + (size_t)D * j, jend - j, mean.data() + j,
                          var.data() + j);
     if (st) return st;
     for (int i = j; i < jend; ++i) {
@@ -317,15 +354,33 @@ int mdgp_hybrid_database(const mdgp_hybrid* H, double* X, double* y, double* se,
   *M = m;
   if (cap < m) return (X || y || se) ? MDGP_E_ARG : MDGP_OK;
   for (int64_t i = 0; i < m; ++i) {
-    if (X) { X[2 * i] = H->X[2 * i]; X[2 * i + 1] = H->X[2 * i + 1]; }
+    if (X) for (int d = 0; d < H->D; ++d) X[H->D * i + d] = H->X[(size_t)H->D * i + d];
     if (y) y[i] = H->y[i];
     if (se) se[i] = H->se[i];
   }
   return MDGP_OK;
 }
 
+int mdgp_hybrid_set_pressure(mdgp_hybrid* H, const double* X, const double* y, int64_t M, double sf2, double l2,
+                             double sn2) {
+  if (!H || M < 0 || (M > 0 && (!X || !y)) || (M > 0 && (!(sf2 > 0) || !(l2 > 0) || !(sn2 >= 0))))
+    return MDGP_E_ARG;
+  if (H->pgp) { mdgp_gp_free(H->pgp); H->pgp = nullptr; }
+  if (M == 0) return MDGP_OK;   // back to the linear equation of state
+  mdgp_gp_params gp;
+  std::memset(&gp, 0, sizeof(gp));
+  gp.sf2 = sf2;
+  gp.l2 = l2;
+  gp.sn2 = sn2;
+  const double fb[2] = {0.5 * H->p.h0, 0.1 * H->p.eos_n0};
+  gp.fallback_scale = 1.0;
+  gp.fallback_scales = fb;
+  return mdgp_gp_fit(H->ctx, X, y, M, 2, &gp, nullptr, &H->pgp);
+}
+
 int mdgp_hybrid_free(mdgp_hybrid* H) {
   if (!H) return MDGP_E_ARG;
+  if (H->pgp) mdgp_gp_free(H->pgp);
   delete H;
   return MDGP_OK;
 }

@@ -54,7 +54,8 @@ class MacroParams(ctypes.Structure):
                 ("eos_K", ctypes.c_double), ("eos_n0", ctypes.c_double), ("dP_amp", ctypes.c_double),
                 ("period", ctypes.c_double), ("dt", ctypes.c_double), ("T", ctypes.c_double),
                 ("md_steps_eq", ctypes.c_int64), ("md_steps_sample", ctypes.c_int64), ("seed", ctypes.c_uint64),
-                ("sf2", ctypes.c_double), ("l2", ctypes.c_double), ("sn2", ctypes.c_double)]
+                ("sf2", ctypes.c_double), ("l2", ctypes.c_double), ("sn2", ctypes.c_double),
+                ("inputs", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class HybridStats(ctypes.Structure):
@@ -118,6 +119,8 @@ def lib():
         "mdgp_hybrid_step": ([vp, ctypes.c_double, ctypes.POINTER(HybridStats)], ctypes.c_int),
         "mdgp_hybrid_state": ([vp, dp, dp, dp, ctypes.POINTER(ctypes.c_int32), dp], ctypes.c_int),
         "mdgp_hybrid_database": ([vp, dp, dp, dp, i64, ctypes.POINTER(i64)], ctypes.c_int),
+        "mdgp_hybrid_set_pressure": ([vp, dp, dp, i64, ctypes.c_double, ctypes.c_double, ctypes.c_double],
+                                     ctypes.c_int),
         "mdgp_hybrid_free": ([vp], ctypes.c_int),
         "mdgp_mlp_params_default": ([ctypes.POINTER(MLPParams)], ctypes.c_int),
         "mdgp_mlp_num_params": ([], ctypes.c_int),
@@ -335,6 +338,7 @@ class Hybrid:
                 raise MdgpError("unknown macro parameter %r" % k)
             setattr(p, k, v)
         self.N = p.n_sections
+        self.D = 3 if p.inputs == 1 else 2
         self.ctx = ctx
         self.h = ctypes.c_void_p()
         d0 = None
@@ -346,7 +350,7 @@ class Hybrid:
         self._mean_cb = None
 
     def set_mean(self, fn):
-        """fn(X (m x 2) -> (m,)) as the GP prior mean, or None."""
+        """fn(X (m x D) -> (m,)) as the GP prior mean, or None."""
         if fn is None:
             self._mean_cb = None
             _check(self.ctx.h, lib().mdgp_hybrid_set_mean(self.h, MEAN_FN(), None), "mdgp_hybrid_set_mean")
@@ -354,7 +358,7 @@ class Hybrid:
 
         def cb(user, x, m, out):
             try:
-                X = np.ctypeslib.as_array(x, shape=(m, 2)).copy() if m else np.zeros((0, 2))
+                X = np.ctypeslib.as_array(x, shape=(m, self.D)).copy() if m else np.zeros((0, self.D))
                 v = np.asarray(fn(X), dtype=np.float64).reshape(m)
                 ctypes.memmove(out, v.ctypes.data, 8 * m)
                 return 0
@@ -385,10 +389,18 @@ class Hybrid:
         M = ctypes.c_int64()
         _check(None, lib().mdgp_hybrid_database(self.h, None, None, None, 0, ctypes.byref(M)), "db size")
         m = M.value
-        X = np.zeros((m, 2)); y = np.zeros(m); se = np.zeros(m)
+        X = np.zeros((m, self.D)); y = np.zeros(m); se = np.zeros(m)
         _check(None, lib().mdgp_hybrid_database(self.h, _dp(X), _dp(y), _dp(se), m, ctypes.byref(M)),
                "mdgp_hybrid_database")
         return X, y, se
+
+    def set_pressure(self, X, y, sf2, l2, sn2):
+        """Pressure GP over (h, n) from pre-simulations (empty X: linear law)."""
+        X = np.ascontiguousarray(np.asarray(X, dtype=np.float64).reshape(-1, 2))
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        _check(self.ctx.h, lib().mdgp_hybrid_set_pressure(self.h, _dp(X) if len(y) else None,
+                                                          _dp(y) if len(y) else None, len(y), float(sf2),
+                                                          float(l2), float(sn2)), "mdgp_hybrid_set_pressure")
 
     def close(self):
         if self.h:

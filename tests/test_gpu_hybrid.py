@@ -70,3 +70,33 @@ def test_learned_mean_leaves_gate_unchanged():
     gp_only = ~sa["from_md"]
     assert np.abs(sb["q"] - sa["q"])[gp_only].max() > 0.05    # the mean moved the predictions
     a.close(); b.close(); ctx.close()
+
+
+def test_paper_inputs_with_pressure_gp_match_sequential_oracle():
+    # the paper's form (Sec. 2.4): q-GP on (h, n, F), pressure from a p-GP on
+    # pre-simulation data; the same decisions and values as the sequential
+    # oracle with the same pressure database
+    from paper_1603_04628_gb300 import native
+    hs = np.linspace(6.0, 18.0, 4)
+    ns = np.linspace(0.6, 1.0, 5)
+    Xp = np.array([[h, n] for h in hs for n in ns])
+    yp = 10.0 * (Xp[:, 1] - 0.8) + 0.02 * np.cos(5.0 * Xp[:, 0] + 17.0 * Xp[:, 1])
+    pdb = (Xp, yp, 1.0, 1.0, 1e-4)
+    ctx = native.Context(0, native.PREC_FP64)
+    hy = native.Hybrid(ctx, inputs=1, **gpu_params(CASE))
+    hy.set_pressure(Xp, yp, 1.0, 1.0, 1e-4)
+    ref = ohy.Channel(inputs=1, pressure_db=pdb, **CASE)
+    for step in range(3):
+        hy.step(0.5)
+        r = ref.step_sequential(0.5, oracle_md)
+        s = hy.state()
+        assert (s["from_md"] == r["from_md"]).all(), step
+        np.testing.assert_allclose(s["G"], r["G"], rtol=1e-8, atol=1e-12)
+        np.testing.assert_allclose(s["sd"], r["sd"], rtol=1e-8, atol=1e-10)
+        np.testing.assert_allclose(s["q"], r["q"], rtol=1e-6, atol=1e-8)
+        np.testing.assert_allclose(s["density"], ref.n, rtol=1e-9)
+    X, y, se = hy.database()
+    assert X.shape[1] == 3 and len(y) == ref.md_calls > 0
+    np.testing.assert_allclose(X, ref.X, rtol=1e-8, atol=1e-12)
+    hy.close()
+    ctx.close()

@@ -71,3 +71,47 @@ def test_error_and_speedup_definitions():
     assert hybrid.relative_error([1.0, 2.0], [1.0, 4.0]) == pytest.approx(2.0 / 5.0)
     assert hybrid.speedup(1000, 5000, 100, 5, 1000) == pytest.approx(10.0)
     assert hybrid.speedup(1000, 5000, 100, 0, 1000) == math.inf
+
+
+def _pressure_db(K=10.0, n0=0.8):
+    # pre-simulation stand-in: a grid over (h, n) with the linear law plus a
+    # small deterministic perturbation
+    hs = np.linspace(6.0, 18.0, 5)
+    ns = np.linspace(0.6, 1.0, 7)
+    X = np.array([[h, n] for h in hs for n in ns])
+    y = K * (X[:, 1] - n0) + 0.01 * np.sin(7.0 * X[:, 0] + 31.0 * X[:, 1])
+    return X, y
+
+
+@pytest.mark.parametrize("sigma_t", [0.05, 0.3])
+def test_paper_inputs_and_pressure_gp_batched_equals_sequential(sigma_t):
+    # the paper's form: q-GP on (h, n, F), pressure from the p-GP; the gate is
+    # still a function of the inputs alone, so both orders agree
+    X, y = _pressure_db()
+    db = (X, y, 1.0, 1.0, 1e-4)
+    a = channel(inputs=1, pressure_db=db)
+    b = channel(inputs=1, pressure_db=db)
+    for step in range(8):
+        ra = a.step_sequential(sigma_t, fake_md)
+        rb = b.step_batched(sigma_t, fake_batch)
+        assert (ra["from_md"] == rb["from_md"]).all(), step
+        np.testing.assert_allclose(ra["q"], rb["q"], rtol=1e-9, atol=1e-12)
+        np.testing.assert_allclose(a.n, b.n, rtol=1e-12)
+    assert a.md_calls == b.md_calls > 0
+    assert a.X.shape[1] == 3
+
+
+def test_paper_inputs_rows_and_pressure_gp_interpolates():
+    X, y = _pressure_db()
+    c = channel(inputs=1, pressure_db=(X, y, 1.0, 1.0, 1e-6))
+    # at its own data the p-GP mean is K (K + sn2 I)^-1 y = y - sn2 alpha
+    # exactly, so it passes through the pre-simulations as sn2 -> 0
+    np.testing.assert_allclose(c.pgp.predict(X)[0], y - 1e-6 * c.pgp.alpha, rtol=0, atol=1e-9)
+    assert np.abs(c.pgp.predict(X)[0] - y).max() < 0.05
+    # F = -G / n: the force per unit mass an element feels (Eq. momentumEq)
+    G = c.gradients(20.0)
+    x = c.inputs(3, G)
+    np.testing.assert_allclose(x, [[c.h[3], c.n[3], -G[3] / c.n[3]]])
+    # no pre-simulation data: the linear law
+    d = channel(inputs=1)
+    np.testing.assert_allclose(d.pressure(), d.K * (d.n - d.n0))
