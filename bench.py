@@ -41,6 +41,10 @@ CPU_SAMPLE_STEPS = 1000              # oracle steps per sampled element (~10-20 
 # workload (ncu capture, cold cache, 400 steps per element)
 STEP_KERNEL_TRAFFIC_BYTES = 73.9e6
 FP64_PEAK_TFLOPS = 0.99              # FP64 FMA chain measured on this GB300
+# the same capture's l1tex throughput and issue-active fractions (the pair
+# loop is a gather: L1 and instruction issue bind, not FP32 arithmetic)
+STEP_KERNEL_L1_FRAC = 0.608
+STEP_KERNEL_ISSUE_FRAC = 0.523
 
 
 def _oracle_element_steps(args):
@@ -311,6 +315,8 @@ def main():
                          "achieved": achieved, "peak": fp32_peak,
                          "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                          "traffic": STEP_KERNEL_TRAFFIC_BYTES if args.workload == "uneven" else None,
+                         "l1_frac": STEP_KERNEL_L1_FRAC if args.workload == "uneven" else None,
+                         "issue_frac": STEP_KERNEL_ISSUE_FRAC if args.workload == "uneven" else None,
                          "peak_note": FP32_PEAK_NOTE + " (derived, max SM clock)",
                          "alg_flops_per_atom_step": ALG_FLOPS_PER_ATOM_STEP,
                          "force_ms": prof["force_ms"], "integrate_ms": prof["integrate_ms"],

@@ -28,16 +28,15 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
-// sum over pairs i < j of |x_ik - x_jk|, per dimension k (atomics into out[k])
+// sum over pairs i < j of |x_ik - x_jk|, per dimension k (atomics into
+// out[k]): block i takes row i, its threads stride over j > i.
 __global__ void k_gp_pairsep(const double* X, int M, int D, double* out) {
-  __shared__ double part[kMaxD][8];
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double acc[kMaxD];
-  for (int k = 0; k < D; ++k) acc[k] = 0.0;
-  if (i < M) {
-    for (int j = i + 1; j < M; ++j)
-      for (int k = 0; k < D; ++k) acc[k] += fabs(X[(size_t)i * D + k] - X[(size_t)j * D + k]);
-  }
+  __shared__ double part[kMaxD][32];
+  const int i = blockIdx.x;
+  double xi[kMaxD], acc[kMaxD];
+  for (int k = 0; k < D; ++k) { xi[k] = X[(size_t)i * D + k]; acc[k] = 0.0; }
+  for (int j = i + 1 + threadIdx.x; j < M; j += blockDim.x)
+    for (int k = 0; k < D; ++k) acc[k] += fabs(xi[k] - X[(size_t)j * D + k]);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int k = 0; k < D; ++k) {
     const double s = warp_sum_d(acc[k]);
@@ -107,8 +106,11 @@ __global__ void k_gp_cov(const double* X, int M, int Mp, int D, const double* sc
 
 // Cholesky of the diagonal tile kb in place (lower).  One block of TB x TB
 // threads; a non-positive pivot sets *status.
+// (FP64 issues at 1/64 of the FP32 rate here: the pivot's reciprocal is
+// taken once and the column multiplied by it.)
 __global__ void k_potrf_diag(double* A, int Mp, int kb, int* status) {
   __shared__ double T[TB][TB + 1];
+  __shared__ double rpiv;
   const int r = threadIdx.y, c = threadIdx.x;
   const size_t base = (size_t)kb * TB;
   T[r][c] = A[(base + r) * Mp + base + c];
@@ -117,10 +119,12 @@ __global__ void k_potrf_diag(double* A, int Mp, int kb, int* status) {
     if (r == k && c == k) {
       const double d = T[k][k];
       if (!(d > 0.0)) atomicMin(status, MDGP_E_NOTPD);
-      T[k][k] = sqrt(d > 0.0 ? d : 1e-300);
+      const double p = sqrt(d > 0.0 ? d : 1e-300);
+      T[k][k] = p;
+      rpiv = 1.0 / p;
     }
     __syncthreads();
-    if (c == k && r > k) T[r][k] /= T[k][k];
+    if (c == k && r > k) T[r][k] *= rpiv;
     __syncthreads();
     if (r > k && c > k && c <= r) T[r][c] -= T[r][k] * T[c][k];
     __syncthreads();
@@ -129,24 +133,26 @@ __global__ void k_potrf_diag(double* A, int Mp, int kb, int* status) {
 }
 
 // Panel: A_ik <- A_ik L_kk^-T for every tile row i > kb (one block per tile).
+// Each of the TB rows solves x L^T = a; the block sweeps the columns: once
+// x_j is final (divided by L_jj) every later column c subtracts x_j L_cj, all
+// rows and columns in parallel.
 __global__ void k_trsm_panel(double* A, int Mp, int kb) {
   __shared__ double L[TB][TB + 1];
   __shared__ double X[TB][TB + 1];
+  __shared__ double rd[TB];
   const int r = threadIdx.y, c = threadIdx.x;
   const int ib = kb + 1 + blockIdx.x;
   const size_t kr = (size_t)kb * TB, ir = (size_t)ib * TB;
   L[r][c] = A[(kr + r) * Mp + kr + c];
   X[r][c] = A[(ir + r) * Mp + kr + c];
+  if (r == c) rd[c] = 1.0 / A[(kr + r) * Mp + kr + c];
   __syncthreads();
-  // row r of X solves x L^T = a: x_j = (a_j - sum_{l<j} x_l L_jl) / L_jj
-  if (c == 0) {
-    for (int j = 0; j < TB; ++j) {
-      double s = X[r][j];
-      for (int l = 0; l < j; ++l) s -= X[r][l] * L[j][l];
-      X[r][j] = s / L[j][j];
-    }
+  for (int j = 0; j < TB; ++j) {
+    if (c == j) X[r][j] *= rd[j];
+    __syncthreads();
+    if (c > j) X[r][c] -= X[r][j] * L[c][j];
+    __syncthreads();
   }
-  __syncthreads();
   A[(ir + r) * Mp + kr + c] = X[r][c];
 }
 
@@ -172,51 +178,62 @@ __global__ void k_syrk_update(double* A, int Mp, int kb, int nt) {
 }
 
 // alpha = C^-1 (y - mu) by blocked forward then backward substitution in one
-// block: for each tile row of TB, the block updates the TB right-hand sides
-// with the part already solved, then one warp solves the TB x TB triangle.
-__global__ void k_gp_alpha(const double* L, int M, int Mp, const double* y, const double* mu, double* alpha) {
+// block of 32 warps.  Forward (L z = r), tile row by tile row: warp w
+// subtracts from z of row r0 + w its dot product with the solved part (lanes
+// over the row: coalesced), the TB x TB diagonal tile is staged in shared
+// memory and warp 0 solves the triangle.  Backward (L^T a = z): lane i owns
+// row r0 + i and the warps split the solved rows below (lanes read one row of
+// L: coalesced), the partial sums meet in shared memory, then warp 0 solves
+// the transposed triangle.
+__global__ void __launch_bounds__(1024) k_gp_alpha(const double* L, int M, int Mp, const double* y,
+                                                   const double* mu, double* alpha) {
   extern __shared__ double z[];
+  __shared__ double T[TB][TB + 1];
+  __shared__ double part[32][TB + 1];
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int lane = tid & 31, wid = tid >> 5;
-  const int per = nt / TB;   // threads per row of a tile (a power of two <= 32)
+  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   for (int i = tid; i < Mp; i += nt) z[i] = i < M ? y[i] - (mu ? mu[i] : 0.0) : 0.0;
   __syncthreads();
   const int nblk = Mp / TB;
-  // forward: L z = r
   for (int kb = 0; kb < nblk; ++kb) {
-    const int r0 = kb * TB, row = r0 + tid / per, sub = tid % per;
-    double s = 0.0;
-    for (int j = sub; j < r0; j += per) s += L[(size_t)row * Mp + j] * z[j];
-    for (int o = per >> 1; o > 0; o >>= 1) s += __shfl_down_sync(kFullMask, s, o, per);
-    __syncthreads();
-    if (sub == 0) z[row] -= s;
+    const int r0 = kb * TB;
+    for (int rr = wid; rr < TB; rr += nw) {
+      const int row = r0 + rr;
+      double s = 0.0;
+      for (int j = lane; j < r0; j += 32) s += L[(size_t)row * Mp + j] * z[j];
+      s = warp_sum_d(s);
+      T[rr][lane] = L[(size_t)row * Mp + r0 + lane];
+      if (lane == 0) z[row] -= s;
+    }
     __syncthreads();
     if (wid == 0) {
       double x = z[r0 + lane];
+      const double rdl = 1.0 / T[lane][lane];
       for (int j = 0; j < TB; ++j) {
-        if (lane == j) x /= L[(size_t)(r0 + j) * Mp + r0 + j];
+        if (lane == j) x *= rdl;
         const double xs = __shfl_sync(kFullMask, x, j);
-        if (lane > j) x -= L[(size_t)(r0 + lane) * Mp + r0 + j] * xs;
+        if (lane > j) x -= T[lane][j] * xs;
       }
       z[r0 + lane] = x;
     }
     __syncthreads();
   }
-  // backward: L^T a = z, tile rows from the last
   for (int kb = nblk - 1; kb >= 0; --kb) {
-    const int r0 = kb * TB, row = r0 + tid / per, sub = tid % per;
+    const int r0 = kb * TB;
     double s = 0.0;
-    for (int j = r0 + TB + sub; j < Mp; j += per) s += L[(size_t)j * Mp + row] * z[j];
-    for (int o = per >> 1; o > 0; o >>= 1) s += __shfl_down_sync(kFullMask, s, o, per);
-    __syncthreads();
-    if (sub == 0) z[row] -= s;
+    for (int j = r0 + TB + wid; j < Mp; j += nw) s += L[(size_t)j * Mp + r0 + lane] * z[j];
+    part[wid][lane] = s;
+    for (int rr = wid; rr < TB; rr += nw) T[rr][lane] = L[(size_t)(r0 + rr) * Mp + r0 + lane];
     __syncthreads();
     if (wid == 0) {
-      double x = z[r0 + lane];
+      double tot = 0.0;
+      for (int w = 0; w < nw; ++w) tot += part[w][lane];
+      double x = z[r0 + lane] - tot;
+      const double rdl = 1.0 / T[lane][lane];
       for (int j = TB - 1; j >= 0; --j) {
-        if (lane == j) x /= L[(size_t)(r0 + j) * Mp + r0 + j];
+        if (lane == j) x *= rdl;
         const double xs = __shfl_sync(kFullMask, x, j);
-        if (lane < j) x -= L[(size_t)(r0 + j) * Mp + r0 + lane] * xs;
+        if (lane < j) x -= T[j][lane] * xs;
       }
       z[r0 + lane] = x;
     }
@@ -226,14 +243,16 @@ __global__ void k_gp_alpha(const double* L, int M, int Mp, const double* y, cons
 }
 
 // One query per block: k*, mean, v = L^-1 k* by blocked forward
-// substitution (tile rows of TB: a block-wide update, then one warp solves
-// the TB x TB triangle), var = sf2 - |v|^2.
+// substitution (tile rows of TB: a warp per row subtracts the solved part,
+// then one warp solves the TB x TB triangle from shared memory),
+// var = sf2 - |v|^2.
 __global__ void k_gp_predict(const double* X, const double* L, const double* alpha, const double* scale,
                              int M, int Mp, int D, double sf2, double l2, const double* Xs, const double* mus,
                              double* mean, double* var) {
   extern __shared__ double v[];
   __shared__ double xq[kMaxD];
   __shared__ double red[32];
+  __shared__ double T[TB][TB + 1];
   const int q = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, wid = tid >> 5;
   if (tid < D) xq[tid] = Xs[(size_t)q * D + tid];
@@ -253,27 +272,29 @@ __global__ void k_gp_predict(const double* X, const double* L, const double* alp
     mean[q] = (mus ? mus[q] : 0.0) + t;
   }
   __syncthreads();
-  const int nblk = Mp / TB;
+  const int nblk = Mp / TB, nw = nt >> 5;
   for (int kb = 0; kb < nblk; ++kb) {
-    // update rows of tile kb with the solved part: v_r -= sum_{j < kb*TB} L_rj v_j
+    // rows of tile kb minus the solved part, v_r -= sum_{j < kb*TB} L_rj v_j:
+    // one warp per row, lanes along the row (coalesced); the diagonal tile
+    // goes to shared memory for the triangle
     const int r0 = kb * TB;
-    // nt/TB threads per row
-    const int per = nt / TB;
-    const int row = r0 + tid / per, sub = tid % per;
-    double s = 0.0;
-    for (int j = sub; j < r0; j += per) s += L[(size_t)row * Mp + j] * v[j];
-    // reduce the `per` partial sums of this row (per is a power of two <= 32)
-    for (int o = per >> 1; o > 0; o >>= 1) s += __shfl_down_sync(kFullMask, s, o, per);
-    __syncthreads();
-    if (sub == 0) v[row] -= s;
+    for (int rr = wid; rr < TB; rr += nw) {
+      const int row = r0 + rr;
+      double s = 0.0;
+      for (int j = lane; j < r0; j += 32) s += L[(size_t)row * Mp + j] * v[j];
+      s = warp_sum_d(s);
+      T[rr][lane] = L[(size_t)row * Mp + r0 + lane];
+      if (lane == 0) v[row] -= s;
+    }
     __syncthreads();
     // triangle solve by warp 0: lane r owns row r0 + r
     if (wid == 0) {
       double x = v[r0 + lane];
+      const double rdl = 1.0 / T[lane][lane];
       for (int j = 0; j < TB; ++j) {
-        if (lane == j) x /= L[(size_t)(r0 + j) * Mp + r0 + j];
+        if (lane == j) x *= rdl;
         const double xs = __shfl_sync(kFullMask, x, j);   // solved unknown j
-        if (lane > j) x -= L[(size_t)(r0 + lane) * Mp + r0 + j] * xs;
+        if (lane > j) x -= T[lane][j] * xs;
       }
       v[r0 + lane] = x;
     }
@@ -356,7 +377,7 @@ static int gp_fit_impl(mdgp_gp* g, const double* X, const double* y, const doubl
   }
   const Fallback fallback = make_fallback(p, D);
   if (!p->fixed_scales) {
-    k_gp_pairsep<<<(M + 255) / 256, 256, 0, s>>>(g->dX, M, D, g->dscale);
+    k_gp_pairsep<<<M, 128, 0, s>>>(g->dX, M, D, g->dscale);
     g->launches++;
   }
   k_gp_scales<<<1, 32, 0, s>>>(g->dscale, M, D, fallback, dfixed);
@@ -373,9 +394,8 @@ static int gp_fit_impl(mdgp_gp* g, const double* X, const double* y, const doubl
       g->launches += 2;
     }
   }
-  if (sizeof(double) * Mp > 48 * 1024)
-    GK(cudaFuncSetAttribute(k_gp_alpha, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(double) * Mp)));
-  k_gp_alpha<<<1, 256, sizeof(double) * Mp, s>>>(g->dL, M, Mp, dy, dmuX, g->dalpha);
+  GK(cudaFuncSetAttribute(k_gp_alpha, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(double) * Mp)));
+  k_gp_alpha<<<1, 1024, sizeof(double) * Mp, s>>>(g->dL, M, Mp, dy, dmuX, g->dalpha);
   g->launches++;
   int status = 0;
   GK(cudaGetLastError());
@@ -442,8 +462,7 @@ int mdgp_gp_predict(mdgp_gp* g, const double* Xs, int64_t m, const double* mu_Xs
   GK(cudaMemcpyAsync(g->dq, Xs, sizeof(double) * m * g->D, cudaMemcpyHostToDevice, s));
   if (mu_Xs) GK(cudaMemcpyAsync(g->dmu, mu_Xs, sizeof(double) * m, cudaMemcpyHostToDevice, s));
   const size_t smem = sizeof(double) * g->Mp;
-  if (smem > 48 * 1024)
-    GK(cudaFuncSetAttribute(k_gp_predict, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  GK(cudaFuncSetAttribute(k_gp_predict, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_gp_predict<<<(unsigned)m, 256, smem, s>>>(g->dX, g->dL, g->dalpha, g->dscale, g->M, g->Mp, g->D, g->sf2,
                                               g->l2, g->dq, mu_Xs ? g->dmu : nullptr, g->dmean, g->dvar);
   g->launches++;
@@ -531,7 +550,7 @@ extern "C" int mdgp_gp_posterior_noalloc(const double* X, const double* y, int64
   // the scratch keeps the previous call's contents: clear the accumulators
   if (cudaMemsetAsync(scale, 0, sizeof(double) * (kMaxD + 8), s) != cudaSuccess) return MDGP_E_CUDA;
   const Fallback fallback = make_fallback(params, D);
-  k_gp_pairsep<<<(Mi + 255) / 256, 256, 0, s>>>(X, Mi, D, scale);
+  k_gp_pairsep<<<Mi, 128, 0, s>>>(X, Mi, D, scale);
   k_gp_scales<<<1, 32, 0, s>>>(scale, Mi, D, fallback, nullptr);
   // the factor is laid out with leading dimension Mp inside the fixed array
   k_gp_cov<<<dim3((Mp + 127) / 128, Mp), 128, 0, s>>>(X, Mi, Mp, D, scale, params->sf2, params->l2, params->sn2,
