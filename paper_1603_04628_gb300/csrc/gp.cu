@@ -104,48 +104,57 @@ __global__ void k_gp_cov(const double* X, int M, int Mp, int D, const double* sc
   C[(size_t)i * Mp + j] = v;
 }
 
-// Cholesky of the diagonal tile kb in place (lower).  One block of TB x TB
-// threads; a non-positive pivot sets *status.
-// (FP64 issues at 1/64 of the FP32 rate here: the pivot's reciprocal is
-// taken once and the column multiplied by it.)
-__global__ void k_potrf_diag(double* A, int Mp, int kb, int* status) {
-  __shared__ double T[TB][TB + 1];
-  __shared__ double rpiv;
-  const int r = threadIdx.y, c = threadIdx.x;
+// Cholesky of the diagonal tile kb in place (lower), one warp: lane i holds
+// row i in registers; at step k the pivot and the scaled column k come from
+// the owning lanes by shuffles (no block barriers on the serial path).  FP64
+// issues at 1/64 of the FP32 rate here, so the pivot comes from one rsqrt
+// (p = d rsqrt(d)) and the column is multiplied by it.  A non-positive pivot
+// sets *status.
+__global__ void __launch_bounds__(32) k_potrf_diag(double* A, int Mp, int kb, int* status) {
+  const int i = threadIdx.x;
   const size_t base = (size_t)kb * TB;
-  T[r][c] = A[(base + r) * Mp + base + c];
-  __syncthreads();
+  double row[TB];
+#pragma unroll
+  for (int c = 0; c < TB; ++c) row[c] = A[(base + i) * Mp + base + c];
+#pragma unroll
   for (int k = 0; k < TB; ++k) {
-    if (r == k && c == k) {
-      const double d = T[k][k];
-      if (!(d > 0.0)) atomicMin(status, MDGP_E_NOTPD);
-      const double p = sqrt(d > 0.0 ? d : 1e-300);
-      T[k][k] = p;
-      rpiv = 1.0 / p;
+    const double d = __shfl_sync(kFullMask, row[k], k);
+    const bool ok = d > 0.0;
+    if (i == k && !ok) atomicMin(status, MDGP_E_NOTPD);
+    const double rp = rsqrt(ok ? d : 1e-300);   // one FP64 routine instead of sqrt and a divide
+    const double p = (ok ? d : 1e-300) * rp;
+    if (i == k) row[k] = p;
+    if (i > k) row[k] *= rp;
+#pragma unroll
+    for (int c = k + 1; c < TB; ++c) {
+      const double tck = __shfl_sync(kFullMask, row[k], c);   // T[c][k], scaled, from lane c
+      if (i >= c) row[c] -= row[k] * tck;
     }
-    __syncthreads();
-    if (c == k && r > k) T[r][k] *= rpiv;
-    __syncthreads();
-    if (r > k && c > k && c <= r) T[r][c] -= T[r][k] * T[c][k];
-    __syncthreads();
   }
-  A[(base + r) * Mp + base + c] = c <= r ? T[r][c] : 0.0;
+#pragma unroll
+  for (int c = 0; c < TB; ++c) A[(base + i) * Mp + base + c] = c <= i ? row[c] : 0.0;
 }
 
-// Panel: A_ik <- A_ik L_kk^-T for every tile row i > kb (one block per tile).
-// Each of the TB rows solves x L^T = a; the block sweeps the columns: once
-// x_j is final (divided by L_jj) every later column c subtracts x_j L_cj, all
-// rows and columns in parallel.
+// Panel: A_ik <- A_ik L_kk^-T for every tile row i > kb.  A block of
+// TB x kTrsmRows threads takes kTrsmRows rows of one tile (TB / kTrsmRows
+// blocks per tile, so early panels spread over more SMs).  Each row solves
+// x L^T = a; the block sweeps the columns: once x_j is final (times 1/L_jj)
+// every later column c subtracts x_j L_cj, rows and columns in parallel.
+constexpr int kTrsmRows = 8;
+
 __global__ void k_trsm_panel(double* A, int Mp, int kb) {
   __shared__ double L[TB][TB + 1];
-  __shared__ double X[TB][TB + 1];
+  __shared__ double X[kTrsmRows][TB + 1];
   __shared__ double rd[TB];
   const int r = threadIdx.y, c = threadIdx.x;
-  const int ib = kb + 1 + blockIdx.x;
-  const size_t kr = (size_t)kb * TB, ir = (size_t)ib * TB;
-  L[r][c] = A[(kr + r) * Mp + kr + c];
+  constexpr int parts = TB / kTrsmRows;
+  const int ib = kb + 1 + blockIdx.x / parts;
+  const int r_off = (blockIdx.x % parts) * kTrsmRows;
+  const size_t kr = (size_t)kb * TB, ir = (size_t)ib * TB + r_off;
+  for (int rr = r; rr < TB; rr += kTrsmRows) L[rr][c] = A[(kr + rr) * Mp + kr + c];
   X[r][c] = A[(ir + r) * Mp + kr + c];
-  if (r == c) rd[c] = 1.0 / A[(kr + r) * Mp + kr + c];
+  __syncthreads();
+  if (r == 0) rd[c] = 1.0 / L[c][c];
   __syncthreads();
   for (int j = 0; j < TB; ++j) {
     if (c == j) X[r][j] *= rd[j];
@@ -385,11 +394,11 @@ static int gp_fit_impl(mdgp_gp* g, const double* X, const double* y, const doubl
   g->launches += 2;
   const int nt = Mp / TB;
   for (int kb = 0; kb < nt; ++kb) {
-    k_potrf_diag<<<1, dim3(TB, TB), 0, s>>>(g->dL, Mp, kb, dstatus);
+    k_potrf_diag<<<1, 32, 0, s>>>(g->dL, Mp, kb, dstatus);
     g->launches++;
     const int rest = nt - kb - 1;
     if (rest > 0) {
-      k_trsm_panel<<<rest, dim3(TB, TB), 0, s>>>(g->dL, Mp, kb);
+      k_trsm_panel<<<rest * (TB / kTrsmRows), dim3(TB, kTrsmRows), 0, s>>>(g->dL, Mp, kb);
       k_syrk_update<<<rest * (rest + 1) / 2, dim3(TB, TB), 0, s>>>(g->dL, Mp, kb, nt);
       g->launches += 2;
     }
@@ -557,10 +566,10 @@ extern "C" int mdgp_gp_posterior_noalloc(const double* X, const double* y, int64
                                                       L);
   const int nt = Mp / TB;
   for (int kb = 0; kb < nt; ++kb) {
-    k_potrf_diag<<<1, dim3(TB, TB), 0, s>>>(L, Mp, kb, status);
+    k_potrf_diag<<<1, 32, 0, s>>>(L, Mp, kb, status);
     const int rest = nt - kb - 1;
     if (rest > 0) {
-      k_trsm_panel<<<rest, dim3(TB, TB), 0, s>>>(L, Mp, kb);
+      k_trsm_panel<<<rest * (TB / kTrsmRows), dim3(TB, kTrsmRows), 0, s>>>(L, Mp, kb);
       k_syrk_update<<<rest * (rest + 1) / 2, dim3(TB, TB), 0, s>>>(L, Mp, kb, nt);
     }
   }
