@@ -155,9 +155,10 @@ def main():
                     help="steps of the FP64-forces pass reported beside the headline")
     ap.add_argument("--steps-per-element", type=int, default=STEPS_PER_ELEMENT,
                     help="MD steps per element (shorter runs for profiling only)")
-    ap.add_argument("--case", default="micro", choices=["micro", "channel"],
+    ap.add_argument("--case", default="micro", choices=["micro", "channel", "gp"],
                     help="micro: the uneven micro-element batch (default); channel: the full hybrid "
-                         "(Algorithm 1) threshold sweep on the 200-section channel")
+                         "(Algorithm 1) threshold sweep on the 200-section channel; gp: the GP and "
+                         "MLP timings alone")
     ap.add_argument("--channel-steps", type=int, default=100)
     ap.add_argument("--paper-form", action="store_true",
                     help="channel case with the paper's p-GP and (h, n, F) q-GP inputs")
@@ -172,6 +173,12 @@ def main():
         return run_reference(args)
     if args.case == "channel":
         return run_channel_case(args)
+    if args.case == "gp":
+        import torch
+        torch.cuda.set_device(0)
+        from paper_1603_04628_gb300 import native
+        print(json.dumps({"case": "gp", "n_gpus": 1, "data": "synthetic", **gp_mlp_timings(native, 0)}), flush=True)
+        return 0
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -261,6 +261,23 @@ int mdgp_gp_posterior_noalloc(const double* X, const double* y, int64_t M, int32
 
 /* The D input scales the fit used (Eq. d2Eq denominators). */
 int mdgp_gp_scales(const mdgp_gp* gp, double* scales);
+
+/* Log marginal likelihood of the fitted data (Eq. evidenceEq, Sec. 2.3):
+ * -1/2 (y - mu)^T C^-1 (y - mu) - 1/2 log det C - M/2 log 2 pi, with the
+ * fit's scales and hyperparameters; 0 for an empty database. */
+int mdgp_gp_log_marginal(const mdgp_gp* gp, double* lml);
+
+/* Hyperparameters by maximum evidence (Sec. 2.3): a pattern search over
+ * (sf2, l2, sn2) from *start (its fallback and fixed scales are kept):
+ * each coordinate in turn tries value x step and value / step and keeps the
+ * better evidence (a gain above 1e-9 relative); a pass without a move takes
+ * the square root of the step, from 4 down to 1.05, or until max_evals fits.
+ * Every trial is a GPU fit.  A trial whose covariance is not positive
+ * definite scores -inf.  *best receives the result and *best_lml (nullable)
+ * its log marginal likelihood.  MDGP_E_ARG for M < 1. */
+int mdgp_gp_optimize(mdgp_ctx* ctx, const double* X, const double* y, int64_t M, int32_t D,
+                     const mdgp_gp_params* start, const double* mu_X, int32_t max_evals, mdgp_gp_params* best,
+                     double* best_lml);
 int mdgp_gp_free(mdgp_gp* gp);
 
 /* ------------------------------------------------------------------------ */

@@ -17,6 +17,8 @@ Follows the paper's Sec. 2.2 and 2.3:
 The Cholesky factorisation and triangular solves are numpy/scipy library
 primitives used as single steps.
 """
+import math
+
 import numpy as np
 import scipy.linalg as sla
 
@@ -100,3 +102,42 @@ def gate(sd, sigma_t):
     """Alg. 1: an MD run is requested when the predicted standard deviation
     exceeds the threshold (strict inequality)."""
     return np.asarray(sd) > sigma_t
+
+
+def optimize(X, y, sf2, l2, sn2, mu=None, fallback=1.0, max_evals=200):
+    """Hyperparameters by maximum evidence (Sec. 2.3, Eq. evidenceEq): a
+    pattern search over (sf2, l2, sn2).  Each coordinate in turn tries
+    value * step and value / step and keeps the better log marginal
+    likelihood when it gains more than 1e-9 relative (+1e-12); a pass with no
+    move takes the square root of the step, from 4 while it exceeds 1.05, or
+    until max_evals evaluations.  A covariance that is not positive definite
+    scores -inf.  Returns (sf2, l2, sn2, lml)."""
+    def lml(h):
+        try:
+            return GP(X, y, h[0], h[1], h[2], mu=mu, fallback=fallback).log_marginal_likelihood()
+        except np.linalg.LinAlgError:
+            return -np.inf
+    cur = [float(sf2), float(l2), float(sn2)]
+    f = lml(cur)
+    evals, step = 1, 4.0
+    while step > 1.05 and evals < max_evals:
+        moved = False
+        for k in range(3):
+            if evals >= max_evals:
+                break
+            v0 = cur[k]
+            bestv, bestf = v0, f
+            for v in (v0 * step, v0 / step):
+                if evals >= max_evals:
+                    break
+                cur[k] = v
+                ft = lml(cur)
+                evals += 1
+                if ft > bestf + 1e-9 * abs(bestf) + 1e-12:
+                    bestf, bestv = ft, v
+            cur[k] = bestv
+            if bestv != v0:
+                f, moved = bestf, True
+        if not moved:
+            step = math.sqrt(step)
+    return cur[0], cur[1], cur[2], f

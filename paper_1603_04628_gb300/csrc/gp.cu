@@ -195,7 +195,7 @@ __global__ void k_syrk_update(double* A, int Mp, int kb, int nt) {
 // L: coalesced), the partial sums meet in shared memory, then warp 0 solves
 // the transposed triangle.
 __global__ void __launch_bounds__(1024) k_gp_alpha(const double* L, int M, int Mp, const double* y,
-                                                   const double* mu, double* alpha) {
+                                                   const double* mu, double* alpha, double* r_dot_alpha) {
   extern __shared__ double z[];
   __shared__ double T[TB][TB + 1];
   __shared__ double part[32][TB + 1];
@@ -249,6 +249,36 @@ __global__ void __launch_bounds__(1024) k_gp_alpha(const double* L, int M, int M
     __syncthreads();
   }
   for (int i = tid; i < M; i += nt) alpha[i] = z[i];
+  if (r_dot_alpha) {
+    // (y - mu)^T alpha, the data term of Eq. evidenceEq
+    double s = 0.0;
+    for (int i = tid; i < M; i += nt) s += (y[i] - (mu ? mu[i] : 0.0)) * z[i];
+    s = warp_sum_d(s);
+    __syncthreads();
+    if (lane == 0) part[wid][0] = s;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < nw; ++w) t += part[w][0];
+      *r_dot_alpha = t;
+    }
+  }
+}
+
+// sum_i log L_ii over the M data rows: half the log-determinant of C
+// (Eq. evidenceEq).
+__global__ void k_gp_logdiag(const double* L, int M, int Mp, double* out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < M; i += blockDim.x) s += log(L[(size_t)i * Mp + i]);
+  s = warp_sum_d(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    *out = t;
+  }
 }
 
 // One query per block: k*, mean, v = L^-1 k* by blocked forward
@@ -357,8 +387,9 @@ static int gp_fit_impl(mdgp_gp* g, const double* X, const double* y, const doubl
                        const mdgp_gp_params* p) {
   const int M = g->M, D = g->D, Mp = g->Mp;
   cudaStream_t s = g->stream;
-  GK(cudaMalloc(&g->dscale, sizeof(double) * kMaxD));
-  GK(cudaMemsetAsync(g->dscale, 0, sizeof(double) * kMaxD, s));
+  // the scales, then (y - mu)^T alpha and sum log L_ii for the evidence
+  GK(cudaMalloc(&g->dscale, sizeof(double) * (kMaxD + 2)));
+  GK(cudaMemsetAsync(g->dscale, 0, sizeof(double) * (kMaxD + 2), s));
   if (M == 0) {
     const Fallback f = make_fallback(p, D);
     std::vector<double> fb(f.v, f.v + D);
@@ -404,7 +435,8 @@ static int gp_fit_impl(mdgp_gp* g, const double* X, const double* y, const doubl
     }
   }
   GK(cudaFuncSetAttribute(k_gp_alpha, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(double) * Mp)));
-  k_gp_alpha<<<1, 1024, sizeof(double) * Mp, s>>>(g->dL, M, Mp, dy, dmuX, g->dalpha);
+  k_gp_alpha<<<1, 1024, sizeof(double) * Mp, s>>>(g->dL, M, Mp, dy, dmuX, g->dalpha, g->dscale + kMaxD);
+  k_gp_logdiag<<<1, 256, 0, s>>>(g->dL, M, Mp, g->dscale + kMaxD + 1);
   g->launches++;
   int status = 0;
   GK(cudaGetLastError());
@@ -479,6 +511,63 @@ int mdgp_gp_predict(mdgp_gp* g, const double* Xs, int64_t m, const double* mu_Xs
   GK(cudaMemcpyAsync(mean, g->dmean, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
   GK(cudaMemcpyAsync(var, g->dvar, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
   GK(cudaStreamSynchronize(s));
+  return MDGP_OK;
+}
+
+int mdgp_gp_log_marginal(const mdgp_gp* g, double* lml) {
+  if (!g || !lml) return MDGP_E_ARG;
+  if (g->M == 0) { *lml = 0.0; return MDGP_OK; }
+  cudaSetDevice(g->device);
+  double t[2];
+  if (cudaMemcpy(t, g->dscale + kMaxD, sizeof(t), cudaMemcpyDeviceToHost) != cudaSuccess) return MDGP_E_CUDA;
+  *lml = -0.5 * t[0] - t[1] - 0.5 * g->M * std::log(2.0 * M_PI);
+  return MDGP_OK;
+}
+
+// Evidence of one hyperparameter set: a fit, its log marginal likelihood;
+// a covariance that is not positive definite scores -inf.
+static int evidence(mdgp_ctx* ctx, const double* X, const double* y, int64_t M, int32_t D,
+                    const mdgp_gp_params& p, const double* mu_X, double* lml) {
+  mdgp_gp* g = nullptr;
+  const int st = mdgp_gp_fit(ctx, X, y, M, D, &p, mu_X, &g);
+  if (st == MDGP_E_NOTPD) { *lml = -INFINITY; return MDGP_OK; }
+  if (st) return st;
+  const int st2 = mdgp_gp_log_marginal(g, lml);
+  mdgp_gp_free(g);
+  return st2;
+}
+
+int mdgp_gp_optimize(mdgp_ctx* ctx, const double* X, const double* y, int64_t M, int32_t D,
+                     const mdgp_gp_params* start, const double* mu_X, int32_t max_evals, mdgp_gp_params* best,
+                     double* best_lml) {
+  if (!ctx || !start || !best || M < 1 || max_evals < 1) return MDGP_E_ARG;
+  mdgp_gp_params cur = *start;
+  double f = 0.0;
+  int st = evidence(ctx, X, y, M, D, cur, mu_X, &f);
+  if (st) return st;
+  int evals = 1;
+  double step = 4.0;   // multiplicative step in each hyperparameter
+  while (step > 1.05 && evals < max_evals) {
+    bool moved = false;
+    for (int k = 0; k < 3 && evals < max_evals; ++k) {
+      double* v = k == 0 ? &cur.sf2 : (k == 1 ? &cur.l2 : &cur.sn2);
+      const double v0 = *v;
+      double bestv = v0, bestf = f;
+      for (int dir = 0; dir < 2 && evals < max_evals; ++dir) {
+        *v = dir == 0 ? v0 * step : v0 / step;
+        double ft = 0.0;
+        if ((st = evidence(ctx, X, y, M, D, cur, mu_X, &ft))) { *best = *start; return st; }
+        ++evals;
+        // a move must gain more than rounding can explain
+        if (ft > bestf + 1e-9 * std::fabs(bestf) + 1e-12) { bestf = ft; bestv = *v; }
+      }
+      *v = bestv;
+      if (bestv != v0) { f = bestf; moved = true; }
+    }
+    if (!moved) step = std::sqrt(step);
+  }
+  *best = cur;
+  if (best_lml) *best_lml = f;
   return MDGP_OK;
 }
 
@@ -573,7 +662,7 @@ extern "C" int mdgp_gp_posterior_noalloc(const double* X, const double* y, int64
       k_syrk_update<<<rest * (rest + 1) / 2, dim3(TB, TB), 0, s>>>(L, Mp, kb, nt);
     }
   }
-  k_gp_alpha<<<1, 256, sizeof(double) * Mp, s>>>(L, Mi, Mp, y, mu_X, alpha);
+  k_gp_alpha<<<1, 256, sizeof(double) * Mp, s>>>(L, Mi, Mp, y, mu_X, alpha, nullptr);
   if (m > 0)
     k_gp_predict<<<(unsigned)m, 256, sizeof(double) * Mp, s>>>(X, L, alpha, scale, Mi, Mp, D, params->sf2,
                                                                params->l2, Xs, mu_Xs, mean, var);

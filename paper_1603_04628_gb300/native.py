@@ -112,6 +112,9 @@ def lib():
                         ctypes.c_int),
         "mdgp_gp_predict": ([vp, dp, i64, dp, dp, dp], ctypes.c_int),
         "mdgp_gp_scales": ([vp, dp], ctypes.c_int),
+        "mdgp_gp_log_marginal": ([vp, dp], ctypes.c_int),
+        "mdgp_gp_optimize": ([vp, dp, dp, i64, ctypes.c_int32, ctypes.POINTER(GPParams), dp, ctypes.c_int32,
+                              ctypes.POINTER(GPParams), dp], ctypes.c_int),
         "mdgp_gp_free": ([vp], ctypes.c_int),
         "mdgp_macro_params_default": ([ctypes.POINTER(MacroParams)], ctypes.c_int),
         "mdgp_hybrid_create": ([vp, ctypes.POINTER(MacroParams), dp, ctypes.POINTER(vp)], ctypes.c_int),
@@ -308,6 +311,11 @@ class GP:
         mu = None if mu_Xs is None else _dp(np.ascontiguousarray(mu_Xs, dtype=np.float64))
         _check(None, lib().mdgp_gp_predict(self.h, _dp(Xs), m, mu, _dp(mean), _dp(var)), "mdgp_gp_predict")
         return mean, var
+
+    def log_marginal(self):
+        out = ctypes.c_double()
+        _check(None, lib().mdgp_gp_log_marginal(self.h, ctypes.byref(out)), "mdgp_gp_log_marginal")
+        return out.value
 
     def scales(self):
         out = np.zeros(self.D)
@@ -520,3 +528,21 @@ def mdgp_hybrid_create(ctx, density0=None, **params):
 
 def mdgp_hybrid_step(hybrid, sigma_t):
     return hybrid.step(sigma_t)
+
+
+def gp_optimize(ctx, X, y, sf2, l2, sn2, mu_X=None, fallback_scale=1.0, fallback_scales=None, max_evals=200):
+    """mdgp_gp_optimize: hyperparameters (sf2, l2, sn2) by maximum evidence."""
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    X = np.ascontiguousarray(np.asarray(X, dtype=np.float64).reshape(len(y), -1))
+    start = GPParams(float(sf2), float(l2), float(sn2), float(fallback_scale), None, None)
+    fb = None
+    if fallback_scales is not None:
+        fb = np.ascontiguousarray(fallback_scales, dtype=np.float64)
+        start.fallback_scales = _dp(fb)
+    best = GPParams()
+    lml = ctypes.c_double()
+    mu = None if mu_X is None else np.ascontiguousarray(mu_X, dtype=np.float64)
+    _check(ctx.h, lib().mdgp_gp_optimize(ctx.h, _dp(X), _dp(y), len(y), X.shape[1], ctypes.byref(start),
+                                         _dp(mu) if mu is not None else None, int(max_evals), ctypes.byref(best),
+                                         ctypes.byref(lml)), "mdgp_gp_optimize")
+    return dict(sf2=best.sf2, l2=best.l2, sn2=best.sn2, lml=lml.value)

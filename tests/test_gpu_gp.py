@@ -102,3 +102,26 @@ def test_per_dimension_fallback_scales(ctx):
     np.testing.assert_allclose(v, vr, rtol=1e-10, atol=1e-12)
     g.close()
 
+
+
+def test_log_marginal_likelihood_matches_oracle(ctx):
+    from paper_1603_04628_gb300 import native
+    X, y = synth.gp_dataset(300, seed=8)
+    mu = lambda Z: 0.2 * Z[:, 0]
+    for args in ((1.0, 1.0, 0.01), (3.0, 0.4, 0.2)):
+        g = native.GP(ctx, X, y, *args, mu_X=mu(X))
+        ref = ogp.GP(X, y, *args, mu=mu)
+        f, fr = g.log_marginal(), ref.log_marginal_likelihood()
+        assert f == pytest.approx(fr, rel=1e-10, abs=1e-8)
+        g.close()
+
+
+def test_optimize_matches_oracle_search(ctx):
+    # same pattern search, same decisions: identical hyperparameters
+    from paper_1603_04628_gb300 import native
+    X, y = synth.gp_dataset(200, seed=9)
+    got = native.gp_optimize(ctx, X, y, 1.0, 1.0, 0.1, max_evals=120)
+    sf2, l2, sn2, f = ogp.optimize(X, y, 1.0, 1.0, 0.1, max_evals=120)
+    np.testing.assert_allclose([got["sf2"], got["l2"], got["sn2"]], [sf2, l2, sn2], rtol=1e-12)
+    assert got["lml"] == pytest.approx(f, rel=1e-9, abs=1e-8)
+    assert f > ogp.GP(X, y, 1.0, 1.0, 0.1).log_marginal_likelihood()

@@ -148,3 +148,36 @@ def test_prior_mean_is_added_back():
 
 def test_gate_is_strict():
     assert list(gp.gate([0.5, 0.5000001, 0.4], 0.5)) == [False, True, False]
+
+
+def _gp_draw(M, sf2, l2, sn2, seed):
+    # inputs in the benchmark's (h, dp/dx) box; outputs drawn from the GP
+    # prior with the same normalised squared-exponential covariance
+    rng = np.random.default_rng(seed)
+    X = np.column_stack([rng.uniform(6.0, 18.0, M), rng.uniform(-0.05, 0.05, M)])
+    d = gp.scales(X)
+    Z = X / d
+    r2 = ((Z[:, None, :] - Z[None, :, :]) ** 2).sum(-1)
+    C = sf2 * np.exp(-r2 / (2.0 * l2)) + sn2 * np.eye(M)
+    y = np.linalg.cholesky(C) @ rng.standard_normal(M)
+    return X, y
+
+
+def test_optimize_recovers_generating_hyperparameters():
+    X, y = _gp_draw(300, 2.0, 0.5, 0.01, seed=3)
+    sf2, l2, sn2, f = gp.optimize(X, y, 1.0, 1.0, 0.1)
+    assert 0.5 < sf2 / 2.0 < 2.0
+    assert 0.5 < l2 / 0.5 < 2.0
+    assert 0.5 < sn2 / 0.01 < 2.0
+    assert f > gp.GP(X, y, 1.0, 1.0, 0.1).log_marginal_likelihood()
+
+
+def test_optimize_ends_at_a_coordinate_maximum():
+    X, y = _gp_draw(120, 1.0, 1.0, 0.05, seed=4)
+    h = list(gp.optimize(X, y, 0.3, 3.0, 0.3)[:3])
+    f = gp.GP(X, y, *h).log_marginal_likelihood()
+    for k in range(3):
+        for fac in (1.1, 1 / 1.1):
+            t = list(h)
+            t[k] *= fac
+            assert gp.GP(X, y, *t).log_marginal_likelihood() <= f + 1e-6 * abs(f)
