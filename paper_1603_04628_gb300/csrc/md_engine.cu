@@ -202,7 +202,8 @@ static void enqueue_step_integrate(mdgp_ctx* ctx, int k, bool stage1, cudaGraphC
 }
 
 // Neighbour-list rebuild: bin, per-element scan, permute into cell order,
-// copy back, build the lists (5 kernels on `s`).
+// copy back (not with the ballot build, which copies per cell), build the
+// lists (4 or 5 kernels on `s`).
 static void enqueue_rebuild(mdgp_ctx* ctx, cudaStream_t s) {
   const unsigned g = grid_for(ctx->B.n_atoms, 256);
   if (ctx->precision == MDGP_PREC_FP32) k_bin<true><<<g, 256, 0, s>>>(ctx->B);
@@ -215,22 +216,25 @@ static void enqueue_rebuild(mdgp_ctx* ctx, cudaStream_t s) {
   const size_t ballot_smem = (size_t)kBallotWarps * kBallotWarpBytes;
   if (ctx->precision == MDGP_PREC_FP32) {
     k_permute<float4><<<g, 256, 0, s>>>(ctx->B);
-    k_copy_back<<<g, 256, 0, s>>>(ctx->B);
+    if (variant != 2) k_copy_back<<<g, 256, 0, s>>>(ctx->B);   // the ballot build copies in its cells
     if (variant == 2) k_build_ballot<<<gw, kBallotWarps * 32, ballot_smem, s>>>(ctx->B, ctx->P);
     else if (variant == 0) k_build_staged<float4><<<gc, 128, ctx->stage_bytes, s>>>(ctx->B, ctx->P, ctx->stage_bytes);
     else k_build<float4><<<gb, 128, 0, s>>>(ctx->B, ctx->P);
   } else {
     k_permute<Pos64><<<g, 256, 0, s>>>(ctx->B);
-    k_copy_back<<<g, 256, 0, s>>>(ctx->B);
+    if (variant != 2) k_copy_back<<<g, 256, 0, s>>>(ctx->B);
     if (variant == 2) k_build_ballot<<<gw, kBallotWarps * 32, ballot_smem, s>>>(ctx->B, ctx->P);
     else if (variant == 0) k_build_staged<Pos64><<<gc, 128, ctx->stage_bytes, s>>>(ctx->B, ctx->P, ctx->stage_bytes);
     else k_build<Pos64><<<gb, 128, 0, s>>>(ctx->B, ctx->P);
   }
 }
 
+// kernels in one rebuild: bin, scan, permute, (copy back,) build
+static int rebuild_kernels(const mdgp_ctx* ctx) { return ctx->params.build_variant == 2 ? 4 : 5; }
+
 static void enqueue_rebuild(mdgp_ctx* ctx) {
   enqueue_rebuild(ctx, ctx->stream);
-  ctx->launches += 5;
+  ctx->launches += rebuild_kernels(ctx);
 }
 
 // Pair forces of step *step_base + k (with per-atom energies if `energy`).
@@ -737,9 +741,9 @@ static int results_impl(mdgp_ctx* ctx, mdgp_result* out, int64_t n) {
   CK(cudaMemcpyAsync(out, ctx->d_results.ptr, sizeof(mdgp_result) * n, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaMemcpyAsync(flags, ctx->B.flags, sizeof(flags), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
-  // every rebuild is 5 kernels; the launch sequence counted one eagerly
+  // every rebuild is rebuild_kernels() launches; the launch sequence counted one eagerly
   ctx->rebuilds = flags[2];
-  ctx->launches_with_rebuilds = ctx->launches + 5LL * (flags[2] - 1) + flags[3];
+  ctx->launches_with_rebuilds = ctx->launches + (long long)rebuild_kernels(ctx) * (flags[2] - 1) + flags[3];
   return MDGP_OK;
 }
 

@@ -365,3 +365,37 @@ def test_persistent_step_loop_matches_per_step_launches(native, mode):
     assert np.abs(va - vb).max() < 1e-2
     for a, b in zip(ra, rb):
         assert a["q"] == pytest.approx(b["q"], rel=1e-2, abs=1e-3)
+
+
+def test_full_uneven_batch_in_bench_configuration():
+    # the 64-element batch exactly as bench.py launches it (FP32 pair forces,
+    # double-float state, persistent step loop, default parameters), 100
+    # steps: every element finishes cleanly, and sampled elements (smallest,
+    # largest, a middle one) run alone follow the same trajectories to FP32
+    # summation order: batching couples nothing
+    from paper_1603_04628_gb300 import native
+    els = synth.batch_uneven(64, steps=100)
+    ctx = native.Context(0, native.PREC_FP32)
+    n = ctx.micro_plan(els)
+    ctx.micro_launch()
+    res = ctx.micro_results()
+    xb, vb = ctx.micro_state()
+    assert all(r["status"] == 0 for r in res)
+    assert ctx.rebuild_count() >= 2
+    sizes = [r["n_fluid"] + r["n_wall"] for r in res]
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    assert offs[-1] == n == len(xb)
+    picks = sorted({int(np.argmin(sizes)), int(np.argmax(sizes)), 31})
+    for k in picks:
+        c1 = native.Context(0, native.PREC_FP32)
+        c1.micro_plan([els[k]])
+        c1.micro_launch()
+        r1 = c1.micro_results()[0]
+        x1, v1 = c1.micro_state()
+        c1.close()
+        d = xb[offs[k]:offs[k + 1]] - x1
+        d[:, 0] -= els[k]["Lx"] * np.round(d[:, 0] / els[k]["Lx"])
+        d[:, 2] -= els[k]["Lz"] * np.round(d[:, 2] / els[k]["Lz"])
+        assert np.abs(d).max() < 1e-3, k
+        assert r1["q"] == pytest.approx(res[k]["q"], rel=2e-2, abs=2e-2), k
+    ctx.close()
