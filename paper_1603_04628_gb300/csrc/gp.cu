@@ -14,6 +14,7 @@
 
 #include "mdgp.h"
 #include "md_ctx.h"
+#include "gp_internal.h"
 
 namespace {
 
@@ -300,7 +301,7 @@ __global__ void k_gp_predict(const double* X, const double* L, const double* alp
   for (int i = tid; i < Mp; i += nt) {
     const double k = i < M ? se_kernel(xq, X + (size_t)i * D, scale, D, sf2, l2) : 0.0;
     v[i] = k;
-    if (i < M) dot += k * alpha[i];
+    if (i < M && alpha) dot += k * alpha[i];
   }
   dot = warp_sum_d(dot);
   if (lane == 0) red[wid] = dot;
@@ -362,6 +363,7 @@ struct mdgp_gp {
   double *dX = nullptr, *dL = nullptr, *dalpha = nullptr, *dscale = nullptr;
   double *dq = nullptr, *dmu = nullptr, *dmean = nullptr, *dvar = nullptr;
   size_t qcap = 0;
+  bool has_alpha = true;   // false: factor only (posterior variances, no means or evidence)
   int launches = 0;
   char err[128] = {0};
 };
@@ -405,7 +407,7 @@ static int gp_fit_impl(mdgp_gp* g, const double* X, const double* y, const doubl
   GK(cudaMalloc(&dy, sizeof(double) * M));
   GK(cudaMalloc(&dstatus, sizeof(int)));
   GK(cudaMemcpyAsync(g->dX, X, sizeof(double) * M * D, cudaMemcpyHostToDevice, s));
-  GK(cudaMemcpyAsync(dy, y, sizeof(double) * M, cudaMemcpyHostToDevice, s));
+  if (y) GK(cudaMemcpyAsync(dy, y, sizeof(double) * M, cudaMemcpyHostToDevice, s));
   GK(cudaMemsetAsync(dstatus, 0, sizeof(int), s));
   if (mu_X) {
     GK(cudaMalloc(&dmuX, sizeof(double) * M));
@@ -434,9 +436,11 @@ static int gp_fit_impl(mdgp_gp* g, const double* X, const double* y, const doubl
       g->launches += 2;
     }
   }
-  GK(cudaFuncSetAttribute(k_gp_alpha, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(double) * Mp)));
-  k_gp_alpha<<<1, 1024, sizeof(double) * Mp, s>>>(g->dL, M, Mp, dy, dmuX, g->dalpha, g->dscale + kMaxD);
-  k_gp_logdiag<<<1, 256, 0, s>>>(g->dL, M, Mp, g->dscale + kMaxD + 1);
+  if (g->has_alpha) {
+    GK(cudaFuncSetAttribute(k_gp_alpha, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(double) * Mp)));
+    k_gp_alpha<<<1, 1024, sizeof(double) * Mp, s>>>(g->dL, M, Mp, dy, dmuX, g->dalpha, g->dscale + kMaxD);
+    k_gp_logdiag<<<1, 256, 0, s>>>(g->dL, M, Mp, g->dscale + kMaxD + 1);
+  }
   g->launches++;
   int status = 0;
   GK(cudaGetLastError());
@@ -451,10 +455,10 @@ static int gp_fit_impl(mdgp_gp* g, const double* X, const double* y, const doubl
 
 extern "C" {
 
-int mdgp_gp_fit(mdgp_ctx* ctx, const double* X, const double* y, int64_t M, int32_t D,
-                const mdgp_gp_params* params, const double* mu_X, mdgp_gp** out) {
+static int gp_fit_entry(mdgp_ctx* ctx, const double* X, const double* y, int64_t M, int32_t D,
+                        const mdgp_gp_params* params, const double* mu_X, bool with_alpha, mdgp_gp** out) {
   if (!ctx || !params || !out || M < 0 || M > kMaxM || D < 1 || D > kMaxD) return MDGP_E_ARG;
-  if (M > 0 && (!X || !y)) return MDGP_E_ARG;
+  if (M > 0 && (!X || (with_alpha && !y))) return MDGP_E_ARG;
   if (!(params->sf2 > 0) || !(params->l2 > 0) || !(params->sn2 >= 0)) return MDGP_E_ARG;
   *out = nullptr;
   cudaSetDevice(ctx->device);
@@ -468,7 +472,8 @@ int mdgp_gp_fit(mdgp_ctx* ctx, const double* X, const double* y, int64_t M, int3
   g->sf2 = params->sf2;
   g->l2 = params->l2;
   g->sn2 = params->sn2;
-  int st = gp_fit_impl(g, X, y, mu_X, params);
+  g->has_alpha = with_alpha;
+  int st = gp_fit_impl(g, X, with_alpha ? y : nullptr, with_alpha ? mu_X : nullptr, params);
   if (st != MDGP_OK) {
     std::snprintf(ctx->err, sizeof(ctx->err), "gp fit: %s", g->err[0] ? g->err : "not positive definite");
     gp_release(g);
@@ -477,6 +482,11 @@ int mdgp_gp_fit(mdgp_ctx* ctx, const double* X, const double* y, int64_t M, int3
   }
   *out = g;
   return MDGP_OK;
+}
+
+int mdgp_gp_fit(mdgp_ctx* ctx, const double* X, const double* y, int64_t M, int32_t D,
+                const mdgp_gp_params* params, const double* mu_X, mdgp_gp** out) {
+  return gp_fit_entry(ctx, X, y, M, D, params, mu_X, true, out);
 }
 
 int mdgp_gp_predict(mdgp_gp* g, const double* Xs, int64_t m, const double* mu_Xs, double* mean, double* var) {
@@ -504,7 +514,8 @@ int mdgp_gp_predict(mdgp_gp* g, const double* Xs, int64_t m, const double* mu_Xs
   if (mu_Xs) GK(cudaMemcpyAsync(g->dmu, mu_Xs, sizeof(double) * m, cudaMemcpyHostToDevice, s));
   const size_t smem = sizeof(double) * g->Mp;
   GK(cudaFuncSetAttribute(k_gp_predict, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_gp_predict<<<(unsigned)m, 256, smem, s>>>(g->dX, g->dL, g->dalpha, g->dscale, g->M, g->Mp, g->D, g->sf2,
+  k_gp_predict<<<(unsigned)m, 256, smem, s>>>(g->dX, g->dL, g->has_alpha ? g->dalpha : nullptr, g->dscale, g->M,
+                                              g->Mp, g->D, g->sf2,
                                               g->l2, g->dq, mu_Xs ? g->dmu : nullptr, g->dmean, g->dvar);
   g->launches++;
   GK(cudaGetLastError());
@@ -515,7 +526,7 @@ int mdgp_gp_predict(mdgp_gp* g, const double* Xs, int64_t m, const double* mu_Xs
 }
 
 int mdgp_gp_log_marginal(const mdgp_gp* g, double* lml) {
-  if (!g || !lml) return MDGP_E_ARG;
+  if (!g || !lml || !g->has_alpha) return MDGP_E_ARG;
   if (g->M == 0) { *lml = 0.0; return MDGP_OK; }
   cudaSetDevice(g->device);
   double t[2];
@@ -588,6 +599,11 @@ int mdgp_gp_free(mdgp_gp* g) {
 }
 
 }  // extern "C"
+
+int gp_fit_variance_only(mdgp_ctx* ctx, const double* X, int64_t M, int32_t D, const mdgp_gp_params* params,
+                         mdgp_gp** out) {
+  return gp_fit_entry(ctx, X, nullptr, M, D, params, nullptr, false, out);
+}
 
 // ---------------------------------------------------------------------------
 // Allocation-free GP posterior.

@@ -20,6 +20,7 @@
 
 #include "mdgp.h"
 #include "md_ctx.h"
+#include "gp_internal.h"
 
 struct mdgp_hybrid {
   mdgp_ctx* ctx = nullptr;
@@ -107,6 +108,28 @@ int fit_predict(mdgp_hybrid* H, const std::vector<double>& X, const std::vector<
   std::vector<double> mq;
   if ((st = prior_mean(H, Xq, m, mq))) { mdgp_gp_free(g); return st; }
   st = mdgp_gp_predict(g, Xq, m, H->mean_fn ? mq.data() : nullptr, mean, var);
+  mdgp_gp_free(g);
+  return st;
+}
+
+// Posterior variances at the rows of Xq for a database with inputs X rows
+// [0, M): the gate needs no outputs, so the fit skips the alpha solve.
+int gate_variances(mdgp_hybrid* H, const std::vector<double>& X, int64_t M, double sn2, const double* Xq,
+                   int64_t m, double* var) {
+  mdgp_gp_params gp;
+  std::memset(&gp, 0, sizeof(gp));
+  gp.sf2 = H->p.sf2;
+  gp.l2 = H->p.l2;
+  gp.sn2 = sn2;
+  double fb[3];
+  fallback_scales(H, fb);
+  gp.fallback_scale = 1.0;
+  gp.fallback_scales = fb;
+  mdgp_gp* g = nullptr;
+  int st = gp_fit_variance_only(H->ctx, M ? X.data() : nullptr, M, H->D, &gp, &g);
+  if (st) return st;
+  std::vector<double> mean((size_t)m);
+  st = mdgp_gp_predict(g, Xq, m, nullptr, mean.data(), var);
   mdgp_gp_free(g);
   return st;
 }
@@ -213,7 +236,7 @@ int mdgp_hybrid_step(mdgp_hybrid* H, double sigma_t, mdgp_hybrid_stats* stats) {
   // sigma_t <= 0 sends every section to MD whatever the variance (the
   // reference run), so no GP work is done then.
   const int64_t M0 = (int64_t)H->y.size();
-  std::vector<double> Xv(H->X), yv((size_t)M0, 0.0), mv(H->mX);
+  std::vector<double> Xv(H->X), mv(H->mX);
   std::vector<int> md_idx;
   std::vector<double> mean((size_t)N), var((size_t)N);
   int j0 = 0;
@@ -232,8 +255,7 @@ int mdgp_hybrid_step(mdgp_hybrid* H, double sigma_t, mdgp_hybrid_stats* stats) {
   }
   while (j0 < N) {
     const int64_t Mv = (int64_t)(Xv.size() / D);
-    int st = fit_predict(H, Xv, yv, mv, Mv, sn2, Xq.data() + (size_t)D * j0, N - j0, mean.data() + j0,
-                         var.data() + j0);
+    int st = gate_variances(H, Xv, Mv, sn2, Xq.data() + (size_t)D * j0, N - j0, var.data() + j0);
     if (st) return st;
     int j = j0;
     for (; j < N; ++j) {
@@ -243,7 +265,6 @@ int mdgp_hybrid_step(mdgp_hybrid* H, double sigma_t, mdgp_hybrid_stats* stats) {
     if (j == N) break;
     md_idx.push_back(j);
     for (int d = 0; d < D; ++d) Xv.push_back(Xq[(size_t)D * j + d]);
-    yv.push_back(0.0);
     if (H->mean_fn) {
       std::vector<double> mq;
       int st2 = prior_mean(H, Xq.data() + (size_t)D * j, 1, mq);
