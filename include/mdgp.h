@@ -191,7 +191,7 @@ int mdgp_md_forces(mdgp_ctx* ctx, const mdgp_element* el, const double* x, int64
  * integration kernel time, ms[1] = mean pair-force kernel time.  FP32 pair
  * forces (one fused launch per step: forces + integration): ms[0] = 0,
  * ms[1] = mean fused step time (with the frozen-wall thermostat, both of
- * its launches).  ms[2] = mean time of one whole neighbour-list rebuild (4 or 5
+ * its launches).  ms[2] = mean time of one whole neighbour-list rebuild (5
  * kernels); all in milliseconds; ms[3] = atoms, ms[4] = cells, ms[5] = steps
  * between rebuilds.  Leaves the batch state mid-run (launch it again for
  * results).  MDGP_E_STATE without a plan. */

@@ -202,8 +202,7 @@ static void enqueue_step_integrate(mdgp_ctx* ctx, int k, bool stage1, cudaGraphC
 }
 
 // Neighbour-list rebuild: bin, per-element scan, permute into cell order,
-// copy back (not with the ballot build, which copies per cell), build the
-// lists (4 or 5 kernels on `s`).
+// copy back, build the lists (5 kernels on `s`).
 static void enqueue_rebuild(mdgp_ctx* ctx, cudaStream_t s) {
   const unsigned g = grid_for(ctx->B.n_atoms, 256);
   if (ctx->precision == MDGP_PREC_FP32) k_bin<true><<<g, 256, 0, s>>>(ctx->B);
@@ -216,21 +215,21 @@ static void enqueue_rebuild(mdgp_ctx* ctx, cudaStream_t s) {
   const size_t ballot_smem = (size_t)kBallotWarps * kBallotWarpBytes;
   if (ctx->precision == MDGP_PREC_FP32) {
     k_permute<float4><<<g, 256, 0, s>>>(ctx->B);
-    if (variant != 2) k_copy_back<<<g, 256, 0, s>>>(ctx->B);   // the ballot build copies in its cells
+    k_copy_back<<<g, 256, 0, s>>>(ctx->B);
     if (variant == 2) k_build_ballot<<<gw, kBallotWarps * 32, ballot_smem, s>>>(ctx->B, ctx->P);
     else if (variant == 0) k_build_staged<float4><<<gc, 128, ctx->stage_bytes, s>>>(ctx->B, ctx->P, ctx->stage_bytes);
     else k_build<float4><<<gb, 128, 0, s>>>(ctx->B, ctx->P);
   } else {
     k_permute<Pos64><<<g, 256, 0, s>>>(ctx->B);
-    if (variant != 2) k_copy_back<<<g, 256, 0, s>>>(ctx->B);
+    k_copy_back<<<g, 256, 0, s>>>(ctx->B);
     if (variant == 2) k_build_ballot<<<gw, kBallotWarps * 32, ballot_smem, s>>>(ctx->B, ctx->P);
     else if (variant == 0) k_build_staged<Pos64><<<gc, 128, ctx->stage_bytes, s>>>(ctx->B, ctx->P, ctx->stage_bytes);
     else k_build<Pos64><<<gb, 128, 0, s>>>(ctx->B, ctx->P);
   }
 }
 
-// kernels in one rebuild: bin, scan, permute, (copy back,) build
-static int rebuild_kernels(const mdgp_ctx* ctx) { return ctx->params.build_variant == 2 ? 4 : 5; }
+// kernels in one rebuild: bin, scan, permute, copy back, build
+static int rebuild_kernels(const mdgp_ctx*) { return 5; }
 
 static void enqueue_rebuild(mdgp_ctx* ctx) {
   enqueue_rebuild(ctx, ctx->stream);

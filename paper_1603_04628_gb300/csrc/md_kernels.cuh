@@ -810,15 +810,6 @@ __global__ void __launch_bounds__(kBallotWarps * 32, 10) k_build_ballot(BatchDev
   unsigned short* oidx = reinterpret_cast<unsigned short*>(cbuf + kBallotCap + 32);
   const int s0 = B.cstart[cell], n0 = B.csize[cell];
   if (n0 == 0) return;
-  // the permuted state of this cell's atoms becomes the current state (the
-  // build itself reads only pbuild), in place of a separate copy pass
-  for (int a = lane; a < n0; a += 32) {
-    const long long i = s0 + a;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) B.st[k][i] = B.st2[k][i];
-    B.orig[i] = B.orig2[i];
-    B.cell[i] = B.cell2[i];
-  }
   const int e = B.cell_el[cell];
   const ElemDev& E = B.el[e];
   int cx, cy, cz;
