@@ -226,8 +226,8 @@ def main():
     launches_per_step = ctx.launch_count()
     rebuilds_per_step = ctx.rebuild_count()
 
-    clk_path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
-                            "bench_clocks_rank%d.csv" % rank)
+    # clock samples during the timed region (nvidia-smi), kept beside the run
+    clk_path = os.path.join(os.environ.get("MDGP_CLOCKS_DIR", "."), "bench_clocks_rank%d.csv" % rank)
     proc, fh = sample_clocks_start(clk_path)
     if dist:
         dist.barrier()
