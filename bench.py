@@ -160,8 +160,10 @@ def main():
                          "(Algorithm 1) threshold sweep on the 200-section channel; gp: the GP and "
                          "MLP timings alone")
     ap.add_argument("--channel-steps", type=int, default=100)
-    ap.add_argument("--paper-form", action="store_true",
-                    help="channel case with the paper's p-GP and (h, n, F) q-GP inputs")
+    ap.add_argument("--form", default="paper", choices=["paper", "linear"],
+                    help="channel case: the paper's p-GP and (h, n, F) q-GP inputs (default), or a linear "
+                         "equation of state with (h, G) inputs")
+    ap.add_argument("--paper-form", action="store_true", help="same as --form paper")
     ap.add_argument("--sample-steps", type=int, default=300,
                     help="oracle steps per sampled element in the reference arm")
     ap.add_argument("--no-gp-mlp", action="store_true", help="skip the GP and MLP timings")
@@ -406,7 +408,7 @@ def run_channel_case(args):
                   sf2=(20 * sn) ** 2, l2=1.0, sn2=sn ** 2, sn2_from_data=0)
     thresholds = [f * sn for f in (0.5, 1.0, 2.0, 4.0, 8.0)]
     pressure_db, form = None, "q-GP on (h, G), linear equation of state"
-    if args.paper_form:
+    if args.paper_form or args.form == "paper":
         # the paper's form (Sec. 2.4): p-GP over (h, n) from pre-simulations,
         # q-GP on (h, n, F)
         import numpy as np
