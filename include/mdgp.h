@@ -112,8 +112,10 @@ typedef struct {
   int32_t build_variant;/* list build: 0 = cell columns staged in shared memory by bulk async
                            copies, 1 = direct reads of global memory (lanes over a cell's
                            atoms), 2 = warp ballots over bounding-box-culled candidates
-                           (lanes over candidates; default).  All three give each atom the
-                           same set of neighbours within r_c + skin. */
+                           (lanes over candidates, one warp per cell), 3 = the ballot
+                           build with one block of four warps per cell (same lists as 2,
+                           entry for entry; default).  All give each atom the same set of
+                           neighbours within r_c + skin. */
   int32_t persistent;   /* FP32 pair forces: 1 = the step loop is one persistent cooperative
                            kernel per list-rebuild interval (steps separated by a grid barrier,
                            inside a graph WHILE loop; default), 0 = one launch per step with a

@@ -211,18 +211,21 @@ static void enqueue_rebuild(mdgp_ctx* ctx, cudaStream_t s) {
   const unsigned gb = grid_for(ctx->B.n_cells * 32, 128);
   const unsigned gc = (unsigned)ctx->n_columns;
   const unsigned gw = grid_for(ctx->B.n_cells, kBallotWarps);
+  const unsigned gk = grid_for(ctx->B.n_cells, 1);
   const int variant = ctx->params.build_variant;
   const size_t ballot_smem = (size_t)kBallotWarps * kBallotWarpBytes;
   if (ctx->precision == MDGP_PREC_FP32) {
     k_permute<float4><<<g, 256, 0, s>>>(ctx->B);
     k_copy_back<<<g, 256, 0, s>>>(ctx->B);
-    if (variant == 2) k_build_ballot<<<gw, kBallotWarps * 32, ballot_smem, s>>>(ctx->B, ctx->P);
+    if (variant == 3) k_build_ballot_blk<<<gk, kBlkWarps * 32, kBlkSmem, s>>>(ctx->B, ctx->P);
+    else if (variant == 2) k_build_ballot<<<gw, kBallotWarps * 32, ballot_smem, s>>>(ctx->B, ctx->P);
     else if (variant == 0) k_build_staged<float4><<<gc, 128, ctx->stage_bytes, s>>>(ctx->B, ctx->P, ctx->stage_bytes);
     else k_build<float4><<<gb, 128, 0, s>>>(ctx->B, ctx->P);
   } else {
     k_permute<Pos64><<<g, 256, 0, s>>>(ctx->B);
     k_copy_back<<<g, 256, 0, s>>>(ctx->B);
-    if (variant == 2) k_build_ballot<<<gw, kBallotWarps * 32, ballot_smem, s>>>(ctx->B, ctx->P);
+    if (variant == 3) k_build_ballot_blk<<<gk, kBlkWarps * 32, kBlkSmem, s>>>(ctx->B, ctx->P);
+    else if (variant == 2) k_build_ballot<<<gw, kBallotWarps * 32, ballot_smem, s>>>(ctx->B, ctx->P);
     else if (variant == 0) k_build_staged<Pos64><<<gc, 128, ctx->stage_bytes, s>>>(ctx->B, ctx->P, ctx->stage_bytes);
     else k_build<Pos64><<<gb, 128, 0, s>>>(ctx->B, ctx->P);
   }
@@ -780,7 +783,7 @@ int mdgp_md_params_default(mdgp_md_params* out) {
   out->list_capacity = 128;
   out->skin = 0.4;
   out->rebuild_every = 0;
-  out->build_variant = 2;
+  out->build_variant = 3;
   out->persistent = 1;
   return MDGP_OK;
 }
@@ -823,7 +826,7 @@ int mdgp_set_md_params(mdgp_ctx* ctx, const mdgp_md_params* p) {
   if (!ctx || !p) return MDGP_E_ARG;
   if (!(p->dt > 0) || !(p->rc > 0) || p->n_blocks < 1 || p->wall_planes < 1 || !(p->mass > 0) ||
       !(p->wall_density > 0) || p->gamma_wall < 0 || p->list_capacity < 0 || !(p->skin >= 0) ||
-      p->rebuild_every < 0 || p->build_variant < 0 || p->build_variant > 2 || p->persistent < 0 || p->persistent > 1)
+      p->rebuild_every < 0 || p->build_variant < 0 || p->build_variant > 3 || p->persistent < 0 || p->persistent > 1)
     return MDGP_E_ARG;
   ctx->params = *p;
   ctx->planned = false;
@@ -1012,7 +1015,7 @@ int mdgp_autotune(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int64_t prob
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   for (double skin : skins) {
-    for (int variant = 0; variant <= 2; ++variant) {
+    for (int variant = 0; variant <= 3; ++variant) {
       mdgp_md_params trial = base;
       trial.skin = skin;
       trial.build_variant = variant;

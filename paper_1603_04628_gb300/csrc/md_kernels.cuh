@@ -801,26 +801,22 @@ constexpr int kBallotWarps = 2;
 constexpr int kBallotCap = 512;   // buffered candidates per warp
 constexpr int kBallotWarpBytes = (kBallotCap + 32) * 16 + (kBallotCap + 32) * 2;
 
-__global__ void __launch_bounds__(kBallotWarps * 32, 10) k_build_ballot(BatchDev B, PhysDev P) {
-  extern __shared__ __align__(16) unsigned char bsm[];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const long long cell = (long long)blockIdx.x * kBallotWarps + wid;
-  if (cell >= B.n_cells) return;
-  float4* cbuf = reinterpret_cast<float4*>(bsm + wid * kBallotWarpBytes);
-  unsigned short* oidx = reinterpret_cast<unsigned short*>(cbuf + kBallotCap + 32);
-  const int s0 = B.cstart[cell], n0 = B.csize[cell];
-  if (n0 == 0) return;
-  const int e = B.cell_el[cell];
-  const ElemDev& E = B.el[e];
+// What one warp knows of its cell for the ballot builds: the bounding box of
+// the cell's atoms and the 27-entry neighbour table with its size prefix.
+struct BallotCell {
+  float lx, ly, lz, hx, hy, hz;   // bounding box of the cell's own atoms
+  int nst, nsz;                   // lane k < 27: start and size of neighbour cell k
+  unsigned ncode;                 // lane k: shift bits of neighbour cell k
+  float nsx, nsy, nsz_f;          // lane k: shift of neighbour cell k in length units
+  int pre, excl, total;           // inclusive / exclusive size prefix, total candidates
+};
+
+__device__ __forceinline__ void ballot_cell(const BatchDev& B, const ElemDev& E, long long cell, int s0, int n0,
+                                            int lane, BallotCell& C) {
   int cx, cy, cz;
   cell_coords(E, cell, cx, cy, cz);
   const int ncx = E.nc[0], ncy = E.nc[1], ncz = E.nc[2];
-  const float csx = E.csf[0], csy = E.csf[1], csz = E.csf[2];
-  const float rl2 = P.rl2f;
-  const unsigned rl2u = __float_as_uint(rl2) - 1u;
   const float4* pb = B.pbuild;
-  const float4 far4 = make_float4(1.0e18f, 1.0e18f, 1.0e18f, 0.0f);
-  // bounding box of the cell's own atoms
   float lx = 3.0e38f, ly = 3.0e38f, lz = 3.0e38f, hx = -3.0e38f, hy = -3.0e38f, hz = -3.0e38f;
   for (int a = lane; a < n0; a += 32) {
     const float4 p = pb[s0 + a];
@@ -833,10 +829,10 @@ __global__ void __launch_bounds__(kBallotWarps * 32, 10) k_build_ballot(BatchDev
     lz = fminf(lz, __shfl_xor_sync(kFull, lz, o)); hx = fmaxf(hx, __shfl_xor_sync(kFull, hx, o));
     hy = fmaxf(hy, __shfl_xor_sync(kFull, hy, o)); hz = fmaxf(hz, __shfl_xor_sync(kFull, hz, o));
   }
+  C.lx = lx; C.ly = ly; C.lz = lz; C.hx = hx; C.hy = hy; C.hz = hz;
   // neighbour table: lane k < 27 holds cell k = 9 (dx+1) + 3 (dy+1) + (dz+1)
-  int nst = 0, nsz = 0;
-  unsigned ncode = 0;
-  float nsx = 0.f, nsy = 0.f, nsz_f = 0.f;
+  C.nst = 0; C.nsz = 0; C.ncode = 0;
+  C.nsx = 0.f; C.nsy = 0.f; C.nsz_f = 0.f;
   if (lane < 27) {
     const int dx = lane / 9 - 1, dy = (lane / 3) % 3 - 1, dz = lane % 3 - 1;
     const int jy = cy + dy;
@@ -845,24 +841,141 @@ __global__ void __launch_bounds__(kBallotWarps * 32, 10) k_build_ballot(BatchDev
       jx = jx < 0 ? jx + ncx : (jx >= ncx ? jx - ncx : jx);
       jz = jz < 0 ? jz + ncz : (jz >= ncz ? jz - ncz : jz);
       const long long c2 = E.cell0 + ((long long)jx * ncy + jy) * ncz + jz;
-      nst = B.cstart[c2];
-      nsz = B.csize[c2];
+      C.nst = B.cstart[c2];
+      C.nsz = B.csize[c2];
     }
-    ncode = ((unsigned)(dx + 1) << 26) | ((unsigned)(dy + 1) << 28) | ((unsigned)(dz + 1) << 30);
-    nsx = (float)dx * csx; nsy = (float)dy * csy; nsz_f = (float)dz * csz;
+    C.ncode = ((unsigned)(dx + 1) << 26) | ((unsigned)(dy + 1) << 28) | ((unsigned)(dz + 1) << 30);
+    C.nsx = (float)dx * E.csf[0]; C.nsy = (float)dy * E.csf[1]; C.nsz_f = (float)dz * E.csf[2];
   }
-  int pre = nsz;   // inclusive prefix of the sizes over the lanes
+  int pre = C.nsz;   // inclusive prefix of the sizes over the lanes
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const int t = __shfl_up_sync(kFull, pre, o);
     if (lane >= o) pre += t;
   }
-  const int excl = pre - nsz;
-  const int total = __shfl_sync(kFull, pre, 31);
+  C.pre = pre;
+  C.excl = pre - C.nsz;
+  C.total = __shfl_sync(kFull, pre, 31);
+}
+
+// Candidate f of the flat neighbour range (f < C.total), shifted into the
+// home cell's frame with its list entry in w, and whether it lies within
+// sqrt(rl2) of the cell's box.  Lanes with f >= C.total return far4, not kept.
+__device__ __forceinline__ bool ballot_candidate(const float4* pb, const ElemDev& E, const BallotCell& C, int f,
+                                                 float rl2, float4 far4, float4& out) {
+  int k = 0;
+#pragma unroll
+  for (int st = 16; st > 0; st >>= 1) {
+    const int pv = __shfl_sync(kFull, C.pre, k + st - 1);
+    if (pv <= f) k += st;
+  }
+  const int jn = __shfl_sync(kFull, C.nst, k), je = __shfl_sync(kFull, C.excl, k);
+  const unsigned code = __shfl_sync(kFull, C.ncode, k);
+  const float ox = __shfl_sync(kFull, C.nsx, k), oy = __shfl_sync(kFull, C.nsy, k),
+              oz = __shfl_sync(kFull, C.nsz_f, k);
+  const bool valid = f < C.total;
+  const int j = jn + (f - je);
+  float4 p = valid ? pb[j] : far4;
+  p.x += ox; p.y += oy; p.z += oz;
+  const float ex = fmaxf(fmaxf(C.lx - p.x, p.x - C.hx), 0.0f);
+  const float ey = fmaxf(fmaxf(C.ly - p.y, p.y - C.hy), 0.0f);
+  const float ez = fmaxf(fmaxf(C.lz - p.z, p.z - C.hz), 0.0f);
+  out = make_float4(p.x, p.y, p.z, __uint_as_float((unsigned)(j - E.atom0) | code));
+  return valid && ex * ex + ey * ey + ez * ez < rl2;
+}
+
+// One warp's share of the list sweep over a gathered buffer cbuf[0, mpad)
+// (cbuf[pad_idx] = far4): the octants o0, o0 + ostep, ... of the cell's
+// atoms, each with its own filtered index list in oidx.  `first` / `last`
+// mark the first and the last pass over the neighbourhood.
+__device__ __forceinline__ void ballot_sweep(const BatchDev& B, const ElemDev& E, int e, const BallotCell& C,
+                                             long long s0, int n0, const float4* cbuf, unsigned short* oidx,
+                                             int mpad, int pad_idx, int o0, int ostep, bool first, bool last,
+                                             float rl2, int lane) {
+  const unsigned rl2u = __float_as_uint(rl2) - 1u;
   const unsigned lt = (1u << lane) - 1u;
   const long long N4 = B.n_atoms * 4;
   const int cap = B.list_cap;
   unsigned* L = B.list;
+  const float4* pb = B.pbuild;
+  for (int base = 0; base < n0; base += 32) {
+    const int na = n0 - base < 32 ? n0 - base : 32;
+    const float4 mine = lane < na ? pb[s0 + base + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int oct = lane < na ? ((mine.x > 0.f ? 1 : 0) | (mine.y > 0.f ? 2 : 0) | (mine.z > 0.f ? 4 : 0)) : 8;
+    for (int o = o0; o < 8; o += ostep) {
+      unsigned mo = __ballot_sync(kFull, oct == o);
+      if (mo == 0) continue;
+      // the octant's box: the cell's box split at the centre
+      const float bxl = (o & 1) ? fmaxf(C.lx, 0.f) : C.lx, bxh = (o & 1) ? C.hx : fminf(C.hx, 0.f);
+      const float byl = (o & 2) ? fmaxf(C.ly, 0.f) : C.ly, byh = (o & 2) ? C.hy : fminf(C.hy, 0.f);
+      const float bzl = (o & 4) ? fmaxf(C.lz, 0.f) : C.lz, bzh = (o & 4) ? C.hz : fminf(C.hz, 0.f);
+      int q = 0;
+      for (int c = 0; c < mpad; c += 32) {
+        const float4 p = cbuf[c + lane];
+        const float ex = fmaxf(fmaxf(bxl - p.x, p.x - bxh), 0.0f);
+        const float ey = fmaxf(fmaxf(byl - p.y, p.y - byh), 0.0f);
+        const float ez = fmaxf(fmaxf(bzl - p.z, p.z - bzh), 0.0f);
+        const bool keep = ex * ex + ey * ey + ez * ez < rl2;
+        const unsigned mk = __ballot_sync(kFull, keep);
+        if (keep) oidx[q + __popc(mk & lt)] = (unsigned short)(c + lane);
+        q += __popc(mk);
+      }
+      const int qpad = (q + 31) & ~31;
+      if (q + lane < qpad) oidx[q + lane] = (unsigned short)pad_idx;
+      __syncwarp();
+      while (mo) {
+        const int a = __ffs(mo) - 1;
+        mo &= mo - 1;
+        const long long i = s0 + base + a;
+        const float mx = __shfl_sync(kFull, mine.x, a), my = __shfl_sync(kFull, mine.y, a),
+                    mz = __shfl_sync(kFull, mine.z, a);
+        int cnt = first ? 0 : B.nlist[i];
+        unsigned* Li = L + i * 4;
+#pragma unroll 2
+        for (int c = 0; c < qpad; c += 32) {
+          const float4 cq = cbuf[oidx[c + lane]];
+          const float ax = mx - cq.x, ay = my - cq.y, az = mz - cq.z;
+          const float d2 = ax * ax + ay * ay + az * az;
+          const bool take = __float_as_uint(d2) - 1u < rl2u;   // 0 < d2 < rl2
+          const unsigned mk = __ballot_sync(kFull, take);
+          const int kk = cnt + __popc(mk & lt);
+          if (take && kk < cap) Li[(long long)(kk >> 2) * N4 + (kk & 3)] = __float_as_uint(cq.w);
+          cnt += __popc(mk);
+        }
+        if (last) {
+          // pad the last partial group with an entry beyond r_c
+          const int kk = cnt + lane;
+          if (cnt < cap && lane < ((4 - (cnt & 3)) & 3))
+            Li[(long long)(kk >> 2) * N4 + (kk & 3)] = pad_entry(i, E);
+          if (lane == 0) {
+            if (cnt > cap) atomicMin(&B.status[e], kStOverflow);
+            B.nlist[i] = cnt < cap ? cnt : cap;
+          }
+        } else if (lane == 0) {
+          B.nlist[i] = cnt;
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kBallotWarps * 32, 10) k_build_ballot(BatchDev B, PhysDev P) {
+  extern __shared__ __align__(16) unsigned char bsm[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const long long cell = (long long)blockIdx.x * kBallotWarps + wid;
+  if (cell >= B.n_cells) return;
+  float4* cbuf = reinterpret_cast<float4*>(bsm + wid * kBallotWarpBytes);
+  unsigned short* oidx = reinterpret_cast<unsigned short*>(cbuf + kBallotCap + 32);
+  const int s0 = B.cstart[cell], n0 = B.csize[cell];
+  if (n0 == 0) return;
+  const int e = B.cell_el[cell];
+  const ElemDev& E = B.el[e];
+  BallotCell C;
+  ballot_cell(B, E, cell, s0, n0, lane, C);
+  const float rl2 = P.rl2f;
+  const float4 far4 = make_float4(1.0e18f, 1.0e18f, 1.0e18f, 0.0f);
+  const unsigned lt = (1u << lane) - 1u;
   if (lane == 0) cbuf[kBallotCap] = far4;   // the padding target of the index lists
   int f0 = 0;
   bool first = true, last = false;
@@ -870,94 +983,90 @@ __global__ void __launch_bounds__(kBallotWarps * 32, 10) k_build_ballot(BatchDev
     // gather up to kBallotCap candidates
     int m = 0;
 #pragma unroll 2
-    for (; f0 < total && m + 32 <= kBallotCap; f0 += 32) {
-      const int f = f0 + lane;
-      int k = 0;
-#pragma unroll
-      for (int st = 16; st > 0; st >>= 1) {
-        const int pv = __shfl_sync(kFull, pre, k + st - 1);
-        if (pv <= f) k += st;
-      }
-      const int jn = __shfl_sync(kFull, nst, k), je = __shfl_sync(kFull, excl, k);
-      const unsigned code = __shfl_sync(kFull, ncode, k);
-      const float ox = __shfl_sync(kFull, nsx, k), oy = __shfl_sync(kFull, nsy, k), oz = __shfl_sync(kFull, nsz_f, k);
-      const bool valid = f < total;
-      const int j = jn + (f - je);
-      float4 p = valid ? pb[j] : far4;
-      p.x += ox; p.y += oy; p.z += oz;
-      const float ex = fmaxf(fmaxf(lx - p.x, p.x - hx), 0.0f);
-      const float ey = fmaxf(fmaxf(ly - p.y, p.y - hy), 0.0f);
-      const float ez = fmaxf(fmaxf(lz - p.z, p.z - hz), 0.0f);
-      const bool keep = valid && ex * ex + ey * ey + ez * ez < rl2;
+    for (; f0 < C.total && m + 32 <= kBallotCap; f0 += 32) {
+      float4 p;
+      const bool keep = ballot_candidate(B.pbuild, E, C, f0 + lane, rl2, far4, p);
       const unsigned mk = __ballot_sync(kFull, keep);
-      if (keep) cbuf[m + __popc(mk & lt)] = make_float4(p.x, p.y, p.z, __uint_as_float((unsigned)(j - E.atom0) | code));
+      if (keep) cbuf[m + __popc(mk & lt)] = p;
       m += __popc(mk);
     }
-    last = f0 >= total;
+    last = f0 >= C.total;
     const int mpad = (m + 31) & ~31;
     if (m + lane < mpad) cbuf[m + lane] = far4;
     __syncwarp();
-    for (int base = 0; base < n0; base += 32) {
-      const int na = n0 - base < 32 ? n0 - base : 32;
-      const float4 mine = lane < na ? pb[s0 + base + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
-      const int oct = lane < na ? ((mine.x > 0.f ? 1 : 0) | (mine.y > 0.f ? 2 : 0) | (mine.z > 0.f ? 4 : 0)) : 8;
-      for (int o = 0; o < 8; ++o) {
-        unsigned mo = __ballot_sync(kFull, oct == o);
-        if (mo == 0) continue;
-        // the octant's box: the cell's box split at the centre
-        const float bxl = (o & 1) ? fmaxf(lx, 0.f) : lx, bxh = (o & 1) ? hx : fminf(hx, 0.f);
-        const float byl = (o & 2) ? fmaxf(ly, 0.f) : ly, byh = (o & 2) ? hy : fminf(hy, 0.f);
-        const float bzl = (o & 4) ? fmaxf(lz, 0.f) : lz, bzh = (o & 4) ? hz : fminf(hz, 0.f);
-        int q = 0;
-        for (int c = 0; c < mpad; c += 32) {
-          const float4 p = cbuf[c + lane];
-          const float ex = fmaxf(fmaxf(bxl - p.x, p.x - bxh), 0.0f);
-          const float ey = fmaxf(fmaxf(byl - p.y, p.y - byh), 0.0f);
-          const float ez = fmaxf(fmaxf(bzl - p.z, p.z - bzh), 0.0f);
-          const bool keep = ex * ex + ey * ey + ez * ez < rl2;
-          const unsigned mk = __ballot_sync(kFull, keep);
-          if (keep) oidx[q + __popc(mk & lt)] = (unsigned short)(c + lane);
-          q += __popc(mk);
-        }
-        const int qpad = (q + 31) & ~31;
-        if (q + lane < qpad) oidx[q + lane] = (unsigned short)kBallotCap;
-        __syncwarp();
-        while (mo) {
-          const int a = __ffs(mo) - 1;
-          mo &= mo - 1;
-          const long long i = s0 + base + a;
-          const float mx = __shfl_sync(kFull, mine.x, a), my = __shfl_sync(kFull, mine.y, a),
-                      mz = __shfl_sync(kFull, mine.z, a);
-          int cnt = first ? 0 : B.nlist[i];
-          unsigned* Li = L + i * 4;
-#pragma unroll 2
-          for (int c = 0; c < qpad; c += 32) {
-            const float4 cq = cbuf[oidx[c + lane]];
-            const float ax = mx - cq.x, ay = my - cq.y, az = mz - cq.z;
-            const float d2 = ax * ax + ay * ay + az * az;
-            const bool take = __float_as_uint(d2) - 1u < rl2u;   // 0 < d2 < rl2
-            const unsigned mk = __ballot_sync(kFull, take);
-            const int kk = cnt + __popc(mk & lt);
-            if (take && kk < cap) Li[(long long)(kk >> 2) * N4 + (kk & 3)] = __float_as_uint(cq.w);
-            cnt += __popc(mk);
-          }
-          if (last) {
-            // pad the last partial group with an entry beyond r_c
-            const int kk = cnt + lane;
-            if (cnt < cap && lane < ((4 - (cnt & 3)) & 3))
-              Li[(long long)(kk >> 2) * N4 + (kk & 3)] = pad_entry(i, E);
-            if (lane == 0) {
-              if (cnt > cap) atomicMin(&B.status[e], kStOverflow);
-              B.nlist[i] = cnt < cap ? cnt : cap;
-            }
-          } else if (lane == 0) {
-            B.nlist[i] = cnt;
-          }
-        }
-        __syncwarp();
-      }
-    }
+    ballot_sweep(B, E, e, C, s0, n0, cbuf, oidx, mpad, kBallotCap, 0, 1, first, last, rl2, lane);
     __syncwarp();
+    first = false;
+  }
+}
+
+// Block form of the ballot build: one block of kBlkWarps warps per cell.
+// The warps gather together, two chunks of 32 candidates each per round
+// (warp w takes chunks w and kBlkWarps + w of the round's 2 kBlkWarps); a
+// prefix over the warps' ballot counts places the kept candidates in flat
+// index order, so the shared buffer holds the same sequence as in the
+// one-warp build.  Warp w then sweeps the octants w, w + kBlkWarps, ... with
+// its own index list.  Each atom is still swept by one warp over the same
+// candidates in the same order, so its list is the one the one-warp build
+// writes, entry for entry; only a cell's time on its SM is about
+// kBlkWarps times shorter, which keeps more warps resident and shortens the
+// tail of the launch.
+constexpr int kBlkWarps = 4;
+constexpr int kBlkCap = 1024;     // buffered candidates per block
+constexpr int kBlkSmem = (kBlkCap + 32) * 16 + kBlkWarps * (kBlkCap + 32) * 2;
+
+__global__ void __launch_bounds__(kBlkWarps * 32, 6) k_build_ballot_blk(BatchDev B, PhysDev P) {
+  extern __shared__ __align__(16) unsigned char bsm[];
+  __shared__ int s_cnt[2][2 * kBlkWarps];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const long long cell = blockIdx.x;
+  if (cell >= B.n_cells) return;
+  const int s0 = B.cstart[cell], n0 = B.csize[cell];
+  if (n0 == 0) return;
+  float4* cbuf = reinterpret_cast<float4*>(bsm);
+  unsigned short* oidx = reinterpret_cast<unsigned short*>(cbuf + kBlkCap + 32) + wid * (kBlkCap + 32);
+  const int e = B.cell_el[cell];
+  const ElemDev& E = B.el[e];
+  BallotCell C;
+  ballot_cell(B, E, cell, s0, n0, lane, C);
+  const float rl2 = P.rl2f;
+  const float4 far4 = make_float4(1.0e18f, 1.0e18f, 1.0e18f, 0.0f);
+  const unsigned lt = (1u << lane) - 1u;
+  if (threadIdx.x == 0) cbuf[kBlkCap] = far4;   // the padding target of the index lists
+  int f0 = 0, round = 0;
+  bool first = true, last = false;
+  while (!last) {
+    // gather up to kBlkCap candidates; f0, m and round are the same in every warp
+    int m = 0;
+    for (; f0 < C.total && m + 64 * kBlkWarps <= kBlkCap; f0 += 64 * kBlkWarps, ++round) {
+      float4 pa, pc;
+      const bool ka = ballot_candidate(B.pbuild, E, C, f0 + 32 * wid + lane, rl2, far4, pa);
+      const bool kc = ballot_candidate(B.pbuild, E, C, f0 + 32 * (kBlkWarps + wid) + lane, rl2, far4, pc);
+      const unsigned ma = __ballot_sync(kFull, ka), mc = __ballot_sync(kFull, kc);
+      int* cnt = s_cnt[round & 1];   // two slots: a slot is rewritten only two barriers later
+      if (lane == 0) {
+        cnt[wid] = __popc(ma);
+        cnt[kBlkWarps + wid] = __popc(mc);
+      }
+      __syncthreads();
+      int offa = m, offc = m, tot = 0;
+#pragma unroll
+      for (int v = 0; v < kBlkWarps; ++v) {
+        const int a = cnt[v], c = cnt[kBlkWarps + v];
+        offa += v < wid ? a : 0;
+        offc += a + (v < wid ? c : 0);
+        tot += a + c;
+      }
+      if (ka) cbuf[offa + __popc(ma & lt)] = pa;
+      if (kc) cbuf[offc + __popc(mc & lt)] = pc;
+      m += tot;
+    }
+    last = f0 >= C.total;
+    const int mpad = (m + 31) & ~31;
+    if (wid == 0 && m + lane < mpad) cbuf[m + lane] = far4;
+    __syncthreads();
+    ballot_sweep(B, E, e, C, s0, n0, cbuf, oidx, mpad, kBlkCap, wid, kBlkWarps, first, last, rl2, lane);
+    __syncthreads();   // the next pass refills cbuf
     first = false;
   }
 }
@@ -1108,7 +1217,6 @@ __global__ void __launch_bounds__(256) k_integrate(BatchDev B, PhysDev P, int k,
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long s = *B.step_base + k;
   int mkey = -1, tzkey = -1;
-  int mblk = 0;
   double mval[3] = {0.0, 0.0, 0.0}, tzval[1] = {0.0};
   if (i < B.n_atoms) {
     const int e = B.atom_el[i];

@@ -255,13 +255,13 @@ def test_energy_conservation_without_thermostat_or_forcing(native, prec):
 
 @pytest.mark.parametrize("cfg", [1, 2])
 def test_list_build_variants_find_the_same_pairs(native, cfg):
-    # staged (0), direct (1) and ballot (2) builds must give every atom the
-    # same neighbours within r_c; the order of atoms inside a cell comes from
-    # binning atomics and differs from call to call, so the forces agree up
-    # to FP64 summation order
+    # staged (0), direct (1), ballot (2) and block ballot (3) builds must give
+    # every atom the same neighbours within r_c; the order of atoms inside a
+    # cell comes from binning atomics and differs from call to call, so the
+    # forces agree up to FP64 summation order
     name, el, x, sp = configs()[cfg]
     out = []
-    for variant in (0, 1, 2):
+    for variant in (0, 1, 2, 3):
         ctx = native.Context(0, native.PREC_FP64, build_variant=variant)
         out.append(ctx.md_forces(el, x))
         ctx.close()
@@ -273,10 +273,11 @@ def test_list_build_variants_find_the_same_pairs(native, cfg):
         assert abs(e.sum() - e0.sum()) <= 1e-12 * max(np.abs(e0).sum(), 1.0)
 
 
-def test_ballot_build_multi_pass_matches_oracle(native):
+@pytest.mark.parametrize("variant", [2, 3])
+def test_ballot_build_multi_pass_matches_oracle(native, variant):
     # dense walls (wall density 4) and r_c = 4 put far more than one shared
     # buffer of candidates around each cell and more than 32 atoms in a cell:
-    # the ballot build sweeps in several passes
+    # the ballot builds sweep in several passes
     el = dict(h=8.0, Lx=13.5, Lz=13.5, density=0.75, T=2.44, g_ext=0.0, dpdx=0.0, steps_eq=0, steps_sample=0,
               seed=3, id=0)
     p = omd.make_params(el, **PAPER_MODE)
@@ -284,7 +285,7 @@ def test_ballot_build_multi_pass_matches_oracle(native):
     rng = np.random.default_rng(5)
     x = x + rng.normal(0.0, 0.05, x.shape) * (sp[:, None] == 0)
     fr, wr, er = omd.lj_forces(p, x, sp, "cells")
-    ctx = native.Context(0, native.PREC_FP64, build_variant=2, list_capacity=1600, **PAPER_MODE)
+    ctx = native.Context(0, native.PREC_FP64, build_variant=variant, list_capacity=1600, **PAPER_MODE)
     f, w, e = ctx.md_forces(el, x)
     ctx.close()
     assert _force_err(f, fr) <= FP_TOL[0]
@@ -296,7 +297,7 @@ def test_autotune_keeps_results_exact(native):
     els = synth.batch_uneven(6, seed=13, steps=60)
     ctx = native.Context(0, native.PREC_FP64)
     chosen, rate = ctx.autotune(els, probe_steps=40)
-    assert chosen["skin"] in (0.3, 0.4, 0.5, 0.6) and chosen["build_variant"] in (0, 1, 2)
+    assert chosen["skin"] in (0.3, 0.4, 0.5, 0.6) and chosen["build_variant"] in (0, 1, 2, 3)
     assert rate > 0
     res = ctx.micro_batch(els)
     for el, r in zip(els, res):
