@@ -230,10 +230,31 @@ typedef struct {
 int mdgp_gp_fit(mdgp_ctx* ctx, const double* X, const double* y, int64_t M, int32_t D,
                 const mdgp_gp_params* params, const double* mu_X, mdgp_gp** out);
 
+/* Factor the covariance of the inputs alone: the scales, C = K + sn2 I and
+ * its Cholesky factor exactly as mdgp_gp_fit builds them, but no alpha.  The
+ * posterior variance of Eq. predVarEq does not involve the outputs, so
+ * Algorithm 1's gate can run on this handle before the MD results it waits
+ * for exist; mdgp_gp_set_outputs adds them later on the same factor.  Until
+ * then mdgp_gp_predict gives the variances and the prior mean (mu_Xs, or 0)
+ * as the mean, and mdgp_gp_log_marginal fails with MDGP_E_ARG.  Arguments,
+ * limits and errors as for mdgp_gp_fit. */
+int mdgp_gp_fit_inputs(mdgp_ctx* ctx, const double* X, int64_t M, int32_t D, const mdgp_gp_params* params,
+                       mdgp_gp** out);
+
+/* Give a handle its M outputs y (and prior mean mu_X at the inputs,
+ * nullable): solves alpha = C^-1 (y - mu_X) and the evidence terms on the
+ * handle's existing factor (Eq. predMeanEq, Eq. evidenceEq).  The result is
+ * the one mdgp_gp_fit gives for the same X, y, mu_X and params, bit for bit:
+ * the same kernels run on the same factor.  May be called again with new
+ * outputs for the same inputs.  Host arrays; blocking. */
+int mdgp_gp_set_outputs(mdgp_gp* gp, const double* y, const double* mu_X);
+
 /* Posterior at m queries Xs (m x D): mean = mu_Xs + K(Xs, X) alpha
  * (Eq. predMeanEq) and the latent variance sf2 - K(Xs, X) C^-1 K(X, Xs) on
  * the diagonal (Eq. predVarEq), clamped at 0.  mu_Xs may be null (zero prior
- * mean).  Host arrays; blocking. */
+ * mean).  var may be null: the means alone, without the per-query
+ * triangular solve the variance needs; mean may be null when var is not.
+ * Host arrays; blocking. */
 int mdgp_gp_predict(mdgp_gp* gp, const double* Xs, int64_t m, const double* mu_Xs, double* mean, double* var);
 
 /* Allocation-free posterior (no counterpart in the paper: an addition for

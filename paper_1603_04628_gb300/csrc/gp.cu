@@ -14,7 +14,6 @@
 
 #include "mdgp.h"
 #include "md_ctx.h"
-#include "gp_internal.h"
 
 namespace {
 
@@ -29,9 +28,10 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
-// sum over pairs i < j of |x_ik - x_jk|, per dimension k (atomics into
-// out[k]): block i takes row i, its threads stride over j > i.
-__global__ void k_gp_pairsep(const double* X, int M, int D, double* out) {
+// Row sums of the pair separations: rows[i D + k] = sum over j > i of
+// |x_ik - x_jk|.  Block i takes row i, its threads stride over j > i; the
+// sums meet in a fixed order, so the scales do not depend on scheduling.
+__global__ void k_gp_pairsep(const double* X, int M, int D, double* rows) {
   __shared__ double part[kMaxD][32];
   const int i = blockIdx.x;
   double xi[kMaxD], acc[kMaxD];
@@ -47,11 +47,10 @@ __global__ void k_gp_pairsep(const double* X, int M, int D, double* out) {
   if (threadIdx.x < D) {
     double s = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += part[threadIdx.x][w];
-    atomicAdd(&out[threadIdx.x], s);
+    rows[(size_t)i * D + threadIdx.x] = s;
   }
 }
 
-// Turn the pair sums into scales; fall back where undefined.
 // Per-dimension scale used where the mean separation is undefined.
 struct Fallback {
   double v[kMaxD];
@@ -67,16 +66,35 @@ static Fallback make_fallback(const mdgp_gp_params* p, int D) {
   return f;
 }
 
-__global__ void k_gp_scales(double* sums, int M, int D, Fallback fallback, const double* fixed) {
-  const int k = threadIdx.x;
-  if (k >= D) return;
-  if (fixed) { sums[k] = fixed[k]; return; }
-  double s = fallback.v[k];
-  if (M >= 2) {
-    const double m = sums[k] / (0.5 * (double)M * (double)(M - 1));
-    if (m > 0.0) s = m;
+// Scales of Eq. d2Eq: the mean separation over all pairs i < j of each
+// dimension (the row sums of k_gp_pairsep added in a fixed order), or the
+// fallback where it is undefined (M < 2 or no spread), or the fixed scales.
+// One block.
+__global__ void k_gp_scales(const double* rows, double* scale, int M, int D, Fallback fallback,
+                            const double* fixed) {
+  __shared__ double red[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int k = 0; k < D; ++k) {
+    double s = 0.0;
+    if (!fixed)
+      for (int i = threadIdx.x; i < M; i += blockDim.x) s += rows[(size_t)i * D + k];
+    s = warp_sum_d(s);
+    if (lane == 0) red[wid] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < nw; ++w) t += red[w];
+      double v = fallback.v[k];
+      if (fixed) {
+        v = fixed[k];
+      } else if (M >= 2) {
+        const double m = t / (0.5 * (double)M * (double)(M - 1));
+        if (m > 0.0) v = m;
+      }
+      scale[k] = v;
+    }
+    __syncthreads();
   }
-  sums[k] = s;
 }
 
 __device__ __forceinline__ double se_kernel(const double* a, const double* b, const double* scale, int D,
@@ -166,14 +184,22 @@ __global__ void k_trsm_panel(double* A, int Mp, int kb) {
   A[(ir + r) * Mp + kr + c] = X[r][c];
 }
 
-// Trailing update: A_ij -= L_ik L_jk^T for kb < j <= i (one block per tile).
-__global__ void k_syrk_update(double* A, int Mp, int kb, int nt) {
+// Trailing update: A_ij -= L_ik L_jk^T (one block per tile) for the tiles
+// kb < j <= i (part 0), the next tile column j = kb + 1 alone (part 1), or
+// the tiles kb + 1 < j <= i (part 2); parts 1 and 2 together are part 0.
+__global__ void k_syrk_update(double* A, int Mp, int kb, int nt, int part) {
   __shared__ double Li[TB][TB + 1];
   __shared__ double Lj[TB][TB + 1];
   // map blockIdx.x to a lower-triangle tile (i, j) of the trailing matrix
-  int t = blockIdx.x, i = 0;
-  while (t > i) { t -= i + 1; ++i; }
-  const int j = t;
+  int i = 0, j = 0;
+  if (part == 1) {
+    i = blockIdx.x;
+  } else {
+    int t = blockIdx.x;
+    while (t > i) { t -= i + 1; ++i; }
+    j = t;
+    if (part == 2) { ++i; ++j; }
+  }
   const int ib = kb + 1 + i, jb = kb + 1 + j;
   if (ib >= nt) return;
   const int r = threadIdx.y, c = threadIdx.x;
@@ -285,10 +311,10 @@ __global__ void k_gp_logdiag(const double* L, int M, int Mp, double* out) {
 // One query per block: k*, mean, v = L^-1 k* by blocked forward
 // substitution (tile rows of TB: a warp per row subtracts the solved part,
 // then one warp solves the TB x TB triangle from shared memory),
-// var = sf2 - |v|^2.
+// var = sf2 - |v|^2.  Without with_var the block stops after the mean.
 __global__ void k_gp_predict(const double* X, const double* L, const double* alpha, const double* scale,
                              int M, int Mp, int D, double sf2, double l2, const double* Xs, const double* mus,
-                             double* mean, double* var) {
+                             double* mean, double* var, bool with_var) {
   extern __shared__ double v[];
   __shared__ double xq[kMaxD];
   __shared__ double red[32];
@@ -312,6 +338,7 @@ __global__ void k_gp_predict(const double* X, const double* L, const double* alp
     mean[q] = (mus ? mus[q] : 0.0) + t;
   }
   __syncthreads();
+  if (!with_var) return;
   const int nblk = Mp / TB, nw = nt >> 5;
   for (int kb = 0; kb < nblk; ++kb) {
     // rows of tile kb minus the solved part, v_r -= sum_{j < kb*TB} L_rj v_j:
@@ -355,6 +382,17 @@ __global__ void k_gp_predict(const double* X, const double* L, const double* alp
 
 }  // namespace
 
+// The solve kernels keep one vector of Mp doubles in dynamic shared memory.
+// Every path sets their limit to the largest database (kMaxM entries) before
+// it launches them, never to less: the limit belongs to the kernel, so a
+// smaller value set for one call would make a later, larger launch fail.
+static cudaError_t allow_solve_smem() {
+  constexpr int kSolveSmem = kMaxM * (int)sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(k_gp_alpha, cudaFuncAttributeMaxDynamicSharedMemorySize, kSolveSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gp_predict, cudaFuncAttributeMaxDynamicSharedMemorySize, kSolveSmem);
+  return e;
+}
+
 struct mdgp_gp {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -364,6 +402,8 @@ struct mdgp_gp {
   double *dq = nullptr, *dmu = nullptr, *dmean = nullptr, *dvar = nullptr;
   size_t qcap = 0;
   bool has_alpha = true;   // false: factor only (posterior variances, no means or evidence)
+  cudaStream_t fs[2] = {nullptr, nullptr};   // lookahead streams and events of the context (fit only)
+  cudaEvent_t fe[4] = {nullptr, nullptr, nullptr, nullptr};
   int launches = 0;
   char err[128] = {0};
 };
@@ -383,6 +423,58 @@ static int gp_err(mdgp_gp* g, cudaError_t e) {
 static void gp_release(mdgp_gp* g) {
   for (double** p : {&g->dX, &g->dL, &g->dalpha, &g->dscale, &g->dq, &g->dmu, &g->dmean, &g->dvar})
     if (*p) { cudaFree(*p); *p = nullptr; }
+}
+
+// Blocked Cholesky with a lookahead of one tile column.  The trailing update
+// of step k is split: its next tile column (k + 1) stays on the chain stream
+// with the diagonal factorisation and the panel solve, the rest of it runs
+// on a second, lower-priority stream and overlaps the next step's diagonal
+// tile and panel.  The next column update waits for the previous bulk update
+// (the same tiles), so every tile receives its updates in the order of k and
+// the factor is the one the single-stream loop computes, bit for bit.
+constexpr int kLookaheadTiles = 4;
+
+static int enqueue_cholesky_lookahead(mdgp_gp* g, int* dstatus) {
+  const int Mp = g->Mp, nt = Mp / TB;
+  cudaStream_t s = g->stream, sa = g->fs[0], sb = g->fs[1];
+  cudaEvent_t e_in = g->fe[0], e_panel = g->fe[1], e_bulk = g->fe[2], e_out = g->fe[3];
+  GK(cudaEventRecord(e_in, s));   // the covariance is built on s
+  GK(cudaStreamWaitEvent(sa, e_in, 0));
+  GK(cudaStreamWaitEvent(sb, e_in, 0));
+  for (int kb = 0; kb < nt; ++kb) {
+    k_potrf_diag<<<1, 32, 0, sa>>>(g->dL, Mp, kb, dstatus);
+    g->launches++;
+    const int rest = nt - kb - 1;
+    if (rest == 0) break;
+    k_trsm_panel<<<rest * (TB / kTrsmRows), dim3(TB, kTrsmRows), 0, sa>>>(g->dL, Mp, kb);
+    GK(cudaEventRecord(e_panel, sa));
+    if (kb > 0) GK(cudaStreamWaitEvent(sa, e_bulk, 0));   // bulk update of step kb - 1
+    k_syrk_update<<<rest, dim3(TB, TB), 0, sa>>>(g->dL, Mp, kb, nt, 1);
+    g->launches += 2;
+    if (rest > 1) {
+      GK(cudaStreamWaitEvent(sb, e_panel, 0));
+      k_syrk_update<<<rest * (rest - 1) / 2, dim3(TB, TB), 0, sb>>>(g->dL, Mp, kb, nt, 2);
+      GK(cudaEventRecord(e_bulk, sb));
+      g->launches++;
+    }
+  }
+  GK(cudaEventRecord(e_out, sb));
+  GK(cudaStreamWaitEvent(s, e_out, 0));
+  GK(cudaEventRecord(e_out, sa));
+  GK(cudaStreamWaitEvent(s, e_out, 0));
+  return MDGP_OK;
+}
+
+// alpha = C^-1 (y - mu) on the factor, (y - mu)^T alpha and sum log L_ii
+// for the evidence (dy, dmu: M device values; dmu nullable).
+static int enqueue_alpha(mdgp_gp* g, const double* dy, const double* dmu) {
+  const int M = g->M, Mp = g->Mp;
+  cudaStream_t s = g->stream;
+  GK(allow_solve_smem());
+  k_gp_alpha<<<1, 1024, sizeof(double) * Mp, s>>>(g->dL, M, Mp, dy, dmu, g->dalpha, g->dscale + kMaxD);
+  k_gp_logdiag<<<1, 256, 0, s>>>(g->dL, M, Mp, g->dscale + kMaxD + 1);
+  g->launches += 2;
+  return MDGP_OK;
 }
 
 static int gp_fit_impl(mdgp_gp* g, const double* X, const double* y, const double* mu_X,
@@ -418,30 +510,35 @@ static int gp_fit_impl(mdgp_gp* g, const double* X, const double* y, const doubl
     GK(cudaMemcpyAsync(dfixed, p->fixed_scales, sizeof(double) * D, cudaMemcpyHostToDevice, s));
   }
   const Fallback fallback = make_fallback(p, D);
+  // the pair-separation row sums (M x D) use the factor's storage before
+  // the covariance fills it
   if (!p->fixed_scales) {
-    k_gp_pairsep<<<M, 128, 0, s>>>(g->dX, M, D, g->dscale);
+    k_gp_pairsep<<<M, 128, 0, s>>>(g->dX, M, D, g->dL);
     g->launches++;
   }
-  k_gp_scales<<<1, 32, 0, s>>>(g->dscale, M, D, fallback, dfixed);
+  k_gp_scales<<<1, 256, 0, s>>>(g->dL, g->dscale, M, D, fallback, dfixed);
   k_gp_cov<<<dim3((Mp + 127) / 128, Mp), 128, 0, s>>>(g->dX, M, Mp, D, g->dscale, g->sf2, g->l2, g->sn2, g->dL);
   g->launches += 2;
   const int nt = Mp / TB;
-  for (int kb = 0; kb < nt; ++kb) {
-    k_potrf_diag<<<1, 32, 0, s>>>(g->dL, Mp, kb, dstatus);
-    g->launches++;
-    const int rest = nt - kb - 1;
-    if (rest > 0) {
-      k_trsm_panel<<<rest * (TB / kTrsmRows), dim3(TB, kTrsmRows), 0, s>>>(g->dL, Mp, kb);
-      k_syrk_update<<<rest * (rest + 1) / 2, dim3(TB, TB), 0, s>>>(g->dL, Mp, kb, nt);
-      g->launches += 2;
+  if (nt >= kLookaheadTiles && g->fs[0]) {
+    const int st = enqueue_cholesky_lookahead(g, dstatus);
+    if (st) return st;
+  } else {
+    for (int kb = 0; kb < nt; ++kb) {
+      k_potrf_diag<<<1, 32, 0, s>>>(g->dL, Mp, kb, dstatus);
+      g->launches++;
+      const int rest = nt - kb - 1;
+      if (rest > 0) {
+        k_trsm_panel<<<rest * (TB / kTrsmRows), dim3(TB, kTrsmRows), 0, s>>>(g->dL, Mp, kb);
+        k_syrk_update<<<rest * (rest + 1) / 2, dim3(TB, TB), 0, s>>>(g->dL, Mp, kb, nt, 0);
+        g->launches += 2;
+      }
     }
   }
   if (g->has_alpha) {
-    GK(cudaFuncSetAttribute(k_gp_alpha, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(double) * Mp)));
-    k_gp_alpha<<<1, 1024, sizeof(double) * Mp, s>>>(g->dL, M, Mp, dy, dmuX, g->dalpha, g->dscale + kMaxD);
-    k_gp_logdiag<<<1, 256, 0, s>>>(g->dL, M, Mp, g->dscale + kMaxD + 1);
+    const int st = enqueue_alpha(g, dy, dmuX);
+    if (st) return st;
   }
-  g->launches++;
   int status = 0;
   GK(cudaGetLastError());
   GK(cudaMemcpyAsync(&status, dstatus, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -473,6 +570,8 @@ static int gp_fit_entry(mdgp_ctx* ctx, const double* X, const double* y, int64_t
   g->l2 = params->l2;
   g->sn2 = params->sn2;
   g->has_alpha = with_alpha;
+  for (int k = 0; k < 2; ++k) g->fs[k] = ctx->fact_stream[k];
+  for (int k = 0; k < 4; ++k) g->fe[k] = ctx->fact_event[k];
   int st = gp_fit_impl(g, X, with_alpha ? y : nullptr, with_alpha ? mu_X : nullptr, params);
   if (st != MDGP_OK) {
     std::snprintf(ctx->err, sizeof(ctx->err), "gp fit: %s", g->err[0] ? g->err : "not positive definite");
@@ -490,13 +589,13 @@ int mdgp_gp_fit(mdgp_ctx* ctx, const double* X, const double* y, int64_t M, int3
 }
 
 int mdgp_gp_predict(mdgp_gp* g, const double* Xs, int64_t m, const double* mu_Xs, double* mean, double* var) {
-  if (!g || m < 0 || (m > 0 && (!Xs || !mean || !var))) return MDGP_E_ARG;
+  if (!g || m < 0 || (m > 0 && (!Xs || (!mean && !var)))) return MDGP_E_ARG;
   if (m == 0) return MDGP_OK;
   cudaSetDevice(g->device);
   if (g->M == 0) {  // empty database: the prior (paper Sec. 3.1)
     for (int64_t q = 0; q < m; ++q) {
-      mean[q] = mu_Xs ? mu_Xs[q] : 0.0;
-      var[q] = g->sf2;
+      if (mean) mean[q] = mu_Xs ? mu_Xs[q] : 0.0;
+      if (var) var[q] = g->sf2;
     }
     return MDGP_OK;
   }
@@ -513,16 +612,43 @@ int mdgp_gp_predict(mdgp_gp* g, const double* Xs, int64_t m, const double* mu_Xs
   GK(cudaMemcpyAsync(g->dq, Xs, sizeof(double) * m * g->D, cudaMemcpyHostToDevice, s));
   if (mu_Xs) GK(cudaMemcpyAsync(g->dmu, mu_Xs, sizeof(double) * m, cudaMemcpyHostToDevice, s));
   const size_t smem = sizeof(double) * g->Mp;
-  GK(cudaFuncSetAttribute(k_gp_predict, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  GK(allow_solve_smem());
   k_gp_predict<<<(unsigned)m, 256, smem, s>>>(g->dX, g->dL, g->has_alpha ? g->dalpha : nullptr, g->dscale, g->M,
-                                              g->Mp, g->D, g->sf2,
-                                              g->l2, g->dq, mu_Xs ? g->dmu : nullptr, g->dmean, g->dvar);
+                                              g->Mp, g->D, g->sf2, g->l2, g->dq, mu_Xs ? g->dmu : nullptr,
+                                              g->dmean, g->dvar, var != nullptr);
   g->launches++;
   GK(cudaGetLastError());
-  GK(cudaMemcpyAsync(mean, g->dmean, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
-  GK(cudaMemcpyAsync(var, g->dvar, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
+  if (mean) GK(cudaMemcpyAsync(mean, g->dmean, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
+  if (var) GK(cudaMemcpyAsync(var, g->dvar, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
   GK(cudaStreamSynchronize(s));
   return MDGP_OK;
+}
+
+int mdgp_gp_set_outputs(mdgp_gp* g, const double* y, const double* mu_X) {
+  if (!g || (g->M > 0 && !y)) return MDGP_E_ARG;
+  if (g->M == 0) {
+    g->has_alpha = true;
+    return MDGP_OK;
+  }
+  cudaSetDevice(g->device);
+  cudaStream_t s = g->stream;
+  const int M = g->M;
+  double *dy = nullptr, *dmu = nullptr;
+  cudaError_t e = cudaMalloc(&dy, sizeof(double) * M);
+  if (e == cudaSuccess && mu_X) e = cudaMalloc(&dmu, sizeof(double) * M);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dy, y, sizeof(double) * M, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && mu_X) e = cudaMemcpyAsync(dmu, mu_X, sizeof(double) * M, cudaMemcpyHostToDevice, s);
+  int st = e == cudaSuccess ? MDGP_OK : gp_err(g, e);
+  if (st == MDGP_OK) st = enqueue_alpha(g, dy, dmu);
+  if (st == MDGP_OK) {
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    st = gp_err(g, e);
+  }
+  if (dy) cudaFree(dy);
+  if (dmu) cudaFree(dmu);
+  if (st == MDGP_OK) g->has_alpha = true;
+  return st;
 }
 
 int mdgp_gp_log_marginal(const mdgp_gp* g, double* lml) {
@@ -598,12 +724,12 @@ int mdgp_gp_free(mdgp_gp* g) {
   return MDGP_OK;
 }
 
-}  // extern "C"
-
-int gp_fit_variance_only(mdgp_ctx* ctx, const double* X, int64_t M, int32_t D, const mdgp_gp_params* params,
-                         mdgp_gp** out) {
+int mdgp_gp_fit_inputs(mdgp_ctx* ctx, const double* X, int64_t M, int32_t D, const mdgp_gp_params* params,
+                       mdgp_gp** out) {
   return gp_fit_entry(ctx, X, nullptr, M, D, params, nullptr, false, out);
 }
+
+}  // extern "C"
 
 // ---------------------------------------------------------------------------
 // Allocation-free GP posterior.
@@ -656,6 +782,7 @@ extern "C" int mdgp_gp_posterior_noalloc(const double* X, const double* y, int64
   int st = noalloc_scratch(device, &base);
   if (st) return st;
   cudaStream_t s = (cudaStream_t)stream;
+  if (allow_solve_smem() != cudaSuccess) return MDGP_E_CUDA;
   const int Mi = (int)M, Mp = (int)((M + TB - 1) / TB * TB);
   double* L = base;
   double* alpha = base + kNoAllocL;
@@ -664,8 +791,8 @@ extern "C" int mdgp_gp_posterior_noalloc(const double* X, const double* y, int64
   // the scratch keeps the previous call's contents: clear the accumulators
   if (cudaMemsetAsync(scale, 0, sizeof(double) * (kMaxD + 8), s) != cudaSuccess) return MDGP_E_CUDA;
   const Fallback fallback = make_fallback(params, D);
-  k_gp_pairsep<<<Mi, 128, 0, s>>>(X, Mi, D, scale);
-  k_gp_scales<<<1, 32, 0, s>>>(scale, Mi, D, fallback, nullptr);
+  k_gp_pairsep<<<Mi, 128, 0, s>>>(X, Mi, D, L);   // row sums in the factor's space, before the covariance
+  k_gp_scales<<<1, 256, 0, s>>>(L, scale, Mi, D, fallback, nullptr);
   // the factor is laid out with leading dimension Mp inside the fixed array
   k_gp_cov<<<dim3((Mp + 127) / 128, Mp), 128, 0, s>>>(X, Mi, Mp, D, scale, params->sf2, params->l2, params->sn2,
                                                       L);
@@ -675,13 +802,13 @@ extern "C" int mdgp_gp_posterior_noalloc(const double* X, const double* y, int64
     const int rest = nt - kb - 1;
     if (rest > 0) {
       k_trsm_panel<<<rest * (TB / kTrsmRows), dim3(TB, kTrsmRows), 0, s>>>(L, Mp, kb);
-      k_syrk_update<<<rest * (rest + 1) / 2, dim3(TB, TB), 0, s>>>(L, Mp, kb, nt);
+      k_syrk_update<<<rest * (rest + 1) / 2, dim3(TB, TB), 0, s>>>(L, Mp, kb, nt, 0);
     }
   }
   k_gp_alpha<<<1, 256, sizeof(double) * Mp, s>>>(L, Mi, Mp, y, mu_X, alpha, nullptr);
   if (m > 0)
     k_gp_predict<<<(unsigned)m, 256, sizeof(double) * Mp, s>>>(X, L, alpha, scale, Mi, Mp, D, params->sf2,
-                                                               params->l2, Xs, mu_Xs, mean, var);
+                                                               params->l2, Xs, mu_Xs, mean, var, true);
   if (cudaGetLastError() != cudaSuccess) return MDGP_E_CUDA;
   int h_status = 0;
   if (cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MDGP_E_CUDA;

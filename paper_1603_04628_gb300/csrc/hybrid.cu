@@ -20,7 +20,6 @@
 
 #include "mdgp.h"
 #include "md_ctx.h"
-#include "gp_internal.h"
 
 struct mdgp_hybrid {
   mdgp_ctx* ctx = nullptr;
@@ -88,51 +87,54 @@ void input_row(const mdgp_hybrid* H, int j, double* x) {
   }
 }
 
-// Fit on (X, y) rows [0, M) and predict the rows of Xq.
-int fit_predict(mdgp_hybrid* H, const std::vector<double>& X, const std::vector<double>& y,
-                const std::vector<double>& mX, int64_t M, double sn2, const double* Xq, int64_t m,
-                double* mean, double* var) {
+// q-GP hyperparameters of a step (Sec. 2.3 values; sn2 as the step fixes it)
+// with the per-dimension fallback scales; fb holds the fallbacks.
+mdgp_gp_params step_params(const mdgp_hybrid* H, double sn2, double* fb) {
   mdgp_gp_params gp;
   std::memset(&gp, 0, sizeof(gp));
   gp.sf2 = H->p.sf2;
   gp.l2 = H->p.l2;
   gp.sn2 = sn2;
-  double fb[3];
   fallback_scales(H, fb);
   gp.fallback_scale = 1.0;
   gp.fallback_scales = fb;
-  mdgp_gp* g = nullptr;
-  int st = mdgp_gp_fit(H->ctx, M ? X.data() : nullptr, M ? y.data() : nullptr, M, H->D, &gp,
-                       (H->mean_fn && M) ? mX.data() : nullptr, &g);
-  if (st) return st;
-  std::vector<double> mq;
-  if ((st = prior_mean(H, Xq, m, mq))) { mdgp_gp_free(g); return st; }
-  st = mdgp_gp_predict(g, Xq, m, H->mean_fn ? mq.data() : nullptr, mean, var);
-  mdgp_gp_free(g);
-  return st;
+  return gp;
 }
 
-// Posterior variances at the rows of Xq for a database with inputs X rows
-// [0, M): the gate needs no outputs, so the fit skips the alpha solve.
-int gate_variances(mdgp_hybrid* H, const std::vector<double>& X, int64_t M, double sn2, const double* Xq,
-                   int64_t m, double* var) {
-  mdgp_gp_params gp;
-  std::memset(&gp, 0, sizeof(gp));
-  gp.sf2 = H->p.sf2;
-  gp.l2 = H->p.l2;
-  gp.sn2 = sn2;
+// Factor for the database inputs X rows [0, M) (no outputs: the gate needs
+// none) and the posterior variances at the rows of Xq.
+int gate_fit(mdgp_hybrid* H, const std::vector<double>& X, int64_t M, double sn2, const double* Xq, int64_t m,
+             double* var, mdgp_gp** out) {
   double fb[3];
-  fallback_scales(H, fb);
-  gp.fallback_scale = 1.0;
-  gp.fallback_scales = fb;
+  const mdgp_gp_params gp = step_params(H, sn2, fb);
   mdgp_gp* g = nullptr;
-  int st = gp_fit_variance_only(H->ctx, M ? X.data() : nullptr, M, H->D, &gp, &g);
+  int st = mdgp_gp_fit_inputs(H->ctx, M ? X.data() : nullptr, M, H->D, &gp, &g);
   if (st) return st;
-  std::vector<double> mean((size_t)m);
-  st = mdgp_gp_predict(g, Xq, m, nullptr, mean.data(), var);
-  mdgp_gp_free(g);
-  return st;
+  st = mdgp_gp_predict(g, Xq, m, nullptr, nullptr, var);
+  if (st) { mdgp_gp_free(g); return st; }
+  *out = g;
+  return MDGP_OK;
 }
+
+// Means at the rows of Xq from a gate factor whose inputs are the database's
+// first M rows: the outputs y (and prior means mX) of those rows are added
+// on the same factor, so the result is that of a fresh fit to (X, y).
+int factor_means(mdgp_hybrid* H, mdgp_gp* g, const std::vector<double>& y, const std::vector<double>& mX,
+                 int64_t M, const double* Xq, int64_t m, double* mean) {
+  int st = mdgp_gp_set_outputs(g, M ? y.data() : nullptr, (H->mean_fn && M) ? mX.data() : nullptr);
+  if (st) return st;
+  std::vector<double> mq;
+  if ((st = prior_mean(H, Xq, m, mq))) return st;
+  return mdgp_gp_predict(g, Xq, m, H->mean_fn ? mq.data() : nullptr, mean, nullptr);
+}
+
+// The gate factors of one step; freed when the step ends.
+struct Factors {
+  std::vector<mdgp_gp*> g;
+  ~Factors() {
+    for (mdgp_gp* x : g) mdgp_gp_free(x);
+  }
+};
 
 }  // namespace
 
@@ -253,10 +255,15 @@ int mdgp_hybrid_step(mdgp_hybrid* H, double sigma_t, mdgp_hybrid_stats* stats) {
     }
     j0 = N;
   }
+  // factors.g[k]: the factor of the database with the first k gated inputs
+  // appended, the one every later mean up to the next MD section uses
+  Factors factors;
   while (j0 < N) {
     const int64_t Mv = (int64_t)(Xv.size() / D);
-    int st = gate_variances(H, Xv, Mv, sn2, Xq.data() + (size_t)D * j0, N - j0, var.data() + j0);
+    mdgp_gp* g = nullptr;
+    int st = gate_fit(H, Xv, Mv, sn2, Xq.data() + (size_t)D * j0, N - j0, var.data() + j0, &g);
     if (st) return st;
+    factors.g.push_back(g);
     int j = j0;
     for (; j < N; ++j) {
       H->sd[j] = std::sqrt(var[j]);
@@ -302,7 +309,8 @@ int mdgp_hybrid_step(mdgp_hybrid* H, double sigma_t, mdgp_hybrid_stats* stats) {
   }
   H->md_total += nmd;
   // means: each run of non-MD sections uses the database with every earlier
-  // MD result of this step appended
+  // MD result of this step appended, i.e. the inputs of gate factor k (k
+  // results appended) with their outputs added
   const double t2 = now_s();
   int k = 0, j = 0;
   while (j < N) {
@@ -319,8 +327,8 @@ int mdgp_hybrid_step(mdgp_hybrid* H, double sigma_t, mdgp_hybrid_stats* stats) {
     }
     const int jend = (k < nmd) ? md_idx[k] : N;
     const int64_t M = (int64_t)H->y.size();
-    int st = fit_predict(H, H->X, H->y, H->mX, M, sn2, Xq.data() + (size_t)D * j, jend - j, mean.data() + j,
-                         var.data() + j);
+    if (k >= (int)factors.g.size()) return MDGP_E_STATE;   // the gate scanned every section it factored for
+    int st = factor_means(H, factors.g[k], H->y, H->mX, M, Xq.data() + (size_t)D * j, jend - j, mean.data() + j);
     if (st) return st;
     for (int i = j; i < jend; ++i) {
       H->q[i] = mean[i];

@@ -20,6 +20,10 @@ struct mdgp_ctx {
   cudaStream_t own_stream = nullptr;  // created with the context
   cudaStream_t side_stream = nullptr; // captures the conditional rebuild bodies
   cudaStream_t side_stream2 = nullptr;  // nested capture (rebuild inside the step loop's WHILE body)
+  // GP factorisation with lookahead: [0] the diagonal/panel chain (high
+  // priority), [1] the bulk trailing updates; events order the two
+  cudaStream_t fact_stream[2] = {nullptr, nullptr};
+  cudaEvent_t fact_event[4] = {nullptr, nullptr, nullptr, nullptr};
   char err[256] = {0};
   // MD batch
   bool planned = false;

@@ -800,8 +800,15 @@ int mdgp_create(mdgp_ctx** out, int device, int precision) {
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->side_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->side_stream2, cudaStreamNonBlocking);
+  int prio_low = 0, prio_high = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
+  if (e == cudaSuccess)
+    e = cudaStreamCreateWithPriority(&ctx->fact_stream[0], cudaStreamNonBlocking, prio_high);
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&ctx->fact_stream[1], cudaStreamNonBlocking, prio_low);
+  for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+    e = cudaEventCreateWithFlags(&ctx->fact_event[k], cudaEventDisableTiming);
   if (e != cudaSuccess) {
-    delete ctx;
+    mdgp_destroy(ctx);
     return MDGP_E_CUDA;
   }
   ctx->stream = ctx->own_stream;
@@ -818,6 +825,8 @@ int mdgp_destroy(mdgp_ctx* ctx) {
   if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
   if (ctx->side_stream) cudaStreamDestroy(ctx->side_stream);
   if (ctx->side_stream2) cudaStreamDestroy(ctx->side_stream2);
+  for (cudaStream_t fs : ctx->fact_stream) if (fs) cudaStreamDestroy(fs);
+  for (cudaEvent_t fe : ctx->fact_event) if (fe) cudaEventDestroy(fe);
   delete ctx;
   return MDGP_OK;
 }

@@ -110,6 +110,9 @@ def lib():
         "mdgp_last_error": ([vp], ctypes.c_char_p),
         "mdgp_gp_fit": ([vp, dp, dp, i64, ctypes.c_int32, ctypes.POINTER(GPParams), dp, ctypes.POINTER(vp)],
                         ctypes.c_int),
+        "mdgp_gp_fit_inputs": ([vp, dp, i64, ctypes.c_int32, ctypes.POINTER(GPParams), ctypes.POINTER(vp)],
+                               ctypes.c_int),
+        "mdgp_gp_set_outputs": ([vp, dp, dp], ctypes.c_int),
         "mdgp_gp_predict": ([vp, dp, i64, dp, dp, dp], ctypes.c_int),
         "mdgp_gp_scales": ([vp, dp], ctypes.c_int),
         "mdgp_gp_log_marginal": ([vp, dp], ctypes.c_int),
@@ -281,13 +284,15 @@ class Context:
 
 
 class GP:
-    """A fitted Gaussian process (mdgp_gp) living on ctx's device."""
+    """A fitted Gaussian process (mdgp_gp) living on ctx's device.  With
+    y=None only the inputs are factored (mdgp_gp_fit_inputs); set_outputs
+    adds the outputs later on the same factor."""
 
     def __init__(self, ctx, X, y, sf2, l2, sn2, mu_X=None, fallback_scale=1.0, fixed_scales=None,
                  fallback_scales=None):
-        X = np.ascontiguousarray(np.asarray(X, dtype=np.float64).reshape(len(y), -1) if len(y) else
+        M = len(X) if y is None else len(y)
+        X = np.ascontiguousarray(np.asarray(X, dtype=np.float64).reshape(M, -1) if M else
                                  np.zeros((0, np.asarray(X).shape[-1] if np.ndim(X) == 2 else 1)))
-        y = np.ascontiguousarray(y, dtype=np.float64)
         self.D = X.shape[1]
         p = GPParams(float(sf2), float(l2), float(sn2), float(fallback_scale), None, None)
         self._fb = None
@@ -298,19 +303,36 @@ class GP:
         if fixed_scales is not None:
             self._fixed = np.ascontiguousarray(fixed_scales, dtype=np.float64)
             p.fixed_scales = _dp(self._fixed)
-        mu = None if mu_X is None else _dp(np.ascontiguousarray(mu_X, dtype=np.float64))
         self.h = ctypes.c_void_p()
         self.ctx = ctx
-        _check(ctx.h, lib().mdgp_gp_fit(ctx.h, _dp(X), _dp(y), len(y), self.D, ctypes.byref(p), mu,
+        self.M = M
+        if y is None:
+            _check(ctx.h, lib().mdgp_gp_fit_inputs(ctx.h, _dp(X), M, self.D, ctypes.byref(p),
+                                                   ctypes.byref(self.h)), "mdgp_gp_fit_inputs")
+            return
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        mu = None if mu_X is None else _dp(np.ascontiguousarray(mu_X, dtype=np.float64))
+        _check(ctx.h, lib().mdgp_gp_fit(ctx.h, _dp(X), _dp(y), M, self.D, ctypes.byref(p), mu,
                                         ctypes.byref(self.h)), "mdgp_gp_fit")
 
-    def predict(self, Xs, mu_Xs=None):
+    def set_outputs(self, y, mu_X=None):
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        if len(y) != self.M:
+            raise ValueError("set_outputs: %d outputs for %d inputs" % (len(y), self.M))
+        mu = None if mu_X is None else _dp(np.ascontiguousarray(mu_X, dtype=np.float64))
+        _check(None, lib().mdgp_gp_set_outputs(self.h, _dp(y), mu), "mdgp_gp_set_outputs")
+
+    def predict(self, Xs, mu_Xs=None, var=True):
+        """Posterior (mean, var) at Xs; with var=False the means alone
+        (no variance solve) and None for var."""
         Xs = np.ascontiguousarray(np.asarray(Xs, dtype=np.float64).reshape(-1, self.D))
         m = len(Xs)
-        mean = np.zeros(m); var = np.zeros(m)
+        mean = np.zeros(m)
+        v = np.zeros(m) if var else None
         mu = None if mu_Xs is None else _dp(np.ascontiguousarray(mu_Xs, dtype=np.float64))
-        _check(None, lib().mdgp_gp_predict(self.h, _dp(Xs), m, mu, _dp(mean), _dp(var)), "mdgp_gp_predict")
-        return mean, var
+        _check(None, lib().mdgp_gp_predict(self.h, _dp(Xs), m, mu, _dp(mean), None if v is None else _dp(v)),
+               "mdgp_gp_predict")
+        return mean, v
 
     def log_marginal(self):
         out = ctypes.c_double()

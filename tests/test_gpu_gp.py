@@ -125,3 +125,71 @@ def test_optimize_matches_oracle_search(ctx):
     np.testing.assert_allclose([got["sf2"], got["l2"], got["sn2"]], [sf2, l2, sn2], rtol=1e-12)
     assert got["lml"] == pytest.approx(f, rel=1e-9, abs=1e-8)
     assert f > ogp.GP(X, y, 1.0, 1.0, 0.1).log_marginal_likelihood()
+
+
+@pytest.mark.parametrize("M", [0, 45, 300])
+def test_inputs_only_factor_then_outputs_equals_full_fit(ctx, M):
+    # Eq. predVarEq holds no outputs: a factor of the inputs alone gives the
+    # full fit's variances, and once its outputs are set the same kernels on
+    # the same factor give the full fit's means and evidence, bit for bit;
+    # the means-only predict skips the variance and changes no mean
+    from paper_1603_04628_gb300 import native
+    X, y = synth.gp_dataset(M, seed=40 + M) if M else (np.zeros((0, 2)), np.zeros(0))
+    Xs = synth.gp_queries(61, seed=41)
+    mu = lambda Z: 0.2 * Z[:, 0] + 0.05
+    sf2, l2, sn2 = 1.7, 1.0, 0.004
+    full = native.GP(ctx, X, y, sf2, l2, sn2, mu_X=mu(X))
+    part = native.GP(ctx, X, None, sf2, l2, sn2)
+    m0, v0 = part.predict(Xs, mu_Xs=mu(Xs))
+    mf, vf = full.predict(Xs, mu_Xs=mu(Xs))
+    assert np.array_equal(v0, vf)
+    assert np.array_equal(m0, mu(Xs))                    # no outputs yet: the prior mean
+    ref = ogp.GP(X, y, sf2, l2, sn2, mu=mu)
+    _cmp((mf, vf), ref.predict(Xs), y, sf2)
+    part.set_outputs(y, mu_X=mu(X))
+    m1, v1 = part.predict(Xs, mu_Xs=mu(Xs))
+    assert np.array_equal(m1, mf) and np.array_equal(v1, vf)
+    assert part.log_marginal() == full.log_marginal()
+    m2, v2 = part.predict(Xs, mu_Xs=mu(Xs), var=False)
+    assert v2 is None and np.array_equal(m2, mf)
+    if M:
+        # new outputs for the same inputs: a fresh fit to them, bit for bit
+        y2 = np.cos(3.0 * X[:, 0]) - X[:, 1]
+        part.set_outputs(y2)
+        fresh = native.GP(ctx, X, y2, sf2, l2, sn2)
+        assert np.array_equal(part.predict(Xs)[0], fresh.predict(Xs)[0])
+        fresh.close()
+    full.close()
+    part.close()
+
+
+def test_lookahead_factor_equals_single_stream_factor(ctx):
+    # from 4 tile columns on, the fit overlaps each step's bulk trailing
+    # update with the next diagonal tile and panel on a second stream; the
+    # allocation-free entry point factors on one stream.  Every tile gets its
+    # updates in the same order either way, so the factors agree bit for bit,
+    # and with them the posterior variances (which depend on the factor alone)
+    torch = pytest.importorskip("torch")
+    import ctypes
+    from paper_1603_04628_gb300 import native
+    fn = native.lib().mdgp_gp_posterior_noalloc
+    vp = ctypes.c_void_p
+    fn.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(native.GPParams), vp, vp,
+                   ctypes.c_int64, vp, vp, vp, vp]
+    fn.restype = ctypes.c_int
+    sf2, l2, sn2 = 1.1, 1.0, 0.003
+    for M in (160, 509):
+        X, y = synth.gp_dataset(M, seed=70 + M)
+        Xs = synth.gp_queries(45, seed=71)
+        g = native.GP(ctx, X, None, sf2, l2, sn2)
+        var = g.predict(Xs)[1]
+        g.close()
+        t = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda")
+        mean_d, var_d = torch.empty(len(Xs), dtype=torch.float64, device="cuda"), \
+            torch.empty(len(Xs), dtype=torch.float64, device="cuda")
+        tX, ty, tXs = t(X), t(y), t(Xs)
+        p = native.GPParams(sf2, l2, sn2, 1.0, None, None)
+        st = fn(tX.data_ptr(), ty.data_ptr(), M, 2, ctypes.byref(p), None, tXs.data_ptr(), len(Xs), None,
+                mean_d.data_ptr(), var_d.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        assert st == 0
+        assert np.array_equal(var_d.cpu().numpy(), var)
