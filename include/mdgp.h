@@ -330,7 +330,10 @@ typedef struct {
   double sf2, l2, sn2;        /* q-GP hyperparameters (Sec. 2.3) */
   int32_t inputs;             /* q-GP inputs: 0 = (h, G); 1 = the paper's (h, n, F) with
                                  F = -G / n the force per unit mass on the fluid (Sec. 2.4) */
-  int32_t reserved;
+  int32_t factor_cache_mb;    /* device memory, in MiB, for the gate's covariance factors that a
+                                 step keeps so that its means reuse them (0 = 4096; < 0 = keep
+                                 none).  A factor not kept is computed again for the means, with
+                                 the same result bit for bit. */
 } mdgp_macro_params;
 
 /* Time step statistics returned by mdgp_hybrid_step. */

@@ -256,14 +256,25 @@ int mdgp_hybrid_step(mdgp_hybrid* H, double sigma_t, mdgp_hybrid_stats* stats) {
     j0 = N;
   }
   // factors.g[k]: the factor of the database with the first k gated inputs
-  // appended, the one every later mean up to the next MD section uses
+  // appended, the one every later mean up to the next MD section uses; null
+  // where keeping it would pass the memory budget
   Factors factors;
+  const long long cache_mb = P.factor_cache_mb ? P.factor_cache_mb : 4096;
+  const long long keep_bytes = P.factor_cache_mb < 0 ? -1 : cache_mb << 20;
+  long long kept = 0;
   while (j0 < N) {
     const int64_t Mv = (int64_t)(Xv.size() / D);
     mdgp_gp* g = nullptr;
     int st = gate_fit(H, Xv, Mv, sn2, Xq.data() + (size_t)D * j0, N - j0, var.data() + j0, &g);
     if (st) return st;
-    factors.g.push_back(g);
+    const long long Mp = (Mv + 31) / 32 * 32, bytes = Mp * Mp * (long long)sizeof(double);
+    if (kept + bytes <= keep_bytes) {
+      kept += bytes;
+      factors.g.push_back(g);
+    } else {
+      mdgp_gp_free(g);
+      factors.g.push_back(nullptr);
+    }
     int j = j0;
     for (; j < N; ++j) {
       H->sd[j] = std::sqrt(var[j]);
@@ -328,7 +339,19 @@ int mdgp_hybrid_step(mdgp_hybrid* H, double sigma_t, mdgp_hybrid_stats* stats) {
     const int jend = (k < nmd) ? md_idx[k] : N;
     const int64_t M = (int64_t)H->y.size();
     if (k >= (int)factors.g.size()) return MDGP_E_STATE;   // the gate scanned every section it factored for
-    int st = factor_means(H, factors.g[k], H->y, H->mX, M, Xq.data() + (size_t)D * j, jend - j, mean.data() + j);
+    mdgp_gp* g = factors.g[k];
+    mdgp_gp* own = nullptr;
+    if (!g) {
+      // not kept: the same inputs factored again (the scales and the factor
+      // are deterministic, so it is the gate's factor bit for bit)
+      double fb[3];
+      const mdgp_gp_params gp = step_params(H, sn2, fb);
+      int st0 = mdgp_gp_fit_inputs(H->ctx, M ? H->X.data() : nullptr, M, D, &gp, &own);
+      if (st0) return st0;
+      g = own;
+    }
+    int st = factor_means(H, g, H->y, H->mX, M, Xq.data() + (size_t)D * j, jend - j, mean.data() + j);
+    if (own) mdgp_gp_free(own);
     if (st) return st;
     for (int i = j; i < jend; ++i) {
       H->q[i] = mean[i];

@@ -55,7 +55,7 @@ class MacroParams(ctypes.Structure):
                 ("period", ctypes.c_double), ("dt", ctypes.c_double), ("T", ctypes.c_double),
                 ("md_steps_eq", ctypes.c_int64), ("md_steps_sample", ctypes.c_int64), ("seed", ctypes.c_uint64),
                 ("sf2", ctypes.c_double), ("l2", ctypes.c_double), ("sn2", ctypes.c_double),
-                ("inputs", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("inputs", ctypes.c_int32), ("factor_cache_mb", ctypes.c_int32)]
 
 
 class HybridStats(ctypes.Structure):

@@ -25,12 +25,14 @@ def oracle_md(el):
     return omd.element(omd.make_params(el))
 
 
-@pytest.mark.parametrize("sigma_t", [0.5, 1.2])
-def test_hybrid_steps_match_sequential_oracle(sigma_t):
+# cache_mb -1 keeps none of the gate's factors, so every run of non-MD
+# sections takes its means from a refit of the same inputs
+@pytest.mark.parametrize("sigma_t,cache_mb", [(0.5, 0), (1.2, 0), (0.5, -1)])
+def test_hybrid_steps_match_sequential_oracle(sigma_t, cache_mb):
     from paper_1603_04628_gb300 import build, native
     build.build()
     ctx = native.Context(0, native.PREC_FP64)
-    hy = native.Hybrid(ctx, **gpu_params(CASE))
+    hy = native.Hybrid(ctx, factor_cache_mb=cache_mb, **gpu_params(CASE))
     ref = ohy.Channel(**CASE)
     total = 0
     for step in range(4):
