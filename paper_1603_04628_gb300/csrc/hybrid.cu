@@ -132,7 +132,8 @@ int factor_means(mdgp_hybrid* H, mdgp_gp* g, const std::vector<double>& y, const
 struct Factors {
   std::vector<mdgp_gp*> g;
   ~Factors() {
-    for (mdgp_gp* x : g) mdgp_gp_free(x);
+    for (mdgp_gp* x : g)
+      if (x) mdgp_gp_free(x);   // null: not kept (memory budget)
   }
 };
 
