@@ -48,3 +48,18 @@ def test_defaults_and_argument_checks_without_a_gpu(built):
     assert L.mdgp_micro_batch(None, None, 0, None) == -1
     assert L.mdgp_micro_launch(None) == -1
     assert L.mdgp_create(None, 0, 0) == -1
+
+
+def test_gp_and_macro_entry_points_reject_null_handles_without_a_gpu(built):
+    import ctypes as C
+    from paper_1603_04628_gb300 import native
+    L = native.lib()
+    p = native.GPParams(1.0, 1.0, 0.01, 1.0, None, None)
+    out = C.c_void_p()
+    assert L.mdgp_gp_fit_inputs(None, None, 0, 2, C.byref(p), C.byref(out)) == -1
+    assert L.mdgp_gp_set_outputs(None, None, None) == -1
+    assert L.mdgp_gp_predict(None, None, 0, None, None, None) == -1
+    mp = native.MacroParams()
+    assert L.mdgp_macro_params_default(C.byref(mp)) == 0
+    # the factor budget defaults to 0 (4 GiB); the q-GP inputs to (h, G)
+    assert (mp.n_sections, mp.inputs, mp.factor_cache_mb) == (200, 0, 0)
