@@ -292,6 +292,93 @@ __global__ void __launch_bounds__(1024) k_gp_alpha(const double* L, int M, int M
   }
 }
 
+// alpha = C^-1 (y - mu) over many SMs: one launch per tile column, forward
+// (L z = r) then backward (L^T a = z).  In the launch for tile kb every block
+// stages the diagonal tile and solves it (its right-hand side is final: the
+// launches for the earlier tiles have subtracted their parts), block 0
+// stores the TB unknowns, and the grid subtracts their contribution from the
+// unknowns still open.  The unknowns of tile kb are read only in its own
+// launch and every open unknown is updated by one thread, so the launches
+// need no synchronisation beyond their order on the stream.
+//
+// Forward, tile kb: z_kb from r_kb, then r_i -= sum_c L_{i, kb TB + c} z_c
+// for the rows i below the tile, one warp per row (lanes along the row).
+__global__ void __launch_bounds__(256) k_tri_fwd(const double* L, int Mp, int kb, double* r, double* z) {
+  __shared__ double T[TB][TB + 1];
+  __shared__ double zt[TB];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int r0 = kb * TB;
+  for (int rr = wid; rr < TB; rr += nw) T[rr][lane] = L[(size_t)(r0 + rr) * Mp + r0 + lane];
+  __syncthreads();
+  if (wid == 0) {
+    double x = r[r0 + lane];
+    const double rdl = 1.0 / T[lane][lane];
+    for (int j = 0; j < TB; ++j) {
+      if (lane == j) x *= rdl;
+      const double xs = __shfl_sync(kFullMask, x, j);
+      if (lane > j) x -= T[lane][j] * xs;
+    }
+    zt[lane] = x;
+    if (blockIdx.x == 0) z[r0 + lane] = x;
+  }
+  __syncthreads();
+  for (int i = r0 + TB + blockIdx.x * nw + wid; i < Mp; i += gridDim.x * nw) {
+    const double t = warp_sum_d(L[(size_t)i * Mp + r0 + lane] * zt[lane]);
+    if (lane == 0) r[i] -= t;
+  }
+}
+
+// Backward, tile kb: a_kb from t_kb (the transposed diagonal tile), then
+// t_i -= sum_c L_{kb TB + c, i} a_c for the unknowns i above the tile, one
+// thread per i (consecutive threads read consecutive columns).
+__global__ void __launch_bounds__(256) k_tri_bwd(const double* L, int Mp, int kb, double* t, double* a) {
+  __shared__ double T[TB][TB + 1];
+  __shared__ double at[TB];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int r0 = kb * TB;
+  for (int rr = wid; rr < TB; rr += nw) T[rr][lane] = L[(size_t)(r0 + rr) * Mp + r0 + lane];
+  __syncthreads();
+  if (wid == 0) {
+    double x = t[r0 + lane];
+    const double rdl = 1.0 / T[lane][lane];
+    for (int j = TB - 1; j >= 0; --j) {
+      if (lane == j) x *= rdl;
+      const double xs = __shfl_sync(kFullMask, x, j);
+      if (lane < j) x -= T[j][lane] * xs;
+    }
+    at[lane] = x;
+    if (blockIdx.x == 0) a[r0 + lane] = x;
+  }
+  __syncthreads();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < r0; i += gridDim.x * blockDim.x) {
+    double sum = 0.0;
+#pragma unroll 8
+    for (int c = 0; c < TB; ++c) sum += L[(size_t)(r0 + c) * Mp + i] * at[c];
+    t[i] -= sum;
+  }
+}
+
+// r = y - mu on the M data rows, 0 on the padding (Mp).
+__global__ void k_gp_resid(const double* y, const double* mu, int M, int Mp, double* r) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < Mp) r[i] = i < M ? y[i] - (mu ? mu[i] : 0.0) : 0.0;
+}
+
+// (y - mu)^T alpha, the data term of Eq. evidenceEq (one block).
+__global__ void k_gp_dot(const double* y, const double* mu, const double* alpha, int M, double* out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < M; i += blockDim.x) s += (y[i] - (mu ? mu[i] : 0.0)) * alpha[i];
+  s = warp_sum_d(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+    *out = tot;
+  }
+}
+
 // sum_i log L_ii over the M data rows: half the log-determinant of C
 // (Eq. evidenceEq).
 __global__ void k_gp_logdiag(const double* L, int M, int Mp, double* out) {
@@ -399,6 +486,7 @@ struct mdgp_gp {
   int M = 0, Mp = 0, D = 0;
   double sf2 = 1, l2 = 1, sn2 = 0;
   double *dX = nullptr, *dL = nullptr, *dalpha = nullptr, *dscale = nullptr;
+  double* dwork = nullptr;   // 2 Mp: right-hand side and forward solution of the alpha solve
   double *dq = nullptr, *dmu = nullptr, *dmean = nullptr, *dvar = nullptr;
   size_t qcap = 0;
   bool has_alpha = true;   // false: factor only (posterior variances, no means or evidence)
@@ -421,7 +509,7 @@ static int gp_err(mdgp_gp* g, cudaError_t e) {
   } while (0)
 
 static void gp_release(mdgp_gp* g) {
-  for (double** p : {&g->dX, &g->dL, &g->dalpha, &g->dscale, &g->dq, &g->dmu, &g->dmean, &g->dvar})
+  for (double** p : {&g->dX, &g->dL, &g->dalpha, &g->dscale, &g->dwork, &g->dq, &g->dmu, &g->dmean, &g->dvar})
     if (*p) { cudaFree(*p); *p = nullptr; }
 }
 
@@ -470,10 +558,22 @@ static int enqueue_cholesky_lookahead(mdgp_gp* g, int* dstatus) {
 static int enqueue_alpha(mdgp_gp* g, const double* dy, const double* dmu) {
   const int M = g->M, Mp = g->Mp;
   cudaStream_t s = g->stream;
-  GK(allow_solve_smem());
-  k_gp_alpha<<<1, 1024, sizeof(double) * Mp, s>>>(g->dL, M, Mp, dy, dmu, g->dalpha, g->dscale + kMaxD);
+  const int nt = Mp / TB;
+  double *r = g->dwork, *z = g->dwork + Mp;
+  k_gp_resid<<<(Mp + 255) / 256, 256, 0, s>>>(dy, dmu, M, Mp, r);
+  for (int kb = 0; kb < nt; ++kb) {
+    const int rows = Mp - (kb + 1) * TB;                 // rows below the tile, 8 per block
+    const int blocks = rows > 0 ? (rows + 7) / 8 : 1;
+    k_tri_fwd<<<blocks, 256, 0, s>>>(g->dL, Mp, kb, r, z);
+  }
+  for (int kb = nt - 1; kb >= 0; --kb) {
+    const int cols = kb * TB;                            // unknowns above the tile, 256 per block
+    const int blocks = cols > 0 ? (cols + 255) / 256 : 1;
+    k_tri_bwd<<<blocks, 256, 0, s>>>(g->dL, Mp, kb, z, g->dalpha);
+  }
+  k_gp_dot<<<1, 1024, 0, s>>>(dy, dmu, g->dalpha, M, g->dscale + kMaxD);
   k_gp_logdiag<<<1, 256, 0, s>>>(g->dL, M, Mp, g->dscale + kMaxD + 1);
-  g->launches += 2;
+  g->launches += 2 * nt + 3;
   return MDGP_OK;
 }
 
@@ -496,6 +596,7 @@ static int gp_fit_impl(mdgp_gp* g, const double* X, const double* y, const doubl
   GK(cudaMalloc(&g->dX, sizeof(double) * M * D));
   GK(cudaMalloc(&g->dL, sizeof(double) * (size_t)Mp * Mp));
   GK(cudaMalloc(&g->dalpha, sizeof(double) * Mp));
+  GK(cudaMalloc(&g->dwork, sizeof(double) * 2 * Mp));
   GK(cudaMalloc(&dy, sizeof(double) * M));
   GK(cudaMalloc(&dstatus, sizeof(int)));
   GK(cudaMemcpyAsync(g->dX, X, sizeof(double) * M * D, cudaMemcpyHostToDevice, s));
