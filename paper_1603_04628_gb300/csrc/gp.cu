@@ -214,7 +214,9 @@ __global__ void k_syrk_update(double* A, int Mp, int kb, int nt, int part) {
 }
 
 // alpha = C^-1 (y - mu) by blocked forward then backward substitution in one
-// block of 32 warps.  Forward (L z = r), tile row by tile row: warp w
+// block (the allocation-free entry point's solve: one launch, no work
+// buffer; fits use the tile-column launches below).  Forward (L z = r), tile
+// row by tile row: warp w
 // subtracts from z of row r0 + w its dot product with the solved part (lanes
 // over the row: coalesced), the TB x TB diagonal tile is staged in shared
 // memory and warp 0 solves the triangle.  Backward (L^T a = z): lane i owns
