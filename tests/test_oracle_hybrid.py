@@ -115,3 +115,40 @@ def test_paper_inputs_rows_and_pressure_gp_interpolates():
     # no pre-simulation data: the linear law
     d = channel(inputs=1)
     np.testing.assert_allclose(d.pressure(), d.K * (d.n - d.n0))
+
+
+def _four_sections(**kw):
+    # x_j = 0, 50, 100, 150 on L = 200: h = 12 (1 - 0.5 cos(2 pi x_j / L)) = 6, 12, 18, 12,
+    # so A_j = h_j L_z = 60, 120, 180, 120
+    base = dict(n_sections=4, dx=50.0, h0=12.0, Lz=10.0, K=10.0, n0=0.8, dt=20.0, dP_amp=400.0, period=1000.0)
+    base.update(kw)
+    return hybrid.Channel(**base)
+
+
+def test_continuity_update_by_hand():
+    # Eq. continuityEq with central differences: flow q_1 = 1 in +x at
+    # section 1 carries mass out of the region around section 0 into the
+    # region around section 2:
+    #   dn_0 = -dt / A_0 (q_1 - q_3) / (2 dx) = -20 / 60 / 100 = -1/300
+    #   dn_2 = -dt / A_2 (q_3 - q_1) / (2 dx) = +20 / 180 / 100 = +1/900
+    c = _four_sections()
+    np.testing.assert_allclose(c.h, [6.0, 12.0, 18.0, 12.0], rtol=1e-15)
+    c.continuity(np.array([0.0, 1.0, 0.0, 0.0]))
+    np.testing.assert_allclose(c.n - 0.8, [-1.0 / 300.0, 0.0, 1.0 / 900.0, 0.0], rtol=1e-12, atol=1e-16)
+
+
+def test_pressure_gradient_and_forcing_by_hand():
+    # p = K (n - n0) = 0, 1, 0, -1 for n = 0.8, 0.9, 0.8, 0.7; periodic central
+    # differences (p_{j+1} - p_{j-1}) / (2 dx) = 0.02, 0, -0.02, 0.  A quarter
+    # period in, the inlet-outlet difference is +dP_amp = 400, a uniform
+    # gradient -400 / 200 = -2, so G = dp/dx - 2, and the element's body
+    # force F = -G / n (Eq. momentumEq) points downstream (+x).
+    c = _four_sections(density0=[0.8, 0.9, 0.8, 0.7])
+    np.testing.assert_allclose(c.pressure(), [0.0, 1.0, 0.0, -1.0], rtol=0, atol=1e-14)
+    G = c.gradients(250.0)
+    np.testing.assert_allclose(G, [0.02 - 2.0, -2.0, -0.02 - 2.0, -2.0], rtol=1e-13)
+    el = c.element(1, G[1], 0)
+    from oracle import md
+    assert md.make_params(el).g == pytest.approx(2.0 / 0.9, rel=1e-14)
+    # no forcing at t = 0 and half a period
+    np.testing.assert_allclose(c.gradients(0.0), [0.02, 0.0, -0.02, 0.0], rtol=1e-13, atol=1e-15)

@@ -225,3 +225,162 @@ def test_block_standard_error_matches_definition():
     assert r["q"] == pytest.approx(vals.mean(), rel=1e-13)
     assert r["q_se"] == pytest.approx(np.std(means, ddof=1) / 2.0, rel=1e-12)
     assert r["p_se"] == pytest.approx(2 * np.std(means, ddof=1) / 2.0, rel=1e-12)
+
+
+# ---------------------------------------------------------------- closed forms in a dilute box
+# Atoms further apart than r_c (and from every wall) feel no pair force, so
+# velocity Verlet with the body force of Eq. momentumEq gives each fluid atom
+# v_x(after k steps) = v_x(0) + k g dt / m exactly (two half kicks of
+# dt g / (2m) per step), and every sampled average has a closed form.  These
+# pin the measurement definitions (q = (m / L_x) sum_fluid v_x, P_xx over the
+# slab volume, the kinetic temperature) and the body force's direction, size
+# and restriction to fluid atoms.
+DILUTE_V = np.array([[0.30, -0.20, 0.10], [-0.70, 0.40, -0.50], [1.10, 0.05, 0.20], [0.25, -0.35, 0.60],
+                     [-0.15, 0.80, -0.90], [0.55, -0.60, 0.35], [-1.00, 0.10, 0.45], [0.65, 0.30, -0.25]])
+
+
+def _dilute_state(mode):
+    # 8 fluid atoms on a 2 x 2 x 2 grid, at least 5 apart (r_c = 2.5); with
+    # walls (mode 0) the slab is 14 high and the atoms sit 4.5 or more from
+    # both walls
+    if mode == 2:
+        el = dict(h=10.0, Lx=10.0, Lz=12.0, density=8 / 1200.0, T=1.0, g=0.01)
+        ys = (2.5, 7.5)
+    else:
+        el = dict(h=14.0, Lx=10.0, Lz=12.0, density=8 / 1680.0, T=1.0, g=0.01)
+        ys = (4.5, 9.5)
+    fl = np.array([[x, y, z] for x in (2.5, 7.5) for y in ys for z in (3.0, 9.0)])
+    return el, fl
+
+
+@pytest.mark.parametrize("mode", [0, 2])
+def test_dilute_box_measurements_are_closed_forms(mode):
+    el, fl = _dilute_state(mode)
+    m, g, dt, eq, S = 2.0, el["g"], 0.005, 10, 40
+    p = md.make_params(dict(el, steps_eq=eq, steps_sample=S), mass=m, dt=dt, n_blocks=4, gamma_wall=0.0, mode=mode)
+    nf, nw = md.counts(p)
+    assert nf == 8
+    x, v, a, sp = md.init(p)
+    x[:nf] = fl
+    v[:nf] = DILUTE_V
+    acc, st = md.simulate(p, x, v, a, sp, 0, eq + S)
+    r = md.finalize(p, acc)
+    assert st == 0
+    V = el["Lx"] * el["h"] * el["Lz"]
+    k = np.arange(eq + 1, eq + S + 1)                       # steps done at each sample
+    vx = DILUTE_V[:, 0][None, :] + (k * g * dt / m)[:, None]   # samples x atoms
+    q_ref = m * vx.sum(axis=1).mean() / el["Lx"]
+    p_ref = m * (vx ** 2).sum(axis=1).mean() / V
+    vyz2 = (DILUTE_V[:, 1:] ** 2).sum()
+    T_ref = (m * ((vx ** 2).sum(axis=1) + vyz2) / (3 * nf)).mean()
+    assert r["q"] == pytest.approx(q_ref, rel=1e-12)
+    assert r["p"] == pytest.approx(p_ref, rel=1e-12)
+    assert r["T_meas"] == pytest.approx(T_ref, rel=1e-12)
+    # q grows linearly in g: the same run at twice the force
+    p2 = md.make_params(dict(el, g=2 * g, steps_eq=eq, steps_sample=S), mass=m, dt=dt, n_blocks=4,
+                        gamma_wall=0.0, mode=mode)
+    x2, v2, a2, sp2 = md.init(p2)
+    x2[:nf] = fl
+    v2[:nf] = DILUTE_V
+    acc2, _ = md.simulate(p2, x2, v2, a2, sp2, 0, eq + S)
+    r2 = md.finalize(p2, acc2)
+    q0 = m * DILUTE_V[:, 0].sum() / el["Lx"]
+    assert (r2["q"] - q0) == pytest.approx(2 * (r["q"] - q0), rel=1e-10)
+    # the final fluid velocities, exactly
+    np.testing.assert_allclose(v[:nf, 0], DILUTE_V[:, 0] + (eq + S) * g * dt / m, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(v[:nf, 1:], DILUTE_V[:, 1:], rtol=0, atol=1e-15)
+
+
+def test_dilute_box_body_force_spares_walls():
+    # tethered, unthermostatted walls far from every fluid atom: the body
+    # force moves the fluid only, so the walls' total momentum stays what
+    # their own (zero-mean) start gave them
+    el, fl = _dilute_state(0)
+    p = md.make_params(dict(el, g=0.5), gamma_wall=0.0)
+    nf, nw = md.counts(p)
+    x, v, a, sp = md.init(p)
+    x[:nf] = fl
+    v[:nf] = DILUTE_V
+    md.simulate(p, x, v, a, sp, 0, 200)
+    assert np.abs(v[nf:].sum(axis=0)).max() < 1e-9
+    np.testing.assert_allclose(v[:nf, 0], DILUTE_V[:, 0] + 200 * 0.5 * 0.005, atol=1e-12)
+
+
+def test_berendsen_z_relaxation_law():
+    # Frozen walls (mode 1) with the Berendsen thermostat on the fluid's v_z,
+    # dilute non-interacting fluid: the thermostat's defining relaxation
+    # dT_z/dt = (T0 - T_z) / tau_T, taken one step at a time, gives
+    # T_z(n) = T0 + (T_z(0) - T0) (1 - dt / tau_T)^n with T_z = m <v_z^2>
+    # over fluid atoms; v_x and v_y are untouched (apart from the body force)
+    # and every v_z is scaled by the same factor.
+    el = dict(h=20.0, Lx=12.0, Lz=12.0, density=4 / 2880.0, T=1.1, g=0.02)
+    m, dt, tau, n = 1.5, 0.005, 0.5, 60
+    p = md.make_params(el, mode=1, mass=m, dt=dt, tau_T=tau)
+    nf, nw = md.counts(p)
+    assert nf == 4
+    x, v, a, sp = md.init(p)
+    x[:nf] = [[3.0, 10.0, 3.0], [9.0, 10.0, 3.0], [3.0, 10.0, 9.0], [9.0, 10.0, 9.0]]
+    v0 = np.array([[0.2, -0.1, 1.0], [-0.4, 0.3, -2.0], [0.1, 0.2, 0.5], [0.6, -0.5, 1.5]])
+    v[:nf] = v0
+    assert np.abs(v[nf:]).max() == 0.0           # frozen walls start at rest
+    md.simulate(p, x, v, a, sp, 0, n)
+    Tz0 = m * (v0[:, 2] ** 2).mean()
+    Tz = m * (v[:nf, 2] ** 2).mean()
+    assert Tz == pytest.approx(1.1 + (Tz0 - 1.1) * (1 - dt / tau) ** n, rel=1e-12)
+    np.testing.assert_allclose(v[:nf, 2] / v0[:, 2], v[0, 2] / v0[0, 2], rtol=1e-13)
+    assert v[0, 2] / v0[0, 2] > 0
+    np.testing.assert_allclose(v[:nf, 0], v0[:, 0] + n * 0.02 * dt / m, atol=1e-13)
+    np.testing.assert_allclose(v[:nf, 1], v0[:, 1], atol=1e-15)
+    assert np.abs(v[nf:]).max() == 0.0           # and stay at rest
+
+
+def test_berendsen_brings_interacting_fluid_to_target():
+    # the interacting fluid between frozen walls, started at T = 1.1 and
+    # thermostatted towards 1.6 on v_z alone: collisions share the heat, so
+    # the kinetic temperature of all three components settles at the target
+    el = dict(h=6.0, Lx=7.5, Lz=7.5, density=0.8, T=1.1, g=0.0, steps_eq=1500, steps_sample=1500, seed=5, id=1)
+    p = md.make_params(el, mode=1, tau_T=0.1)
+    x, v, a, sp = md.init(p)
+    p.T = 1.6
+    acc, st = md.simulate(p, x, v, a, sp, 0, 3000)
+    r = md.finalize(p, acc)
+    assert st == 0
+    assert r["T_meas"] == pytest.approx(1.6, rel=0.03)
+
+
+def test_body_force_from_pressure_gradient():
+    # Eq. momentumEq: F = F_ext - (m / rho) dp/dx with rho = m n
+    p = md.make_params(dict(h=8.0, Lx=10.0, Lz=10.0, density=0.8, T=1.1, g_ext=0.01, dpdx=-0.04))
+    assert p.g == pytest.approx(0.01 + 0.05, rel=1e-15)
+
+
+def _lr_run(args):
+    g, seed = args
+    el = dict(h=12.0, Lx=7.5, Lz=7.5, density=0.8, T=1.1, g=g, steps_eq=1000, steps_sample=3000, seed=seed, id=seed)
+    return md.element(md.make_params(el))
+
+
+@pytest.mark.slow
+def test_linear_response_in_weak_forcing():
+    # Poiseuille-like flow between the tethered walls: in weak forcing the
+    # steady flow rate is linear in the body force, q(2g) = 2 q(g), with base
+    # force g = 0.02.  The fluid's momentum relaxes through the walls over
+    # ~1000 steps, longer than the blocks of one run, so each arm's standard
+    # error is the spread of its eight independent seeds; the bound is two
+    # combined standard errors of the ratio.  (The exact linearity of the
+    # body force itself is pinned by the dilute-box closed forms above.)
+    import multiprocessing as mpr
+    md.build()
+    jobs = [(0.02, 400 + k) for k in range(8)] + [(0.04, 500 + k) for k in range(8)]
+    with mpr.get_context("spawn").Pool(8) as pool:
+        res = pool.map(_lr_run, jobs)
+    assert all(r["status"] == 0 for r in res)
+    q1 = np.array([r["q"] for r in res[:8]])
+    q2 = np.array([r["q"] for r in res[8:]])
+    m1, m2 = q1.mean(), q2.mean()
+    se1, se2 = q1.std(ddof=1) / math.sqrt(len(q1)), q2.std(ddof=1) / math.sqrt(len(q2))
+    ratio = m2 / m1
+    se_ratio = ratio * math.sqrt((se1 / m1) ** 2 + (se2 / m2) ** 2)
+    print("q(g) %.3f +- %.3f  q(2g) %.3f +- %.3f  ratio %.3f +- %.3f" % (m1, se1, m2, se2, ratio, se_ratio))
+    assert m1 > 2 * se1 and m2 > 2 * se2
+    assert abs(ratio - 2.0) < 2.0 * se_ratio

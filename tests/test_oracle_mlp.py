@@ -57,3 +57,24 @@ def test_training_fits_a_smooth_function():
     assert losses[-1] < 0.05 * losses[0]
     pred = mlp.predict(p, s, X)
     assert np.sqrt(np.mean((pred - y) ** 2)) < 0.25 * y.std()
+
+
+def test_adam_moment_recursions_by_hand():
+    # Steps 1-3 with beta1 = 0.5, beta2 = 0.75 and gradients 1, -2, 0.5, by
+    # hand (Kingma & Ba 2015: m_t = b1 m + (1 - b1) g, v_t = b2 v + (1 - b2) g^2,
+    # step -lr m_t / (1 - b1^t) / (sqrt(v_t / (1 - b2^t)) + eps)):
+    #   t = 1: m = 1/2,   v = 1/4,     m^ = 1,    v^ = 1
+    #   t = 2: m = -3/4,  v = 19/16,   m^ = -1,   v^ = (19/16) / (7/16) = 19/7
+    #   t = 3: m = -1/8,  v = 61/64,   m^ = -1/7, v^ = (61/64) / (37/64) = 61/37
+    lr, eps = 0.1, 1e-8
+    steps = [1.0 / (1.0 + eps), -1.0 / (math.sqrt(19.0 / 7.0) + eps), -1.0 / 7.0 / (math.sqrt(61.0 / 37.0) + eps)]
+    p = {k: np.ones(s) for k, s in mlp.SHAPES.items()}
+    m = {k: np.zeros(s) for k, s in mlp.SHAPES.items()}
+    v = {k: np.zeros(s) for k, s in mlp.SHAPES.items()}
+    expect = 1.0
+    for t, (g, st) in enumerate(zip((1.0, -2.0, 0.5), steps), start=1):
+        grads = {k: np.full(s, g) for k, s in mlp.SHAPES.items()}
+        mlp.adam_step(p, grads, m, v, t, lr=lr, b1=0.5, b2=0.75, eps=eps)
+        expect -= lr * st
+        for k in mlp.ORDER:
+            np.testing.assert_allclose(p[k], expect, rtol=1e-14)
