@@ -167,6 +167,9 @@ def main():
     ap.add_argument("--sample-steps", type=int, default=300,
                     help="oracle steps per sampled element in the reference arm")
     ap.add_argument("--no-gp-mlp", action="store_true", help="skip the GP and MLP timings")
+    ap.add_argument("--persistent", type=int, default=None, choices=[0, 1, 2],
+                    help="step loop: 0 one launch per step, 1 persistent kernel in a graph WHILE loop, 2 the "
+                         "persistent kernel launched by the host (profilers capture it)")
     ap.add_argument("--workload", default="uneven", choices=["uneven", "stress"],
                     help="uneven: 64 elements, 500-5000 fluid atoms, 20000 steps (default); stress: 4096 "
                          "elements, 2k-32k fluid atoms, 60 M atoms, 10000 steps")
@@ -207,7 +210,10 @@ def main():
     from paper_1603_04628_gb300 import native
 
     stream = torch.cuda.Stream()
-    ctx = native.Context(local, native.PREC_FP32, stream=stream)
+    path_kw = {}
+    if args.persistent is not None:
+        path_kw["persistent"] = args.persistent
+    ctx = native.Context(local, native.PREC_FP32, stream=stream, **path_kw)
     n_atoms = ctx.micro_plan(els)
     units = n_atoms * steps_el
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -220,7 +226,7 @@ def main():
         if not any(r["status"] == -8 for r in ctx.micro_results()):
             break
         cap = int(cap * 1.5) // 8 * 8
-        ctx.set_md_params(list_capacity=cap)
+        ctx.set_md_params(list_capacity=cap, **path_kw)
         n_atoms = ctx.micro_plan(els)
     for _ in range(args.warmup):
         ctx.micro_launch()

@@ -46,7 +46,9 @@ typedef enum {
 
 typedef enum {
   MDGP_PREC_FP64 = 0,    /* FP64 pair forces and FP64 state */
-  MDGP_PREC_FP32 = 1     /* FP32 pair forces, FP64 positions, velocities and accumulators */
+  MDGP_PREC_FP32 = 1     /* FP32 pair forces; positions, velocities and tether anchors as
+                            double-float pairs (two FP32 words, hi + lo, about 44 significant
+                            bits: ~1e-13 sigma on a cell-relative offset); FP64 accumulators */
 } mdgp_precision;
 
 typedef struct mdgp_ctx mdgp_ctx;
@@ -82,8 +84,9 @@ typedef struct {
   double T_meas;   /* mean fluid kinetic temperature m <|v|^2> / 3 over the samples */
   double e_drift;  /* (E_end - E_start) / N_atoms, E = kinetic + LJ (shifted) + tether */
   int64_t n_fluid, n_wall;
-  int32_t status;  /* MDGP_OK, or MDGP_E_UNSTABLE / _OVERFLOW / _SKIN for this element */
-  int32_t reserved;
+  int32_t status;  /* MDGP_OK, or MDGP_E_UNSTABLE / _OVERFLOW / _SKIN / _TIMEOUT for this element */
+  int32_t start;   /* how the run started: 0 the lattice (cold), 1 the fluid of a snapshot, 2 the
+                      fluid and walls of a snapshot (mdgp_micro_plan_from) */
 } mdgp_result;
 
 /* Physics constants shared by all elements of a context. */
@@ -109,18 +112,25 @@ typedef struct {
   double skin;          /* Verlet-list skin beyond r_c (default 0.4) */
   int32_t rebuild_every;/* eager paths (mdgp_micro_profile): steps between list rebuilds; 0 = from
                            the skin and T.  Graph replays rebuild when an atom has moved skin/2. */
-  int32_t build_variant;/* list build: 0 = cell columns staged in shared memory by bulk async
-                           copies, 1 = direct reads of global memory (lanes over a cell's
-                           atoms), 2 = warp ballots over bounding-box-culled candidates
-                           (lanes over candidates, one warp per cell), 3 = the ballot
-                           build with one block of four warps per cell (same lists as 2,
-                           entry for entry; default).  All give each atom the same set of
-                           neighbours within r_c + skin. */
+  int32_t build_variant;/* list build: 0 or 3, the block-ballot build (one block of four warps
+                           per cell, candidates culled to the cell's bounding box and then
+                           its octants, lanes over candidates) -- the only one kept */
   int32_t persistent;   /* FP32 pair forces: 1 = the step loop is one persistent cooperative
                            kernel per list-rebuild interval (steps separated by a grid barrier,
                            inside a graph WHILE loop; default), 0 = one launch per step with a
-                           conditional rebuild after each.  FP64 pair forces always use the
-                           latter.  Same results either way. */
+                           conditional rebuild after each, 2 = the persistent
+                           kernel launched by the host once per rebuild interval, without a
+                           graph (a host round trip per interval: for profilers, which capture
+                           ordinary launches).  FP64 pair forces always use 0.  Same results
+                           every way. */
+  int32_t wait_timeout_ms;  /* limit of every bounded device-side wait (the persistent step
+                           loop's grid barrier), in milliseconds of the GPU's global timer
+                           (default 2000; <= 0 takes the default).  A wait that runs out
+                           ends the run and marks every element MDGP_E_TIMEOUT. */
+  int32_t inject_barrier_skip;  /* test only (default 0): 1 makes one block of the persistent
+                           step kernel leave out its first grid-barrier arrival, so that the
+                           other blocks' bounded waits run out; the launch then ends with
+                           MDGP_E_TIMEOUT for every element and the context stays usable. */
 } mdgp_md_params;
 
 /* Fill *out with the defaults listed above.  Returns MDGP_E_ARG on null. */
@@ -154,6 +164,35 @@ int mdgp_micro_batch(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, mdgp_resu
  * share steps_eq + steps_sample (MDGP_E_ARG otherwise). */
 int mdgp_micro_plan(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int64_t* n_atoms);
 
+/* Start state of one element: the final snapshot of an earlier run (paper
+ * Sec. 2.4 and Algorithm 1: a new MD run starts from the final state of the
+ * database entry most correlated with it, a cold run from a lattice with
+ * zero mean velocity).  xv holds n_fluid + n_wall rows of
+ * (x, y, z, vx, vy, vz), fluid first, then walls -- the order and the
+ * absolute positions mdgp_micro_state gives; h, Lx, Lz are the geometry the
+ * snapshot was taken in.  xv = null asks for a cold start. */
+typedef struct {
+  const float* xv;
+  int64_t n_fluid, n_wall;
+  double h, Lx, Lz;
+} mdgp_start;
+
+/* mdgp_micro_plan with start states (starts may be null: all cold; copied
+ * during the call).  A snapshot whose Lx or Lz differ from the element's
+ * gives a cold start.  Otherwise the element's fluid starts from the
+ * snapshot's: y scaled by h / h_snapshot (the wall planes stay at 0 and h),
+ * x and z kept; surplus atoms are removed (those with the smallest Philox
+ * key, counter (atom, 0, element id, 2)), missing atoms are inserted at
+ * Philox-drawn sites (counter (k, try, element id, 3)) of the slab
+ * [0.6, h - 0.6] at least 0.85 from every atom, with Maxwell-Boltzmann
+ * velocities at T (counter (atom, 0, element id, 4)) plus the snapshot's
+ * mean fluid velocity; a site not found within 20000 tries gives a cold
+ * start.  When h and the wall atom count also match, the walls start from
+ * the snapshot too.  The tether anchors are the lattice sites either way.
+ * mdgp_result.start reports what was used. */
+int mdgp_micro_plan_from(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, const mdgp_start* starts,
+                         int64_t* n_atoms);
+
 /* Enqueue the planned batch on the context's stream: build the elements,
  * replay the step graph, reduce the results on the device.  Asynchronous;
  * MDGP_E_STATE without a plan. */
@@ -166,6 +205,11 @@ int mdgp_micro_results(mdgp_ctx* ctx, mdgp_result* out, int64_t n);
  * one, including the neighbour-list rebuilds that ran); valid after
  * mdgp_micro_results. */
 int64_t mdgp_micro_launch_count(const mdgp_ctx* ctx);
+
+/* Which step loop the planned batch runs: 0 one launch per step (per-step
+ * graphs), 1 the persistent kernel in a graph WHILE loop, 2 the persistent
+ * kernel launched by the host.  MDGP_E_STATE without a plan. */
+int mdgp_micro_path(const mdgp_ctx* ctx);
 
 /* Number of neighbour-list rebuilds the last batch ran (valid after
  * mdgp_micro_results).  A rebuild runs when some atom has moved more than
@@ -216,6 +260,13 @@ typedef struct {
   const double* fixed_scales; /* D scales to use instead of the database's mean separations, or null */
   const double* fallback_scales; /* D per-dimension fallbacks (entries <= 0 take fallback_scale),
                                     or null; copied during the call */
+  double period;           /* 0: the squared-exponential kernel (Eq. quadraticKernelEq) on the scaled
+                              inputs of Eq. d2Eq.  > 0: the periodic kernel of App. B
+                              (Eq. periodicKernel), sf2 exp(-2 sin^2(pi |t - t'| / period) / l2),
+                              on one input (D = 1, time) with no scaling; fixed_scales must be null */
+  int32_t hold;            /* mdgp_gp_optimize only: bit mask of hyperparameters kept at their start
+                              values (1 sf2, 2 l2, 4 sn2; App. B keeps sf2) */
+  int32_t reserved;
 } mdgp_gp_params;
 
 /* Fit a GP to M database entries (Eqs. quadraticKernelEq, d2Eq,
@@ -268,7 +319,7 @@ int mdgp_gp_predict(mdgp_gp* gp, const double* Xs, int64_t m, const double* mu_X
  * calls no allocator.
  *   X (M x D), y (M), mu_X (M, nullable), Xs (m x D), mu_Xs (m, nullable)
  *   and the outputs mean (m), var (m) are DEVICE pointers on the current
- *   device; params as for mdgp_gp_fit (fixed_scales must be null); stream is
+ *   device; params as for mdgp_gp_fit (fixed_scales must be null, period 0); stream is
  *   a cudaStream_t (0 = legacy default stream).
  *   Limits: 1 <= M <= 512 (MDGP_E_LIMIT beyond), 1 <= D <= 8.
  *   The first call on a device looks up the array's device address once
@@ -282,7 +333,8 @@ int mdgp_gp_posterior_noalloc(const double* X, const double* y, int64_t M, int32
                               const mdgp_gp_params* params, const double* mu_X, const double* Xs, int64_t m,
                               const double* mu_Xs, double* mean, double* var, void* stream);
 
-/* The D input scales the fit used (Eq. d2Eq denominators). */
+/* The D input scales the fit used (Eq. d2Eq denominators); the period for
+ * the periodic kernel. */
 int mdgp_gp_scales(const mdgp_gp* gp, double* scales);
 
 /* Log marginal likelihood of the fitted data (Eq. evidenceEq, Sec. 2.3):
@@ -291,7 +343,8 @@ int mdgp_gp_scales(const mdgp_gp* gp, double* scales);
 int mdgp_gp_log_marginal(const mdgp_gp* gp, double* lml);
 
 /* Hyperparameters by maximum evidence (Sec. 2.3): a pattern search over
- * (sf2, l2, sn2) from *start (its fallback and fixed scales are kept):
+ * (sf2, l2, sn2) from *start (its fallback and fixed scales, its kernel and
+ * the values start->hold names are kept):
  * each coordinate in turn tries value x step and value / step and keeps the
  * better evidence (a gain above 1e-9 relative); a pass without a move takes
  * the square root of the step, from 4 down to 1.05, or until max_evals fits.
@@ -449,8 +502,7 @@ int mdgp_mlp_set(mdgp_mlp* m, const float* params, const double* standardiser);
 /* Use the network as the hybrid's GP prior mean (null: zero mean again). */
 int mdgp_hybrid_set_mlp_mean(mdgp_hybrid* h, mdgp_mlp* m);
 
-/* Choose the neighbour-list skin (0.3-0.6) and the list-build variant for
- * this batch by timing: each candidate runs the batch for probe_steps steps
+/* Choose the neighbour-list skin (0.3-0.6) for this batch by timing: each candidate runs the batch for probe_steps steps
  * (after one warm-up run) with CUDA events on the context's stream; the
  * fastest is kept in the context (and copied to *best, its atom-steps/s to
  * *best_rate; either may be null).  Results do not depend on the choice

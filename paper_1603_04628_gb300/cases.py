@@ -98,6 +98,24 @@ def channel_sweep(ctx, thresholds, n_steps=100, seed_noise=None, pressure_db=Non
     return out
 
 
+def periodic_filter(ctx, t, q, period, sf2=1.0, l2=1.0, sn2=0.01, fit_until=None, max_evals=200):
+    """App. B: filter the noise out of a periodic flow-rate time series q(t)
+    with a GP on time alone and the periodic kernel of Eq. periodicKernel.
+    The length scale and the noise variance maximise the log marginal
+    likelihood (Sec. 2.3, Eq. evidenceEq) of the samples up to fit_until (the
+    paper fits up to the first peak) with sf2 held; then the regression
+    (Eqs. predMeanEq, predVarEq, zero prior mean) runs over the whole series.
+    Returns (mean, var, l2, sn2)."""
+    t = np.asarray(t, dtype=np.float64).reshape(-1, 1)
+    q = np.asarray(q, dtype=np.float64)
+    sel = np.ones(len(q), bool) if fit_until is None else t[:, 0] <= fit_until
+    best = native.gp_optimize(ctx, t[sel], q[sel], sf2, l2, sn2, max_evals=max_evals, period=period, hold=1)
+    g = native.GP(ctx, t, q, sf2, best["l2"], best["sn2"], period=period)
+    mean, var = g.predict(t)
+    g.close()
+    return mean, var, best["l2"], best["sn2"]
+
+
 def md_database(ctx, n_elements, seed, h_range=(6.0, 18.0), G_range=(-0.06, 0.06), density=0.8, T=1.1,
                 steps_eq=1000, steps_sample=2000, Lx=10.0, Lz=10.0):
     """A training database from the library's MD: elements drawn uniformly over

@@ -97,8 +97,16 @@ __global__ void k_gp_scales(const double* rows, double* scale, int M, int D, Fal
   }
 }
 
+// The covariance function.  Squared exponential (Eq. quadraticKernelEq) on
+// the inputs scaled by Eq. d2Eq, or, when the first scale is negative, the
+// periodic kernel of App. B (Eq. periodicKernel) on one input with period
+// -scale[0]: sf2 exp(-2 sin^2(pi |t - t'| / T) / l2).
 __device__ __forceinline__ double se_kernel(const double* a, const double* b, const double* scale, int D,
                                             double sf2, double l2) {
+  if (scale[0] < 0.0) {
+    const double sn = sinpi(fabs(a[0] - b[0]) / -scale[0]);
+    return sf2 * exp(-2.0 * sn * sn / l2);
+  }
   double d2 = 0.0;
   for (int k = 0; k < D; ++k) {
     const double t = (a[k] - b[k]) / scale[k];
@@ -487,6 +495,7 @@ struct mdgp_gp {
   cudaStream_t stream = nullptr;
   int M = 0, Mp = 0, D = 0;
   double sf2 = 1, l2 = 1, sn2 = 0;
+  double period = 0;   // > 0: the periodic kernel of App. B
   double *dX = nullptr, *dL = nullptr, *dalpha = nullptr, *dscale = nullptr;
   double* dwork = nullptr;   // 2 Mp: right-hand side and forward solution of the alpha solve
   double *dq = nullptr, *dmu = nullptr, *dmean = nullptr, *dvar = nullptr;
@@ -586,15 +595,33 @@ static int gp_fit_impl(mdgp_gp* g, const double* X, const double* y, const doubl
   // the scales, then (y - mu)^T alpha and sum log L_ii for the evidence
   GK(cudaMalloc(&g->dscale, sizeof(double) * (kMaxD + 2)));
   GK(cudaMemsetAsync(g->dscale, 0, sizeof(double) * (kMaxD + 2), s));
+  // the periodic kernel takes no scales: its first scale carries -period
+  const double neg_period = -p->period;
+  const double* fixed = p->period > 0.0 ? &neg_period : p->fixed_scales;
   if (M == 0) {
     const Fallback f = make_fallback(p, D);
     std::vector<double> fb(f.v, f.v + D);
+    if (p->period > 0.0) fb[0] = neg_period;
     GK(cudaMemcpyAsync(g->dscale, fb.data(), sizeof(double) * D, cudaMemcpyHostToDevice, s));
     GK(cudaStreamSynchronize(s));
     return MDGP_OK;
   }
-  double *dy = nullptr, *dmuX = nullptr, *dfixed = nullptr;
-  int* dstatus = nullptr;
+  // the fit's own scratch, freed on every way out (error returns included;
+  // cudaFree waits for the work still queued on it)
+  struct Scratch {
+    double *dy = nullptr, *dmuX = nullptr, *dfixed = nullptr;
+    int* dstatus = nullptr;
+    ~Scratch() {
+      if (dy) cudaFree(dy);
+      if (dstatus) cudaFree(dstatus);
+      if (dmuX) cudaFree(dmuX);
+      if (dfixed) cudaFree(dfixed);
+    }
+  } sc;
+  double*& dy = sc.dy;
+  double*& dmuX = sc.dmuX;
+  double*& dfixed = sc.dfixed;
+  int*& dstatus = sc.dstatus;
   GK(cudaMalloc(&g->dX, sizeof(double) * M * D));
   GK(cudaMalloc(&g->dL, sizeof(double) * (size_t)Mp * Mp));
   GK(cudaMalloc(&g->dalpha, sizeof(double) * Mp));
@@ -608,14 +635,14 @@ static int gp_fit_impl(mdgp_gp* g, const double* X, const double* y, const doubl
     GK(cudaMalloc(&dmuX, sizeof(double) * M));
     GK(cudaMemcpyAsync(dmuX, mu_X, sizeof(double) * M, cudaMemcpyHostToDevice, s));
   }
-  if (p->fixed_scales) {
+  if (fixed) {
     GK(cudaMalloc(&dfixed, sizeof(double) * D));
-    GK(cudaMemcpyAsync(dfixed, p->fixed_scales, sizeof(double) * D, cudaMemcpyHostToDevice, s));
+    GK(cudaMemcpyAsync(dfixed, fixed, sizeof(double) * D, cudaMemcpyHostToDevice, s));
   }
   const Fallback fallback = make_fallback(p, D);
   // the pair-separation row sums (M x D) use the factor's storage before
   // the covariance fills it
-  if (!p->fixed_scales) {
+  if (!fixed) {
     k_gp_pairsep<<<M, 128, 0, s>>>(g->dX, M, D, g->dL);
     g->launches++;
   }
@@ -646,10 +673,6 @@ static int gp_fit_impl(mdgp_gp* g, const double* X, const double* y, const doubl
   GK(cudaGetLastError());
   GK(cudaMemcpyAsync(&status, dstatus, sizeof(int), cudaMemcpyDeviceToHost, s));
   GK(cudaStreamSynchronize(s));
-  cudaFree(dy);
-  cudaFree(dstatus);
-  if (dmuX) cudaFree(dmuX);
-  if (dfixed) cudaFree(dfixed);
   return status ? status : MDGP_OK;
 }
 
@@ -660,6 +683,7 @@ static int gp_fit_entry(mdgp_ctx* ctx, const double* X, const double* y, int64_t
   if (!ctx || !params || !out || M < 0 || M > kMaxM || D < 1 || D > kMaxD) return MDGP_E_ARG;
   if (M > 0 && (!X || (with_alpha && !y))) return MDGP_E_ARG;
   if (!(params->sf2 > 0) || !(params->l2 > 0) || !(params->sn2 >= 0)) return MDGP_E_ARG;
+  if (!(params->period >= 0) || (params->period > 0 && (D != 1 || params->fixed_scales))) return MDGP_E_ARG;
   *out = nullptr;
   cudaSetDevice(ctx->device);
   mdgp_gp* g = new (std::nothrow) mdgp_gp();
@@ -672,6 +696,7 @@ static int gp_fit_entry(mdgp_ctx* ctx, const double* X, const double* y, int64_t
   g->sf2 = params->sf2;
   g->l2 = params->l2;
   g->sn2 = params->sn2;
+  g->period = params->period;
   g->has_alpha = with_alpha;
   for (int k = 0; k < 2; ++k) g->fs[k] = ctx->fact_stream[k];
   for (int k = 0; k < 4; ++k) g->fe[k] = ctx->fact_event[k];
@@ -790,6 +815,7 @@ int mdgp_gp_optimize(mdgp_ctx* ctx, const double* X, const double* y, int64_t M,
   while (step > 1.05 && evals < max_evals) {
     bool moved = false;
     for (int k = 0; k < 3 && evals < max_evals; ++k) {
+      if (start->hold & (1 << k)) continue;
       double* v = k == 0 ? &cur.sf2 : (k == 1 ? &cur.l2 : &cur.sn2);
       const double v0 = *v;
       double bestv = v0, bestf = f;
@@ -816,6 +842,7 @@ int mdgp_gp_scales(const mdgp_gp* g, double* scales) {
   cudaSetDevice(g->device);
   if (cudaMemcpy(scales, g->dscale, sizeof(double) * g->D, cudaMemcpyDeviceToHost) != cudaSuccess)
     return MDGP_E_CUDA;
+  if (g->period > 0.0) scales[0] = g->period;   // the periodic kernel: its period
   return MDGP_OK;
 }
 
@@ -878,7 +905,8 @@ extern "C" int mdgp_gp_posterior_noalloc(const double* X, const double* y, int64
   if (!params || M < 1 || D < 1 || D > kMaxD || m < 0 || !X || !y || (m > 0 && (!Xs || !mean || !var)))
     return MDGP_E_ARG;
   if (M > kNoAllocMaxM) return MDGP_E_LIMIT;  // the scratch array holds at most 512 entries
-  if (!(params->sf2 > 0) || !(params->l2 > 0) || !(params->sn2 >= 0) || params->fixed_scales) return MDGP_E_ARG;
+  if (!(params->sf2 > 0) || !(params->l2 > 0) || !(params->sn2 >= 0) || params->fixed_scales || params->period != 0.0)
+    return MDGP_E_ARG;
   int device = 0;
   if (cudaGetDevice(&device) != cudaSuccess) return MDGP_E_CUDA;
   double* base = nullptr;

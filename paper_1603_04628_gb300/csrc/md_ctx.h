@@ -30,24 +30,24 @@ struct mdgp_ctx {
   long long n_el = 0, steps = 0, n_atoms = 0;
   long long chunk = 256;  // steps per captured graph (rounded to the rebuild interval)
   long long rebuild_every = 1;
-  long long n_columns = 0;  // (x, y) cell columns over the batch
-  int stage_bytes = 0;      // dynamic shared memory of the staged list build
   long long graph_K = 0, graph_rem_K = 0;
   cudaGraphExec_t graph_full = nullptr, graph_rem = nullptr;
   cudaGraphExec_t graph_while = nullptr;  // persistent step loop (FP32 pair forces)
   unsigned persist_grid = 0;              // co-resident blocks of the persistent step kernel
   int persist_threads = 128;              // its block size
   int persist_atoms = 128;                // atoms per block (<= persist_threads)
+  bool direct = false;        // persistent = 2: the host launches the persistent kernel itself
+  bool any_warm = false;      // some element of the plan starts from a snapshot
   long long launches = 0;              // kernels enqueued by the last launch (graph bodies: 2 per step)
   long long launches_with_rebuilds = 0;  // ... plus the rebuild kernels that ran
   long long rebuilds = 0;
   mdgp::BatchDev B;
   mdgp::PhysDev P;
-  DevBuf d_el, d_aoff, d_coff, d_koff, d_state, d_ints, d_cells, d_pos, d_pbuild, d_force, d_list, d_out, d_acc,
-      d_grp, d_status, d_results, d_step, d_flags, d_tz;
+  DevBuf d_el, d_aoff, d_coff, d_state, d_ints, d_cells, d_pos, d_pbuild, d_force, d_list, d_out, d_acc,
+      d_grp, d_status, d_results, d_step, d_flags, d_tz, d_warm;
   std::vector<DevBuf*> all_bufs() {
-    return {&d_el, &d_aoff, &d_coff, &d_koff, &d_state, &d_ints, &d_cells, &d_pos, &d_pbuild, &d_force, &d_list,
-            &d_out, &d_acc, &d_grp, &d_status, &d_results, &d_step, &d_flags, &d_tz};
+    return {&d_el, &d_aoff, &d_coff, &d_state, &d_ints, &d_cells, &d_pos, &d_pbuild, &d_force, &d_list,
+            &d_out, &d_acc, &d_grp, &d_status, &d_results, &d_step, &d_flags, &d_tz, &d_warm};
   }
   void release_extra() {}
 };

@@ -141,6 +141,8 @@ PhysDev make_phys(const mdgp_md_params& p, int list_cap) {
   P.wall_planes = p.wall_planes;
   P.tau_T = p.tau_T;
   P.list_cap = list_cap;
+  P.wait_ns = 1000000ull * (unsigned long long)(p.wait_timeout_ms > 0 ? p.wait_timeout_ms : 2000);
+  P.inject_skip = p.inject_barrier_skip != 0 ? 1 : 0;
   P.rc2f = (float)(p.rc * p.rc);
   P.rl2f = (float)P.rl2;
   P.half_skin2f = (float)(0.25 * p.skin * p.skin);
@@ -167,6 +169,183 @@ int rebuild_interval(const mdgp_md_params& p, double Tmax) {
   const double vmax = 8.0 * std::sqrt(Tmax / p.mass);
   int r = (int)std::floor(0.5 * p.skin / (vmax * p.dt));
   return r < 1 ? 1 : r;
+}
+
+// ---------------------------------------------------------------------------
+// Start states from snapshots (paper Sec. 2.4, Algorithm 1).
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11) on the host, the generator the device
+// uses: ten rounds of the two-multiply S-box, key advanced by the Weyl
+// increments between rounds.
+void philox_host(uint32_t c[4], uint32_t k0, uint32_t k1) {
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c[0], p1 = (uint64_t)0xCD9E8D57u * c[2];
+    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c[1] ^ k0, n2 = (uint32_t)(p0 >> 32) ^ c[3] ^ k1;
+    c[0] = n0; c[1] = (uint32_t)p1; c[2] = n2; c[3] = (uint32_t)p0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+
+void philox_draw(uint32_t a, uint32_t b, uint32_t elem, uint32_t stream, uint64_t seed, uint32_t out[4]) {
+  out[0] = a; out[1] = b; out[2] = elem; out[3] = stream;
+  philox_host(out, (uint32_t)seed, (uint32_t)(seed >> 32));
+}
+
+double u01(uint32_t r) { return ((double)r + 0.5) * (1.0 / 4294967296.0); }
+
+// Wall site w of element E (the lattice k_init_atoms builds), absolute.
+void wall_site(const ElemDev& E, int planes, long long w, double& px, double& py, double& pz) {
+  const long long per_plane = 2LL * E.wnx * E.wnz, per_wall = per_plane * planes;
+  const int wall = (int)(w / per_wall);
+  const long long r = w % per_wall;
+  const int k = (int)(r / per_plane);
+  const long long r2 = r % per_plane;
+  const long long i = r2 / (2LL * E.wnz), j = (r2 >> 1) % E.wnz;
+  const int t = (int)(r2 & 1);
+  double ox, oz;
+  if ((k & 1) == 0) { ox = t ? 0.5 : 0.0; oz = t ? 0.5 : 0.0; }
+  else { ox = t ? 0.0 : 0.5; oz = t ? 0.5 : 0.0; }
+  px = ((double)i + ox) * E.wax;
+  py = wall == 0 ? -(double)k * E.wdy : E.h + (double)k * E.wdy;
+  pz = ((double)j + oz) * E.waz;
+}
+
+// Uniform grid over the element (periodic in x and z) for the insertion's
+// distance test.
+struct SiteGrid {
+  double Lx, Lz, ylo, cs;
+  int nx, ny, nz;
+  std::vector<std::vector<int>> cell;
+  std::vector<double> pos;   // 3 per site
+  SiteGrid(double Lx_, double Lz_, double ylo_, double yhi, double side) : Lx(Lx_), Lz(Lz_), ylo(ylo_) {
+    nx = std::max(1, (int)std::floor(Lx / side));
+    nz = std::max(1, (int)std::floor(Lz / side));
+    ny = std::max(1, (int)std::floor((yhi - ylo) / side));
+    cs = side;
+    cell.resize((size_t)nx * ny * nz);
+  }
+  int index(double x, double y, double z, int& ix, int& iy, int& iz) const {
+    ix = std::min(nx - 1, std::max(0, (int)(x / Lx * nx)));
+    iz = std::min(nz - 1, std::max(0, (int)(z / Lz * nz)));
+    iy = std::min(ny - 1, std::max(0, (int)((y - ylo) / cs)));
+    return (ix * ny + iy) * nz + iz;
+  }
+  void add(double x, double y, double z) {
+    int ix, iy, iz;
+    cell[(size_t)index(x, y, z, ix, iy, iz)].push_back((int)(pos.size() / 3));
+    pos.push_back(x); pos.push_back(y); pos.push_back(z);
+  }
+  // true when no site lies within dmin of (x, y, z) (minimum image in x, z)
+  bool clear(double x, double y, double z, double dmin) const {
+    int ix, iy, iz;
+    index(x, y, z, ix, iy, iz);
+    const int rx = std::min(nx / 2, 1 + (int)(dmin / (Lx / nx))), rz = std::min(nz / 2, 1 + (int)(dmin / (Lz / nz)));
+    const int ry = 1 + (int)(dmin / cs);
+    for (int dx = -rx; dx <= rx; ++dx)
+      for (int dy = -ry; dy <= ry; ++dy) {
+        const int jy = iy + dy;
+        if (jy < 0 || jy >= ny) continue;
+        for (int dz = -rz; dz <= rz; ++dz) {
+          const int jx = ((ix + dx) % nx + nx) % nx, jz = ((iz + dz) % nz + nz) % nz;
+          for (int s : cell[(size_t)(jx * ny + jy) * nz + jz]) {
+            double ax = x - pos[3 * s], ay = y - pos[3 * s + 1], az = z - pos[3 * s + 2];
+            ax -= Lx * std::floor(ax / Lx + 0.5);
+            az -= Lz * std::floor(az / Lz + 0.5);
+            if (ax * ax + ay * ay + az * az < dmin * dmin) return false;
+          }
+        }
+      }
+    return true;
+  }
+};
+
+// The start state of element E from snapshot S, the rule mdgp_micro_plan_from
+// documents: xv gets (nf + nw) rows of (x y z vx vy vz); returns 0 for a cold
+// start, 1 when the fluid comes from the snapshot, 2 when the walls do too.
+int adapt_snapshot(const mdgp_md_params& p, const mdgp_element& el, const ElemDev& E, const mdgp_start& S,
+                   std::vector<double>& xv) {
+  if (!S.xv || S.n_fluid < 0 || S.n_wall < 0 || !(S.h > 0) || std::fabs(S.Lx - E.Lx) > 1e-9 ||
+      std::fabs(S.Lz - E.Lz) > 1e-9)
+    return 0;
+  const long long nf = E.nf, nw = E.nw, n_old = S.n_fluid;
+  xv.assign((size_t)6 * (nf + nw), 0.0);
+  // which snapshot fluid atoms stay: all, or all but the n_old - nf with the smallest keys
+  std::vector<long long> keep;
+  keep.reserve((size_t)n_old);
+  if (n_old > nf) {
+    std::vector<std::pair<uint32_t, long long>> key((size_t)n_old);
+    for (long long i = 0; i < n_old; ++i) {
+      uint32_t r[4];
+      philox_draw((uint32_t)i, 0u, (uint32_t)el.id, 2u, el.seed, r);
+      key[(size_t)i] = {r[0], i};
+    }
+    std::sort(key.begin(), key.end());
+    std::vector<char> gone((size_t)n_old, 0);
+    for (long long i = 0; i < n_old - nf; ++i) gone[(size_t)key[(size_t)i].second] = 1;
+    for (long long i = 0; i < n_old; ++i)
+      if (!gone[(size_t)i]) keep.push_back(i);
+  } else {
+    for (long long i = 0; i < n_old; ++i) keep.push_back(i);
+  }
+  const double sy = E.h / S.h;
+  double vm[3] = {0.0, 0.0, 0.0};
+  for (size_t k = 0; k < keep.size(); ++k) {
+    const float* r = S.xv + 6 * keep[k];
+    double* o = xv.data() + 6 * k;
+    o[0] = (double)r[0] - E.Lx * std::floor((double)r[0] / E.Lx);
+    o[1] = (double)r[1] * sy;
+    o[2] = (double)r[2] - E.Lz * std::floor((double)r[2] / E.Lz);
+    for (int d = 0; d < 3; ++d) { o[3 + d] = (double)r[3 + d]; vm[d] += (double)r[3 + d]; }
+  }
+  if (!keep.empty())
+    for (int d = 0; d < 3; ++d) vm[d] /= (double)keep.size();
+  const bool walls = std::fabs(E.h - S.h) < 1e-9 && S.n_wall == nw;
+  // walls: the snapshot's, or the lattice (their velocities then come from the cold start)
+  for (long long w = 0; w < nw; ++w) {
+    double* o = xv.data() + 6 * (nf + w);
+    if (walls) {
+      const float* r = S.xv + 6 * (n_old + w);
+      for (int d = 0; d < 6; ++d) o[d] = (double)r[d];
+      o[0] -= E.Lx * std::floor(o[0] / E.Lx);
+      o[2] -= E.Lz * std::floor(o[2] / E.Lz);
+    } else {
+      wall_site(E, p.wall_planes, w, o[0], o[1], o[2]);
+    }
+  }
+  // missing fluid atoms: Philox-drawn sites of the slab clear of every atom
+  const long long add = nf - (long long)keep.size();
+  if (add > 0) {
+    const double dmin = 0.85;
+    SiteGrid grid(E.Lx, E.Lz, E.ylo, E.h - E.ylo, 1.0);
+    for (size_t k = 0; k < keep.size(); ++k) grid.add(xv[6 * k], xv[6 * k + 1], xv[6 * k + 2]);
+    for (long long w = 0; w < nw; ++w) grid.add(xv[6 * (nf + w)], xv[6 * (nf + w) + 1], xv[6 * (nf + w) + 2]);
+    const double y0 = 0.6, y1 = E.h - 0.6;
+    if (!(y1 > y0)) return 0;
+    for (long long k = 0; k < add; ++k) {
+      bool placed = false;
+      for (uint32_t tr = 0; tr < 20000 && !placed; ++tr) {
+        uint32_t r[4];
+        philox_draw((uint32_t)k, tr, (uint32_t)el.id, 3u, el.seed, r);
+        const double x = u01(r[0]) * E.Lx, y = y0 + u01(r[1]) * (y1 - y0), z = u01(r[2]) * E.Lz;
+        if (!grid.clear(x, y, z, dmin)) continue;
+        const long long a = (long long)keep.size() + k;
+        double* o = xv.data() + 6 * a;
+        o[0] = x; o[1] = y; o[2] = z;
+        uint32_t g[4];
+        philox_draw((uint32_t)a, 0u, (uint32_t)el.id, 4u, el.seed, g);
+        const double two_pi = 6.283185307179586476925286766559;
+        const double rad1 = std::sqrt(-2.0 * std::log(u01(g[0]))), rad2 = std::sqrt(-2.0 * std::log(u01(g[2])));
+        const double n3[3] = {rad1 * std::cos(two_pi * u01(g[1])), rad1 * std::sin(two_pi * u01(g[1])),
+                              rad2 * std::cos(two_pi * u01(g[3]))};
+        for (int d = 0; d < 3; ++d) o[3 + d] = E.vsd * n3[d] + vm[d];
+        grid.add(x, y, z);
+        placed = true;
+      }
+      if (!placed) return 0;
+    }
+  }
+  return walls ? 2 : 1;
 }
 
 }  // namespace
@@ -202,36 +381,26 @@ static void enqueue_step_integrate(mdgp_ctx* ctx, int k, bool stage1, cudaGraphC
 }
 
 // Neighbour-list rebuild: bin, per-element scan, permute into cell order,
-// copy back, build the lists (5 kernels on `s`).
+// settle each cell's order while copying back, build the lists (5 kernels on
+// `s`).
 static void enqueue_rebuild(mdgp_ctx* ctx, cudaStream_t s) {
   const unsigned g = grid_for(ctx->B.n_atoms, 256);
-  if (ctx->precision == MDGP_PREC_FP32) k_bin<true><<<g, 256, 0, s>>>(ctx->B);
-  else k_bin<false><<<g, 256, 0, s>>>(ctx->B);
-  k_scan<<<(unsigned)ctx->n_el, 1024, 0, s>>>(ctx->B);
-  const unsigned gb = grid_for(ctx->B.n_cells * 32, 128);
-  const unsigned gc = (unsigned)ctx->n_columns;
-  const unsigned gw = grid_for(ctx->B.n_cells, kBallotWarps);
   const unsigned gk = grid_for(ctx->B.n_cells, 1);
-  const int variant = ctx->params.build_variant;
-  const size_t ballot_smem = (size_t)kBallotWarps * kBallotWarpBytes;
   if (ctx->precision == MDGP_PREC_FP32) {
+    k_bin<true><<<g, 256, 0, s>>>(ctx->B);
+    k_scan<<<(unsigned)ctx->n_el, 1024, 0, s>>>(ctx->B);
     k_permute<float4><<<g, 256, 0, s>>>(ctx->B);
-    k_copy_back<<<g, 256, 0, s>>>(ctx->B);
-    if (variant == 3) k_build_ballot_blk<<<gk, kBlkWarps * 32, kBlkSmem, s>>>(ctx->B, ctx->P);
-    else if (variant == 2) k_build_ballot<<<gw, kBallotWarps * 32, ballot_smem, s>>>(ctx->B, ctx->P);
-    else if (variant == 0) k_build_staged<float4><<<gc, 128, ctx->stage_bytes, s>>>(ctx->B, ctx->P, ctx->stage_bytes);
-    else k_build<float4><<<gb, 128, 0, s>>>(ctx->B, ctx->P);
+    k_settle<float4><<<g, 256, 0, s>>>(ctx->B);
   } else {
+    k_bin<false><<<g, 256, 0, s>>>(ctx->B);
+    k_scan<<<(unsigned)ctx->n_el, 1024, 0, s>>>(ctx->B);
     k_permute<Pos64><<<g, 256, 0, s>>>(ctx->B);
-    k_copy_back<<<g, 256, 0, s>>>(ctx->B);
-    if (variant == 3) k_build_ballot_blk<<<gk, kBlkWarps * 32, kBlkSmem, s>>>(ctx->B, ctx->P);
-    else if (variant == 2) k_build_ballot<<<gw, kBallotWarps * 32, ballot_smem, s>>>(ctx->B, ctx->P);
-    else if (variant == 0) k_build_staged<Pos64><<<gc, 128, ctx->stage_bytes, s>>>(ctx->B, ctx->P, ctx->stage_bytes);
-    else k_build<Pos64><<<gb, 128, 0, s>>>(ctx->B, ctx->P);
+    k_settle<Pos64><<<g, 256, 0, s>>>(ctx->B);
   }
+  k_build_ballot_blk<<<gk, kBlkWarps * 32, kBlkSmem, s>>>(ctx->B, ctx->P);
 }
 
-// kernels in one rebuild: bin, scan, permute, copy back, build
+// kernels in one rebuild: bin, scan, permute, settle, build
 static int rebuild_kernels(const mdgp_ctx*) { return 5; }
 
 static void enqueue_rebuild(mdgp_ctx* ctx) {
@@ -341,7 +510,7 @@ __global__ void k_finalize(BatchDev B, mdgp_result* out) {
   r.n_fluid = E.nf;
   r.n_wall = E.nw;
   r.status = B.status[e];
-  r.reserved = 0;
+  r.start = E.warm;
   out[e] = r;
 }
 
@@ -435,10 +604,10 @@ static int capture_while(mdgp_ctx* ctx, cudaGraphExec_t* out) {
   const bool uni = ctx->P.uniform != 0, frozen = ctx->params.mode == 1;
   const long long S = ctx->steps;
   const int A = ctx->persist_atoms;
-  if (uni && !frozen) e = cudaLaunchKernelEx(&cfg, k_steps_persist<true, false>, ctx->B, ctx->P, S, A, hr, hw);
-  else if (!uni && !frozen) e = cudaLaunchKernelEx(&cfg, k_steps_persist<false, false>, ctx->B, ctx->P, S, A, hr, hw);
-  else if (uni) e = cudaLaunchKernelEx(&cfg, k_steps_persist<true, true>, ctx->B, ctx->P, S, A, hr, hw);
-  else e = cudaLaunchKernelEx(&cfg, k_steps_persist<false, true>, ctx->B, ctx->P, S, A, hr, hw);
+  if (uni && !frozen) e = cudaLaunchKernelEx(&cfg, k_steps_persist<true, false>, ctx->B, ctx->P, S, A, hr, hw, 1);
+  else if (!uni && !frozen) e = cudaLaunchKernelEx(&cfg, k_steps_persist<false, false>, ctx->B, ctx->P, S, A, hr, hw, 1);
+  else if (uni) e = cudaLaunchKernelEx(&cfg, k_steps_persist<true, true>, ctx->B, ctx->P, S, A, hr, hw, 1);
+  else e = cudaLaunchKernelEx(&cfg, k_steps_persist<false, true>, ctx->B, ctx->P, S, A, hr, hw, 1);
   cudaStreamCaptureStatus cs;
   cudaGraph_t cg;
   const cudaGraphNode_t* deps = nullptr;
@@ -470,7 +639,8 @@ static int capture_while(mdgp_ctx* ctx, cudaGraphExec_t* out) {
   return set_err(ctx, e);
 }
 
-static int plan_impl(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int list_cap_override) {
+static int plan_impl(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int list_cap_override,
+                     const mdgp_start* starts = nullptr) {
   ctx->planned = false;
   drop_graphs(ctx);
   if (ctx->params.mode != 0 && ctx->params.mode != 1) {
@@ -482,7 +652,7 @@ static int plan_impl(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int list_
     return MDGP_E_ARG;
   }
   std::vector<ElemDev> Es((size_t)n);
-  std::vector<long long> aoff((size_t)n + 1), coff((size_t)n + 1), koff((size_t)n + 1);
+  std::vector<long long> aoff((size_t)n + 1), coff((size_t)n + 1);
   long long atoms = 0, cells = 0, columns = 0;
   const long long S = el[0].steps_eq + el[0].steps_sample;
   double Tmax = 0.0;
@@ -502,7 +672,6 @@ static int plan_impl(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int list_
     Es[i].cell0 = cells;
     aoff[i] = atoms;
     coff[i] = cells;
-    koff[i] = columns;
     columns += (long long)Es[i].nc[0] * Es[i].nc[1];
     atoms += (long long)Es[i].nf + Es[i].nw;
     cells += (long long)Es[i].nc[0] * Es[i].nc[1] * Es[i].nc[2];
@@ -513,7 +682,21 @@ static int plan_impl(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int list_
   }
   aoff[n] = atoms;
   coff[n] = cells;
-  koff[n] = columns;
+  // start states from snapshots, prepared on the host (copied to the device below)
+  std::vector<double> warm;
+  bool any_warm = false;
+  if (starts) {
+    for (int64_t i = 0; i < n; ++i) {
+      if (!starts[i].xv) continue;
+      std::vector<double> xv;
+      const int w = adapt_snapshot(ctx->params, el[i], Es[i], starts[i], xv);
+      Es[i].warm = w;
+      if (!w) continue;
+      if (!any_warm) warm.assign((size_t)6 * atoms, 0.0);
+      any_warm = true;
+      std::copy(xv.begin(), xv.end(), warm.begin() + 6 * Es[i].atom0);
+    }
+  }
   if (atoms >= (1LL << 31) - 1) {
     std::snprintf(ctx->err, sizeof(ctx->err), "batch too large (2^31 atoms max)");
     return MDGP_E_ARG;
@@ -528,7 +711,6 @@ static int plan_impl(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int list_
   if ((st = ensure(ctx, ctx->d_el, sizeof(ElemDev) * n))) return st;
   if ((st = ensure(ctx, ctx->d_aoff, sizeof(long long) * (n + 1)))) return st;
   if ((st = ensure(ctx, ctx->d_coff, sizeof(long long) * (n + 1)))) return st;
-  if ((st = ensure(ctx, ctx->d_koff, sizeof(long long) * (n + 1)))) return st;
   if ((st = ensure(ctx, ctx->d_state, sizeof(double) * 18 * N))) return st;
   if ((st = ensure(ctx, ctx->d_ints, sizeof(int) * 8 * N))) return st;
   if ((st = ensure(ctx, ctx->d_cells, sizeof(int) * 4 * C))) return st;
@@ -545,17 +727,19 @@ static int plan_impl(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int list_
   if ((st = ensure(ctx, ctx->d_step, sizeof(long long)))) return st;
   if ((st = ensure(ctx, ctx->d_flags, sizeof(int) * kFlags))) return st;
   if ((st = ensure(ctx, ctx->d_tz, sizeof(double) * 2 * n))) return st;
+  if (any_warm && (st = ensure(ctx, ctx->d_warm, sizeof(double) * 6 * N))) return st;
   CK(cudaMemcpyAsync(ctx->d_el.ptr, Es.data(), sizeof(ElemDev) * n, cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(ctx->d_aoff.ptr, aoff.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(ctx->d_coff.ptr, coff.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, ctx->stream));
-  CK(cudaMemcpyAsync(ctx->d_koff.ptr, koff.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, ctx->stream));
+  if (any_warm)
+    CK(cudaMemcpyAsync(ctx->d_warm.ptr, warm.data(), sizeof(double) * 6 * N, cudaMemcpyHostToDevice, ctx->stream));
+  ctx->any_warm = any_warm;
 
   BatchDev& B = ctx->B;
   std::memset(&B, 0, sizeof(B));
   B.el = (const ElemDev*)ctx->d_el.ptr;
   B.atom_off = (const long long*)ctx->d_aoff.ptr;
   B.cell_off = (const long long*)ctx->d_coff.ptr;
-  B.col_off = (const long long*)ctx->d_koff.ptr;
   B.n_el = (int)n;
   B.list_cap = list_cap;
   B.n_atoms = atoms;
@@ -581,14 +765,8 @@ static int plan_impl(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int list_
   B.step_base = (long long*)ctx->d_step.ptr;
   B.flags = (int*)ctx->d_flags.ptr;
   B.tz = (double*)ctx->d_tz.ptr;
+  B.warm = any_warm ? (const double*)ctx->d_warm.ptr : nullptr;
   ctx->P = make_phys(ctx->params, list_cap);
-  ctx->n_columns = columns;
-  // staging buffer of the column build: 64 KB (FP32) / 112 KB (FP64) of positions
-  ctx->stage_bytes = ctx->precision == MDGP_PREC_FP32 ? 64 * 1024 : 112 * 1024;
-  if (ctx->precision == MDGP_PREC_FP32)
-    CK(cudaFuncSetAttribute(k_build_staged<float4>, cudaFuncAttributeMaxDynamicSharedMemorySize, ctx->stage_bytes));
-  else
-    CK(cudaFuncSetAttribute(k_build_staged<Pos64>, cudaFuncAttributeMaxDynamicSharedMemorySize, ctx->stage_bytes));
   ctx->n_el = n;
   ctx->steps = S;
   ctx->n_atoms = atoms;
@@ -603,6 +781,7 @@ static int plan_impl(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int list_
   // otherwise chunks of K steps with one conditional rebuild per step.
   const long long K = ctx->chunk;
   bool use_while = false;
+  ctx->direct = S > 0 && ctx->precision == MDGP_PREC_FP32 && ctx->params.persistent == 2;
   if (S > 0 && ctx->precision == MDGP_PREC_FP32 && ctx->params.persistent) {
     // Persistent grid: R co-resident blocks per SM, each taking A = N / (R x
     // SMs) atoms rounded up, so that every SM holds about N / SMs atoms (the
@@ -646,7 +825,8 @@ static int plan_impl(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int list_
       ctx->persist_grid = (unsigned)(chunks < cap ? chunks : cap);
     }
     const long long saved = ctx->launches;
-    if (ctx->persist_grid > 0 && capture_while(ctx, &ctx->graph_while) == MDGP_OK) use_while = true;
+    if (ctx->direct) use_while = true;   // no graphs: run_direct launches the persistent kernel itself
+    else if (ctx->persist_grid > 0 && capture_while(ctx, &ctx->graph_while) == MDGP_OK) use_while = true;
     else cudaGetLastError();   // fall back to the per-step graphs
     ctx->launches = saved;
   }
@@ -689,14 +869,60 @@ static int start_batch(mdgp_ctx* ctx) {
   CK(cudaMemsetAsync(ctx->B.flags, 0, sizeof(int) * kFlags, ctx->stream));
   CK(cudaMemsetAsync(ctx->B.tz, 0, sizeof(double) * 2 * n, ctx->stream));
   const unsigned ga = grid_for(ctx->B.n_atoms, 256);
+  const unsigned ge = (unsigned)ctx->n_el;
   if (ctx->precision == MDGP_PREC_FP32) {
     k_init_atoms<true><<<ga, 256, 0, ctx->stream>>>(ctx->B, ctx->P);
+    k_group_sums<true><<<ge, 256, 0, ctx->stream>>>(ctx->B);
     k_init_fix<true><<<ga, 256, 0, ctx->stream>>>(ctx->B, ctx->P);
+    if (ctx->any_warm) k_apply_warm<true><<<ga, 256, 0, ctx->stream>>>(ctx->B);
   } else {
     k_init_atoms<false><<<ga, 256, 0, ctx->stream>>>(ctx->B, ctx->P);
+    k_group_sums<false><<<ge, 256, 0, ctx->stream>>>(ctx->B);
     k_init_fix<false><<<ga, 256, 0, ctx->stream>>>(ctx->B, ctx->P);
+    if (ctx->any_warm) k_apply_warm<false><<<ga, 256, 0, ctx->stream>>>(ctx->B);
   }
-  ctx->launches += 2;
+  ctx->launches += ctx->any_warm ? 4 : 3;
+  return MDGP_OK;
+}
+
+// Persistent step loop launched from the host (persistent = 2): one
+// cooperative launch per list-rebuild interval, no graph.  After each
+// launch the host reads the step counter back; short of the last step, the
+// kernel stopped for a rebuild (or gave up a barrier wait, which flags
+// record), and the host enqueues the rebuild and launches again.  Slower
+// than the WHILE graph (a host round trip per interval) but every launch is
+// an ordinary kernel launch, which a profiler can capture.
+static int run_direct(mdgp_ctx* ctx) {
+  const long long S = ctx->steps;
+  const bool uni = ctx->P.uniform != 0, frozen = ctx->params.mode == 1;
+  const int A = ctx->persist_atoms;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ctx->persist_grid);
+  cfg.blockDim = dim3(ctx->persist_threads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = ctx->stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const cudaGraphConditionalHandle h0 = 0;
+  for (long long guard = 0; guard <= S; ++guard) {
+    cudaError_t e;
+    if (uni && !frozen) e = cudaLaunchKernelEx(&cfg, k_steps_persist<true, false>, ctx->B, ctx->P, S, A, h0, h0, 0);
+    else if (!uni && !frozen) e = cudaLaunchKernelEx(&cfg, k_steps_persist<false, false>, ctx->B, ctx->P, S, A, h0, h0, 0);
+    else if (uni) e = cudaLaunchKernelEx(&cfg, k_steps_persist<true, true>, ctx->B, ctx->P, S, A, h0, h0, 0);
+    else e = cudaLaunchKernelEx(&cfg, k_steps_persist<false, true>, ctx->B, ctx->P, S, A, h0, h0, 0);
+    if (e != cudaSuccess) return set_err(ctx, e);
+    ++ctx->launches;
+    long long step = 0;
+    int failed = 0;
+    CK(cudaMemcpyAsync(&step, ctx->d_step.ptr, sizeof(long long), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(&failed, ctx->B.flags + kFlagExit, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (step >= S || failed) break;
+    enqueue_rebuild(ctx);
+  }
   return MDGP_OK;
 }
 
@@ -710,7 +936,9 @@ static int launch_impl(mdgp_ctx* ctx) {
   enqueue_energy(ctx, kAccE0);
   const long long S = ctx->steps;
   if (S > 0) {
-    if (ctx->graph_while) {
+    if (ctx->direct) {
+      if ((st = run_direct(ctx))) return st;
+    } else if (ctx->graph_while) {
       CK(cudaGraphLaunch(ctx->graph_while, ctx->stream));   // persistent launches counted on the device
     }
     if (ctx->graph_K > 0) {
@@ -785,6 +1013,8 @@ int mdgp_md_params_default(mdgp_md_params* out) {
   out->rebuild_every = 0;
   out->build_variant = 3;
   out->persistent = 1;
+  out->wait_timeout_ms = 2000;
+  out->inject_barrier_skip = 0;
   return MDGP_OK;
 }
 
@@ -835,7 +1065,8 @@ int mdgp_set_md_params(mdgp_ctx* ctx, const mdgp_md_params* p) {
   if (!ctx || !p) return MDGP_E_ARG;
   if (!(p->dt > 0) || !(p->rc > 0) || p->n_blocks < 1 || p->wall_planes < 1 || !(p->mass > 0) ||
       !(p->wall_density > 0) || p->gamma_wall < 0 || p->list_capacity < 0 || !(p->skin >= 0) ||
-      p->rebuild_every < 0 || p->build_variant < 0 || p->build_variant > 3 || p->persistent < 0 || p->persistent > 1)
+      p->rebuild_every < 0 || (p->build_variant != 0 && p->build_variant != 3) || p->persistent < 0 ||
+      p->persistent > 2)
     return MDGP_E_ARG;
   ctx->params = *p;
   ctx->planned = false;
@@ -857,6 +1088,15 @@ int mdgp_micro_plan(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int64_t* n
   return st;
 }
 
+int mdgp_micro_plan_from(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, const mdgp_start* starts,
+                         int64_t* n_atoms) {
+  if (!ctx || !el || n < 1) return MDGP_E_ARG;
+  cudaSetDevice(ctx->device);
+  int st = plan_impl(ctx, el, n, 0, starts);
+  if (st == MDGP_OK && n_atoms) *n_atoms = ctx->n_atoms;
+  return st;
+}
+
 int mdgp_micro_launch(mdgp_ctx* ctx) {
   if (!ctx) return MDGP_E_ARG;
   cudaSetDevice(ctx->device);
@@ -870,6 +1110,12 @@ int mdgp_micro_results(mdgp_ctx* ctx, mdgp_result* out, int64_t n) {
 }
 
 int64_t mdgp_micro_launch_count(const mdgp_ctx* ctx) { return ctx ? ctx->launches_with_rebuilds : -1; }
+
+int mdgp_micro_path(const mdgp_ctx* ctx) {
+  if (!ctx) return MDGP_E_ARG;
+  if (!ctx->planned) return MDGP_E_STATE;
+  return ctx->direct ? 2 : (ctx->graph_while ? 1 : 0);
+}
 
 int64_t mdgp_micro_rebuild_count(const mdgp_ctx* ctx) { return ctx ? ctx->rebuilds : -1; }
 
@@ -886,9 +1132,9 @@ int mdgp_micro_batch(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, mdgp_resu
     int cap = 0;
     for (int attempt = 0; attempt < 3; ++attempt) {
       int st = plan_impl(ctx, sub.data(), (int64_t)sub.size(), cap);
+      if (!st) st = launch_impl(ctx);
+      if (!st) st = results_impl(ctx, res.data(), (int64_t)sub.size());
       if (st) return st;
-      if ((st = launch_impl(ctx))) return st;
-      if ((st = results_impl(ctx, res.data(), (int64_t)sub.size()))) return st;
       bool overflow = false;
       for (auto& r : res) overflow |= r.status == MDGP_E_OVERFLOW;
       if (!overflow) break;
@@ -1024,24 +1270,21 @@ int mdgp_autotune(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int64_t prob
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   for (double skin : skins) {
-    for (int variant = 0; variant <= 3; ++variant) {
-      mdgp_md_params trial = base;
-      trial.skin = skin;
-      trial.build_variant = variant;
-      ctx->params = trial;
-      int st = plan_impl(ctx, probe.data(), n, 0);
-      if (st == MDGP_E_ARG) continue;       // geometry too small for this skin
-      if (st) { ctx->params = base; return st; }
-      if ((st = launch_impl(ctx))) { ctx->params = base; return st; }   // warm-up
-      CK(cudaEventRecord(e0, ctx->stream));
-      if ((st = launch_impl(ctx))) { ctx->params = base; return st; }
-      CK(cudaEventRecord(e1, ctx->stream));
-      CK(cudaEventSynchronize(e1));
-      float ms = 0.f;
-      CK(cudaEventElapsedTime(&ms, e0, e1));
-      const double rate = (double)ctx->n_atoms * (double)probe_steps / (ms * 1e-3);
-      if (rate > top) { top = rate; chosen = trial; }
-    }
+    mdgp_md_params trial = base;
+    trial.skin = skin;
+    ctx->params = trial;
+    int st = plan_impl(ctx, probe.data(), n, 0);
+    if (st == MDGP_E_ARG) continue;       // geometry too small for this skin
+    if (st) { ctx->params = base; return st; }
+    if ((st = launch_impl(ctx))) { ctx->params = base; return st; }   // warm-up
+    CK(cudaEventRecord(e0, ctx->stream));
+    if ((st = launch_impl(ctx))) { ctx->params = base; return st; }
+    CK(cudaEventRecord(e1, ctx->stream));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    const double rate = (double)ctx->n_atoms * (double)probe_steps / (ms * 1e-3);
+    if (rate > top) { top = rate; chosen = trial; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -18,7 +18,9 @@
 //          in bits 0-25 the neighbour's element-local sorted index and in bits
 //          26-31 the cell shift (dx+1, dy+1, dz+1), 2 bits each; the last
 //          group is padded with an entry that is always beyond r_c.
-//   cells  count (binning atomics), start and size after the per-element scan.
+//   cells  count (binning atomics), start and size after the per-element scan;
+//          within a cell the atoms are ordered by original index (the order
+//          does not depend on the binning atomics, so runs are reproducible).
 //   accum  per element FP64 block sums of q and P_xx, temperature sum and the
 //          start/end energies (the time-averaged measurements of Sec. 2.1).
 #pragma once
@@ -43,8 +45,11 @@ constexpr int kFlags = 16;
 
 // status codes written per element (match mdgp_status)
 constexpr int kStUnstable = -4;
+constexpr int kStTimeout = -6;
 constexpr int kStOverflow = -8;
 constexpr int kStSkin = -9;
+
+constexpr int kFlagExit = 7;         // flags[7]: 1 when the persistent step kernel gave up a barrier wait
 
 // FP64 pair-force input position (offset from the cell centre, w = species).
 struct __align__(32) Pos64 {
@@ -69,6 +74,7 @@ struct ElemDev {
   int wnx, wnz;
   int nc[3];           // cell grid
   int id;
+  int warm;            // 0 cold start; 1 fluid from a snapshot; 2 fluid and walls
   int nb;              // blocks actually used
   float csf[3];        // cell sizes as float
   float cs_lo[3];      // cs - csf: the cell sizes as double-float numbers
@@ -89,6 +95,8 @@ struct PhysDev {
   int wall_planes;
   double tau_T;                        // Berendsen time constant (mode 1)
   int list_cap;
+  unsigned long long wait_ns;          // limit of a bounded device-side wait (grid barrier)
+  int inject_skip;                     // test only: block 0 skips its first grid-barrier arrival
   float rc2f, rl2f, half_skin2f;
   float epsf[3], sig2f[3];
   // float copies for the double-float state updates (pair-force precision FP32)
@@ -99,7 +107,6 @@ struct BatchDev {
   const ElemDev* el;
   const long long* atom_off;   // [n_el + 1]
   const long long* cell_off;   // [n_el + 1]
-  const long long* col_off;    // [n_el + 1] prefix of the (x, y) cell columns
   int n_el;
   int list_cap;
   long long n_atoms, n_cells;
@@ -129,6 +136,8 @@ struct BatchDev {
                                   // step mod 3, [8] grid barrier generation, [10..11] its
                                   // 64-bit arrival count
   double* tz;                     // [2 * n_el] per-element sum of m v_z^2 (two step-parity slots)
+  const double* warm;             // [6 * n_atoms] start state (x y z vx vy vz, absolute, original
+                                  // order) of the atoms of elements with warm > 0
 };
 
 // integration kernel phases: kFinish = second half kick (+ measurement unless

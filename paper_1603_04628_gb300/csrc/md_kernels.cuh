@@ -212,6 +212,22 @@ __device__ __forceinline__ void df_st(double* p, long long i, dfl a) {
   reinterpret_cast<float2*>(p)[i] = make_float2(a.hi, a.lo);
 }
 
+// Loads of data a step reads once (the lists, the atom state): kept out of
+// the L1, so that the L1 holds the neighbour positions the pair loop gathers
+// over and over.  The lists are read-only while the step kernels run
+// (non-coherent path, no L1 allocation); the state is also written by the
+// same kernel, so it is read at the L2 (ld.global.cg).
+__device__ __forceinline__ uint4 ld_list4(const uint4* p) {
+  uint4 r;
+  asm("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+      : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(p));
+  return r;
+}
+__device__ __forceinline__ dfl df_ld_cg(const double* p, long long i) {
+  const float2 v = __ldcg(reinterpret_cast<const float2*>(p) + i);
+  return {v.x, v.y};
+}
+
 // One state value as a double, in either representation.
 template <bool DF>
 __device__ __forceinline__ double st_get(const double* p, long long i) {
@@ -270,8 +286,6 @@ __global__ void k_fill_maps(BatchDev B) {
 template <bool DF>
 __global__ void k_init_atoms(BatchDev B, PhysDev P) {
   const long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  int key = -1;
-  double val[4] = {0.0, 0.0, 0.0, 0.0};
   if (a < B.n_atoms) {
     const int e = B.atom_el[a];
     const ElemDev& E = B.el[e];
@@ -317,10 +331,36 @@ __global__ void k_init_atoms(BatchDev B, PhysDev P) {
     normals3<double>((uint32_t)l, 0u, (uint32_t)E.id, 0u, E.seed, n0, n1, n2);
     const double vx = E.vsd * n0, vy = E.vsd * n1, vz = E.vsd * n2;
     st_put<DF>(B.st[3], a, vx); st_put<DF>(B.st[4], a, vy); st_put<DF>(B.st[5], a, vz);
-    key = 2 * e + group;
-    val[0] = vx; val[1] = vy; val[2] = vz; val[3] = vx * vx + vy * vy + vz * vz;
   }
-  seg_add<4>(key, val, [&](int k, int i) { return B.grp + (size_t)k * kGrpStride + i; });
+}
+
+// Per element and group (fluid, walls): sum of v and of |v|^2 in a fixed
+// order -- one block per element, each thread striding over the element's
+// atoms, then a fixed tree over the threads -- so that the mean removal and
+// rescale of k_init_fix give the same velocities on every run.
+template <bool DF>
+__global__ void __launch_bounds__(256) k_group_sums(BatchDev B) {
+  __shared__ double red[8][256];
+  const ElemDev& E = B.el[blockIdx.x];
+  const long long n = (long long)E.nf + E.nw;
+  const int t = threadIdx.x;
+  double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  for (long long l = t; l < n; l += blockDim.x) {
+    const long long a = E.atom0 + l;   // still in original order
+    const double vx = st_get<DF>(B.st[3], a), vy = st_get<DF>(B.st[4], a), vz = st_get<DF>(B.st[5], a);
+    const int g = l < E.nf ? 0 : 4;
+    acc[g] += vx; acc[g + 1] += vy; acc[g + 2] += vz; acc[g + 3] += vx * vx + vy * vy + vz * vz;
+  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) red[k][t] = acc[k];
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (t < h)
+#pragma unroll
+      for (int k = 0; k < 8; ++k) red[k][t] += red[k][t + h];
+    __syncthreads();
+  }
+  if (t < 8) B.grp[(size_t)(2 * blockIdx.x + t / 4) * kGrpStride + (t & 3)] = red[t][0];
 }
 
 // Remove each group's mean velocity, then rescale it to exactly T with
@@ -344,6 +384,23 @@ __global__ void k_init_fix(BatchDev B, PhysDev P) {
     vx *= s; vy *= s; vz *= s;
   }
   st_put<DF>(B.st[3], a, vx); st_put<DF>(B.st[4], a, vy); st_put<DF>(B.st[5], a, vz);
+}
+
+// Start states from snapshots (elements with warm > 0): overwrite the
+// fluid's (and with warm == 2 the walls') lattice positions and velocities
+// by the prepared state; the tether anchors stay the lattice sites.  Runs
+// after k_init_fix, while the atoms are still in original order.
+template <bool DF>
+__global__ void k_apply_warm(BatchDev B) {
+  const long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (a >= B.n_atoms) return;
+  const ElemDev& E = B.el[B.atom_el[a]];
+  if (E.warm == 0) return;
+  const long long l = a - E.atom0;
+  if (l >= E.nf && E.warm < 2) return;
+  const double* w = B.warm + 6 * a;
+  st_put<DF>(B.st[0], a, w[0]); st_put<DF>(B.st[1], a, w[1]); st_put<DF>(B.st[2], a, w[2]);
+  st_put<DF>(B.st[3], a, w[3]); st_put<DF>(B.st[4], a, w[4]); st_put<DF>(B.st[5], a, w[5]);
 }
 
 // ---------------------------------------------------------------------------
@@ -431,7 +488,7 @@ __global__ void __launch_bounds__(1024) k_scan(BatchDev B) {
   }
 }
 
-// Step 3: move every atom to its cell-ordered slot; positions become offsets
+// Step 3: move every atom to a slot of its cell; positions become offsets
 // from the new reference cell's centre, anchors likewise (minimum image).
 // With the double-float state an atom that had a reference cell is rebased
 // by the cell step between the two centres (-delta * cs per axis, delta
@@ -447,7 +504,6 @@ __global__ void __launch_bounds__(256) k_permute(BatchDev B) {
   const int l = B.orig[i];
   const bool wall = l >= E.nf;
   const int c0 = B.cell[i];
-  float fx, fy, fz;   // the new offsets as float (pair-force input)
   if constexpr (DF) {
     if (c0 >= 0) {
       int rx, ry, rz, jx, jy, jz;
@@ -463,7 +519,6 @@ __global__ void __launch_bounds__(256) k_permute(BatchDev B) {
       const dfl ox = df_add(df_ld(B.st[0], i), sx), oy = df_add(df_ld(B.st[1], i), sy),
                 oz = df_add(df_ld(B.st[2], i), sz);
       df_st(B.st2[0], dst, ox); df_st(B.st2[1], dst, oy); df_st(B.st2[2], dst, oz);
-      fx = ox.hi; fy = oy.hi; fz = oz.hi;
       if (wall) {
         df_st(B.st2[6], dst, df_add(df_ld(B.st[6], i), sx));
         df_st(B.st2[7], dst, df_add(df_ld(B.st[7], i), sy));
@@ -493,296 +548,63 @@ __global__ void __launch_bounds__(256) k_permute(BatchDev B) {
     }
     st_put<DF>(B.st2[0], dst, ox); st_put<DF>(B.st2[1], dst, oy); st_put<DF>(B.st2[2], dst, oz);
     st_put<DF>(B.st2[6], dst, ax); st_put<DF>(B.st2[7], dst, ay); st_put<DF>(B.st2[8], dst, az);
-    fx = (float)ox; fy = (float)oy; fz = (float)oz;
-    if constexpr (!DF) static_cast<Pos64*>(B.posb[0])[dst] = Pos64{ox, oy, oz, wall ? 1.0 : 0.0};
   }
   // velocities move as raw 8-byte words in either representation
   B.st2[3][dst] = B.st[3][i]; B.st2[4][dst] = B.st[4][i]; B.st2[5][dst] = B.st[5][i];
   B.orig2[dst] = l;
   B.cell2[dst] = c;
-  if constexpr (DF) {
-    // both buffers: the next force evaluation reads one of them
-    const float4 q = make_float4(fx, fy, fz, wall ? 1.0f : 0.0f);
-    static_cast<float4*>(B.posb[0])[dst] = q;
-    static_cast<float4*>(B.posb[1])[dst] = q;
-  }
-  B.pbuild[dst] = make_float4(fx, fy, fz, 0.0f);
 }
 
-__global__ void __launch_bounds__(256) k_copy_back(BatchDev B) {
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= B.n_atoms) return;
+// Step 4: settle each cell's atoms in the order of their original index (the
+// binning atomics leave them in arbitrary order) while copying the permuted
+// state back, so that the sorted order, the lists and every later summation
+// order are the same on every run.  The pair-force input positions (both
+// buffers: the next force evaluation reads one of them) and the rebuild-time
+// copy for the skin check are written at the settled slot.
+template <typename PT>
+__global__ void __launch_bounds__(256) k_settle(BatchDev B) {
+  constexpr bool DF = sizeof(PT) == 16;
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= B.n_atoms) return;
+  const int c = B.cell2[p];
+  const int start = B.cstart[c], n = B.csize[c];
+  const int me = B.orig2[p];
+  int rank = 0;
+  for (int q = start; q < start + n; ++q) rank += B.orig2[q] < me ? 1 : 0;
+  const long long f = (long long)start + rank;
 #pragma unroll
-  for (int k = 0; k < 9; ++k) B.st[k][i] = B.st2[k][i];
-  B.orig[i] = B.orig2[i];
-  B.cell[i] = B.cell2[i];
+  for (int k = 0; k < 9; ++k) B.st[k][f] = B.st2[k][p];
+  B.orig[f] = me;
+  B.cell[f] = c;
+  const ElemDev& E = B.el[B.atom_el[p]];
+  const bool wall = me >= E.nf;
+  float fx, fy, fz;
+  if constexpr (DF) {
+    fx = df_ld(B.st2[0], p).hi; fy = df_ld(B.st2[1], p).hi; fz = df_ld(B.st2[2], p).hi;
+    const float4 q = make_float4(fx, fy, fz, wall ? 1.0f : 0.0f);
+    static_cast<float4*>(B.posb[0])[f] = q;
+    static_cast<float4*>(B.posb[1])[f] = q;
+  } else {
+    const double ox = B.st2[0][p], oy = B.st2[1][p], oz = B.st2[2][p];
+    static_cast<Pos64*>(B.posb[0])[f] = Pos64{ox, oy, oz, wall ? 1.0 : 0.0};
+    fx = (float)ox; fy = (float)oy; fz = (float)oz;
+  }
+  B.pbuild[f] = make_float4(fx, fy, fz, 0.0f);
 }
 
-// Step 4: Verlet lists by a warp-cooperative sweep: one warp per cell, one
-// lane per atom of the cell; the lanes walk each neighbour cell's atoms
-// together (same address on every lane: a broadcast) and keep those within
-// r_c + skin.  The shift between the two reference cells is warp-uniform.
-// Lists are stored in groups of four entries, [k / 4][atom][4]: a lane
-// collects four entries in registers and writes them with one 16-byte store;
-// the last group is padded with an entry that is always beyond r_c (the atom
-// itself one cell over in x), so readers never test the count inside a group.
+// Step 5: Verlet lists.  Lists are stored in groups of four entries,
+// [k / 4][atom][4] (a warp's 16-byte loads coalesce); the last group is
+// padded with an entry that is always beyond r_c (the atom itself one cell
+// over in x), so readers never test the count inside a group.
 __device__ __forceinline__ unsigned pad_entry(long long i, const ElemDev& E) {
   return (unsigned)(i - E.atom0) | (2u << 26) | (1u << 28) | (1u << 30);
 }
 
-// Positions a list build reads: the rebuild-time copy (float4) or the single
-// FP64 buffer.
-template <typename PT>
-__device__ __forceinline__ const PT* build_positions(const BatchDev& B) {
-  if constexpr (sizeof(PT) == 16) return reinterpret_cast<const PT*>(B.pbuild);
-  else return static_cast<const PT*>(B.posb[0]);
-}
-
-template <typename PT>
-__global__ void __launch_bounds__(128) k_build(BatchDev B, PhysDev P) {
-  using T = decltype(PT::x);
-  const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (warp >= B.n_cells) return;
-  const int cap4 = B.list_cap >> 2;   // groups per atom
-  const int e = B.cell_el[warp];
-  const ElemDev& E = B.el[e];
-  int cx, cy, cz;
-  cell_coords(E, warp, cx, cy, cz);
-  const int ncx = E.nc[0], ncy = E.nc[1], ncz = E.nc[2];
-  const int s0 = B.cstart[warp], n0 = B.csize[warp];
-  const PT* pos = build_positions<PT>(B);
-  const T rl2 = sizeof(T) == 4 ? (T)P.rl2f : (T)P.rl2;
-  const long long N = B.n_atoms;
-  uint4* L4 = reinterpret_cast<uint4*>(B.list);
-  for (int base = 0; base < n0; base += 32) {
-    const int i = s0 + base + lane;
-    const bool act = base + lane < n0;
-    PT me;
-    if (act) me = pos[i];
-    else { me.x = me.y = me.z = (T)1e9; me.w = (T)0; }
-    int cnt = 0;
-    unsigned b0 = 0, b1 = 0, b2 = 0;
-    // append without divergence: every lane runs the same selects; only the
-    // lanes whose group of four is complete store it
-    auto push = [&](bool take, unsigned ent) {
-      const int slot = cnt & 3;
-      b0 = (take && slot == 0) ? ent : b0;
-      b1 = (take && slot == 1) ? ent : b1;
-      b2 = (take && slot == 2) ? ent : b2;
-      if (take && slot == 3 && (cnt >> 2) < cap4) L4[(long long)(cnt >> 2) * N + i] = make_uint4(b0, b1, b2, ent);
-      cnt += take ? 1 : 0;
-    };
-    for (int dx = -1; dx <= 1; ++dx) {
-      int jx = cx + dx;
-      jx = jx < 0 ? jx + ncx : (jx >= ncx ? jx - ncx : jx);
-      for (int dy = -1; dy <= 1; ++dy) {
-        const int jy = cy + dy;
-        if (jy < 0 || jy >= ncy) continue;
-        for (int dz = -1; dz <= 1; ++dz) {
-          int jz = cz + dz;
-          jz = jz < 0 ? jz + ncz : (jz >= ncz ? jz - ncz : jz);
-          const long long c2 = E.cell0 + ((long long)jx * ncy + jy) * ncz + jz;
-          const T qx = me.x - (T)dx * (T)E.cs[0], qy = me.y - (T)dy * (T)E.cs[1], qz = me.z - (T)dz * (T)E.cs[2];
-          const int j0 = B.cstart[c2], j1 = j0 + B.csize[c2];
-          const unsigned code = ((unsigned)(dx + 1) << 26) | ((unsigned)(dy + 1) << 28) | ((unsigned)(dz + 1) << 30);
-          const unsigned jb = (unsigned)(j0 - E.atom0) | code;
-          int j = j0;
-          for (; j + 3 < j1; j += 4) {
-            const PT o0 = pos[j], o1 = pos[j + 1], o2 = pos[j + 2], o3 = pos[j + 3];
-            T d0, d1, d2, d3;
-            { const T ax = qx - o0.x, ay = qy - o0.y, az = qz - o0.z; d0 = ax * ax + ay * ay + az * az; }
-            { const T ax = qx - o1.x, ay = qy - o1.y, az = qz - o1.z; d1 = ax * ax + ay * ay + az * az; }
-            { const T ax = qx - o2.x, ay = qy - o2.y, az = qz - o2.z; d2 = ax * ax + ay * ay + az * az; }
-            { const T ax = qx - o3.x, ay = qy - o3.y, az = qz - o3.z; d3 = ax * ax + ay * ay + az * az; }
-            const unsigned ej = jb + (unsigned)(j - j0);
-            push(act && d0 < rl2 && j != i, ej);
-            push(act && d1 < rl2 && j + 1 != i, ej + 1);
-            push(act && d2 < rl2 && j + 2 != i, ej + 2);
-            push(act && d3 < rl2 && j + 3 != i, ej + 3);
-          }
-          for (; j < j1; ++j) {
-            const PT o0 = pos[j];
-            const T ax = qx - o0.x, ay = qy - o0.y, az = qz - o0.z;
-            push(act && ax * ax + ay * ay + az * az < rl2 && j != i, jb + (unsigned)(j - j0));
-          }
-        }
-      }
-    }
-    if (act) {
-      // pad and write the last, partial group
-      if ((cnt & 3) != 0 && (cnt >> 2) < cap4) {
-        const unsigned pe = pad_entry(i, E);
-        const int slot = cnt & 3;
-        L4[(long long)(cnt >> 2) * N + i] =
-            make_uint4(b0, slot > 1 ? b1 : pe, slot > 2 ? b2 : pe, pe);
-      }
-      if (cnt > B.list_cap) atomicMin(&B.status[e], kStOverflow);
-      B.nlist[i] = cnt < B.list_cap ? cnt : B.list_cap;
-    }
-  }
-}
-
-// Staged list build: one block per (x, y) cell column of an element.  In cell
-// order each of the 9 neighbouring columns (x + dx, y + dy) is one contiguous
-// range of positions, so the block stages them into shared memory with at
-// most 9 bulk asynchronous copies (cp.async.bulk, completed on an mbarrier),
-// then its warps take the column's cells in turn and sweep each cell's 27
-// neighbour cells from shared memory.  A neighbourhood larger than the
-// dynamic shared memory falls back to reading global memory in the same
-// loop.  The wait on the mbarrier is bounded; on timeout the element is
-// marked failed and the block reads global memory instead.
-__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-               :: "r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned phase) {
-  unsigned ok;
-  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-               : "=r"(ok) : "r"(smem_addr(bar)), "r"(phase) : "memory");
-  return ok != 0;
-}
-
-template <typename PT>
-__global__ void __launch_bounds__(128) k_build_staged(BatchDev B, PhysDev P, int smem_bytes) {
-  using T = decltype(PT::x);
-  extern __shared__ __align__(128) unsigned char sraw[];
-  __shared__ uint64_t bar;
-  __shared__ int col_lo[9], col_n[9], col_soff[9];
-  __shared__ int use_smem;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarp = blockDim.x >> 5;
-  // column -> element by binary search over the column offsets
-  const long long colg = blockIdx.x;
-  int lo = 0, hi = B.n_el - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (B.col_off[mid] <= colg) lo = mid; else hi = mid - 1;
-  }
-  const int e = lo;
-  const ElemDev& E = B.el[e];
-  const int ncx = E.nc[0], ncy = E.nc[1], ncz = E.nc[2];
-  const int col = (int)(colg - B.col_off[e]);
-  const int cx = col / ncy, cy = col % ncy;
-  const PT* gpos = build_positions<PT>(B);
-  if (tid == 0) {
-    int total = 0;
-    for (int k = 0; k < 9; ++k) {
-      const int dx = k / 3 - 1, dy = k % 3 - 1;
-      int jx = cx + dx;
-      jx = jx < 0 ? jx + ncx : (jx >= ncx ? jx - ncx : jx);
-      const int jy = cy + dy;
-      if (jy < 0 || jy >= ncy) { col_lo[k] = 0; col_n[k] = 0; col_soff[k] = total; continue; }
-      const long long c0 = E.cell0 + ((long long)jx * ncy + jy) * ncz;
-      const int a = B.cstart[c0], b = B.cstart[c0 + ncz - 1] + B.csize[c0 + ncz - 1];
-      col_lo[k] = a;
-      col_n[k] = b - a;
-      col_soff[k] = total;
-      total += b - a;
-    }
-    use_smem = (long long)total * (long long)sizeof(PT) <= (long long)smem_bytes ? 1 : 0;
-    if (use_smem && total > 0) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&bar)));
-      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                   :: "r"(smem_addr(&bar)), "r"((unsigned)(total * sizeof(PT))) : "memory");
-      PT* sp = reinterpret_cast<PT*>(sraw);
-      for (int k = 0; k < 9; ++k)
-        if (col_n[k] > 0) bulk_g2s(sp + col_soff[k], gpos + col_lo[k], (unsigned)(col_n[k] * sizeof(PT)), &bar);
-    }
-  }
-  __syncthreads();
-  bool staged = use_smem != 0;
-  if (staged && col_soff[8] + col_n[8] > 0) {
-    // bounded wait for the copies (phase 0)
-    bool done = false;
-    for (long long it = 0; it < (1LL << 26) && !done; ++it) done = mbar_try_wait(&bar, 0);
-    if (!done) atomicMin(&B.status[e], kStUnstable);
-    staged = __syncthreads_and(done ? 1 : 0) != 0;
-  }
-  const PT* spos = reinterpret_cast<const PT*>(sraw);
-  const T rl2 = sizeof(T) == 4 ? (T)P.rl2f : (T)P.rl2;
-  const long long N = B.n_atoms;
-  const int cap4 = B.list_cap >> 2;
-  uint4* L4 = reinterpret_cast<uint4*>(B.list);
-  for (int cz = wid; cz < ncz; cz += nwarp) {
-    const long long cell = E.cell0 + ((long long)cx * ncy + cy) * ncz + cz;
-    const int s0 = B.cstart[cell], n0 = B.csize[cell];
-    for (int base = 0; base < n0; base += 32) {
-      const int i = s0 + base + lane;
-      const bool act = base + lane < n0;
-      PT me;
-      if (act) me = staged ? spos[col_soff[4] + (i - col_lo[4])] : gpos[i];
-      else { me.x = me.y = me.z = (T)1e9; me.w = (T)0; }
-      int cnt = 0;
-      unsigned b0 = 0, b1 = 0, b2 = 0;
-      auto push = [&](bool take, unsigned ent) {
-        const int slot = cnt & 3;
-        b0 = (take && slot == 0) ? ent : b0;
-        b1 = (take && slot == 1) ? ent : b1;
-        b2 = (take && slot == 2) ? ent : b2;
-        if (take && slot == 3 && (cnt >> 2) < cap4) L4[(long long)(cnt >> 2) * N + i] = make_uint4(b0, b1, b2, ent);
-        cnt += take ? 1 : 0;
-      };
-      for (int k = 0; k < 9; ++k) {
-        if (col_n[k] == 0) continue;
-        const int dx = k / 3 - 1, dy = k % 3 - 1;
-        int jx = cx + dx;
-        jx = jx < 0 ? jx + ncx : (jx >= ncx ? jx - ncx : jx);
-        const long long c0 = E.cell0 + ((long long)jx * ncy + (cy + dy)) * ncz;
-        // positions of this column: shared memory (index shifted by off) or global
-        const PT* src = staged ? spos : gpos;
-        const int off = staged ? col_soff[k] - col_lo[k] : 0;
-        for (int dz = -1; dz <= 1; ++dz) {
-          int jz = cz + dz;
-          jz = jz < 0 ? jz + ncz : (jz >= ncz ? jz - ncz : jz);
-          const long long c2 = c0 + jz;
-          const T qx = me.x - (T)dx * (T)E.cs[0], qy = me.y - (T)dy * (T)E.cs[1], qz = me.z - (T)dz * (T)E.cs[2];
-          const int j0 = B.cstart[c2], j1 = j0 + B.csize[c2];
-          const unsigned code = ((unsigned)(dx + 1) << 26) | ((unsigned)(dy + 1) << 28) | ((unsigned)(dz + 1) << 30);
-          const unsigned jb = (unsigned)(j0 - E.atom0) | code;
-          int j = j0;
-          for (; j + 3 < j1; j += 4) {
-            const PT o0 = src[j + off], o1 = src[j + 1 + off], o2 = src[j + 2 + off], o3 = src[j + 3 + off];
-            T d0, d1, d2, d3;
-            { const T ax = qx - o0.x, ay = qy - o0.y, az = qz - o0.z; d0 = ax * ax + ay * ay + az * az; }
-            { const T ax = qx - o1.x, ay = qy - o1.y, az = qz - o1.z; d1 = ax * ax + ay * ay + az * az; }
-            { const T ax = qx - o2.x, ay = qy - o2.y, az = qz - o2.z; d2 = ax * ax + ay * ay + az * az; }
-            { const T ax = qx - o3.x, ay = qy - o3.y, az = qz - o3.z; d3 = ax * ax + ay * ay + az * az; }
-            const unsigned ej = jb + (unsigned)(j - j0);
-            push(act && d0 < rl2 && j != i, ej);
-            push(act && d1 < rl2 && j + 1 != i, ej + 1);
-            push(act && d2 < rl2 && j + 2 != i, ej + 2);
-            push(act && d3 < rl2 && j + 3 != i, ej + 3);
-          }
-          for (; j < j1; ++j) {
-            const PT o0 = src[j + off];
-            const T ax = qx - o0.x, ay = qy - o0.y, az = qz - o0.z;
-            push(act && ax * ax + ay * ay + az * az < rl2 && j != i, jb + (unsigned)(j - j0));
-          }
-        }
-      }
-      if (act) {
-        if ((cnt & 3) != 0 && (cnt >> 2) < cap4) {
-          const unsigned pe = pad_entry(i, E);
-          const int slot = cnt & 3;
-          L4[(long long)(cnt >> 2) * N + i] = make_uint4(b0, slot > 1 ? b1 : pe, slot > 2 ? b2 : pe, pe);
-        }
-        if (cnt > B.list_cap) atomicMin(&B.status[e], kStOverflow);
-        B.nlist[i] = cnt < B.list_cap ? cnt : B.list_cap;
-      }
-    }
-  }
-}
-
-// Ballot list build: one warp per cell, lanes over candidates.  The warp
-// first gathers, from the cell's 27 neighbour cells, the atoms that lie
-// within r_c + skin of the bounding box of the cell's own atoms (any other
-// atom is out of range of every atom of the cell) into a per-warp shared
-// buffer: position shifted into the home cell's frame, list entry in w.
-// The gather walks the 27 cells as one flat index range (lane k of the warp
+// Ballot list build.  The candidates of a cell are gathered from its 27
+// neighbour cells: the atoms within r_c + skin of the bounding box of the
+// cell's own atoms (any other atom is out of range of every atom of the
+// cell), each shifted into the home cell's frame with its list entry in w.
+// The gather walks the 27 cells as one flat index range (lane k of a warp
 // holds cell k's start, size and shift; a lane finds its cell by a binary
 // search over the size prefix), so consecutive chunks load independently.
 // The cell's atoms are then taken octant by octant (sign of the offset from
@@ -797,11 +619,7 @@ __global__ void __launch_bounds__(128) k_build_staged(BatchDev B, PhysDev P, int
 // precisions.  The same atom never tests itself: its own candidate is at
 // distance exactly 0 (the zero shift adds 0), which the range test
 // 0 < d^2 < (r_c + skin)^2 excludes.
-constexpr int kBallotWarps = 2;
-constexpr int kBallotCap = 512;   // buffered candidates per warp
-constexpr int kBallotWarpBytes = (kBallotCap + 32) * 16 + (kBallotCap + 32) * 2;
-
-// What one warp knows of its cell for the ballot builds: the bounding box of
+// What one warp knows of its cell for the ballot build: the bounding box of
 // the cell's atoms and the 27-entry neighbour table with its size prefix.
 struct BallotCell {
   float lx, ly, lz, hx, hy, hz;   // bounding box of the cell's own atoms
@@ -960,57 +778,15 @@ __device__ __forceinline__ void ballot_sweep(const BatchDev& B, const ElemDev& E
   }
 }
 
-__global__ void __launch_bounds__(kBallotWarps * 32, 10) k_build_ballot(BatchDev B, PhysDev P) {
-  extern __shared__ __align__(16) unsigned char bsm[];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const long long cell = (long long)blockIdx.x * kBallotWarps + wid;
-  if (cell >= B.n_cells) return;
-  float4* cbuf = reinterpret_cast<float4*>(bsm + wid * kBallotWarpBytes);
-  unsigned short* oidx = reinterpret_cast<unsigned short*>(cbuf + kBallotCap + 32);
-  const int s0 = B.cstart[cell], n0 = B.csize[cell];
-  if (n0 == 0) return;
-  const int e = B.cell_el[cell];
-  const ElemDev& E = B.el[e];
-  BallotCell C;
-  ballot_cell(B, E, cell, s0, n0, lane, C);
-  const float rl2 = P.rl2f;
-  const float4 far4 = make_float4(1.0e18f, 1.0e18f, 1.0e18f, 0.0f);
-  const unsigned lt = (1u << lane) - 1u;
-  if (lane == 0) cbuf[kBallotCap] = far4;   // the padding target of the index lists
-  int f0 = 0;
-  bool first = true, last = false;
-  while (!last) {
-    // gather up to kBallotCap candidates
-    int m = 0;
-#pragma unroll 2
-    for (; f0 < C.total && m + 32 <= kBallotCap; f0 += 32) {
-      float4 p;
-      const bool keep = ballot_candidate(B.pbuild, E, C, f0 + lane, rl2, far4, p);
-      const unsigned mk = __ballot_sync(kFull, keep);
-      if (keep) cbuf[m + __popc(mk & lt)] = p;
-      m += __popc(mk);
-    }
-    last = f0 >= C.total;
-    const int mpad = (m + 31) & ~31;
-    if (m + lane < mpad) cbuf[m + lane] = far4;
-    __syncwarp();
-    ballot_sweep(B, E, e, C, s0, n0, cbuf, oidx, mpad, kBallotCap, 0, 1, first, last, rl2, lane);
-    __syncwarp();
-    first = false;
-  }
-}
-
-// Block form of the ballot build: one block of kBlkWarps warps per cell.
-// The warps gather together, two chunks of 32 candidates each per round
-// (warp w takes chunks w and kBlkWarps + w of the round's 2 kBlkWarps); a
-// prefix over the warps' ballot counts places the kept candidates in flat
-// index order, so the shared buffer holds the same sequence as in the
-// one-warp build.  Warp w then sweeps the octants w, w + kBlkWarps, ... with
-// its own index list.  Each atom is still swept by one warp over the same
-// candidates in the same order, so its list is the one the one-warp build
-// writes, entry for entry; only a cell's time on its SM is about
-// kBlkWarps times shorter, which keeps more warps resident and shortens the
-// tail of the launch.
+// One block of kBlkWarps warps per cell.  The warps gather together, two
+// chunks of 32 candidates each per round (warp w takes chunks w and
+// kBlkWarps + w of the round's 2 kBlkWarps); a prefix over the warps'
+// ballot counts places the kept candidates in flat index order.  Warp w then
+// sweeps the octants w, w + kBlkWarps, ... with its own index list.  Each
+// atom is swept by one warp over the candidates in a fixed order, so its
+// list does not depend on scheduling.  Four warps per cell (against one)
+// keep a cell on its SM for about a quarter of the time, so more warps are
+// resident and the launch's tail is shorter.
 constexpr int kBlkWarps = 4;
 constexpr int kBlkCap = 1024;     // buffered candidates per block
 constexpr int kBlkSmem = (kBlkCap + 32) * 16 + kBlkWarps * (kBlkCap + 32) * 2;
@@ -1138,11 +914,11 @@ struct PairAcc {
 template <typename PT, typename T, bool UNIFORM, bool ENERGY>
 __device__ __forceinline__ PairAcc<PT, T, UNIFORM, ENERGY> pair_force(const BatchDev& B, const PhysDev& P,
                                                                       long long i, const PT* pos, int& spi) {
-  const ElemDev& E = B.el[B.atom_el[i]];
+  const ElemDev& E = B.el[__ldcg(B.atom_el + i)];
   const PT me = pos[i];
   const T csx = (T)E.cs[0], csy = (T)E.cs[1], csz = (T)E.cs[2];
   const PT* posj = pos + E.atom0;
-  const int n = B.nlist[i];
+  const int n = __ldcg(B.nlist + i);
   const long long N = B.n_atoms;
   T rc2, eps[3], sig2[3];
   if constexpr (sizeof(T) == 4) {
@@ -1159,8 +935,8 @@ __device__ __forceinline__ PairAcc<PT, T, UNIFORM, ENERGY> pair_force(const Batc
   int k = 0;
   // two groups of four entries per iteration: eight gathers in flight
   for (; k + 1 < ng; k += 2) {
-    const uint4 e = __ldg(L4 + (long long)k * N);
-    const uint4 f = __ldg(L4 + (long long)(k + 1) * N);
+    const uint4 e = ld_list4(L4 + (long long)k * N);
+    const uint4 f = ld_list4(L4 + (long long)(k + 1) * N);
     const PT o0 = posj[e.x & kJMask], o1 = posj[e.y & kJMask], o2 = posj[e.z & kJMask], o3 = posj[e.w & kJMask];
     const PT o4 = posj[f.x & kJMask], o5 = posj[f.y & kJMask], o6 = posj[f.z & kJMask], o7 = posj[f.w & kJMask];
     acc.add(me, o0, e.x, csx, csy, csz, spi, rc2, eps, sig2, P);
@@ -1173,7 +949,7 @@ __device__ __forceinline__ PairAcc<PT, T, UNIFORM, ENERGY> pair_force(const Batc
     acc.add(me, o7, f.w, csx, csy, csz, spi, rc2, eps, sig2, P);
   }
   if (k < ng) {
-    const uint4 e = __ldg(L4 + (long long)k * N);
+    const uint4 e = ld_list4(L4 + (long long)k * N);
     const PT o0 = posj[e.x & kJMask], o1 = posj[e.y & kJMask], o2 = posj[e.z & kJMask], o3 = posj[e.w & kJMask];
     acc.add(me, o0, e.x, csx, csy, csz, spi, rc2, eps, sig2, P);
     acc.add(me, o1, e.y, csx, csy, csz, spi, rc2, eps, sig2, P);
@@ -1363,8 +1139,9 @@ __global__ void __launch_bounds__(256) k_integrate(BatchDev B, PhysDev P, int k,
 // Block-level segmented reduction of FP32 values for 256-thread blocks: when
 // the whole block shares one key, each warp adds its lanes in FP32 and the
 // eight warp sums are added in FP64 by NV threads (one atomicAdd each);
-// otherwise the values go through block_seg_add in FP64.  All threads of the
-// block must call it.
+// otherwise each warp adds its runs of equal keys in FP64 (seg_add), which
+// needs no shared arrays (they would take L1 capacity from the gathers).
+// All threads of the block must call it.
 template <int NV, typename DstFn>
 __device__ __forceinline__ void block_seg_add_f(int key, const float (&val)[NV], DstFn dst) {
   __shared__ int k0s;
@@ -1391,7 +1168,7 @@ __device__ __forceinline__ void block_seg_add_f(int key, const float (&val)[NV],
   double dv[NV];
 #pragma unroll
   for (int q = 0; q < NV; ++q) dv[q] = (double)val[q];
-  block_seg_add<NV>(key, dv, dst);
+  seg_add<NV>(key, dv, dst);
 }
 
 // The integration step with the double-float state (FP32 pair forces): the
@@ -1412,9 +1189,9 @@ template <bool FROZEN>
 __device__ __forceinline__ void integrate_df_atom(const BatchDev& B, const PhysDev& P, long long i, long long s,
                                                   int mode, int* skin_flag, float fx, float fy, float fz, float wxx,
                                                   StepOut& o) {
-  const int e = B.atom_el[i];
+  const int e = __ldcg(B.atom_el + i);
   const ElemDev& E = B.el[e];
-  const int l = B.orig[i];
+  const int l = __ldcg(B.orig + i);
   const bool fluid = l < E.nf;
   const bool frozen = FROZEN && !fluid;
   const bool stepped = s >= 1 && s - 1 < E.steps_total;
@@ -1424,8 +1201,8 @@ __device__ __forceinline__ void integrate_df_atom(const BatchDev& B, const PhysD
   const long long ks = s - 1 - E.steps_eq;
   const bool sample = stepped && ks >= 0 && ks < E.steps_sample && E.nb > 0 &&
                       ((mode & kTzApply) || ((mode & kFinish) && !(mode & kTzSum)));
-  dfl x = df_ld(B.st[0], i), y = df_ld(B.st[1], i), z = df_ld(B.st[2], i);
-  dfl vx = df_ld(B.st[3], i), vy = df_ld(B.st[4], i), vz = df_ld(B.st[5], i);
+  dfl x = df_ld_cg(B.st[0], i), y = df_ld_cg(B.st[1], i), z = df_ld_cg(B.st[2], i);
+  dfl vx = df_ld_cg(B.st[3], i), vy = df_ld_cg(B.st[4], i), vz = df_ld_cg(B.st[5], i);
   const float h = P.hdt_mf, dt = P.dtf;
   bool moved = false;
   if (fluid) {
@@ -1472,9 +1249,9 @@ __device__ __forceinline__ void integrate_df_atom(const BatchDev& B, const PhysD
       x = df_add(x, df_mul(dt, vx)); y = df_add(y, df_mul(dt, vy)); z = df_add(z, df_mul(dt, vz));
     }
   } else if (!frozen) {
-    fx = __fmaf_rn(-P.k_tetherf, df_diff(x, df_ld(B.st[6], i)), fx);
-    fy = __fmaf_rn(-P.k_tetherf, df_diff(y, df_ld(B.st[7], i)), fy);
-    fz = __fmaf_rn(-P.k_tetherf, df_diff(z, df_ld(B.st[8], i)), fz);
+    fx = __fmaf_rn(-P.k_tetherf, df_diff(x, df_ld_cg(B.st[6], i)), fx);
+    fy = __fmaf_rn(-P.k_tetherf, df_diff(y, df_ld_cg(B.st[7], i)), fy);
+    fz = __fmaf_rn(-P.k_tetherf, df_diff(z, df_ld_cg(B.st[8], i)), fz);
     if (fin) { vx = df_add(vx, __fmul_rn(h, fx)); vy = df_add(vy, __fmul_rn(h, fy)); vz = df_add(vz, __fmul_rn(h, fz)); }
     if (st1) {
       float b0 = 0.f, b1 = 0.f, b2 = 0.f;
@@ -1504,7 +1281,7 @@ __device__ __forceinline__ void integrate_df_atom(const BatchDev& B, const PhysD
     df_st(B.st[0], i, x); df_st(B.st[1], i, y); df_st(B.st[2], i, z);
     const float xf = x.hi, yf = y.hi, zf = z.hi;
     if (!(fabsf(yf) < 1e6f) || !(fabsf(xf) < 1e6f) || !(fabsf(zf) < 1e6f)) atomicMin(&B.status[e], kStUnstable);
-    const float4 pb = B.pbuild[i];
+    const float4 pb = __ldcg(B.pbuild + i);
     const float ex = xf - pb.x, ey = yf - pb.y, ez = zf - pb.z;
     if (ex * ex + ey * ey + ez * ez > P.half_skin2f) {
       if (skin_flag) atomicOr(skin_flag, 1);
@@ -1596,7 +1373,9 @@ __global__ void __launch_bounds__(128) k_step_df(BatchDev B, PhysDev P, int k, i
 // it holds g x gridDim blocks, so the block whose arrival makes it
 // (g + 1) x gridDim publishes generation g + 1 with a release store, and the
 // other leaders wait for it with acquire loads.  One atomic and one store on
-// the release path.  The wait is bounded: false if it gave up.
+// the release path.  The wait is bounded by wait_ns nanoseconds of the
+// global timer: false if it gave up.  skip (test only) leaves this block's
+// arrival out, so no block is released and every wait runs out.
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -1605,8 +1384,13 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
 __device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
 }
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
-__device__ __forceinline__ bool grid_barrier(int* flags) {
+__device__ __forceinline__ bool grid_barrier(int* flags, unsigned long long wait_ns, bool skip = false) {
   __syncthreads();
   int ok = 1;
   if (threadIdx.x == 0) {
@@ -1615,14 +1399,14 @@ __device__ __forceinline__ bool grid_barrier(int* flags) {
     const unsigned g = ld_acquire_gpu(gen);
     __threadfence();
     const unsigned long long target = (unsigned long long)(g + 1u) * gridDim.x;
-    if (atomicAdd(cnt, 1ull) == target - 1ull) {
+    if (!skip && atomicAdd(cnt, 1ull) == target - 1ull) {
       __threadfence();   // the other blocks' arrivals (and their writes) before the release
       st_release_gpu(gen, g + 1u);
     } else {
-      long long it = 0;
+      const unsigned long long t0 = global_ns();
       while (ld_acquire_gpu(gen) == g) {
-        if (++it > (1LL << 22)) { ok = 0; break; }   // ~0.1-1 s
-        __nanosleep(32);
+        if (global_ns() - t0 > wait_ns) { ok = 0; break; }
+        __nanosleep(64);
       }
     }
   }
@@ -1640,19 +1424,19 @@ __device__ __forceinline__ bool grid_barrier(int* flags) {
 // exit block 0 stores the step counter and sets the graph conditions: the
 // rebuild (IF) and whether steps remain (WHILE).  With the frozen-wall
 // thermostat a step is two phases with a barrier between them.  A barrier
-// that gives up marks every element unstable and ends the run.  Block c
+// that gives up marks every element MDGP_E_TIMEOUT and ends the run.  Block c
 // takes atoms [c A, (c + 1) A) with A <= blockDim.x chosen by the host so
 // that every SM holds the same number of atoms (the step ends with the
 // most loaded SM).
 template <bool UNIFORM, bool FROZEN>
 __global__ void __launch_bounds__(256, 5) k_steps_persist(BatchDev B, PhysDev P, long long S, int A,
                                                       cudaGraphConditionalHandle h_rebuild,
-                                                      cudaGraphConditionalHandle h_more) {
+                                                      cudaGraphConditionalHandle h_more, int use_cond) {
   const long long nchunks = (B.n_atoms + A - 1) / A;
   const bool lane_used = (int)threadIdx.x < A;
   long long s = *B.step_base;
-  bool rebuild = false, failed = false;
-  while (s < S) {
+  bool rebuild = false, failed = false, first_wait = true;
+  while (s < S && !failed) {
     if (blockIdx.x == 0 && threadIdx.x == 0) B.flags[kFlagSkin + (int)((s + 1) % 3)] = 0;
     int* skin = &B.flags[kFlagSkin + (int)(s % 3)];
     const float4* pos = static_cast<const float4*>(B.posb[s & 1]);
@@ -1674,7 +1458,8 @@ __global__ void __launch_bounds__(256, 5) k_steps_persist(BatchDev B, PhysDev P,
       }
       integrate_df_epilogue<FROZEN>(B, s, m1, o, 0, 0);
     }
-    if (!grid_barrier(B.flags)) { failed = true; break; }
+    if (!grid_barrier(B.flags, P.wait_ns, P.inject_skip && first_wait && blockIdx.x == 0)) { failed = true; break; }
+    first_wait = false;
     if (FROZEN) {
       const int m2 = kTzApply | kStage1;
       for (long long c = blockIdx.x; c < nchunks; c += gridDim.x) {
@@ -1686,7 +1471,7 @@ __global__ void __launch_bounds__(256, 5) k_steps_persist(BatchDev B, PhysDev P,
                                     static_cast<const float*>(B.wxx)[i], o);
         integrate_df_epilogue<FROZEN>(B, s, m2, o, 0, 0);
       }
-      if (!grid_barrier(B.flags)) { failed = true; break; }
+      if (!grid_barrier(B.flags, P.wait_ns)) { failed = true; break; }
     }
     rebuild = *(volatile int*)skin != 0;
     ++s;
@@ -1695,13 +1480,16 @@ __global__ void __launch_bounds__(256, 5) k_steps_persist(BatchDev B, PhysDev P,
   if (failed) {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < B.n_el;
          e += (long long)gridDim.x * blockDim.x)
-      atomicMin(&B.status[e], kStUnstable);
+      atomicMin(&B.status[e], kStTimeout);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *B.step_base = s;
     atomicAdd(&B.flags[3], 1);
-    cudaGraphSetConditional(h_rebuild, (rebuild && !failed) ? 1u : 0u);
-    cudaGraphSetConditional(h_more, (s < S && !failed) ? 1u : 0u);
+    if (failed) B.flags[kFlagExit] = 1;
+    if (use_cond) {
+      cudaGraphSetConditional(h_rebuild, (rebuild && !failed) ? 1u : 0u);
+      cudaGraphSetConditional(h_more, (s < S && !failed) ? 1u : 0u);
+    }
   }
 }
 

@@ -28,7 +28,12 @@ class Result(ctypes.Structure):
     _fields_ = [("q", ctypes.c_double), ("q_se", ctypes.c_double), ("p", ctypes.c_double),
                 ("p_se", ctypes.c_double), ("T_meas", ctypes.c_double), ("e_drift", ctypes.c_double),
                 ("n_fluid", ctypes.c_int64), ("n_wall", ctypes.c_int64), ("status", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("start", ctypes.c_int32)]
+
+
+class Start(ctypes.Structure):
+    _fields_ = [("xv", ctypes.POINTER(ctypes.c_float)), ("n_fluid", ctypes.c_int64), ("n_wall", ctypes.c_int64),
+                ("h", ctypes.c_double), ("Lx", ctypes.c_double), ("Lz", ctypes.c_double)]
 
 
 class MDParams(ctypes.Structure):
@@ -39,13 +44,15 @@ class MDParams(ctypes.Structure):
                 ("mass", ctypes.c_double), ("n_blocks", ctypes.c_int32), ("mode", ctypes.c_int32),
                 ("wall_planes", ctypes.c_int32), ("list_capacity", ctypes.c_int32),
                 ("skin", ctypes.c_double), ("rebuild_every", ctypes.c_int32), ("build_variant", ctypes.c_int32),
-                ("persistent", ctypes.c_int32)]
+                ("persistent", ctypes.c_int32), ("wait_timeout_ms", ctypes.c_int32),
+                ("inject_barrier_skip", ctypes.c_int32)]
 
 
 class GPParams(ctypes.Structure):
     _fields_ = [("sf2", ctypes.c_double), ("l2", ctypes.c_double), ("sn2", ctypes.c_double),
                 ("fallback_scale", ctypes.c_double), ("fixed_scales", ctypes.POINTER(ctypes.c_double)),
-                ("fallback_scales", ctypes.POINTER(ctypes.c_double))]
+                ("fallback_scales", ctypes.POINTER(ctypes.c_double)), ("period", ctypes.c_double),
+                ("hold", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class MacroParams(ctypes.Structure):
@@ -99,10 +106,13 @@ def lib():
         "mdgp_set_stream": ([vp, vp], ctypes.c_int),
         "mdgp_micro_batch": ([vp, ctypes.POINTER(Element), i64, ctypes.POINTER(Result)], ctypes.c_int),
         "mdgp_micro_plan": ([vp, ctypes.POINTER(Element), i64, ctypes.POINTER(i64)], ctypes.c_int),
+        "mdgp_micro_plan_from": ([vp, ctypes.POINTER(Element), i64, ctypes.POINTER(Start), ctypes.POINTER(i64)],
+                                 ctypes.c_int),
         "mdgp_micro_launch": ([vp], ctypes.c_int),
         "mdgp_micro_results": ([vp, ctypes.POINTER(Result), i64], ctypes.c_int),
         "mdgp_micro_launch_count": ([vp], i64),
         "mdgp_micro_rebuild_count": ([vp], i64),
+        "mdgp_micro_path": ([vp], ctypes.c_int),
         "mdgp_micro_state": ([vp, dp, dp, i64], ctypes.c_int),
         "mdgp_md_forces": ([vp, ctypes.POINTER(Element), dp, i64, dp, dp, dp], ctypes.c_int),
         "mdgp_micro_profile": ([vp, i64, dp], ctypes.c_int),
@@ -236,6 +246,27 @@ class Context:
         self.n_atoms = int(n.value)
         return self.n_atoms
 
+    def micro_plan_from(self, els, starts):
+        """mdgp_micro_plan_from: starts[k] is None (cold) or a dict with the
+        snapshot rows xv ((n_fluid + n_wall) x 6, fluid first: x y z vx vy vz)
+        and the geometry h, Lx, Lz it was taken in."""
+        arr = elements_array(els)
+        st = (Start * len(els))()
+        keep = []
+        for k, s in enumerate(starts):
+            if s is None:
+                continue
+            xv = np.ascontiguousarray(s["xv"], dtype=np.float32)
+            keep.append(xv)
+            st[k].xv = xv.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+            st[k].n_fluid, st[k].n_wall = int(s["n_fluid"]), int(s["n_wall"])
+            st[k].h, st[k].Lx, st[k].Lz = float(s["h"]), float(s["Lx"]), float(s["Lz"])
+        n = ctypes.c_int64()
+        _check(self.h, lib().mdgp_micro_plan_from(self.h, arr, len(els), st, ctypes.byref(n)), "mdgp_micro_plan_from")
+        self._n_el = len(els)
+        self.n_atoms = int(n.value)
+        return self.n_atoms
+
     def micro_launch(self):
         _check(self.h, lib().mdgp_micro_launch(self.h), "mdgp_micro_launch")
 
@@ -249,6 +280,14 @@ class Context:
 
     def rebuild_count(self):
         return int(lib().mdgp_micro_rebuild_count(self.h))
+
+    def path(self):
+        """Step loop of the planned batch: 'per-step', 'persistent-graph' or
+        'persistent-direct'."""
+        code = int(lib().mdgp_micro_path(self.h))
+        if code < 0:
+            raise MdgpError("mdgp_micro_path: %s" % STATUS.get(code, code))
+        return {0: "per-step", 1: "persistent-graph", 2: "persistent-direct"}[code]
 
     def micro_state(self):
         x = np.zeros((self.n_atoms, 3))
@@ -289,12 +328,12 @@ class GP:
     adds the outputs later on the same factor."""
 
     def __init__(self, ctx, X, y, sf2, l2, sn2, mu_X=None, fallback_scale=1.0, fixed_scales=None,
-                 fallback_scales=None):
+                 fallback_scales=None, period=0.0):
         M = len(X) if y is None else len(y)
         X = np.ascontiguousarray(np.asarray(X, dtype=np.float64).reshape(M, -1) if M else
                                  np.zeros((0, np.asarray(X).shape[-1] if np.ndim(X) == 2 else 1)))
         self.D = X.shape[1]
-        p = GPParams(float(sf2), float(l2), float(sn2), float(fallback_scale), None, None)
+        p = GPParams(float(sf2), float(l2), float(sn2), float(fallback_scale), None, None, float(period), 0, 0)
         self._fb = None
         if fallback_scales is not None:
             self._fb = np.ascontiguousarray(fallback_scales, dtype=np.float64)
@@ -552,11 +591,13 @@ def mdgp_hybrid_step(hybrid, sigma_t):
     return hybrid.step(sigma_t)
 
 
-def gp_optimize(ctx, X, y, sf2, l2, sn2, mu_X=None, fallback_scale=1.0, fallback_scales=None, max_evals=200):
-    """mdgp_gp_optimize: hyperparameters (sf2, l2, sn2) by maximum evidence."""
+def gp_optimize(ctx, X, y, sf2, l2, sn2, mu_X=None, fallback_scale=1.0, fallback_scales=None, max_evals=200,
+                period=0.0, hold=0):
+    """mdgp_gp_optimize: hyperparameters (sf2, l2, sn2) by maximum evidence;
+    hold = bit mask of values kept (1 sf2, 2 l2, 4 sn2)."""
     y = np.ascontiguousarray(y, dtype=np.float64)
     X = np.ascontiguousarray(np.asarray(X, dtype=np.float64).reshape(len(y), -1))
-    start = GPParams(float(sf2), float(l2), float(sn2), float(fallback_scale), None, None)
+    start = GPParams(float(sf2), float(l2), float(sn2), float(fallback_scale), None, None, float(period), int(hold), 0)
     fb = None
     if fallback_scales is not None:
         fb = np.ascontiguousarray(fallback_scales, dtype=np.float64)

@@ -116,7 +116,7 @@ def test_pair_forces_at_maximum_element_size(native):
     for prec in (0, 1):
         ctx = native.Context(0, prec)
         f, w, e = ctx.md_forces(el, x)
-        assert _force_err(f, fr, amb) <= FP_TOL[prec]
+        assert _force_err(f, fr, amb) <= FP_TOL[prec], prec
         assert np.abs(f - fr)[amb].max(initial=0.0) <= jump
         ctx.close()
 
@@ -221,7 +221,10 @@ def _oracle_run(el):
 def test_long_run_flow_rate_fp32_within_oracle_ensemble(native):
     # the plain element (2000 + 3000 steps) with body force 0.05, sixteen seeds
     # on each side; the standard error of each ensemble mean is the spread
-    # across seeds / sqrt(16) (independent runs), the bound is |z| < 3
+    # across seeds / sqrt(16) (independent runs), the bound is two combined
+    # standard errors, |z| < 2.  Both sides are deterministic (the oracle, and
+    # the GPU's fixed in-cell order and summation orders), so for these
+    # seeds the outcome is the same on every run.
     seeds = [301 + k for k in range(16)]
     els = [synth.element_plain(seed=s, g=0.05, elem_id=k) for k, s in enumerate(seeds)]
     ctx_pool = mp.get_context("spawn")
@@ -236,7 +239,7 @@ def test_long_run_flow_rate_fp32_within_oracle_ensemble(native):
         se = math.sqrt(g.var(ddof=1) / len(g) + o.var(ddof=1) / len(o))
         z = abs(g.mean() - o.mean()) / se
         print("%s: gpu %.4f oracle %.4f z %.2f" % (key, g.mean(), o.mean(), z))
-        assert z < 3.0, (key, z)
+        assert z < 2.0, (key, z)
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -253,31 +256,10 @@ def test_energy_conservation_without_thermostat_or_forcing(native, prec):
     assert abs(r["e_drift"]) < 2e-3 + 2 * abs(ref["e_drift"])
 
 
-@pytest.mark.parametrize("cfg", [1, 2])
-def test_list_build_variants_find_the_same_pairs(native, cfg):
-    # staged (0), direct (1), ballot (2) and block ballot (3) builds must give
-    # every atom the same neighbours within r_c; the order of atoms inside a
-    # cell comes from binning atomics and differs from call to call, so the
-    # forces agree up to FP64 summation order
-    name, el, x, sp = configs()[cfg]
-    out = []
-    for variant in (0, 1, 2, 3):
-        ctx = native.Context(0, native.PREC_FP64, build_variant=variant)
-        out.append(ctx.md_forces(el, x))
-        ctx.close()
-    f0, w0, e0 = out[0]
-    scale = max(np.abs(f0).max(), 1.0)
-    for f, w, e in out[1:]:
-        assert np.abs(f - f0).max() <= 1e-12 * scale
-        assert np.abs(w - w0).max() <= 1e-12 * max(np.abs(w0).max(), 1.0)
-        assert abs(e.sum() - e0.sum()) <= 1e-12 * max(np.abs(e0).sum(), 1.0)
-
-
-@pytest.mark.parametrize("variant", [2, 3])
-def test_ballot_build_multi_pass_matches_oracle(native, variant):
+def test_ballot_build_multi_pass_matches_oracle(native):
     # dense walls (wall density 4) and r_c = 4 put far more than one shared
     # buffer of candidates around each cell and more than 32 atoms in a cell:
-    # the ballot builds sweep in several passes
+    # the ballot build sweeps in several passes
     el = dict(h=8.0, Lx=13.5, Lz=13.5, density=0.75, T=2.44, g_ext=0.0, dpdx=0.0, steps_eq=0, steps_sample=0,
               seed=3, id=0)
     p = omd.make_params(el, **PAPER_MODE)
@@ -285,7 +267,7 @@ def test_ballot_build_multi_pass_matches_oracle(native, variant):
     rng = np.random.default_rng(5)
     x = x + rng.normal(0.0, 0.05, x.shape) * (sp[:, None] == 0)
     fr, wr, er = omd.lj_forces(p, x, sp, "cells")
-    ctx = native.Context(0, native.PREC_FP64, build_variant=variant, list_capacity=1600, **PAPER_MODE)
+    ctx = native.Context(0, native.PREC_FP64, list_capacity=1600, **PAPER_MODE)
     f, w, e = ctx.md_forces(el, x)
     ctx.close()
     assert _force_err(f, fr) <= FP_TOL[0]
@@ -297,7 +279,7 @@ def test_autotune_keeps_results_exact(native):
     els = synth.batch_uneven(6, seed=13, steps=60)
     ctx = native.Context(0, native.PREC_FP64)
     chosen, rate = ctx.autotune(els, probe_steps=40)
-    assert chosen["skin"] in (0.3, 0.4, 0.5, 0.6) and chosen["build_variant"] in (0, 1, 2, 3)
+    assert chosen["skin"] in (0.3, 0.4, 0.5, 0.6)
     assert rate > 0
     res = ctx.micro_batch(els)
     for el, r in zip(els, res):
@@ -400,3 +382,148 @@ def test_full_uneven_batch_in_bench_configuration():
         assert np.abs(d).max() < 1e-3, k
         assert r1["q"] == pytest.approx(res[k]["q"], rel=2e-2, abs=2e-2), k
     ctx.close()
+
+
+def test_fp32_forces_dense_walls_paper_mode(native):
+    # FP32 pair forces with the paper's parameters: frozen dense walls (wall
+    # density 4), wall-fluid (0.2, 0.75), r_c = 4 -- crowded cells, several
+    # candidate passes per cell, three pair types
+    el = dict(h=8.0, Lx=13.5, Lz=13.5, density=0.75, T=2.44, g_ext=0.0, dpdx=0.0, steps_eq=0, steps_sample=0,
+              seed=3, id=0)
+    p = omd.make_params(el, **PAPER_MODE)
+    x, v, a, sp = omd.init(p)
+    rng = np.random.default_rng(5)
+    x = x + rng.normal(0.0, 0.05, x.shape) * (sp[:, None] == 0)
+    fr, wr, er = omd.lj_forces(p, x, sp, "cells")
+    amb, jump = _cutoff_ambiguous_rc(el, x, sp, fr, 4.0, PAPER_MODE)
+    ctx = native.Context(0, native.PREC_FP32, list_capacity=1600, **PAPER_MODE)
+    f, w, e = ctx.md_forces(el, x)
+    ctx.close()
+    assert _force_err(f, fr, amb) <= FP_TOL[1]
+    fl = sp == 0
+    assert np.abs(w[fl] - wr[fl]).max() <= 2e-5 * max(np.abs(wr[fl]).max(), 1.0)
+    assert e.sum() == pytest.approx(er.sum(), rel=2e-5)
+
+
+def _cutoff_ambiguous_rc(el, x, sp, ref, rc, phys):
+    lo = omd.lj_forces(omd.make_params(el, **dict(phys, rc=rc - 1e-6)), x, sp, "cells")[0]
+    hi = omd.lj_forces(omd.make_params(el, **dict(phys, rc=rc + 1e-6)), x, sp, "cells")[0]
+    return (np.abs(lo - ref).max(axis=1) > 0) | (np.abs(hi - ref).max(axis=1) > 0), None
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_runs_are_reproducible(native, prec):
+    # the in-cell order follows the atoms' original indices and every
+    # per-atom sum runs in a fixed order, so the same batch gives the same
+    # trajectory bit for bit (FP32: the persistent step loop)
+    els = synth.batch_uneven(4, seed=31, steps=120)
+    out = []
+    for _ in range(2):
+        ctx = native.Context(0, prec)
+        ctx.micro_plan(els)
+        ctx.micro_launch()
+        res = ctx.micro_results()
+        x, v = ctx.micro_state()
+        out.append((res, x, v, ctx.rebuild_count()))
+        ctx.close()
+    (ra, xa, va, na), (rb, xb, vb, nb) = out
+    assert na == nb > 1
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+    for a, b in zip(ra, rb):
+        assert a["status"] == b["status"] == 0
+        assert a["q"] == pytest.approx(b["q"], rel=1e-12, abs=1e-14)   # FP64 atomics add the samples
+
+
+def test_barrier_timeout_is_reported_and_context_recovers(native):
+    # failure detection without a fault: one block of the persistent step
+    # kernel leaves out its first grid-barrier arrival (test-only switch), so
+    # every other block's bounded wait runs out after 50 ms of the GPU's
+    # global timer; the launch ends with MDGP_E_TIMEOUT on every element and
+    # the same context then runs the batch cleanly
+    els = synth.batch_uneven(3, seed=41, steps=40)
+    ctx = native.Context(0, native.PREC_FP32, inject_barrier_skip=1, wait_timeout_ms=50)
+    ctx.micro_plan(els)
+    ctx.micro_launch()
+    res = ctx.micro_results()
+    assert [r["status"] for r in res] == [-6] * len(els)
+    ctx.set_md_params(wait_timeout_ms=50)
+    ctx.micro_plan(els)
+    ctx.micro_launch()
+    res = ctx.micro_results()
+    assert all(r["status"] == 0 for r in res)
+    ref = native.Context(0, native.PREC_FP32).micro_batch(els)
+    for a, b in zip(res, ref):
+        assert a["q"] == pytest.approx(b["q"], rel=1e-12, abs=1e-14)
+    ctx.close()
+
+
+def test_double_float_state_against_fp64_over_20000_steps(native):
+    # The FP32-force path keeps positions and velocities as double-float
+    # pairs (~44-bit significand) instead of FP64.  Over 20 000 steps of an
+    # element of the uneven batch's kind (h = 10, 12 x 12, n = 0.8):
+    #  - NVE (no thermostat, no forcing): the energy drift per atom stays at
+    #    the FP64 run's level -- a state rounded like plain FP32 would walk;
+    #  - driven (g = 0.02, thermostatted walls): the ensemble-mean flow rate
+    #    of sixteen seeds matches the FP64 ensemble within two standard
+    #    errors (the runs are chaotic, so seeds, not trajectories, compare).
+    base = dict(h=10.0, Lx=12.0, Lz=12.0, density=0.8, T=1.1, g_ext=0.0, dpdx=0.0, steps_eq=4000,
+                steps_sample=16000, seed=7, id=0)
+    drift = {}
+    for prec in (0, 1):
+        ctx = native.Context(0, prec, gamma_wall=0.0)
+        drift[prec] = ctx.micro_batch([base])[0]["e_drift"]
+        ctx.close()
+    print("NVE e_drift per atom: FP64 %.3g, FP32 forces + double-float state %.3g" % (drift[0], drift[1]))
+    assert abs(drift[1]) <= 2.0 * abs(drift[0]) + 2e-4
+    els = [dict(base, g_ext=0.02, seed=900 + k, id=k) for k in range(16)]
+    q = {}
+    for prec in (0, 1):
+        ctx = native.Context(0, prec)
+        res = ctx.micro_batch(els)
+        ctx.close()
+        assert all(r["status"] == 0 for r in res)
+        q[prec] = np.array([r["q"] for r in res])
+    se = math.sqrt(q[0].var(ddof=1) / 16 + q[1].var(ddof=1) / 16)
+    z = abs(q[0].mean() - q[1].mean()) / se
+    print("q over 16 seeds: FP64 %.4f, FP32 + double-float %.4f, combined SE %.4f, z %.2f"
+          % (q[0].mean(), q[1].mean(), se, z))
+    assert z < 2.0
+
+
+def _oracle_positions(el):
+    p = omd.make_params(el)
+    x, v, a, sp = omd.init(p)
+    omd.simulate(p, x, v, a, sp, 0, el["steps_eq"] + el["steps_sample"])
+    return x
+
+
+def test_full_uneven_batch_against_the_oracle():
+    # every element of the 64-element batch exactly as bench.py launches it
+    # (FP32 pair forces, double-float state, the persistent step loop), 100
+    # steps, against its own FP64 oracle run:
+    # positions agree to FP32 order (the force error, ~1e-5 relative, grows
+    # through the chaotic dynamics to well under 1e-4 sigma in 100 steps)
+    import os
+    from paper_1603_04628_gb300 import native
+    els = synth.batch_uneven(64, steps=100)
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        refs = pool.map(_oracle_positions, els)
+    ctx = native.Context(0, native.PREC_FP32)
+    n = ctx.micro_plan(els)
+    ctx.micro_launch()
+    res = ctx.micro_results()
+    xg, vg = ctx.micro_state()
+    ctx.close()
+    assert all(r["status"] == 0 for r in res)
+    off, worst = 0, 0.0
+    for el, r, xr in zip(els, res, refs):
+        m = r["n_fluid"] + r["n_wall"]
+        assert m == len(xr)
+        d = xg[off:off + m] - xr
+        d[:, 0] -= el["Lx"] * np.round(d[:, 0] / el["Lx"])
+        d[:, 2] -= el["Lz"] * np.round(d[:, 2] / el["Lz"])
+        worst = max(worst, float(np.abs(d).max()))
+        off += m
+    assert off == n
+    print("64-element batch, 100 steps: max |dx| against the oracle %.3g sigma" % worst)
+    assert worst < 1e-4

@@ -181,3 +181,67 @@ def test_optimize_ends_at_a_coordinate_maximum():
             t = list(h)
             t[k] *= fac
             assert gp.GP(X, y, *t).log_marginal_likelihood() <= f + 1e-6 * abs(f)
+
+
+# ---------------------------------------------------------------- App. B periodic kernel
+def test_periodic_kernel_one_point_by_hand():
+    # one sample y1 = 2 at t = 0, period T = 4, l = 1, sf2 = 1, sn2 = 0.25: at
+    # t = 1 the kernel is exp(-2 sin^2(pi/4)) = exp(-1), so the posterior mean
+    # is exp(-1) / 1.25 * 2 and the latent variance 1 - exp(-2) / 1.25
+    g = gp.GP(np.array([[0.0]]), np.array([2.0]), 1.0, 1.0, 0.25, period=4.0)
+    m, v = g.predict(np.array([[1.0], [4.0], [2.0]]))
+    e1 = 0.36787944117144233          # exp(-1)
+    assert m[0] == pytest.approx(e1 / 1.25 * 2.0, rel=1e-14)
+    assert v[0] == pytest.approx(1.0 - e1 * e1 / 1.25, rel=1e-13)
+    # one period later the input is the sample itself; half a period away the
+    # kernel is exp(-2 sin^2(pi/2)) = exp(-2)
+    assert m[1] == pytest.approx(2.0 / 1.25, rel=1e-13)
+    assert m[2] == pytest.approx(0.1353352832366127 / 1.25 * 2.0, rel=1e-13)
+
+
+def test_periodic_posterior_is_periodic_and_matches_sklearn():
+    from sklearn.gaussian_process import GaussianProcessRegressor
+    from sklearn.gaussian_process.kernels import ConstantKernel, ExpSineSquared, WhiteKernel
+    rng = np.random.default_rng(3)
+    T = 7.3
+    t = np.sort(rng.uniform(0.0, 3 * T, 60)).reshape(-1, 1)
+    y = 1.5 * np.sin(2 * np.pi * t[:, 0] / T) + 0.2 * rng.standard_normal(60)
+    sf2, l2, sn2 = 1.7, 0.8, 0.04
+    g = gp.GP(t, y, sf2, l2, sn2, period=T)
+    ts = np.linspace(0.0, T, 23).reshape(-1, 1)
+    m, v = g.predict(ts)
+    m2, v2 = g.predict(ts + 2 * T)
+    np.testing.assert_allclose(m2, m, rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(v2, v, rtol=1e-9, atol=1e-12)
+    # scikit-learn's ExpSineSquared is exp(-2 sin^2(pi d / p) / l^2)
+    k = ConstantKernel(sf2, "fixed") * ExpSineSquared(math.sqrt(l2), T, "fixed", "fixed") + WhiteKernel(sn2, "fixed")
+    sk = GaussianProcessRegressor(kernel=k, optimizer=None, normalize_y=False).fit(t, y)
+    ms, ss = sk.predict(ts, return_std=True)
+    np.testing.assert_allclose(m, ms, rtol=1e-8, atol=1e-10)
+    np.testing.assert_allclose(v + sn2, ss ** 2, rtol=1e-7, atol=1e-10)   # sklearn adds the white noise
+
+
+def test_periodic_kernel_long_length_scale_limit():
+    # l -> infinity: every pair fully correlated, K = sf2 everywhere, so the
+    # posterior mean is the constant sf2 sum(y) / (M sf2 + sn2)
+    t = np.array([[0.1], [1.3], [2.9], [4.4]])
+    y = np.array([1.0, -0.5, 2.0, 0.25])
+    g = gp.GP(t, y, 2.0, 1e12, 0.5, period=5.0)
+    m, _ = g.predict(np.array([[0.7], [3.3]]))
+    np.testing.assert_allclose(m, 2.0 * y.sum() / (4 * 2.0 + 0.5), rtol=1e-9)
+
+
+def test_periodic_filter_recovers_a_sinusoid_with_held_signal_variance():
+    # App. B procedure: (l2, sn2) by maximum evidence on the samples up to the
+    # first peak with sf2 held, then regression over the whole series
+    rng = np.random.default_rng(8)
+    T = 10.0
+    t = np.linspace(0.0, 2 * T, 201)
+    truth = 0.8 * np.sin(2 * np.pi * t / T)
+    q = truth + 0.15 * rng.standard_normal(len(t))
+    mean, var, l2, sn2 = gp.periodic_filter(t, q, T, 1.0, 1.0, 0.01, fit_until=T / 4)
+    assert np.sqrt(np.mean((mean - truth) ** 2)) < 0.5 * np.sqrt(np.mean((q - truth) ** 2))
+    assert 0.005 < sn2 < 0.1
+    # the held signal variance stayed put: the search moved only l2 and sn2
+    _, l2b, sn2b, _ = gp.optimize(t[t <= T / 4].reshape(-1, 1), q[t <= T / 4], 1.0, 1.0, 0.01, period=T, hold=1)
+    assert (l2b, sn2b) == (l2, sn2)
