@@ -155,10 +155,11 @@ def main():
                     help="steps of the FP64-forces pass reported beside the headline")
     ap.add_argument("--steps-per-element", type=int, default=STEPS_PER_ELEMENT,
                     help="MD steps per element (shorter runs for profiling only)")
-    ap.add_argument("--case", default="micro", choices=["micro", "channel", "gp"],
+    ap.add_argument("--case", default="micro", choices=["micro", "channel", "gp", "learned-mean"],
                     help="micro: the uneven micro-element batch (default); channel: the full hybrid "
                          "(Algorithm 1) threshold sweep on the 200-section channel; gp: the GP and "
-                         "MLP timings alone")
+                         "MLP timings alone; learned-mean: the MLP prior mean against the plain GP "
+                         "hybrid at matched thresholds, judged against the MD-everywhere run")
     ap.add_argument("--channel-steps", type=int, default=100)
     ap.add_argument("--form", default="paper", choices=["paper", "linear"],
                     help="channel case: the paper's p-GP and (h, n, F) q-GP inputs (default), or a linear "
@@ -178,6 +179,8 @@ def main():
         return run_reference(args)
     if args.case == "channel":
         return run_channel_case(args)
+    if args.case == "learned-mean":
+        return run_learned_mean_case(args)
     if args.case == "gp":
         import torch
         torch.cuda.set_device(0)
@@ -437,6 +440,33 @@ def run_channel_case(args):
             "reference": {"md_runs": ref["md_runs"], "wall_s": ref["wall_s"]},
             "thermal_noise_error": out.get("noise_error"), "rows": rows}
     print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+def run_learned_mean_case(args):
+    """The learned prior mean (MLP 2 -> 64 -> 64 -> 1 on (h, G)) against the
+    plain GP in the linear-form channel: MD runs and Eq. error against the
+    MD-everywhere run at five thresholds, both arms' hyperparameters by
+    maximum evidence on the same MD database."""
+    import torch
+    from paper_1603_04628_gb300 import cases, native
+    torch.cuda.set_device(0)
+    ctx = native.Context(0, native.PREC_FP32)
+    params = dict(n_sections=200, dx=50.0, h0=12.0, Lx=10.0, Lz=10.0, eos_K=10.0, eos_n0=0.8, dP_amp=400.0,
+                  period=1000.0, dt=20.0, T=1.1, md_steps_eq=2000, md_steps_sample=3000, seed=synth.BASE_SEED,
+                  sn2_from_data=0, inputs=0)
+    t0 = time.perf_counter()
+    thresholds = [0.25, 0.5, 1.0, 2.0, 4.0]
+    rows, info, net = cases.learned_mean_comparison(ctx, thresholds, args.channel_steps, db_elements=256,
+                                                    seed=synth.BASE_SEED + 31, **params)
+    line = {"case": "learned-mean", "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": "200-section channel, linear equation of state, q-GP on (h, G), %d macro "
+                                   "steps, 10 x h x 10 elements (2000 + 3000 steps, FP32 forces); MLP trained on "
+                                   "256 MD runs over h 6-18, G -0.06..0.06" % args.channel_steps},
+            "info": info, "rows": rows, "wall_s": time.perf_counter() - t0}
+    print(json.dumps(line), flush=True)
+    net.close()
     ctx.close()
     return 0
 

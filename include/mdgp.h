@@ -85,8 +85,8 @@ typedef struct {
   double e_drift;  /* (E_end - E_start) / N_atoms, E = kinetic + LJ (shifted) + tether */
   int64_t n_fluid, n_wall;
   int32_t status;  /* MDGP_OK, or MDGP_E_UNSTABLE / _OVERFLOW / _SKIN / _TIMEOUT for this element */
-  int32_t start;   /* how the run started: 0 the lattice (cold), 1 the fluid of a snapshot, 2 the
-                      fluid and walls of a snapshot (mdgp_micro_plan_from) */
+  int32_t start;   /* how the run started: 0 the lattice (cold), 1 a snapshot
+                      (mdgp_micro_plan_from) */
 } mdgp_result;
 
 /* Physics constants shared by all elements of a context. */
@@ -178,20 +178,36 @@ typedef struct {
 } mdgp_start;
 
 /* mdgp_micro_plan with start states (starts may be null: all cold; copied
- * during the call).  A snapshot whose Lx or Lz differ from the element's
- * gives a cold start.  Otherwise the element's fluid starts from the
- * snapshot's: y scaled by h / h_snapshot (the wall planes stay at 0 and h),
- * x and z kept; surplus atoms are removed (those with the smallest Philox
- * key, counter (atom, 0, element id, 2)), missing atoms are inserted at
- * Philox-drawn sites (counter (k, try, element id, 3)) of the slab
- * [0.6, h - 0.6] at least 0.85 from every atom, with Maxwell-Boltzmann
- * velocities at T (counter (atom, 0, element id, 4)) plus the snapshot's
- * mean fluid velocity; a site not found within 20000 tries gives a cold
- * start.  When h and the wall atom count also match, the walls start from
- * the snapshot too.  The tether anchors are the lattice sites either way.
- * mdgp_result.start reports what was used. */
+ * during the call).  A snapshot taken at another h, Lx or Lz, or with
+ * another wall atom count, gives a cold start (the paper starts from the
+ * lattice when the database holds no entry at the channel height).
+ * Otherwise the fluid and the walls start from the snapshot (positions
+ * wrapped into the box in x and z).  Surplus fluid atoms are removed (those
+ * with the smallest Philox key, counter (atom, 0, element id, 2)).  Missing
+ * ones are inserted one at a time: the lowest-energy of 64 Philox-drawn
+ * sites (counter (k, try, element id, 3)) of the slab [0.6, h - 0.6],
+ * steepest descent of the new atom's shifted LJ energy (USHER, De Fabritiis
+ * et al., J. Chem. Phys. 121, 12139 (2004)), then 60 steepest-descent steps
+ * of it and the fluid atoms within 2 sigma (largest move 0.01 sigma a
+ * step); velocities Maxwell-Boltzmann at T (counter (atom, 0, element id,
+ * 4)) plus the snapshot's mean fluid velocity.  The potential energy the
+ * insertions leave above the kept fluid's plus one mean per-atom energy
+ * (sum over its pairs) per new atom is taken out of the fluid's peculiar
+ * kinetic energy (down to a quarter at most).  A new atom left above
+ * 1000 epsilon gives a cold start.  The tether anchors are the lattice
+ * sites either way; mdgp_result.start reports what was used.  Elements are
+ * prepared on up to 16 host threads. */
 int mdgp_micro_plan_from(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, const mdgp_start* starts,
                          int64_t* n_atoms);
+
+/* The start state mdgp_micro_plan_from would give one element, computed on
+ * the host (no device is touched): params may be null (the defaults);
+ * *n_rows receives n_fluid + n_wall.  With xv non-null (cap >= *n_rows
+ * rows of 6 doubles, else MDGP_E_ARG) *kind receives 0 for a cold start
+ * (xv untouched: the lattice is built on the device) or 1 with xv filled
+ * (x y z vx vy vz, fluid first, then walls). */
+int mdgp_start_state(const mdgp_md_params* params, const mdgp_element* el, const mdgp_start* start, double* xv,
+                     int64_t cap, int64_t* n_rows, int32_t* kind);
 
 /* Enqueue the planned batch on the context's stream: build the elements,
  * replay the step graph, reduce the results on the device.  Asynchronous;
@@ -387,6 +403,21 @@ typedef struct {
                                  step keeps so that its means reuse them (0 = 4096; < 0 = keep
                                  none).  A factor not kept is computed again for the means, with
                                  the same result bit for bit. */
+  int32_t warm_start;         /* 1: an MD run starts from the final snapshot of the database entry
+                                 x_in that maximises K(x_in, x*) (Algorithm 1, Sec. 2.4), among the
+                                 entries at the section's height the database held when the step
+                                 began (none: the lattice), through
+                                 mdgp_micro_plan_from, and equilibrates md_steps_eq_warm steps;
+                                 0: every run starts from the lattice (default) */
+  int32_t reserved2;
+  int64_t md_steps_eq_warm;   /* equilibration steps of a warm-started run (0 = md_steps_eq / 4);
+                                 with pseudo_nu > 0 the least of them */
+  double pseudo_nu;           /* > 0: a warm-started run equilibrates for the start-up time t_s
+                                 of mdgp_pseudo_md (Algorithm 1's pseudoMD) from x_in's force to
+                                 x*'s, in MD steps, clamped to [md_steps_eq_warm, md_steps_eq];
+                                 the fluid's kinematic viscosity (LJ units).  0: off (default) */
+  double pseudo_slip;         /* Navier slip length of the walls for pseudoMD */
+  double pseudo_eps_q;        /* pseudoMD's flow-rate tolerance (0 = sqrt(sn2) / 4) */
 } mdgp_macro_params;
 
 /* Time step statistics returned by mdgp_hybrid_step. */
@@ -394,13 +425,14 @@ typedef struct {
   int64_t step;           /* macro steps taken */
   double t;               /* macro time */
   int32_t md_runs;        /* MD runs this step */
-  int32_t reserved;
+  int32_t md_warm;        /* of which started from a snapshot (warm_start) */
   int64_t md_runs_total;
   int64_t db_size;        /* database entries after the step */
   int64_t md_atoms;       /* atoms over this step's MD runs */
   double q_mean;          /* section-averaged flow rate */
   double max_sd;          /* largest predicted standard deviation */
   double gp_seconds, md_seconds;  /* wall time in GP work and in the MD batch */
+  int64_t md_steps_eq_warm;       /* equilibration steps of this step's warm-started runs (0: none) */
 } mdgp_hybrid_stats;
 
 /* Prior mean for the GP (a learned mean): fill out[0..m) at the m rows of
@@ -409,6 +441,22 @@ typedef struct {
 typedef int (*mdgp_mean_fn)(void* user, const double* x, int64_t m, double* out);
 
 int mdgp_macro_params_default(mdgp_macro_params* p);
+
+/* Algorithm 1's pseudoMD (Sec. 2.4: the start-up time t_s of a new MD run
+ * from a 1D Navier-Stokes solution with Navier slip), on the host.  The
+ * streamwise velocity u(y, t) of a channel of height h obeys
+ * du/dt = nu d2u/dy2 + g with u = slip du/dn at both walls (n into the
+ * fluid); it starts at rest (from_rest = 1) or at the steady profile for
+ * force g_from, and g_to drives it.  The flow rate is
+ * Q(t) = q_scale * integral_0^h u dy (q_scale = m n Lz for the elements'
+ * q).  *t_s receives the first time at which |Q(t) - Q_inf| <= eps_q (0
+ * when it holds at t = 0).  Second-order finite differences on 64 cells
+ * (the slip condition through a ghost node), implicit Euler in time with
+ * steps of h^2 / (nu pi^2) / 1000, at most 10^6 of them (then
+ * MDGP_E_LIMIT); Q_inf is the discrete steady state's.  MDGP_E_ARG unless
+ * h, nu, q_scale, eps_q > 0 and slip >= 0. */
+int mdgp_pseudo_md(double h, double nu, double slip, double g_from, double g_to, int32_t from_rest,
+                   double q_scale, double eps_q, double* t_s);
 
 /* New case: densities start at density0 (n_sections values, or eos_n0 when
  * null); empty database.  Uses ctx for the GP and MD work. */

@@ -190,3 +190,70 @@ def speedup(t_end_steps, n_atoms_full, steps_per_sim, n_sims, mean_atoms_per_sim
     if n_sims == 0:
         return math.inf
     return float(t_end_steps * n_atoms_full / (steps_per_sim * n_sims * mean_atoms_per_sim))
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 1's pseudoMD (Sec. 2.4): the start-up time t_s of a new MD run,
+# from the 1D Navier-Stokes (here: unsteady Stokes) solution of a channel of
+# height h with Navier slip, written as its eigenfunction series.
+#
+#   du/dt = nu d2u/dy2 + g,   u = slip du/dn at y = 0 and y = h,
+#
+# started at rest or at the steady profile of force g_from, driven by g_to.
+# The steady profile is u(y) = g / (2 nu) (y (h - y) + slip h); with
+# s = y - h/2 the deviation from it is a sum of cos(lam_k s) exp(-nu lam_k^2 t),
+# theta_k = lam_k h / 2 the roots of theta tan(theta) = h / (2 slip) in
+# (k pi, k pi + pi/2) (theta_k = (2k + 1) pi / 2 without slip).  The flow
+# rate is Q = q_scale * integral_0^h u dy.  READING: the paper names the
+# solver but not its end criterion; t_s is the first time at which
+# |Q(t) - Q_inf| <= eps_q.
+# ---------------------------------------------------------------------------
+def pseudo_md_roots(h, slip, n_modes):
+    """theta_k, k < n_modes: roots of theta tan(theta) = h / (2 slip)."""
+    from scipy.optimize import brentq
+    if slip == 0.0:
+        return np.array([(2 * k + 1) * math.pi / 2 for k in range(n_modes)])
+    bi = h / (2.0 * slip)
+    f = lambda th: th * math.sin(th) - bi * math.cos(th)
+    return np.array([brentq(f, k * math.pi, k * math.pi + math.pi / 2, xtol=1e-15, rtol=1e-15)
+                     for k in range(n_modes)])
+
+
+def pseudo_md_steady_flow(h, nu, slip, g, q_scale):
+    """Q of the steady profile g / (2 nu) (y (h - y) + slip h)."""
+    return q_scale * g / (2.0 * nu) * (h ** 3 / 6.0 + slip * h * h)
+
+
+def pseudo_md_series(h, nu, slip, g_from, g_to, from_rest, q_scale, n_modes=400):
+    """(rates nu lam_k^2, weights w_k): Q(t) - Q_inf = sum_k w_k exp(-rate_k t).
+    Each coefficient is the projection of the initial deviation on the
+    eigenfunction cos(lam_k s) (the eigenfunctions of the Robin problem are
+    orthogonal): the numerator by oscillatory quadrature (QUADPACK's QAWO,
+    scipy's weight='cos'), the norm h/2 + sin(2 theta_k) / (2 lam_k); the
+    eigenfunction's flow-rate integral is 2 sin(theta_k) / lam_k."""
+    from scipy.integrate import quad
+    amp = (-g_to if from_rest else g_from - g_to) / (2.0 * nu)
+    dev = lambda s: amp * (h * h / 4.0 - s * s + slip * h)   # s = y - h/2
+    th = pseudo_md_roots(h, slip, n_modes)
+    lam = 2.0 * th / h
+    w = np.zeros(n_modes)
+    for k in range(n_modes):
+        num = quad(dev, -h / 2.0, h / 2.0, weight="cos", wvar=lam[k], epsabs=1e-15 * abs(amp) * h ** 3,
+                   epsrel=1e-12, limit=200)[0]
+        den = h / 2.0 + math.sin(2.0 * th[k]) / (2.0 * lam[k])
+        w[k] = q_scale * num / den * (2.0 * math.sin(th[k]) / lam[k])
+    return nu * lam ** 2, w
+
+
+def pseudo_md_time(h, nu, slip, g_from, g_to, from_rest, q_scale, eps_q, n_modes=400):
+    """t_s: the first t with |Q(t) - Q_inf| <= eps_q (the deviation decays
+    monotonically: every weight has the sign of the initial deviation)."""
+    from scipy.optimize import brentq
+    rate, w = pseudo_md_series(h, nu, slip, g_from, g_to, from_rest, q_scale, n_modes)
+    dq = lambda t: abs(float(np.sum(w * np.exp(-rate * t))))
+    if dq(0.0) <= eps_q:
+        return 0.0
+    hi = 1.0 / rate[0]
+    while dq(hi) > eps_q:
+        hi *= 2.0
+    return brentq(lambda t: dq(t) - eps_q, 0.0, hi, xtol=1e-14 * hi, rtol=1e-14)

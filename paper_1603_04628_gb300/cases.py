@@ -143,6 +143,52 @@ def learned_mean(ctx, X, y, sigma_n, epochs=2000, lr=3e-3, seed=1):
     return net, sf_res, dict(train_loss=train, holdout_loss=hold, rms_holdout=rms_hold)
 
 
+def evidence_hyperparameters(ctx, X, y, sn2, max_evals=200):
+    """(sf2, l2) of the q-GP by maximum evidence (Sec. 2.3, Eq. evidenceEq)
+    on a database (X, y), sn2 held at the given noise variance."""
+    y = np.asarray(y, dtype=np.float64)
+    sf2 = max(float(np.var(y)), 4.0 * sn2)
+    best = native.gp_optimize(ctx, X, y, sf2, 1.0, sn2, max_evals=max_evals, hold=4)
+    return best["sf2"], best["l2"]
+
+
+def learned_mean_comparison(ctx, thresholds, n_steps, db_elements=256, seed=11, epochs=2000, reference=None,
+                            **params):
+    """The learned prior mean against the plain GP at matched thresholds
+    (benchmark addition to Algorithm 1).  One MD database over the channel's
+    (h, G) range trains the MLP; each arm's (sf2, l2) come from the same
+    rule, maximum evidence with sn2 held at the database's mean squared
+    standard error -- on y for the plain GP, on the residuals y - MLP(X) for
+    the learned mean -- so the two arms differ only by the prior mean.
+    reference: (q history of the sigma_t = 0 run, q history of a second one
+    with other MD seeds) to judge the flow error against and to set the
+    thermal-noise band; run here when not given."""
+    X, y, se = md_database(ctx, db_elements, seed, density=params.get("eos_n0", 0.8), T=params.get("T", 1.1),
+                           Lx=params.get("Lx", 10.0), Lz=params.get("Lz", 10.0),
+                           steps_eq=params.get("md_steps_eq", 2000), steps_sample=params.get("md_steps_sample", 3000))
+    sn2 = float(np.mean(se)) ** 2
+    sf2_p, l2_p = evidence_hyperparameters(ctx, X, y, sn2)
+    net = native.MLP(ctx, seed=seed)
+    train, hold = net.train(X, y, epochs=epochs, lr=3e-3, eval_every=25)
+    sf2_m, l2_m = evidence_hyperparameters(ctx, X, y - net.predict(X), sn2)
+    if reference is None:
+        ref = run_channel(ctx, 0.0, n_steps, **params)["qbar"]
+        ref2 = run_channel(ctx, 0.0, n_steps, **dict(params, seed=params.get("seed", 0) + 1000))["qbar"]
+    else:
+        ref, ref2 = reference
+    noise = error(ref2, ref)
+    rows = []
+    for s in thresholds:
+        a = run_channel(ctx, s, n_steps, **dict(params, sf2=sf2_p, l2=l2_p, sn2=sn2))
+        b = run_channel(ctx, s, n_steps, mlp=net, **dict(params, sf2=sf2_m, l2=l2_m, sn2=sn2))
+        rows.append(dict(sigma_t=s, md_runs_plain=a["md_runs"], md_runs_mlp=b["md_runs"],
+                         error_plain=error(a["qbar"], ref), error_mlp=error(b["qbar"], ref),
+                         wall_plain=a["wall_s"], wall_mlp=b["wall_s"]))
+    info = dict(db_elements=db_elements, sn2=sn2, plain=dict(sf2=sf2_p, l2=l2_p), mlp=dict(sf2=sf2_m, l2=l2_m),
+                mlp_train_loss=train, mlp_holdout_loss=hold, noise_error=noise)
+    return rows, info, net
+
+
 def mlp_comparison(ctx, thresholds, n_steps, net, sf_res, sf_plain, reference_q=None, **params):
     """MD calls and flow error of the plain-GP hybrid against the learned-mean
     hybrid at matched thresholds."""

@@ -16,6 +16,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "mdgp.h"
@@ -35,6 +36,15 @@ struct mdgp_hybrid {
   mdgp_mean_fn mean_fn = nullptr;
   void* mean_user = nullptr;
   mdgp_gp* pgp = nullptr;         // pressure GP over (h, n), if set
+  // final snapshot of each database entry's MD run (warm_start): rows of
+  // (x y z vx vy vz) as floats, fluid first, and the geometry it was taken in
+  struct Snap {
+    std::vector<float> xv;
+    int64_t nf = 0, nw = 0;
+    double h = 0.0;
+    double g = 0.0;   // the run's force per unit mass on the fluid
+  };
+  std::vector<Snap> snaps;
 };
 
 namespace {
@@ -128,6 +138,92 @@ int factor_means(mdgp_hybrid* H, mdgp_gp* g, const std::vector<double>& y, const
   return mdgp_gp_predict(g, Xq, m, H->mean_fn ? mq.data() : nullptr, mean, nullptr);
 }
 
+// Eq. d2Eq scales of the database inputs X (M rows of D): the mean of
+// |x_ik - x_jk| over all pairs i < j, the fallback where it is undefined.
+void host_scales(const mdgp_hybrid* H, const std::vector<double>& X, int64_t M, double* sc) {
+  double fb[3];
+  fallback_scales(H, fb);
+  const int D = H->D;
+  for (int d = 0; d < D; ++d) {
+    double tot = 0.0;
+    for (int64_t i = 0; i < M; ++i)
+      for (int64_t j = i + 1; j < M; ++j) tot += std::fabs(X[(size_t)D * i + d] - X[(size_t)D * j + d]);
+    const double mean = M > 1 ? tot / (0.5 * (double)M * (double)(M - 1)) : 0.0;
+    sc[d] = mean > 0.0 ? mean : fb[d];
+  }
+}
+
+// The entry x_in among the first M database entries with a snapshot taken
+// at channel height h that maximises K(x_in, x*) for the squared-
+// exponential kernel, i.e. the smallest scaled distance (Eq. d2Eq) to x*;
+// -1 when there is none (the run then starts from the lattice).
+int64_t most_correlated(const mdgp_hybrid* H, int64_t M, const double* sc, const double* xs, double h) {
+  int64_t best = -1;
+  double bd = 0.0;
+  for (int64_t i = 0; i < M; ++i) {
+    const mdgp_hybrid::Snap& S = H->snaps[(size_t)i];
+    if (S.xv.empty() || std::fabs(S.h - h) > 1e-9) continue;
+    double d2 = 0.0;
+    for (int d = 0; d < H->D; ++d) {
+      const double t = (H->X[(size_t)H->D * i + d] - xs[d]) / sc[d];
+      d2 += t * t;
+    }
+    if (best < 0 || d2 < bd) { best = i; bd = d2; }
+  }
+  return best;
+}
+
+// One group of MD runs sharing a step count, through the plan / launch /
+// results / state entry points (with mdgp_micro_batch's rerun on list
+// overflow); when keep is set, each run's final state becomes a snapshot.
+int run_group(mdgp_hybrid* H, const std::vector<mdgp_element>& els, const std::vector<mdgp_start>& starts,
+              mdgp_result* res, bool keep, std::vector<mdgp_hybrid::Snap>* out) {
+  mdgp_ctx* ctx = H->ctx;
+  const int64_t n = (int64_t)els.size();
+  const int32_t cap0 = ctx->params.list_capacity;
+  int st = MDGP_OK;
+  for (int attempt = 0; attempt < 3; ++attempt) {
+    int64_t atoms = 0;
+    st = mdgp_micro_plan_from(ctx, els.data(), n, starts.data(), &atoms);
+    if (!st) st = mdgp_micro_launch(ctx);
+    if (!st) st = mdgp_micro_results(ctx, res, n);
+    if (st) break;
+    bool overflow = false;
+    for (int64_t k = 0; k < n; ++k) overflow |= res[k].status == MDGP_E_OVERFLOW;
+    if (!overflow || attempt == 2) {
+      if (keep) {
+        std::vector<double> x((size_t)3 * atoms), v((size_t)3 * atoms);
+        st = mdgp_micro_state(ctx, x.data(), v.data(), atoms);
+        if (st) break;
+        out->resize((size_t)n);
+        int64_t off = 0;
+        for (int64_t k = 0; k < n; ++k) {
+          mdgp_hybrid::Snap& S = (*out)[(size_t)k];
+          S.nf = res[k].n_fluid;
+          S.nw = res[k].n_wall;
+          S.h = els[(size_t)k].h;
+          S.g = els[(size_t)k].density > 0.0 ? els[(size_t)k].g_ext - els[(size_t)k].dpdx / els[(size_t)k].density
+                                               : els[(size_t)k].g_ext;
+          const int64_t m = S.nf + S.nw;
+          S.xv.resize((size_t)6 * m);
+          for (int64_t a = 0; a < m; ++a)
+            for (int d = 0; d < 3; ++d) {
+              S.xv[(size_t)6 * a + d] = (float)x[(size_t)3 * (off + a) + d];
+              S.xv[(size_t)6 * a + 3 + d] = (float)v[(size_t)3 * (off + a) + d];
+            }
+          off += m;
+        }
+      }
+      break;
+    }
+    ctx->params.list_capacity = 2 * (ctx->params.list_capacity > 0 ? ctx->params.list_capacity : 128);
+    ctx->planned = false;
+  }
+  ctx->params.list_capacity = cap0;
+  ctx->planned = false;
+  return st;
+}
+
 // The gate factors of one step; freed when the step ends.
 struct Factors {
   std::vector<mdgp_gp*> g;
@@ -140,6 +236,86 @@ struct Factors {
 }  // namespace
 
 extern "C" {
+
+// Algorithm 1's pseudoMD: the 1D channel-flow start-up with Navier slip
+// (Sec. 2.4), nodes y_i = i h / n, i = 0..n.
+namespace {
+
+// Solve the tridiagonal system a_i x_{i-1} + b_i x_i + c_i x_{i+1} = d_i
+// (Thomas algorithm; a_0 and c_{n-1} unused); d is overwritten by x.
+void thomas(const std::vector<double>& a, const std::vector<double>& b, const std::vector<double>& c,
+            std::vector<double>& d, std::vector<double>& w) {
+  const size_t n = b.size();
+  w.assign(n, 0.0);
+  double beta = b[0];
+  d[0] /= beta;
+  for (size_t i = 1; i < n; ++i) {
+    w[i] = c[i - 1] / beta;
+    beta = b[i] - a[i] * w[i];
+    d[i] = (d[i] - a[i] * d[i - 1]) / beta;
+  }
+  for (size_t i = n - 1; i-- > 0;) d[i] -= w[i + 1] * d[i + 1];
+}
+
+}  // namespace
+
+int mdgp_pseudo_md(double h, double nu, double slip, double g_from, double g_to, int32_t from_rest,
+                   double q_scale, double eps_q, double* t_s) {
+  if (!t_s || !(h > 0) || !(nu > 0) || !(q_scale > 0) || !(eps_q > 0) || !(slip >= 0)) return MDGP_E_ARG;
+  constexpr int n = 64;
+  const double dy = h / n;
+  const double k = nu / (dy * dy);
+  // rows of the operator nu d2/dy2 on u_0..u_n: interior (1, -2, 1) k; a
+  // wall node with slip takes its ghost u_-1 = u_1 - 2 dy u_0 / slip,
+  // giving (2 u_1 - (2 + 2 dy / slip) u_0) k; without slip u_0 = 0
+  std::vector<double> lo(n + 1, k), di(n + 1, -2.0 * k), up(n + 1, k);
+  const bool dirichlet = slip == 0.0;
+  if (!dirichlet) {
+    di[0] = di[n] = -(2.0 + 2.0 * dy / slip) * k;
+    up[0] = 2.0 * k;
+    lo[n] = 2.0 * k;
+  }
+  auto flow = [&](const std::vector<double>& u) {
+    double s = 0.5 * (u[0] + u[n]);
+    for (int i = 1; i < n; ++i) s += u[i];
+    return q_scale * s * dy;
+  };
+  // steady states: nu u'' = -g
+  std::vector<double> w;
+  auto steady = [&](double g, std::vector<double>& u) {
+    std::vector<double> a(lo), b(di), c(up);
+    u.assign(n + 1, -g);
+    if (dirichlet) {
+      b[0] = b[n] = 1.0; c[0] = a[n] = 0.0; u[0] = u[n] = 0.0;
+    }
+    thomas(a, b, c, u, w);
+  };
+  std::vector<double> u, uinf;
+  steady(g_to, uinf);
+  if (from_rest) u.assign(n + 1, 0.0);
+  else steady(g_from, u);
+  const double qinf = flow(uinf);
+  const double tau = h * h / (nu * M_PI * M_PI);
+  const double dt = tau / 1000.0;
+  // implicit Euler: (I - dt A) u' = u + dt g
+  std::vector<double> a(n + 1), b(n + 1), c(n + 1), r(n + 1);
+  for (int i = 0; i <= n; ++i) { a[i] = -dt * lo[i]; b[i] = 1.0 - dt * di[i]; c[i] = -dt * up[i]; }
+  if (dirichlet) { b[0] = b[n] = 1.0; c[0] = a[n] = 0.0; }
+  double t = 0.0;
+  for (long it = 0; it <= 1000000; ++it) {
+    if (std::fabs(flow(u) - qinf) <= eps_q) {
+      *t_s = t;
+      return MDGP_OK;
+    }
+    if (it == 1000000) break;
+    for (int i = 0; i <= n; ++i) r[i] = u[i] + dt * g_to;
+    if (dirichlet) r[0] = r[n] = 0.0;
+    thomas(a, b, c, r, w);
+    u.swap(r);
+    t += dt;
+  }
+  return MDGP_E_LIMIT;
+}
 
 int mdgp_macro_params_default(mdgp_macro_params* p) {
   if (!p) return MDGP_E_ARG;
@@ -163,6 +339,8 @@ int mdgp_macro_params_default(mdgp_macro_params* p) {
   p->sn2 = 0.25;
   p->sn2_from_data = 0;
   p->inputs = 0;
+  p->warm_start = 0;
+  p->md_steps_eq_warm = 0;
   return MDGP_OK;
 }
 
@@ -293,11 +471,25 @@ int mdgp_hybrid_step(mdgp_hybrid* H, double sigma_t, mdgp_hybrid_stats* stats) {
     j0 = j + 1;
   }
   t_gp += now_s() - t0;
-  // one batch of MD elements for the gated sections
+  // one batch of MD elements for the gated sections (two with warm starts:
+  // the runs from snapshots equilibrate for fewer steps)
   const int nmd = (int)md_idx.size();
   std::vector<mdgp_result> res((size_t)nmd);
+  std::vector<mdgp_hybrid::Snap> new_snaps;
+  int n_warm = 0;
+  long long eq_used = 0;
   if (nmd) {
     std::vector<mdgp_element> els((size_t)nmd);
+    std::vector<mdgp_start> starts((size_t)nmd);
+    std::vector<double> sc((size_t)D, 1.0);
+    if (P.warm_start && M0 > 0) host_scales(H, H->X, M0, sc.data());
+    const long long eq_warm = P.md_steps_eq_warm > 0 ? P.md_steps_eq_warm : P.md_steps_eq / 4;
+    // with pseudoMD the warm group equilibrates for the longest start-up
+    // time t_s of its runs (one plan shares its step count), in MD steps,
+    // within [eq_warm, md_steps_eq]
+    const double sn2 = sn2_for_step(H);
+    const double eps_q = P.pseudo_eps_q > 0.0 ? P.pseudo_eps_q : 0.25 * std::sqrt(sn2);
+    long long eq_pseudo = eq_warm;
     for (int k = 0; k < nmd; ++k) {
       const int j = md_idx[k];
       mdgp_element& e = els[k];
@@ -313,9 +505,60 @@ int mdgp_hybrid_step(mdgp_hybrid* H, double sigma_t, mdgp_hybrid_stats* stats) {
       e.g_ext = 0.0;
       e.seed = P.seed;
       e.id = (int32_t)(H->md_total + k);
+      std::memset(&starts[k], 0, sizeof(mdgp_start));
+      if (P.warm_start && M0 > 0) {
+        const int64_t in = most_correlated(H, M0, sc.data(), Xq.data() + (size_t)D * j, H->h[j]);
+        if (in >= 0) {
+          const mdgp_hybrid::Snap& S = H->snaps[(size_t)in];
+          starts[k].xv = S.xv.data();
+          starts[k].n_fluid = S.nf;
+          starts[k].n_wall = S.nw;
+          starts[k].h = S.h;
+          starts[k].Lx = P.Lx;
+          starts[k].Lz = P.Lz;
+          e.steps_eq = eq_warm;
+          if (P.pseudo_nu > 0.0 && eps_q > 0.0) {
+            const double g = e.density > 0.0 ? -e.dpdx / e.density : 0.0;
+            double ts = 0.0;
+            const int ps = mdgp_pseudo_md(e.h, P.pseudo_nu, P.pseudo_slip, S.g, g, 0,
+                                          H->ctx->params.mass * e.density * P.Lz, eps_q, &ts);
+            const long long want = ps == MDGP_OK ? (long long)std::ceil(ts / H->ctx->params.dt) : P.md_steps_eq;
+            eq_pseudo = std::max(eq_pseudo, std::min<long long>(std::max<long long>(want, eq_warm), P.md_steps_eq));
+          }
+        }
+      }
     }
     const double t1 = now_s();
-    int st = mdgp_micro_batch(H->ctx, els.data(), nmd, res.data());
+    int st = MDGP_OK;
+    if (!P.warm_start) {
+      st = mdgp_micro_batch(H->ctx, els.data(), nmd, res.data());
+    } else {
+      // the warm group, then the cold group (a warm start the library
+      // declines runs from the lattice with the warm group's equilibration)
+      new_snaps.resize((size_t)nmd);
+      for (int warm = 1; warm >= 0 && !st; --warm) {
+        std::vector<int> idx;
+        for (int k = 0; k < nmd; ++k)
+          if ((starts[k].xv != nullptr) == (warm == 1)) idx.push_back(k);
+        if (idx.empty()) continue;
+        std::vector<mdgp_element> ge;
+        std::vector<mdgp_start> gs;
+        for (int k : idx) {
+          ge.push_back(els[k]);
+          if (warm) ge.back().steps_eq = eq_pseudo;
+          gs.push_back(starts[k]);
+        }
+        if (warm) eq_used = eq_pseudo;
+        std::vector<mdgp_result> gr(idx.size());
+        std::vector<mdgp_hybrid::Snap> snaps;
+        st = run_group(H, ge, gs, gr.data(), true, &snaps);
+        for (size_t q = 0; q < idx.size() && !st; ++q) {
+          res[(size_t)idx[q]] = gr[q];
+          new_snaps[(size_t)idx[q]] = std::move(snaps[q]);
+          n_warm += gr[q].start > 0 ? 1 : 0;
+        }
+      }
+    }
     t_md += now_s() - t1;
     if (st) return st;
   }
@@ -332,6 +575,8 @@ int mdgp_hybrid_step(mdgp_hybrid* H, double sigma_t, mdgp_hybrid_stats* stats) {
       for (int d = 0; d < D; ++d) H->X.push_back(Xq[(size_t)D * j + d]);
       H->y.push_back(res[k].q);
       H->se.push_back(res[k].q_se);
+      H->snaps.emplace_back();
+      if (P.warm_start) H->snaps.back() = std::move(new_snaps[(size_t)k]);
       if (H->mean_fn) H->mX.push_back(mv[(size_t)M0 + k]);
       ++k;
       ++j;
@@ -373,6 +618,8 @@ int mdgp_hybrid_step(mdgp_hybrid* H, double sigma_t, mdgp_hybrid_stats* stats) {
     stats->step = H->step;
     stats->t = t;
     stats->md_runs = nmd;
+    stats->md_warm = n_warm;
+    stats->md_steps_eq_warm = eq_used;
     stats->md_runs_total = H->md_total;
     stats->db_size = (int64_t)H->y.size();
     double qs = 0.0, mx = 0.0;

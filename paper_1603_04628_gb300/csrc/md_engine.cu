@@ -6,6 +6,7 @@
 #include <cstring>
 #include <map>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "mdgp.h"
@@ -194,30 +195,16 @@ void philox_draw(uint32_t a, uint32_t b, uint32_t elem, uint32_t stream, uint64_
 
 double u01(uint32_t r) { return ((double)r + 0.5) * (1.0 / 4294967296.0); }
 
-// Wall site w of element E (the lattice k_init_atoms builds), absolute.
-void wall_site(const ElemDev& E, int planes, long long w, double& px, double& py, double& pz) {
-  const long long per_plane = 2LL * E.wnx * E.wnz, per_wall = per_plane * planes;
-  const int wall = (int)(w / per_wall);
-  const long long r = w % per_wall;
-  const int k = (int)(r / per_plane);
-  const long long r2 = r % per_plane;
-  const long long i = r2 / (2LL * E.wnz), j = (r2 >> 1) % E.wnz;
-  const int t = (int)(r2 & 1);
-  double ox, oz;
-  if ((k & 1) == 0) { ox = t ? 0.5 : 0.0; oz = t ? 0.5 : 0.0; }
-  else { ox = t ? 0.0 : 0.5; oz = t ? 0.5 : 0.0; }
-  px = ((double)i + ox) * E.wax;
-  py = wall == 0 ? -(double)k * E.wdy : E.h + (double)k * E.wdy;
-  pz = ((double)j + oz) * E.waz;
-}
-
-// Uniform grid over the element (periodic in x and z) for the insertion's
-// distance test.
+// Uniform grid over the element's atoms (periodic in x and z) for the
+// insertion of fluid atoms: the shifted LJ energy (truncated at r_c, pair
+// parameters by species) and force a fluid atom at a site has with the
+// atoms present.
 struct SiteGrid {
   double Lx, Lz, ylo, cs;
   int nx, ny, nz;
   std::vector<std::vector<int>> cell;
   std::vector<double> pos;   // 3 per site
+  std::vector<int> wall;     // species per site
   SiteGrid(double Lx_, double Lz_, double ylo_, double yhi, double side) : Lx(Lx_), Lz(Lz_), ylo(ylo_) {
     nx = std::max(1, (int)std::floor(Lx / side));
     nz = std::max(1, (int)std::floor(Lz / side));
@@ -231,32 +218,79 @@ struct SiteGrid {
     iy = std::min(ny - 1, std::max(0, (int)((y - ylo) / cs)));
     return (ix * ny + iy) * nz + iz;
   }
-  void add(double x, double y, double z) {
+  void add(double x, double y, double z, int is_wall) {
     int ix, iy, iz;
     cell[(size_t)index(x, y, z, ix, iy, iz)].push_back((int)(pos.size() / 3));
     pos.push_back(x); pos.push_back(y); pos.push_back(z);
+    wall.push_back(is_wall);
   }
-  // true when no site lies within dmin of (x, y, z) (minimum image in x, z)
-  bool clear(double x, double y, double z, double dmin) const {
+  void move(int i, double x, double y, double z) {
+    int ix, iy, iz;
+    std::vector<int>& from = cell[(size_t)index(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], ix, iy, iz)];
+    from.erase(std::find(from.begin(), from.end(), i));
+    cell[(size_t)index(x, y, z, ix, iy, iz)].push_back(i);
+    pos[3 * i] = x; pos[3 * i + 1] = y; pos[3 * i + 2] = z;
+  }
+  // the cells of the sites within distance r of (x, y, z), each once
+  // (periodic in x and z; rows outside the grid in y are skipped)
+  template <class Fn>
+  void near_cells(double x, double y, double z, double r, Fn&& fn) const {
     int ix, iy, iz;
     index(x, y, z, ix, iy, iz);
-    const int rx = std::min(nx / 2, 1 + (int)(dmin / (Lx / nx))), rz = std::min(nz / 2, 1 + (int)(dmin / (Lz / nz)));
-    const int ry = 1 + (int)(dmin / cs);
-    for (int dx = -rx; dx <= rx; ++dx)
-      for (int dy = -ry; dy <= ry; ++dy) {
-        const int jy = iy + dy;
-        if (jy < 0 || jy >= ny) continue;
-        for (int dz = -rz; dz <= rz; ++dz) {
-          const int jx = ((ix + dx) % nx + nx) % nx, jz = ((iz + dz) % nz + nz) % nz;
-          for (int s : cell[(size_t)(jx * ny + jy) * nz + jz]) {
-            double ax = x - pos[3 * s], ay = y - pos[3 * s + 1], az = z - pos[3 * s + 2];
-            ax -= Lx * std::floor(ax / Lx + 0.5);
-            az -= Lz * std::floor(az / Lz + 0.5);
-            if (ax * ax + ay * ay + az * az < dmin * dmin) return false;
-          }
+    const int rx = (int)std::ceil(r / (Lx / nx)), rz = (int)std::ceil(r / (Lz / nz)), ry = (int)std::ceil(r / cs);
+    const bool allx = 2 * rx + 1 >= nx, allz = 2 * rz + 1 >= nz;
+    for (int a = allx ? 0 : ix - rx; a <= (allx ? nx - 1 : ix + rx); ++a)
+      for (int jy = std::max(0, iy - ry); jy <= std::min(ny - 1, iy + ry); ++jy)
+        for (int c = allz ? 0 : iz - rz; c <= (allz ? nz - 1 : iz + rz); ++c) {
+          const int jx = (a % nx + nx) % nx, jz = (c % nz + nz) % nz;
+          fn(cell[(size_t)(jx * ny + jy) * nz + jz]);
         }
+  }
+  // shifted LJ pair energy of a fluid atom at (x, y, z) with site s, and
+  // the force on the fluid atom added to f (0 beyond rc)
+  double pair(double x, double y, double z, int s, const mdgp_md_params& p, double f[3]) const {
+    double ax = x - pos[3 * s], ay = y - pos[3 * s + 1], az = z - pos[3 * s + 2];
+    ax -= Lx * std::floor(ax / Lx + 0.5);
+    az -= Lz * std::floor(az / Lz + 0.5);
+    const double r2 = ax * ax + ay * ay + az * az, rc2 = p.rc * p.rc;
+    if (r2 >= rc2) return 0.0;
+    const double eps = wall[s] ? p.eps_wf : 1.0, sig = wall[s] ? p.sig_wf : 1.0;
+    const double s2 = sig * sig / r2, s6 = s2 * s2 * s2;
+    const double c2 = sig * sig / rc2, c6 = c2 * c2 * c2;
+    const double fr = 24.0 * eps * (2.0 * s6 * s6 - s6) / r2;
+    f[0] += fr * ax; f[1] += fr * ay; f[2] += fr * az;
+    return 4.0 * eps * (s6 * s6 - s6) - 4.0 * eps * (c6 * c6 - c6);
+  }
+  // shifted LJ energy of a fluid atom at (x, y, z) with every site within
+  // rc but site self (minimum image in x and z), and the force on it; uw
+  // (if given) receives the part from wall sites
+  double energy(double x, double y, double z, const mdgp_md_params& p, double f[3], int self = -1,
+                double* uw = nullptr) const {
+    double u = 0.0, w = 0.0;
+    f[0] = f[1] = f[2] = 0.0;
+    near_cells(x, y, z, p.rc, [&](const std::vector<int>& c) {
+      for (int s : c) {
+        if (s == self) continue;
+        const double e = pair(x, y, z, s, p, f);
+        u += e;
+        if (wall[s]) w += e;
       }
-    return true;
+    });
+    if (uw) *uw = w;
+    return u;
+  }
+  // the sites but self within distance r of (x, y, z)
+  void within(double x, double y, double z, double r, int self, std::vector<int>& out) const {
+    out.clear();
+    near_cells(x, y, z, r, [&](const std::vector<int>& c) {
+      for (int s : c) {
+        if (s == self) continue;
+        double ax = x - pos[3 * s], ay = y - pos[3 * s + 1], az = z - pos[3 * s + 2];
+        ax -= Lx * std::floor(ax / Lx + 0.5);
+        az -= Lz * std::floor(az / Lz + 0.5);
+        if (ax * ax + ay * ay + az * az < r * r) out.push_back(s);
+      }
+    });
   }
 };
 
@@ -265,7 +299,7 @@ struct SiteGrid {
 // start, 1 when the fluid comes from the snapshot, 2 when the walls do too.
 int adapt_snapshot(const mdgp_md_params& p, const mdgp_element& el, const ElemDev& E, const mdgp_start& S,
                    std::vector<double>& xv) {
-  if (!S.xv || S.n_fluid < 0 || S.n_wall < 0 || !(S.h > 0) || std::fabs(S.Lx - E.Lx) > 1e-9 ||
+  if (!S.xv || S.n_fluid < 0 || S.n_wall != E.nw || std::fabs(S.h - E.h) > 1e-9 || std::fabs(S.Lx - E.Lx) > 1e-9 ||
       std::fabs(S.Lz - E.Lz) > 1e-9)
     return 0;
   const long long nf = E.nf, nw = E.nw, n_old = S.n_fluid;
@@ -288,64 +322,169 @@ int adapt_snapshot(const mdgp_md_params& p, const mdgp_element& el, const ElemDe
   } else {
     for (long long i = 0; i < n_old; ++i) keep.push_back(i);
   }
-  const double sy = E.h / S.h;
   double vm[3] = {0.0, 0.0, 0.0};
   for (size_t k = 0; k < keep.size(); ++k) {
     const float* r = S.xv + 6 * keep[k];
     double* o = xv.data() + 6 * k;
     o[0] = (double)r[0] - E.Lx * std::floor((double)r[0] / E.Lx);
-    o[1] = (double)r[1] * sy;
+    o[1] = (double)r[1];
     o[2] = (double)r[2] - E.Lz * std::floor((double)r[2] / E.Lz);
     for (int d = 0; d < 3; ++d) { o[3 + d] = (double)r[3 + d]; vm[d] += (double)r[3 + d]; }
   }
   if (!keep.empty())
     for (int d = 0; d < 3; ++d) vm[d] /= (double)keep.size();
-  const bool walls = std::fabs(E.h - S.h) < 1e-9 && S.n_wall == nw;
-  // walls: the snapshot's, or the lattice (their velocities then come from the cold start)
   for (long long w = 0; w < nw; ++w) {
+    const float* r = S.xv + 6 * (n_old + w);
     double* o = xv.data() + 6 * (nf + w);
-    if (walls) {
-      const float* r = S.xv + 6 * (n_old + w);
-      for (int d = 0; d < 6; ++d) o[d] = (double)r[d];
-      o[0] -= E.Lx * std::floor(o[0] / E.Lx);
-      o[2] -= E.Lz * std::floor(o[2] / E.Lz);
-    } else {
-      wall_site(E, p.wall_planes, w, o[0], o[1], o[2]);
-    }
+    for (int d = 0; d < 6; ++d) o[d] = (double)r[d];
+    o[0] -= E.Lx * std::floor(o[0] / E.Lx);
+    o[2] -= E.Lz * std::floor(o[2] / E.Lz);
   }
-  // missing fluid atoms: Philox-drawn sites of the slab clear of every atom
+  // missing fluid atoms, one at a time: the lowest-energy of kInsertTries
+  // Philox-drawn sites of the slab (the first at or below 0 ends the draw),
+  // then steepest descent of the new atom's shifted LJ energy with the atoms
+  // present (the USHER scheme of De Fabritiis, Delgado-Buscalioni and
+  // Coveney, J. Chem. Phys. 121, 12139 (2004): steps along the force of
+  // length U/|F|, at most kInsertStep, halved when U rises) until U <= 0 or
+  // kInsertIters steps, then kRelaxIters steepest-descent steps of the new
+  // atom and the fluid atoms within kRelaxR of it together (each atom moves
+  // along its force, the largest move kRelaxStep) so the neighbours make
+  // room; a site above kInsertUMax declines the snapshot.  The potential
+  // energy this leaves above that of the kept fluid plus `add` atoms of its
+  // mean per-atom energy is taken out of the fluid's peculiar kinetic
+  // energy, so the total energy is that of the snapshot's state with nf
+  // atoms and the temperature settles where it was.
   const long long add = nf - (long long)keep.size();
   if (add > 0) {
-    const double dmin = 0.85;
-    SiteGrid grid(E.Lx, E.Lz, E.ylo, E.h - E.ylo, 1.0);
-    for (size_t k = 0; k < keep.size(); ++k) grid.add(xv[6 * k], xv[6 * k + 1], xv[6 * k + 2]);
-    for (long long w = 0; w < nw; ++w) grid.add(xv[6 * (nf + w)], xv[6 * (nf + w) + 1], xv[6 * (nf + w) + 2]);
+    constexpr double kInsertUMax = 1.0e3, kInsertStep = 0.05, kRelaxR = 2.0, kRelaxStep = 0.01;
+    constexpr uint32_t kInsertTries = 64, kInsertIters = 200, kRelaxIters = 60;
+    const int n_keep = (int)keep.size();
+    SiteGrid grid(E.Lx, E.Lz, E.ylo, E.h - E.ylo, p.rc);
+    for (int k = 0; k < n_keep; ++k) grid.add(xv[6 * k], xv[6 * k + 1], xv[6 * k + 2], 0);
+    for (long long w = 0; w < nw; ++w) grid.add(xv[6 * (nf + w)], xv[6 * (nf + w) + 1], xv[6 * (nf + w) + 2], 1);
     const double y0 = 0.6, y1 = E.h - 0.6;
     if (!(y1 > y0)) return 0;
+    // grid index of fluid atom a (kept atoms first, then the walls, then the new atoms)
+    auto gi = [&](long long a) { return (int)(a < n_keep ? a : a + nw); };
+    // potential energy of the fluid (fluid-fluid pairs once, fluid-wall pairs)
+    auto fluid_energy = [&](long long n_fl, double* mean) {
+      double tot = 0.0, sum = 0.0, f[3], w;
+      for (long long a = 0; a < n_fl; ++a) {
+        const int i = gi(a);
+        const double u = grid.energy(grid.pos[3 * i], grid.pos[3 * i + 1], grid.pos[3 * i + 2], p, f, i, &w);
+        tot += 0.5 * (u - w) + w;
+        sum += u;
+      }
+      if (mean) *mean = n_fl > 0 ? sum / (double)n_fl : 0.0;
+      return tot;
+    };
+    double ubar = 0.0;
+    const double pe0 = fluid_energy(n_keep, &ubar);
+    std::vector<int> set;
+    std::vector<std::vector<int>> nbr;
+    std::vector<double> fs, old;
     for (long long k = 0; k < add; ++k) {
-      bool placed = false;
-      for (uint32_t tr = 0; tr < 20000 && !placed; ++tr) {
+      double best = INFINITY, c[3] = {0.0, 0.0, 0.0}, f[3];
+      for (uint32_t tr = 0; tr < kInsertTries && best > 0.0; ++tr) {
         uint32_t r[4];
         philox_draw((uint32_t)k, tr, (uint32_t)el.id, 3u, el.seed, r);
         const double x = u01(r[0]) * E.Lx, y = y0 + u01(r[1]) * (y1 - y0), z = u01(r[2]) * E.Lz;
-        if (!grid.clear(x, y, z, dmin)) continue;
-        const long long a = (long long)keep.size() + k;
-        double* o = xv.data() + 6 * a;
-        o[0] = x; o[1] = y; o[2] = z;
-        uint32_t g[4];
-        philox_draw((uint32_t)a, 0u, (uint32_t)el.id, 4u, el.seed, g);
-        const double two_pi = 6.283185307179586476925286766559;
-        const double rad1 = std::sqrt(-2.0 * std::log(u01(g[0]))), rad2 = std::sqrt(-2.0 * std::log(u01(g[2])));
-        const double n3[3] = {rad1 * std::cos(two_pi * u01(g[1])), rad1 * std::sin(two_pi * u01(g[1])),
-                              rad2 * std::cos(two_pi * u01(g[3]))};
-        for (int d = 0; d < 3; ++d) o[3 + d] = E.vsd * n3[d] + vm[d];
-        grid.add(x, y, z);
-        placed = true;
+        const double u = grid.energy(x, y, z, p, f);
+        if (u < best) { best = u; c[0] = x; c[1] = y; c[2] = z; }
       }
-      if (!placed) return 0;
+      double u = grid.energy(c[0], c[1], c[2], p, f), ds = kInsertStep;
+      for (uint32_t it = 0; it < kInsertIters && u > 0.0 && ds > 1e-6; ++it) {
+        const double fn = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+        if (!(fn > 0.0)) break;
+        const double step = std::min(ds, u / fn);
+        double t[3] = {c[0] + step * f[0] / fn, c[1] + step * f[1] / fn, c[2] + step * f[2] / fn};
+        t[0] -= E.Lx * std::floor(t[0] / E.Lx);
+        t[2] -= E.Lz * std::floor(t[2] / E.Lz);
+        t[1] = std::min(y1, std::max(y0, t[1]));
+        double ft[3];
+        const double ut = grid.energy(t[0], t[1], t[2], p, ft);
+        if (ut < u) {
+          u = ut;
+          for (int d = 0; d < 3; ++d) { c[d] = t[d]; f[d] = ft[d]; }
+        } else {
+          ds = 0.5 * step;
+        }
+      }
+      if (!(u <= kInsertUMax)) return 0;
+      const int g_new = n_keep + (int)nw + (int)k;
+      grid.add(c[0], c[1], c[2], 0);
+      // the new atom and its fluid neighbours relax together
+      grid.within(c[0], c[1], c[2], kRelaxR, g_new, set);
+      set.erase(std::remove_if(set.begin(), set.end(), [&](int i) { return grid.wall[i] != 0; }), set.end());
+      set.insert(set.begin(), g_new);
+      old.resize(3 * set.size());
+      for (size_t m = 0; m < set.size(); ++m)
+        for (int d = 0; d < 3; ++d) old[3 * m + d] = grid.pos[3 * set[m] + d];
+      // the sites each set member can reach within rc while both move at
+      // most kRelaxIters * kRelaxStep
+      const double reach = p.rc + 2.0 * kRelaxIters * kRelaxStep;
+      nbr.resize(set.size());
+      for (size_t m = 0; m < set.size(); ++m) {
+        const int i = set[m];
+        grid.within(grid.pos[3 * i], grid.pos[3 * i + 1], grid.pos[3 * i + 2], reach, i, nbr[m]);
+      }
+      fs.resize(3 * set.size());
+      for (uint32_t it = 0; it < kRelaxIters; ++it) {
+        double fmax = 0.0;
+        for (size_t m = 0; m < set.size(); ++m) {
+          const int i = set[m];
+          double* fm = &fs[3 * m];
+          fm[0] = fm[1] = fm[2] = 0.0;
+          for (int sidx : nbr[m]) grid.pair(grid.pos[3 * i], grid.pos[3 * i + 1], grid.pos[3 * i + 2], sidx, p, fm);
+          fmax = std::max(fmax, std::sqrt(fm[0] * fm[0] + fm[1] * fm[1] + fm[2] * fm[2]));
+        }
+        if (!(fmax > 0.0)) break;
+        const double alpha = kRelaxStep / fmax;
+        for (size_t m = 0; m < set.size(); ++m) {
+          const int i = set[m];
+          double x = grid.pos[3 * i] + alpha * fs[3 * m], z = grid.pos[3 * i + 2] + alpha * fs[3 * m + 2];
+          x -= E.Lx * std::floor(x / E.Lx);
+          z -= E.Lz * std::floor(z / E.Lz);
+          grid.pos[3 * i] = x;
+          grid.pos[3 * i + 1] += alpha * fs[3 * m + 1];
+          grid.pos[3 * i + 2] = z;
+        }
+      }
+      // the moved atoms to their new cells
+      for (size_t m = 0; m < set.size(); ++m) {
+        const int i = set[m];
+        const double x = grid.pos[3 * i], y = grid.pos[3 * i + 1], z = grid.pos[3 * i + 2];
+        grid.pos[3 * i] = old[3 * m]; grid.pos[3 * i + 1] = old[3 * m + 1]; grid.pos[3 * i + 2] = old[3 * m + 2];
+        grid.move(i, x, y, z);
+      }
+      const long long a = (long long)n_keep + k;
+      double* o = xv.data() + 6 * a;
+      uint32_t g[4];
+      philox_draw((uint32_t)a, 0u, (uint32_t)el.id, 4u, el.seed, g);
+      const double two_pi = 6.283185307179586476925286766559;
+      const double rad1 = std::sqrt(-2.0 * std::log(u01(g[0]))), rad2 = std::sqrt(-2.0 * std::log(u01(g[2])));
+      const double n3[3] = {rad1 * std::cos(two_pi * u01(g[1])), rad1 * std::sin(two_pi * u01(g[1])),
+                            rad2 * std::cos(two_pi * u01(g[3]))};
+      for (int d = 0; d < 3; ++d) o[3 + d] = E.vsd * n3[d] + vm[d];
+    }
+    // relaxed positions back, then the energy bookkeeping on the peculiar
+    // kinetic energy (unit mass), scaled down at most to a quarter of itself
+    for (long long a = 0; a < nf; ++a)
+      for (int d = 0; d < 3; ++d) xv[6 * a + d] = grid.pos[3 * gi(a) + d];
+    const double excess = fluid_energy(nf, nullptr) - pe0 - (double)add * ubar;
+    double kin = 0.0;
+    for (long long a = 0; a < nf; ++a)
+      for (int d = 0; d < 3; ++d) kin += 0.5 * (xv[6 * a + 3 + d] - vm[d]) * (xv[6 * a + 3 + d] - vm[d]);
+#ifdef DEBUG_ADAPT
+    fprintf(stderr, "ubar %.3f excess %.2f (%.2f per atom) kin %.1f\n", ubar, excess, excess / add, kin);
+#endif
+    if (kin > 0.0) {
+      const double s = std::sqrt(std::max(0.25, (kin - excess) / kin));
+      for (long long a = 0; a < nf; ++a)
+        for (int d = 0; d < 3; ++d) xv[6 * a + 3 + d] = vm[d] + s * (xv[6 * a + 3 + d] - vm[d]);
     }
   }
-  return walls ? 2 : 1;
+  return 1;
 }
 
 }  // namespace
@@ -683,19 +822,30 @@ static int plan_impl(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int list_
   aoff[n] = atoms;
   coff[n] = cells;
   // start states from snapshots, prepared on the host (copied to the device below)
+  // (elements in parallel on host threads; each writes its own rows)
   std::vector<double> warm;
   bool any_warm = false;
-  if (starts) {
-    for (int64_t i = 0; i < n; ++i) {
-      if (!starts[i].xv) continue;
+  std::vector<int64_t> from;
+  for (int64_t i = 0; starts && i < n; ++i)
+    if (starts[i].xv) from.push_back(i);
+  if (!from.empty()) {
+    warm.assign((size_t)6 * atoms, 0.0);
+    const int nt = (int)std::min<int64_t>((int64_t)from.size(),
+                                          std::max(1u, std::min(16u, std::thread::hardware_concurrency())));
+    auto work = [&](int t) {
       std::vector<double> xv;
-      const int w = adapt_snapshot(ctx->params, el[i], Es[i], starts[i], xv);
-      Es[i].warm = w;
-      if (!w) continue;
-      if (!any_warm) warm.assign((size_t)6 * atoms, 0.0);
-      any_warm = true;
-      std::copy(xv.begin(), xv.end(), warm.begin() + 6 * Es[i].atom0);
-    }
+      for (size_t q = (size_t)t; q < from.size(); q += (size_t)nt) {
+        const int64_t i = from[q];
+        Es[i].warm = adapt_snapshot(ctx->params, el[i], Es[i], starts[i], xv);
+        if (Es[i].warm) std::copy(xv.begin(), xv.end(), warm.begin() + 6 * Es[i].atom0);
+      }
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nt; ++t) pool.emplace_back(work, t);
+    work(0);
+    for (std::thread& th : pool) th.join();
+    for (int64_t i : from) any_warm |= Es[i].warm != 0;
+    if (!any_warm) std::vector<double>().swap(warm);
   }
   if (atoms >= (1LL << 31) - 1) {
     std::snprintf(ctx->err, sizeof(ctx->err), "batch too large (2^31 atoms max)");
@@ -1061,13 +1211,16 @@ int mdgp_destroy(mdgp_ctx* ctx) {
   return MDGP_OK;
 }
 
+static bool params_valid(const mdgp_md_params* p) {
+  return p->dt > 0 && p->rc > 0 && p->n_blocks >= 1 && p->wall_planes >= 1 && p->mass > 0 &&
+         p->wall_density > 0 && p->gamma_wall >= 0 && p->list_capacity >= 0 && p->skin >= 0 &&
+         p->rebuild_every >= 0 && (p->build_variant == 0 || p->build_variant == 3) && p->persistent >= 0 &&
+         p->persistent <= 2;
+}
+
 int mdgp_set_md_params(mdgp_ctx* ctx, const mdgp_md_params* p) {
   if (!ctx || !p) return MDGP_E_ARG;
-  if (!(p->dt > 0) || !(p->rc > 0) || p->n_blocks < 1 || p->wall_planes < 1 || !(p->mass > 0) ||
-      !(p->wall_density > 0) || p->gamma_wall < 0 || p->list_capacity < 0 || !(p->skin >= 0) ||
-      p->rebuild_every < 0 || (p->build_variant != 0 && p->build_variant != 3) || p->persistent < 0 ||
-      p->persistent > 2)
-    return MDGP_E_ARG;
+  if (!params_valid(p)) return MDGP_E_ARG;
   ctx->params = *p;
   ctx->planned = false;
   return MDGP_OK;
@@ -1095,6 +1248,26 @@ int mdgp_micro_plan_from(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, const
   int st = plan_impl(ctx, el, n, 0, starts);
   if (st == MDGP_OK && n_atoms) *n_atoms = ctx->n_atoms;
   return st;
+}
+
+int mdgp_start_state(const mdgp_md_params* params, const mdgp_element* el, const mdgp_start* start, double* xv,
+                     int64_t cap, int64_t* n_rows, int32_t* kind) {
+  if (!el || !start || !n_rows || !kind) return MDGP_E_ARG;
+  mdgp_md_params p;
+  if (params) p = *params;
+  else mdgp_md_params_default(&p);
+  if (!params_valid(&p)) return MDGP_E_ARG;
+  ElemDev E;
+  std::string why;
+  const int st = describe(p, *el, E, &why);
+  if (st) return st;
+  *n_rows = (int64_t)E.nf + E.nw;
+  if (!xv) return MDGP_OK;
+  if (cap < *n_rows) return MDGP_E_ARG;
+  std::vector<double> out;
+  *kind = start->xv ? adapt_snapshot(p, *el, E, *start, out) : 0;
+  if (*kind) std::copy(out.begin(), out.end(), xv);
+  return MDGP_OK;
 }
 
 int mdgp_micro_launch(mdgp_ctx* ctx) {

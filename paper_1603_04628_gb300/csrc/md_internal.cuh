@@ -74,7 +74,7 @@ struct ElemDev {
   int wnx, wnz;
   int nc[3];           // cell grid
   int id;
-  int warm;            // 0 cold start; 1 fluid from a snapshot; 2 fluid and walls
+  int warm;            // 0 cold start (lattice); 1 fluid and walls from a snapshot
   int nb;              // blocks actually used
   float csf[3];        // cell sizes as float
   float cs_lo[3];      // cs - csf: the cell sizes as double-float numbers
@@ -137,7 +137,7 @@ struct BatchDev {
                                   // 64-bit arrival count
   double* tz;                     // [2 * n_el] per-element sum of m v_z^2 (two step-parity slots)
   const double* warm;             // [6 * n_atoms] start state (x y z vx vy vz, absolute, original
-                                  // order) of the atoms of elements with warm > 0
+                                  // order) of the atoms of elements with warm != 0
 };
 
 // integration kernel phases: kFinish = second half kick (+ measurement unless

@@ -386,18 +386,16 @@ __global__ void k_init_fix(BatchDev B, PhysDev P) {
   st_put<DF>(B.st[3], a, vx); st_put<DF>(B.st[4], a, vy); st_put<DF>(B.st[5], a, vz);
 }
 
-// Start states from snapshots (elements with warm > 0): overwrite the
-// fluid's (and with warm == 2 the walls') lattice positions and velocities
-// by the prepared state; the tether anchors stay the lattice sites.  Runs
-// after k_init_fix, while the atoms are still in original order.
+// Start states from snapshots (elements with warm != 0): overwrite the
+// lattice positions and velocities of the fluid and the walls by the
+// prepared state; the tether anchors stay the lattice sites.  Runs after
+// k_init_fix, while the atoms are still in original order.
 template <bool DF>
 __global__ void k_apply_warm(BatchDev B) {
   const long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (a >= B.n_atoms) return;
   const ElemDev& E = B.el[B.atom_el[a]];
   if (E.warm == 0) return;
-  const long long l = a - E.atom0;
-  if (l >= E.nf && E.warm < 2) return;
   const double* w = B.warm + 6 * a;
   st_put<DF>(B.st[0], a, w[0]); st_put<DF>(B.st[1], a, w[1]); st_put<DF>(B.st[2], a, w[2]);
   st_put<DF>(B.st[3], a, w[3]); st_put<DF>(B.st[4], a, w[4]); st_put<DF>(B.st[5], a, w[5]);

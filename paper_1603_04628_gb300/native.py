@@ -62,14 +62,17 @@ class MacroParams(ctypes.Structure):
                 ("period", ctypes.c_double), ("dt", ctypes.c_double), ("T", ctypes.c_double),
                 ("md_steps_eq", ctypes.c_int64), ("md_steps_sample", ctypes.c_int64), ("seed", ctypes.c_uint64),
                 ("sf2", ctypes.c_double), ("l2", ctypes.c_double), ("sn2", ctypes.c_double),
-                ("inputs", ctypes.c_int32), ("factor_cache_mb", ctypes.c_int32)]
+                ("inputs", ctypes.c_int32), ("factor_cache_mb", ctypes.c_int32),
+                ("warm_start", ctypes.c_int32), ("reserved2", ctypes.c_int32), ("md_steps_eq_warm", ctypes.c_int64),
+                ("pseudo_nu", ctypes.c_double), ("pseudo_slip", ctypes.c_double), ("pseudo_eps_q", ctypes.c_double)]
 
 
 class HybridStats(ctypes.Structure):
     _fields_ = [("step", ctypes.c_int64), ("t", ctypes.c_double), ("md_runs", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("md_runs_total", ctypes.c_int64), ("db_size", ctypes.c_int64),
+                ("md_warm", ctypes.c_int32), ("md_runs_total", ctypes.c_int64), ("db_size", ctypes.c_int64),
                 ("md_atoms", ctypes.c_int64), ("q_mean", ctypes.c_double), ("max_sd", ctypes.c_double),
-                ("gp_seconds", ctypes.c_double), ("md_seconds", ctypes.c_double)]
+                ("gp_seconds", ctypes.c_double), ("md_seconds", ctypes.c_double),
+                ("md_steps_eq_warm", ctypes.c_int64)]
 
 
 MEAN_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int64,
@@ -99,6 +102,12 @@ def lib():
     L = ctypes.CDLL(LIB_PATH)
     vp, i64, dp = ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)
     sig = {
+        "mdgp_start_state": ([ctypes.POINTER(MDParams), ctypes.POINTER(Element), ctypes.POINTER(Start),
+                              ctypes.POINTER(ctypes.c_double), ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
+                              ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+        "mdgp_pseudo_md": ([ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                            ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double)],
+                           ctypes.c_int),
         "mdgp_md_params_default": ([ctypes.POINTER(MDParams)], ctypes.c_int),
         "mdgp_create": ([ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "mdgp_destroy": ([vp], ctypes.c_int),
@@ -196,6 +205,45 @@ def md_params_default():
     return p
 
 
+def _start(s, st, keep):
+    """Fill the Start struct st from a snapshot dict (xv rows, n_fluid,
+    n_wall, h, Lx, Lz); keep holds the float32 copy alive."""
+    xv = np.ascontiguousarray(s["xv"], dtype=np.float32)
+    keep.append(xv)
+    st.xv = xv.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+    st.n_fluid, st.n_wall = int(s["n_fluid"]), int(s["n_wall"])
+    st.h, st.Lx, st.Lz = float(s["h"]), float(s["Lx"]), float(s["Lz"])
+
+
+def pseudo_md(h, nu, slip, g_from, g_to, from_rest, q_scale, eps_q):
+    """mdgp_pseudo_md (host only): Algorithm 1's start-up time t_s."""
+    t = ctypes.c_double()
+    _check(None, lib().mdgp_pseudo_md(float(h), float(nu), float(slip), float(g_from), float(g_to),
+                                      int(bool(from_rest)), float(q_scale), float(eps_q), ctypes.byref(t)),
+           "mdgp_pseudo_md")
+    return t.value
+
+
+def start_state(el, snap, **md_params):
+    """mdgp_start_state (host only): the start state mdgp_micro_plan_from
+    gives element el from snapshot snap; returns (rows x 6 array, 1) or
+    (None, 0) for a cold start."""
+    p = md_params_default()
+    for k, v in md_params.items():
+        setattr(p, k, v)
+    e = to_element(el)
+    st, keep = Start(), []
+    _start(snap, st, keep)
+    rows, kind = ctypes.c_int64(), ctypes.c_int32(0)
+    _check(None, lib().mdgp_start_state(ctypes.byref(p), ctypes.byref(e), ctypes.byref(st), None, 0,
+                                        ctypes.byref(rows), ctypes.byref(kind)), "mdgp_start_state")
+    out = np.zeros((rows.value, 6))
+    _check(None, lib().mdgp_start_state(ctypes.byref(p), ctypes.byref(e), ctypes.byref(st),
+                                        out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), rows.value,
+                                        ctypes.byref(rows), ctypes.byref(kind)), "mdgp_start_state")
+    return (out, 1) if kind.value else (None, 0)
+
+
 class Context:
     """Owns one mdgp_ctx (device buffers, stream, captured graphs)."""
 
@@ -254,13 +302,8 @@ class Context:
         st = (Start * len(els))()
         keep = []
         for k, s in enumerate(starts):
-            if s is None:
-                continue
-            xv = np.ascontiguousarray(s["xv"], dtype=np.float32)
-            keep.append(xv)
-            st[k].xv = xv.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
-            st[k].n_fluid, st[k].n_wall = int(s["n_fluid"]), int(s["n_wall"])
-            st[k].h, st[k].Lx, st[k].Lz = float(s["h"]), float(s["Lx"]), float(s["Lz"])
+            if s is not None:
+                _start(s, st[k], keep)
         n = ctypes.c_int64()
         _check(self.h, lib().mdgp_micro_plan_from(self.h, arr, len(els), st, ctypes.byref(n)), "mdgp_micro_plan_from")
         self._n_el = len(els)

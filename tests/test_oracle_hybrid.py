@@ -152,3 +152,61 @@ def test_pressure_gradient_and_forcing_by_hand():
     assert md.make_params(el).g == pytest.approx(2.0 / 0.9, rel=1e-14)
     # no forcing at t = 0 and half a period
     np.testing.assert_allclose(c.gradients(0.0), [0.02, 0.0, -0.02, 0.0], rtol=1e-13, atol=1e-15)
+
+
+# --- Algorithm 1's pseudoMD (Sec. 2.4): closed forms of the start-up ---
+
+def test_pseudo_md_no_slip_first_mode_and_weight():
+    # without slip the slowest mode decays at nu pi^2 / h^2 and carries
+    # 96 / pi^4 of a start-up from rest (sum over odd k of 96 / (pi k)^4 = 1)
+    h, nu = 8.0, 2.5
+    rate, w = hybrid.pseudo_md_series(h, nu, 0.0, 0.0, 0.02, True, 80.0)
+    assert rate[0] == pytest.approx(nu * math.pi ** 2 / h ** 2, rel=1e-14)
+    assert rate[1] == pytest.approx(9.0 * nu * math.pi ** 2 / h ** 2, rel=1e-14)
+    assert w[0] / w.sum() == pytest.approx(96.0 / math.pi ** 4, rel=1e-8)
+    assert w[1] / w.sum() == pytest.approx(96.0 / (3.0 * math.pi) ** 4, rel=1e-6)
+
+
+@pytest.mark.parametrize("slip", [0.0, 0.7, 3.0])
+def test_pseudo_md_series_starts_at_the_initial_flow_rate(slip):
+    # completeness: at t = 0 the series gives Q(0) - Q_inf with the steady
+    # flow rate q_scale g (h^3 / 6 + slip h^2) / (2 nu), from rest and from
+    # another force
+    h, nu, qs = 6.0, 1.7, 55.0
+    for g_from, g_to, rest in ((0.0, 0.03, True), (0.01, 0.03, False), (0.05, -0.02, False)):
+        _, w = hybrid.pseudo_md_series(h, nu, slip, g_from, g_to, rest, qs)
+        q0 = 0.0 if rest else qs * g_from * (h ** 3 / 6 + slip * h * h) / (2 * nu)
+        qinf = qs * g_to * (h ** 3 / 6 + slip * h * h) / (2 * nu)
+        assert hybrid.pseudo_md_steady_flow(h, nu, slip, g_to, qs) == pytest.approx(qinf, rel=1e-15)
+        assert w.sum() == pytest.approx(q0 - qinf, rel=1e-7)
+
+
+def test_pseudo_md_eigenvalues_solve_the_slip_condition():
+    # u = slip du/dn with u = cos(lam (y - h/2)): cos(theta) = (2 slip / h) theta sin(theta)
+    h, slip = 7.0, 0.9
+    th = hybrid.pseudo_md_roots(h, slip, 30)
+    resid = np.cos(th) - 2 * slip / h * th * np.sin(th)
+    assert np.abs(resid / (1 + th)).max() < 1e-14
+    assert np.all(np.diff(th) > 0) and np.all((th > np.arange(30) * math.pi) & (th < np.arange(30) * math.pi + math.pi / 2))
+
+
+def test_pseudo_md_plug_flow_limit():
+    # large slip: the flow is a plug that wall friction slows, dU/dt = -2 nu U / (h slip);
+    # the next order of theta tan(theta) = Bi in Bi = h / (2 slip) divides the rate by 1 + Bi / 3
+    h, nu, slip = 8.0, 2.5, 400.0
+    rate, w = hybrid.pseudo_md_series(h, nu, slip, 0.0, 0.02, True, 80.0)
+    assert rate[0] == pytest.approx(2 * nu / (h * slip), rel=5e-3)
+    assert rate[0] == pytest.approx(2 * nu / (h * slip) / (1 + h / (6 * slip)), rel=1e-4)
+    assert w[0] / w.sum() == pytest.approx(1.0, abs=1e-5)
+
+
+def test_pseudo_md_time_no_slip_closed_form():
+    # late start-up from rest without slip: |Q - Q_inf| ~ Q_inf (96/pi^4) exp(-nu pi^2 t / h^2)
+    h, nu, qs, g = 10.0, 2.0, 80.0, 0.02
+    qinf = hybrid.pseudo_md_steady_flow(h, nu, 0.0, g, qs)
+    eps = 1e-4 * qinf
+    t = hybrid.pseudo_md_time(h, nu, 0.0, 0.0, g, True, qs, eps)
+    t_first = h ** 2 / (nu * math.pi ** 2) * math.log(96 / math.pi ** 4 * qinf / eps)
+    assert t == pytest.approx(t_first, rel=1e-6)
+    # nothing to wait for when the forces agree
+    assert hybrid.pseudo_md_time(h, nu, 0.5, g, g, False, qs, eps) == 0.0
