@@ -37,14 +37,28 @@ ALG_FLOPS_PER_ATOM_STEP = 600.0      # 26.2 unique pairs x ~23 FP32 flops (Newto
                                      # the integration's few flops per atom are not counted
 ALG_BYTES_PER_ATOM_STEP = 96.0       # FP64 x and v read and written once per step
 CPU_SAMPLE_STEPS = 1000              # oracle steps per sampled element (~10-20 s of CPU work)
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_step_df launch on this
-# workload (ncu capture, cold cache, 400 steps per element)
-STEP_KERNEL_TRAFFIC_BYTES = 73.9e6
 FP64_PEAK_TFLOPS = 0.99              # FP64 FMA chain measured on this GB300
-# the same capture's l1tex throughput and issue-active fractions (the pair
-# loop is a gather: L1 and instruction issue bind, not FP32 arithmetic)
-STEP_KERNEL_L1_FRAC = 0.608
-STEP_KERNEL_ISSUE_FRAC = 0.523
+# ncu counters of the persistent step kernel on this workload, written with
+# the capture's command into the profile summary (a "counters:" JSON line);
+# used only while the kernel source still has the hash recorded there
+STEP_PROFILE = os.path.join(ROOT, "profiles", "k_steps_persist_uneven64.md")
+STEP_SOURCE = os.path.join(ROOT, "paper_1603_04628_gb300", "csrc", "md_kernels.cuh")
+
+
+def step_kernel_counters():
+    """The profile's counters dict, or None when the file is missing or the
+    kernel source changed since the capture."""
+    import hashlib
+    try:
+        with open(STEP_PROFILE) as fh:
+            line = next(l for l in fh if l.startswith("counters: "))
+        c = json.loads(line[len("counters: "):])
+        with open(STEP_SOURCE, "rb") as fh:
+            if hashlib.sha256(fh.read()).hexdigest() != c.get("source_sha256"):
+                return None
+        return c
+    except (OSError, StopIteration, ValueError):
+        return None
 
 
 def _oracle_element_steps(args):
@@ -267,12 +281,25 @@ def main():
         ms = float(t.item())
     value = units * world / (ms / 1e3)
 
-    # per-kernel durations (CUDA events on the context's stream) for the roofline
+    # per-kernel durations (CUDA events on the context's stream) for the
+    # roofline: the persistent step kernel launched by the host once per
+    # list-rebuild interval (the timed run's kernel, outside its graph), and
+    # the one-launch-per-step kernel of the same step code
+    path = ctx.path()
     prof = ctx.micro_profile(min(200, steps_el))
-    force_s = prof["force_ms"] / 1e3
+    cdir = native.Context(local, native.PREC_FP32, stream=stream, persistent=2, list_capacity=cap)
+    cdir.micro_plan(els)
+    cdir.micro_launch()
+    cdir.micro_results()
+    cdir.micro_launch()
+    cdir.micro_results()
+    dt = cdir.direct_timing()
+    cdir.close()
+    persist_step_s = dt["kernel_ms"] / 1e3 / max(1, dt["steps"])
     sm_mhz = (clocks or {}).get("sm_max_mhz", 2070.0) or 2070.0
     fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-    achieved = ALG_FLOPS_PER_ATOM_STEP * n_atoms / force_s / 1e12
+    achieved = ALG_FLOPS_PER_ATOM_STEP * n_atoms / persist_step_s / 1e12
+    counters = step_kernel_counters() if args.workload == "uneven" else None
 
     # end to end through the public API: host descriptors in, host results out
     e2e_times = []
@@ -329,21 +356,26 @@ def main():
                        "elements": len(els), "atoms_per_rank": n_atoms, "steps_per_element": steps_el,
                        "l2": "flushed between timed iterations (256 MB write)",
                        "parallelism": "independent elements per rank" if world > 1 else "1 GPU"},
-            "roofline": {"bound": "alu", "kernel": "k_step_df (pair forces + integration, one launch per step)",
+            "roofline": {"bound": "alu", "kernel": "k_steps_persist (pair forces + integration of every step "
+                                                 "of a list-rebuild interval, a grid barrier between steps)",
                          "achieved": achieved, "peak": fp32_peak,
                          "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                         "traffic": STEP_KERNEL_TRAFFIC_BYTES if args.workload == "uneven" else None,
-                         "l1_frac": STEP_KERNEL_L1_FRAC if args.workload == "uneven" else None,
-                         "issue_frac": STEP_KERNEL_ISSUE_FRAC if args.workload == "uneven" else None,
+                         "traffic": counters["dram_bytes_per_step"] if counters else None,
+                         "l1_frac": counters["l1tex_throughput_frac"] if counters else None,
+                         "issue_frac": counters["issue_active_frac"] if counters else None,
+                         "counters_from": os.path.relpath(STEP_PROFILE, ROOT) if counters else None,
                          "peak_note": FP32_PEAK_NOTE + " (derived, max SM clock)",
                          "alg_flops_per_atom_step": ALG_FLOPS_PER_ATOM_STEP,
-                         "force_ms": prof["force_ms"], "integrate_ms": prof["integrate_ms"],
-                         "timing": "one k_step_df launch (= one MD step of the batch) timed with CUDA "
-                                   "events on the context's stream; the timed run executes the same "
-                                   "per-step code inside the persistent k_steps_persist",
-                         "persistent_step_us": (ms * 1e3 - rebuilds_per_step * prof["rebuild_ms"] * 1e3)
-                                               / steps_el,
-                         "rebuilds_per_run": rebuilds_per_step, "rebuild_ms": prof["rebuild_ms"]},
+                         "timing": "k_steps_persist launched by the host once per list-rebuild interval "
+                                   "(persistent = 2), CUDA events around each launch on the context's "
+                                   "stream, %d launches covering %d steps of the same batch"
+                                   % (dt["launches"], dt["steps"]),
+                         "persistent_step_us": persist_step_s * 1e6,
+                         "per_step_launch_us": prof["force_ms"] * 1e3,
+                         "persistent_minus_per_launch_us": persist_step_s * 1e6 - prof["force_ms"] * 1e3,
+                         "rebuilds_per_run": rebuilds_per_step, "rebuild_ms": prof["rebuild_ms"],
+                         "rebuild_share": rebuilds_per_step * prof["rebuild_ms"] / ms},
+            "path": path,
             "hbm_roofline": {"alg_bytes_per_atom_step": ALG_BYTES_PER_ATOM_STEP,
                              "achieved_gbs": value / world * ALG_BYTES_PER_ATOM_STEP / 1e9,
                              "peak_gbs": _peak_hbm(), "frac": value / world * ALG_BYTES_PER_ATOM_STEP / 1e9 /
@@ -459,7 +491,7 @@ def run_learned_mean_case(args):
     t0 = time.perf_counter()
     thresholds = [0.25, 0.5, 1.0, 2.0, 4.0]
     rows, info, net = cases.learned_mean_comparison(ctx, thresholds, args.channel_steps, db_elements=256,
-                                                    seed=synth.BASE_SEED + 31, **params)
+                                                    db_seed=synth.BASE_SEED + 31, **params)
     line = {"case": "learned-mean", "n_gpus": 1, "data": "synthetic",
             "config": {"workload": "200-section channel, linear equation of state, q-GP on (h, G), %d macro "
                                    "steps, 10 x h x 10 elements (2000 + 3000 steps, FP32 forces); MLP trained on "

@@ -227,6 +227,15 @@ int64_t mdgp_micro_launch_count(const mdgp_ctx* ctx);
  * kernel launched by the host.  MDGP_E_STATE without a plan. */
 int mdgp_micro_path(const mdgp_ctx* ctx);
 
+/* With persistent = 2 (the host launches the persistent step kernel once
+ * per list-rebuild interval): CUDA-event times of the last batch's
+ * launches on the context's stream.  out[0] = total milliseconds inside
+ * the persistent kernel, out[1] = the steps those launches ran, out[2] =
+ * the launches, out[3] = total milliseconds of the rebuilds between them,
+ * out[4] = those rebuilds.  MDGP_E_STATE unless the planned batch runs on
+ * that path. */
+int mdgp_micro_direct_timing(const mdgp_ctx* ctx, double* out);
+
 /* Number of neighbour-list rebuilds the last batch ran (valid after
  * mdgp_micro_results).  A rebuild runs when some atom has moved more than
  * half the skin since the previous one. */
@@ -453,8 +462,10 @@ int mdgp_macro_params_default(mdgp_macro_params* p);
  * when it holds at t = 0).  Second-order finite differences on 64 cells
  * (the slip condition through a ghost node), implicit Euler in time with
  * steps of h^2 / (nu pi^2) / 1000, at most 10^6 of them (then
- * MDGP_E_LIMIT); Q_inf is the discrete steady state's.  MDGP_E_ARG unless
- * h, nu, q_scale, eps_q > 0 and slip >= 0. */
+ * MDGP_E_LIMIT); Q_inf is the discrete steady state's.  A negative slip
+ * places no-slip planes -slip inside each wall (the fluid between them and
+ * the wall at rest): the flowing width is h + 2 slip.  MDGP_E_ARG unless
+ * h, nu, q_scale, eps_q > 0 and h + 2 slip > 0. */
 int mdgp_pseudo_md(double h, double nu, double slip, double g_from, double g_to, int32_t from_rest,
                    double q_scale, double eps_q, double* t_s);
 
@@ -492,6 +503,26 @@ int mdgp_hybrid_database(const mdgp_hybrid* h, double* X, double* y, double* se,
  * The arrays are copied.  MDGP_E_ARG on bad sizes or hyperparameters. */
 int mdgp_hybrid_set_pressure(mdgp_hybrid* h, const double* X, const double* y, int64_t M, double sf2, double l2,
                              double sn2);
+/* Replace the case's q database by M entries (X: M x D row-major with the
+ * case's input layout; se may be null = 0); snapshots are dropped, the
+ * prior mean is evaluated at the new inputs.  Sec. 3.3: a case may start
+ * from the database an earlier case ended with. */
+int mdgp_hybrid_set_database(mdgp_hybrid* h, const double* X, const double* y, const double* se, int64_t M);
+
+/* Write the q database (and with with_snapshots != 0 each entry's final MD
+ * snapshot, the warm-start source) to a file: "MDGPDB1\0", int32 D,
+ * int32 with_snapshots, int64 M, double X[M D], y[M], se[M], then per
+ * entry int64 n_fluid, n_wall, double h, g, float xv[6 (n_fluid + n_wall)]
+ * (zero counts: no snapshot); little-endian host layout.  MDGP_E_ARG when
+ * the file cannot be written. */
+int mdgp_hybrid_save(const mdgp_hybrid* h, const char* path, int32_t with_snapshots);
+
+/* Replace the case's q database (and snapshots, if the file has them) by a
+ * file mdgp_hybrid_save wrote.  MDGP_E_ARG when the file is unreadable,
+ * malformed or was written with another input dimension D; the case is
+ * then unchanged. */
+int mdgp_hybrid_load(mdgp_hybrid* h, const char* path);
+
 int mdgp_hybrid_free(mdgp_hybrid* h);
 
 /* ------------------------------------------------------------------------ */

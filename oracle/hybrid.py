@@ -206,8 +206,14 @@ def speedup(t_end_steps, n_atoms_full, steps_per_sim, n_sims, mean_atoms_per_sim
 # (k pi, k pi + pi/2) (theta_k = (2k + 1) pi / 2 without slip).  The flow
 # rate is Q = q_scale * integral_0^h u dy.  READING: the paper names the
 # solver but not its end criterion; t_s is the first time at which
-# |Q(t) - Q_inf| <= eps_q.
+# |Q(t) - Q_inf| <= eps_q.  A negative slip puts no-slip planes -slip inside
+# each wall (the layers next to the walls at rest): the channel of width
+# h + 2 slip without slip.
 # ---------------------------------------------------------------------------
+def _pseudo_md_width(h, slip):
+    return (h + 2.0 * slip, 0.0) if slip < 0.0 else (h, slip)
+
+
 def pseudo_md_roots(h, slip, n_modes):
     """theta_k, k < n_modes: roots of theta tan(theta) = h / (2 slip)."""
     from scipy.optimize import brentq
@@ -221,6 +227,7 @@ def pseudo_md_roots(h, slip, n_modes):
 
 def pseudo_md_steady_flow(h, nu, slip, g, q_scale):
     """Q of the steady profile g / (2 nu) (y (h - y) + slip h)."""
+    h, slip = _pseudo_md_width(h, slip)
     return q_scale * g / (2.0 * nu) * (h ** 3 / 6.0 + slip * h * h)
 
 
@@ -232,6 +239,7 @@ def pseudo_md_series(h, nu, slip, g_from, g_to, from_rest, q_scale, n_modes=400)
     scipy's weight='cos'), the norm h/2 + sin(2 theta_k) / (2 lam_k); the
     eigenfunction's flow-rate integral is 2 sin(theta_k) / lam_k."""
     from scipy.integrate import quad
+    h, slip = _pseudo_md_width(h, slip)
     amp = (-g_to if from_rest else g_from - g_to) / (2.0 * nu)
     dev = lambda s: amp * (h * h / 4.0 - s * s + slip * h)   # s = y - h/2
     th = pseudo_md_roots(h, slip, n_modes)

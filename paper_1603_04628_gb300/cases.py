@@ -60,6 +60,71 @@ def run_channel(ctx, sigma_t, n_steps, mlp=None, sf2=None, pressure_db=None, **p
                 gp_s=gp_s, md_s=md_s, db=(X, y, se))
 
 
+def fit_pseudo_md(ctx, hs=(8.0, 12.0, 16.0), g=0.02, n_seeds=8, density=0.8, T=1.1, Lx=10.0, Lz=10.0,
+                  steps_eq=10000, steps_sample=10000, seed=1, mass=1.0):
+    """The viscosity and slip length pseudoMD needs (Algorithm 1's t_s), from
+    the library's own MD: steady driven elements at several heights, the
+    steady flow rate q = m n Lz g (h^3 / 6 + slip h^2) / (2 nu) fitted by
+    least squares in (1/nu, slip/nu) with weights 1/SE^2.  A negative slip
+    (the fluid next to the walls at rest) is refitted as no-slip planes
+    -slip inside the walls, q = m n Lz g (h + 2 slip)^3 / (12 nu), by a
+    scan over slip.  Returns dict(nu, slip, h, q, q_se)."""
+    els = [dict(h=float(h), Lx=Lx, Lz=Lz, density=density, T=T, g_ext=float(g), dpdx=0.0, steps_eq=steps_eq,
+                steps_sample=steps_sample, seed=int(seed) + k, id=1000 * i + k)
+           for i, h in enumerate(hs) for k in range(n_seeds)]
+    res = ctx.micro_batch(els)
+    q = np.array([r["q"] for r in res]).reshape(len(hs), n_seeds)
+    qm = q.mean(1)
+    qse = q.std(1, ddof=1) / math.sqrt(n_seeds)
+    hv = np.array(hs, dtype=np.float64)
+    scale = mass * density * Lz * g / 2.0
+    A = np.column_stack([scale * hv ** 3 / 6.0, scale * hv ** 2]) / qse[:, None]
+    a, b = np.linalg.lstsq(A, qm / qse, rcond=None)[0]
+    nu, slip = 1.0 / a, b / a
+    if slip < 0.0:
+        best = None
+        for d in np.linspace(0.0, 0.45 * hv.min(), 901):
+            col = scale * (hv - 2.0 * d) ** 3 / 6.0 / qse
+            inv_nu = float(col @ (qm / qse) / (col @ col))
+            chi2 = float(((col * inv_nu - qm / qse) ** 2).sum())
+            if best is None or chi2 < best[0]:
+                best = (chi2, 1.0 / inv_nu, -d)
+        nu, slip = best[1], best[2]
+    return dict(nu=float(nu), slip=float(slip), h=hv.tolist(), q=qm.tolist(), q_se=qse.tolist())
+
+
+def warm_start_comparison(ctx, sigma_t, n_steps, reference, pseudo=None, eq_warm=(500,), pressure_db=None,
+                          **params):
+    """Algorithm 1 with cold starts against warm starts (Sec. 2.4) at one
+    threshold: MD runs, MD seconds, equilibration steps and Eq. error
+    against the reference flow-rate history, for each fixed warm
+    equilibration in eq_warm and, with pseudo = (nu, slip), with pseudoMD's
+    start-up time (floor eq_warm[0])."""
+    rows = []
+    arms = [("cold", dict(warm_start=0))]
+    arms += [("warm %d" % e, dict(warm_start=1, md_steps_eq_warm=int(e))) for e in eq_warm]
+    if pseudo is not None:
+        arms.append(("warm pseudoMD", dict(warm_start=1, md_steps_eq_warm=int(eq_warm[0]),
+                                           pseudo_nu=float(pseudo[0]), pseudo_slip=float(pseudo[1]))))
+    for name, kw in arms:
+        hy = native.Hybrid(ctx, **dict(params, **kw))
+        if pressure_db is not None:
+            hy.set_pressure(*pressure_db)
+        qbar, runs, warm, md_s, eq_steps = [], 0, 0, 0.0, 0
+        for _ in range(n_steps):
+            st = hy.step(sigma_t)
+            qbar.append(st["q_mean"])
+            runs += st["md_runs"]
+            warm += st["md_warm"]
+            md_s += st["md_seconds"]
+            eq_steps += st["md_warm"] * (st["md_steps_eq_warm"] if st["md_warm"] else 0) + \
+                (st["md_runs"] - st["md_warm"]) * params["md_steps_eq"]
+        hy.close()
+        rows.append(dict(arm=name, md_runs=runs, md_warm=warm, md_s=md_s,
+                         mean_eq_steps=eq_steps / runs if runs else 0.0, error=error(qbar, reference)))
+    return rows
+
+
 def error(q, Q):
     return float(np.abs(np.asarray(q) - np.asarray(Q)).sum() / np.abs(np.asarray(Q)).sum())
 
@@ -96,6 +161,34 @@ def channel_sweep(ctx, thresholds, n_steps=100, seed_noise=None, pressure_db=Non
             gp_s=r["gp_s"], md_s=r["md_s"], result=r))
     out["rows"] = rows
     return out
+
+
+def subdomain_refinement(ctx, sigma_t, n_steps, levels=4, pressure_db=None, **params):
+    """Sec. 3.3's cases S1-S4: the same channel with the number of sections
+    doubled at each level (the new sections bisect the old ones, dx halved),
+    each case starting from the database the previous one ended with.
+    Returns per level: sections, MD runs, database size at the start and
+    the end, and the section-averaged flow-rate history."""
+    rows, db = [], None
+    n0, dx0 = params.pop("n_sections"), params.pop("dx")
+    for k in range(levels):
+        p = dict(params, n_sections=n0 * 2 ** k, dx=dx0 / 2 ** k)
+        hy = native.Hybrid(ctx, **p)
+        if pressure_db is not None:
+            hy.set_pressure(*pressure_db)
+        if db is not None:
+            hy.set_database(*db)
+        start = len(hy.database()[1])
+        runs, qbar = 0, []
+        for _ in range(n_steps):
+            st = hy.step(sigma_t)
+            runs += st["md_runs"]
+            qbar.append(st["q_mean"])
+        db = hy.database()
+        hy.close()
+        rows.append(dict(n_sections=p["n_sections"], md_runs=runs, db_start=start, db_end=len(db[1]),
+                         qbar=np.array(qbar)))
+    return rows
 
 
 def periodic_filter(ctx, t, q, period, sf2=1.0, l2=1.0, sn2=0.01, fit_until=None, max_evals=200):
@@ -152,7 +245,7 @@ def evidence_hyperparameters(ctx, X, y, sn2, max_evals=200):
     return best["sf2"], best["l2"]
 
 
-def learned_mean_comparison(ctx, thresholds, n_steps, db_elements=256, seed=11, epochs=2000, reference=None,
+def learned_mean_comparison(ctx, thresholds, n_steps, db_elements=256, db_seed=11, epochs=2000, reference=None,
                             **params):
     """The learned prior mean against the plain GP at matched thresholds
     (benchmark addition to Algorithm 1).  One MD database over the channel's
@@ -163,12 +256,12 @@ def learned_mean_comparison(ctx, thresholds, n_steps, db_elements=256, seed=11, 
     reference: (q history of the sigma_t = 0 run, q history of a second one
     with other MD seeds) to judge the flow error against and to set the
     thermal-noise band; run here when not given."""
-    X, y, se = md_database(ctx, db_elements, seed, density=params.get("eos_n0", 0.8), T=params.get("T", 1.1),
+    X, y, se = md_database(ctx, db_elements, db_seed, density=params.get("eos_n0", 0.8), T=params.get("T", 1.1),
                            Lx=params.get("Lx", 10.0), Lz=params.get("Lz", 10.0),
                            steps_eq=params.get("md_steps_eq", 2000), steps_sample=params.get("md_steps_sample", 3000))
     sn2 = float(np.mean(se)) ** 2
     sf2_p, l2_p = evidence_hyperparameters(ctx, X, y, sn2)
-    net = native.MLP(ctx, seed=seed)
+    net = native.MLP(ctx, seed=db_seed)
     train, hold = net.train(X, y, epochs=epochs, lr=3e-3, eval_every=25)
     sf2_m, l2_m = evidence_hyperparameters(ctx, X, y - net.predict(X), sn2)
     if reference is None:

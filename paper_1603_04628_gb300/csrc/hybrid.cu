@@ -261,7 +261,11 @@ void thomas(const std::vector<double>& a, const std::vector<double>& b, const st
 
 int mdgp_pseudo_md(double h, double nu, double slip, double g_from, double g_to, int32_t from_rest,
                    double q_scale, double eps_q, double* t_s) {
-  if (!t_s || !(h > 0) || !(nu > 0) || !(q_scale > 0) || !(eps_q > 0) || !(slip >= 0)) return MDGP_E_ARG;
+  if (!t_s || !(h > 0) || !(nu > 0) || !(q_scale > 0) || !(eps_q > 0) || !(h + 2.0 * slip > 0)) return MDGP_E_ARG;
+  if (slip < 0.0) {   // no-slip planes -slip inside each wall: the flowing width h + 2 slip
+    h += 2.0 * slip;
+    slip = 0.0;
+  }
   constexpr int n = 64;
   const double dy = h / n;
   const double k = nu / (dy * dy);
@@ -676,6 +680,94 @@ int mdgp_hybrid_set_pressure(mdgp_hybrid* H, const double* X, const double* y, i
   gp.fallback_scale = 1.0;
   gp.fallback_scales = fb;
   return mdgp_gp_fit(H->ctx, X, y, M, 2, &gp, nullptr, &H->pgp);
+}
+
+int mdgp_hybrid_set_database(mdgp_hybrid* H, const double* X, const double* y, const double* se, int64_t M) {
+  if (!H || M < 0 || (M > 0 && (!X || !y))) return MDGP_E_ARG;
+  std::vector<double> nX(X, X + (size_t)H->D * M), ny(y, y + M), nse((size_t)M, 0.0), mX;
+  if (se) nse.assign(se, se + M);
+  const int st = prior_mean(H, nX.data(), M, mX);
+  if (st) return st;
+  H->X.swap(nX);
+  H->y.swap(ny);
+  H->se.swap(nse);
+  H->mX.swap(mX);
+  H->snaps.assign((size_t)M, mdgp_hybrid::Snap());
+  return MDGP_OK;
+}
+
+// Database file (Sec. 3.3: a case starts from the database an earlier case
+// ended with): little-endian host layout.
+//   char magic[8] = "MDGPDB1"; int32 D; int32 with_snapshots; int64 M;
+//   double X[M * D], y[M], se[M];
+//   then with_snapshots: per entry int64 n_fluid, n_wall; double h, g;
+//   float xv[6 * (n_fluid + n_wall)] (n_fluid = n_wall = 0: no snapshot).
+static const char kDbMagic[8] = {'M', 'D', 'G', 'P', 'D', 'B', '1', '\0'};
+
+int mdgp_hybrid_save(const mdgp_hybrid* H, const char* path, int32_t with_snapshots) {
+  if (!H || !path) return MDGP_E_ARG;
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return MDGP_E_ARG;
+  const int32_t D = H->D, ws = with_snapshots ? 1 : 0;
+  const int64_t M = (int64_t)H->y.size();
+  bool ok = std::fwrite(kDbMagic, 1, 8, f) == 8 && std::fwrite(&D, 4, 1, f) == 1 && std::fwrite(&ws, 4, 1, f) == 1 &&
+            std::fwrite(&M, 8, 1, f) == 1;
+  ok = ok && (M == 0 || (std::fwrite(H->X.data(), 8, (size_t)D * M, f) == (size_t)D * M &&
+                         std::fwrite(H->y.data(), 8, (size_t)M, f) == (size_t)M &&
+                         std::fwrite(H->se.data(), 8, (size_t)M, f) == (size_t)M));
+  for (int64_t i = 0; ok && ws && i < M; ++i) {
+    const mdgp_hybrid::Snap& S = H->snaps[(size_t)i];
+    const int64_t nf = S.xv.empty() ? 0 : S.nf, nw = S.xv.empty() ? 0 : S.nw;
+    const size_t nv = (size_t)6 * (nf + nw);
+    ok = std::fwrite(&nf, 8, 1, f) == 1 && std::fwrite(&nw, 8, 1, f) == 1 && std::fwrite(&S.h, 8, 1, f) == 1 &&
+         std::fwrite(&S.g, 8, 1, f) == 1 && (nv == 0 || std::fwrite(S.xv.data(), 4, nv, f) == nv);
+  }
+  ok = std::fclose(f) == 0 && ok;
+  return ok ? MDGP_OK : MDGP_E_ARG;
+}
+
+int mdgp_hybrid_load(mdgp_hybrid* H, const char* path) {
+  if (!H || !path) return MDGP_E_ARG;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return MDGP_E_ARG;
+  char magic[8];
+  int32_t D = 0, ws = 0;
+  int64_t M = -1;
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kDbMagic, 8) == 0 &&
+            std::fread(&D, 4, 1, f) == 1 && std::fread(&ws, 4, 1, f) == 1 && std::fread(&M, 8, 1, f) == 1 &&
+            D == H->D && M >= 0 && M < (int64_t(1) << 31);
+  std::vector<double> X, y, se;
+  std::vector<mdgp_hybrid::Snap> snaps;
+  if (ok) {
+    X.resize((size_t)D * M);
+    y.resize((size_t)M);
+    se.resize((size_t)M);
+    ok = M == 0 || (std::fread(X.data(), 8, X.size(), f) == X.size() && std::fread(y.data(), 8, y.size(), f) == y.size() &&
+                    std::fread(se.data(), 8, se.size(), f) == se.size());
+  }
+  snaps.resize(ok ? (size_t)M : 0);
+  for (int64_t i = 0; ok && ws && i < M; ++i) {
+    mdgp_hybrid::Snap& S = snaps[(size_t)i];
+    int64_t nf = 0, nw = 0;
+    ok = std::fread(&nf, 8, 1, f) == 1 && std::fread(&nw, 8, 1, f) == 1 && std::fread(&S.h, 8, 1, f) == 1 &&
+         std::fread(&S.g, 8, 1, f) == 1 && nf >= 0 && nw >= 0 && nf + nw < (int64_t(1) << 31);
+    if (!ok) break;
+    S.nf = nf;
+    S.nw = nw;
+    S.xv.resize((size_t)6 * (nf + nw));
+    ok = S.xv.empty() || std::fread(S.xv.data(), 4, S.xv.size(), f) == S.xv.size();
+  }
+  std::fclose(f);
+  if (!ok) return MDGP_E_ARG;
+  std::vector<double> mX;
+  const int st = prior_mean(H, X.data(), M, mX);
+  if (st) return st;
+  H->X.swap(X);
+  H->y.swap(y);
+  H->se.swap(se);
+  H->mX.swap(mX);
+  H->snaps.swap(snaps);
+  return MDGP_OK;
 }
 
 int mdgp_hybrid_free(mdgp_hybrid* H) {

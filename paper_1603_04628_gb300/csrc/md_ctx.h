@@ -37,6 +37,11 @@ struct mdgp_ctx {
   int persist_threads = 128;              // its block size
   int persist_atoms = 128;                // atoms per block (<= persist_threads)
   bool direct = false;        // persistent = 2: the host launches the persistent kernel itself
+  // persistent = 2: CUDA-event times of the last batch's persistent launches
+  // and of the rebuilds between them, and the steps they covered
+  cudaEvent_t dir_ev[3] = {nullptr, nullptr, nullptr};
+  double dir_kernel_ms = 0.0, dir_rebuild_ms = 0.0;
+  long long dir_steps = 0, dir_launches = 0, dir_rebuilds = 0;
   bool any_warm = false;      // some element of the plan starts from a snapshot
   long long launches = 0;              // kernels enqueued by the last launch (graph bodies: 2 per step)
   long long launches_with_rebuilds = 0;  // ... plus the rebuild kernels that ran

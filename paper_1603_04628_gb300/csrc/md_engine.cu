@@ -1057,21 +1057,40 @@ static int run_direct(mdgp_ctx* ctx) {
   cfg.attrs = at;
   cfg.numAttrs = 1;
   const cudaGraphConditionalHandle h0 = 0;
+  for (cudaEvent_t& ev : ctx->dir_ev)
+    if (!ev) CK(cudaEventCreate(&ev));
+  ctx->dir_kernel_ms = ctx->dir_rebuild_ms = 0.0;
+  ctx->dir_steps = ctx->dir_launches = ctx->dir_rebuilds = 0;
+  long long prev = 0;
+  bool rebuilt = false;
   for (long long guard = 0; guard <= S; ++guard) {
+    CK(cudaEventRecord(ctx->dir_ev[1], ctx->stream));
     cudaError_t e;
     if (uni && !frozen) e = cudaLaunchKernelEx(&cfg, k_steps_persist<true, false>, ctx->B, ctx->P, S, A, h0, h0, 0);
     else if (!uni && !frozen) e = cudaLaunchKernelEx(&cfg, k_steps_persist<false, false>, ctx->B, ctx->P, S, A, h0, h0, 0);
     else if (uni) e = cudaLaunchKernelEx(&cfg, k_steps_persist<true, true>, ctx->B, ctx->P, S, A, h0, h0, 0);
     else e = cudaLaunchKernelEx(&cfg, k_steps_persist<false, true>, ctx->B, ctx->P, S, A, h0, h0, 0);
     if (e != cudaSuccess) return set_err(ctx, e);
+    CK(cudaEventRecord(ctx->dir_ev[2], ctx->stream));
     ++ctx->launches;
     long long step = 0;
     int failed = 0;
     CK(cudaMemcpyAsync(&step, ctx->d_step.ptr, sizeof(long long), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(&failed, ctx->B.flags + kFlagExit, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    float ms = 0.f;
+    if (rebuilt && cudaEventElapsedTime(&ms, ctx->dir_ev[0], ctx->dir_ev[1]) == cudaSuccess) {
+      ctx->dir_rebuild_ms += ms;
+      ++ctx->dir_rebuilds;
+    }
+    if (cudaEventElapsedTime(&ms, ctx->dir_ev[1], ctx->dir_ev[2]) == cudaSuccess) ctx->dir_kernel_ms += ms;
+    ctx->dir_steps += step - prev;
+    ++ctx->dir_launches;
+    prev = step;
     if (step >= S || failed) break;
+    CK(cudaEventRecord(ctx->dir_ev[0], ctx->stream));
     enqueue_rebuild(ctx);
+    rebuilt = true;
   }
   return MDGP_OK;
 }
@@ -1207,6 +1226,7 @@ int mdgp_destroy(mdgp_ctx* ctx) {
   if (ctx->side_stream2) cudaStreamDestroy(ctx->side_stream2);
   for (cudaStream_t fs : ctx->fact_stream) if (fs) cudaStreamDestroy(fs);
   for (cudaEvent_t fe : ctx->fact_event) if (fe) cudaEventDestroy(fe);
+  for (cudaEvent_t de : ctx->dir_ev) if (de) cudaEventDestroy(de);
   delete ctx;
   return MDGP_OK;
 }
@@ -1375,6 +1395,17 @@ int mdgp_md_forces(mdgp_ctx* ctx, const mdgp_element* el, const double* x, int64
     if (epot) epot[i] = buf[(size_t)4 * n_atoms + i];
   }
   return status ? status : MDGP_OK;
+}
+
+int mdgp_micro_direct_timing(const mdgp_ctx* ctx, double* out) {
+  if (!ctx || !out) return MDGP_E_ARG;
+  if (!ctx->planned || !ctx->direct) return MDGP_E_STATE;
+  out[0] = ctx->dir_kernel_ms;
+  out[1] = (double)ctx->dir_steps;
+  out[2] = (double)ctx->dir_launches;
+  out[3] = ctx->dir_rebuild_ms;
+  out[4] = (double)ctx->dir_rebuilds;
+  return MDGP_OK;
 }
 
 int mdgp_micro_profile(mdgp_ctx* ctx, int64_t steps, double* ms) {

@@ -931,12 +931,22 @@ __device__ __forceinline__ PairAcc<PT, T, UNIFORM, ENERGY> pair_force(const Batc
   const uint4* L4 = reinterpret_cast<const uint4*>(B.list) + i;
   const int ng = (n + 3) >> 2;
   int k = 0;
-  // two groups of four entries per iteration: eight gathers in flight
+  // two groups of four entries per iteration: eight gathers in flight; the
+  // next iteration's two list groups load before this one's arithmetic, so
+  // their latency (they come from L2) overlaps it
+  uint4 en = make_uint4(0u, 0u, 0u, 0u), fn = en;
+  if (ng > 1) {
+    en = ld_list4(L4);
+    fn = ld_list4(L4 + N);
+  }
   for (; k + 1 < ng; k += 2) {
-    const uint4 e = ld_list4(L4 + (long long)k * N);
-    const uint4 f = ld_list4(L4 + (long long)(k + 1) * N);
+    const uint4 e = en, f = fn;
     const PT o0 = posj[e.x & kJMask], o1 = posj[e.y & kJMask], o2 = posj[e.z & kJMask], o3 = posj[e.w & kJMask];
     const PT o4 = posj[f.x & kJMask], o5 = posj[f.y & kJMask], o6 = posj[f.z & kJMask], o7 = posj[f.w & kJMask];
+    if (k + 3 < ng) {
+      en = ld_list4(L4 + (long long)(k + 2) * N);
+      fn = ld_list4(L4 + (long long)(k + 3) * N);
+    }
     acc.add(me, o0, e.x, csx, csy, csz, spi, rc2, eps, sig2, P);
     acc.add(me, o1, e.y, csx, csy, csz, spi, rc2, eps, sig2, P);
     acc.add(me, o2, e.z, csx, csy, csz, spi, rc2, eps, sig2, P);

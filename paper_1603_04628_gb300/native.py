@@ -108,6 +108,11 @@ def lib():
         "mdgp_pseudo_md": ([ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                             ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double)],
                            ctypes.c_int),
+        "mdgp_micro_direct_timing": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+        "mdgp_hybrid_set_database": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double), ctypes.c_int64], ctypes.c_int),
+        "mdgp_hybrid_save": ([ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int32], ctypes.c_int),
+        "mdgp_hybrid_load": ([ctypes.c_void_p, ctypes.c_char_p], ctypes.c_int),
         "mdgp_md_params_default": ([ctypes.POINTER(MDParams)], ctypes.c_int),
         "mdgp_create": ([ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "mdgp_destroy": ([vp], ctypes.c_int),
@@ -348,6 +353,14 @@ class Context:
                                            ctypes.byref(rate)), "mdgp_autotune")
         return {k: getattr(best, k) for k, _ in MDParams._fields_}, rate.value
 
+    def direct_timing(self):
+        """mdgp_micro_direct_timing: CUDA-event times of the last batch's
+        host-launched persistent kernels (persistent = 2)."""
+        out = np.zeros(5)
+        _check(self.h, lib().mdgp_micro_direct_timing(self.h, _dp(out)), "mdgp_micro_direct_timing")
+        return dict(kernel_ms=float(out[0]), steps=int(out[1]), launches=int(out[2]), rebuild_ms=float(out[3]),
+                    rebuilds=int(out[4]))
+
     def micro_profile(self, steps=100):
         """Mean per-launch milliseconds of the integration and pair-force kernels."""
         ms = np.zeros(6)
@@ -496,6 +509,21 @@ class Hybrid:
                                              fm.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dp(G)),
                "mdgp_hybrid_state")
         return dict(density=n, q=q, sd=sd, from_md=fm.astype(bool), G=G)
+
+    def set_database(self, X, y, se=None):
+        """mdgp_hybrid_set_database: start from an earlier case's database."""
+        X = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, self.D)
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        s = None if se is None else np.ascontiguousarray(se, dtype=np.float64)
+        _check(self.ctx.h, lib().mdgp_hybrid_set_database(self.h, _dp(X), _dp(y), None if s is None else _dp(s),
+                                                          len(y)), "mdgp_hybrid_set_database")
+
+    def save(self, path, snapshots=True):
+        _check(self.ctx.h, lib().mdgp_hybrid_save(self.h, os.fsencode(path), int(bool(snapshots))),
+               "mdgp_hybrid_save")
+
+    def load(self, path):
+        _check(self.ctx.h, lib().mdgp_hybrid_load(self.h, os.fsencode(path)), "mdgp_hybrid_load")
 
     def database(self):
         M = ctypes.c_int64()

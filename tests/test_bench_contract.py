@@ -19,3 +19,24 @@ def test_reference_arm_prints_contract_line():
         assert key in line, key
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_step_counters_are_used_only_for_the_captured_source(tmp_path, monkeypatch):
+    import hashlib
+    sys.path.insert(0, ROOT)
+    import bench
+    src = tmp_path / "k.cuh"
+    src.write_text("__global__ void k() {}\n")
+    sha = hashlib.sha256(src.read_bytes()).hexdigest()
+    prof = tmp_path / "p.md"
+    prof.write_text("# summary\n\ncounters: " + json.dumps({"source_sha256": sha, "dram_bytes_per_step": 1.5e6,
+                                                            "l1tex_throughput_frac": 0.4,
+                                                            "issue_active_frac": 0.45}) + "\n")
+    monkeypatch.setattr(bench, "STEP_PROFILE", str(prof))
+    monkeypatch.setattr(bench, "STEP_SOURCE", str(src))
+    c = bench.step_kernel_counters()
+    assert c["dram_bytes_per_step"] == 1.5e6
+    src.write_text("__global__ void k() { /* changed */ }\n")
+    assert bench.step_kernel_counters() is None
+    monkeypatch.setattr(bench, "STEP_PROFILE", str(tmp_path / "missing.md"))
+    assert bench.step_kernel_counters() is None

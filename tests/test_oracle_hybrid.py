@@ -210,3 +210,12 @@ def test_pseudo_md_time_no_slip_closed_form():
     assert t == pytest.approx(t_first, rel=1e-6)
     # nothing to wait for when the forces agree
     assert hybrid.pseudo_md_time(h, nu, 0.5, g, g, False, qs, eps) == 0.0
+
+
+def test_pseudo_md_negative_slip_is_a_narrower_no_slip_channel():
+    # READING: slip < 0 puts the no-slip planes -slip inside each wall
+    h, nu, s = 10.0, 2.0, -0.8
+    rate, w = hybrid.pseudo_md_series(h, nu, s, 0.0, 0.02, True, 80.0)
+    assert rate[0] == pytest.approx(nu * math.pi ** 2 / (h + 2 * s) ** 2, rel=1e-14)
+    assert hybrid.pseudo_md_steady_flow(h, nu, s, 0.02, 80.0) == pytest.approx(
+        80.0 * 0.02 * (h + 2 * s) ** 3 / (12 * nu), rel=1e-14)
