@@ -182,6 +182,7 @@ def main():
     ap.add_argument("--sample-steps", type=int, default=300,
                     help="oracle steps per sampled element in the reference arm")
     ap.add_argument("--no-gp-mlp", action="store_true", help="skip the GP and MLP timings")
+    ap.add_argument("--no-hybrid", action="store_true", help="skip the hybrid-channel summary")
     ap.add_argument("--persistent", type=int, default=None, choices=[0, 1, 2],
                     help="step loop: 0 one launch per step, 1 persistent kernel in a graph WHILE loop, 2 the "
                          "persistent kernel launched by the host (profilers capture it)")
@@ -332,6 +333,9 @@ def main():
     gp_mlp = None
     if rank == 0 and args.workload == "uneven" and not args.no_gp_mlp:
         gp_mlp = gp_mlp_timings(native, local)
+    hybrid = None
+    if rank == 0 and world == 1 and args.workload == "uneven" and not args.no_hybrid:
+        hybrid = hybrid_summary(local)
 
     cpu = None
     if pool is not None:
@@ -386,6 +390,7 @@ def main():
             "clocks": clocks,
             "fp64_forces": fp64,
             "gp_mlp": gp_mlp,
+            "hybrid": hybrid,
             "element_status_errors": len(bad),
             "element_status_codes": sorted(set(bad)),
             "list_capacity": cap,
@@ -395,6 +400,84 @@ def main():
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def hybrid_summary(device, n_sections=100, n_steps=50, long_eq=8000, thresholds=(0.5, 2.0)):
+    """Algorithm 1 on the converging-diverging channel in the paper's form
+    (p-GP over (h, n) from pre-simulations, q-GP on (h, n, F)), one forcing
+    period (50 macro steps of 20), against MD at every section and step.
+    The stand-in for full MD equilibrates each run for long_eq steps (the
+    start-up of the widest sections takes about 5 of its slowest flow time
+    constants, measured below), a second one with other seeds gives the
+    thermal noise.  Each threshold runs with warm starts (Sec. 2.4) and
+    pseudoMD's start-up time (Algorithm 1, viscosity and slip fitted to the
+    library's own MD), the q-GP's hyperparameters by maximum evidence on
+    the stand-in's database.  Reports MD runs, Eq. error against the
+    stand-in and against its App. B filtered series, Eq. speedup and
+    measured wall time."""
+    import numpy as np
+    from paper_1603_04628_gb300 import cases, native
+    t_all = time.perf_counter()
+    ctx = native.Context(device, native.PREC_FP32)
+    sn = 0.5
+    fit = cases.fit_pseudo_md(ctx)
+    params = dict(n_sections=n_sections, dx=10000.0 / n_sections, h0=12.0, Lx=10.0, Lz=10.0, eos_K=10.0,
+                  eos_n0=0.8, dP_amp=400.0, period=1000.0, dt=20.0, T=1.1, md_steps_eq=long_eq,
+                  md_steps_sample=3000, seed=synth.BASE_SEED, sf2=(20 * sn) ** 2, l2=1.0, sn2=sn ** 2,
+                  sn2_from_data=0, inputs=1)
+    X, p, p_se = cases.pressure_sweep(ctx, np.linspace(6.0, 18.0, 5), np.linspace(0.6, 1.0, 9), T=params["T"],
+                                      seed=synth.BASE_SEED + 7)
+    pdb = (X, p, float(np.var(p)), 1.0, float(np.mean(p_se)) ** 2)
+    ref = cases.run_channel(ctx, 0.0, n_steps, pressure_db=pdb, **params)
+    ref2 = cases.run_channel(ctx, 0.0, n_steps, pressure_db=pdb, **dict(params, seed=synth.BASE_SEED + 99))
+    # q-GP hyperparameters by maximum evidence (Sec. 2.3) on 400 entries of
+    # the reference's database, sigma_n^2 held at its mean squared SE
+    Xr, yr, ser = ref["db"]
+    sub = np.random.default_rng(synth.BASE_SEED).choice(len(yr), size=min(400, len(yr)), replace=False)
+    sn2_ev = float(np.mean(ser)) ** 2
+    sf2_ev, l2_ev = cases.evidence_hyperparameters(ctx, Xr[sub], yr[sub], sn2_ev)
+    t = np.arange(1, n_steps + 1) * params["dt"]
+    filt, _, _, _ = cases.periodic_filter(ctx, t, ref["qbar"], params["period"], sf2=float(np.var(ref["qbar"])),
+                                          sn2=1e-4, fit_until=None)
+    n_af = cases.channel_atoms(params)
+    rows = []
+    for s in thresholds:
+        hy = native.Hybrid(ctx, **dict(params, warm_start=1, md_steps_eq_warm=250, pseudo_nu=fit["nu"],
+                                       pseudo_slip=fit["slip"], sf2=sf2_ev, l2=l2_ev, sn2=sn2_ev))
+        hy.set_pressure(*pdb)
+        qbar, runs, warm, steps, atoms, md_s, gp_s = [], 0, 0, 0, 0, 0.0, 0.0
+        t0 = time.perf_counter()
+        for _ in range(n_steps):
+            st = hy.step(s)
+            qbar.append(st["q_mean"])
+            runs += st["md_runs"]
+            warm += st["md_warm"]
+            steps += st["md_warm"] * (st["md_steps_eq_warm"] + params["md_steps_sample"]) + \
+                (st["md_runs"] - st["md_warm"]) * (long_eq + params["md_steps_sample"])
+            atoms += st["md_atoms"]
+            md_s += st["md_seconds"]
+            gp_s += st["gp_seconds"]
+        wall = time.perf_counter() - t0
+        hy.close()
+        t_end_steps = n_steps * params["dt"] / 0.005
+        rows.append(dict(sigma_t=s, md_runs=runs, md_warm=warm, mean_md_steps=steps / runs if runs else 0.0,
+                         error=cases.error(qbar, ref["qbar"]), error_vs_filtered=cases.error(qbar, filt),
+                         speedup_eq=(t_end_steps * n_af / steps / (atoms / runs)) if runs else None,
+                         wall_s=wall, wall_vs_reference=ref["wall_s"] / wall, md_s=md_s, gp_s=gp_s))
+    ctx.close()
+    return {"metric": "hybrid flow error and speed-up against MD everywhere (Eqs. error, speedup)",
+            "config": {"workload": "%d-section converging-diverging channel (h0 = 12, L = 10^4), one forcing "
+                                   "period (%d macro steps of 20), plain 10 x h x 10 elements (FP32 forces), "
+                                   "paper form: p-GP on (h, n) from 45 pre-simulations, q-GP on (h, n, F)"
+                                   % (n_sections, n_steps),
+                       "sigma_n": sn, "sigma_f": 20 * sn, "md_steps_sample": params["md_steps_sample"],
+                       "reference_eq_steps": long_eq, "warm_eq_floor": 250},
+            "pseudo_md_fit": {"nu": fit["nu"], "slip": fit["slip"]},
+            "evidence_hyperparameters": {"sf2": sf2_ev, "l2": l2_ev, "sn2": sn2_ev, "entries": int(len(sub))},
+            "reference": {"md_runs": ref["md_runs"], "wall_s": ref["wall_s"]},
+            "thermal_noise_error": cases.error(ref2["qbar"], ref["qbar"]),
+            "app_b_filter_rms": float(np.sqrt(np.mean((filt - ref["qbar"]) ** 2))),
+            "rows": rows, "wall_s": time.perf_counter() - t_all}
 
 
 def gp_mlp_timings(native, device):
@@ -485,17 +568,20 @@ def run_learned_mean_case(args):
     from paper_1603_04628_gb300 import cases, native
     torch.cuda.set_device(0)
     ctx = native.Context(0, native.PREC_FP32)
-    params = dict(n_sections=200, dx=50.0, h0=12.0, Lx=10.0, Lz=10.0, eos_K=10.0, eos_n0=0.8, dP_amp=400.0,
+    # 50 sections: the plain arm with evidence hyperparameters runs MD at
+    # most sections, and every appended entry refits the GP (O(M^3))
+    params = dict(n_sections=50, dx=200.0, h0=12.0, Lx=10.0, Lz=10.0, eos_K=10.0, eos_n0=0.8, dP_amp=400.0,
                   period=1000.0, dt=20.0, T=1.1, md_steps_eq=2000, md_steps_sample=3000, seed=synth.BASE_SEED,
                   sn2_from_data=0, inputs=0)
     t0 = time.perf_counter()
-    thresholds = [0.25, 0.5, 1.0, 2.0, 4.0]
-    rows, info, net = cases.learned_mean_comparison(ctx, thresholds, args.channel_steps, db_elements=256,
-                                                    db_seed=synth.BASE_SEED + 31, **params)
+    thresholds = [0.5, 1.0, 2.0, 4.0]
+    rows, info, net = cases.learned_mean_comparison(
+        ctx, thresholds, args.channel_steps, db_elements=256, db_seed=synth.BASE_SEED + 31,
+        log=lambda d: print(json.dumps(d), file=sys.stderr, flush=True), **params)
     line = {"case": "learned-mean", "n_gpus": 1, "data": "synthetic",
-            "config": {"workload": "200-section channel, linear equation of state, q-GP on (h, G), %d macro "
-                                   "steps, 10 x h x 10 elements (2000 + 3000 steps, FP32 forces); MLP trained on "
-                                   "256 MD runs over h 6-18, G -0.06..0.06" % args.channel_steps},
+            "config": {"workload": "50-section channel (L = 10^4), linear equation of state, q-GP on (h, G), %d "
+                                   "macro steps, 10 x h x 10 elements (2000 + 3000 steps, FP32 forces); MLP "
+                                   "trained on 256 MD runs over h 6-18, G -0.06..0.06" % args.channel_steps},
             "info": info, "rows": rows, "wall_s": time.perf_counter() - t0}
     print(json.dumps(line), flush=True)
     net.close()

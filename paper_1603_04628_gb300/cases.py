@@ -246,7 +246,7 @@ def evidence_hyperparameters(ctx, X, y, sn2, max_evals=200):
 
 
 def learned_mean_comparison(ctx, thresholds, n_steps, db_elements=256, db_seed=11, epochs=2000, reference=None,
-                            **params):
+                            log=None, **params):
     """The learned prior mean against the plain GP at matched thresholds
     (benchmark addition to Algorithm 1).  One MD database over the channel's
     (h, G) range trains the MLP; each arm's (sf2, l2) come from the same
@@ -255,7 +255,9 @@ def learned_mean_comparison(ctx, thresholds, n_steps, db_elements=256, db_seed=1
     the learned mean -- so the two arms differ only by the prior mean.
     reference: (q history of the sigma_t = 0 run, q history of a second one
     with other MD seeds) to judge the flow error against and to set the
-    thermal-noise band; run here when not given."""
+    thermal-noise band; run here when not given.  log (if given) receives a
+    dict after each stage."""
+    say = log or (lambda d: None)
     X, y, se = md_database(ctx, db_elements, db_seed, density=params.get("eos_n0", 0.8), T=params.get("T", 1.1),
                            Lx=params.get("Lx", 10.0), Lz=params.get("Lz", 10.0),
                            steps_eq=params.get("md_steps_eq", 2000), steps_sample=params.get("md_steps_sample", 3000))
@@ -264,12 +266,14 @@ def learned_mean_comparison(ctx, thresholds, n_steps, db_elements=256, db_seed=1
     net = native.MLP(ctx, seed=db_seed)
     train, hold = net.train(X, y, epochs=epochs, lr=3e-3, eval_every=25)
     sf2_m, l2_m = evidence_hyperparameters(ctx, X, y - net.predict(X), sn2)
+    say(dict(stage="hyperparameters", sn2=sn2, plain=(sf2_p, l2_p), mlp=(sf2_m, l2_m), holdout=hold))
     if reference is None:
         ref = run_channel(ctx, 0.0, n_steps, **params)["qbar"]
         ref2 = run_channel(ctx, 0.0, n_steps, **dict(params, seed=params.get("seed", 0) + 1000))["qbar"]
     else:
         ref, ref2 = reference
     noise = error(ref2, ref)
+    say(dict(stage="reference", noise=noise))
     rows = []
     for s in thresholds:
         a = run_channel(ctx, s, n_steps, **dict(params, sf2=sf2_p, l2=l2_p, sn2=sn2))
@@ -277,6 +281,7 @@ def learned_mean_comparison(ctx, thresholds, n_steps, db_elements=256, db_seed=1
         rows.append(dict(sigma_t=s, md_runs_plain=a["md_runs"], md_runs_mlp=b["md_runs"],
                          error_plain=error(a["qbar"], ref), error_mlp=error(b["qbar"], ref),
                          wall_plain=a["wall_s"], wall_mlp=b["wall_s"]))
+        say(dict(stage="threshold", **rows[-1]))
     info = dict(db_elements=db_elements, sn2=sn2, plain=dict(sf2=sf2_p, l2=l2_p), mlp=dict(sf2=sf2_m, l2=l2_m),
                 mlp_train_loss=train, mlp_holdout_loss=hold, noise_error=noise)
     return rows, info, net

@@ -594,8 +594,13 @@ __global__ void __launch_bounds__(256) k_settle(BatchDev B) {
 // [k / 4][atom][4] (a warp's 16-byte loads coalesce); the last group is
 // padded with an entry that is always beyond r_c (the atom itself one cell
 // over in x), so readers never test the count inside a group.
+// A list entry: the neighbour's index within its element (bits 0-25) and
+// its cell's place among the 27 neighbour cells, k = 9 (dx + 1) + 3 (dy + 1)
+// + (dz + 1) (bits 26-30).  The pad entry points at the atom itself shifted
+// by one cell in x (k = 22): its distance, the cell side, exceeds r_c.
+constexpr unsigned kCodePad = 22u;
 __device__ __forceinline__ unsigned pad_entry(long long i, const ElemDev& E) {
-  return (unsigned)(i - E.atom0) | (2u << 26) | (1u << 28) | (1u << 30);
+  return (unsigned)(i - E.atom0) | (kCodePad << 26);
 }
 
 // Ballot list build.  The candidates of a cell are gathered from its 27
@@ -622,7 +627,7 @@ __device__ __forceinline__ unsigned pad_entry(long long i, const ElemDev& E) {
 struct BallotCell {
   float lx, ly, lz, hx, hy, hz;   // bounding box of the cell's own atoms
   int nst, nsz;                   // lane k < 27: start and size of neighbour cell k
-  unsigned ncode;                 // lane k: shift bits of neighbour cell k
+  unsigned ncode;                 // lane k: code of neighbour cell k (k << 26)
   float nsx, nsy, nsz_f;          // lane k: shift of neighbour cell k in length units
   int pre, excl, total;           // inclusive / exclusive size prefix, total candidates
 };
@@ -660,7 +665,7 @@ __device__ __forceinline__ void ballot_cell(const BatchDev& B, const ElemDev& E,
       C.nst = B.cstart[c2];
       C.nsz = B.csize[c2];
     }
-    C.ncode = ((unsigned)(dx + 1) << 26) | ((unsigned)(dy + 1) << 28) | ((unsigned)(dz + 1) << 30);
+    C.ncode = (unsigned)lane << 26;
     C.nsx = (float)dx * E.csf[0]; C.nsy = (float)dy * E.csf[1]; C.nsz_f = (float)dz * E.csf[2];
   }
   int pre = C.nsz;   // inclusive prefix of the sizes over the lanes
@@ -850,7 +855,7 @@ __global__ void __launch_bounds__(kBlkWarps * 32, 6) k_build_ballot_blk(BatchDev
 // a warp's neighbours are shared in L1).  Eq. LJ truncated at r_c, energy
 // shifted by U(r_c) per pair type.  The displacement is formed from
 // cell-centre offsets: d = (p_i - p_j) - delta * cs, delta in {-1, 0, 1}^3
-// from the entry's shift bits, so FP32 only ever rounds numbers below ~3.
+// from the entry's cell code, so FP32 only ever rounds numbers below ~3.
 // Writes the LJ force, the x-virial share of fluid atoms (half per pair) and,
 // with ENERGY, half the shifted pair energy per atom.
 // ---------------------------------------------------------------------------
@@ -861,17 +866,29 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return r;
 }
 
-__device__ __forceinline__ float shift_unit(unsigned bits2) {
-  // bits2 in {0, 1, 2} -> {-1, 0, 1}, exactly, without an int-to-float convert
-  return __int_as_float(0x4B400000 | (int)bits2) - 12582913.0f;
+// The unit cell shifts (dx, dy, dz) of the 27 neighbour-cell codes, one
+// array per axis in shared memory (27 words: any mix of codes in a warp
+// reads without bank conflicts).  Every thread of the block calls it; the
+// caller synchronises before the first use.
+struct ShiftTab {
+  float d[3][32];
+};
+__device__ __forceinline__ void shift_tab_init(ShiftTab& t) {
+  for (int k = threadIdx.x; k < 96; k += blockDim.x) {
+    const int a = k >> 5, c = k & 31;
+    const int v = c < 27 ? (a == 0 ? c / 9 : (a == 1 ? (c / 3) % 3 : c % 3)) - 1 : 0;
+    t.d[a][c] = (float)v;
+  }
 }
 
 template <typename PT, typename T, bool UNIFORM, bool ENERGY>
 struct PairAcc {
   T fx = 0, fy = 0, fz = 0, w = 0, u = 0;
   __device__ __forceinline__ void add(const PT& me, const PT& o, unsigned ent, T csx, T csy, T csz, int spi,
-                                      T rc2, const T (&eps)[3], const T (&sig2)[3], const PhysDev& P) {
-    const float sx = shift_unit((ent >> 26) & 3u), sy = shift_unit((ent >> 28) & 3u), sz = shift_unit(ent >> 30);
+                                      T rc2, const T (&eps)[3], const T (&sig2)[3], const PhysDev& P,
+                                      const ShiftTab& tab) {
+    const unsigned code = ent >> 26;
+    const float sx = tab.d[0][code], sy = tab.d[1][code], sz = tab.d[2][code];
     T ddx, ddy, ddz;
     if constexpr (sizeof(T) == 4) {
       ddx = fmaf(-sx, csx, me.x - o.x);
@@ -911,7 +928,8 @@ struct PairAcc {
 // buffer); spi = the atom's species.
 template <typename PT, typename T, bool UNIFORM, bool ENERGY>
 __device__ __forceinline__ PairAcc<PT, T, UNIFORM, ENERGY> pair_force(const BatchDev& B, const PhysDev& P,
-                                                                      long long i, const PT* pos, int& spi) {
+                                                                      long long i, const PT* pos, int& spi,
+                                                                      const ShiftTab& tab) {
   const ElemDev& E = B.el[__ldcg(B.atom_el + i)];
   const PT me = pos[i];
   const T csx = (T)E.cs[0], csy = (T)E.cs[1], csz = (T)E.cs[2];
@@ -931,38 +949,30 @@ __device__ __forceinline__ PairAcc<PT, T, UNIFORM, ENERGY> pair_force(const Batc
   const uint4* L4 = reinterpret_cast<const uint4*>(B.list) + i;
   const int ng = (n + 3) >> 2;
   int k = 0;
-  // two groups of four entries per iteration: eight gathers in flight; the
-  // next iteration's two list groups load before this one's arithmetic, so
-  // their latency (they come from L2) overlaps it
-  uint4 en = make_uint4(0u, 0u, 0u, 0u), fn = en;
-  if (ng > 1) {
-    en = ld_list4(L4);
-    fn = ld_list4(L4 + N);
-  }
+  // two groups of four entries per iteration: eight gathers in flight
+  // (loading the next iteration's list groups ahead costs registers the
+  // persistent kernel does not have: measured slower)
   for (; k + 1 < ng; k += 2) {
-    const uint4 e = en, f = fn;
+    const uint4 e = ld_list4(L4 + (long long)k * N);
+    const uint4 f = ld_list4(L4 + (long long)(k + 1) * N);
     const PT o0 = posj[e.x & kJMask], o1 = posj[e.y & kJMask], o2 = posj[e.z & kJMask], o3 = posj[e.w & kJMask];
     const PT o4 = posj[f.x & kJMask], o5 = posj[f.y & kJMask], o6 = posj[f.z & kJMask], o7 = posj[f.w & kJMask];
-    if (k + 3 < ng) {
-      en = ld_list4(L4 + (long long)(k + 2) * N);
-      fn = ld_list4(L4 + (long long)(k + 3) * N);
-    }
-    acc.add(me, o0, e.x, csx, csy, csz, spi, rc2, eps, sig2, P);
-    acc.add(me, o1, e.y, csx, csy, csz, spi, rc2, eps, sig2, P);
-    acc.add(me, o2, e.z, csx, csy, csz, spi, rc2, eps, sig2, P);
-    acc.add(me, o3, e.w, csx, csy, csz, spi, rc2, eps, sig2, P);
-    acc.add(me, o4, f.x, csx, csy, csz, spi, rc2, eps, sig2, P);
-    acc.add(me, o5, f.y, csx, csy, csz, spi, rc2, eps, sig2, P);
-    acc.add(me, o6, f.z, csx, csy, csz, spi, rc2, eps, sig2, P);
-    acc.add(me, o7, f.w, csx, csy, csz, spi, rc2, eps, sig2, P);
+    acc.add(me, o0, e.x, csx, csy, csz, spi, rc2, eps, sig2, P, tab);
+    acc.add(me, o1, e.y, csx, csy, csz, spi, rc2, eps, sig2, P, tab);
+    acc.add(me, o2, e.z, csx, csy, csz, spi, rc2, eps, sig2, P, tab);
+    acc.add(me, o3, e.w, csx, csy, csz, spi, rc2, eps, sig2, P, tab);
+    acc.add(me, o4, f.x, csx, csy, csz, spi, rc2, eps, sig2, P, tab);
+    acc.add(me, o5, f.y, csx, csy, csz, spi, rc2, eps, sig2, P, tab);
+    acc.add(me, o6, f.z, csx, csy, csz, spi, rc2, eps, sig2, P, tab);
+    acc.add(me, o7, f.w, csx, csy, csz, spi, rc2, eps, sig2, P, tab);
   }
   if (k < ng) {
     const uint4 e = ld_list4(L4 + (long long)k * N);
     const PT o0 = posj[e.x & kJMask], o1 = posj[e.y & kJMask], o2 = posj[e.z & kJMask], o3 = posj[e.w & kJMask];
-    acc.add(me, o0, e.x, csx, csy, csz, spi, rc2, eps, sig2, P);
-    acc.add(me, o1, e.y, csx, csy, csz, spi, rc2, eps, sig2, P);
-    acc.add(me, o2, e.z, csx, csy, csz, spi, rc2, eps, sig2, P);
-    acc.add(me, o3, e.w, csx, csy, csz, spi, rc2, eps, sig2, P);
+    acc.add(me, o0, e.x, csx, csy, csz, spi, rc2, eps, sig2, P, tab);
+    acc.add(me, o1, e.y, csx, csy, csz, spi, rc2, eps, sig2, P, tab);
+    acc.add(me, o2, e.z, csx, csy, csz, spi, rc2, eps, sig2, P, tab);
+    acc.add(me, o3, e.w, csx, csy, csz, spi, rc2, eps, sig2, P, tab);
   }
   return acc;
 }
@@ -970,12 +980,15 @@ __device__ __forceinline__ PairAcc<PT, T, UNIFORM, ENERGY> pair_force(const Batc
 // Pair forces of step *step_base + k into fx, fy, fz (+ virial share, energy).
 template <typename PT, typename T, bool UNIFORM, bool ENERGY>
 __global__ void __launch_bounds__(128) k_force(BatchDev B, PhysDev P, int k) {
+  __shared__ ShiftTab tab;
+  shift_tab_init(tab);
+  __syncthreads();
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= B.n_atoms) return;
   const long long s = *B.step_base + k;
   int spi;
   const PairAcc<PT, T, UNIFORM, ENERGY> acc =
-      pair_force<PT, T, UNIFORM, ENERGY>(B, P, i, static_cast<const PT*>(B.posb[s & 1]), spi);
+      pair_force<PT, T, UNIFORM, ENERGY>(B, P, i, static_cast<const PT*>(B.posb[s & 1]), spi, tab);
   static_cast<T*>(B.fx)[i] = acc.fx;
   static_cast<T*>(B.fy)[i] = acc.fy;
   static_cast<T*>(B.fz)[i] = acc.fz;
@@ -1357,13 +1370,17 @@ __global__ void __launch_bounds__(256) k_integrate_df(BatchDev B, PhysDev P, int
 template <bool UNIFORM, bool FROZEN, bool STORE>
 __global__ void __launch_bounds__(128) k_step_df(BatchDev B, PhysDev P, int k, int mode,
                                                  cudaGraphConditionalHandle hcond, int use_cond) {
+  __shared__ ShiftTab tab;
+  shift_tab_init(tab);
+  __syncthreads();
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long s = *B.step_base + k;
   StepOut o;
   if (i < B.n_atoms) {
     const float4* pos = static_cast<const float4*>(B.posb[s & 1]);
     int spi;
-    const PairAcc<float4, float, UNIFORM, false> f = pair_force<float4, float, UNIFORM, false>(B, P, i, pos, spi);
+    const PairAcc<float4, float, UNIFORM, false> f =
+        pair_force<float4, float, UNIFORM, false>(B, P, i, pos, spi, tab);
     const float wxx = spi == 0 ? 0.5f * f.w : 0.0f;
     if (STORE) {
       static_cast<float*>(B.fx)[i] = f.fx;
@@ -1440,6 +1457,9 @@ template <bool UNIFORM, bool FROZEN>
 __global__ void __launch_bounds__(256, 5) k_steps_persist(BatchDev B, PhysDev P, long long S, int A,
                                                       cudaGraphConditionalHandle h_rebuild,
                                                       cudaGraphConditionalHandle h_more, int use_cond) {
+  __shared__ ShiftTab tab;
+  shift_tab_init(tab);
+  __syncthreads();
   const long long nchunks = (B.n_atoms + A - 1) / A;
   const bool lane_used = (int)threadIdx.x < A;
   long long s = *B.step_base;
@@ -1454,7 +1474,8 @@ __global__ void __launch_bounds__(256, 5) k_steps_persist(BatchDev B, PhysDev P,
       StepOut o;
       if (i < B.n_atoms) {
         int spi;
-        const PairAcc<float4, float, UNIFORM, false> f = pair_force<float4, float, UNIFORM, false>(B, P, i, pos, spi);
+        const PairAcc<float4, float, UNIFORM, false> f =
+            pair_force<float4, float, UNIFORM, false>(B, P, i, pos, spi, tab);
         const float wxx = spi == 0 ? 0.5f * f.w : 0.0f;
         if (FROZEN) {
           static_cast<float*>(B.fx)[i] = f.fx;
