@@ -287,6 +287,7 @@ def main():
     # list-rebuild interval (the timed run's kernel, outside its graph), and
     # the one-launch-per-step kernel of the same step code
     path = ctx.path()
+    shape = ctx.launch_shape() if path != "per-step" else None
     prof = ctx.micro_profile(min(200, steps_el))
     cdir = native.Context(local, native.PREC_FP32, stream=stream, persistent=2, list_capacity=cap)
     cdir.micro_plan(els)
@@ -380,6 +381,7 @@ def main():
                          "rebuilds_per_run": rebuilds_per_step, "rebuild_ms": prof["rebuild_ms"],
                          "rebuild_share": rebuilds_per_step * prof["rebuild_ms"] / ms},
             "path": path,
+            "launch_shape": shape,
             "hbm_roofline": {"alg_bytes_per_atom_step": ALG_BYTES_PER_ATOM_STEP,
                              "achieved_gbs": value / world * ALG_BYTES_PER_ATOM_STEP / 1e9,
                              "peak_gbs": _peak_hbm(), "frac": value / world * ALG_BYTES_PER_ATOM_STEP / 1e9 /

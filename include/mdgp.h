@@ -131,6 +131,10 @@ typedef struct {
                            step kernel leave out its first grid-barrier arrival, so that the
                            other blocks' bounded waits run out; the launch then ends with
                            MDGP_E_TIMEOUT for every element and the context stays usable. */
+  int32_t threads_per_atom; /* FP32 persistent step loop: threads that share one atom's pair
+                           loop, 1, 2, 4 or 8; 0 (default) = the largest that the batch fills
+                           (several only for batches too small to occupy every SM with one
+                           thread per atom).  Results differ only by the summation order. */
 } mdgp_md_params;
 
 /* Fill *out with the defaults listed above.  Returns MDGP_E_ARG on null. */
@@ -226,6 +230,12 @@ int64_t mdgp_micro_launch_count(const mdgp_ctx* ctx);
  * graphs), 1 the persistent kernel in a graph WHILE loop, 2 the persistent
  * kernel launched by the host.  MDGP_E_STATE without a plan. */
 int mdgp_micro_path(const mdgp_ctx* ctx);
+
+/* Launch shape of the planned batch's persistent step kernel (FP32 pair
+ * forces, persistent = 1 or 2): out[0] = blocks, out[1] = threads per block,
+ * out[2] = atoms per block, out[3] = threads per atom in the pair loop.
+ * MDGP_E_STATE without a plan or on the per-step path. */
+int mdgp_micro_launch_shape(const mdgp_ctx* ctx, int32_t* out);
 
 /* With persistent = 2 (the host launches the persistent step kernel once
  * per list-rebuild interval): CUDA-event times of the last batch's

@@ -35,7 +35,8 @@ struct mdgp_ctx {
   cudaGraphExec_t graph_while = nullptr;  // persistent step loop (FP32 pair forces)
   unsigned persist_grid = 0;              // co-resident blocks of the persistent step kernel
   int persist_threads = 128;              // its block size
-  int persist_atoms = 128;                // atoms per block (<= persist_threads)
+  int persist_atoms = 128;                // atoms per block (persist_atoms x persist_tpa <= persist_threads)
+  int persist_tpa = 1;                    // threads per atom in its pair loop
   bool direct = false;        // persistent = 2: the host launches the persistent kernel itself
   // persistent = 2: CUDA-event times of the last batch's persistent launches
   // and of the rebuilds between them, and the steps they covered

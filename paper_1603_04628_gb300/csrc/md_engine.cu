@@ -707,6 +707,26 @@ static int capture_steps(mdgp_ctx* ctx, long long nsteps, cudaGraphExec_t* out) 
   return set_err(ctx, e);
 }
 
+// The persistent step kernel for a batch's pair types, wall mode and
+// threads per atom (1, 2, 4 or 8).
+using PersistFn = void (*)(mdgp::BatchDev, mdgp::PhysDev, long long, int, cudaGraphConditionalHandle,
+                           cudaGraphConditionalHandle, int);
+template <bool U, bool F>
+static PersistFn persist_kernel_tpa(int tpa) {
+  switch (tpa) {
+    case 2: return k_steps_persist<U, F, 2>;
+    case 4: return k_steps_persist<U, F, 4>;
+    case 8: return k_steps_persist<U, F, 8>;
+    default: return k_steps_persist<U, F, 1>;
+  }
+}
+static PersistFn persist_kernel(bool uni, bool frozen, int tpa) {
+  if (uni && !frozen) return persist_kernel_tpa<true, false>(tpa);
+  if (!uni && !frozen) return persist_kernel_tpa<false, false>(tpa);
+  if (uni) return persist_kernel_tpa<true, true>(tpa);
+  return persist_kernel_tpa<false, true>(tpa);
+}
+
 // Persistent step loop (FP32 pair forces): a graph with one WHILE node
 // whose body is [cooperative k_steps_persist launch] -> IF (rebuild) {the 5
 // rebuild kernels}.  The step kernel runs steps until the lists need a
@@ -743,10 +763,7 @@ static int capture_while(mdgp_ctx* ctx, cudaGraphExec_t* out) {
   const bool uni = ctx->P.uniform != 0, frozen = ctx->params.mode == 1;
   const long long S = ctx->steps;
   const int A = ctx->persist_atoms;
-  if (uni && !frozen) e = cudaLaunchKernelEx(&cfg, k_steps_persist<true, false>, ctx->B, ctx->P, S, A, hr, hw, 1);
-  else if (!uni && !frozen) e = cudaLaunchKernelEx(&cfg, k_steps_persist<false, false>, ctx->B, ctx->P, S, A, hr, hw, 1);
-  else if (uni) e = cudaLaunchKernelEx(&cfg, k_steps_persist<true, true>, ctx->B, ctx->P, S, A, hr, hw, 1);
-  else e = cudaLaunchKernelEx(&cfg, k_steps_persist<false, true>, ctx->B, ctx->P, S, A, hr, hw, 1);
+  e = cudaLaunchKernelEx(&cfg, persist_kernel(uni, frozen, ctx->persist_tpa), ctx->B, ctx->P, S, A, hr, hw, 1);
   cudaStreamCaptureStatus cs;
   cudaGraph_t cg;
   const cudaGraphNode_t* deps = nullptr;
@@ -935,29 +952,39 @@ static int plan_impl(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int list_
   if (S > 0 && ctx->precision == MDGP_PREC_FP32 && ctx->params.persistent) {
     // Persistent grid: R co-resident blocks per SM, each taking A = N / (R x
     // SMs) atoms rounded up, so that every SM holds about N / SMs atoms (the
-    // step ends with the most loaded SM); the block is A rounded up to whole
-    // warps.  The R with the fewest warps per SM (the least idle lanes) among
-    // those that fit wins.
+    // step ends with the most loaded SM); the block is A x TPA threads
+    // rounded up to whole warps.  The R with the fewest warps per SM (the
+    // least idle lanes) among those that fit wins.  TPA, the threads per
+    // atom, is the largest power of two up to 8 with N x TPA threads within
+    // the SMs' capacity for this kernel (one thread per atom for batches that
+    // fill the GPU; several share an atom's pair loop in smaller ones, which
+    // shortens the step's critical path) unless the parameters fix it.
     int sms = 0;
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
     const bool uni = ctx->P.uniform != 0, frozen = ctx->params.mode == 1;
-    auto occupancy = [&](int threads, int* per_sm) {
-      if (uni && !frozen) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_steps_persist<true, false>, threads, 0);
-      if (!uni && !frozen) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_steps_persist<false, false>, threads, 0);
-      if (uni) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_steps_persist<true, true>, threads, 0);
-      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_steps_persist<false, true>, threads, 0);
+    auto occupancy = [&](int tpa, int threads, int* per_sm) {
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, persist_kernel(uni, frozen, tpa), threads, 0);
     };
+    int tpa = ctx->params.threads_per_atom;
+    if (tpa <= 0) {
+      int per_sm = 0;
+      if (occupancy(1, 256, &per_sm) != cudaSuccess) return set_err(ctx, cudaGetLastError());
+      const long long cap = (long long)sms * per_sm * 256;
+      tpa = 1;
+      while (tpa < 8 && atoms * (2 * tpa) <= cap) tpa *= 2;
+    }
+    ctx->persist_tpa = tpa;
     ctx->persist_grid = 0;
     long long best_warps = 1LL << 40;
     for (int R = 1; R <= 32; ++R) {
       const long long slots = (long long)sms * R;
       const long long A = (atoms + slots - 1) / slots;
-      const int T = (int)((A + 31) / 32 * 32);
+      const int T = (int)((A * tpa + 31) / 32 * 32);
       // at least 128 threads: smaller blocks put more separate atom ranges on
       // an SM and lose L1 reuse of the neighbour positions (measured slower)
       if (T > 256 || T < 128) continue;   // larger batches: 256-thread blocks striding over chunks
       int per_sm = 0;
-      if (occupancy(T, &per_sm) != cudaSuccess) return set_err(ctx, cudaGetLastError());
+      if (occupancy(tpa, T, &per_sm) != cudaSuccess) return set_err(ctx, cudaGetLastError());
       const long long warps = (long long)R * (T / 32);
       if (per_sm >= R && warps < best_warps) {
         best_warps = warps;
@@ -968,9 +995,10 @@ static int plan_impl(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int list_
     }
     if (ctx->persist_grid == 0) {
       int per_sm = 0;
-      if (occupancy(256, &per_sm) != cudaSuccess) return set_err(ctx, cudaGetLastError());
-      const long long chunks = (atoms + 255) / 256, cap = (long long)per_sm * sms;
-      ctx->persist_atoms = 256;
+      if (occupancy(tpa, 256, &per_sm) != cudaSuccess) return set_err(ctx, cudaGetLastError());
+      const int A = 256 / tpa;
+      const long long chunks = (atoms + A - 1) / A, cap = (long long)per_sm * sms;
+      ctx->persist_atoms = A;
       ctx->persist_threads = 256;
       ctx->persist_grid = (unsigned)(chunks < cap ? chunks : cap);
     }
@@ -1066,10 +1094,7 @@ static int run_direct(mdgp_ctx* ctx) {
   for (long long guard = 0; guard <= S; ++guard) {
     CK(cudaEventRecord(ctx->dir_ev[1], ctx->stream));
     cudaError_t e;
-    if (uni && !frozen) e = cudaLaunchKernelEx(&cfg, k_steps_persist<true, false>, ctx->B, ctx->P, S, A, h0, h0, 0);
-    else if (!uni && !frozen) e = cudaLaunchKernelEx(&cfg, k_steps_persist<false, false>, ctx->B, ctx->P, S, A, h0, h0, 0);
-    else if (uni) e = cudaLaunchKernelEx(&cfg, k_steps_persist<true, true>, ctx->B, ctx->P, S, A, h0, h0, 0);
-    else e = cudaLaunchKernelEx(&cfg, k_steps_persist<false, true>, ctx->B, ctx->P, S, A, h0, h0, 0);
+    e = cudaLaunchKernelEx(&cfg, persist_kernel(uni, frozen, ctx->persist_tpa), ctx->B, ctx->P, S, A, h0, h0, 0);
     if (e != cudaSuccess) return set_err(ctx, e);
     CK(cudaEventRecord(ctx->dir_ev[2], ctx->stream));
     ++ctx->launches;
@@ -1235,7 +1260,8 @@ static bool params_valid(const mdgp_md_params* p) {
   return p->dt > 0 && p->rc > 0 && p->n_blocks >= 1 && p->wall_planes >= 1 && p->mass > 0 &&
          p->wall_density > 0 && p->gamma_wall >= 0 && p->list_capacity >= 0 && p->skin >= 0 &&
          p->rebuild_every >= 0 && (p->build_variant == 0 || p->build_variant == 3) && p->persistent >= 0 &&
-         p->persistent <= 2;
+         p->persistent <= 2 && (p->threads_per_atom == 0 || p->threads_per_atom == 1 || p->threads_per_atom == 2 ||
+                                p->threads_per_atom == 4 || p->threads_per_atom == 8);
 }
 
 int mdgp_set_md_params(mdgp_ctx* ctx, const mdgp_md_params* p) {
@@ -1308,6 +1334,16 @@ int mdgp_micro_path(const mdgp_ctx* ctx) {
   if (!ctx) return MDGP_E_ARG;
   if (!ctx->planned) return MDGP_E_STATE;
   return ctx->direct ? 2 : (ctx->graph_while ? 1 : 0);
+}
+
+int mdgp_micro_launch_shape(const mdgp_ctx* ctx, int32_t* out) {
+  if (!ctx || !out) return MDGP_E_ARG;
+  if (!ctx->planned || !(ctx->direct || ctx->graph_while)) return MDGP_E_STATE;
+  out[0] = (int32_t)ctx->persist_grid;
+  out[1] = ctx->persist_threads;
+  out[2] = ctx->persist_atoms;
+  out[3] = ctx->persist_tpa;
+  return MDGP_OK;
 }
 
 int64_t mdgp_micro_rebuild_count(const mdgp_ctx* ctx) { return ctx ? ctx->rebuilds : -1; }

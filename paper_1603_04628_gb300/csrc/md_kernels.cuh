@@ -977,6 +977,168 @@ __device__ __forceinline__ PairAcc<PT, T, UNIFORM, ENERGY> pair_force(const Batc
   return acc;
 }
 
+// ---------------------------------------------------------------------------
+// FP32 pair forces with packed two-lane arithmetic.  The SMs of this GPU
+// family execute add, mul and fma on two FP32 values held in one 64-bit
+// register pair (PTX .f32x2) as one instruction.  The loop below takes its
+// list entries two at a time and evaluates both pair terms with each packed
+// instruction; per pair the arithmetic is PairAcc's (Eq. LJ): d = (p_i - p_j)
+// - delta * cs, r^2, 1/r^2 by rcp.approx, F/r = eps (1/r^2) s^6 (48 s^6 - 24)
+// with s^2 = sig^2 / r^2, and 1/r^2 set to zero beyond r_c or for an inactive
+// pair type, so that such an entry adds nothing.
+// With TPA > 1, TPA consecutive lanes share an atom: lane `sub` of the group
+// takes the list groups sub, sub + TPA, ... and the sums are combined by
+// shuffles, so every lane of the group returns the atom's totals.
+// ---------------------------------------------------------------------------
+typedef unsigned long long f2x;   // two FP32 values: bits 0-31 and 32-63
+
+__device__ __forceinline__ f2x f2_pk(float lo, float hi) {
+  f2x r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2_upk(f2x v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2x f2_add(f2x a, f2x b) {
+  f2x r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2x f2_mul(f2x a, f2x b) {
+  f2x r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2x f2_fma(f2x a, f2x b, f2x c) {
+  f2x r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
+// Per-atom constants of the packed pair loop: the negated cell side in both
+// lanes, and for the neighbour species 0 / 1 the pair type's eps, sig^2,
+// energy shift and whether it interacts.
+struct PairConst {
+  f2x ncsx, ncsy, ncsz, cmh;   // -cs per axis; (-1/2, -1/2)
+  float rc2;
+  float eps0, eps1, sig0, sig1, esh0, esh1;
+  bool act0, act1;
+};
+
+struct PairSum {
+  float fx, fy, fz, w, u;
+};
+
+template <bool UNIFORM, bool ENERGY>
+struct PairAcc2 {
+  f2x fx = 0ull, fy = 0ull, fz = 0ull, w = 0ull;   // all-zero bits: (0, 0)
+  float u = 0.f;
+  __device__ __forceinline__ void add(const float4& me, const float4& oa, const float4& ob, unsigned ea,
+                                      unsigned eb, const PairConst& c, const ShiftTab& tab) {
+    const unsigned ka = ea >> 26, kb = eb >> 26;
+    const f2x dx = f2_fma(f2_pk(tab.d[0][ka], tab.d[0][kb]), c.ncsx, f2_pk(me.x - oa.x, me.x - ob.x));
+    const f2x dy = f2_fma(f2_pk(tab.d[1][ka], tab.d[1][kb]), c.ncsy, f2_pk(me.y - oa.y, me.y - ob.y));
+    const f2x dz = f2_fma(f2_pk(tab.d[2][ka], tab.d[2][kb]), c.ncsz, f2_pk(me.z - oa.z, me.z - ob.z));
+    const f2x r2 = f2_fma(dz, dz, f2_fma(dy, dy, f2_mul(dx, dx)));
+    float r2a, r2b;
+    f2_upk(r2, r2a, r2b);
+    bool ina = r2a < c.rc2, inb = r2b < c.rc2;
+    float sga = 1.f, sgb = 1.f, epa = 1.f, epb = 1.f, sha = 0.f, shb = 0.f;
+    if constexpr (!UNIFORM) {
+      const bool wa = oa.w != 0.f, wb = ob.w != 0.f;
+      ina = ina && (wa ? c.act1 : c.act0);
+      inb = inb && (wb ? c.act1 : c.act0);
+      sga = wa ? c.sig1 : c.sig0; sgb = wb ? c.sig1 : c.sig0;
+      epa = wa ? c.eps1 : c.eps0; epb = wb ? c.eps1 : c.eps0;
+      if (ENERGY) { sha = wa ? c.esh1 : c.esh0; shb = wb ? c.esh1 : c.esh0; }
+    } else if (ENERGY) {
+      sha = c.esh0; shb = c.esh0;
+    }
+    const float ia = ina ? rcp_approx(r2a) : 0.f, ib = inb ? rcp_approx(r2b) : 0.f;
+    const f2x inv2 = f2_pk(ia, ib);
+    const f2x s2 = UNIFORM ? inv2 : f2_mul(f2_pk(sga, sgb), inv2);
+    const f2x s6 = f2_mul(f2_mul(s2, s2), s2);
+    // F/r over 48: eps (1/r^2) s^6 (s^6 - 1/2); the sums are scaled by 48 at the end
+    f2x fs = f2_mul(f2_mul(inv2, s6), f2_add(s6, c.cmh));
+    if constexpr (!UNIFORM) fs = f2_mul(fs, f2_pk(epa, epb));
+    const f2x tx = f2_mul(fs, dx);
+    fx = f2_add(fx, tx);
+    fy = f2_fma(fs, dy, fy);
+    fz = f2_fma(fs, dz, fz);
+    w = f2_fma(tx, dx, w);
+    if constexpr (ENERGY) {
+      float s6a, s6b;
+      f2_upk(s6, s6a, s6b);
+      u += ina ? 4.f * epa * (s6a * s6a - s6a) - sha : 0.f;
+      u += inb ? 4.f * epb * (s6b * s6b - s6b) - shb : 0.f;
+    }
+  }
+};
+
+template <int TPA>
+__device__ __forceinline__ float group_sum(float v) {
+#pragma unroll
+  for (int o = 1; o < TPA; o <<= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+template <bool UNIFORM, bool ENERGY, int TPA>
+__device__ __forceinline__ PairSum pair_force_f32(const BatchDev& B, const PhysDev& P, long long i, int sub,
+                                                  const float4* pos, int& spi, const ShiftTab& tab) {
+  PairAcc2<UNIFORM, ENERGY> acc;
+  int n = 0;
+  if (i < B.n_atoms) {
+    const ElemDev& E = B.el[__ldcg(B.atom_el + i)];
+    const float4 me = pos[i];
+    const float4* posj = pos + E.atom0;
+    n = __ldcg(B.nlist + i);
+    spi = me.w != 0.f ? 1 : 0;
+    PairConst c;
+    const float csx = E.csf[0], csy = E.csf[1], csz = E.csf[2];
+    c.ncsx = f2_pk(-csx, -csx); c.ncsy = f2_pk(-csy, -csy); c.ncsz = f2_pk(-csz, -csz);
+    c.cmh = f2_pk(-0.5f, -0.5f);
+    c.rc2 = P.rc2f;
+    c.eps0 = P.epsf[spi]; c.eps1 = P.epsf[spi + 1];
+    c.sig0 = P.sig2f[spi]; c.sig1 = P.sig2f[spi + 1];
+    c.esh0 = (float)P.eshift[spi]; c.esh1 = (float)P.eshift[spi + 1];
+    c.act0 = P.active[spi] != 0; c.act1 = P.active[spi + 1] != 0;
+    const uint4* L4 = reinterpret_cast<const uint4*>(B.list) + i;
+    const long long N = B.n_atoms;
+    const int ng = (n + 3) >> 2;
+    int k = sub;
+    // two groups of four entries per iteration: eight gathers in flight
+    for (; k + TPA < ng; k += 2 * TPA) {
+      const uint4 e = ld_list4(L4 + (long long)k * N);
+      const uint4 f = ld_list4(L4 + (long long)(k + TPA) * N);
+      const float4 o0 = posj[e.x & kJMask], o1 = posj[e.y & kJMask], o2 = posj[e.z & kJMask],
+                   o3 = posj[e.w & kJMask];
+      const float4 o4 = posj[f.x & kJMask], o5 = posj[f.y & kJMask], o6 = posj[f.z & kJMask],
+                   o7 = posj[f.w & kJMask];
+      acc.add(me, o0, o1, e.x, e.y, c, tab);
+      acc.add(me, o2, o3, e.z, e.w, c, tab);
+      acc.add(me, o4, o5, f.x, f.y, c, tab);
+      acc.add(me, o6, o7, f.z, f.w, c, tab);
+    }
+    if (k < ng) {
+      const uint4 e = ld_list4(L4 + (long long)k * N);
+      const float4 o0 = posj[e.x & kJMask], o1 = posj[e.y & kJMask], o2 = posj[e.z & kJMask],
+                   o3 = posj[e.w & kJMask];
+      acc.add(me, o0, o1, e.x, e.y, c, tab);
+      acc.add(me, o2, o3, e.z, e.w, c, tab);
+    }
+  }
+  float ax, bx, ay, by, az, bz, aw, bw;
+  f2_upk(acc.fx, ax, bx); f2_upk(acc.fy, ay, by); f2_upk(acc.fz, az, bz); f2_upk(acc.w, aw, bw);
+  PairSum r{48.f * (ax + bx), 48.f * (ay + by), 48.f * (az + bz), 48.f * (aw + bw), acc.u};
+  if constexpr (TPA > 1) {
+    r.fx = group_sum<TPA>(r.fx); r.fy = group_sum<TPA>(r.fy); r.fz = group_sum<TPA>(r.fz);
+    r.w = group_sum<TPA>(r.w);
+    if (ENERGY) r.u = group_sum<TPA>(r.u);
+  }
+  return r;
+}
+
 // Pair forces of step *step_base + k into fx, fy, fz (+ virial share, energy).
 template <typename PT, typename T, bool UNIFORM, bool ENERGY>
 __global__ void __launch_bounds__(128) k_force(BatchDev B, PhysDev P, int k) {
@@ -986,14 +1148,22 @@ __global__ void __launch_bounds__(128) k_force(BatchDev B, PhysDev P, int k) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= B.n_atoms) return;
   const long long s = *B.step_base + k;
-  int spi;
-  const PairAcc<PT, T, UNIFORM, ENERGY> acc =
-      pair_force<PT, T, UNIFORM, ENERGY>(B, P, i, static_cast<const PT*>(B.posb[s & 1]), spi, tab);
-  static_cast<T*>(B.fx)[i] = acc.fx;
-  static_cast<T*>(B.fy)[i] = acc.fy;
-  static_cast<T*>(B.fz)[i] = acc.fz;
-  static_cast<T*>(B.wxx)[i] = spi == 0 ? (T)0.5 * acc.w : (T)0;
-  if (ENERGY) static_cast<T*>(B.epot)[i] = (T)0.5 * acc.u;
+  int spi = 0;
+  T afx, afy, afz, aw, au;
+  if constexpr (sizeof(T) == 4) {
+    const PairSum acc =
+        pair_force_f32<UNIFORM, ENERGY, 1>(B, P, i, 0, static_cast<const float4*>(B.posb[s & 1]), spi, tab);
+    afx = acc.fx; afy = acc.fy; afz = acc.fz; aw = acc.w; au = acc.u;
+  } else {
+    const PairAcc<PT, T, UNIFORM, ENERGY> acc =
+        pair_force<PT, T, UNIFORM, ENERGY>(B, P, i, static_cast<const PT*>(B.posb[s & 1]), spi, tab);
+    afx = acc.fx; afy = acc.fy; afz = acc.fz; aw = acc.w; au = acc.u;
+  }
+  static_cast<T*>(B.fx)[i] = afx;
+  static_cast<T*>(B.fy)[i] = afy;
+  static_cast<T*>(B.fz)[i] = afz;
+  static_cast<T*>(B.wxx)[i] = spi == 0 ? (T)0.5 * aw : (T)0;
+  if (ENERGY) static_cast<T*>(B.epot)[i] = (T)0.5 * au;
 }
 
 // ---------------------------------------------------------------------------
@@ -1378,9 +1548,8 @@ __global__ void __launch_bounds__(128) k_step_df(BatchDev B, PhysDev P, int k, i
   StepOut o;
   if (i < B.n_atoms) {
     const float4* pos = static_cast<const float4*>(B.posb[s & 1]);
-    int spi;
-    const PairAcc<float4, float, UNIFORM, false> f =
-        pair_force<float4, float, UNIFORM, false>(B, P, i, pos, spi, tab);
+    int spi = 0;
+    const PairSum f = pair_force_f32<UNIFORM, false, 1>(B, P, i, 0, pos, spi, tab);
     const float wxx = spi == 0 ? 0.5f * f.w : 0.0f;
     if (STORE) {
       static_cast<float*>(B.fx)[i] = f.fx;
@@ -1452,16 +1621,19 @@ __device__ __forceinline__ bool grid_barrier(int* flags, unsigned long long wait
 // that gives up marks every element MDGP_E_TIMEOUT and ends the run.  Block c
 // takes atoms [c A, (c + 1) A) with A <= blockDim.x chosen by the host so
 // that every SM holds the same number of atoms (the step ends with the
-// most loaded SM).
-template <bool UNIFORM, bool FROZEN>
-__global__ void __launch_bounds__(256, 5) k_steps_persist(BatchDev B, PhysDev P, long long S, int A,
+// most loaded SM).  TPA consecutive threads share an atom's pair forces
+// (batches too small to fill the GPU with one thread per atom): the group's
+// first thread integrates the atom.
+template <bool UNIFORM, bool FROZEN, int TPA>
+__global__ void __maxnreg__(56) k_steps_persist(BatchDev B, PhysDev P, long long S, int A,
                                                       cudaGraphConditionalHandle h_rebuild,
                                                       cudaGraphConditionalHandle h_more, int use_cond) {
   __shared__ ShiftTab tab;
   shift_tab_init(tab);
   __syncthreads();
   const long long nchunks = (B.n_atoms + A - 1) / A;
-  const bool lane_used = (int)threadIdx.x < A;
+  const int slot = (int)threadIdx.x / TPA, sub = (int)threadIdx.x % TPA;
+  const bool lane_used = slot < A;
   long long s = *B.step_base;
   bool rebuild = false, failed = false, first_wait = true;
   while (s < S && !failed) {
@@ -1470,12 +1642,11 @@ __global__ void __launch_bounds__(256, 5) k_steps_persist(BatchDev B, PhysDev P,
     const float4* pos = static_cast<const float4*>(B.posb[s & 1]);
     const int m1 = FROZEN ? (kFinish | kTzSum) : (kFinish | kStage1);
     for (long long c = blockIdx.x; c < nchunks; c += gridDim.x) {
-      const long long i = lane_used ? c * A + threadIdx.x : B.n_atoms;
+      const long long i = lane_used ? c * A + slot : B.n_atoms;
       StepOut o;
-      if (i < B.n_atoms) {
-        int spi;
-        const PairAcc<float4, float, UNIFORM, false> f =
-            pair_force<float4, float, UNIFORM, false>(B, P, i, pos, spi, tab);
+      int spi = 0;
+      const PairSum f = pair_force_f32<UNIFORM, false, TPA>(B, P, i, sub, pos, spi, tab);
+      if (i < B.n_atoms && sub == 0) {
         const float wxx = spi == 0 ? 0.5f * f.w : 0.0f;
         if (FROZEN) {
           static_cast<float*>(B.fx)[i] = f.fx;
@@ -1492,9 +1663,9 @@ __global__ void __launch_bounds__(256, 5) k_steps_persist(BatchDev B, PhysDev P,
     if (FROZEN) {
       const int m2 = kTzApply | kStage1;
       for (long long c = blockIdx.x; c < nchunks; c += gridDim.x) {
-        const long long i = lane_used ? c * A + threadIdx.x : B.n_atoms;
+        const long long i = lane_used ? c * A + slot : B.n_atoms;
         StepOut o;
-        if (i < B.n_atoms)
+        if (i < B.n_atoms && sub == 0)
           integrate_df_atom<FROZEN>(B, P, i, s, m2, skin, static_cast<const float*>(B.fx)[i],
                                     static_cast<const float*>(B.fy)[i], static_cast<const float*>(B.fz)[i],
                                     static_cast<const float*>(B.wxx)[i], o);

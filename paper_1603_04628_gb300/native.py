@@ -45,7 +45,7 @@ class MDParams(ctypes.Structure):
                 ("wall_planes", ctypes.c_int32), ("list_capacity", ctypes.c_int32),
                 ("skin", ctypes.c_double), ("rebuild_every", ctypes.c_int32), ("build_variant", ctypes.c_int32),
                 ("persistent", ctypes.c_int32), ("wait_timeout_ms", ctypes.c_int32),
-                ("inject_barrier_skip", ctypes.c_int32)]
+                ("inject_barrier_skip", ctypes.c_int32), ("threads_per_atom", ctypes.c_int32)]
 
 
 class GPParams(ctypes.Structure):
@@ -127,6 +127,7 @@ def lib():
         "mdgp_micro_launch_count": ([vp], i64),
         "mdgp_micro_rebuild_count": ([vp], i64),
         "mdgp_micro_path": ([vp], ctypes.c_int),
+        "mdgp_micro_launch_shape": ([vp, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
         "mdgp_micro_state": ([vp, dp, dp, i64], ctypes.c_int),
         "mdgp_md_forces": ([vp, ctypes.POINTER(Element), dp, i64, dp, dp, dp], ctypes.c_int),
         "mdgp_micro_profile": ([vp, i64, dp], ctypes.c_int),
@@ -336,6 +337,13 @@ class Context:
         if code < 0:
             raise MdgpError("mdgp_micro_path: %s" % STATUS.get(code, code))
         return {0: "per-step", 1: "persistent-graph", 2: "persistent-direct"}[code]
+
+    def launch_shape(self):
+        """The persistent step kernel's launch: blocks, threads per block,
+        atoms per block and threads per atom (mdgp_micro_launch_shape)."""
+        out = (ctypes.c_int32 * 4)()
+        _check(self.h, lib().mdgp_micro_launch_shape(self.h, out), "mdgp_micro_launch_shape")
+        return {"blocks": out[0], "threads": out[1], "atoms_per_block": out[2], "threads_per_atom": out[3]}
 
     def micro_state(self):
         x = np.zeros((self.n_atoms, 3))

