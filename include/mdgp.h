@@ -73,6 +73,12 @@ typedef struct {
   uint64_t seed;     /* Philox key */
   int32_t flags;     /* reserved, 0 */
   int32_t id;        /* element id: Philox counter word 2 */
+  double wall_amp;   /* 0: planar walls h apart.  In [0, 1): the walls follow
+                        h(x) = h (1 - wall_amp cos(2 pi x / Lx)) symmetrically about the
+                        mid-plane of the widest gap h (1 + wall_amp) -- one element is then
+                        a whole periodic converging-diverging channel (the full MD of
+                        Sec. 3); N_fluid = round(n Lx h Lz) fills the gap at uniform
+                        density, P_xx is over the fluid volume Lx h Lz.  FP32 and FP64. */
 } mdgp_element;
 
 /* Time-averaged outputs of one element. */
@@ -230,6 +236,22 @@ int64_t mdgp_micro_launch_count(const mdgp_ctx* ctx);
  * graphs), 1 the persistent kernel in a graph WHILE loop, 2 the persistent
  * kernel launched by the host.  MDGP_E_STATE without a plan. */
 int mdgp_micro_path(const mdgp_ctx* ctx);
+
+/* Continue the last launch's batch from where it ended: another
+ * steps_eq + steps_sample steps (the plan's count) from the device state the
+ * last mdgp_micro_launch or mdgp_micro_continue left, with every measurement
+ * taken afresh over them (steps_eq of them unsampled, as in the plan) and the
+ * energy drift measured from the continued start.  g_ext and dpdx (n
+ * elements each, the plan's order; either may be NULL to keep the last
+ * value) give each element's new forcing, Eq. momentumEq with the element's
+ * density.  The Langevin noise continues its stream (the step counter of
+ * the Philox counter runs on), so a plan of S steps continued once follows
+ * the same trajectory as one of 2 S steps up to the summation order of a
+ * list rebuilt at the boundary.  Used to run a full-channel MD in windows
+ * with the forcing of each macro step (Sec. 3).  Enqueued on the context's
+ * stream; results by mdgp_micro_results.  MDGP_E_STATE without a launch on
+ * the current plan. */
+int mdgp_micro_continue(mdgp_ctx* ctx, const double* g_ext, const double* dpdx);
 
 /* Launch shape of the planned batch's persistent step kernel (FP32 pair
  * forces, persistent = 1 or 2): out[0] = blocks, out[1] = threads per block,
@@ -400,10 +422,12 @@ typedef struct mdgp_hybrid mdgp_hybrid;
 /* Converging-diverging periodic channel and its coupling (Sec. 2.1):
  * n_sections sections at x_j = j dx (Eq. subsEq, L = n_sections dx) with
  * h_j = h0 (1 - 0.5 cos(2 pi x_j / L)); pressure p = eos_K (n - eos_n0);
- * forcing dP(t) = dP_amp sin(2 pi t / period) applied as the uniform
- * gradient -dP / L; section j's GP input is (h_j, G_j) with
- * G_j = dp/dx_j - dP / L (central differences) and its MD element gets
- * dpdx = G_j (Eq. momentumEq); density update by Eq. continuityEq with
+ * forcing dP(t) = dP_amp sin(2 pi t / period), an inlet-outlet pressure
+ * difference turned into the external force F_ext = dP / (L eos_n0) that
+ * every fluid atom of the channel feels (Eq. momentumEq's F_ext); section
+ * j's GP input is (h_j, G_j) with G_j = dp/dx_j - n_j F_ext (central
+ * differences) and its MD element gets dpdx = G_j, i.e. the body force
+ * F = F_ext - dp/dx_j / n_j (Eq. momentumEq); density update by Eq. continuityEq with
  * A_j = h_j Lz.  The MD elements are Lx x Lz x h_j at the section's density. */
 typedef struct {
   int32_t n_sections;     /* >= 3 */

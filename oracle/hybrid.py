@@ -14,12 +14,13 @@ for the parts the paper leaves open are marked READING):
     fitted once to pressures measured in pre-simulations and evaluated at
     its posterior mean;
   - pressure gradient by periodic central differences (Alg. 1, the p' line);
-  - READING: the sinusoidal inlet-outlet pressure difference
-    dP(t) = dP_A sin(2 pi t / period) of the periodic channel acts as a
-    uniform gradient -dP / L; with G_j = dp/dx_j - dP / L an MD element gets
-    dpdx = G_j, so every fluid atom feels F = -G_j / n_j (Eq. momentumEq
-    with F_ext folded into G); the q-GP input is x = (h_j, G_j), or the
-    paper's (h_j, n_j, F_j) (inputs = 1);
+  - Eq. momentumEq: every fluid atom feels F_j = F_ext - p'_j / n_j, the
+    external force F_ext the same on every atom of the channel (Algorithm 1
+    sets one F_ext^i per macro step).  READING: its amplitude is given as an
+    inlet-outlet pressure difference dP(t) = dP_A sin(2 pi t / period) at the
+    initial density, F_ext = dP / (L n0); an MD element gets
+    dpdx = G_j = p'_j - n_j F_ext, so that F = -G_j / n_j; the q-GP input is
+    x = (h_j, G_j), or the paper's (h_j, n_j, F_j) (inputs = 1);
   - q-GP (Eqs. quadraticKernelEq-predVarEq) on the database of (x, q) pairs,
     refit whenever the database grows; gate sd > sigma_t (strict);
   - READING: sigma_n is fixed during a macro step.  The paper measured it
@@ -93,7 +94,8 @@ class Channel:
         p = self.pressure()
         dpdx = (np.roll(p, -1) - np.roll(p, 1)) / (2.0 * self.dx)
         dP = self.dP_amp * math.sin(2.0 * math.pi * t / self.period)
-        return dpdx - dP / (self.N * self.dx)
+        f_ext = dP / (self.N * self.dx * self.n0)     # uniform external force per atom
+        return dpdx - self.n * f_ext
 
     def element(self, j, G, call_id):
         return dict(h=float(self.h[j]), dpdx=float(G), density=float(self.n[j]), T=self.T,

@@ -31,7 +31,7 @@ class Params(ctypes.Structure):
         ("fluid_margin", ctypes.c_double), ("tau_T", ctypes.c_double), ("mass", ctypes.c_double),
         ("steps_eq", ctypes.c_int64), ("steps_sample", ctypes.c_int64),
         ("seed", ctypes.c_uint64), ("elem_id", ctypes.c_int32), ("n_blocks", ctypes.c_int32),
-        ("mode", ctypes.c_int32), ("wall_planes", ctypes.c_int32),
+        ("mode", ctypes.c_int32), ("wall_planes", ctypes.c_int32), ("wall_amp", ctypes.c_double),
     ]
 
 
@@ -135,6 +135,7 @@ def make_params(element, **physics):
     p.seed = int(element.get("seed", 0)) & 0xFFFFFFFFFFFFFFFF
     p.elem_id = int(element.get("id", 0))
     p.n_blocks, p.mode, p.wall_planes = int(kw["n_blocks"]), int(kw["mode"]), int(kw["wall_planes"])
+    p.wall_amp = float(element.get("wall_amp", 0.0))
     return p
 
 

@@ -15,7 +15,11 @@
  *     flow rate q = (m / L_x) * sum_fluid v_x, and Sec. 2.2 / 2.3 footnote the
  *     cross-section averaged pressure (here P_xx from the virial);
  *   - Sec. 2.3: the standard error of the mean output from the raw
- *     time-instantaneous samples (block averaging).
+ *     time-instantaneous samples (block averaging);
+ *   - Sec. 3 (the full MD the hybrid is judged against): with wall_amp > 0
+ *     the walls follow the converging-diverging profile h(x) of the channel
+ *     (the benchmark's form of the paper's channel shape), so that one
+ *     element of length L is a whole periodic channel.
  * Readings where the paper is silent (tethered FCC walls, G-JF Langevin
  * thermostat on wall atoms, lattice layout, block count) are listed in the
  * design notes and restated at each function below.
@@ -61,6 +65,8 @@ typedef struct {
   int32_t mode;       /* 0: tethered walls + Langevin walls; 1: frozen walls + Berendsen on fluid v_z;
                          2: bulk test box (no walls, periodic in y with L_y = h) */
   int32_t wall_planes;
+  double wall_amp;    /* walls following h(x) = h (1 - wall_amp cos(2 pi x / Lx)) about the
+                         mid-plane of the widest gap H = h (1 + wall_amp); 0: planar walls */
 } or_params;
 
 typedef struct {
@@ -149,11 +155,15 @@ int64_t or_n_wall(const or_params* P) {
   return (int64_t)2 * P->wall_planes * 2 * nx * nz;
 }
 
+/* The widest gap between the walls: h for planar walls, h (1 + wall_amp)
+ * for walls that follow the profile (the box is built for it). */
+static double or_gap_max(const or_params* P) { return P->h * (1.0 + P->wall_amp); }
+
 /* Fluid FCC lattice cell counts: spacing near (4/n)^(1/3), enough sites. */
 static void or_fluid_cells(const or_params* P, int64_t nf, long* cx, long* cy, long* cz, double* y0, double* ly) {
   double af = cbrt(4.0 / P->density);
   if (P->mode == 2) { *y0 = 0.0; *ly = P->h; }
-  else { *y0 = P->fluid_margin; *ly = P->h - 2.0 * P->fluid_margin; }
+  else { *y0 = P->fluid_margin; *ly = or_gap_max(P) - 2.0 * P->fluid_margin; }
   *cx = (long)ceil(P->Lx / af - 1e-9);
   *cy = (long)ceil(*ly / af - 1e-9);
   *cz = (long)ceil(P->Lz / af - 1e-9);
@@ -170,14 +180,67 @@ static void or_fluid_cells(const or_params* P, int64_t nf, long* cx, long* cy, l
 /* Build positions, anchors and species (0 fluid, 1 wall) and Maxwell-Boltzmann
  * velocities.  Atom order: fluid atoms first, then the bottom wall planes
  * (k = 0, 1, 2 going outwards), then the top wall planes. */
+/* Walls that follow the profile (wall_amp > 0): the local gap at x and the
+ * height of the lower wall's inner plane, yb(x) = (H - h(x)) / 2, so that
+ * both walls are symmetric about the mid-plane of the widest gap H. */
+static void or_profile(const or_params* P, double x, double* hx, double* yb) {
+  *hx = P->h * (1.0 - P->wall_amp * cos(2.0 * M_PI * x / P->Lx));
+  *yb = 0.5 * (or_gap_max(P) - *hx);
+}
+
+static const double or_basis[4][3] = {{0, 0, 0}, {0.5, 0.5, 0}, {0.5, 0, 0.5}, {0, 0.5, 0.5}};
+
+/* Fluid of a profiled element: the FCC lattice of the widest gap, its sites
+ * taken in lattice order and kept where they lie at least the fluid margin
+ * inside the local walls; the lattice grows (y, x, z in turn) until enough
+ * sites are kept, and the vacancies are spread evenly over the kept sites. */
+static int or_init_fluid_profiled(const or_params* P, int64_t nf, double* x) {
+  long cx, cy, cz; double y0, ly;
+  or_fluid_cells(P, nf, &cx, &cy, &cz, &y0, &ly);
+  double m = P->fluid_margin;
+  for (int turn = 0;; ++turn) {
+    double bx = P->Lx / cx, by = ly / cy, bz = P->Lz / cz;
+    int64_t sites = (int64_t)4 * cx * cy * cz, kept = 0;
+    double* pos = (double*)malloc(sizeof(double) * 3 * (size_t)sites);
+    if (!pos) return -1;
+    for (int64_t s = 0; s < sites; ++s) {
+      int64_t b = s % 4, c = s / 4;
+      int64_t iz = c % cz, iy = (c / cz) % cy, ix = c / (cz * cy);
+      double px = (ix + or_basis[b][0] + 0.25) * bx;
+      double py = y0 + (iy + or_basis[b][1] + 0.25) * by;
+      double pz = (iz + or_basis[b][2] + 0.25) * bz;
+      double hx, yb;
+      or_profile(P, px, &hx, &yb);
+      if (py >= yb + m && py <= yb + hx - m) {
+        pos[3 * kept] = px; pos[3 * kept + 1] = py; pos[3 * kept + 2] = pz;
+        ++kept;
+      }
+    }
+    if (kept >= nf) {
+      for (int64_t i = 0; i < nf; ++i) {
+        int64_t k = (int64_t)(((__int128)i * kept) / nf);
+        for (int d = 0; d < 3; ++d) x[3 * i + d] = pos[3 * k + d];
+      }
+      free(pos);
+      return 0;
+    }
+    free(pos);
+    if (turn % 3 == 0) ++cy; else if (turn % 3 == 1) ++cx; else ++cz;
+  }
+}
+
 int or_init(const or_params* P, double* x, double* v, double* anchor, int32_t* sp) {
   int64_t nf = or_n_fluid(P), nw = or_n_wall(P), n = nf + nw;
   long cx, cy, cz; double y0, ly;
   or_fluid_cells(P, nf, &cx, &cy, &cz, &y0, &ly);
   double bx = P->Lx / cx, by = ly / cy, bz = P->Lz / cz;
-  static const double basis[4][3] = {{0, 0, 0}, {0.5, 0.5, 0}, {0.5, 0, 0.5}, {0, 0.5, 0.5}};
+  const double (*basis)[3] = or_basis;
   int64_t sites = (int64_t)4 * cx * cy * cz;
-  for (int64_t i = 0; i < nf; ++i) {
+  if (P->wall_amp > 0.0 && P->mode != 2) {
+    if (or_init_fluid_profiled(P, nf, x)) return -1;
+    for (int64_t i = 0; i < nf; ++i) sp[i] = 0;
+  }
+  for (int64_t i = 0; i < nf && !(P->wall_amp > 0.0 && P->mode != 2); ++i) {
     /* spread the vacancies evenly over the lattice */
     int64_t s = (int64_t)(((__int128)i * sites) / nf);
     int64_t b = s % 4, c = s / 4;
@@ -203,6 +266,12 @@ int or_init(const or_params* P, double* x, double* v, double* anchor, int32_t* s
               else { ox = t ? 0.0 : 0.5; oz = t ? 0.5 : 0.0; }
               x[3 * a + 0] = (i + ox) * ax;
               x[3 * a + 1] = y;
+              if (P->wall_amp > 0.0) {
+                /* the planes follow the local inner wall: yb(x) - k dy and yb(x) + h(x) + k dy */
+                double hx, yb;
+                or_profile(P, x[3 * a + 0], &hx, &yb);
+                x[3 * a + 1] = wall == 0 ? yb - k * dy : yb + hx + k * dy;
+              }
               x[3 * a + 2] = (j + oz) * az;
               sp[a] = 1;
               ++a;
@@ -335,7 +404,7 @@ void or_lj_cells(const or_params* P, int64_t n, const double* x, const int32_t* 
     long nx, nz; double a0;
     or_wall_cells(P, &nx, &nz, &a0);
     double th = 0.5 * a0 * (P->wall_planes - 1);
-    ylo = -th - 1.0; yhi = P->h + th + 1.0;
+    ylo = -th - 1.0; yhi = or_gap_max(P) + th + 1.0;
   }
   long ncx = (long)floor(P->Lx / P->rc), ncz = (long)floor(P->Lz / P->rc);
   long ncy = (long)floor((yhi - ylo) / P->rc);

@@ -209,6 +209,56 @@ def periodic_filter(ctx, t, q, period, sf2=1.0, l2=1.0, sn2=0.01, fit_until=None
     return mean, var, best["l2"], best["sn2"]
 
 
+def full_channel_md(ctx, n_steps, n_sections=200, dx=50.0, h0=12.0, Lz=10.0, eos_n0=0.8, dP_amp=400.0,
+                    period=1000.0, dt=20.0, T=1.1, seed=1, wall_amp=0.5, md_dt=0.005, sub_steps=400,
+                    eq_steps=10000, log=None, **_):
+    """The full MD of the channel (Sec. 3: the ground truth of Eqs. error and
+    speedup): one element of length L = n_sections dx whose walls follow
+    h(x) = h0 (1 - wall_amp cos(2 pi x / L)), fluid at n0, every fluid atom
+    driven by the external force F_ext(t) = dP_amp sin(2 pi t / period) /
+    (L n0) of the hybrid's macro model (Eq. momentumEq).  The run starts from
+    the lattice at rest, equilibrates eq_steps at F = 0 (t < 0), then runs
+    in windows of sub_steps MD steps, each continued from the last
+    (mdgp_micro_continue) with the force at the window's midpoint; Q_i is the
+    mean flow rate (m / L) sum v_x over the windows within half a macro step
+    of t_i = i dt, the time the hybrid's macro step i stands for.  The
+    context's MD parameters apply (dt must be md_dt).
+    Returns Q (n_steps), the window series (t, q), the atom count and the
+    measured MD wall time."""
+    L = n_sections * dx
+    per_macro = int(round(dt / md_dt))
+    if per_macro % sub_steps:
+        raise ValueError("a macro step must hold whole windows of sub_steps MD steps")
+    f_amp = dP_amp / (L * eos_n0)
+    el = dict(h=h0, Lx=L, Lz=Lz, density=eos_n0, T=T, steps_eq=0, steps_sample=sub_steps, g_ext=0.0,
+              seed=int(seed), id=0, wall_amp=wall_amp)
+    t0 = time.perf_counter()
+    n_atoms = ctx.micro_plan([el])
+    n_eq = max(1, int(math.ceil(eq_steps / sub_steps)))
+    ctx.micro_launch()
+    for _ in range(n_eq - 1):
+        ctx.micro_continue(g_ext=[0.0])
+    ctx.micro_results()
+    # windows from t = 0 to t_n + dt / 2
+    n_win = (n_steps * per_macro + per_macro // 2) // sub_steps
+    tw, qw = [], []
+    for k in range(n_win):
+        tm = (k + 0.5) * sub_steps * md_dt
+        ctx.micro_continue(g_ext=[f_amp * math.sin(2.0 * math.pi * tm / period)])
+        r = ctx.micro_results()[0]
+        if r["status"] != 0:
+            raise RuntimeError("full-channel MD window %d: status %d" % (k, r["status"]))
+        tw.append(tm)
+        qw.append(r["q"])
+        if log and k % 100 == 0:
+            log(dict(stage="full_md", window=k, of=n_win, t=tm, q=r["q"]))
+    wall = time.perf_counter() - t0
+    tw, qw = np.array(tw), np.array(qw)
+    Q = np.array([qw[np.abs(tw - (i + 1) * dt) <= 0.5 * dt].mean() for i in range(n_steps)])
+    return dict(Q=Q, t_windows=tw, q_windows=qw, n_atoms=int(n_atoms), wall_s=wall,
+                md_steps=(n_eq + n_win) * sub_steps, f_amp=f_amp)
+
+
 def md_database(ctx, n_elements, seed, h_range=(6.0, 18.0), G_range=(-0.06, 0.06), density=0.8, T=1.1,
                 steps_eq=1000, steps_sample=2000, Lx=10.0, Lz=10.0):
     """A training database from the library's MD: elements drawn uniformly over

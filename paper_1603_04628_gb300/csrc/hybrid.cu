@@ -411,8 +411,13 @@ int mdgp_hybrid_step(mdgp_hybrid* H, double sigma_t, mdgp_hybrid_stats* stats) {
   } else {
     for (int j = 0; j < N; ++j) pr[j] = P.eos_K * (H->n[j] - P.eos_n0);
   }
+  // Eq. momentumEq: every fluid atom feels F_j = F_ext - (m / rho_j) p'_j with
+  // the external force F_ext uniform over the channel; the inlet-outlet
+  // difference dP(t) sets it at the initial density, F_ext = dP / (L n0).
+  // G_j = p'_j - n_j F_ext is the gradient an element is given (F = -G / n).
+  const double f_ext = dP / (N * P.dx * P.eos_n0);
   for (int j = 0; j < N; ++j)
-    H->G[j] = (pr[(j + 1) % N] - pr[(j + N - 1) % N]) / (2.0 * P.dx) - dP / (N * P.dx);
+    H->G[j] = (pr[(j + 1) % N] - pr[(j + N - 1) % N]) / (2.0 * P.dx) - H->n[j] * f_ext;
   const double sn2 = sn2_for_step(H);
   const int D = H->D;
   std::vector<double> Xq((size_t)D * N);

@@ -44,16 +44,19 @@ struct mdgp_ctx {
   double dir_kernel_ms = 0.0, dir_rebuild_ms = 0.0;
   long long dir_steps = 0, dir_launches = 0, dir_rebuilds = 0;
   bool any_warm = false;      // some element of the plan starts from a snapshot
+  bool ran = false;           // a launch has run: the device state can be continued
+  std::vector<mdgp::ElemDev> el_host;   // the plan's element records (host copy)
+  std::vector<mdgp_element> el_desc;    // and the descriptors they came from
   long long launches = 0;              // kernels enqueued by the last launch (graph bodies: 2 per step)
   long long launches_with_rebuilds = 0;  // ... plus the rebuild kernels that ran
   long long rebuilds = 0;
   mdgp::BatchDev B;
   mdgp::PhysDev P;
   DevBuf d_el, d_aoff, d_coff, d_state, d_ints, d_cells, d_pos, d_pbuild, d_force, d_list, d_out, d_acc,
-      d_grp, d_status, d_results, d_step, d_flags, d_tz, d_warm;
+      d_grp, d_status, d_results, d_step, d_flags, d_tz, d_warm, d_pinit;
   std::vector<DevBuf*> all_bufs() {
     return {&d_el, &d_aoff, &d_coff, &d_state, &d_ints, &d_cells, &d_pos, &d_pbuild, &d_force, &d_list,
-            &d_out, &d_acc, &d_grp, &d_status, &d_results, &d_step, &d_flags, &d_tz, &d_warm};
+            &d_out, &d_acc, &d_grp, &d_status, &d_results, &d_step, &d_flags, &d_tz, &d_warm, &d_pinit};
   }
   void release_extra() {}
 };

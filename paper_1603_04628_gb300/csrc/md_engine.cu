@@ -48,12 +48,22 @@ int ensure(mdgp_ctx* ctx, DevBuf& b, size_t bytes) {
 // least the list radius r_c + skin.
 int describe(const mdgp_md_params& p, const mdgp_element& el, ElemDev& E, std::string* why) {
   if (!(el.h > 2.0 * p.fluid_margin)) { *why = "h must exceed twice the fluid margin"; return MDGP_E_ARG; }
+  if (!(el.wall_amp >= 0.0 && el.wall_amp < 1.0)) { *why = "wall_amp must lie in [0, 1)"; return MDGP_E_ARG; }
+  if (el.wall_amp > 0.0 && !(el.h * (1.0 - el.wall_amp) > 2.0 * p.fluid_margin)) {
+    *why = "the narrowest gap h (1 - wall_amp) must exceed twice the fluid margin";
+    return MDGP_E_ARG;
+  }
+  // the box and the fluid lattice are built for the widest gap H; N_fluid
+  // and the pressure's volume take the mean gap h
+  const double H = el.h * (1.0 + el.wall_amp);
   if (!(el.density >= 0.0) || !(el.T > 0.0) || el.steps_eq < 0 || el.steps_sample < 0) {
     *why = "density >= 0, T > 0 and non-negative step counts required";
     return MDGP_E_ARG;
   }
   std::memset(&E, 0, sizeof(E));
-  E.Lx = el.Lx; E.Lz = el.Lz; E.h = el.h;
+  E.Lx = el.Lx; E.Lz = el.Lz; E.h = H;
+  E.hvol = el.h;
+  E.amp = el.wall_amp;
   E.T = el.T;
   // Eq. momentumEq: F = F_ext - (m / rho) dp/dx with rho = m n
   E.g = el.density > 0.0 ? el.g_ext - el.dpdx / el.density : el.g_ext;
@@ -70,7 +80,7 @@ int describe(const mdgp_md_params& p, const mdgp_element& el, ElemDev& E, std::s
   const long nf = lround_half_up(el.density * el.Lx * el.h * el.Lz);
   E.nf = (int)nf;
   const double af = std::cbrt(4.0 / el.density);
-  const double ly = el.h - 2.0 * p.fluid_margin;
+  const double ly = H - 2.0 * p.fluid_margin;
   long cx = (long)std::ceil(el.Lx / af - 1e-9), cy = (long)std::ceil(ly / af - 1e-9),
        cz = (long)std::ceil(el.Lz / af - 1e-9);
   if (cx < 1) cx = 1;
@@ -90,7 +100,7 @@ int describe(const mdgp_md_params& p, const mdgp_element& el, ElemDev& E, std::s
   E.wax = el.Lx / wnx; E.waz = el.Lz / wnz; E.wdy = 0.5 * a0;
   E.nw = 2 * p.wall_planes * 2 * (int)wnx * (int)wnz;
   const double th = 0.5 * a0 * (p.wall_planes - 1);
-  const double ylo = -th - 1.0, yhi = el.h + th + 1.0;
+  const double ylo = -th - 1.0, yhi = H + th + 1.0;
   E.ylo = ylo;
   const double rl = p.rc + p.skin;
   E.nc[0] = (int)std::floor(el.Lx / rl);
@@ -109,6 +119,75 @@ int describe(const mdgp_md_params& p, const mdgp_element& el, ElemDev& E, std::s
   E.Tf = (float)E.T;
   E.beta_sdf = (float)E.beta_sd;
   return MDGP_OK;
+}
+
+// Initial positions of an element whose walls follow the channel profile
+// (E.amp > 0), in k_init_atoms's atom order, 3 doubles per atom:
+//  - the local gap h(x) = hvol (1 - amp cos(2 pi x / Lx)) and the lower
+//    wall's inner plane yb(x) = (H - h(x)) / 2, H the widest gap;
+//  - fluid: the FCC lattice of the widest gap, its sites in lattice order
+//    kept where they lie at least the fluid margin inside the local walls,
+//    the lattice grown (y, x, z in turn) until enough are kept, the
+//    vacancies spread evenly over the kept sites;
+//  - walls: the planar element's (100) planes with each site moved to
+//    yb(x) - k dy (lower wall) or yb(x) + h(x) + k dy (upper wall).
+void profiled_positions(const mdgp_md_params& p, const ElemDev& E, double* out) {
+  const double m = p.fluid_margin, H = E.h;
+  auto profile = [&](double x, double& hx, double& yb) {
+    hx = E.hvol * (1.0 - E.amp * std::cos(2.0 * M_PI * x / E.Lx));
+    yb = 0.5 * (H - hx);
+  };
+  long cx = E.fc[0], cy = E.fc[1], cz = E.fc[2];
+  const double ly = H - 2.0 * m;
+  const long long nf = E.nf;
+  std::vector<double> pos;
+  for (int turn = 0;; ++turn) {
+    const double bx = E.Lx / cx, by = ly / cy, bz = E.Lz / cz;
+    const long long sites = 4LL * cx * cy * cz;
+    pos.clear();
+    for (long long s = 0; s < sites; ++s) {
+      const int b = (int)(s & 3);
+      const long long c = s >> 2;
+      const long long iz = c % cz, iy = (c / cz) % cy, ix = c / (cz * cy);
+      const double ox = (b == 1 || b == 2) ? 0.5 : 0.0;
+      const double oy = (b == 1 || b == 3) ? 0.5 : 0.0;
+      const double oz = (b == 2 || b == 3) ? 0.5 : 0.0;
+      const double px = ((double)ix + ox + 0.25) * bx;
+      const double py = m + ((double)iy + oy + 0.25) * by;
+      const double pz = ((double)iz + oz + 0.25) * bz;
+      double hx, yb;
+      profile(px, hx, yb);
+      if (py >= yb + m && py <= yb + hx - m) {
+        pos.push_back(px); pos.push_back(py); pos.push_back(pz);
+      }
+    }
+    if ((long long)pos.size() / 3 >= nf) break;
+    if (turn % 3 == 0) ++cy; else if (turn % 3 == 1) ++cx; else ++cz;
+  }
+  const long long kept = (long long)pos.size() / 3;
+  for (long long l = 0; l < nf; ++l) {
+    const long long k = (long long)(((__int128)l * kept) / nf);
+    for (int d = 0; d < 3; ++d) out[3 * l + d] = pos[(size_t)(3 * k + d)];
+  }
+  const long long per_plane = 2LL * E.wnx * E.wnz, per_wall = per_plane * p.wall_planes;
+  for (long long w = 0; w < E.nw; ++w) {
+    const int wall = (int)(w / per_wall);
+    const long long r = w % per_wall;
+    const int k = (int)(r / per_plane);
+    const long long r2 = r % per_plane;
+    const long long i = r2 / (2LL * E.wnz), j = (r2 >> 1) % E.wnz;
+    const int tt = (int)(r2 & 1);
+    double ox, oz;
+    if ((k & 1) == 0) { ox = tt ? 0.5 : 0.0; oz = tt ? 0.5 : 0.0; }
+    else { ox = tt ? 0.0 : 0.5; oz = tt ? 0.5 : 0.0; }
+    const double px = ((double)i + ox) * E.wax, pz = ((double)j + oz) * E.waz;
+    double hx, yb;
+    profile(px, hx, yb);
+    double* o = out + 3 * (nf + w);
+    o[0] = px;
+    o[1] = wall == 0 ? yb - (double)k * E.wdy : yb + hx + (double)k * E.wdy;
+    o[2] = pz;
+  }
 }
 
 PhysDev make_phys(const mdgp_md_params& p, int list_cap) {
@@ -300,7 +379,7 @@ struct SiteGrid {
 int adapt_snapshot(const mdgp_md_params& p, const mdgp_element& el, const ElemDev& E, const mdgp_start& S,
                    std::vector<double>& xv) {
   if (!S.xv || S.n_fluid < 0 || S.n_wall != E.nw || std::fabs(S.h - E.h) > 1e-9 || std::fabs(S.Lx - E.Lx) > 1e-9 ||
-      std::fabs(S.Lz - E.Lz) > 1e-9)
+      std::fabs(S.Lz - E.Lz) > 1e-9 || E.amp != 0.0)
     return 0;
   const long long nf = E.nf, nw = E.nw, n_old = S.n_fluid;
   xv.assign((size_t)6 * (nf + nw), 0.0);
@@ -618,7 +697,7 @@ __global__ void k_finalize(BatchDev B, mdgp_result* out) {
   mdgp_result r;
   const int nb = E.nb;
   const long long S = E.steps_sample;
-  const double vol = E.Lx * E.h * E.Lz;
+  const double vol = E.Lx * E.hvol * E.Lz;
   double qs = 0.0, ps = 0.0, qm[kMaxBlocks], pm[kMaxBlocks];
   for (int b = 0; b < nb; ++b) {
     const long long lo = (b * S + nb - 1) / nb, hi = ((b + 1) * S + nb - 1) / nb;
@@ -868,6 +947,13 @@ static int plan_impl(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int list_
     std::snprintf(ctx->err, sizeof(ctx->err), "batch too large (2^31 atoms max)");
     return MDGP_E_ARG;
   }
+  // initial positions of elements with profiled walls, built on the host
+  std::vector<double> pinit;
+  for (int64_t i = 0; i < n; ++i) {
+    if (Es[i].amp == 0.0) continue;
+    if (pinit.empty()) pinit.assign((size_t)3 * atoms, 0.0);
+    profiled_positions(ctx->params, Es[i], pinit.data() + 3 * Es[i].atom0);
+  }
   int list_cap = ctx->params.list_capacity > 0 ? ctx->params.list_capacity : 128;
   if (list_cap_override > list_cap) list_cap = list_cap_override;
   list_cap = (list_cap + 3) / 4 * 4;  // whole groups of four
@@ -895,7 +981,13 @@ static int plan_impl(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int list_
   if ((st = ensure(ctx, ctx->d_flags, sizeof(int) * kFlags))) return st;
   if ((st = ensure(ctx, ctx->d_tz, sizeof(double) * 2 * n))) return st;
   if (any_warm && (st = ensure(ctx, ctx->d_warm, sizeof(double) * 6 * N))) return st;
+  if (!pinit.empty() && (st = ensure(ctx, ctx->d_pinit, sizeof(double) * 3 * N))) return st;
+  if (!pinit.empty())
+    CK(cudaMemcpyAsync(ctx->d_pinit.ptr, pinit.data(), sizeof(double) * 3 * N, cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(ctx->d_el.ptr, Es.data(), sizeof(ElemDev) * n, cudaMemcpyHostToDevice, ctx->stream));
+  ctx->el_host = Es;
+  ctx->el_desc.assign(el, el + n);
+  ctx->ran = false;
   CK(cudaMemcpyAsync(ctx->d_aoff.ptr, aoff.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(ctx->d_coff.ptr, coff.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, ctx->stream));
   if (any_warm)
@@ -933,6 +1025,7 @@ static int plan_impl(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int list_
   B.flags = (int*)ctx->d_flags.ptr;
   B.tz = (double*)ctx->d_tz.ptr;
   B.warm = any_warm ? (const double*)ctx->d_warm.ptr : nullptr;
+  B.pinit = pinit.empty() ? nullptr : (const double*)ctx->d_pinit.ptr;
   ctx->P = make_phys(ctx->params, list_cap);
   ctx->n_el = n;
   ctx->steps = S;
@@ -1120,11 +1213,24 @@ static int run_direct(mdgp_ctx* ctx) {
   return MDGP_OK;
 }
 
-static int launch_impl(mdgp_ctx* ctx) {
+// A continued run (resume) keeps the atom state of the last launch and
+// clears only the measurements, the counters and the step.
+static int resume_batch(mdgp_ctx* ctx) {
+  const int n = (int)ctx->n_el;
+  CK(cudaMemsetAsync(ctx->d_acc.ptr, 0, sizeof(double) * kAccStride * n, ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_status.ptr, 0, sizeof(int) * n, ctx->stream));
+  CK(cudaMemsetAsync(ctx->B.ccount, 0, sizeof(int) * ctx->B.n_cells, ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_step.ptr, 0, sizeof(long long), ctx->stream));
+  CK(cudaMemsetAsync(ctx->B.flags, 0, sizeof(int) * kFlags, ctx->stream));
+  CK(cudaMemsetAsync(ctx->B.tz, 0, sizeof(double) * 2 * n, ctx->stream));
+  return MDGP_OK;
+}
+
+static int launch_impl(mdgp_ctx* ctx, bool resume = false) {
   if (!ctx->planned) return MDGP_E_STATE;
   ctx->launches = 0;
   int st;
-  if ((st = start_batch(ctx))) return st;
+  if ((st = resume ? resume_batch(ctx) : start_batch(ctx))) return st;
   enqueue_rebuild(ctx);
   enqueue_force(ctx, true, 0);
   enqueue_energy(ctx, kAccE0);
@@ -1155,6 +1261,7 @@ static int launch_impl(mdgp_ctx* ctx) {
   k_finalize<<<grid_for(ctx->n_el, 128), 128, 0, ctx->stream>>>(ctx->B, (mdgp_result*)ctx->d_results.ptr);
   ctx->launches++;
   CK(cudaGetLastError());
+  ctx->ran = true;
   return MDGP_OK;
 }
 
@@ -1334,6 +1441,26 @@ int mdgp_micro_path(const mdgp_ctx* ctx) {
   if (!ctx) return MDGP_E_ARG;
   if (!ctx->planned) return MDGP_E_STATE;
   return ctx->direct ? 2 : (ctx->graph_while ? 1 : 0);
+}
+
+int mdgp_micro_continue(mdgp_ctx* ctx, const double* g_ext, const double* dpdx) {
+  if (!ctx) return MDGP_E_ARG;
+  if (!ctx->planned || !ctx->ran) return MDGP_E_STATE;
+  cudaSetDevice(ctx->device);
+  const unsigned S = (unsigned)ctx->steps;
+  for (size_t e = 0; e < ctx->el_host.size(); ++e) {
+    ElemDev& E = ctx->el_host[e];
+    mdgp_element& d = ctx->el_desc[e];
+    if (g_ext) d.g_ext = g_ext[e];
+    if (dpdx) d.dpdx = dpdx[e];
+    // Eq. momentumEq with the element's density as described
+    E.g = d.density > 0.0 ? d.g_ext - d.dpdx / d.density : d.g_ext;
+    E.g_kick = (float)(0.5 * ctx->params.dt / ctx->params.mass * E.g);
+    E.step0 += S;
+  }
+  CK(cudaMemcpyAsync(ctx->d_el.ptr, ctx->el_host.data(), sizeof(ElemDev) * ctx->el_host.size(),
+                     cudaMemcpyHostToDevice, ctx->stream));
+  return launch_impl(ctx, true);
 }
 
 int mdgp_micro_launch_shape(const mdgp_ctx* ctx, int32_t* out) {

@@ -81,6 +81,9 @@ struct ElemDev {
   float inv_csf[3];
   float g_kick;        // dt/(2m) g as float (double-float state)
   float Tf, beta_sdf;
+  double amp;          // profiled walls: h(x) = hvol (1 - amp cos(2 pi x / Lx)); 0 = planar
+  double hvol;         // mean gap: the fluid volume is Lx hvol Lz (h is the widest gap)
+  unsigned step0;      // steps run before this launch (continued runs): Philox step offset
 };
 
 struct PhysDev {
@@ -120,6 +123,7 @@ struct BatchDev {
                                // the forces of step s read posb[s & 1] (FP32: two
                                // buffers; FP64: both point to one)
   float4* pbuild;              // pos at the last rebuild
+  const double* pinit;         // [3 n_atoms] initial positions of profiled elements (else null)
   void *fx, *fy, *fz, *wxx, *epot;
   int *ccount, *cstart, *csize;   // [n_cells]
   int *newcell, *slot;            // [n_atoms]

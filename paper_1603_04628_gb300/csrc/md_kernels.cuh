@@ -292,7 +292,11 @@ __global__ void k_init_atoms(BatchDev B, PhysDev P) {
     const long long l = a - E.atom0;
     double px, py, pz;
     int group;
-    if (l < E.nf) {
+    if (E.amp != 0.0) {
+      // walls that follow the channel profile: positions built by the host
+      group = l < E.nf ? 0 : 1;
+      px = B.pinit[3 * a]; py = B.pinit[3 * a + 1]; pz = B.pinit[3 * a + 2];
+    } else if (l < E.nf) {
       group = 0;
       const long long sites = 4LL * E.fc[0] * E.fc[1] * E.fc[2];
       const long long s = (l * sites) / E.nf;
@@ -1254,7 +1258,7 @@ __global__ void __launch_bounds__(256) k_integrate(BatchDev B, PhysDev P, int k,
       if (st1) {
         double b0 = 0.0, b1 = 0.0, b2 = 0.0;
         if (E.beta_sd > 0.0) {
-          normals3<FT>((uint32_t)l, (uint32_t)s, (uint32_t)E.id, 1u, E.seed, b0, b1, b2);
+          normals3<FT>((uint32_t)l, (uint32_t)s + E.step0, (uint32_t)E.id, 1u, E.seed, b0, b1, b2);
           b0 *= E.beta_sd; b1 *= E.beta_sd; b2 *= E.beta_sd;
         }
         const double bdt = P.gjf_b * P.dt, h2m = P.dt / (2.0 * P.mass), i2m = 1.0 / (2.0 * P.mass);
@@ -1447,7 +1451,7 @@ __device__ __forceinline__ void integrate_df_atom(const BatchDev& B, const PhysD
     if (st1) {
       float b0 = 0.f, b1 = 0.f, b2 = 0.f;
       if (E.beta_sdf > 0.f) {
-        normals3f((uint32_t)l, (uint32_t)s, (uint32_t)E.id, 1u, E.seed, b0, b1, b2);
+        normals3f((uint32_t)l, (uint32_t)s + E.step0, (uint32_t)E.id, 1u, E.seed, b0, b1, b2);
         b0 *= E.beta_sdf; b1 *= E.beta_sdf; b2 *= E.beta_sdf;
       }
       // G-JF: x += b dt (v + dt/(2m) f + beta/(2m)); v = a v + a dt/(2m) f + (b/m) beta

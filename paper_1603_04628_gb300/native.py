@@ -21,7 +21,8 @@ class Element(ctypes.Structure):
     _fields_ = [("h", ctypes.c_double), ("dpdx", ctypes.c_double), ("density", ctypes.c_double),
                 ("T", ctypes.c_double), ("steps_eq", ctypes.c_int64), ("steps_sample", ctypes.c_int64),
                 ("Lx", ctypes.c_double), ("Lz", ctypes.c_double), ("g_ext", ctypes.c_double),
-                ("seed", ctypes.c_uint64), ("flags", ctypes.c_int32), ("id", ctypes.c_int32)]
+                ("seed", ctypes.c_uint64), ("flags", ctypes.c_int32), ("id", ctypes.c_int32),
+                ("wall_amp", ctypes.c_double)]
 
 
 class Result(ctypes.Structure):
@@ -128,6 +129,7 @@ def lib():
         "mdgp_micro_rebuild_count": ([vp], i64),
         "mdgp_micro_path": ([vp], ctypes.c_int),
         "mdgp_micro_launch_shape": ([vp, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+        "mdgp_micro_continue": ([vp, dp, dp], ctypes.c_int),
         "mdgp_micro_state": ([vp, dp, dp, i64], ctypes.c_int),
         "mdgp_md_forces": ([vp, ctypes.POINTER(Element), dp, i64, dp, dp, dp], ctypes.c_int),
         "mdgp_micro_profile": ([vp, i64, dp], ctypes.c_int),
@@ -191,6 +193,7 @@ def to_element(d):
     e.seed = int(d.get("seed", 0)) & 0xFFFFFFFFFFFFFFFF
     e.flags = int(d.get("flags", 0))
     e.id = int(d.get("id", 0))
+    e.wall_amp = float(d.get("wall_amp", 0.0))
     return e
 
 
@@ -337,6 +340,20 @@ class Context:
         if code < 0:
             raise MdgpError("mdgp_micro_path: %s" % STATUS.get(code, code))
         return {0: "per-step", 1: "persistent-graph", 2: "persistent-direct"}[code]
+
+    def micro_continue(self, g_ext=None, dpdx=None):
+        """Run the planned batch for another plan's worth of steps from the
+        state the last launch left (mdgp_micro_continue), optionally with new
+        per-element forcing."""
+        def arr(v):
+            if v is None:
+                return None
+            a = np.ascontiguousarray(np.broadcast_to(np.asarray(v, dtype=np.float64), (self._n_el,)))
+            self._keep = getattr(self, "_keep", []) + [a]
+            return _dp(a)
+        ga, da = arr(g_ext), arr(dpdx)
+        _check(self.h, lib().mdgp_micro_continue(self.h, ga, da), "mdgp_micro_continue")
+        self._keep = []
 
     def launch_shape(self):
         """The persistent step kernel's launch: blocks, threads per block,

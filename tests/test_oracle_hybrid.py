@@ -140,16 +140,18 @@ def test_continuity_update_by_hand():
 def test_pressure_gradient_and_forcing_by_hand():
     # p = K (n - n0) = 0, 1, 0, -1 for n = 0.8, 0.9, 0.8, 0.7; periodic central
     # differences (p_{j+1} - p_{j-1}) / (2 dx) = 0.02, 0, -0.02, 0.  A quarter
-    # period in, the inlet-outlet difference is +dP_amp = 400, a uniform
-    # gradient -400 / 200 = -2, so G = dp/dx - 2, and the element's body
-    # force F = -G / n (Eq. momentumEq) points downstream (+x).
+    # period in, the inlet-outlet difference is +dP_amp = 400, so the
+    # external force on every atom is F_ext = 400 / (L n0) = 400 / 160 = 2.5
+    # (Eq. momentumEq's F_ext, uniform over the channel); an element gets
+    # G = dp/dx - n F_ext, and its body force F = -G / n = F_ext - p' / n
+    # points downstream (+x).
     c = _four_sections(density0=[0.8, 0.9, 0.8, 0.7])
     np.testing.assert_allclose(c.pressure(), [0.0, 1.0, 0.0, -1.0], rtol=0, atol=1e-14)
     G = c.gradients(250.0)
-    np.testing.assert_allclose(G, [0.02 - 2.0, -2.0, -0.02 - 2.0, -2.0], rtol=1e-13)
-    el = c.element(1, G[1], 0)
+    np.testing.assert_allclose(G, [0.02 - 2.0, -2.25, -0.02 - 2.0, -1.75], rtol=1e-13)
     from oracle import md
-    assert md.make_params(el).g == pytest.approx(2.0 / 0.9, rel=1e-14)
+    for j, f in enumerate([2.5 - 0.02 / 0.8, 2.5, 2.5 + 0.02 / 0.8, 2.5]):
+        assert md.make_params(c.element(j, G[j], 0)).g == pytest.approx(f, rel=1e-13)
     # no forcing at t = 0 and half a period
     np.testing.assert_allclose(c.gradients(0.0), [0.02, 0.0, -0.02, 0.0], rtol=1e-13, atol=1e-15)
 

@@ -87,6 +87,77 @@ def test_element_counts_and_lattice():
     assert np.array_equal(a, x)
 
 
+# A whole converging-diverging channel as one element: walls that follow
+# h(x) = h (1 - a cos(2 pi x / Lx)) (the full MD of Sec. 3).
+CHANNEL = dict(h=8.0, Lx=120.0, Lz=8.0, density=0.8, T=1.1, g=0.0, wall_amp=0.5, seed=3, id=2)
+
+
+def test_profiled_walls_reduce_to_planar_ones():
+    el = dict(h=8.0, Lx=10.0, Lz=10.0, density=0.8, T=1.1, g=0.0, seed=9, id=4)
+    planar = md.init(md.make_params(el))
+    flat = md.init(md.make_params(dict(el, wall_amp=0.0)))
+    for u, w in zip(planar, flat):
+        assert np.array_equal(u, w)
+
+
+def test_profiled_channel_geometry():
+    p = md.make_params(CHANNEL)
+    nf, nw = md.counts(p)
+    h0, a, Lx, Lz = 8.0, 0.5, 120.0, 8.0
+    # N_fluid is the mean gap's: round(n Lx h Lz); the walls keep their lattice counts
+    assert nf == round(0.8 * Lx * h0 * Lz)
+    assert nw == md.counts(md.make_params(dict(CHANNEL, wall_amp=0.0)))[1]
+    x, v, anc, sp = md.init(p)
+    fl, wl = x[:nf], x[nf:]
+    # the two walls mirror each other about the mid-plane of the widest gap
+    H = h0 * (1 + a)
+    half = nw // 2
+    assert np.allclose(wl[:half, 1] + wl[half:, 1], H, atol=1e-12)
+    assert np.array_equal(wl[:half, [0, 2]], wl[half:, [0, 2]])
+    # the innermost planes are the local gap apart: h(x) at every wall site
+    planes = 3
+    per_plane = half // planes
+    inner_lo, inner_hi = wl[:per_plane], wl[half:half + per_plane]
+    gap = inner_hi[:, 1] - inner_lo[:, 1]
+    assert np.allclose(gap, h0 * (1 - a * np.cos(2 * math.pi * inner_lo[:, 0] / Lx)), atol=1e-12)
+    # the narrowest and widest gaps sit at x = 0 and x = Lx / 2
+    assert gap.min() == pytest.approx(h0 * (1 - a), abs=0.02)
+    assert gap.max() == pytest.approx(h0 * (1 + a), abs=0.02)
+    # every fluid atom is at least the margin inside the local walls
+    hx = h0 * (1 - a * np.cos(2 * math.pi * fl[:, 0] / Lx))
+    yb = 0.5 * (H - hx)
+    assert (fl[:, 1] >= yb + 0.7 - 1e-12).all() and (fl[:, 1] <= yb + hx - 0.7 + 1e-12).all()
+    # uniform density: the fluid in each eighth of the channel is n Lz times
+    # the area between the margins there (closed-form integral of h), to
+    # within the lattice's granularity
+    edges = np.linspace(0.0, Lx, 9)
+    counts = np.histogram(fl[:, 0], bins=edges)[0]
+    area = [(e1 - e0) * (h0 - 1.4) - a * h0 * Lx / (2 * math.pi) *
+            (math.sin(2 * math.pi * e1 / Lx) - math.sin(2 * math.pi * e0 / Lx)) for e0, e1 in zip(edges, edges[1:])]
+    expect = np.array(area) * Lz * nf / sum(area) / Lz
+    assert np.abs(counts / expect - 1.0).max() < 0.06
+    assert counts.sum() == nf
+    # nobody overlapping; anchors are the sites; Maxwell-Boltzmann start
+    from scipy.spatial import cKDTree
+    box = np.array([Lx, 1000.0, Lz])
+    r, _ = cKDTree(np.mod(x + [0.0, 100.0, 0.0], box), boxsize=box).query(np.mod(x + [0.0, 100.0, 0.0], box), k=2)
+    assert r[:, 1].min() > 0.85
+    assert np.array_equal(anc, x)
+    assert (v[:nf] ** 2).sum() / (3 * (nf - 1)) == pytest.approx(1.1, rel=1e-12)
+
+
+def test_profiled_channel_cell_list_equals_all_pairs():
+    rng = np.random.default_rng(8)
+    el = dict(CHANNEL, Lx=30.0, wall_amp=0.2)
+    p = md.make_params(el)
+    x, v, a, sp = md.init(p)
+    x = x + rng.uniform(-0.1, 0.1, x.shape)
+    fb, wb, eb = md.lj_forces(p, x, sp, "brute")
+    fc, wc, ec = md.lj_forces(p, x, sp, "cells")
+    assert np.abs(fb - fc).max() <= 1e-12 * np.abs(fb).max()
+    assert eb.sum() == pytest.approx(ec.sum(), rel=1e-12)
+
+
 # ---------------------------------------------------------------- forces
 def _jitter(x, rng, amp):
     return x + rng.uniform(-amp, amp, x.shape)
