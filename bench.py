@@ -183,6 +183,9 @@ def main():
                     help="oracle steps per sampled element in the reference arm")
     ap.add_argument("--no-gp-mlp", action="store_true", help="skip the GP and MLP timings")
     ap.add_argument("--no-hybrid", action="store_true", help="skip the hybrid-channel summary")
+    ap.add_argument("--h-amp", type=float, default=0.5,
+                    help="relative amplitude of the channel's height profile in the hybrid summary (0.5: the "
+                         "benchmark channel; 0.25: the paper's Eq. heightEq)")
     ap.add_argument("--persistent", type=int, default=None, choices=[0, 1, 2],
                     help="step loop: 0 one launch per step, 1 persistent kernel in a graph WHILE loop, 2 the "
                          "persistent kernel launched by the host (profilers capture it)")
@@ -336,7 +339,7 @@ def main():
         gp_mlp = gp_mlp_timings(native, local)
     hybrid = None
     if rank == 0 and world == 1 and args.workload == "uneven" and not args.no_hybrid:
-        hybrid = hybrid_summary(local)
+        hybrid = hybrid_summary(local, h_amp=args.h_amp)
 
     cpu = None
     if pool is not None:
@@ -404,7 +407,7 @@ def main():
     return 0
 
 
-def hybrid_summary(device, n_sections=100, n_steps=50, long_eq=8000, thresholds=(1.0, 4.0)):
+def hybrid_summary(device, n_sections=100, n_steps=50, long_eq=8000, thresholds=(1.0, 4.0), h_amp=0.5):
     """Algorithm 1 on the converging-diverging channel in the paper's form
     (p-GP over (h, n) from pre-simulations, q-GP on (h, n, F)), one forcing
     period (50 macro steps of 20), judged as the paper does (Sec. 3) against
@@ -423,13 +426,18 @@ def hybrid_summary(device, n_sections=100, n_steps=50, long_eq=8000, thresholds=
     t_all = time.perf_counter()
     ctx = native.Context(device, native.PREC_FP32)
     sn = 0.5
-    fit = cases.fit_pseudo_md(ctx)
-    params = dict(n_sections=n_sections, dx=10000.0 / n_sections, h0=12.0, Lx=10.0, Lz=10.0, eos_K=10.0,
+    # elements 6 x 6 wall-lattice cells across (9.52 sigma): the full MD's
+    # walls have the unstretched FCC lattice, and a 10 sigma element would
+    # stretch its walls by 5 % along x and z, which changes the wall friction
+    # and the flow rate by about 10 % (measured at h = 12 and 18)
+    box = 6.0 * 4.0 ** (1.0 / 3.0)
+    fit = cases.fit_pseudo_md(ctx, Lx=box, Lz=box)
+    params = dict(n_sections=n_sections, dx=10000.0 / n_sections, h0=12.0, Lx=box, Lz=box, eos_K=10.0,
                   eos_n0=0.8, dP_amp=400.0, period=1000.0, dt=20.0, T=1.1, md_steps_eq=long_eq,
                   md_steps_sample=3000, seed=synth.BASE_SEED, sf2=(20 * sn) ** 2, l2=1.0, sn2=sn ** 2,
-                  sn2_from_data=0, inputs=1)
-    X, p, p_se = cases.pressure_sweep(ctx, np.linspace(6.0, 18.0, 5), np.linspace(0.6, 1.0, 9), T=params["T"],
-                                      seed=synth.BASE_SEED + 7)
+                  sn2_from_data=0, inputs=1, h_amp=h_amp)
+    X, p, p_se = cases.pressure_sweep(ctx, np.linspace(12.0 * (1 - h_amp), 12.0 * (1 + h_amp), 5),
+                                      np.linspace(0.6, 1.0, 9), T=params["T"], seed=synth.BASE_SEED + 7, Lx=box, Lz=box)
     pdb = (X, p, float(np.var(p)), 1.0, float(np.mean(p_se)) ** 2)
     # the full MD of the channel and its App. B filtered history
     full = cases.full_channel_md(ctx, n_steps, **dict(params, seed=synth.BASE_SEED + 55))
@@ -472,10 +480,10 @@ def hybrid_summary(device, n_sections=100, n_steps=50, long_eq=8000, thresholds=
     ctx.close()
     return {"metric": "hybrid flow error against a full MD of the channel and speed-up over it (Eqs. error, "
                       "speedup)",
-            "config": {"workload": "%d-section converging-diverging channel (h0 = 12, L = 10^4), one forcing "
-                                   "period (%d macro steps of 20), plain 10 x h x 10 elements (FP32 forces), "
-                                   "paper form: p-GP on (h, n) from 45 pre-simulations, q-GP on (h, n, F)"
-                                   % (n_sections, n_steps),
+            "config": {"workload": "%d-section converging-diverging channel (h0 = 12, a = %g, L = 10^4), one forcing "
+                                   "period (%d macro steps of 20), %.3f x h x %.3f elements (6 x 6 wall cells, FP32 "
+                                   "forces), paper form: p-GP on (h, n) from 45 pre-simulations, q-GP on (h, n, F)"
+                                   % (n_sections, h_amp, n_steps, box, box),
                        "sigma_n": sn, "md_steps_sample": params["md_steps_sample"],
                        "md_everywhere_eq_steps": long_eq, "warm_eq_floor": 250},
             "full_md": {"atoms": full["n_atoms"], "md_steps": full["md_steps"], "wall_s": full["wall_s"],

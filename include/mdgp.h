@@ -421,7 +421,7 @@ typedef struct mdgp_hybrid mdgp_hybrid;
 
 /* Converging-diverging periodic channel and its coupling (Sec. 2.1):
  * n_sections sections at x_j = j dx (Eq. subsEq, L = n_sections dx) with
- * h_j = h0 (1 - 0.5 cos(2 pi x_j / L)); pressure p = eos_K (n - eos_n0);
+ * h_j = h0 (1 - h_amp cos(2 pi x_j / L)); pressure p = eos_K (n - eos_n0);
  * forcing dP(t) = dP_amp sin(2 pi t / period), an inlet-outlet pressure
  * difference turned into the external force F_ext = dP / (L eos_n0) that
  * every fluid atom of the channel feels (Eq. momentumEq's F_ext); section
@@ -461,6 +461,9 @@ typedef struct {
                                  the fluid's kinematic viscosity (LJ units).  0: off (default) */
   double pseudo_slip;         /* Navier slip length of the walls for pseudoMD */
   double pseudo_eps_q;        /* pseudoMD's flow-rate tolerance (0 = sqrt(sn2) / 4) */
+  double h_amp;               /* relative amplitude a of the height profile
+                                 h_j = h0 (1 - a cos(2 pi x_j / L)), in [0, 1) (default 0.5; the
+                                 paper's channel, Eq. heightEq, has a / mean height = 0.25) */
 } mdgp_macro_params;
 
 /* Time step statistics returned by mdgp_hybrid_step. */

@@ -6,7 +6,7 @@ leg may import this module; the product package never does.
 Macro model (paper Sec. 2.1, Eqs. subsEq, continuityEq, momentumEq; readings
 for the parts the paper leaves open are marked READING):
   - N periodic sections at x_j = j dx (Eq. subsEq with L = N dx); heights
-    h_j = h0 (1 - 0.5 cos(2 pi x_j / L)) (the converging-diverging channel in
+    h_j = h0 (1 - a cos(2 pi x_j / L)), a = 0.5 by default (the converging-diverging channel in
     the benchmark's form; the paper's Eq. heightEq has the same shape);
   - state: fluid number density n_j (mass density m n_j, m = 1);
   - pressure from a linear equation of state p = K (n - n0) (READING), or
@@ -41,7 +41,7 @@ from . import gp as ogp
 class Channel:
     def __init__(self, n_sections=8, dx=50.0, h0=12.0, Lx=10.0, Lz=10.0, K=10.0, n0=0.8, dP_amp=0.0,
                  period=1000.0, dt=20.0, T=1.1, steps_eq=100, steps_sample=100, seed=7, sf2=1.0, l2=1.0,
-                 sn2_default=0.0025, sn2_from_data=False, density0=None, inputs=0, pressure_db=None):
+                 sn2_default=0.0025, sn2_from_data=False, density0=None, inputs=0, pressure_db=None, h_amp=0.5):
         self.N = int(n_sections)
         self.dx, self.h0, self.Lx, self.Lz = float(dx), float(h0), float(Lx), float(Lz)
         self.K, self.n0, self.dP_amp, self.period, self.dt = float(K), float(n0), float(dP_amp), float(period), float(dt)
@@ -49,7 +49,7 @@ class Channel:
         self.sf2, self.l2, self.sn2_default, self.sn2_from_data = float(sf2), float(l2), float(sn2_default), bool(sn2_from_data)
         L = self.N * self.dx
         x = np.arange(self.N) * self.dx
-        self.h = self.h0 * (1.0 - 0.5 * np.cos(2.0 * math.pi * x / L))
+        self.h = self.h0 * (1.0 - h_amp * np.cos(2.0 * math.pi * x / L))
         # Eq. d2Eq's mean separation is undefined for an input without spread
         # (all h equal; the uniform gradient of the first steps; a uniform
         # density): h then takes h0 / 2, G the forcing gradient amplitude

@@ -27,7 +27,7 @@ def channel_atoms(params):
     over every section's cross-section plus the two tethered walls."""
     N, dx, h0, Lz, n0 = params["n_sections"], params["dx"], params["h0"], params["Lz"], params["eos_n0"]
     x = np.arange(N) * dx
-    h = h0 * (1.0 - 0.5 * np.cos(2.0 * math.pi * x / (N * dx)))
+    h = h0 * (1.0 - params.get("h_amp", 0.5) * np.cos(2.0 * math.pi * x / (N * dx)))
     fluid = float((n0 * h * Lz * dx).sum())
     a0 = 4.0 ** (1.0 / 3.0)
     walls = 2 * 3 * 2 * (N * dx / a0) * (Lz / a0)
@@ -210,11 +210,11 @@ def periodic_filter(ctx, t, q, period, sf2=1.0, l2=1.0, sn2=0.01, fit_until=None
 
 
 def full_channel_md(ctx, n_steps, n_sections=200, dx=50.0, h0=12.0, Lz=10.0, eos_n0=0.8, dP_amp=400.0,
-                    period=1000.0, dt=20.0, T=1.1, seed=1, wall_amp=0.5, md_dt=0.005, sub_steps=400,
+                    period=1000.0, dt=20.0, T=1.1, seed=1, h_amp=0.5, md_dt=0.005, sub_steps=400,
                     eq_steps=10000, log=None, **_):
     """The full MD of the channel (Sec. 3: the ground truth of Eqs. error and
     speedup): one element of length L = n_sections dx whose walls follow
-    h(x) = h0 (1 - wall_amp cos(2 pi x / L)), fluid at n0, every fluid atom
+    h(x) = h0 (1 - h_amp cos(2 pi x / L)), fluid at n0, every fluid atom
     driven by the external force F_ext(t) = dP_amp sin(2 pi t / period) /
     (L n0) of the hybrid's macro model (Eq. momentumEq).  The run starts from
     the lattice at rest, equilibrates eq_steps at F = 0 (t < 0), then runs
@@ -231,7 +231,7 @@ def full_channel_md(ctx, n_steps, n_sections=200, dx=50.0, h0=12.0, Lz=10.0, eos
         raise ValueError("a macro step must hold whole windows of sub_steps MD steps")
     f_amp = dP_amp / (L * eos_n0)
     el = dict(h=h0, Lx=L, Lz=Lz, density=eos_n0, T=T, steps_eq=0, steps_sample=sub_steps, g_ext=0.0,
-              seed=int(seed), id=0, wall_amp=wall_amp)
+              seed=int(seed), id=0, wall_amp=h_amp)
     t0 = time.perf_counter()
     n_atoms = ctx.micro_plan([el])
     n_eq = max(1, int(math.ceil(eq_steps / sub_steps)))

@@ -345,12 +345,14 @@ int mdgp_macro_params_default(mdgp_macro_params* p) {
   p->inputs = 0;
   p->warm_start = 0;
   p->md_steps_eq_warm = 0;
+  p->h_amp = 0.5;
   return MDGP_OK;
 }
 
 int mdgp_hybrid_create(mdgp_ctx* ctx, const mdgp_macro_params* p, const double* density0, mdgp_hybrid** out) {
   if (!ctx || !p || !out || p->n_sections < 3 || !(p->dx > 0) || !(p->h0 > 0) || !(p->dt > 0) ||
-      !(p->period > 0) || !(p->sf2 > 0) || !(p->l2 > 0) || !(p->sn2 >= 0) || p->inputs < 0 || p->inputs > 1)
+      !(p->period > 0) || !(p->sf2 > 0) || !(p->l2 > 0) || !(p->sn2 >= 0) || p->inputs < 0 || p->inputs > 1 ||
+      !(p->h_amp >= 0.0 && p->h_amp < 1.0))
     return MDGP_E_ARG;
   *out = nullptr;
   mdgp_hybrid* H = new (std::nothrow) mdgp_hybrid();
@@ -363,7 +365,7 @@ int mdgp_hybrid_create(mdgp_ctx* ctx, const mdgp_macro_params* p, const double* 
   H->h.resize(H->N);
   H->n.resize(H->N);
   for (int j = 0; j < H->N; ++j) {
-    H->h[j] = p->h0 * (1.0 - 0.5 * std::cos(2.0 * M_PI * (j * p->dx) / L));
+    H->h[j] = p->h0 * (1.0 - p->h_amp * std::cos(2.0 * M_PI * (j * p->dx) / L));
     H->n[j] = density0 ? density0[j] : p->eos_n0;
   }
   H->q.assign(H->N, 0.0);

@@ -65,7 +65,8 @@ class MacroParams(ctypes.Structure):
                 ("sf2", ctypes.c_double), ("l2", ctypes.c_double), ("sn2", ctypes.c_double),
                 ("inputs", ctypes.c_int32), ("factor_cache_mb", ctypes.c_int32),
                 ("warm_start", ctypes.c_int32), ("reserved2", ctypes.c_int32), ("md_steps_eq_warm", ctypes.c_int64),
-                ("pseudo_nu", ctypes.c_double), ("pseudo_slip", ctypes.c_double), ("pseudo_eps_q", ctypes.c_double)]
+                ("pseudo_nu", ctypes.c_double), ("pseudo_slip", ctypes.c_double), ("pseudo_eps_q", ctypes.c_double),
+                ("h_amp", ctypes.c_double)]
 
 
 class HybridStats(ctypes.Structure):
