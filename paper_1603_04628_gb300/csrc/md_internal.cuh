@@ -39,8 +39,7 @@ constexpr int kAccStride = 2 * kMaxBlocks + 4;
 constexpr int kGrpStride = 8;                 // init sums per group: sum v, sum v^2
 constexpr unsigned kJMask = 0x03FFFFFFu;      // neighbour index bits of a list entry
 constexpr int kFlagSkin = 4;                  // flag words (see BatchDev::flags)
-constexpr int kFlagBarGen = 8;
-constexpr int kFlagBarCount = 10;             // 64-bit, words 10-11
+constexpr int kFlagBarCount = 10;             // grid-barrier arrivals, 64-bit, words 10-11
 constexpr int kFlags = 16;
 
 // status codes written per element (match mdgp_status)
@@ -137,8 +136,8 @@ struct BatchDev {
   double* out;                    // export scratch [6 * n_atoms] (original order)
   int* flags;                     // [kFlags]: [0] rebuild needed, [1] blocks done, [2] rebuilds
                                   // run, [3] persistent step launches, [4..6] skin flags by
-                                  // step mod 3, [8] grid barrier generation, [10..11] its
-                                  // 64-bit arrival count
+                                  // step mod 3, [7] barrier wait given up, [10..11] the grid
+                                  // barrier's 64-bit arrival count
   double* tz;                     // [2 * n_el] per-element sum of m v_z^2 (two step-parity slots)
   const double* warm;             // [6 * n_atoms] start state (x y z vx vy vz, absolute, original
                                   // order) of the atoms of elements with warm != 0

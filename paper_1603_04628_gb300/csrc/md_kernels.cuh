@@ -1567,20 +1567,20 @@ __global__ void __launch_bounds__(128) k_step_df(BatchDev B, PhysDev P, int k, i
 }
 
 // Grid-wide barrier for a cooperative launch (every block resident).  The
-// arrival count never resets: before barrier g (the generation word's value)
-// it holds g x gridDim blocks, so the block whose arrival makes it
-// (g + 1) x gridDim publishes generation g + 1 with a release store, and the
-// other leaders wait for it with acquire loads.  One atomic and one store on
-// the release path.  The wait is bounded by wait_ns nanoseconds of the
+// arrival count never resets within a run: before barrier k of a launch it
+// holds (g0 + k) x gridDim, g0 the count's whole multiples of the grid when
+// the launch began (each block's leader reads it before its first arrival,
+// and no barrier completes before every block has arrived, so every leader
+// reads the same g0).  A leader makes its block's writes visible (fence),
+// adds its arrival without waiting for the result, and waits until the
+// count reaches its target: the last arrival is itself the release, with no
+// second round trip.  The wait is bounded by wait_ns nanoseconds of the
 // global timer: false if it gave up.  skip (test only) leaves this block's
 // arrival out, so no block is released and every wait runs out.
-__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ unsigned long long ld_acquire_gpu_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
-}
-__device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
 }
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
@@ -1588,24 +1588,25 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-__device__ __forceinline__ bool grid_barrier(int* flags, unsigned long long wait_ns, bool skip = false) {
+// The first target of a launch (leader thread only, before its first arrival).
+__device__ __forceinline__ unsigned long long grid_barrier_base(int* flags) {
+  const unsigned long long* cnt = reinterpret_cast<const unsigned long long*>(flags + kFlagBarCount);
+  return ld_acquire_gpu_u64(cnt) / gridDim.x * gridDim.x;
+}
+
+__device__ __forceinline__ bool grid_barrier(int* flags, unsigned long long& target, unsigned long long wait_ns,
+                                             bool skip = false) {
   __syncthreads();
   int ok = 1;
   if (threadIdx.x == 0) {
-    unsigned* gen = reinterpret_cast<unsigned*>(flags + kFlagBarGen);
     unsigned long long* cnt = reinterpret_cast<unsigned long long*>(flags + kFlagBarCount);
-    const unsigned g = ld_acquire_gpu(gen);
+    target += gridDim.x;
     __threadfence();
-    const unsigned long long target = (unsigned long long)(g + 1u) * gridDim.x;
-    if (!skip && atomicAdd(cnt, 1ull) == target - 1ull) {
-      __threadfence();   // the other blocks' arrivals (and their writes) before the release
-      st_release_gpu(gen, g + 1u);
-    } else {
-      const unsigned long long t0 = global_ns();
-      while (ld_acquire_gpu(gen) == g) {
-        if (global_ns() - t0 > wait_ns) { ok = 0; break; }
-        __nanosleep(64);
-      }
+    if (!skip) atomicAdd(cnt, 1ull);
+    const unsigned long long t0 = global_ns();
+    while (ld_acquire_gpu_u64(cnt) < target) {
+      if (global_ns() - t0 > wait_ns) { ok = 0; break; }
+      __nanosleep(32);
     }
   }
   return __syncthreads_and(ok) != 0;
@@ -1640,6 +1641,7 @@ __global__ void __maxnreg__(56) k_steps_persist(BatchDev B, PhysDev P, long long
   const bool lane_used = slot < A;
   long long s = *B.step_base;
   bool rebuild = false, failed = false, first_wait = true;
+  unsigned long long bar_target = threadIdx.x == 0 ? grid_barrier_base(B.flags) : 0ull;
   while (s < S && !failed) {
     if (blockIdx.x == 0 && threadIdx.x == 0) B.flags[kFlagSkin + (int)((s + 1) % 3)] = 0;
     int* skin = &B.flags[kFlagSkin + (int)(s % 3)];
@@ -1662,7 +1664,10 @@ __global__ void __maxnreg__(56) k_steps_persist(BatchDev B, PhysDev P, long long
       }
       integrate_df_epilogue<FROZEN>(B, s, m1, o, 0, 0);
     }
-    if (!grid_barrier(B.flags, P.wait_ns, P.inject_skip && first_wait && blockIdx.x == 0)) { failed = true; break; }
+    if (!grid_barrier(B.flags, bar_target, P.wait_ns, P.inject_skip && first_wait && blockIdx.x == 0)) {
+      failed = true;
+      break;
+    }
     first_wait = false;
     if (FROZEN) {
       const int m2 = kTzApply | kStage1;
@@ -1675,7 +1680,7 @@ __global__ void __maxnreg__(56) k_steps_persist(BatchDev B, PhysDev P, long long
                                     static_cast<const float*>(B.wxx)[i], o);
         integrate_df_epilogue<FROZEN>(B, s, m2, o, 0, 0);
       }
-      if (!grid_barrier(B.flags, P.wait_ns)) { failed = true; break; }
+      if (!grid_barrier(B.flags, bar_target, P.wait_ns)) { failed = true; break; }
     }
     rebuild = *(volatile int*)skin != 0;
     ++s;
