@@ -238,6 +238,16 @@ __device__ __forceinline__ void st_put(double* p, long long i, double v) {
   if constexpr (DF) df_st(p, i, df_from(v)); else p[i] = v;
 }
 
+// The standard-error block of sampling step ks (0 <= ks < steps_sample):
+// floor(ks nb / steps_sample), in 32-bit unsigned arithmetic whenever
+// steps_sample nb fits (the 64-bit division is a long software sequence and
+// this runs for every atom every step).
+__device__ __forceinline__ int sample_block(long long ks, const ElemDev& E) {
+  if (E.steps_sample * (long long)E.nb < (1LL << 32))
+    return (int)((unsigned)ks * (unsigned)E.nb / (unsigned)E.steps_sample);
+  return (int)((ks * E.nb) / E.steps_sample);
+}
+
 // Absolute position of atom i (x and z wrapped into the periodic box).
 template <bool DF>
 __device__ __forceinline__ void abs_position(const BatchDev& B, const ElemDev& E, long long i, double& x,
@@ -1276,7 +1286,7 @@ __global__ void __launch_bounds__(256) k_integrate(BatchDev B, PhysDev P, int k,
     }
     if (sample || (FROZEN && (mode & kTzSum) && stepped)) {
       // every atom of the element joins its element's reduction (walls add 0)
-      mkey = e * kMaxBlocks + (int)(sample ? (ks * E.nb) / E.steps_sample : 0);
+      mkey = e * kMaxBlocks + (sample ? sample_block(ks, E) : 0);
       tzkey = e;
     }
     if (moved) {
@@ -1469,7 +1479,7 @@ __device__ __forceinline__ void integrate_df_atom(const BatchDev& B, const PhysD
     vx = vy = vz = dfl{0.f, 0.f};
   }
   if (sample || (FROZEN && (mode & kTzSum) && stepped)) {
-    o.mkey = e * kMaxBlocks + (int)(sample ? (ks * E.nb) / E.steps_sample : 0);
+    o.mkey = e * kMaxBlocks + (sample ? sample_block(ks, E) : 0);
     o.tzkey = e;
   }
   if (moved) {
