@@ -169,11 +169,13 @@ def main():
                     help="steps of the FP64-forces pass reported beside the headline")
     ap.add_argument("--steps-per-element", type=int, default=STEPS_PER_ELEMENT,
                     help="MD steps per element (shorter runs for profiling only)")
-    ap.add_argument("--case", default="micro", choices=["micro", "channel", "gp", "learned-mean"],
-                    help="micro: the uneven micro-element batch (default); channel: the full hybrid "
-                         "(Algorithm 1) threshold sweep on the 200-section channel; gp: the GP and "
-                         "MLP timings alone; learned-mean: the MLP prior mean against the plain GP "
-                         "hybrid at matched thresholds, judged against the MD-everywhere run")
+    ap.add_argument("--case", default="micro", choices=["micro", "channel", "channel-evidence", "gp", "learned-mean"],
+                    help="micro: the uneven micro-element batch (default; its line also carries the channel "
+                         "case); channel: the full hybrid (Algorithm 1) threshold sweep on the 200-section channel "
+                         "judged against the full MD; channel-evidence: the same judged with evidence "
+                         "hyperparameters, warm starts and long equilibration; gp: the GP and MLP timings alone; "
+                         "learned-mean: the MLP prior mean against the plain GP hybrid at matched thresholds, "
+                         "judged against the MD-everywhere run")
     ap.add_argument("--channel-steps", type=int, default=100)
     ap.add_argument("--form", default="paper", choices=["paper", "linear"],
                     help="channel case: the paper's p-GP and (h, n, F) q-GP inputs (default), or a linear "
@@ -197,6 +199,8 @@ def main():
         return run_reference(args)
     if args.case == "channel":
         return run_channel_case(args)
+    if args.case == "channel-evidence":
+        return run_channel_evidence_case(args)
     if args.case == "learned-mean":
         return run_learned_mean_case(args)
     if args.case == "gp":
@@ -339,7 +343,7 @@ def main():
         gp_mlp = gp_mlp_timings(native, local)
     hybrid = None
     if rank == 0 and world == 1 and args.workload == "uneven" and not args.no_hybrid:
-        hybrid = hybrid_summary(local, h_amp=args.h_amp)
+        hybrid = channel_case(local, h_amp=args.h_amp, noise_run=False)
 
     cpu = None
     if pool is not None:
@@ -407,7 +411,7 @@ def main():
     return 0
 
 
-def hybrid_summary(device, n_sections=100, n_steps=50, long_eq=8000, thresholds=(1.0, 4.0), h_amp=0.5):
+def evidence_warm_summary(device, n_sections=100, n_steps=50, long_eq=8000, thresholds=(1.0, 4.0), h_amp=0.5):
     """Algorithm 1 on the converging-diverging channel in the paper's form
     (p-GP over (h, n) from pre-simulations, q-GP on (h, n, F)), one forcing
     period (50 macro steps of 20), judged as the paper does (Sec. 3) against
@@ -537,25 +541,28 @@ def gp_mlp_timings(native, device):
             "timing": "wall clock of the C-ABI calls (host in/out), mean of 5 for the GP"}
 
 
-def run_channel_case(args):
-    """Hybrid speed-up against the MD-everywhere reference at each threshold
-    of the sweep (paper Sec. 3.1, Eqs. error and speedup)."""
-    import torch
+def channel_case(device, n_steps=100, h_amp=0.5, paper_form=True, noise_run=True):
+    """Configured channel case (cfg 3): Algorithm 1 on the 200-section
+    converging-diverging channel, 100 macro steps, the cfg 1 elements
+    (2000 + 3000 steps) in 6 x 6 wall cells, sigma_f = 20 sigma_n and l^2 = 1
+    (the paper's ratios, Sec. 2.3), thresholds 0.5-8 sigma_n from an empty
+    database; judged against the full MD of the channel (App. B filtered,
+    Sec. 3) and against MD at every section.  Returns the result dict."""
     from paper_1603_04628_gb300 import cases, native
     import numpy as np
-    torch.cuda.set_device(0)
-    ctx = native.Context(0, native.PREC_FP32)
+    ctx = native.Context(device, native.PREC_FP32)
+    t_all = time.perf_counter()
     sn = 0.5
     box = 6.0 * 4.0 ** (1.0 / 3.0)   # 6 x 6 wall-lattice cells, like the full MD's walls
     params = dict(n_sections=200, dx=50.0, h0=12.0, Lx=box, Lz=box, eos_K=10.0, eos_n0=0.8, dP_amp=400.0,
                   period=1000.0, dt=20.0, T=1.1, md_steps_eq=2000, md_steps_sample=3000, seed=synth.BASE_SEED,
-                  sf2=(20 * sn) ** 2, l2=1.0, sn2=sn ** 2, sn2_from_data=0, h_amp=args.h_amp)
+                  sf2=(20 * sn) ** 2, l2=1.0, sn2=sn ** 2, sn2_from_data=0, h_amp=h_amp)
     thresholds = [f * sn for f in (0.5, 1.0, 2.0, 4.0, 8.0)]
     pressure_db, form = None, "q-GP on (h, G), linear equation of state"
-    if args.paper_form or args.form == "paper":
+    if paper_form:
         # the paper's form (Sec. 2.4): p-GP over (h, n) from pre-simulations,
         # q-GP on (h, n, F)
-        X, p, p_se = cases.pressure_sweep(ctx, np.linspace(12.0 * (1 - args.h_amp), 12.0 * (1 + args.h_amp), 5),
+        X, p, p_se = cases.pressure_sweep(ctx, np.linspace(12.0 * (1 - h_amp), 12.0 * (1 + h_amp), 5),
                                           np.linspace(0.6, 1.0, 9), T=params["T"], seed=synth.BASE_SEED + 7,
                                           Lx=box, Lz=box)
         psn = float(np.mean(p_se))
@@ -563,30 +570,61 @@ def run_channel_case(args):
         params["inputs"] = 1
         form = "q-GP on (h, n, F), p-GP on (h, n) from %d pre-simulations (mean p SE %.3f)" % (len(p), psn)
     # the full MD of the channel (Sec. 3's judge), its App. B filtered history
-    full = cases.full_channel_md(ctx, args.channel_steps, **dict(params, seed=synth.BASE_SEED + 55))
-    t = np.arange(1, args.channel_steps + 1) * params["dt"]
+    full = cases.full_channel_md(ctx, n_steps, **dict(params, seed=synth.BASE_SEED + 55))
+    t = np.arange(1, n_steps + 1) * params["dt"]
     full["Q_filtered"] = cases.periodic_filter(ctx, t, full["Q"], params["period"], sf2=float(np.var(full["Q"])),
                                                sn2=1e-4, fit_until=None)[0]
-    out = cases.channel_sweep(ctx, thresholds, n_steps=args.channel_steps, seed_noise=synth.BASE_SEED + 99,
+    out = cases.channel_sweep(ctx, thresholds, n_steps=n_steps,
+                              seed_noise=synth.BASE_SEED + 99 if noise_run else None,
                               pressure_db=pressure_db, full_md=full, **params)
-    ref = out["reference"]
-    keys = ("sigma_t", "md_runs", "error", "speedup_eq", "wall_s", "wall_vs_reference", "gp_s", "md_s",
-            "error_vs_full_md", "speedup_eq_full_md", "wall_vs_full_md")
-    rows = [{k: r[k] for k in keys if k in r} for r in out["rows"]]
-    line = {"metric": "hybrid speed-up vs MD-everywhere at set flow error", "case": "channel",
-            "unit": "x", "n_gpus": 1, "data": "synthetic",
-            "config": {"workload": "200-section converging-diverging channel, h0 = 12, a = %g, %d macro steps, "
-                                   "%.3f x h x %.3f elements (2000 + 3000 steps, FP32 forces), judged against "
-                                   "the full MD of the channel and MD at every section"
-                                   % (args.h_amp, args.channel_steps, box, box),
-                       "sigma_n": sn, "sigma_f": 20 * sn, "form": form},
-            "reference": {"md_runs": ref["md_runs"], "wall_s": ref["wall_s"],
-                          "error_vs_full_md": out["reference_error_vs_full_md"]},
-            "full_md": {"atoms": full["n_atoms"], "md_steps": full["md_steps"], "wall_s": full["wall_s"],
-                        "noise_error": out["full_md_noise"]},
-            "thermal_noise_error": out.get("noise_error"), "rows": rows}
-    print(json.dumps(line), flush=True)
     ctx.close()
+    ref = out["reference"]
+    keys = ("sigma_t", "md_runs", "error_vs_full_md", "speedup_eq_full_md", "wall_s", "wall_vs_full_md",
+            "error", "speedup_eq", "wall_vs_reference", "gp_s", "md_s")
+    rows = []
+    for r in out["rows"]:
+        row = {k: r[k] for k in keys if k in r}
+        row["error_vs_md_everywhere"] = row.pop("error")
+        row["speedup_eq_estimated_atoms"] = row.pop("speedup_eq")
+        row["wall_vs_md_everywhere"] = row.pop("wall_vs_reference")
+        rows.append(row)
+    return {"metric": "hybrid flow error against a full MD of the channel and speed-up over it (Eqs. error, "
+                      "speedup)",
+            "config": {"workload": "200-section converging-diverging channel, h0 = 12, a = %g, L = 10^4, %d macro "
+                                   "steps of 20 (two forcing periods), %.3f x h x %.3f elements (2000 + 3000 "
+                                   "steps, FP32 forces), thresholds 0.5-8 sigma_n from an empty database"
+                                   % (h_amp, n_steps, box, box),
+                       "sigma_n": sn, "sigma_f": 20 * sn, "l2": 1.0, "form": form},
+            "full_md": {"atoms": full["n_atoms"], "md_steps": full["md_steps"], "wall_s": full["wall_s"],
+                        "atom_steps_per_s": full["n_atoms"] * full["md_steps"] / full["wall_s"],
+                        "windows": len(full["q_windows"]), "f_ext_amplitude": full["f_amp"]},
+            "thermal_noise_error": out["full_md_noise"],
+            "md_everywhere": {"md_runs": ref["md_runs"], "wall_s": ref["wall_s"],
+                              "error_vs_full_md": out["reference_error_vs_full_md"],
+                              "noise_error_two_runs": out.get("noise_error")},
+            "rows": rows, "wall_s": time.perf_counter() - t_all}
+
+
+def run_channel_case(args):
+    """cfg 3's sweep as a JSON line (bench.py --case channel)."""
+    import torch
+    torch.cuda.set_device(0)
+    line = channel_case(0, n_steps=args.channel_steps, h_amp=args.h_amp,
+                        paper_form=args.paper_form or args.form == "paper", noise_run=True)
+    line.update({"case": "channel", "n_gpus": 1, "data": "synthetic"})
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_channel_evidence_case(args):
+    """The channel judged against the full MD with the q-GP's hyperparameters
+    by maximum evidence, warm starts and pseudoMD, elements equilibrated
+    8000 steps (bench.py --case channel-evidence)."""
+    import torch
+    torch.cuda.set_device(0)
+    line = evidence_warm_summary(0, h_amp=args.h_amp)
+    line.update({"case": "channel-evidence", "n_gpus": 1, "data": "synthetic"})
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -601,18 +639,25 @@ def run_learned_mean_case(args):
     ctx = native.Context(0, native.PREC_FP32)
     # 50 sections: the plain arm with evidence hyperparameters runs MD at
     # most sections, and every appended entry refits the GP (O(M^3))
-    params = dict(n_sections=50, dx=200.0, h0=12.0, Lx=10.0, Lz=10.0, eos_K=10.0, eos_n0=0.8, dP_amp=400.0,
+    import numpy as np
+    box = 6.0 * 4.0 ** (1.0 / 3.0)   # 6 x 6 wall-lattice cells, like the full MD's walls
+    params = dict(n_sections=50, dx=200.0, h0=12.0, Lx=box, Lz=box, eos_K=10.0, eos_n0=0.8, dP_amp=400.0,
                   period=1000.0, dt=20.0, T=1.1, md_steps_eq=2000, md_steps_sample=3000, seed=synth.BASE_SEED,
                   sn2_from_data=0, inputs=0)
     t0 = time.perf_counter()
+    full = cases.full_channel_md(ctx, args.channel_steps, **dict(params, seed=synth.BASE_SEED + 55))
+    t = np.arange(1, args.channel_steps + 1) * params["dt"]
+    full["Q_filtered"] = cases.periodic_filter(ctx, t, full["Q"], params["period"], sf2=float(np.var(full["Q"])),
+                                               sn2=1e-4, fit_until=None)[0]
     thresholds = [0.5, 1.0, 2.0, 4.0]
     rows, info, net = cases.learned_mean_comparison(
         ctx, thresholds, args.channel_steps, db_elements=256, db_seed=synth.BASE_SEED + 31,
-        log=lambda d: print(json.dumps(d), file=sys.stderr, flush=True), **params)
+        log=lambda d: print(json.dumps(d), file=sys.stderr, flush=True), full_md=full, **params)
     line = {"case": "learned-mean", "n_gpus": 1, "data": "synthetic",
             "config": {"workload": "50-section channel (L = 10^4), linear equation of state, q-GP on (h, G), %d "
-                                   "macro steps, 10 x h x 10 elements (2000 + 3000 steps, FP32 forces); MLP "
-                                   "trained on 256 MD runs over h 6-18, G -0.06..0.06" % args.channel_steps},
+                                   "macro steps, %.3f x h x %.3f elements (2000 + 3000 steps, FP32 forces); MLP "
+                                   "trained on 256 MD runs over h 6-18, G -0.06..0.06; judged against MD at every "
+                                   "section and against the full MD of the channel" % (args.channel_steps, box, box)},
             "info": info, "rows": rows, "wall_s": time.perf_counter() - t0}
     print(json.dumps(line), flush=True)
     net.close()

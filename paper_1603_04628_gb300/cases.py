@@ -310,7 +310,7 @@ def evidence_hyperparameters(ctx, X, y, sn2, max_evals=200):
 
 
 def learned_mean_comparison(ctx, thresholds, n_steps, db_elements=256, db_seed=11, epochs=2000, reference=None,
-                            log=None, **params):
+                            log=None, full_md=None, **params):
     """The learned prior mean against the plain GP at matched thresholds
     (benchmark addition to Algorithm 1).  One MD database over the channel's
     (h, G) range trains the MLP; each arm's (sf2, l2) come from the same
@@ -319,8 +319,10 @@ def learned_mean_comparison(ctx, thresholds, n_steps, db_elements=256, db_seed=1
     the learned mean -- so the two arms differ only by the prior mean.
     reference: (q history of the sigma_t = 0 run, q history of a second one
     with other MD seeds) to judge the flow error against and to set the
-    thermal-noise band; run here when not given.  log (if given) receives a
-    dict after each stage."""
+    thermal-noise band; run here when not given.  full_md (optional, the
+    dict of full_channel_md with its App. B filtered history in "Q_filtered")
+    adds each arm's Eq. error against the full MD of the channel.  log (if
+    given) receives a dict after each stage."""
     say = log or (lambda d: None)
     X, y, se = md_database(ctx, db_elements, db_seed, density=params.get("eos_n0", 0.8), T=params.get("T", 1.1),
                            Lx=params.get("Lx", 10.0), Lz=params.get("Lz", 10.0),
@@ -345,9 +347,15 @@ def learned_mean_comparison(ctx, thresholds, n_steps, db_elements=256, db_seed=1
         rows.append(dict(sigma_t=s, md_runs_plain=a["md_runs"], md_runs_mlp=b["md_runs"],
                          error_plain=error(a["qbar"], ref), error_mlp=error(b["qbar"], ref),
                          wall_plain=a["wall_s"], wall_mlp=b["wall_s"]))
+        if full_md is not None:
+            rows[-1].update(error_plain_vs_full_md=error(a["qbar"], full_md["Q_filtered"]),
+                            error_mlp_vs_full_md=error(b["qbar"], full_md["Q_filtered"]))
         say(dict(stage="threshold", **rows[-1]))
     info = dict(db_elements=db_elements, sn2=sn2, plain=dict(sf2=sf2_p, l2=l2_p), mlp=dict(sf2=sf2_m, l2=l2_m),
                 mlp_train_loss=train, mlp_holdout_loss=hold, noise_error=noise)
+    if full_md is not None:
+        info.update(md_everywhere_vs_full_md=error(ref, full_md["Q_filtered"]),
+                    full_md_noise=error(full_md["Q"], full_md["Q_filtered"]))
     return rows, info, net
 
 
