@@ -416,44 +416,76 @@ __global__ void k_apply_warm(BatchDev B) {
 }
 
 // ---------------------------------------------------------------------------
-// Neighbour-list rebuild, step 1: bin every atom into its cell (counting
-// sort histogram by atomics; x and z periodic, y clamped to the edge cells).
+// Neighbour-list rebuild, step 1: bin every atom into its cell, the counting
+// sort's histogram (x and z periodic, y clamped to the edge cells).  The atoms
+// of a block are in cell order from the last rebuild, so their new cells span
+// a short range: the block counts them in shared memory (slot = rank among
+// the block's atoms of that cell), then adds each cell's count to the global
+// histogram with one atomic, whose old value is the block's base in the cell.
+// A block whose cells span more than kBinCells (the first rebuild, from the
+// lattice order) counts in the global histogram directly.  Slots differ from
+// run to run either way; k_settle orders each cell's atoms afterwards.
 // ---------------------------------------------------------------------------
 // With the double-float state an atom already in a reference cell is binned
 // from its offset: the new cell is the reference cell plus
 // floor(offset / cs + 1/2) per axis (x, z wrapped, y clamped), in FP32.
+constexpr int kBinCells = 1024;
+
 template <bool DF>
 __global__ void __launch_bounds__(256) k_bin(BatchDev B) {
+  __shared__ int s_cnt[kBinCells];
+  __shared__ int s_lo, s_hi;
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i == 0) atomicAdd(&B.flags[2], 1);
-  if (i >= B.n_atoms) return;
-  const ElemDev& E = B.el[B.atom_el[i]];
-  int ix, iy, iz;
-  const int c0 = B.cell[i];
-  if (DF && c0 >= 0) {
-    int rx, ry, rz;
-    cell_coords(E, c0, rx, ry, rz);
-    const float ox = df_ld(B.st[0], i).hi, oy = df_ld(B.st[1], i).hi, oz = df_ld(B.st[2], i).hi;
-    ix = rx + (int)floorf(fmaf(ox, E.inv_csf[0], 0.5f));
-    iy = ry + (int)floorf(fmaf(oy, E.inv_csf[1], 0.5f));
-    iz = rz + (int)floorf(fmaf(oz, E.inv_csf[2], 0.5f));
-    ix = ix < 0 ? ix + E.nc[0] : (ix >= E.nc[0] ? ix - E.nc[0] : ix);
-    iz = iz < 0 ? iz + E.nc[2] : (iz >= E.nc[2] ? iz - E.nc[2] : iz);
-    ix = ix < 0 ? 0 : (ix >= E.nc[0] ? E.nc[0] - 1 : ix);
-    iz = iz < 0 ? 0 : (iz >= E.nc[2] ? E.nc[2] - 1 : iz);
-    iy = iy < 0 ? 0 : (iy >= E.nc[1] ? E.nc[1] - 1 : iy);
-  } else {
-    double x, y, z;
-    abs_position<DF>(B, E, i, x, y, z);
-    ix = (int)(x * E.inv_cs[0]); iz = (int)(z * E.inv_cs[2]);
-    const double yr = (y - E.ylo) * E.inv_cs[1];
-    iy = yr < 0.0 ? 0 : (yr >= (double)E.nc[1] ? E.nc[1] - 1 : (int)yr);
-    ix = ix < 0 ? 0 : (ix >= E.nc[0] ? E.nc[0] - 1 : ix);
-    iz = iz < 0 ? 0 : (iz >= E.nc[2] ? E.nc[2] - 1 : iz);
+  if (threadIdx.x == 0) { s_lo = 0x7fffffff; s_hi = -1; }
+  int c = -1;
+  if (i < B.n_atoms) {
+    const ElemDev& E = B.el[B.atom_el[i]];
+    int ix, iy, iz;
+    const int c0 = B.cell[i];
+    if (DF && c0 >= 0) {
+      int rx, ry, rz;
+      cell_coords(E, c0, rx, ry, rz);
+      const float ox = df_ld(B.st[0], i).hi, oy = df_ld(B.st[1], i).hi, oz = df_ld(B.st[2], i).hi;
+      ix = rx + (int)floorf(fmaf(ox, E.inv_csf[0], 0.5f));
+      iy = ry + (int)floorf(fmaf(oy, E.inv_csf[1], 0.5f));
+      iz = rz + (int)floorf(fmaf(oz, E.inv_csf[2], 0.5f));
+      ix = ix < 0 ? ix + E.nc[0] : (ix >= E.nc[0] ? ix - E.nc[0] : ix);
+      iz = iz < 0 ? iz + E.nc[2] : (iz >= E.nc[2] ? iz - E.nc[2] : iz);
+      ix = ix < 0 ? 0 : (ix >= E.nc[0] ? E.nc[0] - 1 : ix);
+      iz = iz < 0 ? 0 : (iz >= E.nc[2] ? E.nc[2] - 1 : iz);
+      iy = iy < 0 ? 0 : (iy >= E.nc[1] ? E.nc[1] - 1 : iy);
+    } else {
+      double x, y, z;
+      abs_position<DF>(B, E, i, x, y, z);
+      ix = (int)(x * E.inv_cs[0]); iz = (int)(z * E.inv_cs[2]);
+      const double yr = (y - E.ylo) * E.inv_cs[1];
+      iy = yr < 0.0 ? 0 : (yr >= (double)E.nc[1] ? E.nc[1] - 1 : (int)yr);
+      ix = ix < 0 ? 0 : (ix >= E.nc[0] ? E.nc[0] - 1 : ix);
+      iz = iz < 0 ? 0 : (iz >= E.nc[2] ? E.nc[2] - 1 : iz);
+    }
+    c = (int)(E.cell0 + ((long long)ix * E.nc[1] + iy) * E.nc[2] + iz);
+    B.newcell[i] = c;
   }
-  const long long c = E.cell0 + ((long long)ix * E.nc[1] + iy) * E.nc[2] + iz;
-  B.newcell[i] = (int)c;
-  B.slot[i] = atomicAdd(&B.ccount[c], 1);
+  __syncthreads();
+  if (c >= 0) { atomicMin(&s_lo, c); atomicMax(&s_hi, c); }
+  __syncthreads();
+  if (s_hi < 0) return;                // no atom in this block
+  const int lo = s_lo, range = s_hi - s_lo + 1;
+  if (range > kBinCells) {            // whole block: the same lo and hi
+    if (c >= 0) B.slot[i] = atomicAdd(&B.ccount[c], 1);
+    return;
+  }
+  for (int r = threadIdx.x; r < range; r += blockDim.x) s_cnt[r] = 0;
+  __syncthreads();
+  const int rank = c >= 0 ? atomicAdd(&s_cnt[c - lo], 1) : 0;
+  __syncthreads();
+  for (int r = threadIdx.x; r < range; r += blockDim.x) {
+    const int n = s_cnt[r];
+    s_cnt[r] = n > 0 ? atomicAdd(&B.ccount[lo + r], n) : 0;   // the block's base in cell lo + r
+  }
+  __syncthreads();
+  if (c >= 0) B.slot[i] = s_cnt[c - lo] + rank;
 }
 
 // Step 2: per element (one block), exclusive scan of the cell counts; cell c
