@@ -131,35 +131,49 @@ __global__ void k_gp_cov(const double* X, int M, int Mp, int D, const double* sc
   C[(size_t)i * Mp + j] = v;
 }
 
-// Cholesky of the diagonal tile kb in place (lower), one warp: lane i holds
-// row i in registers; at step k the pivot and the scaled column k come from
-// the owning lanes by shuffles (no block barriers on the serial path).  FP64
-// issues at 1/64 of the FP32 rate here, so the pivot comes from one rsqrt
-// (p = d rsqrt(d)) and the column is multiplied by it.  A non-positive pivot
+// Cholesky of the diagonal tile kb in place (lower), four warps: the tile
+// sits in shared memory, lane i of every warp works on row i, and warp w owns
+// the columns c = w (mod 4), so that the right-looking updates of each step
+// run on all four FP64 pipes of the SM (one warp would leave three idle, and
+// FP64 issues at 1/64 of the FP32 rate here).  Step k: the owner of column k
+// has scaled it (pivot p = d rsqrt(d), column times rsqrt(d)); after a block
+// barrier every warp applies T[i][c] -= T[i][k] T[c][k] to its columns c > k,
+// the owner of column k + 1 first, which then takes the next pivot and scales
+// its column while the others are still updating.  Each element receives its
+// updates in the order of k, as in the one-warp form.  A non-positive pivot
 // sets *status.
-__global__ void __launch_bounds__(32) k_potrf_diag(double* A, int Mp, int kb, int* status) {
-  const int i = threadIdx.x;
+__device__ __forceinline__ void potrf_pivot(double (*T)[TB + 1], int k, int i, int* status) {   // whole warp
+  const double d = T[k][k];
+  __syncwarp();   // every lane has read the pivot before lane k overwrites it
+  const bool ok = d > 0.0;
+  if (i == k && !ok) atomicMin(status, MDGP_E_NOTPD);
+  const double dd = ok ? d : 1e-300;
+  const double rp = rsqrt(dd);   // one FP64 routine instead of sqrt and a divide
+  if (i == k) T[k][k] = dd * rp;
+  if (i > k) T[i][k] *= rp;
+}
+
+__global__ void __launch_bounds__(4 * TB) k_potrf_diag(double* A, int Mp, int kb, int* status) {
+  __shared__ double T[TB][TB + 1];
+  const int i = threadIdx.x & (TB - 1), w = threadIdx.x >> 5;
   const size_t base = (size_t)kb * TB;
-  double row[TB];
-#pragma unroll
-  for (int c = 0; c < TB; ++c) row[c] = A[(base + i) * Mp + base + c];
-#pragma unroll
-  for (int k = 0; k < TB; ++k) {
-    const double d = __shfl_sync(kFullMask, row[k], k);
-    const bool ok = d > 0.0;
-    if (i == k && !ok) atomicMin(status, MDGP_E_NOTPD);
-    const double rp = rsqrt(ok ? d : 1e-300);   // one FP64 routine instead of sqrt and a divide
-    const double p = (ok ? d : 1e-300) * rp;
-    if (i == k) row[k] = p;
-    if (i > k) row[k] *= rp;
-#pragma unroll
-    for (int c = k + 1; c < TB; ++c) {
-      const double tck = __shfl_sync(kFullMask, row[k], c);   // T[c][k], scaled, from lane c
-      if (i >= c) row[c] -= row[k] * tck;
+  for (int c = w; c < TB; c += 4) T[i][c] = A[(base + i) * Mp + base + c];
+  __syncthreads();
+  if (w == 0) potrf_pivot(T, 0, i, status);
+  for (int k = 0; k < TB - 1; ++k) {
+    __syncthreads();   // column k scaled
+    const double tik = T[i][k];
+    // the owner of column k + 1 updates it first and takes the next pivot
+    if (w == ((k + 1) & 3)) {
+      if (i >= k + 1) T[i][k + 1] -= tik * T[k + 1][k];
+      __syncwarp();
+      potrf_pivot(T, k + 1, i, status);
     }
+    for (int c = (k + 2) + ((w - (k + 2)) & 3); c < TB; c += 4)
+      if (i >= c) T[i][c] -= tik * T[c][k];
   }
-#pragma unroll
-  for (int c = 0; c < TB; ++c) A[(base + i) * Mp + base + c] = c <= i ? row[c] : 0.0;
+  __syncthreads();
+  for (int c = w; c < TB; c += 4) A[(base + i) * Mp + base + c] = c <= i ? T[i][c] : 0.0;
 }
 
 // Panel: A_ik <- A_ik L_kk^-T for every tile row i > kb.  A block of
@@ -541,7 +555,7 @@ static int enqueue_cholesky_lookahead(mdgp_gp* g, int* dstatus) {
   GK(cudaStreamWaitEvent(sa, e_in, 0));
   GK(cudaStreamWaitEvent(sb, e_in, 0));
   for (int kb = 0; kb < nt; ++kb) {
-    k_potrf_diag<<<1, 32, 0, sa>>>(g->dL, Mp, kb, dstatus);
+    k_potrf_diag<<<1, 4 * TB, 0, sa>>>(g->dL, Mp, kb, dstatus);
     g->launches++;
     const int rest = nt - kb - 1;
     if (rest == 0) break;
@@ -655,7 +669,7 @@ static int gp_fit_impl(mdgp_gp* g, const double* X, const double* y, const doubl
     if (st) return st;
   } else {
     for (int kb = 0; kb < nt; ++kb) {
-      k_potrf_diag<<<1, 32, 0, s>>>(g->dL, Mp, kb, dstatus);
+      k_potrf_diag<<<1, 4 * TB, 0, s>>>(g->dL, Mp, kb, dstatus);
       g->launches++;
       const int rest = nt - kb - 1;
       if (rest > 0) {
@@ -929,7 +943,7 @@ extern "C" int mdgp_gp_posterior_noalloc(const double* X, const double* y, int64
                                                       L);
   const int nt = Mp / TB;
   for (int kb = 0; kb < nt; ++kb) {
-    k_potrf_diag<<<1, 32, 0, s>>>(L, Mp, kb, status);
+    k_potrf_diag<<<1, 4 * TB, 0, s>>>(L, Mp, kb, status);
     const int rest = nt - kb - 1;
     if (rest > 0) {
       k_trsm_panel<<<rest * (TB / kTrsmRows), dim3(TB, kTrsmRows), 0, s>>>(L, Mp, kb);
