@@ -346,15 +346,11 @@ class Context:
         """Run the planned batch for another plan's worth of steps from the
         state the last launch left (mdgp_micro_continue), optionally with new
         per-element forcing."""
-        def arr(v):
-            if v is None:
-                return None
-            a = np.ascontiguousarray(np.broadcast_to(np.asarray(v, dtype=np.float64), (self._n_el,)))
-            self._keep = getattr(self, "_keep", []) + [a]
-            return _dp(a)
-        ga, da = arr(g_ext), arr(dpdx)
+        arrays = [None if v is None else
+                  np.ascontiguousarray(np.broadcast_to(np.asarray(v, dtype=np.float64), (self._n_el,)))
+                  for v in (g_ext, dpdx)]   # alive until the call returns
+        ga, da = (None if a is None else _dp(a) for a in arrays)
         _check(self.h, lib().mdgp_micro_continue(self.h, ga, da), "mdgp_micro_continue")
-        self._keep = []
 
     def launch_shape(self):
         """The persistent step kernel's launch: blocks, threads per block,
