@@ -141,6 +141,13 @@ typedef struct {
                            loop, 1, 2, 4 or 8; 0 (default) = the largest that the batch fills
                            (several only for batches too small to occupy every SM with one
                            thread per atom).  Results differ only by the summation order. */
+  int32_t resident;     /* FP32 persistent step loop with several threads per atom and tethered
+                           walls: 1 (default) = keep each atom's state and element constants in
+                           registers and the block's lists in shared memory for a whole
+                           list-rebuild interval (a step then reads global memory only for the
+                           neighbour positions), when every block holds one chunk of atoms and
+                           the shared memory fits; 0 = always the general persistent kernel.
+                           The same trajectory bit for bit either way. */
 } mdgp_md_params;
 
 /* Fill *out with the defaults listed above.  Returns MDGP_E_ARG on null. */
@@ -254,9 +261,11 @@ int mdgp_micro_path(const mdgp_ctx* ctx);
 int mdgp_micro_continue(mdgp_ctx* ctx, const double* g_ext, const double* dpdx);
 
 /* Launch shape of the planned batch's persistent step kernel (FP32 pair
- * forces, persistent = 1 or 2): out[0] = blocks, out[1] = threads per block,
- * out[2] = atoms per block, out[3] = threads per atom in the pair loop.
- * MDGP_E_STATE without a plan or on the per-step path. */
+ * forces, persistent = 1 or 2) into out[0..4]: out[0] = blocks, out[1] =
+ * threads per block, out[2] = atoms per block, out[3] = threads per atom in
+ * the pair loop, out[4] = 1 when the kernel keeps the atoms resident (see
+ * mdgp_md_params.resident), else 0.  MDGP_E_STATE without a plan or on the
+ * per-step path. */
 int mdgp_micro_launch_shape(const mdgp_ctx* ctx, int32_t* out);
 
 /* With persistent = 2 (the host launches the persistent step kernel once

@@ -37,6 +37,8 @@ struct mdgp_ctx {
   int persist_threads = 128;              // its block size
   int persist_atoms = 128;                // atoms per block (persist_atoms x persist_tpa <= persist_threads)
   int persist_tpa = 1;                    // threads per atom in its pair loop
+  bool persist_resident = false;          // k_steps_resident (state in registers, lists in shared memory)
+  size_t persist_smem = 0;                // its dynamic shared memory per block
   bool direct = false;        // persistent = 2: the host launches the persistent kernel itself
   // persistent = 2: CUDA-event times of the last batch's persistent launches
   // and of the rebuilds between them, and the steps they covered

@@ -11,6 +11,7 @@
 
 #include "mdgp.h"
 #include "md_kernels.cuh"
+#include "md_resident.cuh"
 #include "md_ctx.h"
 
 using namespace mdgp;
@@ -806,6 +807,26 @@ static PersistFn persist_kernel(bool uni, bool frozen, int tpa) {
   return persist_kernel_tpa<false, true>(tpa);
 }
 
+// The resident-atom step kernel (tethered walls, 2, 4 or 8 threads per atom).
+template <bool U>
+static PersistFn resident_kernel_tpa(int tpa) {
+  switch (tpa) {
+    case 2: return k_steps_resident<U, 2>;
+    case 4: return k_steps_resident<U, 4>;
+    default: return k_steps_resident<U, 8>;
+  }
+}
+static PersistFn resident_kernel(bool uni, int tpa) {
+  return uni ? resident_kernel_tpa<true>(tpa) : resident_kernel_tpa<false>(tpa);
+}
+
+// The step-loop kernel the plan chose.
+static PersistFn step_loop_kernel(const mdgp_ctx* ctx) {
+  const bool uni = ctx->P.uniform != 0, frozen = ctx->params.mode == 1;
+  return ctx->persist_resident ? resident_kernel(uni, ctx->persist_tpa)
+                               : persist_kernel(uni, frozen, ctx->persist_tpa);
+}
+
 // Persistent step loop (FP32 pair forces): a graph with one WHILE node
 // whose body is [cooperative k_steps_persist launch] -> IF (rebuild) {the 5
 // rebuild kernels}.  The step kernel runs steps until the lists need a
@@ -832,17 +853,16 @@ static int capture_while(mdgp_ctx* ctx, cudaGraphExec_t* out) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(ctx->persist_grid);
   cfg.blockDim = dim3(ctx->persist_threads);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = ctx->persist_smem;
   cfg.stream = ctx->side_stream;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeCooperative;
   at[0].val.cooperative = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  const bool uni = ctx->P.uniform != 0, frozen = ctx->params.mode == 1;
   const long long S = ctx->steps;
   const int A = ctx->persist_atoms;
-  e = cudaLaunchKernelEx(&cfg, persist_kernel(uni, frozen, ctx->persist_tpa), ctx->B, ctx->P, S, A, hr, hw, 1);
+  e = cudaLaunchKernelEx(&cfg, step_loop_kernel(ctx), ctx->B, ctx->P, S, A, hr, hw, 1);
   cudaStreamCaptureStatus cs;
   cudaGraph_t cg;
   const cudaGraphNode_t* deps = nullptr;
@@ -1068,22 +1088,77 @@ static int plan_impl(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int list_
     }
     ctx->persist_tpa = tpa;
     ctx->persist_grid = 0;
-    long long best_warps = 1LL << 40;
-    for (int R = 1; R <= 32; ++R) {
-      const long long slots = (long long)sms * R;
-      const long long A = (atoms + slots - 1) / slots;
-      const int T = (int)((A * tpa + 31) / 32 * 32);
-      // at least 128 threads: smaller blocks put more separate atom ranges on
-      // an SM and lose L1 reuse of the neighbour positions (measured slower)
-      if (T > 256 || T < 128) continue;   // larger batches: 256-thread blocks striding over chunks
+    ctx->persist_resident = false;
+    ctx->persist_smem = 0;
+    // One block per chunk of A atoms, R blocks per SM; the resident-atom
+    // kernel (tethered walls, several threads per atom) is tried first, with
+    // its lists' shared memory in the occupancy, then the general one.
+    const int list_cap = ctx->B.list_cap;
+    size_t res_max_smem = 0;   // dynamic shared memory a block of the resident kernel may take
+    auto search = [&](bool resident) -> cudaError_t {
+      long long best_warps = 1LL << 40;
+      for (int R = 1; R <= 32; ++R) {
+        const long long slots = (long long)sms * R;
+        const long long A = (atoms + slots - 1) / slots;
+        const int T = (int)((A * tpa + 31) / 32 * 32);
+        // at least 128 threads: smaller blocks put more separate atom ranges on
+        // an SM and lose L1 reuse of the neighbour positions (measured slower)
+        if (T > 256 || T < 128) continue;   // larger batches: 256-thread blocks striding over chunks
+        int per_sm = 0;
+        const size_t smem = resident ? resident_smem_bytes((int)A, list_cap) : 0;
+        if (smem > res_max_smem && resident) continue;   // the lists do not fit
+        const cudaError_t oe =
+            resident ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, resident_kernel(uni, tpa), T, smem)
+                     : occupancy(tpa, T, &per_sm);
+        if (oe != cudaSuccess) return oe;
+        const long long warps = (long long)R * (T / 32);
+        if (per_sm >= R && warps < best_warps) {
+          best_warps = warps;
+          ctx->persist_atoms = (int)A;
+          ctx->persist_threads = T;
+          ctx->persist_grid = (unsigned)((atoms + A - 1) / A);
+          ctx->persist_resident = resident;
+          ctx->persist_smem = smem;
+        }
+      }
+      return cudaSuccess;
+    };
+    const bool try_resident = ctx->params.resident && !frozen && tpa > 1;
+    if (try_resident) {
+      // the lists may need more than the default 48 KB of dynamic shared memory
+      int optin = 0;
+      cudaFuncAttributes fa = {};
+      CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+      CK(cudaFuncGetAttributes(&fa, resident_kernel(uni, tpa)));
+      res_max_smem = (size_t)(optin - (int)fa.sharedSizeBytes);
+      CK(cudaFuncSetAttribute(resident_kernel(uni, tpa), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)res_max_smem));
+      const cudaError_t se = search(true);
+      if (se != cudaSuccess) return set_err(ctx, se);
+    }
+    if (ctx->persist_grid == 0) {
+      const cudaError_t se = search(false);
+      if (se != cudaSuccess) return set_err(ctx, se);
+    }
+    if (ctx->persist_grid == 0) {
+      // 256-thread blocks of 256 / TPA atoms: batches too small for 128-thread
+      // blocks on every SM (one chunk per block; the resident kernel when its
+      // blocks all fit at once) and batches large enough to stride
+      const int A = 256 / tpa;
+      const long long chunks = (atoms + A - 1) / A;
       int per_sm = 0;
-      if (occupancy(tpa, T, &per_sm) != cudaSuccess) return set_err(ctx, cudaGetLastError());
-      const long long warps = (long long)R * (T / 32);
-      if (per_sm >= R && warps < best_warps) {
-        best_warps = warps;
-        ctx->persist_atoms = (int)A;
-        ctx->persist_threads = T;
-        ctx->persist_grid = (unsigned)((atoms + A - 1) / A);
+      const size_t smem = try_resident ? resident_smem_bytes(A, list_cap) : 0;
+      if (try_resident && smem <= res_max_smem) {
+        const cudaError_t oe =
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, resident_kernel(uni, tpa), 256, smem);
+        if (oe != cudaSuccess) return set_err(ctx, oe);
+        if (chunks <= (long long)per_sm * sms) {
+          ctx->persist_atoms = A;
+          ctx->persist_threads = 256;
+          ctx->persist_grid = (unsigned)chunks;
+          ctx->persist_resident = true;
+          ctx->persist_smem = smem;
+        }
       }
     }
     if (ctx->persist_grid == 0) {
@@ -1165,12 +1240,11 @@ static int start_batch(mdgp_ctx* ctx) {
 // an ordinary kernel launch, which a profiler can capture.
 static int run_direct(mdgp_ctx* ctx) {
   const long long S = ctx->steps;
-  const bool uni = ctx->P.uniform != 0, frozen = ctx->params.mode == 1;
   const int A = ctx->persist_atoms;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(ctx->persist_grid);
   cfg.blockDim = dim3(ctx->persist_threads);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = ctx->persist_smem;
   cfg.stream = ctx->stream;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeCooperative;
@@ -1187,7 +1261,7 @@ static int run_direct(mdgp_ctx* ctx) {
   for (long long guard = 0; guard <= S; ++guard) {
     CK(cudaEventRecord(ctx->dir_ev[1], ctx->stream));
     cudaError_t e;
-    e = cudaLaunchKernelEx(&cfg, persist_kernel(uni, frozen, ctx->persist_tpa), ctx->B, ctx->P, S, A, h0, h0, 0);
+    e = cudaLaunchKernelEx(&cfg, step_loop_kernel(ctx), ctx->B, ctx->P, S, A, h0, h0, 0);
     if (e != cudaSuccess) return set_err(ctx, e);
     CK(cudaEventRecord(ctx->dir_ev[2], ctx->stream));
     ++ctx->launches;
@@ -1316,6 +1390,8 @@ int mdgp_md_params_default(mdgp_md_params* out) {
   out->persistent = 1;
   out->wait_timeout_ms = 2000;
   out->inject_barrier_skip = 0;
+  out->threads_per_atom = 0;
+  out->resident = 1;
   return MDGP_OK;
 }
 
@@ -1368,7 +1444,8 @@ static bool params_valid(const mdgp_md_params* p) {
          p->wall_density > 0 && p->gamma_wall >= 0 && p->list_capacity >= 0 && p->skin >= 0 &&
          p->rebuild_every >= 0 && (p->build_variant == 0 || p->build_variant == 3) && p->persistent >= 0 &&
          p->persistent <= 2 && (p->threads_per_atom == 0 || p->threads_per_atom == 1 || p->threads_per_atom == 2 ||
-                                p->threads_per_atom == 4 || p->threads_per_atom == 8);
+                                p->threads_per_atom == 4 || p->threads_per_atom == 8) &&
+         (p->resident == 0 || p->resident == 1);
 }
 
 int mdgp_set_md_params(mdgp_ctx* ctx, const mdgp_md_params* p) {
@@ -1470,6 +1547,7 @@ int mdgp_micro_launch_shape(const mdgp_ctx* ctx, int32_t* out) {
   out[1] = ctx->persist_threads;
   out[2] = ctx->persist_atoms;
   out[3] = ctx->persist_tpa;
+  out[4] = ctx->persist_resident ? 1 : 0;
   return MDGP_OK;
 }
 

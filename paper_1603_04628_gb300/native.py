@@ -46,7 +46,8 @@ class MDParams(ctypes.Structure):
                 ("wall_planes", ctypes.c_int32), ("list_capacity", ctypes.c_int32),
                 ("skin", ctypes.c_double), ("rebuild_every", ctypes.c_int32), ("build_variant", ctypes.c_int32),
                 ("persistent", ctypes.c_int32), ("wait_timeout_ms", ctypes.c_int32),
-                ("inject_barrier_skip", ctypes.c_int32), ("threads_per_atom", ctypes.c_int32)]
+                ("inject_barrier_skip", ctypes.c_int32), ("threads_per_atom", ctypes.c_int32),
+                ("resident", ctypes.c_int32)]
 
 
 class GPParams(ctypes.Structure):
@@ -354,10 +355,12 @@ class Context:
 
     def launch_shape(self):
         """The persistent step kernel's launch: blocks, threads per block,
-        atoms per block and threads per atom (mdgp_micro_launch_shape)."""
-        out = (ctypes.c_int32 * 4)()
+        atoms per block, threads per atom and whether the atoms are kept
+        resident (mdgp_micro_launch_shape)."""
+        out = (ctypes.c_int32 * 5)()
         _check(self.h, lib().mdgp_micro_launch_shape(self.h, out), "mdgp_micro_launch_shape")
-        return {"blocks": out[0], "threads": out[1], "atoms_per_block": out[2], "threads_per_atom": out[3]}
+        return {"blocks": out[0], "threads": out[1], "atoms_per_block": out[2], "threads_per_atom": out[3],
+                "resident": out[4]}
 
     def micro_state(self):
         x = np.zeros((self.n_atoms, 3))

@@ -415,6 +415,59 @@ def test_threads_per_atom_paper_mode_and_auto_choice(native):
     ctx.close()
 
 
+@pytest.mark.parametrize("tpa,persistent,cap", [(8, 1, 128), (4, 1, 128), (2, 2, 128), (2, 1, 256)])
+def test_resident_kernel_matches_the_general_one_bit_for_bit(native, tpa, persistent, cap):
+    # the small-batch kernel that keeps each atom's state in registers and
+    # its list in shared memory for a rebuild interval runs the same
+    # arithmetic in the same order as the general persistent kernel: after
+    # 300 steps (~30 rebuilds, each a fresh launch that reloads and writes
+    # back the state) positions and velocities are identical bit for bit.  The
+    # measurements are not part of the state: their per-atom terms are formed
+    # in FP32 (the compiler may fuse their multiply-adds differently in the
+    # two kernels) and summed by FP64 atomics in arbitrary order, so q, P_xx
+    # and T are held to 1e-6 relative, far inside their standard errors.  A
+    # list capacity of 256 puts the shared memory above the default 48 KB per
+    # block.
+    els = synth.batch_uneven(3, seed=29, steps=300)
+    out = []
+    for resident in (0, 1):
+        ctx = native.Context(0, native.PREC_FP32, threads_per_atom=tpa, persistent=persistent,
+                             list_capacity=cap, resident=resident)
+        ctx.micro_plan(els)
+        shape = ctx.launch_shape()
+        ctx.micro_launch()
+        res = ctx.micro_results()
+        x, v = ctx.micro_state()
+        out.append((shape, res, x, v, ctx.rebuild_count()))
+        ctx.close()
+    (sa, ra, xa, va, na), (sb, rb, xb, vb, nb) = out
+    assert sa["resident"] == 0 and sb["resident"] == 1
+    assert sa["threads_per_atom"] == sb["threads_per_atom"] == tpa
+    assert all(r["status"] == 0 for r in ra + rb)
+    assert na == nb > 10
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+    for a, b in zip(ra, rb):
+        for key in ("q", "p", "T_meas"):
+            assert a[key] == pytest.approx(b[key], rel=1e-6, abs=1e-12)
+
+
+def test_resident_kernel_only_where_it_applies(native):
+    # frozen walls (two phases per step), one thread per atom and batches
+    # whose blocks would stride over several chunks keep the general kernel
+    els = [dict(e, T=2.44, density=0.75, Lx=15.0, Lz=15.0) for e in synth.batch_uneven(2, seed=21, steps=20)]
+    ctx = native.Context(0, native.PREC_FP32, list_capacity=640, **PAPER_MODE)
+    ctx.micro_plan(els)
+    assert ctx.launch_shape()["threads_per_atom"] > 1
+    assert ctx.launch_shape()["resident"] == 0
+    ctx.close()
+    ctx = native.Context(0, native.PREC_FP32)
+    ctx.micro_plan([synth.element_plain(steps_eq=10, steps_sample=10)] * 2)
+    assert ctx.launch_shape()["resident"] == 1
+    ctx.micro_plan(synth.batch_uneven(64, steps=10))
+    assert ctx.launch_shape()["resident"] == 0
+    ctx.close()
+
+
 def test_full_uneven_batch_in_bench_configuration():
     # the 64-element batch exactly as bench.py launches it (FP32 pair forces,
     # double-float state, persistent step loop, default parameters), 100
@@ -499,24 +552,28 @@ def test_runs_are_reproducible(native, prec):
         assert a["q"] == pytest.approx(b["q"], rel=1e-12, abs=1e-14)   # FP64 atomics add the samples
 
 
-def test_barrier_timeout_is_reported_and_context_recovers(native):
+@pytest.mark.parametrize("resident", [0, 1])
+def test_barrier_timeout_is_reported_and_context_recovers(native, resident):
     # failure detection without a fault: one block of the persistent step
-    # kernel leaves out its first grid-barrier arrival (test-only switch), so
-    # every other block's bounded wait runs out after 50 ms of the GPU's
-    # global timer; the launch ends with MDGP_E_TIMEOUT on every element and
-    # the same context then runs the batch cleanly
+    # kernel (the general one and the resident-atom one) leaves out its first
+    # grid-barrier arrival (test-only switch), so every other block's bounded
+    # wait runs out after 50 ms of the GPU's global timer; the launch ends
+    # with MDGP_E_TIMEOUT on every element and the same context then runs the
+    # batch cleanly
     els = synth.batch_uneven(3, seed=41, steps=40)
-    ctx = native.Context(0, native.PREC_FP32, inject_barrier_skip=1, wait_timeout_ms=50)
+    ctx = native.Context(0, native.PREC_FP32, inject_barrier_skip=1, wait_timeout_ms=50, resident=resident)
     ctx.micro_plan(els)
+    assert ctx.launch_shape()["resident"] == resident
     ctx.micro_launch()
     res = ctx.micro_results()
     assert [r["status"] for r in res] == [-6] * len(els)
-    ctx.set_md_params(wait_timeout_ms=50)
+    ctx.set_md_params(wait_timeout_ms=50, resident=resident)
     ctx.micro_plan(els)
+    assert ctx.launch_shape()["resident"] == resident
     ctx.micro_launch()
     res = ctx.micro_results()
     assert all(r["status"] == 0 for r in res)
-    ref = native.Context(0, native.PREC_FP32).micro_batch(els)
+    ref = native.Context(0, native.PREC_FP32, resident=resident).micro_batch(els)
     for a, b in zip(res, ref):
         assert a["q"] == pytest.approx(b["q"], rel=1e-12, abs=1e-14)
     ctx.close()
