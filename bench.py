@@ -169,13 +169,19 @@ def main():
                     help="steps of the FP64-forces pass reported beside the headline")
     ap.add_argument("--steps-per-element", type=int, default=STEPS_PER_ELEMENT,
                     help="MD steps per element (shorter runs for profiling only)")
-    ap.add_argument("--case", default="micro", choices=["micro", "channel", "channel-evidence", "gp", "learned-mean"],
+    ap.add_argument("--case", default="micro",
+                    choices=["micro", "channel", "channel-evidence", "gp", "learned-mean", "small-batch"],
                     help="micro: the uneven micro-element batch (default; its line also carries the channel "
                          "case); channel: the full hybrid (Algorithm 1) threshold sweep on the 200-section channel "
                          "judged against the full MD; channel-evidence: the same judged with evidence "
                          "hyperparameters, warm starts and long equilibration; gp: the GP and MLP timings alone; "
                          "learned-mean: the MLP prior mean against the plain GP hybrid at matched thresholds, "
-                         "judged against the MD-everywhere run")
+                         "judged against the MD-everywhere run; small-batch: per-step time of the hybrid's MD "
+                         "batches (1-30 channel elements), general and resident-atom step kernels")
+    ap.add_argument("--elements", type=str, default="1,2,4,8,16,30",
+                    help="small-batch case: batch sizes (comma separated)")
+    ap.add_argument("--resident", type=str, default="0,1",
+                    help="small-batch case: step kernels to time (0 general, 1 resident atoms)")
     ap.add_argument("--channel-steps", type=int, default=100)
     ap.add_argument("--form", default="paper", choices=["paper", "linear"],
                     help="channel case: the paper's p-GP and (h, n, F) q-GP inputs (default), or a linear "
@@ -203,6 +209,8 @@ def main():
         return run_channel_evidence_case(args)
     if args.case == "learned-mean":
         return run_learned_mean_case(args)
+    if args.case == "small-batch":
+        return run_small_batch_case(args)
     if args.case == "gp":
         import torch
         torch.cuda.set_device(0)
@@ -603,6 +611,49 @@ def channel_case(device, n_steps=100, h_amp=0.5, paper_form=True, noise_run=True
                               "error_vs_full_md": out["reference_error_vs_full_md"],
                               "noise_error_two_runs": out.get("noise_error")},
             "rows": rows, "wall_s": time.perf_counter() - t_all}
+
+
+def run_small_batch_case(args):
+    """Per-step time of batches of the hybrid's MD elements (9.524 x h x 9.524,
+    h ~ U[6, 18], n = 0.8, 2000 + 3000 steps, FP32 forces), one JSON line per
+    batch size, step-loop path and kernel (bench.py --case small-batch)."""
+    import numpy as np
+    import torch
+    from paper_1603_04628_gb300 import native
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    box = 6.0 * 4.0 ** (1.0 / 3.0)
+    rng = np.random.default_rng(synth.BASE_SEED + 17)
+    pers = [args.persistent] if args.persistent is not None else [1, 2]
+    for nel in [int(v) for v in args.elements.split(",")]:
+        hs = rng.uniform(6.0, 18.0, nel)
+        els = [dict(h=float(h), Lx=box, Lz=box, density=0.8, T=1.1, g_ext=0.03, dpdx=0.0, steps_eq=2000,
+                    steps_sample=3000, seed=synth.BASE_SEED + 11 + k, id=k) for k, h in enumerate(hs)]
+        steps = 5000
+        for resident in [int(v) for v in args.resident.split(",")]:
+            for p in pers:
+                ctx = native.Context(0, native.PREC_FP32, stream=stream, persistent=p, resident=resident)
+                n = ctx.micro_plan(els)
+                ctx.micro_launch()
+                ctx.micro_results()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                ctx.micro_launch()
+                e1.record(stream)
+                e1.synchronize()
+                res = ctx.micro_results()
+                row = {"case": "small-batch", "elements": nel, "atoms": n, "persistent": p,
+                       "launch_shape": ctx.launch_shape(), "us_per_step": 1e3 * e0.elapsed_time(e1) / steps,
+                       "rebuilds": ctx.rebuild_count(), "clean": all(r["status"] == 0 for r in res),
+                       "q": [r["q"] for r in res]}
+                if p == 2:
+                    dt = ctx.direct_timing()
+                    row["kernel_us_per_step"] = 1e3 * dt["kernel_ms"] / max(1, dt["steps"])
+                    row["rebuild_us"] = 1e3 * dt["rebuild_ms"] / max(1, dt["rebuilds"])
+                print(json.dumps(row), flush=True)
+                ctx.close()
+    return 0
 
 
 def run_channel_case(args):
