@@ -6,9 +6,9 @@
 // its list count and list groups, the neighbour positions, its state, the
 // skin reference, then the grid barrier.  Between two list rebuilds none of
 // that changes except the positions, so this kernel loads it once per launch:
-// each atom's double-float position and velocity, tether anchor, skin
-// reference and element constants stay in registers, and the block's lists
-// are copied into shared memory.  A step then reads global memory only to
+// each atom's double-float position and velocity stay in registers, its
+// tether anchor, skin reference and element constants in a shared-memory
+// record, and the block's lists are copied into shared memory.  A step then reads global memory only to
 // gather the neighbour positions of the previous step (Eq. LJ), integrates
 // in registers (velocity Verlet for the fluid, G-JF Langevin for the
 // tethered walls, the body force as its own kick), publishes the new
@@ -28,7 +28,8 @@
 // walls (mode 0; the frozen-wall thermostat's two phases per step stay with
 // k_steps_persist), FP32 pair forces with the double-float state, and one
 // block per chunk of A atoms (the grid covers every atom once, no striding),
-// with A x list_cap x 4 bytes of dynamic shared memory.
+// with the dynamic shared memory of resident_smem_bytes (the lists, A x
+// list_cap x 4 bytes, and A slot records).
 #pragma once
 #include "md_kernels.cuh"
 
@@ -42,8 +43,9 @@ constexpr int kResDepth = 2;
 // own position me: up to kResDepth list groups per round are loaded and
 // their neighbour positions gathered before any is used, so one round trip
 // to the L2 serves them all (a lane of an eight-thread group has two or
-// three groups at the usual list lengths).  Groups are added in the order
-// sub, sub + TPA, sub + 2 TPA, ..., as in pair_force_f32.
+// three groups at the usual list lengths: one or two rounds; a depth of
+// three spills at the two-blocks-per-SM register budget).  Groups are added
+// in the order sub, sub + TPA, sub + 2 TPA, ..., as in pair_force_f32.
 template <bool UNIFORM, int TPA>
 __device__ __forceinline__ PairSum pair_force_resident(const float4& me, const float4* posj, const uint4* sl,
                                                        int A, int slot, int sub, int n, bool live,
