@@ -1079,7 +1079,8 @@ static int plan_impl(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int list_
       return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, persist_kernel(uni, frozen, tpa), threads, 0);
     };
     int tpa = ctx->params.threads_per_atom;
-    if (tpa <= 0) {
+    const bool auto_tpa = tpa <= 0;
+    if (auto_tpa) {
       int per_sm = 0;
       if (occupancy(1, 256, &per_sm) != cudaSuccess) return set_err(ctx, cudaGetLastError());
       const long long cap = (long long)sms * per_sm * 256;
@@ -1090,17 +1091,18 @@ static int plan_impl(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int list_
     ctx->persist_grid = 0;
     ctx->persist_resident = false;
     ctx->persist_smem = 0;
-    // One block per chunk of A atoms, R blocks per SM; the resident-atom
-    // kernel (tethered walls, several threads per atom) is tried first, with
-    // its lists' shared memory in the occupancy, then the general one.
+    // One block per chunk of A atoms, R blocks per SM, t threads per atom;
+    // the resident-atom kernel (tethered walls, several threads per atom) is
+    // tried first, with its lists' shared memory in the occupancy, then the
+    // general one.
     const int list_cap = ctx->B.list_cap;
     size_t res_max_smem = 0;   // dynamic shared memory a block of the resident kernel may take
-    auto search = [&](bool resident) -> cudaError_t {
+    auto search = [&](bool resident, int t) -> cudaError_t {
       long long best_warps = 1LL << 40;
       for (int R = 1; R <= 32; ++R) {
         const long long slots = (long long)sms * R;
         const long long A = (atoms + slots - 1) / slots;
-        const int T = (int)((A * tpa + 31) / 32 * 32);
+        const int T = (int)((A * t + 31) / 32 * 32);
         // at least 128 threads: smaller blocks put more separate atom ranges on
         // an SM and lose L1 reuse of the neighbour positions (measured slower)
         if (T > 256 || T < 128) continue;   // larger batches: 256-thread blocks striding over chunks
@@ -1108,8 +1110,8 @@ static int plan_impl(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int list_
         const size_t smem = resident ? resident_smem_bytes((int)A, list_cap) : 0;
         if (smem > res_max_smem && resident) continue;   // the lists do not fit
         const cudaError_t oe =
-            resident ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, resident_kernel(uni, tpa), T, smem)
-                     : occupancy(tpa, T, &per_sm);
+            resident ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, resident_kernel(uni, t), T, smem)
+                     : occupancy(t, T, &per_sm);
         if (oe != cudaSuccess) return oe;
         const long long warps = (long long)R * (T / 32);
         if (per_sm >= R && warps < best_warps) {
@@ -1117,49 +1119,56 @@ static int plan_impl(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int list_
           ctx->persist_atoms = (int)A;
           ctx->persist_threads = T;
           ctx->persist_grid = (unsigned)((atoms + A - 1) / A);
+          ctx->persist_tpa = t;
           ctx->persist_resident = resident;
           ctx->persist_smem = smem;
         }
       }
       return cudaSuccess;
     };
-    const bool try_resident = ctx->params.resident && !frozen && tpa > 1;
-    if (try_resident) {
-      // the lists may need more than the default 48 KB of dynamic shared memory
-      int optin = 0;
-      cudaFuncAttributes fa = {};
-      CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
-      CK(cudaFuncGetAttributes(&fa, resident_kernel(uni, tpa)));
-      res_max_smem = (size_t)(optin - (int)fa.sharedSizeBytes);
-      CK(cudaFuncSetAttribute(resident_kernel(uni, tpa), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)res_max_smem));
-      const cudaError_t se = search(true);
-      if (se != cudaSuccess) return set_err(ctx, se);
-    }
-    if (ctx->persist_grid == 0) {
-      const cudaError_t se = search(false);
-      if (se != cudaSuccess) return set_err(ctx, se);
-    }
-    if (ctx->persist_grid == 0) {
-      // 256-thread blocks of 256 / TPA atoms: batches too small for 128-thread
-      // blocks on every SM (one chunk per block; the resident kernel when its
-      // blocks all fit at once) and batches large enough to stride
-      const int A = 256 / tpa;
+    // 256-thread blocks of 256 / t atoms, one chunk per block, for batches too
+    // small for 128-thread blocks on every SM: the resident kernel when all
+    // its blocks fit at once
+    auto resident_small = [&](int t) -> cudaError_t {
+      const int A = 256 / t;
       const long long chunks = (atoms + A - 1) / A;
+      const size_t smem = resident_smem_bytes(A, list_cap);
+      if (smem > res_max_smem) return cudaSuccess;
       int per_sm = 0;
-      const size_t smem = try_resident ? resident_smem_bytes(A, list_cap) : 0;
-      if (try_resident && smem <= res_max_smem) {
-        const cudaError_t oe =
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, resident_kernel(uni, tpa), 256, smem);
-        if (oe != cudaSuccess) return set_err(ctx, oe);
-        if (chunks <= (long long)per_sm * sms) {
-          ctx->persist_atoms = A;
-          ctx->persist_threads = 256;
-          ctx->persist_grid = (unsigned)chunks;
-          ctx->persist_resident = true;
-          ctx->persist_smem = smem;
-        }
+      const cudaError_t oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, resident_kernel(uni, t), 256, smem);
+      if (oe != cudaSuccess) return oe;
+      if (chunks <= (long long)per_sm * sms) {
+        ctx->persist_atoms = A;
+        ctx->persist_threads = 256;
+        ctx->persist_grid = (unsigned)chunks;
+        ctx->persist_tpa = t;
+        ctx->persist_resident = true;
+        ctx->persist_smem = smem;
       }
+      return cudaSuccess;
+    };
+    if (ctx->params.resident && !frozen && tpa > 1) {
+      // with the automatic choice, the most threads per atom (from tpa down to
+      // two) at which the resident kernel fits: in small batches it beats more
+      // threads per atom with the general kernel
+      for (int t = tpa; t >= 2 && ctx->persist_grid == 0; t = auto_tpa ? t / 2 : 1) {
+        // the lists may need more than the default 48 KB of dynamic shared memory
+        int optin = 0;
+        cudaFuncAttributes fa = {};
+        CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+        CK(cudaFuncGetAttributes(&fa, resident_kernel(uni, t)));
+        res_max_smem = (size_t)(optin - (int)fa.sharedSizeBytes);
+        CK(cudaFuncSetAttribute(resident_kernel(uni, t), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)res_max_smem));
+        cudaError_t se = search(true, t);
+        if (se == cudaSuccess && ctx->persist_grid == 0) se = resident_small(t);
+        if (se != cudaSuccess) return set_err(ctx, se);
+      }
+    }
+    if (ctx->persist_grid == 0) {
+      ctx->persist_tpa = tpa;
+      const cudaError_t se = search(false, tpa);
+      if (se != cudaSuccess) return set_err(ctx, se);
     }
     if (ctx->persist_grid == 0) {
       int per_sm = 0;
