@@ -138,9 +138,11 @@ typedef struct {
                            other blocks' bounded waits run out; the launch then ends with
                            MDGP_E_TIMEOUT for every element and the context stays usable. */
   int32_t threads_per_atom; /* FP32 persistent step loop: threads that share one atom's pair
-                           loop, 1, 2, 4 or 8; 0 (default) = the largest that the batch fills
-                           (several only for batches too small to occupy every SM with one
-                           thread per atom).  Results differ only by the summation order. */
+                           loop, 1, 2, 4 or 8; 0 (default) = automatic: the largest that the
+                           batch fills (several only for batches too small to occupy every SM
+                           with one thread per atom), or, where the resident-atom kernel
+                           applies (see resident), the largest from there down to two at which
+                           it fits.  Results differ only by the summation order. */
   int32_t resident;     /* FP32 persistent step loop with several threads per atom and tethered
                            walls: 1 (default) = keep each atom's state and element constants in
                            registers and the block's lists in shared memory for a whole
