@@ -8,8 +8,10 @@
 // that changes except the positions, so this kernel loads it once per launch:
 // each atom's double-float position and velocity stay in registers, its
 // tether anchor, skin reference and element constants in a shared-memory
-// record, and the block's lists are copied into shared memory.  A step then reads global memory only to
-// gather the neighbour positions of the previous step (Eq. LJ), integrates
+// record, and the block's lists are staged into shared memory by bulk
+// asynchronous copies (one per list group, completed on an mbarrier whose
+// wait is bounded).  A step then reads global memory only to gather the
+// neighbour positions of the previous step (Eq. LJ), integrates
 // in registers (velocity Verlet for the fluid, G-JF Langevin for the
 // tethered walls, the body force as its own kick), publishes the new
 // position and meets the other blocks at the grid barrier.  The state is
@@ -83,6 +85,30 @@ __device__ __forceinline__ PairSum pair_force_resident(const float4& me, const f
     r.w = group_sum<TPA>(r.w);
   }
   return r;
+}
+
+// Bulk asynchronous copy (the TMA's one-dimensional form) of `bytes` from
+// global to this block's shared memory, completed on the mbarrier `bar`.
+// Both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ unsigned res_smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void res_bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               :: "r"(res_smem_addr(dst)), "l"(src), "r"(bytes), "r"(res_smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool res_mbar_try_wait(uint64_t* bar, unsigned phase) {
+  unsigned ok;
+  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+               : "=r"(ok) : "r"(res_smem_addr(bar)), "r"(phase) : "memory");
+  return ok != 0;
+}
+// Wait for phase 0 of bar, bounded by wait_ns of the global timer.
+__device__ __forceinline__ bool res_mbar_wait(uint64_t* bar, unsigned long long wait_ns) {
+  const unsigned long long t0 = global_ns();
+  while (!res_mbar_try_wait(bar, 0))
+    if (global_ns() - t0 > wait_ns) return false;
+  return true;
 }
 
 // What one atom keeps for a whole launch: its double-float state and list
@@ -202,21 +228,27 @@ __global__ void __launch_bounds__(256, 2) k_steps_resident(BatchDev B, PhysDev P
                                                           cudaGraphConditionalHandle h_more, int use_cond) {
   extern __shared__ __align__(16) uint4 s_list[];
   __shared__ ShiftTab tab;
+  __shared__ uint64_t s_bar;
   shift_tab_init(tab);
   const int slot = (int)threadIdx.x / TPA, sub = (int)threadIdx.x % TPA;
   const long long N = B.n_atoms;
   const long long i = slot < A ? (long long)blockIdx.x * A + slot : N;
   const bool live = i < N;
   const bool owner = live && sub == 0;
-  // the block's lists, group g of atom slot a at s_list[g A + a]
-  {
+  // the block's lists, group g of atom slot a at s_list[g A + a]: group g of
+  // the block's atoms is one contiguous run of 16-byte entries in the
+  // [group][atom] layout, so one bulk copy per group stages it
+  const long long a0 = (long long)blockIdx.x * A;
+  const int nslot = (int)(N - a0 < A ? N - a0 : A);   // >= 1: the grid covers the atoms once
+  if (threadIdx.x == 0) {
     const int G = B.list_cap >> 2;
     const uint4* L4 = reinterpret_cast<const uint4*>(B.list);
-    for (int t = threadIdx.x; t < G * A; t += blockDim.x) {
-      const int g = t / A, sa = t - g * A;
-      const long long j = (long long)blockIdx.x * A + sa;
-      if (j < N) s_list[t] = ld_list4(L4 + (long long)g * N + j);
-    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(res_smem_addr(&s_bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 :: "r"(res_smem_addr(&s_bar)), "r"((unsigned)(G * nslot * 16)) : "memory");
+    for (int g = 0; g < G; ++g)
+      res_bulk_g2s(s_list + (size_t)g * A, L4 + (long long)g * N + a0, (unsigned)(nslot * 16), &s_bar);
   }
   // the atoms' slot records follow the lists (16-byte aligned: list_cap is a
   // multiple of four entries)
@@ -254,9 +286,14 @@ __global__ void __launch_bounds__(256, 2) k_steps_resident(BatchDev B, PhysDev P
     c.esh0 = (float)P.eshift[spi]; c.esh1 = (float)P.eshift[spi + 1];
     c.act0 = P.active[spi] != 0; c.act1 = P.active[spi + 1] != 0;
   }
-  __syncthreads();
+  __syncthreads();   // the mbarrier is initialised before anyone waits on it
+  // a copy that has not landed within the wait limit ends this block's run
+  // (after a second bounded wait for the copies in flight): the other blocks'
+  // barrier waits then run out and the launch ends with MDGP_E_TIMEOUT
+  const bool staged = __syncthreads_and(res_mbar_wait(&s_bar, P.wait_ns) ? 1 : 0) != 0;
+  if (!staged) res_mbar_wait(&s_bar, P.wait_ns);
   long long s = *B.step_base;
-  bool rebuild = false, failed = false, first_wait = true;
+  bool rebuild = false, failed = !staged, first_wait = true;
   unsigned long long bar_target = threadIdx.x == 0 ? grid_barrier_base(B.flags) : 0ull;
   while (s < S && !failed) {
     if (blockIdx.x == 0 && threadIdx.x == 0) B.flags[kFlagSkin + (int)((s + 1) % 3)] = 0;
