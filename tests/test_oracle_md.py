@@ -425,6 +425,44 @@ def test_body_force_from_pressure_gradient():
     assert p.g == pytest.approx(0.01 + 0.05, rel=1e-15)
 
 
+def _crn_run(args):
+    g, seed, steps = args
+    el = dict(h=12.0, Lx=7.5, Lz=7.5, density=0.8, T=1.1, g=g, steps_eq=0, steps_sample=steps, seed=seed, id=seed)
+    r = md.element(md.make_params(el))
+    return r["q"], r["n_fluid"], r["status"]
+
+
+def test_linear_response_with_common_random_numbers():
+    # start-up from the lattice under body forces 0, g and 2g with the same
+    # seed: the three runs share the initial state and every thermostat
+    # random number, so over half a time unit (100 steps, before the chaotic
+    # dynamics separates them) their thermal fluctuations coincide and
+    #  - the second difference q(2g) - 2 q(g) + q(0), zero under linear
+    #    response, stays below 1e-3 of the first difference q(2g) - q(0)
+    #    (measured 6e-6 to 1.1e-4 over four seeds);
+    #  - the first difference is the fluid's momentum balance: free
+    #    acceleration adds 2g k dt / m to every fluid atom's v_x after k
+    #    steps, so q = (m / L_x) sum v_x averaged over steps 1..K gives
+    #    N_f 2g dt (K + 1) / (2 L_x), less the momentum the tethered walls
+    #    have taken up, a few per cent this early (measured 0.971-0.979)
+    import multiprocessing as mpr
+    md.build()
+    g, K, seeds = 0.02, 100, [600 + k for k in range(4)]
+    jobs = [(gg, sd, K) for sd in seeds for gg in (0.0, g, 2 * g)]
+    with mpr.get_context("spawn").Pool(6) as pool:
+        res = pool.map(_crn_run, jobs)
+    assert all(r[2] == 0 for r in res)
+    dt = md.make_params(dict(h=12.0, Lx=7.5, Lz=7.5, density=0.8, T=1.1, steps_eq=0, steps_sample=K)).dt
+    for k in range(len(seeds)):
+        (q0, nf, _), (q1, _, _), (q2, _, _) = res[3 * k:3 * k + 3]
+        first, second = q2 - q0, q2 - 2.0 * q1 + q0
+        free = nf * 2 * g * dt * (K + 1) / (2 * 7.5)
+        print("seed %d: first %.5f second %.2e (%.1e of first), first / free acceleration %.4f"
+              % (seeds[k], first, second, second / first, first / free))
+        assert abs(second) < 1e-3 * abs(first)
+        assert 0.95 < first / free < 1.0
+
+
 def _lr_run(args):
     g, seed = args
     el = dict(h=12.0, Lx=7.5, Lz=7.5, density=0.8, T=1.1, g=g, steps_eq=1000, steps_sample=3000, seed=seed, id=seed)
