@@ -1071,7 +1071,9 @@ static int plan_impl(mdgp_ctx* ctx, const mdgp_element* el, int64_t n, int list_
     // atom, is the largest power of two up to 8 with N x TPA threads within
     // the SMs' capacity for this kernel (one thread per atom for batches that
     // fill the GPU; several share an atom's pair loop in smaller ones, which
-    // shortens the step's critical path) unless the parameters fix it.
+    // shortens the step's critical path) unless the parameters fix it; where
+    // the resident-atom kernel applies, the automatic choice steps down from
+    // there to the most threads per atom at which that kernel fits.
     int sms = 0;
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
     const bool uni = ctx->P.uniform != 0, frozen = ctx->params.mode == 1;
