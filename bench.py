@@ -352,6 +352,17 @@ def main():
     hybrid = None
     if rank == 0 and world == 1 and args.workload == "uneven" and not args.no_hybrid:
         hybrid = channel_case(local, h_amp=args.h_amp, noise_run=False)
+    small = None
+    if rank == 0 and world == 1 and args.workload == "uneven" and not args.no_hybrid:
+        # the hybrid's MD batch sizes with either step kernel (graph path);
+        # a failure here is reported in the key, not in the headline
+        try:
+            small = [{k: r[k] for k in ("elements", "atoms", "us_per_step", "rebuilds", "clean")}
+                     | {"threads_per_atom": r["launch_shape"]["threads_per_atom"],
+                        "resident": r["launch_shape"]["resident"]}
+                     for r in small_batch_rows(local, [1, 2, 8], [0, 1], [1])]
+        except Exception as exc:   # noqa: BLE001
+            small = {"error": repr(exc)}
 
     cpu = None
     if pool is not None:
@@ -408,6 +419,7 @@ def main():
             "fp64_forces": fp64,
             "gp_mlp": gp_mlp,
             "hybrid": hybrid,
+            "small_batch": small,
             "element_status_errors": len(bad),
             "element_status_codes": sorted(set(bad)),
             "list_capacity": cap,
@@ -613,26 +625,26 @@ def channel_case(device, n_steps=100, h_amp=0.5, paper_form=True, noise_run=True
             "rows": rows, "wall_s": time.perf_counter() - t_all}
 
 
-def run_small_batch_case(args):
+def small_batch_rows(device, elements, residents, paths):
     """Per-step time of batches of the hybrid's MD elements (9.524 x h x 9.524,
-    h ~ U[6, 18], n = 0.8, 2000 + 3000 steps, FP32 forces), one JSON line per
-    batch size, step-loop path and kernel (bench.py --case small-batch)."""
+    h ~ U[6, 18], n = 0.8, 2000 + 3000 steps, FP32 forces): one row per batch
+    size, step kernel (resident 0: the general one, 1: resident atoms where
+    it applies) and step-loop path (persistent 1 or 2)."""
     import numpy as np
     import torch
     from paper_1603_04628_gb300 import native
-    torch.cuda.set_device(0)
-    stream = torch.cuda.Stream()
+    stream = torch.cuda.Stream(device)
     box = 6.0 * 4.0 ** (1.0 / 3.0)
     rng = np.random.default_rng(synth.BASE_SEED + 17)
-    pers = [args.persistent] if args.persistent is not None else [1, 2]
-    for nel in [int(v) for v in args.elements.split(",")]:
+    rows = []
+    for nel in elements:
         hs = rng.uniform(6.0, 18.0, nel)
         els = [dict(h=float(h), Lx=box, Lz=box, density=0.8, T=1.1, g_ext=0.03, dpdx=0.0, steps_eq=2000,
                     steps_sample=3000, seed=synth.BASE_SEED + 11 + k, id=k) for k, h in enumerate(hs)]
         steps = 5000
-        for resident in [int(v) for v in args.resident.split(",")]:
-            for p in pers:
-                ctx = native.Context(0, native.PREC_FP32, stream=stream, persistent=p, resident=resident)
+        for resident in residents:
+            for p in paths:
+                ctx = native.Context(device, native.PREC_FP32, stream=stream, persistent=p, resident=resident)
                 n = ctx.micro_plan(els)
                 ctx.micro_launch()
                 ctx.micro_results()
@@ -643,16 +655,26 @@ def run_small_batch_case(args):
                 e1.record(stream)
                 e1.synchronize()
                 res = ctx.micro_results()
-                row = {"case": "small-batch", "elements": nel, "atoms": n, "persistent": p,
-                       "launch_shape": ctx.launch_shape(), "us_per_step": 1e3 * e0.elapsed_time(e1) / steps,
-                       "rebuilds": ctx.rebuild_count(), "clean": all(r["status"] == 0 for r in res),
-                       "q": [r["q"] for r in res]}
+                row = {"elements": nel, "atoms": n, "persistent": p, "launch_shape": ctx.launch_shape(),
+                       "us_per_step": 1e3 * e0.elapsed_time(e1) / steps, "rebuilds": ctx.rebuild_count(),
+                       "clean": all(r["status"] == 0 for r in res), "q": [r["q"] for r in res]}
                 if p == 2:
                     dt = ctx.direct_timing()
                     row["kernel_us_per_step"] = 1e3 * dt["kernel_ms"] / max(1, dt["steps"])
                     row["rebuild_us"] = 1e3 * dt["rebuild_ms"] / max(1, dt["rebuilds"])
-                print(json.dumps(row), flush=True)
+                rows.append(row)
                 ctx.close()
+    return rows
+
+
+def run_small_batch_case(args):
+    """bench.py --case small-batch: small_batch_rows as JSON lines."""
+    import torch
+    torch.cuda.set_device(0)
+    pers = [args.persistent] if args.persistent is not None else [1, 2]
+    for row in small_batch_rows(0, [int(v) for v in args.elements.split(",")],
+                                [int(v) for v in args.resident.split(",")], pers):
+        print(json.dumps({"case": "small-batch", **row}), flush=True)
     return 0
 
 
