@@ -264,6 +264,34 @@ def test_langevin_walls_reach_target_temperature():
     assert np.mean(temps) == pytest.approx(1.3, rel=0.03)
 
 
+def test_gjf_samples_a_harmonic_tether_exactly_at_large_steps():
+    # G-JF's defining property (Gronbech-Jensen and Farago, 2013): for a
+    # linear force the configurational distribution is exact at any stable
+    # time step, <(x - x0)^2> = T / kappa per axis, while the on-site velocity
+    # gives <v^2> = (T / m) (1 - Omega^2 dt^2 / 4), Omega^2 = kappa / m.  Wall
+    # atoms alone with the wall-wall interaction off are independent tethered
+    # oscillators (kappa = 150); at dt = 0.08, Omega dt = 0.98, both hold to
+    # 1 % (measured 1.002 and 1.002), where a scheme without G-JF's noise in
+    # the drift, with its coefficients a and b swapped, with gamma dt / m for
+    # gamma dt / (2 m) or with the noise short by sqrt(2) misses by 22-85 %.
+    T, dt, kappa = 1.3, 0.08, 150.0
+    p = md.make_params(small_element(density=0.0, T=T, seed=77), gamma_wall=1.0, eps_ww=0.0, dt=dt)
+    assert p.k_tether == kappa
+    x, v, a, sp = md.init(p)
+    assert (sp == 1).all()
+    md.simulate(p, x, v, a, sp, 0, 1000)
+    d2, v2 = [], []
+    for s in range(1000, 11000, 10):
+        md.simulate(p, x, v, a, sp, s, s + 10)
+        d = x - a
+        d[:, 0] -= p.Lx * np.round(d[:, 0] / p.Lx)
+        d[:, 2] -= p.Lz * np.round(d[:, 2] / p.Lz)
+        d2.append((d ** 2).mean())
+        v2.append((v ** 2).mean())
+    assert np.mean(d2) == pytest.approx(T / kappa, rel=0.01)
+    assert np.mean(v2) == pytest.approx(T / p.mass * (1.0 - kappa / p.mass * dt * dt / 4.0), rel=0.01)
+
+
 def test_body_force_drives_flow_in_its_direction():
     el = small_element(h=6.0, g=0.3, steps_eq=800, steps_sample=1600)
     r = md.element(md.make_params(el))
