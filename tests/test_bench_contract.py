@@ -40,3 +40,14 @@ def test_step_counters_are_used_only_for_the_captured_source(tmp_path, monkeypat
     assert bench.step_kernel_counters() is None
     monkeypatch.setattr(bench, "STEP_PROFILE", str(tmp_path / "missing.md"))
     assert bench.step_kernel_counters() is None
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    # under torchrun every rank starts bench.py; the reference arm (the host
+    # oracle) runs and prints on rank 0 alone, the other ranks exit 0 at once
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+                          "--steps", "1", "--warmup", "0", "--sample-steps", "5"], capture_output=True, text=True,
+                         timeout=300, cwd=ROOT, env=env)
+    assert out.returncode == 0, out.stderr
+    assert out.stdout.strip() == ""
